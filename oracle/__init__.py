@@ -1,0 +1,217 @@
+"""FP64 CPU oracle for Kirchhoff prestack migration (paper Sec. 3, Eq. 1).
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  The product (``paper_1204_1225_gb300``)
+never does, and this package never imports the product.
+
+The arithmetic lives in ``kh_oracle.c`` (plain C, double precision, OpenMP over image
+columns or traces); this module compiles it with gcc and wraps it with ctypes, and adds
+the textbook CGLS iteration in numpy for least-squares migration.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libkh_oracle.so")
+_SRC = os.path.join(_HERE, "kh_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no fast-math, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("ox", ctypes.c_double), ("oy", ctypes.c_double),
+                ("oz", ctypes.c_double), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("n_bins", ctypes.c_int),
+                ("bin_width", ctypes.c_double), ("vel", ctypes.c_int), ("v0", ctypes.c_double),
+                ("k", ctypes.c_double), ("weight", ctypes.c_int), ("r0", ctypes.c_double),
+                ("aperture", ctypes.c_double), ("nt", ctypes.c_int), ("t0", ctypes.c_double),
+                ("dt", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            L = ctypes.c_long
+            D = ctypes.POINTER(_Desc)
+            for name in ("ko_migrate", "ko_demigrate", "ko_vgrad"):
+                getattr(_lib, name).argtypes = [D, L, P, P, P, P, P, P]
+                getattr(_lib, name).restype = ctypes.c_int
+            _lib.ko_migrate_points.argtypes = [D, L, P, P, P, P, P, L, P, P]
+            _lib.ko_migrate_points.restype = ctypes.c_int
+            _lib.ko_bins.argtypes = [D, L, P, P, P, P, P]
+            _lib.ko_traveltime.argtypes = [D, L, P, P, P, P, P]
+            _lib.ko_count.argtypes = [D, L, P, P, P, P]
+            _lib.ko_count.restype = ctypes.c_longlong
+            _lib.ko_set_mutation.argtypes = [ctypes.c_int]
+            _lib.ko_set_threads.argtypes = [ctypes.c_int]
+            _lib.ko_max_threads.restype = ctypes.c_int
+    return _lib
+
+
+def desc(s) -> _Desc:
+    """Oracle descriptor from a ``Survey`` (any object with the same attribute names)."""
+    return _Desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
+                 s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1}[s.vel], s.v0, s.k,
+                 {"one": 0, "obliq": 1}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _hdr(s):
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return f(s.sx), f(s.sy), f(s.rx), f(s.ry)
+
+
+def set_mutation(m: int) -> None:
+    """Plant a deliberate mistake in the oracle (tests of the pins only); 0 restores it."""
+    lib().ko_set_mutation(int(m))
+
+
+def set_threads(n: int) -> None:
+    lib().ko_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().ko_max_threads())
+
+
+def bins(s) -> np.ndarray:
+    sx, sy, rx, ry = _hdr(s)
+    out = np.empty(s.ntr, dtype=np.int32)
+    lib().ko_bins(ctypes.byref(desc(s)), s.ntr, _ptr(sx), _ptr(sy), _ptr(rx), _ptr(ry), _ptr(out))
+    return out
+
+
+def traveltime(s, R, z, grad: bool = False):
+    """One-way time (and d/dv0, d/dk) from a surface point to distance R, depth z."""
+    R = np.asarray(R, dtype=np.float64)
+    z = np.ascontiguousarray(np.broadcast_to(np.asarray(z, dtype=np.float64), R.shape)).ravel()
+    R = np.ascontiguousarray(R).ravel()
+    T = np.empty_like(R)
+    gv = np.empty_like(R) if grad else None
+    gk = np.empty_like(R) if grad else None
+    lib().ko_traveltime(ctypes.byref(desc(s)), R.size, _ptr(R), _ptr(z), _ptr(T), _ptr(gv), _ptr(gk))
+    return (T, gv, gk) if grad else T
+
+
+def migrate(s, traces) -> np.ndarray:
+    """Eq. 1 for every image sample: returns float64 [n_bins, ny, nx, nz]."""
+    sx, sy, rx, ry = _hdr(s)
+    d = np.ascontiguousarray(traces, dtype=np.float64).reshape(s.ntr, s.nt)
+    img = np.empty(s.image_shape, dtype=np.float64)
+    rc = lib().ko_migrate(ctypes.byref(desc(s)), s.ntr, _ptr(sx), _ptr(sy), _ptr(rx), _ptr(ry),
+                          _ptr(d), _ptr(img))
+    assert rc == 0
+    return img
+
+
+def migrate_points(s, traces, flat_idx) -> np.ndarray:
+    """Eq. 1 at selected image samples (flat indices into [n_bins, ny, nx, nz])."""
+    sx, sy, rx, ry = _hdr(s)
+    d = np.ascontiguousarray(traces, dtype=np.float64).reshape(s.ntr, s.nt)
+    p = np.ascontiguousarray(flat_idx, dtype=np.int64)
+    out = np.empty(p.size, dtype=np.float64)
+    rc = lib().ko_migrate_points(ctypes.byref(desc(s)), s.ntr, _ptr(sx), _ptr(sy), _ptr(rx),
+                                 _ptr(ry), _ptr(d), p.size, _ptr(p), _ptr(out))
+    assert rc == 0
+    return out
+
+
+def demigrate(s, image) -> np.ndarray:
+    """The transpose of ``migrate``: returns float64 traces [ntr, nt]."""
+    sx, sy, rx, ry = _hdr(s)
+    m = np.ascontiguousarray(image, dtype=np.float64).reshape(s.image_shape)
+    out = np.empty((s.ntr, s.nt), dtype=np.float64)
+    rc = lib().ko_demigrate(ctypes.byref(desc(s)), s.ntr, _ptr(sx), _ptr(sy), _ptr(rx), _ptr(ry),
+                            _ptr(m), _ptr(out))
+    assert rc == 0
+    return out
+
+
+def vgrad(s, image, traces) -> np.ndarray:
+    """[dB/dv0, dB/dk] of B(m, D) = <m, migrate(D)>."""
+    sx, sy, rx, ry = _hdr(s)
+    m = np.ascontiguousarray(image, dtype=np.float64).reshape(s.image_shape)
+    d = np.ascontiguousarray(traces, dtype=np.float64).reshape(s.ntr, s.nt)
+    out = np.empty(2, dtype=np.float64)
+    rc = lib().ko_vgrad(ctypes.byref(desc(s)), s.ntr, _ptr(sx), _ptr(sy), _ptr(rx), _ptr(ry),
+                        _ptr(m), _ptr(d), _ptr(out))
+    assert rc == 0
+    return out
+
+
+def count(s) -> int:
+    """Eq. 2 work count: (image point, in-aperture trace) pairs with a valid offset bin."""
+    sx, sy, rx, ry = _hdr(s)
+    return int(lib().ko_count(ctypes.byref(desc(s)), s.ntr, _ptr(sx), _ptr(sy), _ptr(rx), _ptr(ry)))
+
+
+def arrival_times(points, s, trace_idx) -> np.ndarray:
+    """Two-way times source -> scatterer -> receiver (for trace synthesis), float64
+    [n_points, len(trace_idx)], using this oracle's traveltime."""
+    pts = np.asarray(points, dtype=np.float64)
+    j = np.asarray(trace_idx)
+    sx = s.sx[j].astype(np.float64)[None, :]
+    rx = s.rx[j].astype(np.float64)[None, :]
+    sy = (s.sy[j].astype(np.float64) if s.dim == 3 else np.zeros(j.size))[None, :]
+    ry = (s.ry[j].astype(np.float64) if s.dim == 3 else np.zeros(j.size))[None, :]
+    x, y, z = pts[:, 0:1], pts[:, 1:2], pts[:, 2:3]
+    if s.dim == 2:
+        y = np.zeros_like(y)
+    Rs = np.sqrt((x - sx) ** 2 + (y - sy) ** 2 + z ** 2)
+    Rr = np.sqrt((x - rx) ** 2 + (y - ry) ** 2 + z ** 2)
+    zz = np.broadcast_to(z, Rs.shape)
+    return (traveltime(s, Rs, zz) + traveltime(s, Rr, zz)).reshape(Rs.shape)
+
+
+def cgls(s, data, n_iter: int, m0=None):
+    """Textbook CGLS for min_m ||A m - d||^2 with A = demigrate, A^T = migrate, in FP64.
+
+    Returns (m, residual norms ||r_i||, normal-equation residual norms ||A^T r_i||)."""
+    d = np.asarray(data, dtype=np.float64)
+    m = np.zeros(s.image_shape) if m0 is None else np.array(m0, dtype=np.float64)
+    r = d - demigrate(s, m) if m0 is not None else d.copy()
+    g = migrate(s, r)
+    p = g.copy()
+    gamma = float(np.vdot(g, g))
+    rn, gn = [float(np.linalg.norm(r))], [float(np.sqrt(gamma))]
+    for _ in range(n_iter):
+        q = demigrate(s, p)
+        qq = float(np.vdot(q, q))
+        if qq == 0.0 or gamma == 0.0:
+            break
+        alpha = gamma / qq
+        m += alpha * p
+        r -= alpha * q
+        g = migrate(s, r)
+        gamma_new = float(np.vdot(g, g))
+        p = g + (gamma_new / gamma) * p
+        gamma = gamma_new
+        rn.append(float(np.linalg.norm(r)))
+        gn.append(float(np.sqrt(gamma)))
+    return m, np.array(rn), np.array(gn)

@@ -1,0 +1,395 @@
+/*
+ * FP64 CPU oracle for Kirchhoff prestack migration (Eq. 1 of "Distributed computing
+ * of Seismic Imaging Algorithms", Sec. 3).  TEST INFRASTRUCTURE ONLY: it is called
+ * by the tests, by smoke() and by the bench's CPU-baseline leg, never by the product
+ * path.  It shares no code, header or constant with the CUDA library.
+ *
+ * It evaluates the definitions by brute force over every (image point, trace) pair,
+ * in double precision, with no blocking or reordering:
+ *
+ *   I(x, X) = sum_traces W(x, x_s, x_r) * delta(X - |x_s - x_r|) * D(x_s, x_r, T(x,x_s) + T(x,x_r))
+ *                                                                          (Sec. 3, Eq. 1)
+ *
+ * The delta selects one offset bin per trace; D is read at t = T_s + T_r by linear
+ * interpolation; "traces close enough" (Sec. 3, after Eq. 2) is a hard aperture on the
+ * horizontal distance from the image column to the trace midpoint.  The paper gives no
+ * formula for T or W ("times/amplitude of propagation in the model", Sec. 3); the
+ * readings taken are:
+ *   T, constant v:      R / v0,  R = |x - x_a| (sources/receivers at z = 0, Sec. 2)
+ *   T, v(z) = v0 + k z:  T = (2/k) asinh(s),  s = k R / (2 sqrt(v0 (v0 + k z))),
+ *                        the closed form of the circular-ray traveltime, written as
+ *                        T = (R/g) h(s) with g = sqrt(v0 vz), h(s) = asinh(s)/s (series near 0)
+ *   W = 1, or W = 1/2 (cos th_s + cos th_r) R_s R_r / R0^2 with cos th = z / R
+ *                        (chord obliquity times spreading), W := 0 where |z| < 1e-6 |dz|.
+ * Decisions that turn floating point into a discrete choice are taken in the same
+ * precision as the GPU library: the offset bin in FP64, the aperture test in FP32
+ * with a fixed operation order (no contraction; compile with -ffp-contract=off).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int dim;                 /* 2 or 3 */
+    int nx, ny, nz;
+    double ox, oy, oz, dx, dy, dz;
+    int n_bins;
+    double bin_width;
+    int vel;                 /* 0 constant, 1 linear in z */
+    double v0, k;
+    int weight;              /* 0 W=1, 1 obliquity x spreading */
+    double r0;
+    double aperture;         /* <= 0: full aperture */
+    int nt;
+    double t0, dt;
+} ko_desc;
+
+/* Deliberate-mistake switch used only by the tests that show the pins catch errors.
+ * 0 = the oracle as written. */
+static int ko_mutation = 0;
+void ko_set_mutation(int m) { ko_mutation = m; }
+
+void ko_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int ko_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---- traveltime and its derivatives (Sec. 3: "times for propagation in the model") ---- */
+
+/* asinh(s)/s and its derivative; Taylor series of asinh for small |s|. */
+static void asinh_over_s(double s, double* h, double* hp)
+{
+    if (fabs(s) < 1e-2) {
+        double s2 = s * s;
+        *h = 1.0 - s2 / 6.0 + 3.0 * s2 * s2 / 40.0 - 5.0 * s2 * s2 * s2 / 112.0
+             + 35.0 * s2 * s2 * s2 * s2 / 1152.0;
+        *hp = s * (-1.0 / 3.0 + 3.0 * s2 / 10.0 - 15.0 * s2 * s2 / 56.0
+                   + 35.0 * s2 * s2 * s2 / 144.0);
+    } else {
+        *h = asinh(s) / s;
+        *hp = (1.0 / sqrt(1.0 + s * s) - *h) / s;
+    }
+}
+
+/* One-way time from a surface point (z = 0) to a point at distance R and depth z. */
+static void traveltime(const ko_desc* d, double R, double z, double* T, double* dTdv0, double* dTdk)
+{
+    if (d->vel == 0) {
+        *T = R / d->v0;
+        if (dTdv0) *dTdv0 = -R / (d->v0 * d->v0);
+        if (dTdk) *dTdk = 0.0;
+        return;
+    }
+    double v0 = d->v0, k = d->k;
+    double vz = v0 + k * z;
+    double g = sqrt(v0 * vz);
+    double s = k * R / (2.0 * g);
+    double h, hp;
+    asinh_over_s(s, &h, &hp);
+    *T = R / g * h;
+    if (dTdv0 || dTdk) {
+        /* g^2 = v0 vz: dg/dv0 = (vz + v0)/(2g), dg/dk = v0 z/(2g);
+         * s = k R/(2g): ds/dth = (R/2) (dk/dth g - k dg/dth) / g^2 */
+        double dg_dv0 = (vz + v0) / (2.0 * g);
+        double dg_dk = v0 * z / (2.0 * g);
+        double ds_dv0 = 0.5 * R * (-k * dg_dv0) / (g * g);
+        double ds_dk = 0.5 * R * (g - k * dg_dk) / (g * g);
+        double a = -R / (g * g) * h, b = R / g * hp;
+        if (ko_mutation == 5) b = -b;
+        if (dTdv0) *dTdv0 = a * dg_dv0 + b * ds_dv0;
+        if (dTdk) *dTdk = a * dg_dk + b * ds_dk;
+    }
+}
+
+int ko_traveltime(const ko_desc* d, long n, const double* R, const double* z, double* T,
+                  double* dTdv0, double* dTdk)
+{
+    for (long i = 0; i < n; ++i)
+        traveltime(d, R[i], z[i], &T[i], dTdv0 ? &dTdv0[i] : NULL, dTdk ? &dTdk[i] : NULL);
+    return 0;
+}
+
+/* Amplitude weight W(x, x_s, x_r) (Sec. 3, Eq. 1). */
+static double weight(const ko_desc* d, double z, double Rs, double Rr)
+{
+    if (d->weight == 0 || ko_mutation == 1) return 1.0;
+    if (fabs(z) < 1e-6 * fabs(d->dz)) return 0.0;
+    double cs = z / Rs, cr = z / Rr;
+    return 0.5 * (cs + cr) * Rs * Rr / (d->r0 * d->r0);
+}
+
+/* ---- offset bin (the delta(X - |x_s - x_r|) of Eq. 1), decided in FP64 ---- */
+static int offset_bin(const ko_desc* d, float sx, float sy, float rx, float ry)
+{
+    double ex = (double)sx - (double)rx;
+    double ey = (d->dim == 3) ? (double)sy - (double)ry : 0.0;
+    double X = sqrt(ex * ex + ey * ey);
+    double q = X / d->bin_width;
+    double b = floor(q);
+    if (ko_mutation == 4) b = floor(q + 0.5);
+    if (b < (double)d->n_bins) return (int)b;
+    if (X == (double)d->n_bins * d->bin_width) return d->n_bins - 1;
+    return -1;
+}
+
+int ko_bins(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
+            const float* ry, int* bin)
+{
+    for (long j = 0; j < ntr; ++j)
+        bin[j] = offset_bin(d, sx[j], d->dim == 3 ? sy[j] : 0.f, rx[j], d->dim == 3 ? ry[j] : 0.f);
+    return 0;
+}
+
+/* ---- aperture ("traces close enough", Sec. 3), decided in FP32 with a fixed order ---- */
+static float col_coord(double o, int i, double h) { return (float)(o + (double)i * h); }
+
+static int inside_aperture(const ko_desc* d, float cx, float cy, float sx, float sy, float rx,
+                           float ry)
+{
+    if (d->aperture <= 0.0) return 1;
+    float mx = (sx + rx) * 0.5f;
+    float my = (sy + ry) * 0.5f;
+    float ex = cx - mx;
+    float ey = cy - my;
+    float ex2 = ex * ex;
+    float ey2 = ey * ey;
+    float d2 = ex2 + ey2;
+    float a2 = (float)(d->aperture * d->aperture);
+    return d2 <= a2;
+}
+
+/* ---- the contribution of one trace to one image point ---- */
+typedef struct {
+    int valid;      /* 0 <= tau <= nt-1 */
+    int i;          /* left sample */
+    double f;       /* fraction */
+    double W;
+    double dtau_dv0, dtau_dk;
+} contrib;
+
+static contrib contribution(const ko_desc* d, double x, double y, double z, double sx, double sy,
+                            double rx, double ry, int want_grad)
+{
+    contrib c;
+    memset(&c, 0, sizeof c);
+    double Rs = sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy) + z * z);
+    double Rr = sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry) + z * z);
+    if (ko_mutation == 3) Rr = Rs;
+    double Ts, Tr, dsv, dsk, drv, drk;
+    traveltime(d, Rs, z, &Ts, want_grad ? &dsv : NULL, want_grad ? &dsk : NULL);
+    traveltime(d, Rr, z, &Tr, want_grad ? &drv : NULL, want_grad ? &drk : NULL);
+    double tau = (Ts + Tr - d->t0) / d->dt;
+    if (ko_mutation == 2) tau = (Ts + Tr + d->t0) / d->dt;
+    if (!(tau >= 0.0 && tau <= (double)(d->nt - 1))) return c;
+    int i = (int)floor(tau);
+    if (i > d->nt - 2) i = d->nt - 2;
+    c.valid = 1;
+    c.i = i;
+    c.f = tau - (double)i;
+    if (ko_mutation == 6) c.f = 1.0 - c.f;
+    c.W = weight(d, z, Rs, Rr);
+    if (want_grad) {
+        c.dtau_dv0 = (dsv + drv) / d->dt;
+        c.dtau_dk = (dsk + drk) / d->dt;
+    }
+    return c;
+}
+
+static inline float hdr(const float* a, long j) { return a ? a[j] : 0.f; }
+
+/* Migration, Eq. 1: image[b][iy][ix][iz] = sum over traces j of bin b in aperture of
+ * W * ((1-f) D_j[i] + f D_j[i+1]).  traces: ntr x nt, image: n_bins x ny x nx x nz. */
+int ko_migrate(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
+               const float* ry, const double* traces, double* image)
+{
+    const long ncol = (long)d->nx * d->ny, nz = d->nz, nt = d->nt;
+    int* bin = (int*)malloc(sizeof(int) * (ntr > 0 ? ntr : 1));
+    if (!bin) return 1;
+    ko_bins(d, ntr, sx, sy, rx, ry, bin);
+    memset(image, 0, sizeof(double) * (size_t)d->n_bins * ncol * nz);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long c = 0; c < ncol; ++c) {
+        int iy = (int)(c / d->nx), ix = (int)(c % d->nx);
+        double x = d->ox + ix * d->dx, y = (d->dim == 3) ? d->oy + iy * d->dy : 0.0;
+        float cx = col_coord(d->ox, ix, d->dx), cy = (d->dim == 3) ? col_coord(d->oy, iy, d->dy) : 0.f;
+        for (long j = 0; j < ntr; ++j) {
+            if (bin[j] < 0) continue;
+            float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
+            if (d->dim == 2) { fsy = 0.f; fry = 0.f; }
+            if (!inside_aperture(d, cx, cy, fsx, fsy, frx, fry)) continue;
+            const double* D = traces + j * nt;
+            double* out = image + ((long)bin[j] * ncol + c) * nz;
+            for (long iz = 0; iz < nz; ++iz) {
+                double z = d->oz + iz * d->dz;
+                contrib q = contribution(d, x, y, z, fsx, fsy, frx, fry, 0);
+                if (!q.valid) continue;
+                double val = (1.0 - q.f) * D[q.i] + q.f * D[q.i + 1];
+                out[iz] += q.W * val;
+            }
+        }
+    }
+    free(bin);
+    return 0;
+}
+
+/* Migration at a list of image samples (flat indices into the n_bins x ny x nx x nz image). */
+int ko_migrate_points(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
+                      const float* ry, const double* traces, long npts, const long* pidx,
+                      double* out)
+{
+    const long ncol = (long)d->nx * d->ny, nz = d->nz, nt = d->nt;
+    int* bin = (int*)malloc(sizeof(int) * (ntr > 0 ? ntr : 1));
+    if (!bin) return 1;
+    ko_bins(d, ntr, sx, sy, rx, ry, bin);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long p = 0; p < npts; ++p) {
+        long q = pidx[p];
+        int iz = (int)(q % nz);
+        long c = (q / nz) % ncol;
+        int b = (int)(q / (nz * ncol));
+        int iy = (int)(c / d->nx), ix = (int)(c % d->nx);
+        double x = d->ox + ix * d->dx, y = (d->dim == 3) ? d->oy + iy * d->dy : 0.0;
+        double z = d->oz + iz * d->dz;
+        float cx = col_coord(d->ox, ix, d->dx), cy = (d->dim == 3) ? col_coord(d->oy, iy, d->dy) : 0.f;
+        double acc = 0.0;
+        for (long j = 0; j < ntr; ++j) {
+            if (bin[j] != b) continue;
+            float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
+            if (d->dim == 2) { fsy = 0.f; fry = 0.f; }
+            if (!inside_aperture(d, cx, cy, fsx, fsy, frx, fry)) continue;
+            contrib w = contribution(d, x, y, z, fsx, fsy, frx, fry, 0);
+            if (!w.valid) continue;
+            const double* D = traces + j * nt;
+            acc += w.W * ((1.0 - w.f) * D[w.i] + w.f * D[w.i + 1]);
+        }
+        out[p] = acc;
+    }
+    free(bin);
+    return 0;
+}
+
+/* Demigration: the exact transpose of ko_migrate ("each data sample is summed into the
+ * image at all the points where the measured time agrees", Sec. 3, read from the data
+ * side).  traces_out[j][i] += W (1-f) m, traces_out[j][i+1] += W f m. */
+int ko_demigrate(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
+                 const float* ry, const double* image, double* traces_out)
+{
+    const long ncol = (long)d->nx * d->ny, nz = d->nz, nt = d->nt;
+    int* bin = (int*)malloc(sizeof(int) * (ntr > 0 ? ntr : 1));
+    if (!bin) return 1;
+    ko_bins(d, ntr, sx, sy, rx, ry, bin);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long j = 0; j < ntr; ++j) {
+        double* D = traces_out + j * nt;
+        memset(D, 0, sizeof(double) * nt);
+        if (bin[j] < 0) continue;
+        float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
+        if (d->dim == 2) { fsy = 0.f; fry = 0.f; }
+        for (long c = 0; c < ncol; ++c) {
+            int iy = (int)(c / d->nx), ix = (int)(c % d->nx);
+            float cx = col_coord(d->ox, ix, d->dx), cy = (d->dim == 3) ? col_coord(d->oy, iy, d->dy) : 0.f;
+            if (!inside_aperture(d, cx, cy, fsx, fsy, frx, fry)) continue;
+            double x = d->ox + ix * d->dx, y = (d->dim == 3) ? d->oy + iy * d->dy : 0.0;
+            const double* m = image + ((long)bin[j] * ncol + c) * nz;
+            for (long iz = 0; iz < nz; ++iz) {
+                double z = d->oz + iz * d->dz;
+                contrib q = contribution(d, x, y, z, fsx, fsy, frx, fry, 0);
+                if (!q.valid) continue;
+                D[q.i] += q.W * (1.0 - q.f) * m[iz];
+                D[q.i + 1] += q.W * q.f * m[iz];
+            }
+        }
+    }
+    free(bin);
+    return 0;
+}
+
+/* Gradient of the bilinear form B(m, D) = sum_j sum_x W m[b_j, x] lerp(D_j, tau_j(x))
+ * with respect to (v0, k): dB/dth = sum W m (D_j[i+1] - D_j[i]) dtau/dth.  This is
+ * the velocity-model derivative that both the migration and the demigration operator
+ * need in their backward pass; out[0] = dB/dv0, out[1] = dB/dk. */
+int ko_vgrad(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
+             const float* ry, const double* image, const double* traces, double* out)
+{
+    const long ncol = (long)d->nx * d->ny, nz = d->nz, nt = d->nt;
+    int* bin = (int*)malloc(sizeof(int) * (ntr > 0 ? ntr : 1));
+    double* part = (double*)calloc((size_t)(ncol > 0 ? ncol : 1) * 2, sizeof(double));
+    if (!bin || !part) { free(bin); free(part); return 1; }
+    ko_bins(d, ntr, sx, sy, rx, ry, bin);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long c = 0; c < ncol; ++c) {
+        int iy = (int)(c / d->nx), ix = (int)(c % d->nx);
+        double x = d->ox + ix * d->dx, y = (d->dim == 3) ? d->oy + iy * d->dy : 0.0;
+        float cx = col_coord(d->ox, ix, d->dx), cy = (d->dim == 3) ? col_coord(d->oy, iy, d->dy) : 0.f;
+        double gv = 0.0, gk = 0.0;
+        for (long j = 0; j < ntr; ++j) {
+            if (bin[j] < 0) continue;
+            float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
+            if (d->dim == 2) { fsy = 0.f; fry = 0.f; }
+            if (!inside_aperture(d, cx, cy, fsx, fsy, frx, fry)) continue;
+            const double* D = traces + j * nt;
+            const double* m = image + ((long)bin[j] * ncol + c) * nz;
+            for (long iz = 0; iz < nz; ++iz) {
+                double z = d->oz + iz * d->dz;
+                contrib q = contribution(d, x, y, z, fsx, fsy, frx, fry, 1);
+                if (!q.valid) continue;
+                double slope = D[q.i + 1] - D[q.i];
+                gv += q.W * m[iz] * slope * q.dtau_dv0;
+                gk += q.W * m[iz] * slope * q.dtau_dk;
+            }
+        }
+        part[2 * c] = gv;
+        part[2 * c + 1] = gk;
+    }
+    out[0] = 0.0;
+    out[1] = 0.0;
+    for (long c = 0; c < ncol; ++c) {
+        out[0] += part[2 * c];
+        out[1] += part[2 * c + 1];
+    }
+    free(bin);
+    free(part);
+    return 0;
+}
+
+/* Work count of Eq. 2: number of (image point, in-aperture trace) pairs with a valid bin. */
+long long ko_count(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
+                   const float* ry)
+{
+    const long ncol = (long)d->nx * d->ny;
+    int* bin = (int*)malloc(sizeof(int) * (ntr > 0 ? ntr : 1));
+    if (!bin) return -1;
+    ko_bins(d, ntr, sx, sy, rx, ry, bin);
+    long long total = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : total)
+    for (long j = 0; j < ntr; ++j) {
+        if (bin[j] < 0) continue;
+        float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
+        if (d->dim == 2) { fsy = 0.f; fry = 0.f; }
+        long n = 0;
+        for (long c = 0; c < ncol; ++c) {
+            int iy = (int)(c / d->nx), ix = (int)(c % d->nx);
+            float cx = col_coord(d->ox, ix, d->dx), cy = (d->dim == 3) ? col_coord(d->oy, iy, d->dy) : 0.f;
+            n += inside_aperture(d, cx, cy, fsx, fsy, frx, fry);
+        }
+        total += (long long)n * d->nz;
+    }
+    free(bin);
+    return total;
+}

@@ -1,0 +1,340 @@
+"""Benchmark of the Kirchhoff migration hot path (Eq. 1) on GB300.
+
+One step = one full migration call through the C ABI: offset binning and sort of the
+traces, then the migration kernel over every (image tile, offset bin).  The metric is
+G image-point x trace contributions per second (Eq. 2: one contribution is one image point
+and one in-aperture trace; the count is exact, computed on the device).
+
+Default workload: 3D survey with v(z) = 1500 + 0.5 z (analytic linear-gradient
+traveltimes), 100 000 traces x 1500 FP32 samples at 4 ms, 256^3 image at 12.5 m, 16 offset
+bins of 100 m, 2 km aperture, obliquity x spreading weight.  Synthetic data: 20 Hz Ricker
+reflections from 4 seeded dipping planes (sheets of point scatterers every 100 m) and 40
+diffractors, arrival times from the library's traveltime kernel.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (bounded
+samples of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1204_1225_gb300 import survey as sv  # noqa: E402
+
+# Hardware figures for the ALU roofline (GB300): SM count, MUFU (special-function) results
+# per SM per clock.  The MUFU rate is the figure measured on this part by the throughput
+# probe summarised in profiles/mufu_fma_throughput.md.
+N_SM = 152
+MUFU_PER_SM_CLK = 16
+# Transcendental (MUFU) operations each contribution needs by construction of the kernel's
+# formula: square roots of the two ray lengths and of the two q(q + 2) terms, one log2.
+MUFU_PER_CONTRIB = {("const", "one"): 2, ("const", "obliq"): 2, ("linear", "one"): 3,
+                    ("linear", "obliq"): 5}
+
+
+def workloads():
+    return {
+        "3d-vz-100k-256cube": lambda: sv.survey_3d_gradient(),
+        "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
+        "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
+    }
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=ws)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        ident = str(self.dev)
+        try:
+            uuid = torch.cuda.get_device_properties(self.dev).uuid
+            ident = "GPU-" + str(uuid)
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            if vis:
+                ident = vis.split(",")[self.dev]
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", ident, "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def synth_traces(s, plan, device):
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    rng = np.random.default_rng(sv.BASE_SEED)
+    if s.dim == 3:
+        sc = sv.reflectors_3d(rng, s, spacing=100.0)
+        freq = 20.0
+    else:
+        sc = sv.point_scatterers_2d(rng, xr=(0.1 * s.nx * s.dx, 0.9 * s.nx * s.dx),
+                                    zr=(0.2 * s.nz * s.dz, 0.9 * s.nz * s.dz))
+        freq = 25.0
+    return sv.synthesize(s, sc, kh.arrival_times_fn(plan), freq, noise_sigma=0.0,
+                         device=device, chunk=1 << 23)
+
+
+def cpu_baseline(s, traces_cpu, target_s: float, seed: int):
+    """The FP64 oracle on a bounded sample of image points of the same workload."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    d64 = traces_cpu
+    probe = sv.sample_points(s, 64, seed)
+    t0 = time.perf_counter()
+    oracle.migrate_points(s, d64, probe)
+    t_probe = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(max(64, 64 * target_s / t_probe), np.prod(s.image_shape)))
+    pts = sv.sample_points(s, n, seed + 1)
+    t0 = time.perf_counter()
+    _, ncontrib = oracle.migrate_points(s, d64, pts, return_count=True)
+    el = time.perf_counter() - t0
+    return {"value": ncontrib / el / 1e9, "unit": "Gcontrib/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} random image samples of {s.name} (all bins), {ncontrib} contributions, "
+                      f"FP64 brute force, {el:.1f} s"}
+
+
+def run_reference(args, s):
+    """Reference arm: the FP64 CPU oracle, each step a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    rng_traces = sv.random_traces(s, sv.BASE_SEED, smooth=0) if s.ntr * s.nt < 2e8 else None
+    if rng_traces is None:
+        rng_traces = np.random.default_rng(sv.BASE_SEED).standard_normal((s.ntr, s.nt)).astype(np.float32)
+    d64 = rng_traces.astype(np.float64)
+    del rng_traces
+    probe = sv.sample_points(s, 32, 7)
+    t0 = time.perf_counter()
+    oracle.migrate_points(s, d64, probe)
+    t_probe = max(time.perf_counter() - t0, 1e-3)
+    per_step = float(os.environ.get("KH_REF_STEP_S", "8"))
+    n = int(min(max(32, 32 * per_step / t_probe), np.prod(s.image_shape)))
+    for w in range(args.warmup):
+        oracle.migrate_points(s, d64, sv.sample_points(s, max(8, n // 8), 100 + w))
+    tot_c, tot_t = 0, 0.0
+    for k in range(args.steps):
+        pts = sv.sample_points(s, n, 1000 + k)
+        t0 = time.perf_counter()
+        _, c = oracle.migrate_points(s, d64, pts, return_count=True)
+        tot_t += time.perf_counter() - t0
+        tot_c += c
+    v = tot_c / tot_t / 1e9
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": "G image-point x trace contributions/s", "value": v,
+            "unit": "Gcontrib/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": s.name, "sample_points_per_step": n},
+            "cpu_baseline": {"value": v, "unit": "Gcontrib/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} random image samples per step of {s.name}"},
+            "e2e": {"value": v, "unit": "Gcontrib/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d-vz-100k-256cube", choices=sorted(workloads()))
+    ap.add_argument("--fast-math", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_init()
+    s = workloads()[args.workload]()
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, s)
+        return
+
+    from paper_1204_1225_gb300 import build as khbuild
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    khbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    plan = kh.Plan(s, fast_math=bool(args.fast_math))
+    hdr = kh.Headers.of(s, device=dev)
+    traces = synth_traces(s, plan, dev).contiguous()
+    image = torch.empty(plan.image_shape, dtype=torch.float32, device=dev)
+    contrib = plan.count(hdr)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        plan.migrate(hdr, traces, out=image)
+    plan.sync()
+    plan.profile(True)
+    plan.profile_read()
+    launches0 = plan.launches
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.migrate(hdr, traces, out=image)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    plan.sync()
+    launches = plan.launches - launches0
+    kern_ms, kern_n = plan.profile_read()
+    plan.profile(False)
+    t_ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    barrier(ws)
+    value = contrib * args.steps * ws / (t_ms / 1e3) / 1e9
+    clocks = clk.summary()
+
+    # end to end through the public API: pinned host inputs in, image back to pinned host
+    e2e = None
+    if not args.no_e2e:
+        h_tr = traces.cpu().pin_memory()
+        h_hdr = [t.cpu().pin_memory() for t in hdr.args()]
+        h_img = torch.empty(plan.image_shape, dtype=torch.float32).pin_memory()
+        d_tr = torch.empty_like(traces)
+        d_hdr = kh.Headers(*[torch.empty_like(t) for t in hdr.args()], device=dev)
+        h2d = h_tr.numel() * 4 + sum(t.numel() * 4 for t in h_hdr)
+        d2h = h_img.numel() * 4
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            d_tr.copy_(h_tr, non_blocking=True)
+            for dst, src in zip(d_hdr.args(), h_hdr):
+                dst.copy_(src, non_blocking=True)
+            plan.migrate(d_hdr, d_tr, out=image)
+            h_img.copy_(image, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        plan.sync()
+        te = max_over_ranks(ws, e0.elapsed_time(e1))
+        e2e = {"value": contrib * args.steps * ws / (te / 1e3) / 1e9, "unit": "Gcontrib/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        del h_tr, h_img, d_tr
+
+    if rank != 0:
+        return
+    # ALU roofline of the migration kernel: contributions/s that the MUFU pipe allows at
+    # the median SM clock of the timed region, given the transcendentals per contribution.
+    mufu = MUFU_PER_CONTRIB[(s.vel if s.k != 0 or s.vel == "const" else "const", s.weight)]
+    clk_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = N_SM * MUFU_PER_SM_CLK * clk_mhz * 1e6 / mufu / 1e9
+    achieved = contrib / (kern_ms / max(kern_n, 1) / 1e3) / 1e9 if kern_n else None
+    roof = {"bound": "alu", "kernel": "k_migrate", "achieved": achieved, "peak": peak,
+            "unit": "Gcontrib/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": None,
+            "peak_basis": f"{N_SM} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {clk_mhz:.0f} MHz (median "
+                          f"SM clock of the timed region) / {mufu} MUFU ops per contribution",
+            "kernel_ms_per_launch": kern_ms / max(kern_n, 1)}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(s, traces.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)
+    line = {
+        "metric": "G image-point x trace contributions/s", "value": value, "unit": "Gcontrib/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": s.name, "image": list(plan.image_shape), "ntr": s.ntr, "nt": s.nt,
+                   "velocity": f"{s.vel} v0={s.v0} k={s.k}", "weight": s.weight,
+                   "aperture_m": s.aperture, "contributions_per_step": contrib,
+                   "fast_math": bool(args.fast_math),
+                   "l2": "inputs larger than L2 (traces %.0f MB, image %.0f MB)" % (
+                       traces.numel() * 4 / 1e6, image.numel() * 4 / 1e6),
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

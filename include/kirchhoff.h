@@ -1,0 +1,206 @@
+/*
+ * kirchhoff.h -- C ABI of a GB300 (sm_103a) library for Kirchhoff prestack migration.
+ *
+ * The operation is Eq. (1), Sec. 3 of "Distributed computing of Seismic Imaging
+ * Algorithms":
+ *
+ *     I(x, X) = integral dx_s dx_r W(x, x_s, x_r) delta(X - |x_s - x_r|) D(x_s, x_r, T(x,x_s) + T(x,x_r))
+ *
+ * evaluated as a sum over recorded traces (Sec. 3: "each data sample is summed into the
+ * image at all the points where the measured time agrees with the total propagation
+ * time"), one offset image per offset bin, at the cost f_K N_xyz N_tr of Eq. (2) where
+ * N_tr counts the traces "close enough" to the image point (a horizontal aperture).
+ *
+ * Conventions shared by every entry point
+ *  - Every array argument is a DEVICE pointer owned by the caller unless stated.  Trace
+ *    headers are FP32 metres: source (sx, sy), receiver (rx, ry), all at the surface
+ *    z = 0 (Sec. 2).  For dim == 2, sy and ry may be NULL and are treated as 0.
+ *  - Traces are row-major [ntr][nt] (time fastest) of the plan's trace dtype.
+ *  - Images are FP32 row-major [n_bins][ny][nx][nz] (z fastest); ny == 1 for dim == 2.
+ *  - Calls are asynchronous on `cuda_stream` (a cudaStream_t, NULL = legacy default
+ *    stream).  Outputs are overwritten, never accumulated.  A plan may be used by one
+ *    thread at a time.
+ *  - Every failure returns a status code and sets a thread-local message readable with
+ *    kirchhoff_last_error(); nothing aborts or traps.  Errors raised inside a kernel
+ *    (a bounded wait that ran out) are reported by kirchhoff_sync(), which waits for the
+ *    plan's work on the stream.
+ *  - The plan owns its device workspace (trace sort order, headers, padded traces,
+ *    traveltime tables); it grows on demand and is freed by kirchhoff_destroy().
+ */
+#ifndef KIRCHHOFF_H
+#define KIRCHHOFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KH_API __attribute__((visibility("default")))
+#else
+#define KH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KH_OK = 0,
+    KH_ERR_INVALID_ARG = 1,  /* NULL pointer, bad size, misaligned pointer, bad enum */
+    KH_ERR_UNSUPPORTED = 2,  /* valid but not implemented (e.g. v(z) <= 0 inside the grid) */
+    KH_ERR_OOM = 3,          /* device allocation for the plan workspace failed */
+    KH_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    KH_ERR_TIMEOUT = 5,      /* a bounded in-kernel wait ran out; results are invalid */
+    KH_ERR_INTERNAL = 6
+} kh_status;
+
+typedef enum { KH_F32 = 0, KH_F16 = 1, KH_BF16 = 2 } kh_dtype;
+
+/* Traveltime T(x, x_a) from a surface point x_a to an image point x (Sec. 3: "times for
+ * propagation in the model"; the paper gives no formula):
+ *  KH_VEL_CONST:    T = R / v0, R = |x - x_a|.
+ *  KH_VEL_LINEAR_Z: v(z) = v0 + k z, the circular-ray closed form
+ *                   T = (2/k) asinh(k R / (2 sqrt(v0 (v0 + k z)))), evaluated as
+ *                   T = arccosh(1 + q) / k, q = k^2 R^2 / (2 v0 (v0 + k z)).
+ *  KH_VEL_TABLE:    T read from per-location tables on a coarse grid (table_spacing),
+ *                   built from the LINEAR_Z closed form with the plan's v0, k, stored
+ *                   as table_dtype, interpolated linearly in FP32. */
+typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2 } kh_vel;
+
+/* Weight W(x, x_s, x_r) of Eq. (1) ("amplitude of propagation"; no formula in the paper):
+ *  KH_W_ONE:          W = 1.
+ *  KH_W_OBLIQ_SPREAD: W = 1/2 (cos th_s + cos th_r) R_s R_r / r0^2 with cos th = z / R
+ *                     (chord obliquity times spreading) = z (R_s + R_r) / (2 r0^2);
+ *                     W = 0 where |z| < 1e-6 |dz|. */
+typedef enum { KH_W_ONE = 0, KH_W_OBLIQ_SPREAD = 1 } kh_weight;
+
+typedef struct {
+    int dim;                 /* 2 or 3 */
+    int nx, ny, nz;          /* image samples; ny = 1 for dim = 2 */
+    double ox, oy, oz;       /* image origin, metres (z positive down from the surface) */
+    double dx, dy, dz;       /* image spacing, metres, > 0 */
+    int n_bins;              /* offset bins: X in [b w, (b+1) w) goes to bin b; X = n_bins w goes to
+                                the last bin; larger offsets are not imaged (Eq. 1's delta) */
+    double bin_width;        /* w > 0, metres */
+    kh_vel vel;
+    double v0, k;            /* v(z) = v0 + k z; k ignored for KH_VEL_CONST */
+    double table_spacing;    /* KH_VEL_TABLE: node spacing of the traveltime tables, metres */
+    kh_dtype table_dtype;    /* KH_VEL_TABLE: KH_F32 or KH_F16 (FP16 with per-table offset) */
+    kh_weight weight;
+    double r0;               /* spreading normaliser, metres (KH_W_OBLIQ_SPREAD) */
+    double aperture;         /* horizontal image-column to trace-midpoint distance limit, metres;
+                                <= 0 means every trace reaches every column ("traces close
+                                enough", Sec. 3 after Eq. 2) */
+    int nt;                  /* samples per trace, >= 2 */
+    double t0, dt;           /* time of sample 0 and sample interval, seconds */
+    kh_dtype trace_dtype;    /* storage type of the traces passed to migrate */
+} kh_desc;
+
+typedef struct kh_plan_s* kh_plan;
+
+/* Validates `d` and creates a plan.  On success *out owns host and device state.
+ * Returns KH_ERR_INVALID_ARG for a NULL pointer or out-of-range field and
+ * KH_ERR_UNSUPPORTED when v(z) <= 0 somewhere in [min(0, oz), oz + (nz-1) dz]. */
+KH_API kh_status kirchhoff_create(const kh_desc* d, kh_plan* out);
+
+/* Frees the plan and its device workspace (synchronises the device first).  NULL is a no-op. */
+KH_API kh_status kirchhoff_destroy(kh_plan p);
+
+/* Migration, Eq. (1): image[b][iy][ix][iz] = sum over traces j with offset bin b whose
+ * midpoint lies within the aperture of column (ix, iy) of
+ *     W * ((1 - f) D_j[i] + f D_j[i+1]),  tau = (T_s + T_r - t0)/dt, i = floor(tau), f = tau - i,
+ * for 0 <= tau <= nt-1 (at tau = nt-1: i = nt-2, f = 1); other tau contribute nothing.
+ * sx, sy, rx, ry: [ntr] FP32; traces: [ntr][nt] of the plan's trace_dtype, 16-byte
+ * aligned; image: [n_bins][ny][nx][nz] FP32, overwritten.  ntr == 0 gives a zero image.
+ * Accumulation is FP32; the result is bitwise reproducible run to run. */
+KH_API kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
+                            const float* ry, const void* traces, float* image, void* cuda_stream);
+
+/* Demigration: the transpose of kirchhoff_migrate for the same plan and headers (the
+ * same sum read from the data side, Sec. 3).  image: [n_bins][ny][nx][nz] FP32;
+ * traces_out: [ntr][nt] FP32, overwritten:
+ *     traces_out[j][i] += W (1-f) image[b_j][x],  traces_out[j][i+1] += W f image[b_j][x]. */
+KH_API kh_status kirchhoff_demigrate(kh_plan p, int ntr, const float* sx, const float* sy,
+                              const float* rx, const float* ry, const float* image,
+                              float* traces_out, void* cuda_stream);
+
+/* Derivative of the bilinear form B(m, D) = <m, migrate(D)> with respect to the
+ * velocity parameters (v0, k) of KH_VEL_LINEAR_Z (or v0 alone for KH_VEL_CONST):
+ *     dB/dth = sum W m[b_j][x] (D_j[i+1] - D_j[i]) dtau/dth,  dtau/dth = (dT_s/dth + dT_r/dth)/dt.
+ * It is the velocity-update gradient of the inverse flow (Sec. 4, Inverse PKTM) and serves
+ * the backward pass of both migrate and demigrate.  image: FP32 [n_bins][ny][nx][nz];
+ * traces: FP32 [ntr][nt]; out_dv0_dk: DEVICE double[2], overwritten.  Per-CTA FP64
+ * partials are reduced in a fixed order (bitwise reproducible).  KH_ERR_UNSUPPORTED for
+ * KH_VEL_TABLE. */
+KH_API kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, const float* sy,
+                                  const float* rx, const float* ry, const float* image,
+                                  const float* traces, double* out_dv0_dk, void* cuda_stream);
+
+/* Traveltime evaluation (the T of Eq. 1 under the plan's velocity model) for n
+ * elementwise (point, surface location) pairs: T[i] = T((px,py,pz)[i], (lx,ly)[i]).
+ * All arrays device FP32 [n]; ly/py may be NULL for dim 2. */
+KH_API kh_status kirchhoff_traveltime(kh_plan p, int n, const float* px, const float* py,
+                               const float* pz, const float* lx, const float* ly, float* T,
+                               void* cuda_stream);
+
+/* Work count of Eq. (2): number of (image point, trace) pairs with a valid offset bin
+ * and the trace midpoint within the aperture of the point's column, computed on the
+ * device with the same FP32 aperture test as the migration kernel.  *out_count is a
+ * HOST int64; the call synchronises `cuda_stream`. */
+KH_API kh_status kirchhoff_count(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
+                          const float* ry, int64_t* out_count, void* cuda_stream);
+
+/* One migration job of a batch (see kirchhoff_migrate_batched). */
+typedef struct {
+    kh_plan plan;            /* the job's plan (grid, bins, velocity, dtype) */
+    int ntr;
+    const float *sx, *sy, *rx, *ry;
+    const void* traces;
+    float* image;
+} kh_job;
+
+/* Migrates `njobs` independent jobs with ONE persistent kernel launch: a device work list
+ * of (job, tile, bin) items, longest first, pulled by persistent CTAs from one work
+ * counter (a scheduler counter, not an accumulation).  Results equal njobs calls of
+ * kirchhoff_migrate.  All plans must share the trace dtype and velocity kind.  The launch
+ * itself may be captured in a CUDA graph once kirchhoff_batched_prepare() has been called
+ * on the same job list (it sizes the workspace and uploads headers; it synchronises). */
+KH_API kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, void* cuda_stream);
+KH_API kh_status kirchhoff_migrate_batched(int njobs, const kh_job* jobs, void* cuda_stream);
+
+/* Waits for the plan's work on `cuda_stream` and returns KH_ERR_TIMEOUT if a bounded
+ * in-kernel wait ran out since the last call (clearing the flag), else KH_OK. */
+KH_API kh_status kirchhoff_sync(kh_plan p, void* cuda_stream);
+
+/* Tuning and test options of a plan (kirchhoff_set_option).
+ *  KH_OPT_WAIT_POLLS: limit every bounded in-kernel wait to `value` polls (0 restores the
+ *                     default, about two seconds of polling).  A test sets 1 to check that
+ *                     a wait which runs out returns KH_ERR_TIMEOUT with the context intact.
+ *  KH_OPT_FAST_MATH:  1 = hardware approximate sqrt/log2 in the hot loop, 0 = IEEE sqrt and
+ *                     the accurate log2 (default 1 after the accuracy study; both are
+ *                     parity-tested).
+ *  KH_OPT_TILE:       image tile of one CTA, encoded as cx | cy << 8 | cz << 16 (threads per
+ *                     CTA along x, y and z-groups, cx*cy*cz == 256; each thread owns 16
+ *                     consecutive z samples of one column); 0 restores the default. */
+typedef enum { KH_OPT_WAIT_POLLS = 1, KH_OPT_FAST_MATH = 2, KH_OPT_TILE = 3 } kh_option;
+KH_API kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value);
+
+/* Profiling: while enabled, CUDA events bracket the main kernel of every migrate /
+ * demigrate / gradient call of this plan on the call's stream.  kirchhoff_profile_read()
+ * waits for those events and returns the summed main-kernel time in milliseconds and the
+ * number of timed launches since the previous read, then resets both. */
+KH_API kh_status kirchhoff_profile(kh_plan p, int enable);
+KH_API kh_status kirchhoff_profile_read(kh_plan p, double* kernel_ms, long long* timed_launches);
+
+/* Number of kernel launches issued by this plan since creation (for launch accounting). */
+KH_API long long kirchhoff_launch_count(kh_plan p);
+
+/* Thread-local message of the last failure ("" if none). */
+KH_API const char* kirchhoff_last_error(void);
+
+/* Library version string. */
+KH_API const char* kirchhoff_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KIRCHHOFF_H */

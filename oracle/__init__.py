@@ -59,7 +59,7 @@ def lib():
             for name in ("ko_migrate", "ko_demigrate", "ko_vgrad"):
                 getattr(_lib, name).argtypes = [D, L, P, P, P, P, P, P]
                 getattr(_lib, name).restype = ctypes.c_int
-            _lib.ko_migrate_points.argtypes = [D, L, P, P, P, P, P, L, P, P]
+            _lib.ko_migrate_points.argtypes = [D, L, P, P, P, P, P, L, P, P, P]
             _lib.ko_migrate_points.restype = ctypes.c_int
             _lib.ko_bins.argtypes = [D, L, P, P, P, P, P]
             _lib.ko_traveltime.argtypes = [D, L, P, P, P, P, P]
@@ -130,16 +130,18 @@ def migrate(s, traces) -> np.ndarray:
     return img
 
 
-def migrate_points(s, traces, flat_idx) -> np.ndarray:
-    """Eq. 1 at selected image samples (flat indices into [n_bins, ny, nx, nz])."""
+def migrate_points(s, traces, flat_idx, return_count: bool = False):
+    """Eq. 1 at selected image samples (flat indices into [n_bins, ny, nx, nz]); with
+    ``return_count`` also the number of (point, in-aperture trace) pairs visited."""
     sx, sy, rx, ry = _hdr(s)
     d = np.ascontiguousarray(traces, dtype=np.float64).reshape(s.ntr, s.nt)
     p = np.ascontiguousarray(flat_idx, dtype=np.int64)
     out = np.empty(p.size, dtype=np.float64)
+    n = ctypes.c_longlong(0)
     rc = lib().ko_migrate_points(ctypes.byref(desc(s)), s.ntr, _ptr(sx), _ptr(sy), _ptr(rx),
-                                 _ptr(ry), _ptr(d), p.size, _ptr(p), _ptr(out))
+                                 _ptr(ry), _ptr(d), p.size, _ptr(p), _ptr(out), ctypes.byref(n))
     assert rc == 0
-    return out
+    return (out, int(n.value)) if return_count else out
 
 
 def demigrate(s, image) -> np.ndarray:

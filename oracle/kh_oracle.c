@@ -251,13 +251,14 @@ int ko_migrate(const ko_desc* d, long ntr, const float* sx, const float* sy, con
 /* Migration at a list of image samples (flat indices into the n_bins x ny x nx x nz image). */
 int ko_migrate_points(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
                       const float* ry, const double* traces, long npts, const long* pidx,
-                      double* out)
+                      double* out, long long* ncontrib)
 {
     const long ncol = (long)d->nx * d->ny, nz = d->nz, nt = d->nt;
     int* bin = (int*)malloc(sizeof(int) * (ntr > 0 ? ntr : 1));
     if (!bin) return 1;
     ko_bins(d, ntr, sx, sy, rx, ry, bin);
-#pragma omp parallel for schedule(dynamic, 1)
+    long long total = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
     for (long p = 0; p < npts; ++p) {
         long q = pidx[p];
         int iz = (int)(q % nz);
@@ -273,6 +274,7 @@ int ko_migrate_points(const ko_desc* d, long ntr, const float* sx, const float* 
             float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
             if (d->dim == 2) { fsy = 0.f; fry = 0.f; }
             if (!inside_aperture(d, cx, cy, fsx, fsy, frx, fry)) continue;
+            ++total;
             contrib w = contribution(d, x, y, z, fsx, fsy, frx, fry, 0);
             if (!w.valid) continue;
             const double* D = traces + j * nt;
@@ -280,6 +282,7 @@ int ko_migrate_points(const ko_desc* d, long ntr, const float* sx, const float* 
         }
         out[p] = acc;
     }
+    if (ncontrib) *ncontrib = total;
     free(bin);
     return 0;
 }

@@ -1,0 +1,624 @@
+// C ABI (include/kirchhoff.h): plan creation, argument validation, the trace binning pass
+// (offset bin per trace and a stable counting sort by bin), the Eq. 2 work count, the
+// traveltime evaluator and the dispatch to the migration / demigration / gradient kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kh_device.cuh"
+#include "kh_plan.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+kh_status fail(kh_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+kh_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? KH_ERR_OOM : KH_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+}  // namespace
+
+namespace kh {
+
+kh_status set_error(kh_status s, const char* msg)
+{
+    g_err = msg;
+    return s;
+}
+
+kh_status set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+// ------------------------------------------------------------------ binning kernels
+
+__global__ void k_bin(int ntr, const float* __restrict__ sx, const float* __restrict__ sy,
+                      const float* __restrict__ rx, const float* __restrict__ ry, int dim,
+                      int n_bins, double w, int* __restrict__ bin)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ntr) return;
+    const float ys = (dim == 3 && sy) ? sy[j] : 0.f, yr = (dim == 3 && ry) ? ry[j] : 0.f;
+    bin[j] = offset_bin(sx[j], ys, rx[j], yr, n_bins, w);
+}
+
+// Stable counting sort of the traces by bin in one CTA of 1024 threads.  Traces without a
+// bin are dropped.  bin_start[b] .. bin_start[b+1] is the range of bin b in perm.
+constexpr int SORT_THREADS = 1024;
+constexpr int MAX_BINS = 256;
+
+__global__ void __launch_bounds__(SORT_THREADS)
+    k_sort(int ntr, int n_bins, const int* __restrict__ bin, int* __restrict__ perm,
+           int* __restrict__ bin_start)
+{
+    __shared__ int cnt[MAX_BINS + 1];
+    __shared__ int wc[SORT_THREADS / 32][MAX_BINS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int b = tid; b <= n_bins; b += SORT_THREADS) cnt[b] = 0;
+    __syncthreads();
+    for (int j = tid; j < ntr; j += SORT_THREADS) {
+        const int b = bin[j];
+        if (b >= 0) atomicAdd(&cnt[b], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int b = 0; b < n_bins; ++b) {
+            const int c = cnt[b];
+            cnt[b] = run;
+            bin_start[b] = run;
+            run += c;
+        }
+        bin_start[n_bins] = run;
+    }
+    __syncthreads();
+    // cnt[b] is now the running insertion offset of bin b
+    for (int base = 0; base < ntr; base += SORT_THREADS) {
+        for (int i = tid; i < (SORT_THREADS / 32) * n_bins; i += SORT_THREADS) (&wc[0][0])[(i / n_bins) * MAX_BINS + i % n_bins] = 0;
+        __syncthreads();
+        const int j = base + tid;
+        const int b = (j < ntr) ? bin[j] : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        if (b >= 0 && rank == 0) wc[warp][b] = __popc(same);
+        __syncthreads();
+        for (int bb = tid; bb < n_bins; bb += SORT_THREADS) {
+            int run = cnt[bb];
+            for (int w = 0; w < SORT_THREADS / 32; ++w) {
+                const int c = wc[w][bb];
+                wc[w][bb] = run;
+                run += c;
+            }
+            cnt[bb] = run;
+        }
+        __syncthreads();
+        if (b >= 0) perm[wc[warp][b] + rank] = j;
+        __syncthreads();
+    }
+}
+
+__global__ void k_gather(const int* __restrict__ bin_start, int n_bins,
+                         const int* __restrict__ perm, const float* __restrict__ sx,
+                         const float* __restrict__ sy, const float* __restrict__ rx,
+                         const float* __restrict__ ry, int dim, float4* __restrict__ hdr,
+                         float2* __restrict__ mid)
+{
+    const int n = bin_start[n_bins];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int j = perm[k];
+        const float a = sx[j], c = rx[j];
+        const float b = (dim == 3 && sy) ? sy[j] : 0.f, d = (dim == 3 && ry) ? ry[j] : 0.f;
+        hdr[k] = make_float4(a, b, c, d);
+        mid[k] = make_float2(__fmul_rn(__fadd_rn(a, c), 0.5f), __fmul_rn(__fadd_rn(b, d), 0.5f));
+    }
+}
+
+// Rows of `nt` samples copied to rows of `ld` (a multiple of 16 bytes) for the bulk copies.
+template <typename T>
+__global__ void k_pad(int ntr, int nt, long long ld, const T* __restrict__ src, T* __restrict__ dst)
+{
+    const long long total = (long long)ntr * ld;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long j = i / ld, t = i - j * ld;
+        dst[i] = (t < nt) ? src[j * nt + t] : T(0);
+    }
+}
+
+// Eq. 2 work count: per trace (one CTA each), the in-aperture columns times nz.
+__global__ void k_count(int ntr, const float* __restrict__ sx, const float* __restrict__ sy,
+                        const float* __restrict__ rx, const float* __restrict__ ry, GeomParams g,
+                        double bin_width, long long* __restrict__ out)
+{
+    __shared__ long long part[32];
+    const int j = blockIdx.x;
+    const float a = sx[j], c = rx[j];
+    const float b = (g.dim == 3 && sy) ? sy[j] : 0.f, d = (g.dim == 3 && ry) ? ry[j] : 0.f;
+    const int bin = offset_bin(a, b, c, d, g.n_bins, bin_width);
+    long long n = 0;
+    if (bin >= 0) {
+        if (!g.use_aperture) {
+            n = (threadIdx.x == 0) ? (long long)g.nx * g.ny : 0;
+        } else {
+            const float mx = __fmul_rn(__fadd_rn(a, c), 0.5f), my = __fmul_rn(__fadd_rn(b, d), 0.5f);
+            for (long long col = threadIdx.x; col < (long long)g.nx * g.ny; col += blockDim.x) {
+                const int iy = (int)(col / g.nx), ix = (int)(col % g.nx);
+                const float cx = col_coord(g.ox, ix, g.dx);
+                const float cy = g.dim == 3 ? col_coord(g.oy, iy, g.dy) : 0.f;
+                n += in_aperture(cx, cy, mx, my, g.A2) ? 1 : 0;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+        out[j] = s * g.nz;
+    }
+}
+
+// Traveltime of the plan's model in FP64, rounded to FP32 (a utility, not the hot loop).
+__device__ double tt_exact(double R, double z, int vel, double v0, double k)
+{
+    if (vel == VK_CONST || k == 0.0) return R / v0;
+    const double vz = v0 + k * z;
+    const double g = sqrt(v0 * vz);
+    const double s = fabs(k) * R / (2.0 * g);
+    if (s < 1e-4) return R / g * (1.0 - s * s / 6.0 + 3.0 * s * s * s * s / 40.0);
+    return 2.0 * asinh(s) / fabs(k);
+}
+
+__global__ void k_traveltime(int n, const float* __restrict__ px, const float* __restrict__ py,
+                             const float* __restrict__ pz, const float* __restrict__ lx,
+                             const float* __restrict__ ly, int vel, double v0, double k,
+                             float* __restrict__ T)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double ex = (double)px[i] - lx[i];
+    const double ey = (py && ly) ? (double)py[i] - ly[i] : 0.0;
+    const double z = pz[i];
+    T[i] = (float)tt_exact(sqrt(ex * ex + ey * ey + z * z), z, vel, v0, k);
+}
+
+}  // namespace kh
+
+using namespace kh;
+
+// ------------------------------------------------------------------ plan helpers
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static int dtype_size(kh_dtype t) { return t == KH_F32 ? 4 : 2; }
+
+static kh_status validate_desc(const kh_desc* d)
+{
+    if (!d) return fail(KH_ERR_INVALID_ARG, "desc is NULL");
+    if (d->dim != 2 && d->dim != 3) return fail(KH_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", d->dim);
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(KH_ERR_INVALID_ARG, "image sizes must be >= 1");
+    if (d->dim == 2 && d->ny != 1) return fail(KH_ERR_INVALID_ARG, "ny must be 1 for dim 2");
+    if (!(d->dx > 0) || !(d->dz > 0) || (d->dim == 3 && !(d->dy > 0)))
+        return fail(KH_ERR_INVALID_ARG, "image spacing must be > 0");
+    if ((long long)d->nx * d->ny * d->nz * (long long)d->n_bins > (1LL << 40))
+        return fail(KH_ERR_INVALID_ARG, "image too large");
+    if (d->n_bins < 1 || d->n_bins > kh::MAX_BINS)
+        return fail(KH_ERR_INVALID_ARG, "n_bins must be in [1, %d]", kh::MAX_BINS);
+    if (!(d->bin_width > 0)) return fail(KH_ERR_INVALID_ARG, "bin_width must be > 0");
+    if (d->vel != KH_VEL_CONST && d->vel != KH_VEL_LINEAR_Z && d->vel != KH_VEL_TABLE)
+        return fail(KH_ERR_INVALID_ARG, "bad velocity kind %d", (int)d->vel);
+    if (!(d->v0 > 0) || !std::isfinite(d->v0)) return fail(KH_ERR_INVALID_ARG, "v0 must be > 0");
+    if (!std::isfinite(d->k)) return fail(KH_ERR_INVALID_ARG, "k must be finite");
+    if (d->weight != KH_W_ONE && d->weight != KH_W_OBLIQ_SPREAD)
+        return fail(KH_ERR_INVALID_ARG, "bad weight kind %d", (int)d->weight);
+    if (d->weight == KH_W_OBLIQ_SPREAD && !(d->r0 > 0)) return fail(KH_ERR_INVALID_ARG, "r0 must be > 0");
+    if (d->nt < 2) return fail(KH_ERR_UNSUPPORTED, "nt must be >= 2 (got %d)", d->nt);
+    if (!(d->dt > 0) || !std::isfinite(d->t0)) return fail(KH_ERR_INVALID_ARG, "dt must be > 0, t0 finite");
+    if (d->trace_dtype != KH_F32 && d->trace_dtype != KH_F16 && d->trace_dtype != KH_BF16)
+        return fail(KH_ERR_INVALID_ARG, "bad trace dtype");
+    if (d->vel != KH_VEL_CONST) {
+        const double zlo = std::min(0.0, std::min(d->oz, d->oz + (d->nz - 1) * d->dz));
+        const double zhi = std::max(d->oz, d->oz + (d->nz - 1) * d->dz);
+        if (!(d->v0 + d->k * zlo > 0) || !(d->v0 + d->k * zhi > 0))
+            return fail(KH_ERR_UNSUPPORTED, "v(z) = v0 + k z must stay > 0 over the image depths");
+    }
+    if (d->vel == KH_VEL_TABLE)
+        return fail(KH_ERR_UNSUPPORTED, "KH_VEL_TABLE plans are created with kirchhoff_create "
+                                        "only once the table path is built into this library");
+    const int ealign = 16 / dtype_size(d->trace_dtype);
+    const int cap = std::max((d->nt + 3 * ealign) / ealign * ealign, 24576 / 4);
+    if ((size_t)kh::STAGES * cap * dtype_size(d->trace_dtype) > 200u * 1024u)
+        return fail(KH_ERR_UNSUPPORTED, "nt = %d too long for the shared-memory trace ring", d->nt);
+    return KH_OK;
+}
+
+static GeomParams geom_of(const kh_desc& d)
+{
+    GeomParams g;
+    std::memset(&g, 0, sizeof g);
+    g.dim = d.dim;
+    g.nx = d.nx;
+    g.ny = d.ny;
+    g.nz = d.nz;
+    g.n_bins = d.n_bins;
+    g.ox = d.ox;
+    g.oy = d.oy;
+    g.oz = d.oz;
+    g.dx = d.dx;
+    g.dy = d.dy;
+    g.dz = d.dz;
+    g.fdz = (float)d.dz;
+    const bool lin = d.vel != KH_VEL_CONST && d.k != 0.0;
+    g.v0 = d.v0;
+    g.k = lin ? d.k : 0.0;
+    g.kabs = std::fabs(g.k);
+    g.t0 = (float)d.t0;
+    g.dt = (float)d.dt;
+    if (lin) g.C1 = (float)(std::log(2.0) / (g.kabs * d.dt));
+    else g.C1 = (float)(1.0 / (d.v0 * d.dt));
+    g.C0h = (float)(-d.t0 / d.dt - 0.5);
+    g.weight = d.weight == KH_W_OBLIQ_SPREAD ? 1 : 0;
+    g.wscale = 1.0 / (2.0 * d.r0 * d.r0);
+    g.use_aperture = d.aperture > 0 ? 1 : 0;
+    g.A2 = (float)(d.aperture * d.aperture);
+    g.A2cull = (float)((d.aperture * (1.0 + 1e-5) + 1.0) * (d.aperture * (1.0 + 1e-5) + 1.0));
+    g.nt = d.nt;
+    g.esize = dtype_size(d.trace_dtype);
+    g.elem_align = 16 / g.esize;
+    g.ld = d.nt;
+    return g;
+}
+
+static TileShape tile_of(const kh_plan_s* p)
+{
+    TileShape t;
+    int cx, cy, cz;
+    if (p->tile_code) {
+        cx = (int)(p->tile_code & 0xff);
+        cy = (int)((p->tile_code >> 8) & 0xff);
+        cz = (int)((p->tile_code >> 16) & 0xff);
+    } else if (p->d.dim == 3) {
+        cx = 16; cy = 16; cz = 1;
+    } else {
+        cx = 32; cy = 1; cz = 8;
+    }
+    t.cx = cx;
+    t.cy = cy;
+    t.cz = cz;
+    t.tiles_x = (p->d.nx + cx - 1) / cx;
+    t.tiles_y = (p->d.ny + cy - 1) / cy;
+    t.tiles_z = (p->d.nz + cz * NZ - 1) / (cz * NZ);
+    return t;
+}
+
+template <typename T>
+static cudaError_t grow(T*& ptr, size_t& cap, size_t n)
+{
+    if (n <= cap && ptr) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(n + n / 4, 256);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), want * sizeof(T));
+    if (e == cudaSuccess) cap = want;
+    return e;
+}
+
+namespace kh {
+
+static cudaEvent_t take_event(kh_plan_s* p)
+{
+    if (!p->ev_pool.empty()) {
+        cudaEvent_t e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(kh_plan_s* p, cudaStream_t s)
+{
+    if (!p->profiling) return;
+    cudaEvent_t a = take_event(p);
+    cudaEventRecord(a, s);
+    p->ev_open.push_back({a, nullptr});
+}
+
+void prof_end(kh_plan_s* p, cudaStream_t s)
+{
+    if (!p->profiling || p->ev_open.empty() || p->ev_open.back().second) return;
+    cudaEvent_t b = take_event(p);
+    cudaEventRecord(b, s);
+    p->ev_open.back().second = b;
+}
+
+kh_status ensure_traces_ws(kh_plan_s* p, int ntr)
+{
+    cudaError_t e;
+    if ((e = grow(p->ws_bin, p->cap_bin, (size_t)ntr)) != cudaSuccess) return cuda_fail(e, "workspace (bins)");
+    if ((e = grow(p->ws_perm, p->cap_perm, (size_t)ntr)) != cudaSuccess) return cuda_fail(e, "workspace (perm)");
+    if ((e = grow(p->ws_hdr, p->cap_hdr, (size_t)ntr)) != cudaSuccess) return cuda_fail(e, "workspace (headers)");
+    if ((e = grow(p->ws_mid, p->cap_mid, (size_t)ntr)) != cudaSuccess) return cuda_fail(e, "workspace (midpoints)");
+    return KH_OK;
+}
+
+// Offset bin per trace, stable sort by bin, sorted headers: three launches on `s`.
+kh_status bin_traces(kh_plan_s* p, int ntr, const float* sx, const float* sy, const float* rx,
+                     const float* ry, cudaStream_t s)
+{
+    kh_status st = ensure_traces_ws(p, ntr);
+    if (st != KH_OK) return st;
+    if (ntr > 0) {
+        k_bin<<<(ntr + 255) / 256, 256, 0, s>>>(ntr, sx, sy, rx, ry, p->d.dim, p->d.n_bins,
+                                                p->d.bin_width, p->ws_bin);
+        ++p->launches;
+    }
+    k_sort<<<1, SORT_THREADS, 0, s>>>(ntr, p->d.n_bins, p->ws_bin, p->ws_perm, p->ws_bin_start);
+    ++p->launches;
+    k_gather<<<std::max(1, std::min((ntr + 255) / 256, 4096)), 256, 0, s>>>(
+        p->ws_bin_start, p->d.n_bins, p->ws_perm, sx, sy, rx, ry, p->d.dim, p->ws_hdr, p->ws_mid);
+    ++p->launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "binning kernels");
+    return KH_OK;
+}
+
+// Traces as the kernels read them: rows 16-byte aligned.  Returns the pointer and row stride.
+kh_status staged_traces(kh_plan_s* p, int ntr, const void* traces, cudaStream_t s,
+                        const void** out, long long* ld)
+{
+    const int es = dtype_size(p->d.trace_dtype);
+    const int ealign = 16 / es;
+    if (aligned16(traces) && (p->d.nt % ealign) == 0) {
+        *out = traces;
+        *ld = p->d.nt;
+        return KH_OK;
+    }
+    const long long L = (p->d.nt + ealign - 1) / ealign * ealign;
+    const size_t bytes = (size_t)ntr * L * es;
+    cudaError_t e = grow(p->ws_pad, p->cap_pad, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace (padded traces)");
+    const int blocks = (int)std::min<long long>(((long long)ntr * L + 255) / 256, 65535);
+    if (es == 4)
+        k_pad<float><<<std::max(blocks, 1), 256, 0, s>>>(ntr, p->d.nt, L, (const float*)traces,
+                                                          (float*)p->ws_pad);
+    else
+        k_pad<unsigned short><<<std::max(blocks, 1), 256, 0, s>>>(
+            ntr, p->d.nt, L, (const unsigned short*)traces, (unsigned short*)p->ws_pad);
+    ++p->launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "trace padding kernel");
+    *out = p->ws_pad;
+    *ld = L;
+    return KH_OK;
+}
+
+}  // namespace kh
+
+static kh_status check_headers(const kh_plan_s* p, int ntr, const float* sx, const float* sy,
+                               const float* rx, const float* ry)
+{
+    if (ntr < 0) return fail(KH_ERR_INVALID_ARG, "ntr must be >= 0");
+    if (ntr > 0 && (!sx || !rx)) return fail(KH_ERR_INVALID_ARG, "sx/rx must not be NULL");
+    if (ntr > 0 && p->d.dim == 3 && (!sy || !ry)) return fail(KH_ERR_INVALID_ARG, "sy/ry must not be NULL for dim 3");
+    return KH_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+kh_status kirchhoff_create(const kh_desc* d, kh_plan* out)
+{
+    if (!out) return fail(KH_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    kh_status st = validate_desc(d);
+    if (st != KH_OK) return st;
+    kh_plan_s* p = new (std::nothrow) kh_plan_s();
+    if (!p) return fail(KH_ERR_OOM, "host allocation failed");
+    p->d = *d;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->ws_status), 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->ws_status, 0, 2 * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void**>(&p->ws_bin_start), (MAX_BINS + 1) * sizeof(int));
+    if (e != cudaSuccess) {
+        kirchhoff_destroy(p);
+        return cuda_fail(e, "kirchhoff_create");
+    }
+    *out = p;
+    return KH_OK;
+}
+
+kh_status kirchhoff_destroy(kh_plan p)
+{
+    if (!p) return KH_OK;
+    cudaDeviceSynchronize();
+    cudaFree(p->ws_status);
+    cudaFree(p->ws_bin_start);
+    cudaFree(p->ws_bin);
+    cudaFree(p->ws_perm);
+    cudaFree(p->ws_hdr);
+    cudaFree(p->ws_mid);
+    cudaFree(p->ws_pad);
+    cudaFree(p->ws_count);
+    cudaFree(p->ws_partial);
+    for (auto& pr : p->ev_open) {
+        if (pr.first) cudaEventDestroy(pr.first);
+        if (pr.second) cudaEventDestroy(pr.second);
+    }
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    delete p;
+    return KH_OK;
+}
+
+kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value)
+{
+    if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    switch (opt) {
+        case KH_OPT_WAIT_POLLS:
+            if (value < 0) return fail(KH_ERR_INVALID_ARG, "wait polls must be >= 0");
+            p->wait_polls = value;
+            return KH_OK;
+        case KH_OPT_FAST_MATH:
+            p->fast_math = value ? 1 : 0;
+            return KH_OK;
+        case KH_OPT_TILE: {
+            if (value == 0) {
+                p->tile_code = 0;
+                return KH_OK;
+            }
+            const int cx = (int)(value & 0xff), cy = (int)((value >> 8) & 0xff), cz = (int)((value >> 16) & 0xff);
+            if (cx < 1 || cy < 1 || cz < 1 || cx * cy * cz != CONSUMERS || (value >> 24) != 0)
+                return fail(KH_ERR_INVALID_ARG, "tile cx*cy*cz must equal %d", CONSUMERS);
+            if (p->d.dim == 2 && cy != 1) return fail(KH_ERR_INVALID_ARG, "tile cy must be 1 for dim 2");
+            p->tile_code = value;
+            return KH_OK;
+        }
+        default:
+            return fail(KH_ERR_INVALID_ARG, "unknown option %d", (int)opt);
+    }
+}
+
+kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
+                            const float* ry, const void* traces, float* image, void* cuda_stream)
+{
+    if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    kh_status st = check_headers(p, ntr, sx, sy, rx, ry);
+    if (st != KH_OK) return st;
+    if (!image) return fail(KH_ERR_INVALID_ARG, "image is NULL");
+    if (ntr > 0 && !traces) return fail(KH_ERR_INVALID_ARG, "traces is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t img_bytes = (size_t)p->d.n_bins * p->d.ny * p->d.nx * p->d.nz * sizeof(float);
+    if (ntr == 0) {
+        cudaError_t e = cudaMemsetAsync(image, 0, img_bytes, s);
+        return e == cudaSuccess ? KH_OK : cuda_fail(e, "cudaMemsetAsync");
+    }
+    if ((st = bin_traces(p, ntr, sx, sy, rx, ry, s)) != KH_OK) return st;
+    const void* tr_ptr = nullptr;
+    GeomParams g = geom_of(p->d);
+    if ((st = staged_traces(p, ntr, traces, s, &tr_ptr, &g.ld)) != KH_OK) return st;
+    TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};
+    WaitCfg w{p->ws_status, p->wait_polls, WAIT_NS};
+    const int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
+    prof_begin(p, s);
+    cudaError_t e = launch_migrate(g, tile_of(p), ts, tr_ptr, image, vk, p->fast_math, w, s);
+    prof_end(p, s);
+    ++p->launches;
+    if (e != cudaSuccess) return cuda_fail(e, "migration kernel");
+    return KH_OK;
+}
+
+kh_status kirchhoff_count(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
+                          const float* ry, int64_t* out_count, void* cuda_stream)
+{
+    if (!p || !out_count) return fail(KH_ERR_INVALID_ARG, "plan/out_count is NULL");
+    kh_status st = check_headers(p, ntr, sx, sy, rx, ry);
+    if (st != KH_OK) return st;
+    *out_count = 0;
+    if (ntr == 0) return KH_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = grow(p->ws_count, p->cap_count, (size_t)ntr);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace (count)");
+    GeomParams g = geom_of(p->d);
+    k_count<<<ntr, 256, 0, s>>>(ntr, sx, sy, rx, ry, g, p->d.bin_width, p->ws_count);
+    ++p->launches;
+    std::vector<long long> h((size_t)ntr);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), p->ws_count, sizeof(long long) * ntr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_count");
+    long long total = 0;
+    for (long long v : h) total += v;
+    *out_count = total;
+    return KH_OK;
+}
+
+kh_status kirchhoff_traveltime(kh_plan p, int n, const float* px, const float* py, const float* pz,
+                               const float* lx, const float* ly, float* T, void* cuda_stream)
+{
+    if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    if (n < 0) return fail(KH_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return KH_OK;
+    if (!px || !pz || !lx || !T) return fail(KH_ERR_INVALID_ARG, "NULL array");
+    const bool lin = p->d.vel != KH_VEL_CONST && p->d.k != 0.0;
+    k_traveltime<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+        n, px, p->d.dim == 3 ? py : nullptr, pz, lx, p->d.dim == 3 ? ly : nullptr,
+        lin ? VK_LINEAR : VK_CONST, p->d.v0, lin ? p->d.k : 0.0, T);
+    ++p->launches;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KH_OK : cuda_fail(e, "traveltime kernel");
+}
+
+kh_status kirchhoff_sync(kh_plan p, void* cuda_stream)
+{
+    if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int h = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, p->ws_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_sync");
+    if (h != 0) {
+        cudaMemset(p->ws_status, 0, sizeof(int));
+        return fail(KH_ERR_TIMEOUT, "a bounded in-kernel wait ran out (status 0x%x); results are invalid", h);
+    }
+    return KH_OK;
+}
+
+kh_status kirchhoff_profile(kh_plan p, int enable)
+{
+    if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    p->profiling = enable ? 1 : 0;
+    return KH_OK;
+}
+
+kh_status kirchhoff_profile_read(kh_plan p, double* kernel_ms, long long* timed_launches)
+{
+    if (!p || !kernel_ms || !timed_launches) return fail(KH_ERR_INVALID_ARG, "NULL argument");
+    double total = 0.0;
+    long long n = 0;
+    for (auto& pr : p->ev_open) {
+        if (pr.second) {
+            cudaError_t e = cudaEventSynchronize(pr.second);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+            if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_profile_read");
+            total += ms;
+            ++n;
+            p->ev_pool.push_back(pr.second);
+        }
+        p->ev_pool.push_back(pr.first);
+    }
+    p->ev_open.clear();
+    *kernel_ms = total;
+    *timed_launches = n;
+    return KH_OK;
+}
+
+long long kirchhoff_launch_count(kh_plan p) { return p ? p->launches : 0; }
+
+const char* kirchhoff_last_error(void) { return g_err.c_str(); }
+
+const char* kirchhoff_version(void) { return "kirchhoff-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Device helpers: shared-memory mbarriers, bulk async copies (non-multicast), bounded
+// waits and the fast-math primitives of the hot loop.  sm_100+ PTX, written for sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kh_internal.h"
+
+namespace kh {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// Makes barrier initialisation visible to the async (bulk-copy) proxy.
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of `bar` with the given parity to complete.  Gives up, returning
+// false, after `polls` polls (if > 0), after `ns` nanoseconds of wall clock, or as soon as
+// another CTA has raised the status word (if `status` is not NULL).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long polls,
+                                                  long long ns, const int* status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (polls > 0 && i >= polls) return false;
+        if ((i & 63) == 0) {
+            if ((long long)(global_ns() - t0) > ns) return false;
+            if (status && *reinterpret_cast<const volatile int*>(status) != 0) return false;
+        }
+    }
+}
+
+// Every lane of the warp waits (so each lane acquires the phase) and the warp agrees on the
+// outcome, so a wait that runs out for one lane ends the loop for all lanes together.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, long long polls,
+                                          long long ns, const int* status)
+{
+    const bool ok = mbar_wait_bounded(bar, parity, polls, ns, status);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// One contiguous global -> shared copy by the bulk-copy engine; completion is counted in
+// bytes on `bar`.  dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---- hot-loop math: hardware approximations (FAST) or IEEE-rounded / accurate library calls
+template <bool FAST>
+__device__ __forceinline__ float hsqrt(float x)
+{
+    if constexpr (FAST) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    } else {
+        return __fsqrt_rn(x);
+    }
+}
+
+template <bool FAST>
+__device__ __forceinline__ float hlog2(float x)
+{
+    if constexpr (FAST) {
+        float r;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    } else {
+        return log2f(x);
+    }
+}
+
+// Column coordinate o + i h in FP64 without contraction, rounded to FP32 (the same value the
+// aperture decision uses everywhere).
+__device__ __forceinline__ float col_coord(double o, int i, double h)
+{
+    return (float)__dadd_rn(o, __dmul_rn((double)i, h));
+}
+
+// The aperture decision in FP32 with a fixed order and no contraction.
+__device__ __forceinline__ bool in_aperture(float cx, float cy, float mx, float my, float A2)
+{
+    const float ex = __fsub_rn(cx, mx), ey = __fsub_rn(cy, my);
+    return __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= A2;
+}
+
+// Offset bin in FP64 (uniform bins; X == n_bins * w goes to the last bin; beyond: -1).
+__device__ __forceinline__ int offset_bin(float sx, float sy, float rx, float ry, int n_bins,
+                                          double w)
+{
+    const double ex = __dadd_rn((double)sx, -(double)rx);
+    const double ey = __dadd_rn((double)sy, -(double)ry);
+    const double X = __dsqrt_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)));
+    const double b = floor(__ddiv_rn(X, w));
+    if (b < (double)n_bins) return (int)b;
+    if (X == __dmul_rn((double)n_bins, w)) return n_bins - 1;
+    return -1;
+}
+
+// One-way traveltime in FP32 for window bounds (not the hot loop): constant or linear v(z).
+__device__ __forceinline__ float tt_bound(float h, float z, int vel, float v0, float k)
+{
+    const float R = sqrtf(h * h + z * z);
+    if (vel == VK_CONST || k == 0.f) return R / v0;
+    const float vz = v0 + k * z;
+    const float g = sqrtf(v0 * vz);
+    const float s = fabsf(k) * R / (2.f * g);
+    if (s < 1e-3f) return R / g * (1.f - s * s * (1.f / 6.f));
+    return 2.f * asinhf(s) / fabsf(k);
+}
+
+}  // namespace kh

@@ -1,0 +1,51 @@
+// The opaque plan behind kh_plan: the descriptor, options and the device workspace it owns.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "kh_internal.h"
+
+struct kh_plan_s {
+    kh_desc d;
+    int device = 0;
+    long long launches = 0;
+    long long wait_polls = 0;     // 0 = wall-clock limit only
+    int fast_math = 1;
+    long long tile_code = 0;      // 0 = default tile for the dimension
+    // device workspace (grown on demand, freed by kirchhoff_destroy)
+    int* ws_status = nullptr;     // [2]: bit 0 of [0] = a bounded wait ran out
+    int* ws_bin_start = nullptr;  // [MAX_BINS + 1]
+    int* ws_bin = nullptr;
+    size_t cap_bin = 0;
+    int* ws_perm = nullptr;
+    size_t cap_perm = 0;
+    float4* ws_hdr = nullptr;
+    size_t cap_hdr = 0;
+    float2* ws_mid = nullptr;
+    size_t cap_mid = 0;
+    unsigned char* ws_pad = nullptr;
+    size_t cap_pad = 0;
+    long long* ws_count = nullptr;
+    size_t cap_count = 0;
+    double* ws_partial = nullptr;
+    size_t cap_partial = 0;
+    // profiling: event pairs recorded around main kernels while enabled
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_open;
+};
+
+namespace kh {
+kh_status set_error(kh_status s, const char* msg);
+kh_status set_cuda_error(cudaError_t e, const char* what);
+kh_status ensure_traces_ws(kh_plan_s* p, int ntr);
+kh_status bin_traces(kh_plan_s* p, int ntr, const float* sx, const float* sy, const float* rx,
+                     const float* ry, cudaStream_t s);
+// Brackets a main-kernel launch with profiling events (no-op unless profiling is on).
+void prof_begin(kh_plan_s* p, cudaStream_t s);
+void prof_end(kh_plan_s* p, cudaStream_t s);
+kh_status staged_traces(kh_plan_s* p, int ntr, const void* traces, cudaStream_t s,
+                        const void** out, long long* ld);
+}  // namespace kh

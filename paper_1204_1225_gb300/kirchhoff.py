@@ -1,0 +1,337 @@
+"""Thin ctypes binding of libkirchhoff.so (include/kirchhoff.h).
+
+Argument marshalling only: every step of the migration runs in the library's CUDA
+kernels.  Tensors must be CUDA tensors; there is no CPU path.  The functions named
+``kirchhoff_*`` mirror the C entry points one to one; ``Plan`` is a convenience wrapper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkirchhoff.so")
+
+KH_OK, KH_ERR_INVALID_ARG, KH_ERR_UNSUPPORTED, KH_ERR_OOM, KH_ERR_CUDA, KH_ERR_TIMEOUT, \
+    KH_ERR_INTERNAL = range(7)
+KH_F32, KH_F16, KH_BF16 = 0, 1, 2
+KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE = 0, 1, 2
+KH_W_ONE, KH_W_OBLIQ_SPREAD = 0, 1
+KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE = 1, 2, 3
+
+_STATUS = {0: "KH_OK", 1: "KH_ERR_INVALID_ARG", 2: "KH_ERR_UNSUPPORTED", 3: "KH_ERR_OOM",
+           4: "KH_ERR_CUDA", 5: "KH_ERR_TIMEOUT", 6: "KH_ERR_INTERNAL"}
+
+
+class KirchhoffError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kh_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("ox", ctypes.c_double), ("oy", ctypes.c_double),
+                ("oz", ctypes.c_double), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("n_bins", ctypes.c_int), ("bin_width", ctypes.c_double),
+                ("vel", ctypes.c_int), ("v0", ctypes.c_double), ("k", ctypes.c_double),
+                ("table_spacing", ctypes.c_double), ("table_dtype", ctypes.c_int),
+                ("weight", ctypes.c_int), ("r0", ctypes.c_double), ("aperture", ctypes.c_double),
+                ("nt", ctypes.c_int), ("t0", ctypes.c_double), ("dt", ctypes.c_double),
+                ("trace_dtype", ctypes.c_int)]
+
+
+class kh_job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("ntr", ctypes.c_int), ("sx", ctypes.c_void_p),
+                ("sy", ctypes.c_void_p), ("rx", ctypes.c_void_p), ("ry", ctypes.c_void_p),
+                ("traces", ctypes.c_void_p), ("image", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ["kirchhoff_create", "kirchhoff_destroy", "kirchhoff_migrate", "kirchhoff_demigrate",
+           "kirchhoff_velocity_grad", "kirchhoff_traveltime", "kirchhoff_count",
+           "kirchhoff_batched_prepare", "kirchhoff_migrate_batched", "kirchhoff_sync",
+           "kirchhoff_set_option", "kirchhoff_launch_count", "kirchhoff_last_error",
+           "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read"]
+
+
+def lib(path: str = LIB_PATH):
+    """Loads the CUDA library; raises if it has not been built (there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"{path} is missing: build it with "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(path)
+            P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+            L.kirchhoff_create.argtypes = [ctypes.POINTER(kh_desc), ctypes.POINTER(P)]
+            L.kirchhoff_destroy.argtypes = [P]
+            L.kirchhoff_migrate.argtypes = [P, I, P, P, P, P, P, P, P]
+            L.kirchhoff_demigrate.argtypes = [P, I, P, P, P, P, P, P, P]
+            L.kirchhoff_velocity_grad.argtypes = [P, I, P, P, P, P, P, P, P, P]
+            L.kirchhoff_traveltime.argtypes = [P, I, P, P, P, P, P, P, P]
+            L.kirchhoff_count.argtypes = [P, I, P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]
+            L.kirchhoff_batched_prepare.argtypes = [I, ctypes.POINTER(kh_job), P]
+            L.kirchhoff_migrate_batched.argtypes = [I, ctypes.POINTER(kh_job), P]
+            L.kirchhoff_sync.argtypes = [P, P]
+            L.kirchhoff_set_option.argtypes = [P, I, ctypes.c_longlong]
+            L.kirchhoff_launch_count.argtypes = [P]
+            L.kirchhoff_profile.argtypes = [P, I]
+            L.kirchhoff_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_longlong)]
+            L.kirchhoff_launch_count.restype = ctypes.c_longlong
+            L.kirchhoff_last_error.restype = ctypes.c_char_p
+            L.kirchhoff_version.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                f = getattr(L, name)
+                if f.restype is ctypes.c_int or f.restype is None:
+                    f.restype = S
+            L.kirchhoff_launch_count.restype = ctypes.c_longlong
+            L.kirchhoff_last_error.restype = ctypes.c_char_p
+            L.kirchhoff_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != KH_OK:
+        raise KirchhoffError(status, lib().kirchhoff_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("kirchhoff: tensors must live on a CUDA device (no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError("kirchhoff: tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+_DT = {torch.float32: KH_F32, torch.float16: KH_F16, torch.bfloat16: KH_BF16}
+
+
+def desc_from(s, trace_dtype=torch.float32, vel=None, table_spacing=25.0,
+              table_dtype=torch.float16) -> kh_desc:
+    """kh_desc from any object with the survey attributes (dim, nx, ..., nt, t0, dt)."""
+    if vel is None:
+        vel = {"const": KH_VEL_CONST, "linear": KH_VEL_LINEAR_Z}[s.vel]
+    return kh_desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
+                   s.dz, s.n_bins, s.bin_width, vel, s.v0, s.k, table_spacing,
+                   _DT[table_dtype], {"one": KH_W_ONE, "obliq": KH_W_OBLIQ_SPREAD}[s.weight],
+                   s.r0, s.aperture, s.nt, s.t0, s.dt, _DT[trace_dtype])
+
+
+# ------------------------------------------------------------ functions named as the C ABI
+
+def kirchhoff_create(desc: kh_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().kirchhoff_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def kirchhoff_destroy(plan: int) -> None:
+    _check(lib().kirchhoff_destroy(ctypes.c_void_p(plan)))
+
+
+def kirchhoff_migrate(plan, ntr, sx, sy, rx, ry, traces, image, stream=None) -> None:
+    _check(lib().kirchhoff_migrate(ctypes.c_void_p(plan), int(ntr), _ptr(sx), _ptr(sy), _ptr(rx),
+                                   _ptr(ry), _ptr(traces), _ptr(image), _stream(stream)))
+
+
+def kirchhoff_demigrate(plan, ntr, sx, sy, rx, ry, image, traces_out, stream=None) -> None:
+    _check(lib().kirchhoff_demigrate(ctypes.c_void_p(plan), int(ntr), _ptr(sx), _ptr(sy),
+                                     _ptr(rx), _ptr(ry), _ptr(image), _ptr(traces_out),
+                                     _stream(stream)))
+
+
+def kirchhoff_velocity_grad(plan, ntr, sx, sy, rx, ry, image, traces, out2, stream=None) -> None:
+    _check(lib().kirchhoff_velocity_grad(ctypes.c_void_p(plan), int(ntr), _ptr(sx), _ptr(sy),
+                                         _ptr(rx), _ptr(ry), _ptr(image), _ptr(traces), _ptr(out2),
+                                         _stream(stream)))
+
+
+def kirchhoff_traveltime(plan, n, px, py, pz, lx, ly, T, stream=None) -> None:
+    _check(lib().kirchhoff_traveltime(ctypes.c_void_p(plan), int(n), _ptr(px), _ptr(py), _ptr(pz),
+                                      _ptr(lx), _ptr(ly), _ptr(T), _stream(stream)))
+
+
+def kirchhoff_count(plan, ntr, sx, sy, rx, ry, stream=None) -> int:
+    out = ctypes.c_int64(0)
+    _check(lib().kirchhoff_count(ctypes.c_void_p(plan), int(ntr), _ptr(sx), _ptr(sy), _ptr(rx),
+                                 _ptr(ry), ctypes.byref(out), _stream(stream)))
+    return int(out.value)
+
+
+def kirchhoff_sync(plan, stream=None) -> None:
+    _check(lib().kirchhoff_sync(ctypes.c_void_p(plan), _stream(stream)))
+
+
+def kirchhoff_set_option(plan, opt: int, value: int) -> None:
+    _check(lib().kirchhoff_set_option(ctypes.c_void_p(plan), int(opt), int(value)))
+
+
+def kirchhoff_launch_count(plan) -> int:
+    return int(lib().kirchhoff_launch_count(ctypes.c_void_p(plan)))
+
+
+def kirchhoff_profile(plan, enable: bool) -> None:
+    _check(lib().kirchhoff_profile(ctypes.c_void_p(plan), 1 if enable else 0))
+
+
+def kirchhoff_profile_read(plan):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _check(lib().kirchhoff_profile_read(ctypes.c_void_p(plan), ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)
+
+
+def kirchhoff_version() -> str:
+    return lib().kirchhoff_version().decode()
+
+
+def _jobs_array(jobs):
+    arr = (kh_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i] = kh_job(j["plan"], int(j["ntr"]), *(t.data_ptr() if t is not None else None
+                                                     for t in (j["sx"], j["sy"], j["rx"], j["ry"],
+                                                               j["traces"], j["image"])))
+    return arr
+
+
+def kirchhoff_batched_prepare(jobs, stream=None) -> None:
+    arr = _jobs_array(jobs)
+    _check(lib().kirchhoff_batched_prepare(len(jobs), arr, _stream(stream)))
+
+
+def kirchhoff_migrate_batched(jobs, stream=None) -> None:
+    arr = _jobs_array(jobs)
+    _check(lib().kirchhoff_migrate_batched(len(jobs), arr, _stream(stream)))
+
+
+# ------------------------------------------------------------ convenience wrapper
+
+class Headers:
+    """Trace headers on the device: FP32 (sx, sy, rx, ry)."""
+
+    def __init__(self, sx, sy, rx, ry, device="cuda"):
+        f = lambda a: torch.as_tensor(a, dtype=torch.float32).to(device).contiguous()
+        self.sx, self.sy, self.rx, self.ry = f(sx), f(sy), f(rx), f(ry)
+
+    @classmethod
+    def of(cls, s, device="cuda"):
+        return cls(s.sx, s.sy, s.rx, s.ry, device)
+
+    @property
+    def ntr(self) -> int:
+        return int(self.sx.numel())
+
+    def args(self):
+        return self.sx, self.sy, self.rx, self.ry
+
+
+class Plan:
+    """Owns a kh_plan for one image grid / bin set / velocity model / trace dtype."""
+
+    def __init__(self, s, trace_dtype=torch.float32, fast_math: bool = True, tile=None, **kw):
+        self.survey = s
+        self.trace_dtype = trace_dtype
+        self.desc = desc_from(s, trace_dtype=trace_dtype, **kw)
+        self.handle = kirchhoff_create(self.desc)
+        self.image_shape = (s.n_bins, s.ny if s.dim == 3 else 1, s.nx, s.nz)
+        self.nt = s.nt
+        kirchhoff_set_option(self.handle, KH_OPT_FAST_MATH, 1 if fast_math else 0)
+        if tile is not None:
+            cx, cy, cz = tile
+            kirchhoff_set_option(self.handle, KH_OPT_TILE, cx | (cy << 8) | (cz << 16))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            kirchhoff_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, opt, value):
+        kirchhoff_set_option(self.handle, opt, value)
+
+    def migrate(self, hdr: Headers, traces, out=None, stream=None):
+        if out is None:
+            out = torch.empty(self.image_shape, dtype=torch.float32, device=traces.device)
+        kirchhoff_migrate(self.handle, hdr.ntr, *hdr.args(), traces, out, stream)
+        return out
+
+    def demigrate(self, hdr: Headers, image, out=None, stream=None):
+        if out is None:
+            out = torch.empty((hdr.ntr, self.nt), dtype=torch.float32, device=image.device)
+        kirchhoff_demigrate(self.handle, hdr.ntr, *hdr.args(), image, out, stream)
+        return out
+
+    def velocity_grad(self, hdr: Headers, image, traces, out=None, stream=None):
+        if out is None:
+            out = torch.empty(2, dtype=torch.float64, device=image.device)
+        kirchhoff_velocity_grad(self.handle, hdr.ntr, *hdr.args(), image, traces, out, stream)
+        return out
+
+    def count(self, hdr: Headers, stream=None) -> int:
+        return kirchhoff_count(self.handle, hdr.ntr, *hdr.args(), stream)
+
+    def traveltime(self, px, py, pz, lx, ly, stream=None):
+        T = torch.empty_like(px)
+        kirchhoff_traveltime(self.handle, px.numel(), px, py, pz, lx, ly, T, stream)
+        return T
+
+    def sync(self, stream=None):
+        kirchhoff_sync(self.handle, stream)
+
+    def profile(self, enable: bool = True):
+        kirchhoff_profile(self.handle, enable)
+
+    def profile_read(self):
+        """(summed main-kernel milliseconds, timed launches) since the previous read."""
+        return kirchhoff_profile_read(self.handle)
+
+    @property
+    def launches(self) -> int:
+        return kirchhoff_launch_count(self.handle)
+
+
+def arrival_times_fn(plan: "Plan"):
+    """Arrival-time callable for ``survey.synthesize`` computed by the library's traveltime
+    kernel: two-way time source -> point -> receiver, float64 tensor [n_points, m]."""
+
+    def fn(points, s, trace_idx):
+        dev = torch.device("cuda")
+        p = torch.as_tensor(points, dtype=torch.float32, device=dev)
+        j = torch.as_tensor(trace_idx, device=dev, dtype=torch.int64)
+        n, m = p.shape[0], j.numel()
+        sx = torch.as_tensor(s.sx, device=dev)[j]
+        rx = torch.as_tensor(s.rx, device=dev)[j]
+        sy = torch.as_tensor(s.sy, device=dev)[j]
+        ry = torch.as_tensor(s.ry, device=dev)[j]
+        px = p[:, 0:1].expand(n, m).contiguous().view(-1)
+        py = p[:, 1:2].expand(n, m).contiguous().view(-1)
+        pz = p[:, 2:3].expand(n, m).contiguous().view(-1)
+        ts = plan.traveltime(px, py, pz, sx.expand(n, m).contiguous().view(-1),
+                             sy.expand(n, m).contiguous().view(-1))
+        tr = plan.traveltime(px, py, pz, rx.expand(n, m).contiguous().view(-1),
+                             ry.expand(n, m).contiguous().view(-1))
+        return (ts.double() + tr.double()).view(n, m)
+
+    return fn

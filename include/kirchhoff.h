@@ -175,12 +175,11 @@ KH_API kh_status kirchhoff_sync(kh_plan p, void* cuda_stream);
  *  KH_OPT_WAIT_POLLS: limit every bounded in-kernel wait to `value` polls (0 restores the
  *                     default, about two seconds of polling).  A test sets 1 to check that
  *                     a wait which runs out returns KH_ERR_TIMEOUT with the context intact.
- *  KH_OPT_FAST_MATH:  1 = hardware approximate sqrt/log2 in the hot loop, 0 = IEEE sqrt and
- *                     the accurate log2 (default 1 after the accuracy study; both are
- *                     parity-tested).
- *  KH_OPT_TILE:       image tile of one CTA, encoded as cx | cy << 8 | cz << 16 (threads per
- *                     CTA along x, y and z-groups, cx*cy*cz == 256; each thread owns 16
- *                     consecutive z samples of one column); 0 restores the default. */
+ *  KH_OPT_FAST_MATH:  1 = hardware approximate square root and reciprocal in the hot loop
+ *                     (default), 0 = IEEE-rounded ones; both are parity-tested.
+ *  KH_OPT_TILE:       image tile of one CTA, encoded as cx | cy << 10 | cz << 20 (threads per
+ *                     CTA along x, y and z-groups, cx*cy*cz == 256, cz <= 16; each thread owns
+ *                     16 consecutive z samples of one column); 0 restores the default. */
 typedef enum { KH_OPT_WAIT_POLLS = 1, KH_OPT_FAST_MATH = 2, KH_OPT_TILE = 3 } kh_option;
 KH_API kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value);
 

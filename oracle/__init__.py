@@ -64,6 +64,7 @@ def lib():
             _lib.ko_bins.argtypes = [D, L, P, P, P, P, P]
             _lib.ko_traveltime.argtypes = [D, L, P, P, P, P, P]
             _lib.ko_count.argtypes = [D, L, P, P, P, P]
+            _lib.ko_arrivals.argtypes = [D, L, P, P, P, L, P, P, P, P, P]
             _lib.ko_count.restype = ctypes.c_longlong
             _lib.ko_set_mutation.argtypes = [ctypes.c_int]
             _lib.ko_set_threads.argtypes = [ctypes.c_int]
@@ -178,17 +179,13 @@ def arrival_times(points, s, trace_idx) -> np.ndarray:
     [n_points, len(trace_idx)], using this oracle's traveltime."""
     pts = np.asarray(points, dtype=np.float64)
     j = np.asarray(trace_idx)
-    sx = s.sx[j].astype(np.float64)[None, :]
-    rx = s.rx[j].astype(np.float64)[None, :]
-    sy = (s.sy[j].astype(np.float64) if s.dim == 3 else np.zeros(j.size))[None, :]
-    ry = (s.ry[j].astype(np.float64) if s.dim == 3 else np.zeros(j.size))[None, :]
-    x, y, z = pts[:, 0:1], pts[:, 1:2], pts[:, 2:3]
-    if s.dim == 2:
-        y = np.zeros_like(y)
-    Rs = np.sqrt((x - sx) ** 2 + (y - sy) ** 2 + z ** 2)
-    Rr = np.sqrt((x - rx) ** 2 + (y - ry) ** 2 + z ** 2)
-    zz = np.broadcast_to(z, Rs.shape)
-    return (traveltime(s, Rs, zz) + traveltime(s, Rr, zz)).reshape(Rs.shape)
+    px, py, pz = (np.ascontiguousarray(pts[:, i]) for i in range(3))
+    sx, sy, rx, ry = (np.ascontiguousarray(np.asarray(a)[j], dtype=np.float32)
+                      for a in (s.sx, s.sy, s.rx, s.ry))
+    out = np.empty((pts.shape[0], j.size), dtype=np.float64)
+    lib().ko_arrivals(ctypes.byref(desc(s)), pts.shape[0], _ptr(px), _ptr(py), _ptr(pz), j.size,
+                      _ptr(sx), _ptr(sy), _ptr(rx), _ptr(ry), _ptr(out))
+    return out
 
 
 def cgls(s, data, n_iter: int, m0=None):

@@ -371,6 +371,28 @@ int ko_vgrad(const ko_desc* d, long ntr, const float* sx, const float* sy, const
     return 0;
 }
 
+/* Two-way times source -> point -> receiver for every (point, trace) pair, for the
+ * synthesis of test data: out[p * ntr + j] = T(x_p, s_j) + T(x_p, r_j). */
+int ko_arrivals(const ko_desc* d, long npts, const double* px, const double* py, const double* pz,
+                long ntr, const float* sx, const float* sy, const float* rx, const float* ry,
+                double* out)
+{
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < npts; ++p) {
+        double x = px[p], y = (d->dim == 3) ? py[p] : 0.0, z = pz[p];
+        for (long j = 0; j < ntr; ++j) {
+            double ssy = (d->dim == 3) ? (double)sy[j] : 0.0, rry = (d->dim == 3) ? (double)ry[j] : 0.0;
+            double Rs = sqrt((x - sx[j]) * (x - sx[j]) + (y - ssy) * (y - ssy) + z * z);
+            double Rr = sqrt((x - rx[j]) * (x - rx[j]) + (y - rry) * (y - rry) + z * z);
+            double Ts, Tr;
+            traveltime(d, Rs, z, &Ts, NULL, NULL);
+            traveltime(d, Rr, z, &Tr, NULL, NULL);
+            out[p * ntr + j] = Ts + Tr;
+        }
+    }
+    return 0;
+}
+
 /* Work count of Eq. 2: number of (image point, in-aperture trace) pairs with a valid bin. */
 long long ko_count(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
                    const float* ry)

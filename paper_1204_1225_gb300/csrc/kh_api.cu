@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#define _USE_MATH_DEFINES
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -272,9 +273,13 @@ static GeomParams geom_of(const kh_desc& d)
     g.kabs = std::fabs(g.k);
     g.t0 = (float)d.t0;
     g.dt = (float)d.dt;
-    if (lin) g.C1 = (float)(std::log(2.0) / (g.kabs * d.dt));
-    else g.C1 = (float)(1.0 / (d.v0 * d.dt));
-    g.C0h = (float)(-d.t0 / d.dt - 0.5);
+    g.t0d = d.t0;
+    g.dtd = d.dt;
+    g.a = lin ? g.k * g.k / (2.0 * d.v0) : 0.0;
+    const double c1 = lin ? 1.0 / (g.kabs * d.dt) : 1.0 / (d.v0 * d.dt);
+    g.C1 = (float)c1;
+    g.C1lo = (float)(c1 - (double)g.C1);
+    g.c0 = -d.t0 / d.dt - 0.5;
     g.weight = d.weight == KH_W_OBLIQ_SPREAD ? 1 : 0;
     g.wscale = 1.0 / (2.0 * d.r0 * d.r0);
     g.use_aperture = d.aperture > 0 ? 1 : 0;
@@ -287,26 +292,134 @@ static GeomParams geom_of(const kh_desc& d)
     return g;
 }
 
-static TileShape tile_of(const kh_plan_s* p)
+// Fits ln(1 + x) = x (1 + x Q) on [lo, hi], Q a polynomial in t = (x - m)/h (m, h: centre
+// and half-width), by interpolation at the Chebyshev nodes of [-1, 1] (well conditioned in
+// t); then checks the FP32-coefficient evaluation against log1p in double on a dense grid.
+// Returns false if the interval is too wide for the term count.
+static bool fit_log1p(double lo, double hi, int terms, float* coef, float* scale, float* offset,
+                      double tol = 2e-9)
+{
+    const int n = terms - 1;
+    const double m = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
+    double A[LP_LONG][LP_LONG + 1];
+    for (int i = 0; i < n; ++i) {
+        const double t = std::cos((2.0 * i + 1.0) * M_PI / (2.0 * n));
+        const double x = m + h * t;
+        double q;
+        if (std::fabs(x) < 1e-4) {
+            q = -0.5 + x / 3.0 - x * x / 4.0 + x * x * x / 5.0 - x * x * x * x / 6.0;
+        } else {
+            q = (std::log1p(x) / x - 1.0) / x;
+        }
+        double pw = 1.0;
+        for (int j = 0; j < n; ++j) {
+            A[i][j] = pw;
+            pw *= t;
+        }
+        A[i][n] = q;
+    }
+    for (int c = 0; c < n; ++c) {   // Gaussian elimination, partial pivoting
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return false;
+        if (piv != c)
+            for (int j = 0; j <= n; ++j) std::swap(A[c][j], A[piv][j]);
+        for (int r = c + 1; r < n; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int j = c; j <= n; ++j) A[r][j] -= f * A[c][j];
+        }
+    }
+    double cq[LP_LONG];
+    for (int r = n - 1; r >= 0; --r) {
+        double v = A[r][n];
+        for (int j = r + 1; j < n; ++j) v -= A[r][j] * cq[j];
+        cq[r] = v / A[r][r];
+    }
+    coef[0] = 1.f;
+    for (int j = 0; j < n; ++j) coef[j + 1] = (float)cq[j];
+    *scale = (float)(1.0 / h);
+    *offset = (float)(-m / h);
+    double worst = 0.0;
+    for (int i = 0; i <= 4000; ++i) {
+        const double x = lo + (hi - lo) * i / 4000.0;
+        const double t = (double)*scale * x + (double)*offset;
+        double p = coef[terms - 1];
+        for (int j = terms - 2; j >= 1; --j) p = p * t + coef[j];
+        worst = std::max(worst, std::fabs(x * (1.0 + x * p) - std::log1p(x)));
+    }
+    return worst <= tol;
+}
+
+// Linear v(z): the bound on rho = U/U_c - 1 over a tile (|dT| <= distance / v_min along the
+// straight segment from the tile centre, per leg).
+static double rho_bound(const kh_desc& d, const GeomParams& g, int cx, int cy, int cz)
+{
+    const double ex = (cx - 1) * d.dx, ey = (d.dim == 3 ? (cy - 1) * d.dy : 0.0);
+    const double ez = (cz * NZ - 1) * d.dz;
+    const double half = 0.5 * std::sqrt(ex * ex + ey * ey + ez * ez);
+    const double zlo = std::min(d.oz, d.oz + (d.nz - 1) * d.dz), zhi = std::max(d.oz, d.oz + (d.nz - 1) * d.dz);
+    const double vmin = std::min(d.v0 + d.k * zlo, d.v0 + d.k * zhi);
+    return 2.0 * g.kabs * half / vmin * 1.02 + 1e-6;
+}
+
+// The ln(1 + rho) fit for the tile: 12 terms if they reach 2e-9, else 20, else unsupported.
+static kh_status prepare_linear(const kh_desc& d, const TileShape& t, GeomParams& g)
+{
+    g.lp_terms = LP_SHORT;
+    if (g.k == 0.0) return KH_OK;
+    const double b = rho_bound(d, g, t.cx, t.cy, t.cz);
+    g.rho_max = (float)std::expm1(b);
+    // ln-error budget: 5e-6 of a sample in tau, i.e. 5e-6 |k| dt in ln U
+    const double tol = std::max(5e-6 * g.kabs * d.dt, 1e-12);
+    if (fit_log1p(std::expm1(-b), std::expm1(b), LP_SHORT, g.lp, &g.lp_s, &g.lp_o, tol)) return KH_OK;
+    g.lp_terms = LP_LONG;
+    if (fit_log1p(std::expm1(-b), std::expm1(b), LP_LONG, g.lp, &g.lp_s, &g.lp_o, tol)) return KH_OK;
+    return fail(KH_ERR_UNSUPPORTED, "tile too large for the v(z) delta evaluation (rho up to %.3f); "
+                                    "choose a smaller tile with KH_OPT_TILE", std::expm1(b));
+}
+
+static TileShape shape(const kh_desc& d, int cx, int cy, int cz)
 {
     TileShape t;
-    int cx, cy, cz;
-    if (p->tile_code) {
-        cx = (int)(p->tile_code & 0xff);
-        cy = (int)((p->tile_code >> 8) & 0xff);
-        cz = (int)((p->tile_code >> 16) & 0xff);
-    } else if (p->d.dim == 3) {
-        cx = 16; cy = 16; cz = 1;
-    } else {
-        cx = 32; cy = 1; cz = 8;
-    }
     t.cx = cx;
     t.cy = cy;
     t.cz = cz;
-    t.tiles_x = (p->d.nx + cx - 1) / cx;
-    t.tiles_y = (p->d.ny + cy - 1) / cy;
-    t.tiles_z = (p->d.nz + cz * NZ - 1) / (cz * NZ);
+    t.tiles_x = (d.nx + cx - 1) / cx;
+    t.tiles_y = (d.ny + cy - 1) / cy;
+    t.tiles_z = (d.nz + cz * NZ - 1) / (cz * NZ);
     return t;
+}
+
+// The CTA tile: the caller's choice, else the most compact candidate whose v(z) rho range the
+// short polynomial covers (any candidate for constant velocity).
+static TileShape tile_of(const kh_plan_s* p)
+{
+    const kh_desc& d = p->d;
+    if (p->tile_code)
+        return shape(d, (int)(p->tile_code & 0x3ff), (int)((p->tile_code >> 10) & 0x3ff),
+                     (int)((p->tile_code >> 20) & 0x3ff));
+    static const int c3[][3] = {{16, 16, 1}, {32, 8, 1}, {8, 8, 4}, {16, 8, 2}};
+    static const int c2[][3] = {{64, 1, 4}, {32, 1, 8}, {128, 1, 2}, {16, 1, 16}};
+    const int(*c)[3] = d.dim == 3 ? c3 : c2;
+    const int nc = 4;
+    GeomParams g = geom_of(d);
+    if (g.k == 0.0) return shape(d, c[0][0], c[0][1], c[0][2]);
+    int best = 0;
+    double bb = 1e30;
+    for (int i = 0; i < nc; ++i) {
+        // prefer shapes the short fit covers; among the rest the smallest rho bound
+        const double b = rho_bound(d, g, c[i][0], c[i][1], c[i][2]);
+        float tmp[LP_LONG], ts, to;
+        if (fit_log1p(std::expm1(-b), std::expm1(b), LP_SHORT, tmp, &ts, &to,
+                      std::max(5e-6 * g.kabs * d.dt, 1e-12)))
+            return shape(d, c[i][0], c[i][1], c[i][2]);
+        if (b < bb) {
+            bb = b;
+            best = i;
+        }
+    }
+    return shape(d, c[best][0], c[best][1], c[best][2]);
 }
 
 template <typename T>
@@ -488,9 +601,10 @@ kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value)
                 p->tile_code = 0;
                 return KH_OK;
             }
-            const int cx = (int)(value & 0xff), cy = (int)((value >> 8) & 0xff), cz = (int)((value >> 16) & 0xff);
-            if (cx < 1 || cy < 1 || cz < 1 || cx * cy * cz != CONSUMERS || (value >> 24) != 0)
+            const int cx = (int)(value & 0x3ff), cy = (int)((value >> 10) & 0x3ff), cz = (int)((value >> 20) & 0x3ff);
+            if (cx < 1 || cy < 1 || cz < 1 || cx * cy * cz != CONSUMERS || (value >> 30) != 0)
                 return fail(KH_ERR_INVALID_ARG, "tile cx*cy*cz must equal %d", CONSUMERS);
+            if (cz > 16) return fail(KH_ERR_INVALID_ARG, "tile cz must be <= 16");
             if (p->d.dim == 2 && cy != 1) return fail(KH_ERR_INVALID_ARG, "tile cy must be 1 for dim 2");
             p->tile_code = value;
             return KH_OK;
@@ -518,11 +632,13 @@ kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy
     const void* tr_ptr = nullptr;
     GeomParams g = geom_of(p->d);
     if ((st = staged_traces(p, ntr, traces, s, &tr_ptr, &g.ld)) != KH_OK) return st;
+    const TileShape tile = tile_of(p);
+    if ((st = prepare_linear(p->d, tile, g)) != KH_OK) return st;
     TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};
     WaitCfg w{p->ws_status, p->wait_polls, WAIT_NS};
     const int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
     prof_begin(p, s);
-    cudaError_t e = launch_migrate(g, tile_of(p), ts, tr_ptr, image, vk, p->fast_math, w, s);
+    cudaError_t e = launch_migrate(g, tile, ts, tr_ptr, image, vk, p->fast_math, w, s);
     prof_end(p, s);
     ++p->launches;
     if (e != cudaSuccess) return cuda_fail(e, "migration kernel");

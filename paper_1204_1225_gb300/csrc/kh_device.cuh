@@ -54,6 +54,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// Non-blocking probe of the phase (used when a poll budget is set, so one poll is one probe).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -67,11 +81,15 @@ __device__ __forceinline__ unsigned long long global_ns()
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long polls,
                                                   long long ns, const int* status)
 {
+    if (polls > 0) {
+        for (long long i = 0; i < polls; ++i)
+            if (mbar_test_wait(bar, parity)) return true;
+        return false;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (long long i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (polls > 0 && i >= polls) return false;
         if ((i & 63) == 0) {
             if ((long long)(global_ns() - t0) > ns) return false;
             if (status && *reinterpret_cast<const volatile int*>(status) != 0) return false;
@@ -109,6 +127,18 @@ __device__ __forceinline__ float hsqrt(float x)
         return r;
     } else {
         return __fsqrt_rn(x);
+    }
+}
+
+template <bool FAST>
+__device__ __forceinline__ float hrcp(float x)
+{
+    if constexpr (FAST) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    } else {
+        return __frcp_rn(x);
     }
 }
 

@@ -21,6 +21,11 @@ constexpr int BMAX = 64;
 constexpr float MAGIC = 12582912.0f;
 constexpr int MAGIC_BITS = 0x4B400000;
 
+// Coefficients of the ln(1 + rho) polynomial of the linear-velocity delta formulation:
+// 12 terms for compact tiles, 20 for wide ones (chosen per launch from the tile's rho bound).
+constexpr int LP_SHORT = 12;
+constexpr int LP_LONG = 20;
+
 // Default wait limit: polls of mbarrier.try_wait, each checked against a 2 s wall clock.
 constexpr long long WAIT_NS = 2000000000LL;
 
@@ -40,10 +45,20 @@ struct GeomParams {
     double ox, oy, oz, dx, dy, dz;
     float fdz;
     // velocity (FP32 constants for the hot loop, FP64 for per-z set-up)
-    double v0, k;            // k already |k| for the hot loop's log form
+    double v0, k;            // v(z) = v0 + k z (k = 0: constant velocity)
     double kabs;
-    float C1, C0h;           // tau - 1/2 = L * C1 + C0h (L = R_s+R_r or log2 U)
-    float t0, dt;
+    double a;                // k^2 / (2 v0): q = a R^2 / (v0 + k z)
+    float lp[LP_LONG];       // ln(1 + rho) = rho (1 + rho Q(t)), t = rho lp_s + lp_o,
+                             // Q(t) = sum_j lp[j + 1] t^j (Chebyshev-node fit in t on [-1, 1])
+    float lp_s, lp_o;
+    int lp_terms;            // LP_SHORT or LP_LONG
+    float rho_max;           // |rho| bound the polynomial was fitted for
+    float C1, C1lo;          // tau - tau_ref = L * (C1 + C1lo) with L = R_s + R_r (constant v,
+                             // tau_ref = -t0/dt) or ln(U/U_c) (linear v); C1lo = FP32 rounding
+                             // error of C1
+    double c0;               // -t0/dt - 1/2 (the window origin is subtracted per trace)
+    float t0, dt;            // FP32 copies for the window bounds
+    double t0d, dtd;         // exact values for the FP64 references
     // weight
     int weight;              // 0 one, 1 obliquity x spreading
     double wscale;           // 1 / (2 r0^2)

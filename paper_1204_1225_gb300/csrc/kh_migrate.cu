@@ -5,15 +5,17 @@
 // z samples of one image column and keeps their FP32 accumulators in registers for the
 // whole kernel; nothing is accumulated in global memory.  The producer warp walks the
 // bin's traces (sorted by bin), culls those whose midpoint is outside the aperture of the
-// tile footprint, bounds the two-way time over the tile box to a sample window, and stages
-// each window into a 3-deep shared-memory ring with one cp.async.bulk per trace (16-byte
-// aligned, no multicast) completing on the stage's mbarrier.  Consumers read the staged
-// samples at tau = (T_s + T_r - t0)/dt, interpolate linearly, weight and accumulate.
-// All mbarrier waits are bounded; a wait that runs out sets the plan's status word.
+// tile footprint, bounds the two-way time over the tile box to a sample window
+// [lo, hi], computes the trace's FP64 reference at the tile centre (linear v(z)), and
+// stages the window into a 3-deep shared-memory ring with one cp.async.bulk per trace
+// (16-byte aligned, no multicast) completing on the stage's mbarrier.  Consumers evaluate
+// tau for their points (kh_tau.cuh), read the staged samples, interpolate linearly, weight
+// and accumulate.  All mbarrier waits are bounded; a wait that runs out sets the plan's
+// status word and the CTA leaves only after its copies have landed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
-#include "kh_device.cuh"
+#include "kh_tau.cuh"
 
 namespace kh {
 
@@ -26,14 +28,23 @@ __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(
 template <>
 __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+constexpr int MAX_ZG = 16;          // z-groups per CTA (cz)
+constexpr int SLACK = 16;           // zeroed elements after the ring (reads one past a window)
+
 struct __align__(16) MigSmem {
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
     int cnt[STAGES];
     int last[STAGES];
-    float4 hdr[STAGES][BMAX];   // sx, sy, rx, ry
-    float2 mid[STAGES][BMAX];   // FP32 midpoint
-    int4 win[STAGES][BMAX];     // cb = -MAGIC_BITS - lo, sb = smem index of sample lo, lim = hi - lo
+    // per staged trace
+    float4 hdr[STAGES][BMAX];   // const v: (sx, sy, rx, ry); linear: (c_x-2s_x, c_y-2s_y, c_x-2r_x, c_y-2r_y)
+    float4 refs[STAGES][BMAX];  // linear: source-leg LegRef
+    float4 refr[STAGES][BMAX];  // linear: receiver-leg LegRef
+    float2 mid[STAGES][BMAX];   // FP32 midpoint (aperture test)
+    int4 win[STAGES][BMAX];     // x: tau_ref - lo - 1/2 (float bits), y: smem index of sample lo
+                                // minus MAGIC_BITS, z/w: c_mid/c_half (float bits) of the valid
+                                // range -1/2 <= tau - lo - 1/2 <= hi - lo - 1/2
+    float4 zc[MAX_ZG * NZ];     // per-z constants (ZConst for linear v; (z^2, w_z, 0, 0) for constant v)
     float zero[4];
 };
 
@@ -43,13 +54,13 @@ __host__ __device__ constexpr size_t mig_static_bytes() { return (sizeof(MigSmem
 __host__ __device__ inline int mig_cap(int nt, int ealign)
 {
     const int need = (nt + 2 * ealign + ealign - 1) / ealign * ealign;
-    const int base = 24576 / 4;   // 24 KB of FP32 (48 KB worth of 16-bit samples is the same count)
+    const int base = 24576 / 4;
     return need > base ? need : base;
 }
 
 size_t migrate_smem_bytes(const GeomParams& g)
 {
-    return mig_static_bytes() + (size_t)STAGES * mig_cap(g.nt, g.elem_align) * g.esize;
+    return mig_static_bytes() + ((size_t)STAGES * mig_cap(g.nt, g.elem_align) + SLACK) * g.esize;
 }
 
 // Smallest and largest one-way time from a surface point at horizontal distance [hmin, hmax]
@@ -78,16 +89,21 @@ __device__ __forceinline__ void rect_dist(float px, float py, float xlo, float x
     dmax = sqrtf(bx * bx + by * by);
 }
 
+struct TileBox {
+    float xlo, xhi, ylo, yhi, zlo, zhi;   // FP32 box of the valid samples (window bounds)
+    double cx, cy, cz;                    // FP64 centre (linear-path reference point)
+};
+
 // ------------------------------------------------------------------ producer warp
-template <typename TT>
+template <int VEL, typename TT>
 __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                              const TraceSet& tr, const TT* __restrict__ traces, int tb, int te,
-                             float xlo, float xhi, float ylo, float yhi, float zlo, float zhi,
-                             int vel, const WaitCfg& wc)
+                             const TileBox& box, const WaitCfg& wc)
 {
     const int lane = threadIdx.x & 31;
     const float v0 = (float)g.v0, kf = (float)g.k;
     const float inv_dt = 1.f / g.dt;
+    const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
     int cur = tb;
     int n = 0;
     bool failed = false;
@@ -112,16 +128,16 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                 m = tr.mid[k];
                 ok = true;
                 if (g.use_aperture) {
-                    const float ax = fmaxf(fmaxf(xlo - m.x, m.x - xhi), 0.f);
-                    const float ay = fmaxf(fmaxf(ylo - m.y, m.y - yhi), 0.f);
+                    const float ax = fmaxf(fmaxf(box.xlo - m.x, m.x - box.xhi), 0.f);
+                    const float ay = fmaxf(fmaxf(box.ylo - m.y, m.y - box.yhi), 0.f);
                     ok = ax * ax + ay * ay <= g.A2cull;
                 }
                 if (ok) {
                     float hs0, hs1, hr0, hr1, ts0, ts1, tr0, tr1;
-                    rect_dist(h.x, h.y, xlo, xhi, ylo, yhi, hs0, hs1);
-                    rect_dist(h.z, h.w, xlo, xhi, ylo, yhi, hr0, hr1);
-                    leg_bounds(hs0, hs1, zlo, zhi, vel, v0, kf, ts0, ts1);
-                    leg_bounds(hr0, hr1, zlo, zhi, vel, v0, kf, tr0, tr1);
+                    rect_dist(h.x, h.y, box.xlo, box.xhi, box.ylo, box.yhi, hs0, hs1);
+                    rect_dist(h.z, h.w, box.xlo, box.xhi, box.ylo, box.yhi, hr0, hr1);
+                    leg_bounds(hs0, hs1, box.zlo, box.zhi, VEL, v0, kf, ts0, ts1);
+                    leg_bounds(hr0, hr1, box.zlo, box.zhi, VEL, v0, kf, tr0, tr1);
                     const float tlo = (ts0 + tr0 - g.t0) * inv_dt;
                     const float thi = (ts1 + tr1 - g.t0) * inv_dt;
                     const float slo = 2.f + 2e-4f * fabsf(tlo), shi = 2.f + 2e-4f * fabsf(thi);
@@ -138,8 +154,7 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                 }
             }
             const unsigned okm = __ballot_sync(0xffffffffu, ok);
-            // exclusive prefix of window lengths over accepted lanes
-            int pre = ok ? len_al : 0;
+            int pre = ok ? len_al : 0;   // inclusive prefix of window lengths
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, pre, o);
@@ -152,19 +167,34 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
             const unsigned nofit = okm & ~fm;
             const int consumed = nofit ? (__ffs(nofit) - 1) : min(32, te - cur);
             const int nfit = __popc(fm);
-            // bytes staged by the fitting lanes
             int bytes = fits ? len_al * g.esize : 0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
             int used_add = fits ? len_al : 0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) used_add += __shfl_xor_sync(0xffffffffu, used_add, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+                used_add += __shfl_xor_sync(0xffffffffu, used_add, o);
+            }
             if (fits) {
                 const int slot = cnt + rank;
                 const int dst = s * cap + used + excl;
-                S.hdr[s][slot] = h;
+                double tau_ref = -g.t0d / g.dtd;
+                if constexpr (VEL == VK_LINEAR) {
+                    LegRef rs, rr;
+                    const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs);
+                    const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr);
+                    tau_ref += (ls + lr) * inv_kdt;
+                    S.refs[s][slot] = make_float4(rs.Rc2, rs.qc, rs.wc, rs.iuc);
+                    S.refr[s][slot] = make_float4(rr.Rc2, rr.qc, rr.wc, rr.iuc);
+                    S.hdr[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
+                                                 (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
+                } else {
+                    S.hdr[s][slot] = h;
+                }
                 S.mid[s][slot] = m;
-                S.win[s][slot] = make_int4(-MAGIC_BITS - lo, dst + (lo - lo_al), hi - lo, 0);
+                const float lim = (float)(hi - lo);
+                S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo - 0.5)),
+                                           dst + (lo - lo_al) - MAGIC_BITS,
+                                           __float_as_int(0.5f * (lim - 1.f)), __float_as_int(0.5f * lim));
             }
             if (lane == 0 && bytes > 0) mbar_expect_tx(&S.full[s], (uint32_t)bytes);
             __syncwarp();
@@ -198,64 +228,25 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
 }
 
 // ------------------------------------------------------------------ consumer warps
-template <int VEL, int WGT, bool FAST>
-__device__ __forceinline__ float tau_half(float dhs2, float dhr2, float z2, float a, float az2,
-                                          float b, float wz, const GeomParams& g, float& W)
-{
-    // returns tau - 1/2; W is the weight of this contribution
-    if constexpr (VEL == VK_CONST) {
-        const float Rs = hsqrt<FAST>(dhs2 + z2);
-        const float Rr = hsqrt<FAST>(dhr2 + z2);
-        const float S = Rs + Rr;
-        if constexpr (WGT == 1) W = wz * S; else W = 1.f;
-        return fmaf(S, g.C1, g.C0h);
-    } else {
-        float xs, xr;
-        if constexpr (WGT == 1) {
-            const float Rs = hsqrt<FAST>(dhs2 + z2);
-            const float Rr = hsqrt<FAST>(dhr2 + z2);
-            const float ss = b * Rs, sr = b * Rr;            // sqrt(q)
-            const float qs = ss * ss, qr = sr * sr;
-            xs = fmaf(ss, hsqrt<FAST>(qs + 2.f), qs);       // e^{|k| T} - 1
-            xr = fmaf(sr, hsqrt<FAST>(qr + 2.f), qr);
-            W = wz * (Rs + Rr);
-        } else {
-            const float qs = fmaf(dhs2, a, az2), qr = fmaf(dhr2, a, az2);
-            xs = qs + hsqrt<FAST>(qs * (qs + 2.f));
-            xr = qr + hsqrt<FAST>(qr * (qr + 2.f));
-            W = 1.f;
-        }
-        const float y = fmaf(xs, xr, xs + xr);              // (1+xs)(1+xr) - 1
-        const float L = hlog2<FAST>(1.f + y);               // |k| (T_s + T_r) / ln 2
-        return fmaf(L, g.C1, g.C0h);
-    }
-}
-
-template <int VEL, int WGT, bool FAST, typename TT>
+template <int VEL, int WGT, bool FAST, typename TT, int LPT>
 __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, const TileShape& ts,
-                             int x0, int y0, int z0, int bin, float* __restrict__ image,
-                             const WaitCfg& wc)
+                             int x0, int y0, int z0, const TileBox& box, int bin,
+                             float* __restrict__ image, const WaitCfg& wc)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
     const int ix = x0 + tx, iy = y0 + ty, izb = z0 + tzg * NZ;
     const bool col_ok = ix < g.nx && iy < g.ny;
     const float cxf = col_coord(g.ox, ix, g.dx);
     const float cyf = (g.dim == 3) ? col_coord(g.oy, iy, g.dy) : 0.f;
-
-    float z2[NZ], ca[NZ], cb[NZ], wz[NZ], acc[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) {
-        const double zd = __dadd_rn(g.oz, __dmul_rn((double)(izb + i), g.dz));
-        z2[i] = (float)(zd * zd);
-        const double vz = g.v0 + g.k * zd;
-        const double alpha = (VEL == VK_LINEAR) ? g.kabs * g.kabs / (2.0 * g.v0 * vz) : 0.0;
-        ca[i] = (float)alpha;                               // q = a R^2
-        cb[i] = (float)((WGT == 1) ? sqrt(fmax(alpha, 0.0)) : alpha * zd * zd);
-        wz[i] = (WGT == 1 && fabs(zd) >= 1e-6 * fabs(g.dz)) ? (float)(zd * g.wscale) : 0.f;
-        acc[i] = 0.f;
-    }
+    const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
+    const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
+    const float4* zc = &S.zc[tzg * NZ];
     const int zero_off = (int)(((const char*)S.zero - (const char*)data) / (int)sizeof(TT));
+
+    float acc[NZ];
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) acc[i] = 0.f;
 
     bool failed = false;
     int n = 0;
@@ -268,33 +259,65 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
         const int cnt = S.cnt[s];
         const int last = S.last[s];
         for (int t = 0; t < cnt; ++t) {
-            const float4 h = S.hdr[s][t];
             const int4 w = S.win[s][t];
-            unsigned lim = col_ok ? (unsigned)w.z : 0u;
+            bool inside = col_ok;
             if (g.use_aperture) {
                 const float2 m = S.mid[s][t];
-                if (!in_aperture(cxf, cyf, m.x, m.y, g.A2)) lim = 0u;
+                inside = inside && in_aperture(cxf, cyf, m.x, m.y, g.A2);
             }
-            if (!__any_sync(0xffffffffu, lim != 0u)) continue;
-            const float dxs = cxf - h.x, dys = cyf - h.y;
-            const float dxr = cxf - h.z, dyr = cyf - h.w;
-            const float dhs2 = fmaf(dxs, dxs, dys * dys);
-            const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
+            if (!__any_sync(0xffffffffu, inside)) continue;
+            const float c0rel = __int_as_float(w.x);
+            const float cmid = __int_as_float(w.z);
+            const float chalf = inside ? __int_as_float(w.w) : -1.f;
+            const float4 h = S.hdr[s][t];
+            if constexpr (VEL == VK_CONST) {
+                const float dxs = cxf - h.x, dys = cyf - h.y;
+                const float dxr = cxf - h.z, dyr = cyf - h.w;
+                const float dhs2 = fmaf(dxs, dxs, dys * dys);
+                const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
 #pragma unroll
-            for (int i = 0; i < NZ; ++i) {
-                float W;
-                const float th = tau_half<VEL, WGT, FAST>(dhs2, dhr2, z2[i], ca[i], cb[i], cb[i],
-                                                          wz[i], g, W);
-                const float tm = __fadd_rn(th, MAGIC);
-                const float r = __fadd_rn(tm, -MAGIC);
-                const float f = __fadd_rn(__fadd_rn(th, -r), 0.5f);
-                const int idx = __float_as_int(tm) + w.x;   // i - lo
-                const int off = ((unsigned)idx < lim) ? idx + w.y : zero_off;
-                const float d0 = to_f32<TT>(data[off]);
-                const float d1 = to_f32<TT>(data[off + 1]);
-                const float val = fmaf(f, d1 - d0, d0);
-                if constexpr (WGT == 1) acc[i] = fmaf(W, val, acc[i]);
-                else acc[i] += val;
+                for (int i = 0; i < NZ; ++i) {
+                    const float4 c = zc[i];   // (z^2, w_z)
+                    const float Rs = hsqrt<FAST>(dhs2 + c.x);
+                    const float Rr = hsqrt<FAST>(dhr2 + c.x);
+                    const float Ssum = Rs + Rr;
+                    const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
+                    const float tm = __fadd_rn(th, MAGIC);
+                    const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
+                    const bool ok = fabsf(th - cmid) <= chalf;
+                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
+                    const float d0 = to_f32<TT>(data[off]);
+                    const float d1 = to_f32<TT>(data[off + 1]);
+                    const float val = fmaf(f, d1 - d0, d0);
+                    if constexpr (WGT == 1) acc[i] = fmaf(c.y * Ssum, val, acc[i]);
+                    else acc[i] += val;
+                }
+            } else {
+                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t];
+                const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w}, rr{rrv.x, rrv.y, rrv.z, rrv.w};
+                const float dPs = fmaf(dxc, cxf + h.x, dyc * (cyf + h.y));
+                const float dPr = fmaf(dxc, cxf + h.z, dyc * (cyf + h.w));
+                const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) {
+                    const float4 c4 = zc[i];
+                    const ZConst c{c4.x, c4.y, c4.z, c4.w};
+                    float sqs, sqr;
+                    const float rho_s = leg_delta<WGT, FAST>(dPs, c, rs, qc2s, sqs);
+                    const float rho_r = leg_delta<WGT, FAST>(dPr, c, rr, qc2r, sqr);
+                    const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);   // U/U_c - 1
+                    const float L = log1p_poly<LPT>(rho, g);
+                    const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
+                    const float tm = __fadd_rn(th, MAGIC);
+                    const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
+                    const bool ok = fabsf(th - cmid) <= chalf;
+                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
+                    const float d0 = to_f32<TT>(data[off]);
+                    const float d1 = to_f32<TT>(data[off + 1]);
+                    const float val = fmaf(f, d1 - d0, d0);
+                    if constexpr (WGT == 1) acc[i] = fmaf(c.gamma * (sqs + sqr), val, acc[i]);
+                    else acc[i] += val;
+                }
             }
         }
         __syncwarp();
@@ -302,7 +325,6 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
         ++n;
         if (last) break;
     }
-    (void)warp;
     if (failed) {
         if (lane == 0) atomicOr(wc.status, 1);
         return;
@@ -322,7 +344,7 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
     }
 }
 
-template <int VEL, int WGT, bool FAST, typename TT>
+template <int VEL, int WGT, bool FAST, typename TT, int LPT>
 __global__ void __launch_bounds__(THREADS, 2)
     k_migrate(GeomParams g, TileShape ts, TraceSet tr, const TT* __restrict__ traces,
               float* __restrict__ image, int cap, WaitCfg wc)
@@ -330,14 +352,33 @@ __global__ void __launch_bounds__(THREADS, 2)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MigSmem& S = *reinterpret_cast<MigSmem*>(smem_raw);
     TT* data = reinterpret_cast<TT*>(smem_raw + mig_static_bytes());
+    __shared__ int s_abort;
     const int bin = blockIdx.y;
     int t = blockIdx.x;
     const int tzi = t % ts.tiles_z;
     t /= ts.tiles_z;
     const int txi = t % ts.tiles_x, tyi = t / ts.tiles_x;
     const int x0 = txi * ts.cx, y0 = tyi * ts.cy, z0 = tzi * ts.cz * NZ;
+    const int xe = min(x0 + ts.cx, g.nx) - 1, ye = min(y0 + ts.cy, g.ny) - 1;
+    const int ze = min(z0 + ts.cz * NZ, g.nz) - 1;
 
-    __shared__ int s_abort;
+    TileBox box;
+    {
+        const float xa = col_coord(g.ox, x0, g.dx), xb = col_coord(g.ox, xe, g.dx);
+        const float ya = g.dim == 3 ? col_coord(g.oy, y0, g.dy) : 0.f;
+        const float yb = g.dim == 3 ? col_coord(g.oy, ye, g.dy) : 0.f;
+        const float za = (float)(g.oz + z0 * g.dz), zb = (float)(g.oz + ze * g.dz);
+        box.xlo = fminf(xa, xb);
+        box.xhi = fmaxf(xa, xb);
+        box.ylo = fminf(ya, yb);
+        box.yhi = fmaxf(ya, yb);
+        box.zlo = fminf(za, zb);
+        box.zhi = fmaxf(za, zb);
+        box.cx = g.ox + 0.5 * (x0 + xe) * g.dx;
+        box.cy = g.dim == 3 ? g.oy + 0.5 * (y0 + ye) * g.dy : 0.0;
+        box.cz = g.oz + 0.5 * (z0 + ze) * g.dz;
+    }
+
     if (threadIdx.x == 0) {
         // a wait in another CTA of this plan already ran out: results are invalid anyway
         s_abort = *reinterpret_cast<const volatile int*>(wc.status);
@@ -348,20 +389,28 @@ __global__ void __launch_bounds__(THREADS, 2)
         S.zero[0] = S.zero[1] = S.zero[2] = S.zero[3] = 0.f;
         fence_barrier_init();
     }
+    // per-z constants of the tile and a zero-filled ring (edge reads stay finite)
+    for (int i = threadIdx.x; i < ts.cz * NZ; i += blockDim.x) {
+        const double z = g.oz + (z0 + i) * g.dz;
+        if constexpr (VEL == VK_LINEAR) {
+            const ZConst c = z_constants(z, box.cz, g);
+            S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
+        } else {
+            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
+            S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
+        }
+    }
+    {
+        const int total = STAGES * cap + SLACK;
+        for (int i = threadIdx.x; i < total; i += blockDim.x) data[i] = TT(0.f);
+    }
     __syncthreads();
     if (s_abort) return;
     if (threadIdx.x >= CONSUMERS) {
-        const int xe = min(x0 + ts.cx, g.nx) - 1, ye = min(y0 + ts.cy, g.ny) - 1;
-        const int ze = min(z0 + ts.cz * NZ, g.nz) - 1;
-        const float xlo = col_coord(g.ox, x0, g.dx), xhi = col_coord(g.ox, xe, g.dx);
-        const float ylo = g.dim == 3 ? col_coord(g.oy, y0, g.dy) : 0.f;
-        const float yhi = g.dim == 3 ? col_coord(g.oy, ye, g.dy) : 0.f;
-        const float zlo = (float)(g.oz + z0 * g.dz), zhi = (float)(g.oz + ze * g.dz);
-        mig_producer<TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
-                         fminf(xlo, xhi), fmaxf(xlo, xhi), fminf(ylo, yhi), fmaxf(ylo, yhi),
-                         fminf(zlo, zhi), fmaxf(zlo, zhi), VEL, wc);
+        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
+                              box, wc);
     } else {
-        mig_consumer<VEL, WGT, FAST, TT>(S, data, g, ts, x0, y0, z0, bin, image, wc);
+        mig_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, wc);
     }
 }
 
@@ -369,7 +418,8 @@ template <int VEL, int WGT, bool FAST, typename TT>
 static cudaError_t launch_t(const GeomParams& g, const TileShape& t, const TraceSet& tr,
                             const void* traces, float* image, const WaitCfg& w, cudaStream_t s)
 {
-    auto kern = k_migrate<VEL, WGT, FAST, TT>;
+    auto kern = (VEL == VK_LINEAR && g.lp_terms == LP_LONG) ? k_migrate<VEL, WGT, FAST, TT, LP_LONG>
+                                                          : k_migrate<VEL, WGT, FAST, TT, LP_SHORT>;
     const size_t smem = migrate_smem_bytes(g);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -402,6 +452,7 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
                            const void* traces, float* image, int vel_kind, int fast_math,
                            const WaitCfg& w, cudaStream_t s)
 {
+    if (t.cz > MAX_ZG) return cudaErrorInvalidValue;
     switch (g.esize) {
         case 4: return launch_dtype<float>(g, t, tr, traces, image, vel_kind, fast_math, w, s);
         default: return cudaErrorInvalidValue;

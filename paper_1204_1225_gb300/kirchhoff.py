@@ -255,7 +255,7 @@ class Plan:
         kirchhoff_set_option(self.handle, KH_OPT_FAST_MATH, 1 if fast_math else 0)
         if tile is not None:
             cx, cy, cz = tile
-            kirchhoff_set_option(self.handle, KH_OPT_TILE, cx | (cy << 8) | (cz << 16))
+            kirchhoff_set_option(self.handle, KH_OPT_TILE, cx | (cy << 10) | (cz << 20))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -206,6 +206,29 @@ def reflectors_3d(rng: np.random.Generator, survey: Survey, n_planes: int = 4,
     return np.concatenate(pts, 0)
 
 
+def reflectors_2d(rng: np.random.Generator, survey: Survey, n_lines: int = 3,
+                  n_diffractors: int = 10, spacing: float = 5.0, line_amp: float = 0.1,
+                  max_dip_deg: float = 15.0) -> np.ndarray:
+    """Flat and dipping reflector lines z = z0 + a (x - xc) sampled every ``spacing`` m, plus
+    point diffractors (2D sections; y = 0)."""
+    xc = survey.ox + 0.5 * (survey.nx - 1) * survey.dx
+    wx = (survey.nx - 1) * survey.dx
+    zmax = survey.oz + (survey.nz - 1) * survey.dz
+    gx = np.arange(survey.ox, survey.ox + wx + 1e-9, spacing)
+    pts = []
+    amp = line_amp * spacing / 5.0
+    for i in range(n_lines):
+        z0 = rng.uniform(0.2 * zmax, 0.9 * zmax)
+        a = 0.0 if i == 0 else math.tan(math.radians(rng.uniform(-max_dip_deg, max_dip_deg)))
+        Z = z0 + a * (gx - xc)
+        keep = (Z > 0.0) & (Z < zmax)
+        pts.append(np.stack([gx[keep], np.zeros(int(keep.sum())), Z[keep],
+                             np.full(int(keep.sum()), amp)], 1))
+    pts.append(np.stack([rng.uniform(survey.ox, survey.ox + wx, n_diffractors), np.zeros(n_diffractors),
+                         rng.uniform(0.1 * zmax, zmax, n_diffractors), np.ones(n_diffractors)], 1))
+    return np.concatenate(pts, 0)
+
+
 # --------------------------------------------------------------------------------------
 # Trace synthesis
 # --------------------------------------------------------------------------------------

@@ -31,3 +31,23 @@ def cfg1_inputs(noise=0.1):
     sc = sv.point_scatterers_2d(np.random.default_rng(sv.BASE_SEED))
     d = sv.synthesize(s, sc, oracle.arrival_times, 25.0, noise_sigma=noise).numpy()
     return s, d
+
+
+def synth_on_gpu(s, scatterers, freq, noise=0.0, seed=sv.BASE_SEED):
+    """Paper-shaped traces (Ricker events at oracle arrival times) synthesised with torch on
+    the GPU; the arrival times come from the FP64 oracle, never from the library."""
+    return sv.synthesize(s, scatterers, oracle.arrival_times, freq, noise_sigma=noise, seed=seed,
+                         device="cuda").cpu().numpy()
+
+
+def cfg2_reduced(ntr=2000, n=64):
+    """The 3D v(z) survey geometry on a coarser image (n^3 covering the same volume)."""
+    s = sv.survey_3d_gradient(ntr=ntr, n=n)
+    sc = sv.reflectors_3d(np.random.default_rng(sv.BASE_SEED), s, spacing=100.0)
+    return s, synth_on_gpu(s, sc, 20.0)
+
+
+def cfg4_reduced(n_shots=12, nx=160, nz=120, nt=1000):
+    s = sv.survey_25d_lsm(nx=nx, nz=nz, nt=nt, n_shots=n_shots)
+    sc = sv.reflectors_2d(np.random.default_rng(sv.BASE_SEED), s, spacing=5.0)
+    return s, synth_on_gpu(s, sc, 25.0)

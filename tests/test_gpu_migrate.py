@@ -55,7 +55,7 @@ def test_random_surveys(case, fast_math):
     assert rel_l2(got, want) < FP32_REL_L2
 
 
-@pytest.mark.parametrize("tile", [(32, 1, 8), (64, 1, 4), (256, 1, 1), (8, 1, 32)])
+@pytest.mark.parametrize("tile", [(32, 1, 8), (64, 1, 4), (128, 1, 2), (16, 1, 16)])
 def test_tile_shapes_2d(tile):
     rng = np.random.default_rng(5)
     s = sv.survey_random(rng, 2, 64, 75, 1, 90, 300, vel="linear", n_bins=3, h=10.0, k=0.5)
@@ -64,13 +64,25 @@ def test_tile_shapes_2d(tile):
     assert rel_l2(got, oracle.migrate(s, d)) < FP32_REL_L2
 
 
-@pytest.mark.parametrize("tile", [(16, 16, 1), (8, 8, 4), (32, 8, 1), (4, 4, 16)])
+@pytest.mark.parametrize("tile", [(16, 16, 1), (8, 8, 4), (32, 8, 1), (16, 8, 2)])
 def test_tile_shapes_3d(tile):
     rng = np.random.default_rng(6)
     s = sv.survey_random(rng, 3, 60, 21, 19, 35, 300, vel="linear", weight="obliq", aperture=120.0,
                          n_bins=3, h=12.5, k=0.5)
     d = sv.random_traces(s, 4, smooth=5)
     got, _ = gpu_migrate(s, d, tile=tile)
+    assert rel_l2(got, oracle.migrate(s, d)) < FP32_REL_L2
+
+
+def test_oversized_tile_is_refused_cleanly():
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    rng = np.random.default_rng(6)
+    s = sv.survey_random(rng, 3, 20, 8, 8, 256, 600, vel="linear", n_bins=2, h=25.0, k=0.8)
+    d = sv.random_traces(s, 4)
+    with pytest.raises(kh.KirchhoffError) as ei:
+        gpu_migrate(s, d, tile=(4, 4, 16))
+    assert ei.value.status == kh.KH_ERR_UNSUPPORTED
+    got, _ = gpu_migrate(s, d)          # the default tile adapts to the same survey
     assert rel_l2(got, oracle.migrate(s, d)) < FP32_REL_L2
 
 

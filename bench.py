@@ -39,15 +39,17 @@ from paper_1204_1225_gb300 import survey as sv  # noqa: E402
 # probe summarised in profiles/mufu_fma_throughput.md.
 N_SM = 152
 MUFU_PER_SM_CLK = 16
-# Transcendental (MUFU) operations each contribution needs by construction of the kernel's
-# formula: square roots of the two ray lengths and of the two q(q + 2) terms, one log2.
-MUFU_PER_CONTRIB = {("const", "one"): 2, ("const", "obliq"): 2, ("linear", "one"): 3,
-                    ("linear", "obliq"): 5}
+# Transcendental (MUFU) operations each contribution needs in the kernel's formulation:
+# constant v: the two ray lengths (2 sqrt); linear v(z): per leg sqrt(q) (weight only),
+# sqrt(q + 2) or sqrt(q (q + 2)), and the reciprocal of the cancellation-free w - w_c.
+MUFU_PER_CONTRIB = {("const", "one"): 2, ("const", "obliq"): 2, ("linear", "one"): 4,
+                    ("linear", "obliq"): 6}
 
 
 def workloads():
     return {
         "3d-vz-100k-256cube": lambda: sv.survey_3d_gradient(),
+        "3d-vz-40k-128cube": lambda: sv.survey_3d_gradient(ntr=40_000, n=128),
         "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
         "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
     }

@@ -193,6 +193,25 @@ KH_API kh_status kirchhoff_profile_read(kh_plan p, double* kernel_ms, long long*
 /* Number of kernel launches issued by this plan since creation (for launch accounting). */
 KH_API long long kirchhoff_launch_count(kh_plan p);
 
+/* Allocation-free migration (no counterpart in the paper: an interface for callers that
+ * cannot allocate device memory, such as services whose HBM is owned by another allocator's
+ * pool, or that must not call cudaMalloc after start-up because it can synchronise the
+ * device).  Same operation, arguments and result as kirchhoff_migrate, without a plan: the
+ * descriptor is validated on every call and the trace-sort scratch is one fixed 2.1 MB
+ * __device__ array inside the library, held by every GPU that loads it until the process
+ * exits.  Limits: ntr <= 65536, FP32 traces, trace rows 16-byte aligned (nt a multiple of 4).
+ * Larger inputs return KH_ERR_INVALID_ARG with a message; nothing is allocated.
+ * `status` is an optional DEVICE int: it is zeroed, then bit 0 is set if a bounded in-kernel
+ * wait ran out (NULL: a word inside the scratch is used and the outcome is not reported).
+ * The first call on each device looks up the scratch's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls on a device share the scratch
+ * and it keeps the previous call's contents: calls that overlap on the GPU (for example on
+ * two streams) race and must be serialised by the caller. */
+KH_API kh_status kirchhoff_migrate_noalloc(const kh_desc* d, int ntr, const float* sx,
+                                           const float* sy, const float* rx, const float* ry,
+                                           const void* traces, float* image, int* status,
+                                           void* cuda_stream);
+
 /* Thread-local message of the last failure ("" if none). */
 KH_API const char* kirchhoff_last_error(void);
 

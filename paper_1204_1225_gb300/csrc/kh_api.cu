@@ -738,3 +738,33 @@ const char* kirchhoff_last_error(void) { return g_err.c_str(); }
 const char* kirchhoff_version(void) { return "kirchhoff-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ helpers for the
+// allocation-free entry point (kh_noalloc.cu): the same validation, geometry, tile choice and
+// binning launches as the plan path, writing into caller-supplied device buffers.
+namespace kh {
+
+kh_status noalloc_prepare(const kh_desc* d, GeomParams* g, TileShape* t)
+{
+    kh_status st = validate_desc(d);
+    if (st != KH_OK) return st;
+    *g = geom_of(*d);
+    kh_plan_s tmp;   // host-only view for the tile choice; owns no device memory
+    tmp.d = *d;
+    *t = tile_of(&tmp);
+    return prepare_linear(*d, *t, *g);
+}
+
+cudaError_t noalloc_bin(int ntr, const float* sx, const float* sy, const float* rx, const float* ry,
+                        const kh_desc& d, int* bin, int* perm, int* bin_start, float4* hdr,
+                        float2* mid, cudaStream_t s)
+{
+    if (ntr > 0)
+        k_bin<<<(ntr + 255) / 256, 256, 0, s>>>(ntr, sx, sy, rx, ry, d.dim, d.n_bins, d.bin_width, bin);
+    k_sort<<<1, SORT_THREADS, 0, s>>>(ntr, d.n_bins, bin, perm, bin_start);
+    k_gather<<<std::max(1, std::min((ntr + 255) / 256, 4096)), 256, 0, s>>>(bin_start, d.n_bins, perm,
+                                                                            sx, sy, rx, ry, d.dim, hdr, mid);
+    return cudaGetLastError();
+}
+
+}  // namespace kh

@@ -48,4 +48,10 @@ void prof_begin(kh_plan_s* p, cudaStream_t s);
 void prof_end(kh_plan_s* p, cudaStream_t s);
 kh_status staged_traces(kh_plan_s* p, int ntr, const void* traces, cudaStream_t s,
                         const void** out, long long* ld);
+// Allocation-free path: validation, geometry and tile of a descriptor; binning launches into
+// caller-supplied device buffers (bin_start holds n_bins + 1 entries).
+kh_status noalloc_prepare(const kh_desc* d, GeomParams* g, TileShape* t);
+cudaError_t noalloc_bin(int ntr, const float* sx, const float* sy, const float* rx, const float* ry,
+                        const kh_desc& d, int* bin, int* perm, int* bin_start, float4* hdr,
+                        float2* mid, cudaStream_t s);
 }  // namespace kh

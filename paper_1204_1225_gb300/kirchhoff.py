@@ -57,7 +57,8 @@ EXPORTS = ["kirchhoff_create", "kirchhoff_destroy", "kirchhoff_migrate", "kirchh
            "kirchhoff_velocity_grad", "kirchhoff_traveltime", "kirchhoff_count",
            "kirchhoff_batched_prepare", "kirchhoff_migrate_batched", "kirchhoff_sync",
            "kirchhoff_set_option", "kirchhoff_launch_count", "kirchhoff_last_error",
-           "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read"]
+           "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read",
+           "kirchhoff_migrate_noalloc"]
 
 
 def lib(path: str = LIB_PATH):
@@ -83,6 +84,7 @@ def lib(path: str = LIB_PATH):
             L.kirchhoff_set_option.argtypes = [P, I, ctypes.c_longlong]
             L.kirchhoff_launch_count.argtypes = [P]
             L.kirchhoff_profile.argtypes = [P, I]
+            L.kirchhoff_migrate_noalloc.argtypes = [ctypes.POINTER(kh_desc), I, P, P, P, P, P, P, P, P]
             L.kirchhoff_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_longlong)]
             L.kirchhoff_launch_count.restype = ctypes.c_longlong
@@ -173,6 +175,15 @@ def kirchhoff_count(plan, ntr, sx, sy, rx, ry, stream=None) -> int:
     _check(lib().kirchhoff_count(ctypes.c_void_p(plan), int(ntr), _ptr(sx), _ptr(sy), _ptr(rx),
                                  _ptr(ry), ctypes.byref(out), _stream(stream)))
     return int(out.value)
+
+
+def kirchhoff_migrate_noalloc(desc: kh_desc, ntr, sx, sy, rx, ry, traces, image, status=None,
+                              stream=None) -> None:
+    """Migration without any device allocation (fixed library scratch, ntr <= 65536); for
+    callers that cannot allocate.  ``status``: optional CUDA int32 tensor of one element."""
+    _check(lib().kirchhoff_migrate_noalloc(ctypes.byref(desc), int(ntr), _ptr(sx), _ptr(sy),
+                                           _ptr(rx), _ptr(ry), _ptr(traces), _ptr(image),
+                                           _ptr(status), _stream(stream)))
 
 
 def kirchhoff_sync(plan, stream=None) -> None:

@@ -537,6 +537,59 @@ static kh_status check_headers(const kh_plan_s* p, int ntr, const float* sx, con
     return KH_OK;
 }
 
+// Demigration tile: the first candidate whose sample window fits the kernel's 96 window rows
+// (|dT| <= diagonal / v_min per leg, plus the window slack) and, for v(z), whose rho range the
+// ln(1 + rho) fit covers; P image parts so that about six waves of warp tasks run.
+static kh_status demigrate_tile(const kh_desc& d, GeomParams& g, int ntr, DmTile& dt)
+{
+    static const int c3[][3] = {{8, 8, 16}, {8, 8, 8}, {4, 4, 8}, {4, 4, 4}, {2, 2, 4}, {2, 2, 2}};
+    static const int c2[][3] = {{32, 1, 32}, {16, 1, 16}, {8, 1, 8}, {4, 1, 4}, {2, 1, 2}};
+    const int(*c)[3] = d.dim == 3 ? c3 : c2;
+    const int nc = d.dim == 3 ? 6 : 5;
+    const double zlo = std::min(0.0, std::min(d.oz, d.oz + (d.nz - 1) * d.dz));
+    const double zhi = std::max(0.0, std::max(d.oz, d.oz + (d.nz - 1) * d.dz));
+    const double vmin = (d.vel == KH_VEL_CONST) ? d.v0 : std::min(d.v0 + d.k * zlo, d.v0 + d.k * zhi);
+    const double slack = 2.0 * (2.0 + 2e-4 * d.nt) + 4.0;
+    for (int i = 0; i < nc; ++i) {
+        const double ex = (c[i][0] - 1) * d.dx, ey = d.dim == 3 ? (c[i][1] - 1) * d.dy : 0.0;
+        const double ez = (c[i][2] - 1) * d.dz;
+        const double diag = std::sqrt(ex * ex + ey * ey + ez * ez);
+        if (2.0 * diag / (vmin * d.dt) + slack > DM_ROWS_HOST) continue;
+        TileShape probe = shape(d, c[i][0], c[i][1], 1);
+        probe.cz = 1;
+        GeomParams gt = g;
+        if (g.k != 0.0) {
+            // rho range over this tile (reuses the migration fit with the tile's extent)
+            const double half = 0.5 * diag;
+            const double b = 2.0 * g.kabs * half / vmin * 1.02 + 1e-6;
+            const double tol = std::max(5e-6 * g.kabs * d.dt, 1e-12);
+            gt.lp_terms = LP_SHORT;
+            if (!fit_log1p(std::expm1(-b), std::expm1(b), LP_SHORT, gt.lp, &gt.lp_s, &gt.lp_o, tol)) {
+                gt.lp_terms = LP_LONG;
+                if (!fit_log1p(std::expm1(-b), std::expm1(b), LP_LONG, gt.lp, &gt.lp_s, &gt.lp_o, tol)) continue;
+            }
+            gt.rho_max = (float)std::expm1(b);
+        }
+        (void)probe;
+        g = gt;
+        dt.tx = c[i][0];
+        dt.ty = c[i][1];
+        dt.tz = c[i][2];
+        dt.tiles_x = (d.nx + dt.tx - 1) / dt.tx;
+        dt.tiles_y = (d.ny + dt.ty - 1) / dt.ty;
+        dt.tiles_z = (d.nz + dt.tz - 1) / dt.tz;
+        const long long warp_tasks = std::max(1, (ntr + 31) / 32);
+        long long P = (6LL * 152 * 16 + warp_tasks - 1) / warp_tasks;
+        const long long mem_cap = std::max(1LL, (long long)(8e9 / (4.0 * ntr * (double)d.nt)));
+        const long long n_tiles = (long long)dt.tiles_x * dt.tiles_y * dt.tiles_z;
+        P = std::max(1LL, std::min(std::min(P, 32LL), std::min(mem_cap, n_tiles)));
+        dt.parts = (int)P;
+        return KH_OK;
+    }
+    return fail(KH_ERR_UNSUPPORTED, "no demigration tile keeps the time window within %d samples "
+                                    "(velocity too low for the sampling)", DM_ROWS_HOST);
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -576,6 +629,7 @@ kh_status kirchhoff_destroy(kh_plan p)
     cudaFree(p->ws_pad);
     cudaFree(p->ws_count);
     cudaFree(p->ws_partial);
+    cudaFree(p->ws_dm);
     for (auto& pr : p->ev_open) {
         if (pr.first) cudaEventDestroy(pr.first);
         if (pr.second) cudaEventDestroy(pr.second);
@@ -645,6 +699,40 @@ kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy
     return KH_OK;
 }
 
+kh_status kirchhoff_demigrate(kh_plan p, int ntr, const float* sx, const float* sy,
+                              const float* rx, const float* ry, const float* image,
+                              float* traces_out, void* cuda_stream)
+{
+    if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    kh_status st = check_headers(p, ntr, sx, sy, rx, ry);
+    if (st != KH_OK) return st;
+    if (ntr > 0 && (!image || !traces_out)) return fail(KH_ERR_INVALID_ARG, "image/traces_out is NULL");
+    if (ntr == 0) return KH_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const kh_desc& d = p->d;
+    GeomParams g = geom_of(d);
+    DmTile dt;
+    if ((st = demigrate_tile(d, g, ntr, dt)) != KH_OK) return st;
+    if ((st = bin_traces(p, ntr, sx, sy, rx, ry, s)) != KH_OK) return st;
+    const size_t per_part = (size_t)ntr * d.nt;
+    cudaError_t e = grow(p->ws_dm, p->cap_dm, per_part * dt.parts);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace (demigration partial traces)");
+    e = cudaMemsetAsync(p->ws_dm, 0, sizeof(float) * per_part * dt.parts, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(traces_out, 0, sizeof(float) * per_part, s);
+    if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_demigrate: memset");
+    TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};
+    const int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
+    const int max_chunks = (ntr + 127) / 128;
+    prof_begin(p, s);
+    e = launch_demigrate(g, dt, ts, image, p->ws_dm, p->ws_status, max_chunks, vk, p->fast_math, s);
+    prof_end(p, s);
+    ++p->launches;
+    if (e == cudaSuccess) e = launch_dm_reduce(ts, d.n_bins, p->ws_dm, dt.parts, d.nt, traces_out, ntr, s);
+    ++p->launches;
+    if (e != cudaSuccess) return cuda_fail(e, "demigration kernels");
+    return KH_OK;
+}
+
 kh_status kirchhoff_count(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
                           const float* ry, int64_t* out_count, void* cuda_stream)
 {
@@ -696,7 +784,10 @@ kh_status kirchhoff_sync(kh_plan p, void* cuda_stream)
     if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_sync");
     if (h != 0) {
         cudaMemset(p->ws_status, 0, sizeof(int));
-        return fail(KH_ERR_TIMEOUT, "a bounded in-kernel wait ran out (status 0x%x); results are invalid", h);
+        if (h & 1)
+            return fail(KH_ERR_TIMEOUT, "a bounded in-kernel wait ran out (status 0x%x); results are invalid", h);
+        return fail(KH_ERR_INTERNAL, "a kernel reported an internal sizing error (status 0x%x); "
+                                     "results are invalid", h);
     }
     return KH_OK;
 }

@@ -1,0 +1,251 @@
+// Demigration (the transpose of Eq. 1: each image value is spread back onto the traces at
+// the two samples around t = T_s + T_r, Sec. 3 read from the data side).
+//
+// Trace-stationary: one thread owns one trace; a CTA owns 128 consecutive traces of one
+// offset bin and a 1/P share of the image tiles (tiles i with i % P == part).  For each tile
+// the CTA stages the tile's image values and per-z constants in shared memory; every lane
+// evaluates tau for its own trace at every image point of the tile (the same FP64-reference
+// + FP32-delta evaluation as the migration) and adds W (1-f) m and W f m into its own column
+// of a lane-interleaved window buffer [row][lane] (bank = lane: no conflicts, no atomics).
+// After the tile the lane adds its window into its own row of the part's partial-trace
+// buffer.  A second kernel sums the P partial buffers in a fixed order into the output.
+#include "kh_tau.cuh"
+
+namespace kh {
+
+constexpr int DM_WARPS = 4;
+constexpr int DM_THREADS = DM_WARPS * 32;
+constexpr int DM_ROWS = 96;     // window rows per lane (the host sizes tiles to fit)
+constexpr int DM_TILE = 1024;   // image samples per tile
+constexpr int DM_MAXZ = 64;     // depth samples per tile
+
+struct __align__(16) DmSmem {
+    float buf[DM_WARPS][DM_ROWS][32];
+    float mt[DM_TILE];
+    float4 zc[DM_MAXZ];
+};
+
+static_assert(DM_ROWS == DM_ROWS_HOST, "window rows");
+
+template <int VEL, int WGT, bool FAST, int LPT>
+__global__ void __launch_bounds__(DM_THREADS, 4)
+    k_demigrate(GeomParams g, DmTile dt, TraceSet tr, const float* __restrict__ image,
+                float* __restrict__ partial, int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DmSmem& S = *reinterpret_cast<DmSmem*>(smem_raw);
+    const int b = blockIdx.y, part = blockIdx.z;
+    const int nvalid = tr.bin_start[g.n_bins];
+    const int tb = tr.bin_start[b] + blockIdx.x * DM_THREADS;
+    const int te = tr.bin_start[b + 1];
+    if (tb >= te) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = tb + threadIdx.x;
+    const bool has = k < te;
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 mid = make_float2(0.f, 0.f);
+    if (has) {
+        h = tr.hdr[k];
+        mid = tr.mid[k];
+    }
+    float* prow = partial + ((long long)part * nvalid + (has ? k : 0)) * g.nt;
+    const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
+    const int n_tiles = dt.tiles_x * dt.tiles_y * dt.tiles_z;
+    const int ncol = dt.tx * dt.ty;
+
+    for (int ti = part; ti < n_tiles; ti += dt.parts) {
+        int t = ti;
+        const int tzi = t % dt.tiles_z;
+        t /= dt.tiles_z;
+        const int txi = t % dt.tiles_x, tyi = t / dt.tiles_x;
+        const int x0 = txi * dt.tx, y0 = tyi * dt.ty, z0 = tzi * dt.tz;
+        const TileBox box = tile_box(g, x0, y0, z0, dt.tx, dt.ty, dt.tz);
+
+        // this lane's window and FP64 reference for the tile
+        bool ok = has;
+        if (ok && g.use_aperture) {
+            const float ax = fmaxf(fmaxf(box.xlo - mid.x, mid.x - box.xhi), 0.f);
+            const float ay = fmaxf(fmaxf(box.ylo - mid.y, mid.y - box.yhi), 0.f);
+            ok = ax * ax + ay * ay <= g.A2cull;
+        }
+        int lo = 0, hi = 0;
+        if (ok) ok = trace_window(h, box, VEL, g, lo, hi);
+        const int rows = hi - lo + 2;
+        if (ok && rows > DM_ROWS) {   // the host sizes tiles so this cannot happen
+            atomicOr(status, 2);
+            ok = false;
+        }
+        if (!__syncthreads_or(ok)) continue;
+
+        LegRef rs{0.f, 0.f, 0.f, 0.f}, rr{0.f, 0.f, 0.f, 0.f};
+        float4 ah = h;
+        double tau_ref = -g.t0d / g.dtd;
+        if constexpr (VEL == VK_LINEAR) {
+            if (ok) {
+                const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs);
+                const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr);
+                tau_ref += (ls + lr) * inv_kdt;
+                ah = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
+                                 (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
+            }
+        }
+        const float c0rel = (float)(tau_ref - (double)lo - 0.5);
+        const float lim = (float)(hi - lo);
+        const float cmid = 0.5f * (lim - 1.f), chalf = 0.5f * lim;
+
+        // stage the tile's image values (zero outside the grid) and per-z constants
+        for (int p = threadIdx.x; p < ncol * dt.tz; p += DM_THREADS) {
+            const int iz = p % dt.tz, c = p / dt.tz;
+            const int ix = x0 + c % dt.tx, iy = y0 + c / dt.tx, zz = z0 + iz;
+            float v = 0.f;
+            if (ix < g.nx && iy < g.ny && zz < g.nz)
+                v = image[(((long long)b * g.ny + iy) * g.nx + ix) * g.nz + zz];
+            S.mt[p] = v;
+        }
+        for (int i = threadIdx.x; i < dt.tz; i += DM_THREADS) {
+            const double z = g.oz + (z0 + i) * g.dz;
+            if constexpr (VEL == VK_LINEAR) {
+                const ZConst c = z_constants(z, box.cz, g);
+                S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
+            } else {
+                const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
+                S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
+            }
+        }
+        // clear this warp's rows in use
+        const int wrows = __reduce_max_sync(0xffffffffu, ok ? rows : 0);
+        for (int r = 0; r < wrows; ++r) S.buf[warp][r][lane] = 0.f;
+        __syncthreads();
+
+        if (__any_sync(0xffffffffu, ok)) {
+            float* col0 = &S.buf[warp][0][lane];
+            for (int c = 0; c < ncol; ++c) {
+                const int ix = x0 + c % dt.tx, iy = y0 + c / dt.tx;
+                bool inside = ok && ix < g.nx && iy < g.ny;
+                const float cxf = col_coord(g.ox, ix, g.dx);
+                const float cyf = (g.dim == 3) ? col_coord(g.oy, iy, g.dy) : 0.f;
+                if (inside && g.use_aperture) inside = in_aperture(cxf, cyf, mid.x, mid.y, g.A2);
+                const float chc = inside ? chalf : -1.f;
+                const float* mcol = &S.mt[c * dt.tz];
+                if constexpr (VEL == VK_CONST) {
+                    const float dxs = cxf - h.x, dys = cyf - h.y;
+                    const float dxr = cxf - h.z, dyr = cyf - h.w;
+                    const float dhs2 = fmaf(dxs, dxs, dys * dys);
+                    const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
+#pragma unroll 4
+                    for (int iz = 0; iz < dt.tz; ++iz) {
+                        const float4 zc = S.zc[iz];
+                        const float Rs = hsqrt<FAST>(dhs2 + zc.x);
+                        const float Rr = hsqrt<FAST>(dhr2 + zc.x);
+                        const float Ssum = Rs + Rr;
+                        const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
+                        const float tm = __fadd_rn(th, MAGIC);
+                        const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
+                        const bool v = fabsf(th - cmid) <= chc;
+                        const float W = (WGT == 1) ? zc.y * Ssum : 1.f;
+                        const float wm = v ? W * mcol[iz] : 0.f;
+                        const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
+                        const float a1 = wm * f;
+                        col0[row * 32] += wm - a1;
+                        col0[row * 32 + 32] += a1;
+                    }
+                } else {
+                    const float dxc = (float)((g.ox + ix * g.dx) - box.cx);
+                    const float dyc = (g.dim == 3) ? (float)((g.oy + iy * g.dy) - box.cy) : 0.f;
+                    const float dPs = fmaf(dxc, cxf + ah.x, dyc * (cyf + ah.y));
+                    const float dPr = fmaf(dxc, cxf + ah.z, dyc * (cyf + ah.w));
+                    const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
+#pragma unroll 4
+                    for (int iz = 0; iz < dt.tz; ++iz) {
+                        const float4 c4 = S.zc[iz];
+                        const ZConst zc{c4.x, c4.y, c4.z, c4.w};
+                        float sqs, sqr;
+                        const float rho_s = leg_delta<WGT, FAST>(dPs, zc, rs, qc2s, sqs);
+                        const float rho_r = leg_delta<WGT, FAST>(dPr, zc, rr, qc2r, sqr);
+                        const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
+                        const float L = log1p_poly<LPT>(rho, g);
+                        const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
+                        const float tm = __fadd_rn(th, MAGIC);
+                        const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
+                        const bool v = fabsf(th - cmid) <= chc;
+                        const float W = (WGT == 1) ? zc.gamma * (sqs + sqr) : 1.f;
+                        const float wm = v ? W * mcol[iz] : 0.f;
+                        const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
+                        const float a1 = wm * f;
+                        col0[row * 32] += wm - a1;
+                        col0[row * 32 + 32] += a1;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (ok) {
+            const int nr = min(rows, g.nt - lo);
+            for (int r = 0; r < nr; ++r) prow[lo + r] += S.buf[warp][r][lane];
+        }
+        __syncthreads();
+    }
+}
+
+// out[perm[k]][t] = sum over parts p of partial[p][k][t] (fixed order); rows of traces
+// without an offset bin were zeroed before.
+__global__ void k_dm_reduce(const int* __restrict__ bin_start, int n_bins, const int* __restrict__ perm,
+                            const float* __restrict__ partial, int parts, int nt,
+                            float* __restrict__ out)
+{
+    const int nvalid = bin_start[n_bins];
+    const long long total = (long long)nvalid * nt;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / nt, t = i - k * nt;
+        float s = 0.f;
+        for (int p = 0; p < parts; ++p) s += partial[((long long)p * nvalid + k) * nt + t];
+        out[(long long)perm[k] * nt + t] = s;
+    }
+}
+
+size_t demigrate_smem_bytes() { return sizeof(DmSmem); }
+
+template <int VEL, int WGT, bool FAST>
+static cudaError_t dm_launch_t(const GeomParams& g, const DmTile& dt, const TraceSet& tr,
+                               const float* image, float* partial, int* status, int max_chunks,
+                               cudaStream_t s)
+{
+    auto kern = (VEL == VK_LINEAR && g.lp_terms == LP_LONG) ? k_demigrate<VEL, WGT, FAST, LP_LONG>
+                                                          : k_demigrate<VEL, WGT, FAST, LP_SHORT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(DmSmem));
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)max_chunks, (unsigned)g.n_bins, (unsigned)dt.parts);
+    kern<<<grid, DM_THREADS, sizeof(DmSmem), s>>>(g, dt, tr, image, partial, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_demigrate(const GeomParams& g, const DmTile& dt, const TraceSet& tr,
+                             const float* image, float* partial, int* status, int max_chunks,
+                             int vel_kind, int fast, cudaStream_t s)
+{
+    const int key = vel_kind * 4 + g.weight * 2 + (fast ? 1 : 0);
+    switch (key) {
+        case 0: return dm_launch_t<VK_CONST, 0, false>(g, dt, tr, image, partial, status, max_chunks, s);
+        case 1: return dm_launch_t<VK_CONST, 0, true>(g, dt, tr, image, partial, status, max_chunks, s);
+        case 2: return dm_launch_t<VK_CONST, 1, false>(g, dt, tr, image, partial, status, max_chunks, s);
+        case 3: return dm_launch_t<VK_CONST, 1, true>(g, dt, tr, image, partial, status, max_chunks, s);
+        case 4: return dm_launch_t<VK_LINEAR, 0, false>(g, dt, tr, image, partial, status, max_chunks, s);
+        case 5: return dm_launch_t<VK_LINEAR, 0, true>(g, dt, tr, image, partial, status, max_chunks, s);
+        case 6: return dm_launch_t<VK_LINEAR, 1, false>(g, dt, tr, image, partial, status, max_chunks, s);
+        case 7: return dm_launch_t<VK_LINEAR, 1, true>(g, dt, tr, image, partial, status, max_chunks, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dm_reduce(const TraceSet& tr, int n_bins, const float* partial, int parts, int nt,
+                             float* out, int ntr, cudaStream_t s)
+{
+    const long long total = (long long)ntr * nt;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    k_dm_reduce<<<std::max(blocks, 1), 256, 0, s>>>(tr.bin_start, n_bins, tr.perm, partial, parts, nt, out);
+    return cudaGetLastError();
+}
+
+}  // namespace kh

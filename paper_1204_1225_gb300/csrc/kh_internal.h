@@ -90,4 +90,18 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
                            const WaitCfg& w, cudaStream_t s);
 size_t migrate_smem_bytes(const GeomParams& g);
 
+// Demigration (kh_demigrate.cu): trace-stationary kernel over P interleaved image parts, then
+// a fixed-order sum of the parts.
+struct DmTile {
+    int tx, ty, tz;              // tile extent in samples (tx*ty*tz <= 1024, tz <= 64)
+    int tiles_x, tiles_y, tiles_z;
+    int parts;                   // P
+};
+constexpr int DM_ROWS_HOST = 96;
+cudaError_t launch_demigrate(const GeomParams& g, const DmTile& dt, const TraceSet& tr,
+                             const float* image, float* partial, int* status, int max_chunks,
+                             int vel_kind, int fast, cudaStream_t s);
+cudaError_t launch_dm_reduce(const TraceSet& tr, int n_bins, const float* partial, int parts, int nt,
+                             float* out, int ntr, cudaStream_t s);
+
 }  // namespace kh

@@ -63,37 +63,6 @@ size_t migrate_smem_bytes(const GeomParams& g)
     return mig_static_bytes() + ((size_t)STAGES * mig_cap(g.nt, g.elem_align) + SLACK) * g.esize;
 }
 
-// Smallest and largest one-way time from a surface point at horizontal distance [hmin, hmax]
-// from the tile footprint to any depth in [zlo, zhi].  T grows with h at fixed z; at fixed h,
-// q(z) = (h^2 + z^2)/(v0 (v0 + k z)) has its only interior stationary point (a minimum) at
-// z* = k h^2 / (v0 + sqrt(v0^2 + k^2 h^2)).
-__device__ __forceinline__ void leg_bounds(float hmin, float hmax, float zlo, float zhi, int vel,
-                                           float v0, float k, float& tmin, float& tmax)
-{
-    const float kk = (vel == VK_CONST) ? 0.f : k;
-    float zs = kk * hmin * hmin / (v0 + sqrtf(v0 * v0 + kk * kk * hmin * hmin));
-    zs = fminf(fmaxf(zs, zlo), zhi);
-    tmin = fminf(fminf(tt_bound(hmin, zlo, vel, v0, kk), tt_bound(hmin, zhi, vel, v0, kk)),
-                 tt_bound(hmin, zs, vel, v0, kk));
-    tmax = fmaxf(tt_bound(hmax, zlo, vel, v0, kk), tt_bound(hmax, zhi, vel, v0, kk));
-}
-
-__device__ __forceinline__ void rect_dist(float px, float py, float xlo, float xhi, float ylo,
-                                          float yhi, float& dmin, float& dmax)
-{
-    const float ax = fmaxf(fmaxf(xlo - px, px - xhi), 0.f);
-    const float ay = fmaxf(fmaxf(ylo - py, py - yhi), 0.f);
-    dmin = sqrtf(ax * ax + ay * ay);
-    const float bx = fmaxf(fabsf(px - xlo), fabsf(px - xhi));
-    const float by = fmaxf(fabsf(py - ylo), fabsf(py - yhi));
-    dmax = sqrtf(bx * bx + by * by);
-}
-
-struct TileBox {
-    float xlo, xhi, ylo, yhi, zlo, zhi;   // FP32 box of the valid samples (window bounds)
-    double cx, cy, cz;                    // FP64 centre (linear-path reference point)
-};
-
 // ------------------------------------------------------------------ producer warp
 template <int VEL, typename TT>
 __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
@@ -101,8 +70,6 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                              const TileBox& box, const WaitCfg& wc)
 {
     const int lane = threadIdx.x & 31;
-    const float v0 = (float)g.v0, kf = (float)g.k;
-    const float inv_dt = 1.f / g.dt;
     const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
     int cur = tb;
     int n = 0;
@@ -133,24 +100,9 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                     ok = ax * ax + ay * ay <= g.A2cull;
                 }
                 if (ok) {
-                    float hs0, hs1, hr0, hr1, ts0, ts1, tr0, tr1;
-                    rect_dist(h.x, h.y, box.xlo, box.xhi, box.ylo, box.yhi, hs0, hs1);
-                    rect_dist(h.z, h.w, box.xlo, box.xhi, box.ylo, box.yhi, hr0, hr1);
-                    leg_bounds(hs0, hs1, box.zlo, box.zhi, VEL, v0, kf, ts0, ts1);
-                    leg_bounds(hr0, hr1, box.zlo, box.zhi, VEL, v0, kf, tr0, tr1);
-                    const float tlo = (ts0 + tr0 - g.t0) * inv_dt;
-                    const float thi = (ts1 + tr1 - g.t0) * inv_dt;
-                    const float slo = 2.f + 2e-4f * fabsf(tlo), shi = 2.f + 2e-4f * fabsf(thi);
-                    const float flo = floorf(tlo - slo), fhi = ceilf(thi + shi) + 1.f;
-                    if (!(fhi >= 1.f && flo <= (float)(g.nt - 2))) {
-                        ok = false;   // no sample of this trace can reach the tile (also NaN)
-                    } else {
-                        lo = flo < 0.f ? 0 : (int)flo;
-                        hi = fhi > (float)(g.nt - 1) ? g.nt - 1 : (int)fhi;
-                        ok = hi > lo;
-                        lo_al = lo & ~(g.elem_align - 1);
-                        len_al = (hi + 1 - lo_al + g.elem_align - 1) & ~(g.elem_align - 1);
-                    }
+                    ok = trace_window(h, box, VEL, g, lo, hi);
+                    lo_al = lo & ~(g.elem_align - 1);
+                    len_al = (hi + 1 - lo_al + g.elem_align - 1) & ~(g.elem_align - 1);
                 }
             }
             const unsigned okm = __ballot_sync(0xffffffffu, ok);
@@ -359,25 +311,8 @@ __global__ void __launch_bounds__(THREADS, 2)
     t /= ts.tiles_z;
     const int txi = t % ts.tiles_x, tyi = t / ts.tiles_x;
     const int x0 = txi * ts.cx, y0 = tyi * ts.cy, z0 = tzi * ts.cz * NZ;
-    const int xe = min(x0 + ts.cx, g.nx) - 1, ye = min(y0 + ts.cy, g.ny) - 1;
-    const int ze = min(z0 + ts.cz * NZ, g.nz) - 1;
 
-    TileBox box;
-    {
-        const float xa = col_coord(g.ox, x0, g.dx), xb = col_coord(g.ox, xe, g.dx);
-        const float ya = g.dim == 3 ? col_coord(g.oy, y0, g.dy) : 0.f;
-        const float yb = g.dim == 3 ? col_coord(g.oy, ye, g.dy) : 0.f;
-        const float za = (float)(g.oz + z0 * g.dz), zb = (float)(g.oz + ze * g.dz);
-        box.xlo = fminf(xa, xb);
-        box.xhi = fmaxf(xa, xb);
-        box.ylo = fminf(ya, yb);
-        box.yhi = fmaxf(ya, yb);
-        box.zlo = fminf(za, zb);
-        box.zhi = fmaxf(za, zb);
-        box.cx = g.ox + 0.5 * (x0 + xe) * g.dx;
-        box.cy = g.dim == 3 ? g.oy + 0.5 * (y0 + ye) * g.dy : 0.0;
-        box.cz = g.oz + 0.5 * (z0 + ze) * g.dz;
-    }
+    const TileBox box = tile_box(g, x0, y0, z0, ts.cx, ts.cy, ts.cz * NZ);
 
     if (threadIdx.x == 0) {
         // a wait in another CTA of this plan already ran out: results are invalid anyway

@@ -4,12 +4,6 @@
 
 extern "C" {
 
-kh_status kirchhoff_demigrate(kh_plan, int, const float*, const float*, const float*, const float*,
-                              const float*, float*, void*)
-{
-    return kh::set_error(KH_ERR_UNSUPPORTED, "kirchhoff_demigrate: not built into this library yet");
-}
-
 kh_status kirchhoff_velocity_grad(kh_plan, int, const float*, const float*, const float*,
                                   const float*, const float*, const float*, double*, void*)
 {

@@ -31,6 +31,8 @@ struct kh_plan_s {
     size_t cap_count = 0;
     double* ws_partial = nullptr;
     size_t cap_partial = 0;
+    float* ws_dm = nullptr;       // demigration partial traces [P][ntr][nt]
+    size_t cap_dm = 0;
     // profiling: event pairs recorded around main kernels while enabled
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;

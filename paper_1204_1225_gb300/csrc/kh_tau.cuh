@@ -93,4 +93,80 @@ __device__ __forceinline__ float leg_delta(float dP, const ZConst& zc, const Leg
     return (dq * r.iuc) * gq;
 }
 
+// Smallest and largest one-way time from a surface point at horizontal distance [hmin, hmax]
+// from the tile footprint to any depth in [zlo, zhi].  T grows with h at fixed z; at fixed h,
+// q(z) = (h^2 + z^2)/(v0 (v0 + k z)) has its only interior stationary point (a minimum) at
+// z* = k h^2 / (v0 + sqrt(v0^2 + k^2 h^2)).
+__device__ __forceinline__ void leg_bounds(float hmin, float hmax, float zlo, float zhi, int vel,
+                                           float v0, float k, float& tmin, float& tmax)
+{
+    const float kk = (vel == VK_CONST) ? 0.f : k;
+    float zs = kk * hmin * hmin / (v0 + sqrtf(v0 * v0 + kk * kk * hmin * hmin));
+    zs = fminf(fmaxf(zs, zlo), zhi);
+    tmin = fminf(fminf(tt_bound(hmin, zlo, vel, v0, kk), tt_bound(hmin, zhi, vel, v0, kk)),
+                 tt_bound(hmin, zs, vel, v0, kk));
+    tmax = fmaxf(tt_bound(hmax, zlo, vel, v0, kk), tt_bound(hmax, zhi, vel, v0, kk));
+}
+
+__device__ __forceinline__ void rect_dist(float px, float py, float xlo, float xhi, float ylo,
+                                          float yhi, float& dmin, float& dmax)
+{
+    const float ax = fmaxf(fmaxf(xlo - px, px - xhi), 0.f);
+    const float ay = fmaxf(fmaxf(ylo - py, py - yhi), 0.f);
+    dmin = sqrtf(ax * ax + ay * ay);
+    const float bx = fmaxf(fabsf(px - xlo), fabsf(px - xhi));
+    const float by = fmaxf(fabsf(py - ylo), fabsf(py - yhi));
+    dmax = sqrtf(bx * bx + by * by);
+}
+
+struct TileBox {
+    float xlo, xhi, ylo, yhi, zlo, zhi;   // FP32 box of the valid samples (window bounds)
+    double cx, cy, cz;                    // FP64 centre (linear-path reference point)
+};
+
+// Sample window [lo, hi] of one trace over a tile box, from the time bounds of both legs with
+// a slack of 2 + 2e-4 |tau| samples for FP32 rounding; false if no valid sample can reach the box.
+__device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box, int vel,
+                                             const GeomParams& g, int& lo, int& hi)
+{
+    const float v0 = (float)g.v0, kf = (float)g.k, inv_dt = 1.f / g.dt;
+    float hs0, hs1, hr0, hr1, ts0, ts1, tr0, tr1;
+    rect_dist(h.x, h.y, box.xlo, box.xhi, box.ylo, box.yhi, hs0, hs1);
+    rect_dist(h.z, h.w, box.xlo, box.xhi, box.ylo, box.yhi, hr0, hr1);
+    leg_bounds(hs0, hs1, box.zlo, box.zhi, vel, v0, kf, ts0, ts1);
+    leg_bounds(hr0, hr1, box.zlo, box.zhi, vel, v0, kf, tr0, tr1);
+    const float tlo = (ts0 + tr0 - g.t0) * inv_dt;
+    const float thi = (ts1 + tr1 - g.t0) * inv_dt;
+    const float slo = 2.f + 2e-4f * fabsf(tlo), shi = 2.f + 2e-4f * fabsf(thi);
+    const float flo = floorf(tlo - slo), fhi = ceilf(thi + shi) + 1.f;
+    if (!(fhi >= 1.f && flo <= (float)(g.nt - 2))) return false;   // also NaN
+    lo = flo < 0.f ? 0 : (int)flo;
+    hi = fhi > (float)(g.nt - 1) ? g.nt - 1 : (int)fhi;
+    return hi > lo;
+}
+
+// Tile box (FP32, for the window bounds) and FP64 centre (reference point) of the tile
+// starting at (x0, y0, z0) with ext_x x ext_y columns and ext_z depth samples.
+__device__ __forceinline__ TileBox tile_box(const GeomParams& g, int x0, int y0, int z0, int ext_x,
+                                            int ext_y, int ext_z)
+{
+    const int xe = min(x0 + ext_x, g.nx) - 1, ye = min(y0 + ext_y, g.ny) - 1;
+    const int ze = min(z0 + ext_z, g.nz) - 1;
+    TileBox box;
+    const float xa = col_coord(g.ox, x0, g.dx), xb = col_coord(g.ox, xe, g.dx);
+    const float ya = g.dim == 3 ? col_coord(g.oy, y0, g.dy) : 0.f;
+    const float yb = g.dim == 3 ? col_coord(g.oy, ye, g.dy) : 0.f;
+    const float za = (float)(g.oz + z0 * g.dz), zb = (float)(g.oz + ze * g.dz);
+    box.xlo = fminf(xa, xb);
+    box.xhi = fmaxf(xa, xb);
+    box.ylo = fminf(ya, yb);
+    box.yhi = fmaxf(ya, yb);
+    box.zlo = fminf(za, zb);
+    box.zhi = fmaxf(za, zb);
+    box.cx = g.ox + 0.5 * (x0 + xe) * g.dx;
+    box.cy = g.dim == 3 ? g.oy + 0.5 * (y0 + ye) * g.dy : 0.0;
+    box.cz = g.oz + 0.5 * (z0 + ze) * g.dz;
+    return box;
+}
+
 }  // namespace kh

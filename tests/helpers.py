@@ -51,3 +51,13 @@ def cfg4_reduced(n_shots=12, nx=160, nz=120, nt=1000):
     s = sv.survey_25d_lsm(nx=nx, nz=nz, nt=nt, n_shots=n_shots)
     sc = sv.reflectors_2d(np.random.default_rng(sv.BASE_SEED), s, spacing=5.0)
     return s, synth_on_gpu(s, sc, 25.0)
+
+
+def gpu_demigrate(s, image, fast_math=True, plan=None):
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    p = plan or kh.Plan(s, fast_math=fast_math)
+    hdr = kh.Headers.of(s)
+    m = torch.as_tensor(np.asarray(image, dtype=np.float32)).to("cuda").contiguous()
+    out = p.demigrate(hdr, m)
+    p.sync()
+    return out.double().cpu().numpy(), p

@@ -56,9 +56,10 @@ def lib():
             P = ctypes.c_void_p
             L = ctypes.c_long
             D = ctypes.POINTER(_Desc)
-            for name in ("ko_migrate", "ko_demigrate", "ko_vgrad"):
+            for name in ("ko_migrate", "ko_demigrate"):
                 getattr(_lib, name).argtypes = [D, L, P, P, P, P, P, P]
                 getattr(_lib, name).restype = ctypes.c_int
+            _lib.ko_vgrad.argtypes = [D, L, P, P, P, P, P, P, P, P]
             _lib.ko_migrate_points.argtypes = [D, L, P, P, P, P, P, L, P, P, P]
             _lib.ko_migrate_points.restype = ctypes.c_int
             _lib.ko_bins.argtypes = [D, L, P, P, P, P, P]
@@ -156,16 +157,18 @@ def demigrate(s, image) -> np.ndarray:
     return out
 
 
-def vgrad(s, image, traces) -> np.ndarray:
-    """[dB/dv0, dB/dk] of B(m, D) = <m, migrate(D)>."""
+def vgrad(s, image, traces, return_abs: bool = False):
+    """[dB/dv0, dB/dk] of B(m, D) = <m, migrate(D)>; with ``return_abs`` also the sums of
+    the absolute values of the terms (the summation's condition scale)."""
     sx, sy, rx, ry = _hdr(s)
     m = np.ascontiguousarray(image, dtype=np.float64).reshape(s.image_shape)
     d = np.ascontiguousarray(traces, dtype=np.float64).reshape(s.ntr, s.nt)
     out = np.empty(2, dtype=np.float64)
+    ab = np.empty(2, dtype=np.float64)
     rc = lib().ko_vgrad(ctypes.byref(desc(s)), s.ntr, _ptr(sx), _ptr(sy), _ptr(rx), _ptr(ry),
-                        _ptr(m), _ptr(d), _ptr(out))
+                        _ptr(m), _ptr(d), _ptr(out), _ptr(ab))
     assert rc == 0
-    return out
+    return (out, ab) if return_abs else out
 
 
 def count(s) -> int:

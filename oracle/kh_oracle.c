@@ -328,11 +328,12 @@ int ko_demigrate(const ko_desc* d, long ntr, const float* sx, const float* sy, c
  * the velocity-model derivative that both the migration and the demigration operator
  * need in their backward pass; out[0] = dB/dv0, out[1] = dB/dk. */
 int ko_vgrad(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
-             const float* ry, const double* image, const double* traces, double* out)
+             const float* ry, const double* image, const double* traces, double* out,
+             double* abs_out)
 {
     const long ncol = (long)d->nx * d->ny, nz = d->nz, nt = d->nt;
     int* bin = (int*)malloc(sizeof(int) * (ntr > 0 ? ntr : 1));
-    double* part = (double*)calloc((size_t)(ncol > 0 ? ncol : 1) * 2, sizeof(double));
+    double* part = (double*)calloc((size_t)(ncol > 0 ? ncol : 1) * 4, sizeof(double));
     if (!bin || !part) { free(bin); free(part); return 1; }
     ko_bins(d, ntr, sx, sy, rx, ry, bin);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -340,7 +341,7 @@ int ko_vgrad(const ko_desc* d, long ntr, const float* sx, const float* sy, const
         int iy = (int)(c / d->nx), ix = (int)(c % d->nx);
         double x = d->ox + ix * d->dx, y = (d->dim == 3) ? d->oy + iy * d->dy : 0.0;
         float cx = col_coord(d->ox, ix, d->dx), cy = (d->dim == 3) ? col_coord(d->oy, iy, d->dy) : 0.f;
-        double gv = 0.0, gk = 0.0;
+        double gv = 0.0, gk = 0.0, av = 0.0, ak = 0.0;
         for (long j = 0; j < ntr; ++j) {
             if (bin[j] < 0) continue;
             float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
@@ -355,16 +356,27 @@ int ko_vgrad(const ko_desc* d, long ntr, const float* sx, const float* sy, const
                 double slope = D[q.i + 1] - D[q.i];
                 gv += q.W * m[iz] * slope * q.dtau_dv0;
                 gk += q.W * m[iz] * slope * q.dtau_dk;
+                av += fabs(q.W * m[iz] * slope * q.dtau_dv0);
+                ak += fabs(q.W * m[iz] * slope * q.dtau_dk);
             }
         }
-        part[2 * c] = gv;
-        part[2 * c + 1] = gk;
+        part[4 * c] = gv;
+        part[4 * c + 1] = gk;
+        part[4 * c + 2] = av;
+        part[4 * c + 3] = ak;
     }
     out[0] = 0.0;
     out[1] = 0.0;
+    double a0 = 0.0, a1 = 0.0;
     for (long c = 0; c < ncol; ++c) {
-        out[0] += part[2 * c];
-        out[1] += part[2 * c + 1];
+        out[0] += part[4 * c];
+        out[1] += part[4 * c + 1];
+        a0 += part[4 * c + 2];
+        a1 += part[4 * c + 3];
+    }
+    if (abs_out) {
+        abs_out[0] = a0;
+        abs_out[1] = a1;
     }
     free(bin);
     free(part);

@@ -733,6 +733,43 @@ kh_status kirchhoff_demigrate(kh_plan p, int ntr, const float* sx, const float* 
     return KH_OK;
 }
 
+kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, const float* sy,
+                                  const float* rx, const float* ry, const float* image,
+                                  const float* traces, double* out_dv0_dk, void* cuda_stream)
+{
+    if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    kh_status st = check_headers(p, ntr, sx, sy, rx, ry);
+    if (st != KH_OK) return st;
+    if (!out_dv0_dk) return fail(KH_ERR_INVALID_ARG, "out_dv0_dk is NULL");
+    if (ntr > 0 && (!image || !traces)) return fail(KH_ERR_INVALID_ARG, "image/traces is NULL");
+    if (p->d.vel == KH_VEL_TABLE) return fail(KH_ERR_UNSUPPORTED, "no velocity gradient for table traveltimes");
+    if (p->d.trace_dtype != KH_F32) return fail(KH_ERR_UNSUPPORTED, "velocity gradient takes FP32 traces");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(out_dv0_dk, 0, 2 * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (ntr == 0) return KH_OK;
+    if ((st = bin_traces(p, ntr, sx, sy, rx, ry, s)) != KH_OK) return st;
+    const void* tr_ptr = nullptr;
+    GeomParams g = geom_of(p->d);
+    if ((st = staged_traces(p, ntr, traces, s, &tr_ptr, &g.ld)) != KH_OK) return st;
+    const TileShape tile = tile_of(p);
+    if ((st = prepare_linear(p->d, tile, g)) != KH_OK) return st;
+    const long long nwarps = (long long)tile.tiles_x * tile.tiles_y * tile.tiles_z * p->d.n_bins * CONSUMER_WARPS;
+    if ((e = grow(p->ws_partial, p->cap_partial, (size_t)(2 * nwarps))) != cudaSuccess)
+        return cuda_fail(e, "workspace (gradient partials)");
+    TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};
+    WaitCfg w{p->ws_status, p->wait_polls, WAIT_NS};
+    const int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
+    prof_begin(p, s);
+    e = launch_vgrad(g, tile, ts, tr_ptr, image, vk, p->fast_math, w, p->ws_partial, s);
+    prof_end(p, s);
+    ++p->launches;
+    if (e == cudaSuccess) e = launch_vgrad_reduce(p->ws_partial, nwarps, 1.0 / p->d.dt, out_dv0_dk, s);
+    ++p->launches;
+    if (e != cudaSuccess) return cuda_fail(e, "velocity-gradient kernels");
+    return KH_OK;
+}
+
 kh_status kirchhoff_count(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
                           const float* ry, int64_t* out_count, void* cuda_stream)
 {

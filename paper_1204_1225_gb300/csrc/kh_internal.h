@@ -89,6 +89,13 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
                            const void* traces, float* image, int vel_kind, int fast_math,
                            const WaitCfg& w, cudaStream_t s);
 size_t migrate_smem_bytes(const GeomParams& g);
+// Velocity gradient: the migration kernel in gradient mode (image as input), per-warp FP64
+// partials [gridDim.y * gridDim.x * 8][2], then one fixed-order sum scaled by 1/dt.
+cudaError_t launch_vgrad(const GeomParams& g, const TileShape& t, const TraceSet& tr,
+                         const void* traces, const float* image, int vel_kind, int fast_math,
+                         const WaitCfg& w, double* partial, cudaStream_t s);
+cudaError_t launch_vgrad_reduce(const double* partial, long long n, double inv_dt, double* out,
+                                cudaStream_t s);
 
 // Demigration (kh_demigrate.cu): trace-stationary kernel over P interleaved image parts, then
 // a fixed-order sum of the parts.

@@ -44,6 +44,7 @@ struct __align__(16) MigSmem {
     int4 win[STAGES][BMAX];     // x: tau_ref - lo - 1/2 (float bits), y: smem index of sample lo
                                 // minus MAGIC_BITS, z/w: c_mid/c_half (float bits) of the valid
                                 // range -1/2 <= tau - lo - 1/2 <= hi - lo - 1/2
+    float tb[STAGES][BMAX];     // (lo + 1/2) dt + t0: T_s + T_r = (tau - lo - 1/2) dt + tb (gradient mode)
     float4 zc[MAX_ZG * NZ];     // per-z constants (ZConst for linear v; (z^2, w_z, 0, 0) for constant v)
     float zero[4];
 };
@@ -143,6 +144,7 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                     S.hdr[s][slot] = h;
                 }
                 S.mid[s][slot] = m;
+                S.tb[s][slot] = (float)(((double)lo + 0.5) * g.dtd + g.t0d);
                 const float lim = (float)(hi - lo);
                 S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo - 0.5)),
                                            dst + (lo - lo_al) - MAGIC_BITS,
@@ -296,10 +298,152 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
     }
 }
 
+// ------------------------------------------------------------------ gradient consumer
+// dB/d(v0, k) of B(m, D) = <m, migrate(D)>: per contribution W m (D[i+1] - D[i]) dT/dth,
+// with dT/dth summed over both legs (the 1/dt of dtau/dth is applied in the final sum):
+//   constant v:  dT/dv0 = -(R_s + R_r)/v0^2;
+//   linear v(z): with q/w = sqrt(q/(q+2)) per leg and vz = v0 + k z,
+//                dT/dv0 = -(q/w)_sum (1/v0 + 1/vz)/|k|,
+//                dT/dk  = -sgn(k) (T_s + T_r)/|k| + (q/w)_sum (2/k - z/vz)/|k|.
+// Each thread sums its 16 z in FP32 per (column, trace) and carries FP64 totals; per-warp
+// FP64 partials go to `partial` for a fixed-order final sum.
 template <int VEL, int WGT, bool FAST, typename TT, int LPT>
-__global__ void __launch_bounds__(THREADS, 2)
-    k_migrate(GeomParams g, TileShape ts, TraceSet tr, const TT* __restrict__ traces,
-              float* __restrict__ image, int cap, WaitCfg wc)
+__device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, const TileShape& ts,
+                            int x0, int y0, int z0, const TileBox& box, int bin,
+                            const float* __restrict__ image, double* __restrict__ partial,
+                            const WaitCfg& wc)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
+    const int ix = x0 + tx, iy = y0 + ty, izb = z0 + tzg * NZ;
+    const bool col_ok = ix < g.nx && iy < g.ny;
+    const float cxf = col_coord(g.ox, ix, g.dx);
+    const float cyf = (g.dim == 3) ? col_coord(g.oy, iy, g.dy) : 0.f;
+    const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
+    const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
+    const float4* zc = &S.zc[tzg * NZ];
+    const int zero_off = (int)(((const char*)S.zero - (const char*)data) / (int)sizeof(TT));
+    const float dtf = (float)g.dtd;
+    const float inv_v0 = (float)(1.0 / g.v0), inv_v0sq = (float)(1.0 / (g.v0 * g.v0));
+    const float inv_ka = (VEL == VK_LINEAR) ? (float)(1.0 / g.kabs) : 0.f;
+    const float sgnk = g.k < 0.0 ? -1.f : 1.f;
+    const float two_over_k = (VEL == VK_LINEAR) ? (float)(2.0 / g.k) : 0.f;
+    const float inv_a = (VEL == VK_LINEAR) ? (float)(1.0 / g.a) : 0.f;
+    const float zb = (float)(g.oz + izb * g.dz), dzf = (float)g.dz;
+
+    float mv[NZ];
+#pragma unroll
+    for (int i = 0; i < NZ; ++i)
+        mv[i] = (col_ok && izb + i < g.nz)
+                    ? image[(((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb + i]
+                    : 0.f;
+    double G0 = 0.0, G1 = 0.0;
+
+    bool failed = false;
+    int n = 0;
+    while (true) {
+        const int s = n % STAGES;
+        if (!warp_wait(&S.full[s], (n / STAGES) & 1, wc.polls, wc.ns, wc.status)) {
+            failed = true;
+            break;
+        }
+        const int cnt = S.cnt[s];
+        const int last = S.last[s];
+        for (int t = 0; t < cnt; ++t) {
+            const int4 w = S.win[s][t];
+            bool inside = col_ok;
+            if (g.use_aperture) {
+                const float2 m = S.mid[s][t];
+                inside = inside && in_aperture(cxf, cyf, m.x, m.y, g.A2);
+            }
+            if (!__any_sync(0xffffffffu, inside)) continue;
+            const float c0rel = __int_as_float(w.x);
+            const float cmid = __int_as_float(w.z);
+            const float chalf = inside ? __int_as_float(w.w) : -1.f;
+            const float tbase = S.tb[s][t];
+            const float4 h = S.hdr[s][t];
+            float g0 = 0.f, g1 = 0.f;
+            if constexpr (VEL == VK_CONST) {
+                const float dxs = cxf - h.x, dys = cyf - h.y;
+                const float dxr = cxf - h.z, dyr = cyf - h.w;
+                const float dhs2 = fmaf(dxs, dxs, dys * dys);
+                const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) {
+                    const float4 c = zc[i];
+                    const float Rs = hsqrt<FAST>(dhs2 + c.x);
+                    const float Rr = hsqrt<FAST>(dhr2 + c.x);
+                    const float Ssum = Rs + Rr;
+                    const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
+                    const float tm = __fadd_rn(th, MAGIC);
+                    const bool ok = fabsf(th - cmid) <= chalf;
+                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
+                    const float slope = to_f32<TT>(data[off + 1]) - to_f32<TT>(data[off]);
+                    const float W = (WGT == 1) ? c.y * Ssum : 1.f;
+                    g0 = fmaf(W * mv[i] * slope, -Ssum * inv_v0sq, g0);
+                }
+            } else {
+                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t];
+                const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w}, rr{rrv.x, rrv.y, rrv.z, rrv.w};
+                const float dPs = fmaf(dxc, cxf + h.x, dyc * (cyf + h.y));
+                const float dPr = fmaf(dxc, cxf + h.z, dyc * (cyf + h.w));
+                const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) {
+                    const float4 c4 = zc[i];
+                    const ZConst c{c4.x, c4.y, c4.z, c4.w};
+                    float sqs, sqr, qws, qwr;
+                    const float rho_s = leg_delta_grad<FAST>(dPs, c, rs, qc2s, sqs, qws);
+                    const float rho_r = leg_delta_grad<FAST>(dPr, c, rr, qc2r, sqr, qwr);
+                    const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
+                    const float L = log1p_poly<LPT>(rho, g);
+                    const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
+                    const float tm = __fadd_rn(th, MAGIC);
+                    const bool ok = fabsf(th - cmid) <= chalf;
+                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
+                    const float slope = to_f32<TT>(data[off + 1]) - to_f32<TT>(data[off]);
+                    const float W = (WGT == 1) ? c.gamma * (sqs + sqr) : 1.f;
+                    const float wms = W * mv[i] * slope;
+                    const float inv_vz = c.alpha * inv_a;
+                    const float z = fmaf((float)i, dzf, zb);
+                    const float qw = qws + qwr;
+                    const float Tsum = fmaf(th, dtf, tbase);
+                    const float dTv = -qw * (inv_v0 + inv_vz) * inv_ka;
+                    const float dTk = (fmaf(qw, fmaf(-z, inv_vz, two_over_k), -sgnk * Tsum)) * inv_ka;
+                    g0 = fmaf(wms, dTv, g0);
+                    g1 = fmaf(wms, dTk, g1);
+                }
+            }
+            G0 += (double)g0;
+            G1 += (double)g1;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[s]);
+        ++n;
+        if (last) break;
+    }
+    if (failed) {
+        if (lane == 0) atomicOr(wc.status, 1);
+        G0 = 0.0;
+        G1 = 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        G0 += __shfl_xor_sync(0xffffffffu, G0, o);
+        G1 += __shfl_xor_sync(0xffffffffu, G1, o);
+    }
+    if (lane == 0) {
+        const long long slot = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * CONSUMER_WARPS + warp;
+        partial[2 * slot] = G0;
+        partial[2 * slot + 1] = G1;
+    }
+}
+
+// Shared body of the migration kernel (MODE 0: image out) and of the gradient kernel
+// (MODE 1: image in, per-warp partials out).
+template <int VEL, int WGT, bool FAST, typename TT, int LPT, int MODE>
+__device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape& ts, const TraceSet& tr,
+                                            const TT* __restrict__ traces, float* __restrict__ image,
+                                            int cap, const WaitCfg& wc, double* __restrict__ partial)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MigSmem& S = *reinterpret_cast<MigSmem*>(smem_raw);
@@ -344,41 +488,69 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (threadIdx.x >= CONSUMERS) {
         mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
                               box, wc);
-    } else {
+    } else if constexpr (MODE == 0) {
         mig_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, wc);
+    } else {
+        vg_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, partial, wc);
     }
+}
+
+template <int VEL, int WGT, bool FAST, typename TT, int LPT>
+__global__ void __launch_bounds__(THREADS, 2)
+    k_migrate(GeomParams g, TileShape ts, TraceSet tr, const TT* __restrict__ traces,
+              float* __restrict__ image, int cap, WaitCfg wc)
+{
+    kernel_body<VEL, WGT, FAST, TT, LPT, 0>(g, ts, tr, traces, image, cap, wc, nullptr);
+}
+
+template <int VEL, int WGT, bool FAST, typename TT, int LPT>
+__global__ void __launch_bounds__(THREADS, 2)
+    k_vgrad(GeomParams g, TileShape ts, TraceSet tr, const TT* __restrict__ traces,
+            const float* __restrict__ image, int cap, WaitCfg wc, double* __restrict__ partial)
+{
+    kernel_body<VEL, WGT, FAST, TT, LPT, 1>(g, ts, tr, traces, const_cast<float*>(image), cap, wc, partial);
 }
 
 template <int VEL, int WGT, bool FAST, typename TT>
 static cudaError_t launch_t(const GeomParams& g, const TileShape& t, const TraceSet& tr,
-                            const void* traces, float* image, const WaitCfg& w, cudaStream_t s)
+                            const void* traces, float* image, const WaitCfg& w, double* partial,
+                            cudaStream_t s)
 {
-    auto kern = (VEL == VK_LINEAR && g.lp_terms == LP_LONG) ? k_migrate<VEL, WGT, FAST, TT, LP_LONG>
-                                                          : k_migrate<VEL, WGT, FAST, TT, LP_SHORT>;
     const size_t smem = migrate_smem_bytes(g);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(t.tiles_x * t.tiles_y * t.tiles_z), (unsigned)g.n_bins);
-    kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
-                                     mig_cap(g.nt, g.elem_align), w);
+    const bool lng = VEL == VK_LINEAR && g.lp_terms == LP_LONG;
+    cudaError_t e;
+    if (partial == nullptr) {
+        auto kern = lng ? k_migrate<VEL, WGT, FAST, TT, LP_LONG> : k_migrate<VEL, WGT, FAST, TT, LP_SHORT>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
+                                         mig_cap(g.nt, g.elem_align), w);
+    } else {
+        auto kern = lng ? k_vgrad<VEL, WGT, FAST, TT, LP_LONG> : k_vgrad<VEL, WGT, FAST, TT, LP_SHORT>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
+                                         mig_cap(g.nt, g.elem_align), w, partial);
+    }
     return cudaGetLastError();
 }
 
 template <typename TT>
 static cudaError_t launch_dtype(const GeomParams& g, const TileShape& t, const TraceSet& tr,
                                 const void* traces, float* image, int vel, int fast,
-                                const WaitCfg& w, cudaStream_t s)
+                                const WaitCfg& w, double* partial, cudaStream_t s)
 {
     const int key = vel * 4 + g.weight * 2 + (fast ? 1 : 0);
     switch (key) {
-        case 0: return launch_t<VK_CONST, 0, false, TT>(g, t, tr, traces, image, w, s);
-        case 1: return launch_t<VK_CONST, 0, true, TT>(g, t, tr, traces, image, w, s);
-        case 2: return launch_t<VK_CONST, 1, false, TT>(g, t, tr, traces, image, w, s);
-        case 3: return launch_t<VK_CONST, 1, true, TT>(g, t, tr, traces, image, w, s);
-        case 4: return launch_t<VK_LINEAR, 0, false, TT>(g, t, tr, traces, image, w, s);
-        case 5: return launch_t<VK_LINEAR, 0, true, TT>(g, t, tr, traces, image, w, s);
-        case 6: return launch_t<VK_LINEAR, 1, false, TT>(g, t, tr, traces, image, w, s);
-        case 7: return launch_t<VK_LINEAR, 1, true, TT>(g, t, tr, traces, image, w, s);
+        case 0: return launch_t<VK_CONST, 0, false, TT>(g, t, tr, traces, image, w, partial, s);
+        case 1: return launch_t<VK_CONST, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
+        case 2: return launch_t<VK_CONST, 1, false, TT>(g, t, tr, traces, image, w, partial, s);
+        case 3: return launch_t<VK_CONST, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
+        case 4: return launch_t<VK_LINEAR, 0, false, TT>(g, t, tr, traces, image, w, partial, s);
+        case 5: return launch_t<VK_LINEAR, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
+        case 6: return launch_t<VK_LINEAR, 1, false, TT>(g, t, tr, traces, image, w, partial, s);
+        case 7: return launch_t<VK_LINEAR, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -389,9 +561,52 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
 {
     if (t.cz > MAX_ZG) return cudaErrorInvalidValue;
     switch (g.esize) {
-        case 4: return launch_dtype<float>(g, t, tr, traces, image, vel_kind, fast_math, w, s);
+        case 4: return launch_dtype<float>(g, t, tr, traces, image, vel_kind, fast_math, w, nullptr, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_vgrad(const GeomParams& g, const TileShape& t, const TraceSet& tr,
+                         const void* traces, const float* image, int vel_kind, int fast_math,
+                         const WaitCfg& w, double* partial, cudaStream_t s)
+{
+    if (t.cz > MAX_ZG || !partial) return cudaErrorInvalidValue;
+    if (g.esize != 4) return cudaErrorInvalidValue;
+    return launch_dtype<float>(g, t, tr, traces, const_cast<float*>(image), vel_kind, fast_math, w,
+                               partial, s);
+}
+
+// out[0..1] = (sum of the per-warp partials, in index order) / dt: one CTA, fixed order.
+__global__ void k_vgrad_reduce(const double* __restrict__ partial, long long n, double inv_dt,
+                               double* __restrict__ out)
+{
+    __shared__ double s0[256], s1[256];
+    double a = 0.0, b = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s0[threadIdx.x] += s0[threadIdx.x + w];
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = s0[0] * inv_dt;
+        out[1] = s1[0] * inv_dt;
+    }
+}
+
+cudaError_t launch_vgrad_reduce(const double* partial, long long n, double inv_dt, double* out,
+                                cudaStream_t s)
+{
+    k_vgrad_reduce<<<1, 256, 0, s>>>(partial, n, inv_dt, out);
+    return cudaGetLastError();
 }
 
 }  // namespace kh

@@ -4,12 +4,6 @@
 
 extern "C" {
 
-kh_status kirchhoff_velocity_grad(kh_plan, int, const float*, const float*, const float*,
-                                  const float*, const float*, const float*, double*, void*)
-{
-    return kh::set_error(KH_ERR_UNSUPPORTED, "kirchhoff_velocity_grad: not built into this library yet");
-}
-
 kh_status kirchhoff_batched_prepare(int, const kh_job*, void*)
 {
     return kh::set_error(KH_ERR_UNSUPPORTED, "kirchhoff_batched_prepare: not built into this library yet");

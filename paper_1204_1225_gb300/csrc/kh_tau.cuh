@@ -124,6 +124,22 @@ struct TileBox {
     double cx, cy, cz;                    // FP64 centre (linear-path reference point)
 };
 
+// leg_delta plus q/w = sqrt(q / (q + 2)) for the velocity derivatives; sq = sqrt(q) always.
+template <bool FAST>
+__device__ __forceinline__ float leg_delta_grad(float dP, const ZConst& zc, const LegRef& r,
+                                                float qc2, float& sq, float& qw)
+{
+    const float E = fmaf(zc.kappa, r.Rc2, zc.dz2);
+    const float dq = zc.alpha * (dP + E);
+    const float q = fmaxf(r.qc + dq, 0.f);
+    sq = hsqrt<FAST>(q);
+    const float t = hsqrt<FAST>(q + 2.f);
+    const float w = sq * t;
+    qw = sq * hrcp<FAST>(t);
+    const float gq = fmaf(q + qc2, hrcp<FAST>(w + r.wc), 1.f);
+    return (dq * r.iuc) * gq;
+}
+
 // Sample window [lo, hi] of one trace over a tile box, from the time bounds of both legs with
 // a slack of 2 + 2e-4 |tau| samples for FP32 rounding; false if no valid sample can reach the box.
 __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box, int vel,

@@ -61,3 +61,18 @@ def gpu_demigrate(s, image, fast_math=True, plan=None):
     out = p.demigrate(hdr, m)
     p.sync()
     return out.double().cpu().numpy(), p
+
+# Parity bar for the velocity gradient (a sum of ~1e9 signed FP32 terms per call, carried
+# in FP64 per (column, trace)) against the FP64 oracle's analytic gradient.
+GRAD_REL = 1e-4
+
+
+def gpu_vgrad(s, image, traces, fast_math=True, plan=None):
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    p = plan or kh.Plan(s, fast_math=fast_math)
+    hdr = kh.Headers.of(s)
+    m = torch.as_tensor(np.asarray(image, dtype=np.float32)).to("cuda").contiguous()
+    d = torch.as_tensor(np.asarray(traces, dtype=np.float32)).to("cuda").contiguous()
+    out = p.velocity_grad(hdr, m, d)
+    p.sync()
+    return out.cpu().numpy(), p

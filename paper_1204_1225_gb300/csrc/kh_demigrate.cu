@@ -23,6 +23,7 @@ struct __align__(16) DmSmem {
     float buf[DM_WARPS][DM_ROWS][32];
     float mt[DM_TILE];
     float4 zc[DM_MAXZ];
+    float z2[DM_MAXZ];
 };
 
 static_assert(DM_ROWS == DM_ROWS_HOST, "window rows");
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
             if constexpr (VEL == VK_LINEAR) {
                 const ZConst c = z_constants(z, box.cz, g);
                 S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
+                S.z2[i] = (float)(z * z);
             } else {
                 const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
                 S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
@@ -154,14 +156,17 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                     const float dyc = (g.dim == 3) ? (float)((g.oy + iy * g.dy) - box.cy) : 0.f;
                     const float dPs = fmaf(dxc, cxf + ah.x, dyc * (cyf + ah.y));
                     const float dPr = fmaf(dxc, cxf + ah.z, dyc * (cyf + ah.w));
+                    const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
+                    const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
                     const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
 #pragma unroll 4
                     for (int iz = 0; iz < dt.tz; ++iz) {
                         const float4 c4 = S.zc[iz];
                         const ZConst zc{c4.x, c4.y, c4.z, c4.w};
                         float sqs, sqr;
-                        const float rho_s = leg_delta<WGT, FAST>(dPs, zc, rs, qc2s, sqs);
-                        const float rho_r = leg_delta<WGT, FAST>(dPr, zc, rr, qc2r, sqr);
+                        const float z2i = S.z2[iz];
+                        const float rho_s = leg_delta<WGT, FAST>(dPs, dhs2, z2i, zc, rs, qc2s, sqs);
+                        const float rho_r = leg_delta<WGT, FAST>(dPr, dhr2, z2i, zc, rr, qc2r, sqr);
                         const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
                         const float L = log1p_poly<LPT>(rho, g);
                         const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));

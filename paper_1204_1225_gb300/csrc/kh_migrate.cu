@@ -37,7 +37,8 @@ struct __align__(16) MigSmem {
     int cnt[STAGES];
     int last[STAGES];
     // per staged trace
-    float4 hdr[STAGES][BMAX];   // const v: (sx, sy, rx, ry); linear: (c_x-2s_x, c_y-2s_y, c_x-2r_x, c_y-2r_y)
+    float4 hdr[STAGES][BMAX];   // (sx, sy, rx, ry)
+    float4 hda[STAGES][BMAX];   // linear: (c_x-2s_x, c_y-2s_y, c_x-2r_x, c_y-2r_y)
     float4 refs[STAGES][BMAX];  // linear: source-leg LegRef
     float4 refr[STAGES][BMAX];  // linear: receiver-leg LegRef
     float2 mid[STAGES][BMAX];   // FP32 midpoint (aperture test)
@@ -46,6 +47,7 @@ struct __align__(16) MigSmem {
                                 // range -1/2 <= tau - lo - 1/2 <= hi - lo - 1/2
     float tb[STAGES][BMAX];     // (lo + 1/2) dt + t0: T_s + T_r = (tau - lo - 1/2) dt + tb (gradient mode)
     float4 zc[MAX_ZG * NZ];     // per-z constants (ZConst for linear v; (z^2, w_z, 0, 0) for constant v)
+    float z2[MAX_ZG * NZ];      // linear: z^2 (exact for grid depths)
     float zero[4];
 };
 
@@ -138,11 +140,10 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                     tau_ref += (ls + lr) * inv_kdt;
                     S.refs[s][slot] = make_float4(rs.Rc2, rs.qc, rs.wc, rs.iuc);
                     S.refr[s][slot] = make_float4(rr.Rc2, rr.qc, rr.wc, rr.iuc);
-                    S.hdr[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
+                    S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
                                                  (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
-                } else {
-                    S.hdr[s][slot] = h;
                 }
+                S.hdr[s][slot] = h;
                 S.mid[s][slot] = m;
                 S.tb[s][slot] = (float)(((double)lo + 0.5) * g.dtd + g.t0d);
                 const float lim = (float)(hi - lo);
@@ -196,6 +197,7 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
     const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
     const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
     const float4* zc = &S.zc[tzg * NZ];
+    const float* zq = &S.z2[tzg * NZ];
     const int zero_off = (int)(((const char*)S.zero - (const char*)data) / (int)sizeof(TT));
 
     float acc[NZ];
@@ -247,18 +249,21 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
                     else acc[i] += val;
                 }
             } else {
-                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t];
+                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t], a = S.hda[s][t];
                 const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w}, rr{rrv.x, rrv.y, rrv.z, rrv.w};
-                const float dPs = fmaf(dxc, cxf + h.x, dyc * (cyf + h.y));
-                const float dPr = fmaf(dxc, cxf + h.z, dyc * (cyf + h.w));
+                const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
+                const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
+                const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
+                const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
                 const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
 #pragma unroll
                 for (int i = 0; i < NZ; ++i) {
                     const float4 c4 = zc[i];
                     const ZConst c{c4.x, c4.y, c4.z, c4.w};
                     float sqs, sqr;
-                    const float rho_s = leg_delta<WGT, FAST>(dPs, c, rs, qc2s, sqs);
-                    const float rho_r = leg_delta<WGT, FAST>(dPr, c, rr, qc2r, sqr);
+                    const float z2i = zq[i];
+                    const float rho_s = leg_delta<WGT, FAST>(dPs, dhs2, z2i, c, rs, qc2s, sqs);
+                    const float rho_r = leg_delta<WGT, FAST>(dPr, dhr2, z2i, c, rr, qc2r, sqr);
                     const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);   // U/U_c - 1
                     const float L = log1p_poly<LPT>(rho, g);
                     const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
@@ -322,6 +327,7 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
     const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
     const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
     const float4* zc = &S.zc[tzg * NZ];
+    const float* zq = &S.z2[tzg * NZ];
     const int zero_off = (int)(((const char*)S.zero - (const char*)data) / (int)sizeof(TT));
     const float dtf = (float)g.dtd;
     const float inv_v0 = (float)(1.0 / g.v0), inv_v0sq = (float)(1.0 / (g.v0 * g.v0));
@@ -383,18 +389,21 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
                     g0 = fmaf(W * mv[i] * slope, -Ssum * inv_v0sq, g0);
                 }
             } else {
-                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t];
+                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t], a = S.hda[s][t];
                 const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w}, rr{rrv.x, rrv.y, rrv.z, rrv.w};
-                const float dPs = fmaf(dxc, cxf + h.x, dyc * (cyf + h.y));
-                const float dPr = fmaf(dxc, cxf + h.z, dyc * (cyf + h.w));
+                const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
+                const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
+                const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
+                const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
                 const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
 #pragma unroll
                 for (int i = 0; i < NZ; ++i) {
                     const float4 c4 = zc[i];
                     const ZConst c{c4.x, c4.y, c4.z, c4.w};
                     float sqs, sqr, qws, qwr;
-                    const float rho_s = leg_delta_grad<FAST>(dPs, c, rs, qc2s, sqs, qws);
-                    const float rho_r = leg_delta_grad<FAST>(dPr, c, rr, qc2r, sqr, qwr);
+                    const float z2i = zq[i];
+                    const float rho_s = leg_delta_grad<FAST>(dPs, dhs2, z2i, c, rs, qc2s, sqs, qws);
+                    const float rho_r = leg_delta_grad<FAST>(dPr, dhr2, z2i, c, rr, qc2r, sqr, qwr);
                     const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
                     const float L = log1p_poly<LPT>(rho, g);
                     const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
@@ -474,6 +483,7 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
         if constexpr (VEL == VK_LINEAR) {
             const ZConst c = z_constants(z, box.cz, g);
             S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
+            S.z2[i] = (float)(z * z);
         } else {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
             S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);

@@ -74,13 +74,16 @@ __device__ __forceinline__ float log1p_poly(float rho, const GeomParams& g)
 }
 
 // One leg of the linear path: returns rho_leg = u/u_c - 1 and sqrt(q) (for the weight).
+// q itself is evaluated directly, q = alpha(z) (dh^2 + z^2), so that it keeps its relative
+// precision as R -> 0, where w = sqrt(q (q + 2)) has an infinite slope; the difference
+// q - q_c comes from the cancellation-free form and only scales the result.
 template <int WGT, bool FAST>
-__device__ __forceinline__ float leg_delta(float dP, const ZConst& zc, const LegRef& r, float qc2,
-                                           float& sq)
+__device__ __forceinline__ float leg_delta(float dP, float dh2, float z2, const ZConst& zc,
+                                           const LegRef& r, float qc2, float& sq)
 {
     const float E = fmaf(zc.kappa, r.Rc2, zc.dz2);
     const float dq = zc.alpha * (dP + E);
-    const float q = fmaxf(r.qc + dq, 0.f);   // q >= 0; rounding can leave -1 ulp at R = 0
+    const float q = zc.alpha * (dh2 + z2);
     float w;
     if constexpr (WGT == 1) {
         sq = hsqrt<FAST>(q);
@@ -126,12 +129,12 @@ struct TileBox {
 
 // leg_delta plus q/w = sqrt(q / (q + 2)) for the velocity derivatives; sq = sqrt(q) always.
 template <bool FAST>
-__device__ __forceinline__ float leg_delta_grad(float dP, const ZConst& zc, const LegRef& r,
-                                                float qc2, float& sq, float& qw)
+__device__ __forceinline__ float leg_delta_grad(float dP, float dh2, float z2, const ZConst& zc,
+                                                const LegRef& r, float qc2, float& sq, float& qw)
 {
     const float E = fmaf(zc.kappa, r.Rc2, zc.dz2);
     const float dq = zc.alpha * (dP + E);
-    const float q = fmaxf(r.qc + dq, 0.f);
+    const float q = zc.alpha * (dh2 + z2);
     sq = hsqrt<FAST>(q);
     const float t = hsqrt<FAST>(q + 2.f);
     const float w = sq * t;

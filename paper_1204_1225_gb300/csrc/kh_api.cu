@@ -287,6 +287,7 @@ static GeomParams geom_of(const kh_desc& d)
     g.A2cull = (float)((d.aperture * (1.0 + 1e-5) + 1.0) * (d.aperture * (1.0 + 1e-5) + 1.0));
     g.nt = d.nt;
     g.esize = dtype_size(d.trace_dtype);
+    g.tdtype = (int)d.trace_dtype;
     g.elem_align = 16 / g.esize;
     g.ld = d.nt;
     return g;

@@ -70,6 +70,7 @@ struct GeomParams {
     int nt;
     long long ld;            // row stride in elements
     int esize;               // bytes per sample
+    int tdtype;              // kh_dtype of the traces (F32, F16, BF16)
     int elem_align;          // samples per 16 bytes
 };
 

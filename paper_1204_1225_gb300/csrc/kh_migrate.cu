@@ -1,577 +1,28 @@
-// Migration kernel (Eq. 1, Sec. 3): output-stationary gather over an image tile and one
-// offset bin.
-//
-// CTA = 8 consumer warps + 1 producer warp.  Each consumer thread owns NZ = 16 consecutive
-// z samples of one image column and keeps their FP32 accumulators in registers for the
-// whole kernel; nothing is accumulated in global memory.  The producer warp walks the
-// bin's traces (sorted by bin), culls those whose midpoint is outside the aperture of the
-// tile footprint, bounds the two-way time over the tile box to a sample window
-// [lo, hi], computes the trace's FP64 reference at the tile centre (linear v(z)), and
-// stages the window into a 3-deep shared-memory ring with one cp.async.bulk per trace
-// (16-byte aligned, no multicast) completing on the stage's mbarrier.  Consumers evaluate
-// tau for their points (kh_tau.cuh), read the staged samples, interpolate linearly, weight
-// and accumulate.  All mbarrier waits are bounded; a wait that runs out sets the plan's
-// status word and the CTA leaves only after its copies have landed.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include "kh_tau.cuh"
+// Migration and velocity-gradient launches: dispatch on the trace type to the per-type
+// translation units (kh_migrate_f32.cu, kh_migrate_f16.cu), and the gradient's final sum.
+#include "kh_migrate_impl.cuh"
 
 namespace kh {
 
-template <typename TT>
-__device__ __forceinline__ float to_f32(TT v);
-template <>
-__device__ __forceinline__ float to_f32<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
-template <>
-__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+cudaError_t launch_dtype_f32(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int,
+                             int, const WaitCfg&, double*, cudaStream_t);
+cudaError_t launch_dtype_f16(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int,
+                             int, const WaitCfg&, double*, cudaStream_t);
+cudaError_t launch_dtype_bf16(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int,
+                              int, const WaitCfg&, double*, cudaStream_t);
 
-constexpr int MAX_ZG = 16;          // z-groups per CTA (cz)
-constexpr int SLACK = 16;           // zeroed elements after the ring (reads one past a window)
-
-struct __align__(16) MigSmem {
-    uint64_t full[STAGES];
-    uint64_t empty[STAGES];
-    int cnt[STAGES];
-    int last[STAGES];
-    // per staged trace
-    float4 hdr[STAGES][BMAX];   // (sx, sy, rx, ry)
-    float4 hda[STAGES][BMAX];   // linear: (c_x-2s_x, c_y-2s_y, c_x-2r_x, c_y-2r_y)
-    float4 refs[STAGES][BMAX];  // linear: source-leg LegRef
-    float4 refr[STAGES][BMAX];  // linear: receiver-leg LegRef
-    float2 mid[STAGES][BMAX];   // FP32 midpoint (aperture test)
-    int4 win[STAGES][BMAX];     // x: tau_ref - lo - 1/2 (float bits), y: smem index of sample lo
-                                // minus MAGIC_BITS, z/w: c_mid/c_half (float bits) of the valid
-                                // range -1/2 <= tau - lo - 1/2 <= hi - lo - 1/2
-    float tb[STAGES][BMAX];     // (lo + 1/2) dt + t0: T_s + T_r = (tau - lo - 1/2) dt + tb (gradient mode)
-    float4 zc[MAX_ZG * NZ];     // per-z constants (ZConst for linear v; (z^2, w_z, 0, 0) for constant v)
-    float z2[MAX_ZG * NZ];      // linear: z^2 (exact for grid depths)
-    float zero[4];
-};
-
-__host__ __device__ constexpr size_t mig_static_bytes() { return (sizeof(MigSmem) + 127) / 128 * 128; }
-
-// Elements of one stage's sample area: a full trace always fits, so every trace is stageable.
-__host__ __device__ inline int mig_cap(int nt, int ealign)
-{
-    const int need = (nt + 2 * ealign + ealign - 1) / ealign * ealign;
-    const int base = 24576 / 4;
-    return need > base ? need : base;
-}
-
-size_t migrate_smem_bytes(const GeomParams& g)
-{
-    return mig_static_bytes() + ((size_t)STAGES * mig_cap(g.nt, g.elem_align) + SLACK) * g.esize;
-}
-
-// ------------------------------------------------------------------ producer warp
-template <int VEL, typename TT>
-__device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
-                             const TraceSet& tr, const TT* __restrict__ traces, int tb, int te,
-                             const TileBox& box, const WaitCfg& wc)
-{
-    const int lane = threadIdx.x & 31;
-    const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
-    int cur = tb;
-    int n = 0;
-    bool failed = false;
-    while (true) {
-        const int s = n % STAGES;
-        if (n >= STAGES) {
-            if (!warp_wait(&S.empty[s], ((n / STAGES) - 1) & 1, wc.polls, wc.ns, wc.status)) {
-                failed = true;
-                break;
-            }
-        }
-        int cnt = 0, used = 0;
-        bool full = false;
-        while (cur < te && !full) {
-            const int k = cur + lane;
-            bool ok = false;
-            int lo = 0, hi = 0, lo_al = 0, len_al = 0;
-            float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 m = make_float2(0.f, 0.f);
-            if (k < te) {
-                h = tr.hdr[k];
-                m = tr.mid[k];
-                ok = true;
-                if (g.use_aperture) {
-                    const float ax = fmaxf(fmaxf(box.xlo - m.x, m.x - box.xhi), 0.f);
-                    const float ay = fmaxf(fmaxf(box.ylo - m.y, m.y - box.yhi), 0.f);
-                    ok = ax * ax + ay * ay <= g.A2cull;
-                }
-                if (ok) {
-                    ok = trace_window(h, box, VEL, g, lo, hi);
-                    lo_al = lo & ~(g.elem_align - 1);
-                    len_al = (hi + 1 - lo_al + g.elem_align - 1) & ~(g.elem_align - 1);
-                }
-            }
-            const unsigned okm = __ballot_sync(0xffffffffu, ok);
-            int pre = ok ? len_al : 0;   // inclusive prefix of window lengths
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, pre, o);
-                if (lane >= o) pre += v;
-            }
-            const int excl = pre - (ok ? len_al : 0);
-            const int rank = __popc(okm & ((1u << lane) - 1u));
-            const bool fits = ok && (cnt + rank < BMAX) && (used + excl + len_al <= cap);
-            const unsigned fm = __ballot_sync(0xffffffffu, fits);
-            const unsigned nofit = okm & ~fm;
-            const int consumed = nofit ? (__ffs(nofit) - 1) : min(32, te - cur);
-            const int nfit = __popc(fm);
-            int bytes = fits ? len_al * g.esize : 0;
-            int used_add = fits ? len_al : 0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-                used_add += __shfl_xor_sync(0xffffffffu, used_add, o);
-            }
-            if (fits) {
-                const int slot = cnt + rank;
-                const int dst = s * cap + used + excl;
-                double tau_ref = -g.t0d / g.dtd;
-                if constexpr (VEL == VK_LINEAR) {
-                    LegRef rs, rr;
-                    const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs);
-                    const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr);
-                    tau_ref += (ls + lr) * inv_kdt;
-                    S.refs[s][slot] = make_float4(rs.Rc2, rs.qc, rs.wc, rs.iuc);
-                    S.refr[s][slot] = make_float4(rr.Rc2, rr.qc, rr.wc, rr.iuc);
-                    S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
-                                                 (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
-                }
-                S.hdr[s][slot] = h;
-                S.mid[s][slot] = m;
-                S.tb[s][slot] = (float)(((double)lo + 0.5) * g.dtd + g.t0d);
-                const float lim = (float)(hi - lo);
-                S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo - 0.5)),
-                                           dst + (lo - lo_al) - MAGIC_BITS,
-                                           __float_as_int(0.5f * (lim - 1.f)), __float_as_int(0.5f * lim));
-            }
-            if (lane == 0 && bytes > 0) mbar_expect_tx(&S.full[s], (uint32_t)bytes);
-            __syncwarp();
-            if (fits) {
-                const int j = tr.perm[k];
-                const TT* src = traces + (long long)j * g.ld + lo_al;
-                bulk_g2s(data + s * cap + used + excl, src, (uint32_t)(len_al * g.esize), &S.full[s]);
-            }
-            cnt += nfit;
-            used += used_add;
-            cur += consumed;
-            full = (nofit != 0u) || cnt >= BMAX;
-        }
-        __syncwarp();
-        if (lane == 0) {
-            S.cnt[s] = cnt;
-            S.last[s] = (cur >= te) ? 1 : 0;
-            mbar_arrive(&S.full[s]);
-        }
-        __syncwarp();
-        ++n;
-        if (cur >= te) break;
-    }
-    if (failed) {
-        if (lane == 0) atomicOr(wc.status, 1);
-        // let every copy already issued land before the CTA can exit
-        const int first = n > STAGES ? n - STAGES : 0;
-        for (int f = first; f < n; ++f)
-            mbar_wait_bounded(&S.full[f % STAGES], (f / STAGES) & 1, 0, WAIT_NS, nullptr);
-    }
-}
-
-// ------------------------------------------------------------------ consumer warps
-template <int VEL, int WGT, bool FAST, typename TT, int LPT>
-__device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, const TileShape& ts,
-                             int x0, int y0, int z0, const TileBox& box, int bin,
-                             float* __restrict__ image, const WaitCfg& wc)
-{
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
-    const int ix = x0 + tx, iy = y0 + ty, izb = z0 + tzg * NZ;
-    const bool col_ok = ix < g.nx && iy < g.ny;
-    const float cxf = col_coord(g.ox, ix, g.dx);
-    const float cyf = (g.dim == 3) ? col_coord(g.oy, iy, g.dy) : 0.f;
-    const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
-    const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
-    const float4* zc = &S.zc[tzg * NZ];
-    const float* zq = &S.z2[tzg * NZ];
-    const int zero_off = (int)(((const char*)S.zero - (const char*)data) / (int)sizeof(TT));
-
-    float acc[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i) acc[i] = 0.f;
-
-    bool failed = false;
-    int n = 0;
-    while (true) {
-        const int s = n % STAGES;
-        if (!warp_wait(&S.full[s], (n / STAGES) & 1, wc.polls, wc.ns, wc.status)) {
-            failed = true;
-            break;
-        }
-        const int cnt = S.cnt[s];
-        const int last = S.last[s];
-        for (int t = 0; t < cnt; ++t) {
-            const int4 w = S.win[s][t];
-            bool inside = col_ok;
-            if (g.use_aperture) {
-                const float2 m = S.mid[s][t];
-                inside = inside && in_aperture(cxf, cyf, m.x, m.y, g.A2);
-            }
-            if (!__any_sync(0xffffffffu, inside)) continue;
-            const float c0rel = __int_as_float(w.x);
-            const float cmid = __int_as_float(w.z);
-            const float chalf = inside ? __int_as_float(w.w) : -1.f;
-            const float4 h = S.hdr[s][t];
-            if constexpr (VEL == VK_CONST) {
-                const float dxs = cxf - h.x, dys = cyf - h.y;
-                const float dxr = cxf - h.z, dyr = cyf - h.w;
-                const float dhs2 = fmaf(dxs, dxs, dys * dys);
-                const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
-#pragma unroll
-                for (int i = 0; i < NZ; ++i) {
-                    const float4 c = zc[i];   // (z^2, w_z)
-                    const float Rs = hsqrt<FAST>(dhs2 + c.x);
-                    const float Rr = hsqrt<FAST>(dhr2 + c.x);
-                    const float Ssum = Rs + Rr;
-                    const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
-                    const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
-                    const bool ok = fabsf(th - cmid) <= chalf;
-                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float d0 = to_f32<TT>(data[off]);
-                    const float d1 = to_f32<TT>(data[off + 1]);
-                    const float val = fmaf(f, d1 - d0, d0);
-                    if constexpr (WGT == 1) acc[i] = fmaf(c.y * Ssum, val, acc[i]);
-                    else acc[i] += val;
-                }
-            } else {
-                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t], a = S.hda[s][t];
-                const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w}, rr{rrv.x, rrv.y, rrv.z, rrv.w};
-                const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
-                const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
-                const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
-                const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
-                const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
-#pragma unroll
-                for (int i = 0; i < NZ; ++i) {
-                    const float4 c4 = zc[i];
-                    const ZConst c{c4.x, c4.y, c4.z, c4.w};
-                    float sqs, sqr;
-                    const float z2i = zq[i];
-                    const float rho_s = leg_delta<WGT, FAST>(dPs, dhs2, z2i, c, rs, qc2s, sqs);
-                    const float rho_r = leg_delta<WGT, FAST>(dPr, dhr2, z2i, c, rr, qc2r, sqr);
-                    const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);   // U/U_c - 1
-                    const float L = log1p_poly<LPT>(rho, g);
-                    const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
-                    const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
-                    const bool ok = fabsf(th - cmid) <= chalf;
-                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float d0 = to_f32<TT>(data[off]);
-                    const float d1 = to_f32<TT>(data[off + 1]);
-                    const float val = fmaf(f, d1 - d0, d0);
-                    if constexpr (WGT == 1) acc[i] = fmaf(c.gamma * (sqs + sqr), val, acc[i]);
-                    else acc[i] += val;
-                }
-            }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.empty[s]);
-        ++n;
-        if (last) break;
-    }
-    if (failed) {
-        if (lane == 0) atomicOr(wc.status, 1);
-        return;
-    }
-    if (!col_ok) return;
-    float* out = image + (((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb;
-    const bool vec = ((g.nz & 3) == 0) && (izb + NZ <= g.nz) &&
-                     ((reinterpret_cast<uintptr_t>(image) & 15) == 0);
-    if (vec) {
-#pragma unroll
-        for (int i = 0; i < NZ; i += 4)
-            *reinterpret_cast<float4*>(out + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < NZ; ++i)
-            if (izb + i < g.nz) out[i] = acc[i];
-    }
-}
-
-// ------------------------------------------------------------------ gradient consumer
-// dB/d(v0, k) of B(m, D) = <m, migrate(D)>: per contribution W m (D[i+1] - D[i]) dT/dth,
-// with dT/dth summed over both legs (the 1/dt of dtau/dth is applied in the final sum):
-//   constant v:  dT/dv0 = -(R_s + R_r)/v0^2;
-//   linear v(z): with q/w = sqrt(q/(q+2)) per leg and vz = v0 + k z,
-//                dT/dv0 = -(q/w)_sum (1/v0 + 1/vz)/|k|,
-//                dT/dk  = -sgn(k) (T_s + T_r)/|k| + (q/w)_sum (2/k - z/vz)/|k|.
-// Each thread sums its 16 z in FP32 per (column, trace) and carries FP64 totals; per-warp
-// FP64 partials go to `partial` for a fixed-order final sum.
-template <int VEL, int WGT, bool FAST, typename TT, int LPT>
-__device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, const TileShape& ts,
-                            int x0, int y0, int z0, const TileBox& box, int bin,
-                            const float* __restrict__ image, double* __restrict__ partial,
-                            const WaitCfg& wc)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
-    const int ix = x0 + tx, iy = y0 + ty, izb = z0 + tzg * NZ;
-    const bool col_ok = ix < g.nx && iy < g.ny;
-    const float cxf = col_coord(g.ox, ix, g.dx);
-    const float cyf = (g.dim == 3) ? col_coord(g.oy, iy, g.dy) : 0.f;
-    const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
-    const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
-    const float4* zc = &S.zc[tzg * NZ];
-    const float* zq = &S.z2[tzg * NZ];
-    const int zero_off = (int)(((const char*)S.zero - (const char*)data) / (int)sizeof(TT));
-    const float dtf = (float)g.dtd;
-    const float inv_v0 = (float)(1.0 / g.v0), inv_v0sq = (float)(1.0 / (g.v0 * g.v0));
-    const float inv_ka = (VEL == VK_LINEAR) ? (float)(1.0 / g.kabs) : 0.f;
-    const float sgnk = g.k < 0.0 ? -1.f : 1.f;
-    const float two_over_k = (VEL == VK_LINEAR) ? (float)(2.0 / g.k) : 0.f;
-    const float inv_a = (VEL == VK_LINEAR) ? (float)(1.0 / g.a) : 0.f;
-    const float zb = (float)(g.oz + izb * g.dz), dzf = (float)g.dz;
-
-    float mv[NZ];
-#pragma unroll
-    for (int i = 0; i < NZ; ++i)
-        mv[i] = (col_ok && izb + i < g.nz)
-                    ? image[(((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb + i]
-                    : 0.f;
-    double G0 = 0.0, G1 = 0.0;
-
-    bool failed = false;
-    int n = 0;
-    while (true) {
-        const int s = n % STAGES;
-        if (!warp_wait(&S.full[s], (n / STAGES) & 1, wc.polls, wc.ns, wc.status)) {
-            failed = true;
-            break;
-        }
-        const int cnt = S.cnt[s];
-        const int last = S.last[s];
-        for (int t = 0; t < cnt; ++t) {
-            const int4 w = S.win[s][t];
-            bool inside = col_ok;
-            if (g.use_aperture) {
-                const float2 m = S.mid[s][t];
-                inside = inside && in_aperture(cxf, cyf, m.x, m.y, g.A2);
-            }
-            if (!__any_sync(0xffffffffu, inside)) continue;
-            const float c0rel = __int_as_float(w.x);
-            const float cmid = __int_as_float(w.z);
-            const float chalf = inside ? __int_as_float(w.w) : -1.f;
-            const float tbase = S.tb[s][t];
-            const float4 h = S.hdr[s][t];
-            float g0 = 0.f, g1 = 0.f;
-            if constexpr (VEL == VK_CONST) {
-                const float dxs = cxf - h.x, dys = cyf - h.y;
-                const float dxr = cxf - h.z, dyr = cyf - h.w;
-                const float dhs2 = fmaf(dxs, dxs, dys * dys);
-                const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
-#pragma unroll
-                for (int i = 0; i < NZ; ++i) {
-                    const float4 c = zc[i];
-                    const float Rs = hsqrt<FAST>(dhs2 + c.x);
-                    const float Rr = hsqrt<FAST>(dhr2 + c.x);
-                    const float Ssum = Rs + Rr;
-                    const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
-                    const bool ok = fabsf(th - cmid) <= chalf;
-                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float slope = to_f32<TT>(data[off + 1]) - to_f32<TT>(data[off]);
-                    const float W = (WGT == 1) ? c.y * Ssum : 1.f;
-                    g0 = fmaf(W * mv[i] * slope, -Ssum * inv_v0sq, g0);
-                }
-            } else {
-                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t], a = S.hda[s][t];
-                const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w}, rr{rrv.x, rrv.y, rrv.z, rrv.w};
-                const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
-                const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
-                const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
-                const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
-                const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
-#pragma unroll
-                for (int i = 0; i < NZ; ++i) {
-                    const float4 c4 = zc[i];
-                    const ZConst c{c4.x, c4.y, c4.z, c4.w};
-                    float sqs, sqr, qws, qwr;
-                    const float z2i = zq[i];
-                    const float rho_s = leg_delta_grad<FAST>(dPs, dhs2, z2i, c, rs, qc2s, sqs, qws);
-                    const float rho_r = leg_delta_grad<FAST>(dPr, dhr2, z2i, c, rr, qc2r, sqr, qwr);
-                    const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
-                    const float L = log1p_poly<LPT>(rho, g);
-                    const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
-                    const bool ok = fabsf(th - cmid) <= chalf;
-                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float slope = to_f32<TT>(data[off + 1]) - to_f32<TT>(data[off]);
-                    const float W = (WGT == 1) ? c.gamma * (sqs + sqr) : 1.f;
-                    const float wms = W * mv[i] * slope;
-                    const float inv_vz = c.alpha * inv_a;
-                    const float z = fmaf((float)i, dzf, zb);
-                    const float qw = qws + qwr;
-                    const float Tsum = fmaf(th, dtf, tbase);
-                    const float dTv = -qw * (inv_v0 + inv_vz) * inv_ka;
-                    const float dTk = (fmaf(qw, fmaf(-z, inv_vz, two_over_k), -sgnk * Tsum)) * inv_ka;
-                    g0 = fmaf(wms, dTv, g0);
-                    g1 = fmaf(wms, dTk, g1);
-                }
-            }
-            G0 += (double)g0;
-            G1 += (double)g1;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.empty[s]);
-        ++n;
-        if (last) break;
-    }
-    if (failed) {
-        if (lane == 0) atomicOr(wc.status, 1);
-        G0 = 0.0;
-        G1 = 0.0;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        G0 += __shfl_xor_sync(0xffffffffu, G0, o);
-        G1 += __shfl_xor_sync(0xffffffffu, G1, o);
-    }
-    if (lane == 0) {
-        const long long slot = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * CONSUMER_WARPS + warp;
-        partial[2 * slot] = G0;
-        partial[2 * slot + 1] = G1;
-    }
-}
-
-// Shared body of the migration kernel (MODE 0: image out) and of the gradient kernel
-// (MODE 1: image in, per-warp partials out).
-template <int VEL, int WGT, bool FAST, typename TT, int LPT, int MODE>
-__device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape& ts, const TraceSet& tr,
-                                            const TT* __restrict__ traces, float* __restrict__ image,
-                                            int cap, const WaitCfg& wc, double* __restrict__ partial)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    MigSmem& S = *reinterpret_cast<MigSmem*>(smem_raw);
-    TT* data = reinterpret_cast<TT*>(smem_raw + mig_static_bytes());
-    __shared__ int s_abort;
-    const int bin = blockIdx.y;
-    int t = blockIdx.x;
-    const int tzi = t % ts.tiles_z;
-    t /= ts.tiles_z;
-    const int txi = t % ts.tiles_x, tyi = t / ts.tiles_x;
-    const int x0 = txi * ts.cx, y0 = tyi * ts.cy, z0 = tzi * ts.cz * NZ;
-
-    const TileBox box = tile_box(g, x0, y0, z0, ts.cx, ts.cy, ts.cz * NZ);
-
-    if (threadIdx.x == 0) {
-        // a wait in another CTA of this plan already ran out: results are invalid anyway
-        s_abort = *reinterpret_cast<const volatile int*>(wc.status);
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&S.full[s], 1);
-            mbar_init(&S.empty[s], CONSUMER_WARPS);
-        }
-        S.zero[0] = S.zero[1] = S.zero[2] = S.zero[3] = 0.f;
-        fence_barrier_init();
-    }
-    // per-z constants of the tile and a zero-filled ring (edge reads stay finite)
-    for (int i = threadIdx.x; i < ts.cz * NZ; i += blockDim.x) {
-        const double z = g.oz + (z0 + i) * g.dz;
-        if constexpr (VEL == VK_LINEAR) {
-            const ZConst c = z_constants(z, box.cz, g);
-            S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
-            S.z2[i] = (float)(z * z);
-        } else {
-            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-            S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
-        }
-    }
-    {
-        const int total = STAGES * cap + SLACK;
-        for (int i = threadIdx.x; i < total; i += blockDim.x) data[i] = TT(0.f);
-    }
-    __syncthreads();
-    if (s_abort) return;
-    if (threadIdx.x >= CONSUMERS) {
-        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
-                              box, wc);
-    } else if constexpr (MODE == 0) {
-        mig_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, wc);
-    } else {
-        vg_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, partial, wc);
-    }
-}
-
-template <int VEL, int WGT, bool FAST, typename TT, int LPT>
-__global__ void __launch_bounds__(THREADS, 2)
-    k_migrate(GeomParams g, TileShape ts, TraceSet tr, const TT* __restrict__ traces,
-              float* __restrict__ image, int cap, WaitCfg wc)
-{
-    kernel_body<VEL, WGT, FAST, TT, LPT, 0>(g, ts, tr, traces, image, cap, wc, nullptr);
-}
-
-template <int VEL, int WGT, bool FAST, typename TT, int LPT>
-__global__ void __launch_bounds__(THREADS, 2)
-    k_vgrad(GeomParams g, TileShape ts, TraceSet tr, const TT* __restrict__ traces,
-            const float* __restrict__ image, int cap, WaitCfg wc, double* __restrict__ partial)
-{
-    kernel_body<VEL, WGT, FAST, TT, LPT, 1>(g, ts, tr, traces, const_cast<float*>(image), cap, wc, partial);
-}
-
-template <int VEL, int WGT, bool FAST, typename TT>
-static cudaError_t launch_t(const GeomParams& g, const TileShape& t, const TraceSet& tr,
-                            const void* traces, float* image, const WaitCfg& w, double* partial,
-                            cudaStream_t s)
-{
-    const size_t smem = migrate_smem_bytes(g);
-    dim3 grid((unsigned)(t.tiles_x * t.tiles_y * t.tiles_z), (unsigned)g.n_bins);
-    const bool lng = VEL == VK_LINEAR && g.lp_terms == LP_LONG;
-    cudaError_t e;
-    if (partial == nullptr) {
-        auto kern = lng ? k_migrate<VEL, WGT, FAST, TT, LP_LONG> : k_migrate<VEL, WGT, FAST, TT, LP_SHORT>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
-                                         mig_cap(g.nt, g.elem_align), w);
-    } else {
-        auto kern = lng ? k_vgrad<VEL, WGT, FAST, TT, LP_LONG> : k_vgrad<VEL, WGT, FAST, TT, LP_SHORT>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
-                                         mig_cap(g.nt, g.elem_align), w, partial);
-    }
-    return cudaGetLastError();
-}
-
-template <typename TT>
-static cudaError_t launch_dtype(const GeomParams& g, const TileShape& t, const TraceSet& tr,
-                                const void* traces, float* image, int vel, int fast,
-                                const WaitCfg& w, double* partial, cudaStream_t s)
-{
-    const int key = vel * 4 + g.weight * 2 + (fast ? 1 : 0);
-    switch (key) {
-        case 0: return launch_t<VK_CONST, 0, false, TT>(g, t, tr, traces, image, w, partial, s);
-        case 1: return launch_t<VK_CONST, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
-        case 2: return launch_t<VK_CONST, 1, false, TT>(g, t, tr, traces, image, w, partial, s);
-        case 3: return launch_t<VK_CONST, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
-        case 4: return launch_t<VK_LINEAR, 0, false, TT>(g, t, tr, traces, image, w, partial, s);
-        case 5: return launch_t<VK_LINEAR, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
-        case 6: return launch_t<VK_LINEAR, 1, false, TT>(g, t, tr, traces, image, w, partial, s);
-        case 7: return launch_t<VK_LINEAR, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
+size_t migrate_smem_bytes(const GeomParams& g) { return mig_smem_bytes(g); }
 
 cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceSet& tr,
                            const void* traces, float* image, int vel_kind, int fast_math,
                            const WaitCfg& w, cudaStream_t s)
 {
     if (t.cz > MAX_ZG) return cudaErrorInvalidValue;
-    switch (g.esize) {
-        case 4: return launch_dtype<float>(g, t, tr, traces, image, vel_kind, fast_math, w, nullptr, s);
+    switch (g.tdtype) {
+        case KH_F32: return launch_dtype_f32(g, t, tr, traces, image, vel_kind, fast_math, w, nullptr, s);
+        case KH_F16: return launch_dtype_f16(g, t, tr, traces, image, vel_kind, fast_math, w, nullptr, s);
+        case KH_BF16:
+            return launch_dtype_bf16(g, t, tr, traces, image, vel_kind, fast_math, w, nullptr, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -581,8 +32,8 @@ cudaError_t launch_vgrad(const GeomParams& g, const TileShape& t, const TraceSet
                          const WaitCfg& w, double* partial, cudaStream_t s)
 {
     if (t.cz > MAX_ZG || !partial) return cudaErrorInvalidValue;
-    if (g.esize != 4) return cudaErrorInvalidValue;
-    return launch_dtype<float>(g, t, tr, traces, const_cast<float*>(image), vel_kind, fast_math, w,
+    if (g.tdtype != KH_F32) return cudaErrorInvalidValue;
+    return launch_dtype_f32(g, t, tr, traces, const_cast<float*>(image), vel_kind, fast_math, w,
                                partial, s);
 }
 

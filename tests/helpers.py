@@ -76,3 +76,11 @@ def gpu_vgrad(s, image, traces, fast_math=True, plan=None):
     out = p.velocity_grad(hdr, m, d)
     p.sync()
     return out.cpu().numpy(), p
+
+# Mixed-precision bar: relative L2 error of the image against the FP64 oracle fed the FP32 traces.
+MIXED_REL_L2 = 3e-3
+
+
+def quantize(traces, dtype):
+    """The trace values the kernel sees when they are stored as `dtype` (round to nearest even)."""
+    return torch.as_tensor(np.asarray(traces, dtype=np.float32)).to(dtype).to(torch.float64).numpy()

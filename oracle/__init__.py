@@ -45,7 +45,7 @@ class _Desc(ctypes.Structure):
                 ("bin_width", ctypes.c_double), ("vel", ctypes.c_int), ("v0", ctypes.c_double),
                 ("k", ctypes.c_double), ("weight", ctypes.c_int), ("r0", ctypes.c_double),
                 ("aperture", ctypes.c_double), ("nt", ctypes.c_int), ("t0", ctypes.c_double),
-                ("dt", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("table_spacing", ctypes.c_double)]
 
 
 def lib():
@@ -64,6 +64,7 @@ def lib():
             _lib.ko_migrate_points.restype = ctypes.c_int
             _lib.ko_bins.argtypes = [D, L, P, P, P, P, P]
             _lib.ko_traveltime.argtypes = [D, L, P, P, P, P, P]
+            _lib.ko_table_traveltime.argtypes = [D, L, P, P, P]
             _lib.ko_count.argtypes = [D, L, P, P, P, P]
             _lib.ko_arrivals.argtypes = [D, L, P, P, P, L, P, P, P, P, P]
             _lib.ko_count.restype = ctypes.c_longlong
@@ -76,8 +77,9 @@ def lib():
 def desc(s) -> _Desc:
     """Oracle descriptor from a ``Survey`` (any object with the same attribute names)."""
     return _Desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
-                 s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1}[s.vel], s.v0, s.k,
-                 {"one": 0, "obliq": 1}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt)
+                 s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1, "table": 2}[s.vel], s.v0, s.k,
+                 {"one": 0, "obliq": 1}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt,
+                 float(getattr(s, "table_spacing", 25.0)))
 
 
 def _ptr(a):
@@ -119,6 +121,16 @@ def traveltime(s, R, z, grad: bool = False):
     gk = np.empty_like(R) if grad else None
     lib().ko_traveltime(ctypes.byref(desc(s)), R.size, _ptr(R), _ptr(z), _ptr(T), _ptr(gv), _ptr(gk))
     return (T, gv, gk) if grad else T
+
+
+def table_traveltime(s, h, z) -> np.ndarray:
+    """Traveltime of the radial table (vel "table"): bilinear in (horizontal distance, depth)
+    between closed-form node values."""
+    h = np.ascontiguousarray(h, dtype=np.float64).ravel()
+    z = np.ascontiguousarray(np.broadcast_to(np.asarray(z, dtype=np.float64), h.shape)).ravel()
+    T = np.empty_like(h)
+    lib().ko_table_traveltime(ctypes.byref(desc(s)), h.size, _ptr(h), _ptr(z), _ptr(T))
+    return T
 
 
 def migrate(s, traces) -> np.ndarray:

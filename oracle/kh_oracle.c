@@ -38,13 +38,14 @@ typedef struct {
     double ox, oy, oz, dx, dy, dz;
     int n_bins;
     double bin_width;
-    int vel;                 /* 0 constant, 1 linear in z */
+    int vel;                 /* 0 constant, 1 linear in z, 2 table of the linear model */
     double v0, k;
     int weight;              /* 0 W=1, 1 obliquity x spreading */
     double r0;
     double aperture;         /* <= 0: full aperture */
     int nt;
     double t0, dt;
+    double table_spacing;    /* vel 2: node spacing of the radial traveltime table */
 } ko_desc;
 
 /* Deliberate-mistake switch used only by the tests that show the pins catch errors.
@@ -117,6 +118,34 @@ static void traveltime(const ko_desc* d, double R, double z, double* T, double* 
     }
 }
 
+/* Table traveltime (vel 2): the model v(z) = v0 + k z depends on depth only, so the time
+ * from a surface point to (h, z) (h = horizontal distance) is one function T(h, z).  It is
+ * tabulated at nodes h_i = i D, z_j = z_a + j D (D = table_spacing, z_a = D floor(z_min / D)
+ * with z_min the shallowest image depth) with the closed form, and read by bilinear
+ * interpolation in (h, z). */
+static double table_node(const ko_desc* d, double h, double z)
+{
+    ko_desc m = *d;
+    m.vel = (d->k == 0.0) ? 0 : 1;
+    double T;
+    traveltime(&m, sqrt(h * h + z * z), z, &T, NULL, NULL);
+    return T;
+}
+
+static double table_traveltime(const ko_desc* d, double h, double z)
+{
+    const double D = d->table_spacing;
+    const double zmin = (d->dz >= 0) ? d->oz : d->oz + (d->nz - 1) * d->dz;
+    const double za = D * floor(zmin / D);
+    const double uh = h / D, uz = (z - za) / D;
+    const double ih = floor(uh), jz = floor(uz);
+    const double fh = uh - ih, fz = uz - jz;
+    const double h0 = ih * D, h1 = (ih + 1.0) * D, z0 = za + jz * D, z1 = za + (jz + 1.0) * D;
+    const double a = (1.0 - fz) * table_node(d, h0, z0) + fz * table_node(d, h0, z1);
+    const double b = (1.0 - fz) * table_node(d, h1, z0) + fz * table_node(d, h1, z1);
+    return (1.0 - fh) * a + fh * b;
+}
+
 int ko_traveltime(const ko_desc* d, long n, const double* R, const double* z, double* T,
                   double* dTdv0, double* dTdk)
 {
@@ -146,6 +175,12 @@ static int offset_bin(const ko_desc* d, float sx, float sy, float rx, float ry)
     if (b < (double)d->n_bins) return (int)b;
     if (X == (double)d->n_bins * d->bin_width) return d->n_bins - 1;
     return -1;
+}
+
+int ko_table_traveltime(const ko_desc* d, long n, const double* h, const double* z, double* T)
+{
+    for (long i = 0; i < n; ++i) T[i] = table_traveltime(d, h[i], z[i]);
+    return 0;
 }
 
 int ko_bins(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
@@ -191,9 +226,15 @@ static contrib contribution(const ko_desc* d, double x, double y, double z, doub
     double Rs = sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy) + z * z);
     double Rr = sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry) + z * z);
     if (ko_mutation == 3) Rr = Rs;
-    double Ts, Tr, dsv, dsk, drv, drk;
-    traveltime(d, Rs, z, &Ts, want_grad ? &dsv : NULL, want_grad ? &dsk : NULL);
-    traveltime(d, Rr, z, &Tr, want_grad ? &drv : NULL, want_grad ? &drk : NULL);
+    double Ts, Tr, dsv = 0, dsk = 0, drv = 0, drk = 0;
+    if (d->vel == 2) {
+        Ts = table_traveltime(d, sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy)), z);
+        Tr = table_traveltime(d, sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry)), z);
+        if (ko_mutation == 3) Tr = Ts;
+    } else {
+        traveltime(d, Rs, z, &Ts, want_grad ? &dsv : NULL, want_grad ? &dsk : NULL);
+        traveltime(d, Rr, z, &Tr, want_grad ? &drv : NULL, want_grad ? &drk : NULL);
+    }
     double tau = (Ts + Tr - d->t0) / d->dt;
     if (ko_mutation == 2) tau = (Ts + Tr + d->t0) / d->dt;
     if (!(tau >= 0.0 && tau <= (double)(d->nt - 1))) return c;
@@ -397,8 +438,13 @@ int ko_arrivals(const ko_desc* d, long npts, const double* px, const double* py,
             double Rs = sqrt((x - sx[j]) * (x - sx[j]) + (y - ssy) * (y - ssy) + z * z);
             double Rr = sqrt((x - rx[j]) * (x - rx[j]) + (y - rry) * (y - rry) + z * z);
             double Ts, Tr;
-            traveltime(d, Rs, z, &Ts, NULL, NULL);
-            traveltime(d, Rr, z, &Tr, NULL, NULL);
+            if (d->vel == 2) {
+                Ts = table_traveltime(d, sqrt((x - sx[j]) * (x - sx[j]) + (y - ssy) * (y - ssy)), z);
+                Tr = table_traveltime(d, sqrt((x - rx[j]) * (x - rx[j]) + (y - rry) * (y - rry)), z);
+            } else {
+                traveltime(d, Rs, z, &Ts, NULL, NULL);
+                traveltime(d, Rr, z, &Tr, NULL, NULL);
+            }
             out[p * ntr + j] = Ts + Tr;
         }
     }

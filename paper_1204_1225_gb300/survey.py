@@ -25,7 +25,9 @@ class Survey:
     """Image grid, offset bins, velocity model, weight, trace sampling and trace headers.
 
     Image layout is ``[n_bins][ny][nx][nz]`` (z fastest); traces are ``[ntr][nt]``.
-    ``vel`` is ``"const"`` or ``"linear"`` (v(z) = v0 + k z, z from the surface);
+    ``vel`` is ``"const"``, ``"linear"`` (v(z) = v0 + k z, z from the surface) or ``"table"``
+    (the same v0 + k z model read from a radial traveltime table with node spacing
+    ``table_spacing``);
     ``weight`` is ``"one"`` or ``"obliq"``; ``aperture <= 0`` means full aperture.
     """
 
@@ -55,6 +57,7 @@ class Survey:
     rx: np.ndarray
     ry: np.ndarray
     name: str = ""
+    table_spacing: float = 25.0
 
     @property
     def ntr(self) -> int:

@@ -350,3 +350,27 @@ def test_pins_catch_planted_mistakes(mutation, check):
             check()
     finally:
         oracle.set_mutation(0)
+
+
+# ------------------------------------------------------------------ table traveltimes
+
+def test_table_traveltime_nodes_and_cells():
+    # nodes reproduce the closed form; a cell centre is the mean of its four corners
+    # (bilinear interpolation); the error against the closed form shrinks ~D^2
+    base = tiny_survey(vel="table", v0=1500.0, k=0.5, oz=0.0, dz=10.0, nz=200)
+    D = base.table_spacing
+    lin = base.replace(vel="linear")
+    h = np.array([0.0, D, 7 * D, 40 * D])
+    z = np.array([0.0, 3 * D, 11 * D, 60 * D])
+    T = oracle.table_traveltime(base, h, z)
+    assert rel(T, oracle.traveltime(lin, np.hypot(h, z), z)) < 1e-15
+    hc, zc = 7.5 * D, 11.5 * D
+    corners = oracle.traveltime(lin, np.hypot([7 * D, 7 * D, 8 * D, 8 * D], [11 * D, 12 * D, 11 * D, 12 * D]),
+                                np.array([11 * D, 12 * D, 11 * D, 12 * D]))
+    assert abs(oracle.table_traveltime(base, [hc], [zc])[0] - corners.mean()) < 1e-14
+    rng = np.random.default_rng(1)
+    hh, zz = rng.uniform(200, 2000, 200), rng.uniform(200, 2000, 200)
+    exact = oracle.traveltime(lin, np.hypot(hh, zz), zz)
+    e1 = np.max(np.abs(oracle.table_traveltime(base, hh, zz) - exact))
+    e2 = np.max(np.abs(oracle.table_traveltime(base.replace(table_spacing=D / 4), hh, zz) - exact))
+    assert 8.0 < e1 / e2 < 24.0                       # second-order convergence

@@ -53,7 +53,7 @@ typedef enum {
     KH_ERR_INTERNAL = 6
 } kh_status;
 
-typedef enum { KH_F32 = 0, KH_F16 = 1, KH_BF16 = 2 } kh_dtype;
+typedef enum { KH_F32 = 0, KH_F16 = 1, KH_BF16 = 2, KH_U16 = 3 } kh_dtype;
 
 /* Traveltime T(x, x_a) from a surface point x_a to an image point x (Sec. 3: "times for
  * propagation in the model"; the paper gives no formula):
@@ -61,9 +61,17 @@ typedef enum { KH_F32 = 0, KH_F16 = 1, KH_BF16 = 2 } kh_dtype;
  *  KH_VEL_LINEAR_Z: v(z) = v0 + k z, the circular-ray closed form
  *                   T = (2/k) asinh(k R / (2 sqrt(v0 (v0 + k z)))), evaluated as
  *                   T = arccosh(1 + q) / k, q = k^2 R^2 / (2 v0 (v0 + k z)).
- *  KH_VEL_TABLE:    T read from per-location tables on a coarse grid (table_spacing),
- *                   built from the LINEAR_Z closed form with the plan's v0, k, stored
- *                   as table_dtype, interpolated linearly in FP32. */
+ *  KH_VEL_TABLE:    the same v(z) = v0 + k z model read from a traveltime table.  Because
+ *                   the model depends on depth only, the table of every surface location
+ *                   is one radial table T(h, z) (h = horizontal distance), tabulated with
+ *                   the closed form at nodes h_i = i D, z_j = z_a + j D (D = table_spacing,
+ *                   z_a = D floor(shallowest image depth / D)) over the largest h of the
+ *                   call's traces, stored as table_dtype, staged into shared memory and
+ *                   read by bilinear interpolation in FP32.  table_dtype: KH_F32 (seconds),
+ *                   KH_F16 (T - T_min as FP16) or KH_U16 (16-bit fixed point
+ *                   T = T_min + scale u, scale = (T_max - T_min)/65535).  A migrate call
+ *                   with a table plan reads the headers' extent back to the host (it
+ *                   synchronises the stream). */
 typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2 } kh_vel;
 
 /* Weight W(x, x_s, x_r) of Eq. (1) ("amplitude of propagation"; no formula in the paper):
@@ -84,7 +92,7 @@ typedef struct {
     kh_vel vel;
     double v0, k;            /* v(z) = v0 + k z; k ignored for KH_VEL_CONST */
     double table_spacing;    /* KH_VEL_TABLE: node spacing of the traveltime tables, metres */
-    kh_dtype table_dtype;    /* KH_VEL_TABLE: KH_F32 or KH_F16 (FP16 with per-table offset) */
+    kh_dtype table_dtype;    /* KH_VEL_TABLE: KH_F32, KH_F16 (offset T_min) or KH_U16 (offset + scale) */
     kh_weight weight;
     double r0;               /* spreading normaliser, metres (KH_W_OBLIQ_SPREAD) */
     double aperture;         /* horizontal image-column to trace-midpoint distance limit, metres;

@@ -1,6 +1,7 @@
 // C ABI (include/kirchhoff.h): plan creation, argument validation, the trace binning pass
 // (offset bin per trace and a stable counting sort by bin), the Eq. 2 work count, the
 // traveltime evaluator and the dispatch to the migration / demigration / gradient kernels.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -241,9 +242,13 @@ static kh_status validate_desc(const kh_desc* d)
         if (!(d->v0 + d->k * zlo > 0) || !(d->v0 + d->k * zhi > 0))
             return fail(KH_ERR_UNSUPPORTED, "v(z) = v0 + k z must stay > 0 over the image depths");
     }
-    if (d->vel == KH_VEL_TABLE)
-        return fail(KH_ERR_UNSUPPORTED, "KH_VEL_TABLE plans are created with kirchhoff_create "
-                                        "only once the table path is built into this library");
+    if (d->vel == KH_VEL_TABLE) {
+        if (!(d->table_spacing > 0) || !std::isfinite(d->table_spacing))
+            return fail(KH_ERR_INVALID_ARG, "table_spacing must be > 0");
+        if (d->table_dtype != KH_F32 && d->table_dtype != KH_F16 && d->table_dtype != KH_U16)
+            return fail(KH_ERR_INVALID_ARG, "table_dtype must be KH_F32, KH_F16 or KH_U16");
+    }
+    if (d->trace_dtype == KH_U16) return fail(KH_ERR_INVALID_ARG, "traces cannot be KH_U16");
     const int ealign = 16 / dtype_size(d->trace_dtype);
     const int cap = std::max((d->nt + 3 * ealign) / ealign * ealign, 24576 / 4);
     if ((size_t)kh::STAGES * cap * dtype_size(d->trace_dtype) > 200u * 1024u)
@@ -368,7 +373,7 @@ static double rho_bound(const kh_desc& d, const GeomParams& g, int cx, int cy, i
 static kh_status prepare_linear(const kh_desc& d, const TileShape& t, GeomParams& g)
 {
     g.lp_terms = LP_SHORT;
-    if (g.k == 0.0) return KH_OK;
+    if (g.k == 0.0 || d.vel == KH_VEL_TABLE) return KH_OK;
     const double b = rho_bound(d, g, t.cx, t.cy, t.cz);
     g.rho_max = (float)std::expm1(b);
     // ln-error budget: 5e-6 of a sample in tau, i.e. 5e-6 |k| dt in ln U
@@ -405,7 +410,7 @@ static TileShape tile_of(const kh_plan_s* p)
     const int(*c)[3] = d.dim == 3 ? c3 : c2;
     const int nc = 4;
     GeomParams g = geom_of(d);
-    if (g.k == 0.0) return shape(d, c[0][0], c[0][1], c[0][2]);
+    if (g.k == 0.0 || d.vel == KH_VEL_TABLE) return shape(d, c[0][0], c[0][1], c[0][2]);
     int best = 0;
     double bb = 1e30;
     for (int i = 0; i < nc; ++i) {
@@ -538,6 +543,163 @@ static kh_status check_headers(const kh_plan_s* p, int ntr, const float* sx, con
     return KH_OK;
 }
 
+// ------------------------------------------------------------------ radial traveltime table
+
+// Largest horizontal distance from any source or receiver to the image footprint (a max is
+// order independent, so the atomic keeps the result deterministic).
+__global__ void k_hmax(int ntr, const float* __restrict__ sx, const float* __restrict__ sy,
+                       const float* __restrict__ rx, const float* __restrict__ ry, int dim, float xlo,
+                       float xhi, float ylo, float yhi, unsigned* __restrict__ out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (j < ntr) {
+        const float px[2] = {sx[j], rx[j]};
+        const float py[2] = {(dim == 3 && sy) ? sy[j] : 0.f, (dim == 3 && ry) ? ry[j] : 0.f};
+        for (int a = 0; a < 2; ++a) {
+            const float bx = fmaxf(fabsf(px[a] - xlo), fabsf(px[a] - xhi));
+            const float by = fmaxf(fabsf(py[a] - ylo), fabsf(py[a] - yhi));
+            m = fmaxf(m, sqrtf(bx * bx + by * by));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// FP64 closed-form node values T(i D, z_a + j D), nodes [nh][nz] with z fastest.
+__global__ void k_table_nodes(int nh, int nz, double D, double za, int vel, double v0, double k,
+                              double* __restrict__ T)
+{
+    const long long n = (long long)nh * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double h = (double)(i / nz) * D, z = za + (double)(i % nz) * D;
+        T[i] = tt_exact(sqrt(h * h + z * z), z, vel, v0, k);
+    }
+}
+
+__global__ void k_table_minmax(long long n, const double* __restrict__ T, double* __restrict__ mm)
+{
+    __shared__ double lo[256], hi[256];
+    double a = 1e300, b = -1e300;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        a = fmin(a, T[i]);
+        b = fmax(b, T[i]);
+    }
+    lo[threadIdx.x] = a;
+    hi[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            lo[threadIdx.x] = fmin(lo[threadIdx.x], lo[threadIdx.x + w]);
+            hi[threadIdx.x] = fmax(hi[threadIdx.x], hi[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        mm[0] = lo[0];
+        mm[1] = hi[0];
+    }
+}
+
+// Stored values: F32 seconds; F16 T - T_min; U16 round((T - T_min) / scale).
+__global__ void k_table_store(long long n, const double* __restrict__ T, int dt, double tmin,
+                              double scale, void* __restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (dt == KH_F32) {
+            static_cast<float*>(out)[i] = (float)T[i];
+        } else if (dt == KH_F16) {
+            static_cast<__half*>(out)[i] = __double2half(T[i] - tmin);
+        } else {
+            const double u = rint((T[i] - tmin) / scale);
+            static_cast<unsigned short*>(out)[i] = (unsigned short)fmin(fmax(u, 0.0), 65535.0);
+        }
+    }
+}
+
+// Builds (or reuses) the radial table for this call's traces and fills the table fields of
+// g, including the scale and offset folded into C1 and c0.  Synchronises the stream.
+static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const float* sy, const float* rx,
+                              const float* ry, cudaStream_t s, GeomParams& g)
+{
+    const kh_desc& d = p->d;
+    cudaError_t e = cudaSuccess;
+    if (!p->ws_hmax) e = cudaMalloc(reinterpret_cast<void**>(&p->ws_hmax), sizeof(unsigned));
+    if (e == cudaSuccess && !p->ws_tmm) e = cudaMalloc(reinterpret_cast<void**>(&p->ws_tmm), 2 * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "workspace (table)");
+    const double x0 = d.ox, x1 = d.ox + (d.nx - 1) * d.dx;
+    const double y0 = d.dim == 3 ? d.oy : 0.0, y1 = d.dim == 3 ? d.oy + (d.ny - 1) * d.dy : 0.0;
+    e = cudaMemsetAsync(p->ws_hmax, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess && ntr > 0) {
+        k_hmax<<<(ntr + 255) / 256, 256, 0, s>>>(ntr, sx, sy, rx, ry, d.dim, (float)std::min(x0, x1),
+                                                 (float)std::max(x0, x1), (float)std::min(y0, y1),
+                                                 (float)std::max(y0, y1), p->ws_hmax);
+        ++p->launches;
+        e = cudaGetLastError();
+    }
+    unsigned hb = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, p->ws_hmax, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "table extent");
+    float hmax;
+    std::memcpy(&hmax, &hb, sizeof hmax);
+    const double D = d.table_spacing;
+    const double zmin = std::min(d.oz, d.oz + (d.nz - 1) * d.dz), zmax = std::max(d.oz, d.oz + (d.nz - 1) * d.dz);
+    const double za = D * std::floor(zmin / D);
+    const int nh = (int)std::floor(hmax * (1.0 + 1e-6) / D) + 3;
+    const int nz = (int)std::floor((zmax - za) / D) + 3;
+    const size_t es = d.table_dtype == KH_F32 ? 4 : 2;
+    const size_t bytes = ((size_t)nh * nz * es + 15) / 16 * 16;
+    if (bytes > 96u * 1024u)
+        return fail(KH_ERR_UNSUPPORTED, "traveltime table of %d x %d nodes (%zu bytes) exceeds the 96 KB "
+                                        "shared-memory budget; use a larger table_spacing", nh, nz, bytes);
+    if (p->tab_nh < nh || p->tab_nz != nz) {
+        const long long n = (long long)nh * nz;
+        if ((e = grow(p->ws_tab64, p->cap_tab64, (size_t)n)) != cudaSuccess) return cuda_fail(e, "workspace (table)");
+        if ((e = grow(p->ws_tab, p->cap_tab, bytes)) != cudaSuccess) return cuda_fail(e, "workspace (table)");
+        const int vel = d.k == 0.0 ? VK_CONST : VK_LINEAR;
+        const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+        k_table_nodes<<<blocks, 256, 0, s>>>(nh, nz, D, za, vel, d.v0, d.k, p->ws_tab64);
+        k_table_minmax<<<1, 256, 0, s>>>(n, p->ws_tab64, p->ws_tmm);
+        p->launches += 2;
+        double mm[2] = {0.0, 0.0};
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(mm, p->ws_tmm, sizeof mm, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "table build");
+        const double tmin = d.table_dtype == KH_F32 ? 0.0 : mm[0];
+        const double scale = d.table_dtype == KH_U16 ? std::max(mm[1] - mm[0], 1e-30) / 65535.0 : 1.0;
+        e = cudaMemsetAsync(p->ws_tab, 0, bytes, s);
+        if (e == cudaSuccess) {
+            k_table_store<<<blocks, 256, 0, s>>>(n, p->ws_tab64, (int)d.table_dtype, tmin, scale, p->ws_tab);
+            ++p->launches;
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "table store");
+        p->tab_nh = nh;
+        p->tab_nz = nz;
+        p->tab_tmin = tmin;
+        p->tab_scale = scale;
+    }
+    g.table = p->ws_tab;
+    g.tnh = p->tab_nh;
+    g.tnz = p->tab_nz;
+    g.tdt = (int)d.table_dtype;
+    g.tinv = (float)(1.0 / D);
+    g.thmax = (float)(g.tnh - 1) - 1e-3f;
+    g.tza = za;
+    g.tsp = D;
+    const double vmin = std::min(d.v0 + d.k * std::min(0.0, zmin), d.v0 + d.k * std::max(0.0, zmax));
+    g.tslack = (float)(2.0 * D / (vmin * d.dt) + 2.0);
+    const double c1 = p->tab_scale / d.dt;
+    g.C1 = (float)c1;
+    g.C1lo = (float)(c1 - (double)g.C1);
+    g.c0 = (2.0 * p->tab_tmin - d.t0) / d.dt - 0.5;
+    return KH_OK;
+}
+
 // Demigration tile: the first candidate whose sample window fits the kernel's 96 window rows
 // (|dT| <= diagonal / v_min per leg, plus the window slack) and, for v(z), whose rho range the
 // ln(1 + rho) fit covers; P image parts so that about six waves of warp tasks run.
@@ -631,6 +793,10 @@ kh_status kirchhoff_destroy(kh_plan p)
     cudaFree(p->ws_count);
     cudaFree(p->ws_partial);
     cudaFree(p->ws_dm);
+    cudaFree(p->ws_tab);
+    cudaFree(p->ws_tab64);
+    cudaFree(p->ws_tmm);
+    cudaFree(p->ws_hmax);
     for (auto& pr : p->ev_open) {
         if (pr.first) cudaEventDestroy(pr.first);
         if (pr.second) cudaEventDestroy(pr.second);
@@ -689,9 +855,13 @@ kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy
     if ((st = staged_traces(p, ntr, traces, s, &tr_ptr, &g.ld)) != KH_OK) return st;
     const TileShape tile = tile_of(p);
     if ((st = prepare_linear(p->d, tile, g)) != KH_OK) return st;
+    int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
+    if (p->d.vel == KH_VEL_TABLE) {
+        if ((st = ensure_table(p, ntr, sx, sy, rx, ry, s, g)) != KH_OK) return st;
+        vk = VK_TABLE;
+    }
     TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};
     WaitCfg w{p->ws_status, p->wait_polls, WAIT_NS};
-    const int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
     prof_begin(p, s);
     cudaError_t e = launch_migrate(g, tile, ts, tr_ptr, image, vk, p->fast_math, w, s);
     prof_end(p, s);
@@ -708,6 +878,8 @@ kh_status kirchhoff_demigrate(kh_plan p, int ntr, const float* sx, const float* 
     kh_status st = check_headers(p, ntr, sx, sy, rx, ry);
     if (st != KH_OK) return st;
     if (ntr > 0 && (!image || !traces_out)) return fail(KH_ERR_INVALID_ARG, "image/traces_out is NULL");
+    if (p->d.vel == KH_VEL_TABLE) return fail(KH_ERR_UNSUPPORTED, "demigration uses the analytic traveltimes; "
+                                                                  "create the plan with KH_VEL_LINEAR_Z");
     if (ntr == 0) return KH_OK;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const kh_desc& d = p->d;

@@ -57,6 +57,14 @@ struct GeomParams {
                              // tau_ref = -t0/dt) or ln(U/U_c) (linear v); C1lo = FP32 rounding
                              // error of C1
     double c0;               // -t0/dt - 1/2 (the window origin is subtracted per trace)
+    // radial traveltime table (KH_VEL_TABLE)
+    const void* table;       // [tnh][tnz] nodes, z fastest
+    int tnh, tnz;            // nodes along h and z
+    int tdt;                 // storage kh_dtype: KH_F32, KH_F16, KH_U16
+    float tinv;              // 1 / table_spacing
+    float thmax;             // largest usable h coordinate (tnh - 1 - 1e-3)
+    double tza, tsp;         // first z node, spacing
+    float tslack;            // extra window slack (samples) for the interpolation error
     float t0, dt;            // FP32 copies for the window bounds
     double t0d, dtd;         // exact values for the FP64 references
     // weight

@@ -65,9 +65,37 @@ __host__ __device__ inline int mig_cap(int nt, int ealign)
     return need > base ? need : base;
 }
 
-inline size_t mig_smem_bytes(const GeomParams& g)
+__host__ __device__ inline size_t mig_ring_bytes(const GeomParams& g)
 {
-    return mig_static_bytes() + ((size_t)STAGES * mig_cap(g.nt, g.elem_align) + SLACK) * g.esize;
+    return (((size_t)STAGES * mig_cap(g.nt, g.elem_align) + SLACK) * g.esize + 15) / 16 * 16;
+}
+
+__host__ __device__ inline size_t table_bytes(const GeomParams& g)
+{
+    if (!g.table) return 0;
+    const size_t es = g.tdt == KH_F32 ? 4 : 2;
+    return ((size_t)g.tnh * g.tnz * es + 15) / 16 * 16;
+}
+
+inline size_t mig_smem_bytes(const GeomParams& g) { return mig_static_bytes() + mig_ring_bytes(g) + table_bytes(g); }
+
+template <typename TB>
+__device__ __forceinline__ float tab_f32(TB v);
+template <>
+__device__ __forceinline__ float tab_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float tab_f32<__half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float tab_f32<unsigned short>(unsigned short v) { return (float)v; }
+
+// Bilinear read of the radial table at row pointer `r` (h row ih), depth node jz.
+template <typename TB>
+__device__ __forceinline__ float tab_bilerp(const TB* r, int tnz, int jz, float fz, float fh)
+{
+    const float a0 = tab_f32<TB>(r[jz]), a1 = tab_f32<TB>(r[jz + 1]);
+    const float b0 = tab_f32<TB>(r[jz + tnz]), b1 = tab_f32<TB>(r[jz + tnz + 1]);
+    const float a = fmaf(fz, a1 - a0, a0), b = fmaf(fz, b1 - b0, b0);
+    return fmaf(fh, b - a, a);
 }
 
 // ------------------------------------------------------------------ producer warp
@@ -107,7 +135,8 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                     ok = ax * ax + ay * ay <= g.A2cull;
                 }
                 if (ok) {
-                    ok = trace_window(h, box, VEL, g, lo, hi);
+                    ok = trace_window(h, box, VEL == VK_TABLE ? (g.k == 0.0 ? VK_CONST : VK_LINEAR) : VEL,
+                                      g, lo, hi);
                     lo_al = lo & ~(g.elem_align - 1);
                     len_al = (hi + 1 - lo_al + g.elem_align - 1) & ~(g.elem_align - 1);
                 }
@@ -136,7 +165,7 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
             if (fits) {
                 const int slot = cnt + rank;
                 const int dst = s * cap + used + excl;
-                double tau_ref = -g.t0d / g.dtd;
+                double tau_ref = (VEL == VK_TABLE) ? g.c0 + 0.5 : -g.t0d / g.dtd;
                 if constexpr (VEL == VK_LINEAR) {
                     LegRef rs, rr;
                     const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs);
@@ -187,10 +216,10 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
 }
 
 // ------------------------------------------------------------------ consumer warps
-template <int VEL, int WGT, bool FAST, typename TT, int LPT>
+template <int VEL, int WGT, bool FAST, typename TT, int LPT, typename TB>
 __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, const TileShape& ts,
                              int x0, int y0, int z0, const TileBox& box, int bin,
-                             float* __restrict__ image, const WaitCfg& wc)
+                             float* __restrict__ image, const WaitCfg& wc, const TB* tab)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
@@ -230,7 +259,39 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
             const float cmid = __int_as_float(w.z);
             const float chalf = inside ? __int_as_float(w.w) : -1.f;
             const float4 h = S.hdr[s][t];
-            if constexpr (VEL == VK_CONST) {
+            if constexpr (VEL == VK_TABLE) {
+                const float dxs = cxf - h.x, dys = cyf - h.y;
+                const float dxr = cxf - h.z, dyr = cyf - h.w;
+                const float dhs2 = fmaf(dxs, dxs, dys * dys);
+                const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
+                const float us = fminf(hsqrt<FAST>(dhs2) * g.tinv, g.thmax);
+                const float ur = fminf(hsqrt<FAST>(dhr2) * g.tinv, g.thmax);
+                const int ihs = (int)us, ihr = (int)ur;
+                const float fhs = us - (float)ihs, fhr = ur - (float)ihr;
+                const TB* rows = tab + ihs * g.tnz;
+                const TB* rowr = tab + ihr * g.tnz;
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) {
+                    const float4 c = zc[i];   // (jz bits, fz, w_z, z^2)
+                    const int jz = __float_as_int(c.x);
+                    const float Ssum = tab_bilerp<TB>(rows, g.tnz, jz, c.y, fhs) +
+                                       tab_bilerp<TB>(rowr, g.tnz, jz, c.y, fhr);
+                    const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
+                    const float tm = __fadd_rn(th, MAGIC);
+                    const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
+                    const bool ok = fabsf(th - cmid) <= chalf;
+                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
+                    const float d0 = to_f32<TT>(data[off]);
+                    const float d1 = to_f32<TT>(data[off + 1]);
+                    const float val = fmaf(f, d1 - d0, d0);
+                    if constexpr (WGT == 1) {
+                        const float Wt = c.z * (hsqrt<FAST>(dhs2 + c.w) + hsqrt<FAST>(dhr2 + c.w));
+                        acc[i] = fmaf(Wt, val, acc[i]);
+                    } else {
+                        acc[i] += val;
+                    }
+                }
+            } else if constexpr (VEL == VK_CONST) {
                 const float dxs = cxf - h.x, dys = cyf - h.y;
                 const float dxr = cxf - h.z, dyr = cyf - h.w;
                 const float dhs2 = fmaf(dxs, dxs, dys * dys);
@@ -453,7 +514,7 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
 
 // Shared body of the migration kernel (MODE 0: image out) and of the gradient kernel
 // (MODE 1: image in, per-warp partials out).
-template <int VEL, int WGT, bool FAST, typename TT, int LPT, int MODE>
+template <int VEL, int WGT, bool FAST, typename TT, int LPT, int MODE, typename TB = float>
 __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape& ts, const TraceSet& tr,
                                             const TT* __restrict__ traces, float* __restrict__ image,
                                             int cap, const WaitCfg& wc, double* __restrict__ partial)
@@ -488,6 +549,11 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
             const ZConst c = z_constants(z, box.cz, g);
             S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
             S.z2[i] = (float)(z * z);
+        } else if constexpr (VEL == VK_TABLE) {
+            const double u = (z - g.tza) / g.tsp;
+            const double j = floor(u);
+            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
+            S.zc[i] = make_float4(__int_as_float((int)j), (float)(u - j), wz, (float)(z * z));
         } else {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
             S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
@@ -497,24 +563,31 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
         const int total = STAGES * cap + SLACK;
         for (int i = threadIdx.x; i < total; i += blockDim.x) data[i] = TT(0.f);
     }
+    TB* tab = reinterpret_cast<TB*>(smem_raw + mig_static_bytes() + mig_ring_bytes(g));
+    if constexpr (VEL == VK_TABLE) {
+        const uint4* src = reinterpret_cast<const uint4*>(g.table);
+        uint4* dst = reinterpret_cast<uint4*>(tab);
+        const int n16 = (int)(table_bytes(g) / 16);
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
     __syncthreads();
     if (s_abort) return;
     if (threadIdx.x >= CONSUMERS) {
         mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
                               box, wc);
     } else if constexpr (MODE == 0) {
-        mig_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, wc);
+        mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab);
     } else {
         vg_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, partial, wc);
     }
 }
 
-template <int VEL, int WGT, bool FAST, typename TT, int LPT>
+template <int VEL, int WGT, bool FAST, typename TT, int LPT, typename TB = float>
 __global__ void __launch_bounds__(THREADS, 2)
     k_migrate(GeomParams g, TileShape ts, TraceSet tr, const TT* __restrict__ traces,
               float* __restrict__ image, int cap, WaitCfg wc)
 {
-    kernel_body<VEL, WGT, FAST, TT, LPT, 0>(g, ts, tr, traces, image, cap, wc, nullptr);
+    kernel_body<VEL, WGT, FAST, TT, LPT, 0, TB>(g, ts, tr, traces, image, cap, wc, nullptr);
 }
 
 template <int VEL, int WGT, bool FAST, typename TT, int LPT>
@@ -539,11 +612,15 @@ static cudaError_t launch_t(const GeomParams& g, const TileShape& t, const Trace
         auto kern = k_migrate<VEL, WGT, FAST, TT, LP_SHORT>;
         if constexpr (VEL == VK_LINEAR)
             if (lng) kern = k_migrate<VEL, WGT, FAST, TT, LP_LONG>;
+        if constexpr (VEL == VK_TABLE) {
+            if (g.tdt == KH_F16) kern = k_migrate<VEL, WGT, FAST, TT, LP_SHORT, __half>;
+            if (g.tdt == KH_U16) kern = k_migrate<VEL, WGT, FAST, TT, LP_SHORT, unsigned short>;
+        }
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
                                          mig_cap(g.nt, g.elem_align), w);
-    } else if constexpr (std::is_same<TT, float>::value) {
+    } else if constexpr (std::is_same<TT, float>::value && VEL != VK_TABLE) {
         auto kern = k_vgrad<VEL, WGT, FAST, TT, LP_SHORT>;
         if constexpr (VEL == VK_LINEAR)
             if (lng) kern = k_vgrad<VEL, WGT, FAST, TT, LP_LONG>;
@@ -572,6 +649,10 @@ cudaError_t launch_dtype(const GeomParams& g, const TileShape& t, const TraceSet
         case 5: return launch_t<VK_LINEAR, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
         case 6: return launch_t<VK_LINEAR, 1, false, TT>(g, t, tr, traces, image, w, partial, s);
         case 7: return launch_t<VK_LINEAR, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
+        case 8:
+        case 9: return launch_t<VK_TABLE, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
+        case 10:
+        case 11: return launch_t<VK_TABLE, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
         default: return cudaErrorInvalidValue;
     }
 }

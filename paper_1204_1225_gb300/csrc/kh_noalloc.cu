@@ -69,6 +69,9 @@ extern "C" kh_status kirchhoff_migrate_noalloc(const kh_desc* d, int ntr, const 
                          "holds 65536 traces); use kirchhoff_migrate for larger surveys");
     if (d->trace_dtype != KH_F32)
         return set_error(KH_ERR_UNSUPPORTED, "kirchhoff_migrate_noalloc: FP32 traces only");
+    if (d->vel == KH_VEL_TABLE)
+        return set_error(KH_ERR_UNSUPPORTED, "kirchhoff_migrate_noalloc: analytic traveltimes only "
+                                             "(a table needs device workspace)");
     if (!image || (ntr > 0 && (!sx || !rx || !traces)) || (ntr > 0 && d->dim == 3 && (!sy || !ry)))
         return set_error(KH_ERR_INVALID_ARG, "kirchhoff_migrate_noalloc: NULL array");
     if (ntr > 0 && ((reinterpret_cast<uintptr_t>(traces) & 15u) != 0 || (d->nt % 4) != 0))

@@ -33,6 +33,15 @@ struct kh_plan_s {
     size_t cap_partial = 0;
     float* ws_dm = nullptr;       // demigration partial traces [P][ntr][nt]
     size_t cap_dm = 0;
+    // radial traveltime table (KH_VEL_TABLE), rebuilt when a call needs a wider h range
+    unsigned char* ws_tab = nullptr;
+    size_t cap_tab = 0;
+    double* ws_tab64 = nullptr;
+    size_t cap_tab64 = 0;
+    double* ws_tmm = nullptr;     // [2] table min / max
+    unsigned* ws_hmax = nullptr;  // [1] largest horizontal distance (float bits)
+    int tab_nh = 0, tab_nz = 0;
+    double tab_tmin = 0.0, tab_scale = 1.0;
     // profiling: event pairs recorded around main kernels while enabled
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;

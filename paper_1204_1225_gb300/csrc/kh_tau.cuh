@@ -156,7 +156,7 @@ __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box
     leg_bounds(hr0, hr1, box.zlo, box.zhi, vel, v0, kf, tr0, tr1);
     const float tlo = (ts0 + tr0 - g.t0) * inv_dt;
     const float thi = (ts1 + tr1 - g.t0) * inv_dt;
-    const float slo = 2.f + 2e-4f * fabsf(tlo), shi = 2.f + 2e-4f * fabsf(thi);
+    const float slo = 2.f + 2e-4f * fabsf(tlo) + g.tslack, shi = 2.f + 2e-4f * fabsf(thi) + g.tslack;
     const float flo = floorf(tlo - slo), fhi = ceilf(thi + shi) + 1.f;
     if (!(fhi >= 1.f && flo <= (float)(g.nt - 2))) return false;   // also NaN
     lo = flo < 0.f ? 0 : (int)flo;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libkirchhoff.so")
 
 KH_OK, KH_ERR_INVALID_ARG, KH_ERR_UNSUPPORTED, KH_ERR_OOM, KH_ERR_CUDA, KH_ERR_TIMEOUT, \
     KH_ERR_INTERNAL = range(7)
-KH_F32, KH_F16, KH_BF16 = 0, 1, 2
+KH_F32, KH_F16, KH_BF16, KH_U16 = 0, 1, 2, 3
 KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE = 0, 1, 2
 KH_W_ONE, KH_W_OBLIQ_SPREAD = 0, 1
 KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE = 1, 2, 3
@@ -125,14 +125,21 @@ def _stream(stream):
 _DT = {torch.float32: KH_F32, torch.float16: KH_F16, torch.bfloat16: KH_BF16}
 
 
-def desc_from(s, trace_dtype=torch.float32, vel=None, table_spacing=25.0,
-              table_dtype=torch.float16) -> kh_desc:
-    """kh_desc from any object with the survey attributes (dim, nx, ..., nt, t0, dt)."""
+_TABLE_DT = {torch.float32: KH_F32, torch.float16: KH_F16, "f32": KH_F32, "f16": KH_F16, "u16": KH_U16}
+
+
+def desc_from(s, trace_dtype=torch.float32, vel=None, table_spacing=None,
+              table_dtype="u16") -> kh_desc:
+    """kh_desc from any object with the survey attributes (dim, nx, ..., nt, t0, dt).
+    ``s.vel == "table"`` selects the radial traveltime table of the v0 + k z model;
+    ``table_dtype`` is "f32", "f16" or "u16" (or torch.float32 / torch.float16)."""
     if vel is None:
-        vel = {"const": KH_VEL_CONST, "linear": KH_VEL_LINEAR_Z}[s.vel]
+        vel = {"const": KH_VEL_CONST, "linear": KH_VEL_LINEAR_Z, "table": KH_VEL_TABLE}[s.vel]
+    if table_spacing is None:
+        table_spacing = float(getattr(s, "table_spacing", 25.0))
     return kh_desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
                    s.dz, s.n_bins, s.bin_width, vel, s.v0, s.k, table_spacing,
-                   _DT[table_dtype], {"one": KH_W_ONE, "obliq": KH_W_OBLIQ_SPREAD}[s.weight],
+                   _TABLE_DT[table_dtype], {"one": KH_W_ONE, "obliq": KH_W_OBLIQ_SPREAD}[s.weight],
                    s.r0, s.aperture, s.nt, s.t0, s.dt, _DT[trace_dtype])
 
 

@@ -11,6 +11,13 @@ bins of 100 m, 2 km aperture, obliquity x spreading weight.  Synthetic data: 20 
 reflections from 4 seeded dipping planes (sheets of point scatterers every 100 m) and 40
 diffractors, arrival times from the library's traveltime kernel.
 
+Workload ``batch64-3d-vz``: 64 independent 3D v(z) migrations of uneven size (per job,
+seeded: n^3 image with n ~ U{64..192}, 1k-50k traces, 750-2000 samples), tiles chosen by the
+autotuner, run as one graph-captured persistent launch; the line also reports a loop of
+per-job kirchhoff_migrate calls on the same stream with the same tiles.
+
+``--trace-dtype f16|bf16`` stores the traces in 16 bits (FP32 arithmetic).
+
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (bounded
 samples of the same workload on the host cores).
 """
@@ -52,7 +59,11 @@ def workloads():
         "3d-vz-40k-128cube": lambda: sv.survey_3d_gradient(ntr=40_000, n=128),
         "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
         "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
+        "batch64-3d-vz": lambda: sv.survey_batch_3d(64),
     }
+
+
+_TDT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
 
 
 def dist_init():
@@ -230,6 +241,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--trace-dtype", default="f32", choices=sorted(_TDT))
+    ap.add_argument("--no-tune", action="store_true", help="batch: default tiles, no autotuning")
+    ap.add_argument("--tile-cache", default=None, help="batch: autotuner JSON cache path")
+    ap.add_argument("--no-loop", action="store_true", help="batch: skip the per-job loop arm")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -237,7 +252,10 @@ def main():
     s = workloads()[args.workload]()
     if args.impl == "reference":
         if rank == 0:
-            run_reference(args, s)
+            run_reference(args, s[0] if isinstance(s, list) else s)
+        return
+    if isinstance(s, list):
+        run_batched(args, s, ws, rank, local)
         return
 
     from paper_1204_1225_gb300 import build as khbuild
@@ -245,9 +263,10 @@ def main():
     khbuild.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    plan = kh.Plan(s, fast_math=bool(args.fast_math))
+    tdt = _TDT[args.trace_dtype]
+    plan = kh.Plan(s, fast_math=bool(args.fast_math), trace_dtype=tdt)
     hdr = kh.Headers.of(s, device=dev)
-    traces = synth_traces(s, plan, dev).contiguous()
+    traces = synth_traces(s, plan, dev).to(tdt).contiguous()
     image = torch.empty(plan.image_shape, dtype=torch.float32, device=dev)
     contrib = plan.count(hdr)
     stream = torch.cuda.current_stream(dev)
@@ -284,7 +303,7 @@ def main():
         h_img = torch.empty(plan.image_shape, dtype=torch.float32).pin_memory()
         d_tr = torch.empty_like(traces)
         d_hdr = kh.Headers(*[torch.empty_like(t) for t in hdr.args()], device=dev)
-        h2d = h_tr.numel() * 4 + sum(t.numel() * 4 for t in h_hdr)
+        h2d = h_tr.numel() * h_tr.element_size() + sum(t.numel() * 4 for t in h_hdr)
         d2h = h_img.numel() * 4
         barrier(ws)
         torch.cuda.synchronize(dev)
@@ -320,6 +339,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(s, traces.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)
+    tbytes = traces.numel() * traces.element_size()
     line = {
         "metric": "G image-point x trace contributions/s", "value": value, "unit": "Gcontrib/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -328,11 +348,113 @@ def main():
         "config": {"workload": s.name, "image": list(plan.image_shape), "ntr": s.ntr, "nt": s.nt,
                    "velocity": f"{s.vel} v0={s.v0} k={s.k}", "weight": s.weight,
                    "aperture_m": s.aperture, "contributions_per_step": contrib,
-                   "fast_math": bool(args.fast_math),
+                   "fast_math": bool(args.fast_math), "trace_storage": args.trace_dtype,
                    "l2": "inputs larger than L2 (traces %.0f MB, image %.0f MB)" % (
-                       traces.numel() * 4 / 1e6, image.numel() * 4 / 1e6),
+                       tbytes / 1e6, image.numel() * 4 / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args, surveys, ws, rank, local):
+    """64 uneven jobs: one graph-captured persistent launch per step vs a per-job loop."""
+    from paper_1204_1225_gb300 import build as khbuild
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    from paper_1204_1225_gb300.autotune import TileTuner
+    khbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    tdt = _TDT[args.trace_dtype]
+    jobs = []
+    for j, s in enumerate(surveys):
+        p = kh.Plan(s, fast_math=bool(args.fast_math), trace_dtype=tdt)
+        h = kh.Headers.of(s, device=dev)
+        g = torch.Generator(device=dev).manual_seed(sv.BASE_SEED + j)
+        d = torch.randn((s.ntr, s.nt), generator=g, device=dev).to(tdt).contiguous()
+        jobs.append((p, h, d, torch.empty(p.image_shape, dtype=torch.float32, device=dev)))
+    contrib = sum(p.count(h) for (p, h, _, _) in jobs)
+    t_tune = time.perf_counter()
+    tiles = {}
+    if not args.no_tune:
+        tuner = TileTuner(path=args.tile_cache or os.path.join(ROOT, "gpurun_out", "tiles.json"))
+        for (p, h, d, _) in jobs:
+            t = tuner.choose(p, h, d)
+            tiles[f"{t[0]}x{t[1]}x{t[2]}"] = tiles.get(f"{t[0]}x{t[1]}x{t[2]}", 0) + 1
+    t_tune = time.perf_counter() - t_tune
+    batch = kh.Batch(jobs)
+    graph = batch.capture()
+    info = batch.info()
+    launches_per_step = info["launches"]   # the capture ran the launch sequence once
+    for _ in range(args.warmup):
+        graph.replay()
+    batch.sync()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    batch.sync()
+    t_ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    value = contrib * args.steps * ws / (t_ms / 1e3) / 1e9
+    clocks = clk.summary()
+    loop = None
+    if not args.no_loop:
+        for _ in range(args.warmup):
+            for (p, h, d, m) in jobs:
+                p.migrate(h, d, out=m)
+        torch.cuda.synchronize(dev)
+        l0 = sum(p.launches for (p, _, _, _) in jobs)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for (p, h, d, m) in jobs:
+                p.migrate(h, d, out=m)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        for (p, _, _, _) in jobs:
+            p.sync()
+        tl = max_over_ranks(ws, e0.elapsed_time(e1))
+        loop = {"value": contrib * args.steps * ws / (tl / 1e3) / 1e9, "unit": "Gcontrib/s",
+                "ms_per_step": tl / args.steps,
+                "launches_per_step": (sum(p.launches for (p, _, _, _) in jobs) - l0) // args.steps,
+                "what": "per-job kirchhoff_migrate calls on the same stream, same tiles and precision"}
+    barrier(ws)
+    if rank != 0:
+        return
+    mufu = MUFU_PER_CONTRIB[("linear", "obliq")]
+    clk_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = N_SM * MUFU_PER_SM_CLK * clk_mhz * 1e6 / mufu / 1e9
+    roof = {"bound": "alu", "kernel": "k_migrate_batched", "achieved": value, "peak": peak,
+            "unit": "Gcontrib/s", "frac": value / peak, "traffic": None,
+            "peak_basis": f"{N_SM} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {clk_mhz:.0f} MHz / {mufu} "
+                          "MUFU ops per contribution; achieved over the whole graph replay"}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        s0, d0 = surveys[0], jobs[0][2]
+        cpu = cpu_baseline(s0, d0.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)
+    tb = sum(d.numel() * d.element_size() for (_, _, d, _) in jobs)
+    ib = sum(m.numel() * 4 for (_, _, _, m) in jobs)
+    line = {
+        "metric": "G image-point x trace contributions/s", "value": value, "unit": "Gcontrib/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {len(surveys)} jobs, n^3 n~U{{64..192}}, "
+                               "N_tr~U{1000..50000}, nt~U{750..2000}, 3D v(z) 1500+0.5z, 16 bins, "
+                               "obliquity weight, Gaussian traces seeded per job",
+                   "contributions_per_step": contrib, "trace_storage": args.trace_dtype,
+                   "work_items": info["items"], "ctas": info["ctas"], "tiles": tiles,
+                   "autotune_s": round(t_tune, 2),
+                   "l2": "inputs larger than L2 (traces %.1f GB, images %.1f GB)" % (tb / 1e9, ib / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "loop": loop, "speedup_vs_loop": (value / loop["value"]) if loop else None,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

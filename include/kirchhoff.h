@@ -157,23 +157,54 @@ KH_API kh_status kirchhoff_traveltime(kh_plan p, int n, const float* px, const f
 KH_API kh_status kirchhoff_count(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
                           const float* ry, int64_t* out_count, void* cuda_stream);
 
-/* One migration job of a batch (see kirchhoff_migrate_batched). */
+/* ---------------------------------------------------------------- batched persistent launch
+ * Many independent migrations, each with its own plan (grid, bins, v(z), tile), headers,
+ * traces and image, in ONE launch of a persistent kernel.  Each job computes Eq. (1) exactly
+ * as kirchhoff_migrate does with the same plan (bit-identical images: the same tile code,
+ * traces in the same order).  A job list becomes a device work list of (job, image tile,
+ * offset bin) items sorted by estimated cost, longest first (cost = tile points x traces of
+ * the bin that pass the aperture cull of the tile); one CTA per SM slot takes items from a
+ * single work counter (a scheduler index; no image value is accumulated in global memory).
+ * This balances jobs of very different sizes (Eq. 2: work ~ N_xyz N_tr per job) across the
+ * 152 SMs with no tail per job.  The paper distributes independent images over cluster
+ * nodes; it has no single-GPU counterpart of this entry point. */
+
+/* One migration job of a batch. */
 typedef struct {
-    kh_plan plan;            /* the job's plan (grid, bins, velocity, dtype) */
+    kh_plan plan;            /* the job's plan (grid, bins, velocity, dtype, KH_OPT_TILE) */
     int ntr;
-    const float *sx, *sy, *rx, *ry;
-    const void* traces;
-    float* image;
+    const float *sx, *sy, *rx, *ry;   /* device headers, read once by kirchhoff_batched_prepare */
+    const void* traces;      /* device [ntr][nt] rows in the plan's trace dtype, read at every launch */
+    float* image;            /* device [n_bins][ny][nx][nz], written (fully) at every launch */
 } kh_job;
 
-/* Migrates `njobs` independent jobs with ONE persistent kernel launch: a device work list
- * of (job, tile, bin) items, longest first, pulled by persistent CTAs from one work
- * counter (a scheduler counter, not an accumulation).  Results equal njobs calls of
- * kirchhoff_migrate.  All plans must share the trace dtype and velocity kind.  The launch
- * itself may be captured in a CUDA graph once kirchhoff_batched_prepare() has been called
- * on the same job list (it sizes the workspace and uploads headers; it synchronises). */
-KH_API kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, void* cuda_stream);
-KH_API kh_status kirchhoff_migrate_batched(int njobs, const kh_job* jobs, void* cuda_stream);
+typedef struct kh_batch_s* kh_batch;
+
+/* Plans a batch: validates the jobs, bins each job's headers into the batch's own device
+ * buffers, counts culled traces per (tile, bin), builds and uploads the sorted work list and
+ * sizes the grid (152 x resident CTAs per SM).  It allocates and synchronises `cuda_stream`;
+ * the plans and header arrays may be used for other calls afterwards.  The trace and image
+ * pointers are recorded and used by every kirchhoff_migrate_batched() call.
+ * All jobs must share the trace dtype, weight, fast-math option and velocity kind (constant,
+ * k = 0, or linear v(z)); tables (KH_VEL_TABLE) are refused with KH_ERR_UNSUPPORTED.
+ * Wait limits follow jobs[0].plan's KH_OPT_WAIT_POLLS.  Errors: KH_ERR_INVALID_ARG (NULL
+ * pointers, plans of another device), KH_ERR_UNSUPPORTED, KH_ERR_OOM, KH_ERR_CUDA. */
+KH_API kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out,
+                                           void* cuda_stream);
+/* Runs the batch on `cuda_stream`: row padding for jobs whose trace rows are not 16-byte
+ * aligned, a reset of the work counter and the persistent kernel.  Stream work only (no
+ * allocation, no synchronisation, no host read), so a CUDA graph may capture it; replays
+ * read the traces and write the images recorded at prepare.  Two launches of one batch
+ * must not overlap (they share the work counter). */
+KH_API kh_status kirchhoff_migrate_batched(kh_batch b, void* cuda_stream);
+/* Waits for `cuda_stream`; KH_ERR_TIMEOUT if a bounded wait of the batch's kernel ran out. */
+KH_API kh_status kirchhoff_batch_sync(kh_batch b, void* cuda_stream);
+/* Work items, grid size (CTAs), estimated contributions (culled traces x tile points,
+ * summed over items) and launches issued so far; any output pointer may be NULL. */
+KH_API kh_status kirchhoff_batch_info(kh_batch b, long long* n_items, int* n_ctas,
+                                      double* est_contributions, long long* launches);
+/* Frees the batch's device workspace (synchronises the device through cudaFree). */
+KH_API kh_status kirchhoff_batch_destroy(kh_batch b);
 
 /* Waits for the plan's work on `cuda_stream` and returns KH_ERR_TIMEOUT if a bounded
  * in-kernel wait ran out since the last call (clearing the flag), else KH_OK. */

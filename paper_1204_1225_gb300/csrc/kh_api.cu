@@ -1041,8 +1041,9 @@ const char* kirchhoff_version(void) { return "kirchhoff-gb300 0.1 (sm_103a)"; }
 }  // extern "C"
 
 // ------------------------------------------------------------------ helpers for the
-// allocation-free entry point (kh_noalloc.cu): the same validation, geometry, tile choice and
-// binning launches as the plan path, writing into caller-supplied device buffers.
+// allocation-free entry point (kh_noalloc.cu) and the batched launch (kh_batch.cu): the same
+// validation, geometry, tile choice, padding and binning launches as the plan path, writing
+// into caller-supplied device buffers.
 namespace kh {
 
 kh_status noalloc_prepare(const kh_desc* d, GeomParams* g, TileShape* t)
@@ -1054,6 +1055,30 @@ kh_status noalloc_prepare(const kh_desc* d, GeomParams* g, TileShape* t)
     tmp.d = *d;
     *t = tile_of(&tmp);
     return prepare_linear(*d, *t, *g);
+}
+
+kh_status plan_geometry(const kh_plan_s* p, GeomParams* g, TileShape* t)
+{
+    *g = geom_of(p->d);
+    *t = tile_of(p);
+    return prepare_linear(p->d, *t, *g);
+}
+
+kh_status plan_check_headers(const kh_plan_s* p, int ntr, const float* sx, const float* sy,
+                             const float* rx, const float* ry)
+{
+    return check_headers(p, ntr, sx, sy, rx, ry);
+}
+
+cudaError_t launch_pad(int ntr, int nt, long long ld, int esize, const void* src, void* dst, cudaStream_t s)
+{
+    const int blocks = (int)std::min<long long>(((long long)ntr * ld + 255) / 256, 65535);
+    if (esize == 4)
+        k_pad<float><<<std::max(blocks, 1), 256, 0, s>>>(ntr, nt, ld, (const float*)src, (float*)dst);
+    else
+        k_pad<unsigned short><<<std::max(blocks, 1), 256, 0, s>>>(ntr, nt, ld, (const unsigned short*)src,
+                                                                 (unsigned short*)dst);
+    return cudaGetLastError();
 }
 
 cudaError_t noalloc_bin(int ntr, const float* sx, const float* sy, const float* rx, const float* ry,

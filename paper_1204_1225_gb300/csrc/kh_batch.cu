@@ -1,0 +1,363 @@
+// Batched persistent migration: many independent migrations (each with its own plan, headers,
+// traces and image) in one launch of k_migrate_batched.
+//
+// kirchhoff_batched_prepare does everything that allocates, synchronises or reads back:
+// validation, each job's geometry, tile and ln(1 + rho) fit, binning of its headers into the
+// batch's own buffers, a per-(tile, bin) count of the traces that survive the aperture cull,
+// and the work list of (job, tile, bin) items sorted by estimated cost, longest first.
+// kirchhoff_migrate_batched then issues only stream work (row padding where a job's rows are
+// not 16-byte aligned, a 4-byte memset of the work counter and the persistent kernel), so a
+// CUDA graph can capture it and replay it.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <numeric>
+#include <vector>
+
+#include "kh_plan.h"
+#include "kh_tau.cuh"
+
+using namespace kh;
+
+struct kh_batch_s {
+    int device = 0;
+    int njobs = 0;
+    GeomParams g_max{};            // sizes the shared-memory ring (largest nt of the jobs)
+    int vel = VK_CONST, weight = 0, fast = 1, lp_terms = LP_SHORT, tdtype = KH_F32;
+    long long wait_polls = 0;
+    unsigned char* ws = nullptr;   // one device allocation holding everything below
+    BatchJob* d_jobs = nullptr;
+    int4* d_items = nullptr;
+    int* d_next = nullptr;         // work counter, zeroed before every launch
+    int* d_status = nullptr;       // bit 0: a bounded wait ran out
+    int n_items = 0;
+    int ctas = 0;
+    double work = 0.0;             // estimated contributions: culled traces x points, summed
+    long long launches = 0;
+    struct Pad {
+        int ntr, nt;
+        long long ld;
+        int esize;
+        const void* src;
+        void* dst;
+    };
+    std::vector<Pad> pads;
+};
+
+namespace {
+
+kh_status bfail(kh_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    return set_error(s, buf);
+}
+
+// Traces of bin `blockIdx.y` whose midpoint passes the producer's aperture cull for the
+// column footprint of xy tile `blockIdx.x` (all z tiles share it).
+__global__ void k_cull_count(GeomParams g, TileShape ts, const float2* __restrict__ mid,
+                             const int* __restrict__ bin_start, int* __restrict__ out)
+{
+    __shared__ int total;
+    const int txy = blockIdx.x, bin = blockIdx.y;
+    const int txi = txy % ts.tiles_x, tyi = txy / ts.tiles_x;
+    const TileBox box = tile_box(g, txi * ts.cx, tyi * ts.cy, 0, ts.cx, ts.cy, ts.cz * NZ);
+    if (threadIdx.x == 0) total = 0;
+    __syncthreads();
+    int c = 0;
+    for (int k = bin_start[bin] + threadIdx.x; k < bin_start[bin + 1]; k += blockDim.x) {
+        bool ok = true;
+        if (g.use_aperture) {
+            const float2 m = mid[k];
+            const float ax = fmaxf(fmaxf(box.xlo - m.x, m.x - box.xhi), 0.f);
+            const float ay = fmaxf(fmaxf(box.ylo - m.y, m.y - box.yhi), 0.f);
+            ok = ax * ax + ay * ay <= g.A2cull;
+        }
+        c += ok ? 1 : 0;
+    }
+    atomicAdd(&total, c);   // integer sum: order independent
+    __syncthreads();
+    if (threadIdx.x == 0) out[(size_t)bin * gridDim.x + txy] = total;
+}
+
+// Bump allocator over one device block (256-byte aligned pieces).
+struct Layout {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    }
+};
+
+int dtype_bytes(kh_dtype t) { return t == KH_F32 ? 4 : 2; }
+
+}  // namespace
+
+extern "C" {
+
+kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out, void* cuda_stream)
+{
+    if (!out) return bfail(KH_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (njobs < 1 || !jobs) return bfail(KH_ERR_INVALID_ARG, "need njobs >= 1 and a job array");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
+
+    // ---- validation and per-job geometry
+    std::vector<GeomParams> gs(njobs);
+    std::vector<TileShape> tss(njobs);
+    int vel = -1, weight = -1, fast = -1, tdt = -1, lp_max = LP_SHORT, nt_max = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const kh_job& J = jobs[j];
+        const kh_plan_s* p = J.plan;
+        if (!p) return bfail(KH_ERR_INVALID_ARG, "job %d: plan is NULL", j);
+        if (p->device != dev) return bfail(KH_ERR_INVALID_ARG, "job %d: plan belongs to device %d, current is %d",
+                                           j, p->device, dev);
+        kh_status st = plan_check_headers(p, J.ntr, J.sx, J.sy, J.rx, J.ry);
+        if (st != KH_OK) return st;
+        if (!J.image) return bfail(KH_ERR_INVALID_ARG, "job %d: image is NULL", j);
+        if (J.ntr > 0 && !J.traces) return bfail(KH_ERR_INVALID_ARG, "job %d: traces is NULL", j);
+        if (p->d.vel == KH_VEL_TABLE)
+            return bfail(KH_ERR_UNSUPPORTED, "job %d: the batched launch takes analytic traveltimes "
+                                             "(KH_VEL_CONST / KH_VEL_LINEAR_Z)", j);
+        if ((st = plan_geometry(p, &gs[j], &tss[j])) != KH_OK) return st;
+        if (tss[j].cz > 16 || tss[j].cx * tss[j].cy * tss[j].cz != CONSUMERS)
+            return bfail(KH_ERR_INTERNAL, "job %d: tile %dx%dx%d is not a 256-thread tile with cz <= 16", j,
+                         tss[j].cx, tss[j].cy, tss[j].cz);
+        const int vk = gs[j].k == 0.0 ? VK_CONST : VK_LINEAR;
+        if (j == 0) {
+            vel = vk;
+            weight = (int)p->d.weight;
+            fast = p->fast_math ? 1 : 0;
+            tdt = (int)p->d.trace_dtype;
+        } else if (vk != vel || (int)p->d.weight != weight || (p->fast_math ? 1 : 0) != fast ||
+                   (int)p->d.trace_dtype != tdt) {
+            return bfail(KH_ERR_UNSUPPORTED, "job %d: all jobs of a batch need the same velocity kind "
+                                             "(constant or linear), weight, fast-math option and trace dtype", j);
+        }
+        lp_max = std::max(lp_max, gs[j].lp_terms);
+        nt_max = std::max(nt_max, p->d.nt);
+    }
+
+    // ---- device layout
+    const int es = dtype_bytes((kh_dtype)tdt), ealign = 16 / es;
+    Layout L;
+    struct Off {
+        size_t bin, perm, bs, hdr, mid, pad, cull;
+        long long ld;
+        bool padded;
+    };
+    std::vector<Off> off(njobs);
+    size_t n_items = 0, n_cull = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const kh_job& J = jobs[j];
+        const kh_desc& d = J.plan->d;
+        const size_t n = (size_t)std::max(J.ntr, 1);
+        Off& o = off[j];
+        o.bin = L.take(n * sizeof(int));
+        o.perm = L.take(n * sizeof(int));
+        o.bs = L.take((size_t)(d.n_bins + 1) * sizeof(int));
+        o.hdr = L.take(n * sizeof(float4));
+        o.mid = L.take(n * sizeof(float2));
+        o.padded = J.ntr > 0 && !((reinterpret_cast<uintptr_t>(J.traces) & 15u) == 0 && d.nt % ealign == 0);
+        o.ld = o.padded ? (d.nt + ealign - 1) / ealign * ealign : d.nt;
+        o.pad = o.padded ? L.take((size_t)J.ntr * o.ld * es) : 0;
+        const TileShape& t = tss[j];
+        n_items += (size_t)t.tiles_x * t.tiles_y * t.tiles_z * d.n_bins;
+        n_cull += (size_t)t.tiles_x * t.tiles_y * d.n_bins;
+    }
+    if (n_items > (size_t)INT32_MAX) return bfail(KH_ERR_UNSUPPORTED, "more than 2^31 work items");
+    const size_t o_jobs = L.take(sizeof(BatchJob) * njobs);
+    const size_t o_items = L.take(sizeof(int4) * n_items);
+    const size_t o_next = L.take(sizeof(int));
+    const size_t o_status = L.take(sizeof(int));
+    const size_t o_cull = L.take(sizeof(int) * std::max<size_t>(n_cull, 1));
+
+    kh_batch_s* b = new kh_batch_s();
+    b->device = dev;
+    b->njobs = njobs;
+    b->vel = vel;
+    b->weight = weight;
+    b->fast = fast;
+    b->lp_terms = lp_max;
+    b->tdtype = tdt;
+    b->wait_polls = jobs[0].plan->wait_polls;
+    b->n_items = (int)n_items;
+    e = cudaMalloc(&b->ws, L.off);
+    if (e != cudaSuccess) {
+        delete b;
+        return set_cuda_error(e, "kirchhoff_batched_prepare: workspace");
+    }
+    auto fail_free = [&](kh_status st) {
+        cudaFree(b->ws);
+        delete b;
+        return st;
+    };
+    unsigned char* w = b->ws;
+    b->d_jobs = reinterpret_cast<BatchJob*>(w + o_jobs);
+    b->d_items = reinterpret_cast<int4*>(w + o_items);
+    b->d_next = reinterpret_cast<int*>(w + o_next);
+    b->d_status = reinterpret_cast<int*>(w + o_status);
+    int* d_cull = reinterpret_cast<int*>(w + o_cull);
+    if ((e = cudaMemsetAsync(b->d_status, 0, sizeof(int), s)) != cudaSuccess)
+        return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: memset"));
+
+    // ---- per job: binning, staged rows, cull counts
+    std::vector<BatchJob> hj(njobs);
+    std::vector<size_t> cull_at(njobs);
+    size_t cull_off = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const kh_job& J = jobs[j];
+        const kh_desc& d = J.plan->d;
+        const Off& o = off[j];
+        GeomParams g = gs[j];
+        if (g.lp_terms < lp_max)   // the longer Horner loop reads zeros above the job's own fit
+            for (int i = g.lp_terms; i < LP_LONG; ++i) g.lp[i] = 0.f;
+        g.ld = o.ld;
+        float4* hdr = reinterpret_cast<float4*>(w + o.hdr);
+        float2* mid = reinterpret_cast<float2*>(w + o.mid);
+        int* perm = reinterpret_cast<int*>(w + o.perm);
+        int* bs = reinterpret_cast<int*>(w + o.bs);
+        TraceSet tr{hdr, mid, perm, bs};
+        e = noalloc_bin(J.ntr, J.sx, J.sy, J.rx, J.ry, d, reinterpret_cast<int*>(w + o.bin), perm, bs, hdr, mid, s);
+        if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: binning"));
+        const void* rows = J.traces;
+        if (o.padded) {
+            rows = w + o.pad;
+            b->pads.push_back({J.ntr, d.nt, o.ld, es, J.traces, w + o.pad});
+        }
+        hj[j] = BatchJob{g, tss[j], tr, rows, J.image};
+        cull_at[j] = cull_off;
+        const TileShape& t = tss[j];
+        dim3 grid((unsigned)(t.tiles_x * t.tiles_y), (unsigned)d.n_bins);
+        k_cull_count<<<grid, 256, 0, s>>>(g, t, tr.mid, tr.bin_start, d_cull + cull_off);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: cull count"));
+        cull_off += (size_t)t.tiles_x * t.tiles_y * d.n_bins;
+    }
+    std::vector<int> cull(std::max<size_t>(n_cull, 1));
+    e = cudaMemcpyAsync(cull.data(), d_cull, sizeof(int) * n_cull, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: cull read-back"));
+
+    // ---- work list: (job, tile, bin), estimated cost = points x (culled traces + 4), longest first
+    std::vector<int4> items(n_items);
+    std::vector<double> cost(n_items);
+    size_t k = 0;
+    double work = 0.0;
+    for (int j = 0; j < njobs; ++j) {
+        const kh_desc& d = jobs[j].plan->d;
+        const TileShape& t = tss[j];
+        const int ntxy = t.tiles_x * t.tiles_y;
+        for (int tyi = 0; tyi < t.tiles_y; ++tyi)
+            for (int txi = 0; txi < t.tiles_x; ++txi) {
+                const int cols = std::min(t.cx, d.nx - txi * t.cx) * std::min(t.cy, d.ny - tyi * t.cy);
+                for (int tzi = 0; tzi < t.tiles_z; ++tzi) {
+                    const int zs = std::min(t.cz * NZ, d.nz - tzi * t.cz * NZ);
+                    const int tile = (tyi * t.tiles_x + txi) * t.tiles_z + tzi;
+                    for (int bin = 0; bin < d.n_bins; ++bin) {
+                        const int c = cull[cull_at[j] + (size_t)bin * ntxy + tyi * t.tiles_x + txi];
+                        items[k] = make_int4(j, tile, bin, 0);
+                        cost[k] = (double)cols * zs * (c + 4);
+                        work += (double)cols * zs * c;
+                        ++k;
+                    }
+                }
+            }
+    }
+    std::vector<int> order(n_items);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<int4> sorted(n_items);
+    for (size_t i = 0; i < n_items; ++i) sorted[i] = items[order[i]];
+    b->work = work;
+
+    e = cudaMemcpyAsync(b->d_jobs, hj.data(), sizeof(BatchJob) * njobs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_items)
+        e = cudaMemcpyAsync(b->d_items, sorted.data(), sizeof(int4) * n_items, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host vectors go out of scope
+    if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: upload"));
+
+    GeomParams gm = gs[0];
+    gm.nt = nt_max;
+    gm.esize = es;
+    gm.elem_align = ealign;
+    gm.table = nullptr;
+    b->g_max = gm;
+    WaitCfg wc{b->d_status, b->wait_polls, WAIT_NS};
+    e = launch_migrate_batched(gm, b->d_jobs, b->d_items, b->n_items, b->d_next, vel, weight, fast, lp_max, tdt,
+                               wc, 0, &b->ctas, s);
+    if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: kernel set-up"));
+    *out = b;
+    return KH_OK;
+}
+
+kh_status kirchhoff_migrate_batched(kh_batch b, void* cuda_stream)
+{
+    if (!b) return bfail(KH_ERR_INVALID_ARG, "batch is NULL");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
+    if (dev != b->device) return bfail(KH_ERR_INVALID_ARG, "batch belongs to device %d, current is %d", b->device, dev);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    for (const auto& p : b->pads) {
+        if ((e = launch_pad(p.ntr, p.nt, p.ld, p.esize, p.src, p.dst, s)) != cudaSuccess)
+            return set_cuda_error(e, "kirchhoff_migrate_batched: row padding");
+        ++b->launches;
+    }
+    if (b->n_items == 0) return KH_OK;
+    if ((e = cudaMemsetAsync(b->d_next, 0, sizeof(int), s)) != cudaSuccess)
+        return set_cuda_error(e, "kirchhoff_migrate_batched: counter reset");
+    WaitCfg wc{b->d_status, b->wait_polls, WAIT_NS};
+    e = launch_migrate_batched(b->g_max, b->d_jobs, b->d_items, b->n_items, b->d_next, b->vel, b->weight,
+                               b->fast, b->lp_terms, b->tdtype, wc, b->ctas, nullptr, s);
+    ++b->launches;
+    if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_migrate_batched: persistent kernel");
+    return KH_OK;
+}
+
+kh_status kirchhoff_batch_sync(kh_batch b, void* cuda_stream)
+{
+    if (!b) return bfail(KH_ERR_INVALID_ARG, "batch is NULL");
+    int h = 0;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    if (e == cudaSuccess) e = cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_batch_sync");
+    if (h != 0) {
+        cudaMemset(b->d_status, 0, sizeof(int));
+        return bfail(KH_ERR_TIMEOUT, "a bounded in-kernel wait ran out (status 0x%x); results are invalid", h);
+    }
+    return KH_OK;
+}
+
+kh_status kirchhoff_batch_info(kh_batch b, long long* n_items, int* n_ctas, double* est_contributions,
+                               long long* launches)
+{
+    if (!b) return bfail(KH_ERR_INVALID_ARG, "batch is NULL");
+    if (n_items) *n_items = b->n_items;
+    if (n_ctas) *n_ctas = b->ctas;
+    if (est_contributions) *est_contributions = b->work;
+    if (launches) *launches = b->launches;
+    return KH_OK;
+}
+
+kh_status kirchhoff_batch_destroy(kh_batch b)
+{
+    if (!b) return KH_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    cudaFree(b->ws);
+    if (prev != b->device) cudaSetDevice(prev);
+    delete b;
+    return KH_OK;
+}
+
+}  // extern "C"

@@ -98,6 +98,26 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
                            const void* traces, float* image, int vel_kind, int fast_math,
                            const WaitCfg& w, cudaStream_t s);
 size_t migrate_smem_bytes(const GeomParams& g);
+
+// One job of a batched persistent launch: its geometry (with the ln(1 + rho) fit of its tile),
+// tile shape, binned headers, trace rows (16-byte aligned, row stride g.ld) and image.
+struct BatchJob {
+    GeomParams g;
+    TileShape ts;
+    TraceSet tr;
+    const void* traces;
+    float* image;
+};
+
+// The persistent kernel over `n_items` work items (job, tile, bin, -) taken in list order from
+// the counter `*next` (zeroed before the launch).  `g_max` sizes the shared-memory ring (its
+// nt is the largest of the jobs'); vel_kind/weight/fast/lp_terms/trace dtype are common to all
+// jobs.  `ctas` <= 0 launches nothing: it sets the kernel's shared-memory attribute and returns
+// the occupancy-sized grid through `ctas_out` (call it once before launching with that grid).
+cudaError_t launch_migrate_batched(const GeomParams& g_max, const BatchJob* jobs, const int4* items,
+                                   int n_items, int* next, int vel_kind, int weight, int fast,
+                                   int lp_terms, int trace_dtype, const WaitCfg& w, int ctas,
+                                   int* ctas_out, cudaStream_t s);
 // Velocity gradient: the migration kernel in gradient mode (image as input), per-warp FP64
 // partials [gridDim.y * gridDim.x * 8][2], then one fixed-order sum scaled by 1/dt.
 cudaError_t launch_vgrad(const GeomParams& g, const TileShape& t, const TraceSet& tr,

@@ -1,4 +1,4 @@
-// Migration and velocity-gradient launches: dispatch on the trace type to the per-type
+// Migration, batched-migration and velocity-gradient launches: dispatch on the trace type to the per-type
 // translation units (kh_migrate_f32.cu, kh_migrate_f16.cu), and the gradient's final sum.
 #include "kh_migrate_impl.cuh"
 
@@ -11,7 +11,34 @@ cudaError_t launch_dtype_f16(const GeomParams&, const TileShape&, const TraceSet
 cudaError_t launch_dtype_bf16(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int,
                               int, const WaitCfg&, double*, cudaStream_t);
 
+#define KH_BATCHED_DECL(name)                                                                            \
+    cudaError_t name(const GeomParams&, const BatchJob*, const int4*, int, int*, int, int, int, int,          \
+                     const WaitCfg&, int, int*, cudaStream_t);
+KH_BATCHED_DECL(launch_batched_f32)
+KH_BATCHED_DECL(launch_batched_f16)
+KH_BATCHED_DECL(launch_batched_bf16)
+#undef KH_BATCHED_DECL
+
 size_t migrate_smem_bytes(const GeomParams& g) { return mig_smem_bytes(g); }
+
+cudaError_t launch_migrate_batched(const GeomParams& gm, const BatchJob* jobs, const int4* items, int n_items,
+                                   int* next, int vel_kind, int weight, int fast, int lp_terms,
+                                   int trace_dtype, const WaitCfg& w, int ctas, int* ctas_out,
+                                   cudaStream_t s)
+{
+    switch (trace_dtype) {
+        case KH_F32:
+            return launch_batched_f32(gm, jobs, items, n_items, next, vel_kind, weight, fast, lp_terms, w, ctas,
+                                      ctas_out, s);
+        case KH_F16:
+            return launch_batched_f16(gm, jobs, items, n_items, next, vel_kind, weight, fast, lp_terms, w, ctas,
+                                      ctas_out, s);
+        case KH_BF16:
+            return launch_batched_bf16(gm, jobs, items, n_items, next, vel_kind, weight, fast, lp_terms, w, ctas,
+                                       ctas_out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceSet& tr,
                            const void* traces, float* image, int vel_kind, int fast_math,

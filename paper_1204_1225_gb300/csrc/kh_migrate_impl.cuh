@@ -99,15 +99,17 @@ __device__ __forceinline__ float tab_bilerp(const TB* r, int tnz, int jz, float 
 }
 
 // ------------------------------------------------------------------ producer warp
+// `n` is the number of stages this CTA's producer has filled before (mbarrier phases carry
+// over from one work item to the next in the persistent kernel); returns the new count.
 template <int VEL, typename TT>
-__device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
-                             const TraceSet& tr, const TT* __restrict__ traces, int tb, int te,
-                             const TileBox& box, const WaitCfg& wc)
+__device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
+                                            const TraceSet& tr, const TT* __restrict__ traces, int tb,
+                                            int te, const TileBox& box, const WaitCfg& wc, int n)
 {
     const int lane = threadIdx.x & 31;
     const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
     int cur = tb;
-    int n = 0;
+    const int n_begin = n;
     bool failed = false;
     while (true) {
         const int s = n % STAGES;
@@ -209,17 +211,20 @@ __device__ void mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
     if (failed) {
         if (lane == 0) atomicOr(wc.status, 1);
         // let every copy already issued land before the CTA can exit
-        const int first = n > STAGES ? n - STAGES : 0;
+        const int first = n - STAGES > n_begin ? n - STAGES : n_begin;
         for (int f = first; f < n; ++f)
             mbar_wait_bounded(&S.full[f % STAGES], (f / STAGES) & 1, 0, WAIT_NS, nullptr);
     }
+    return n;
 }
 
 // ------------------------------------------------------------------ consumer warps
+// `n`: stages consumed before this tile (see mig_producer); returns the new count.
 template <int VEL, int WGT, bool FAST, typename TT, int LPT, typename TB>
-__device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, const TileShape& ts,
-                             int x0, int y0, int z0, const TileBox& box, int bin,
-                             float* __restrict__ image, const WaitCfg& wc, const TB* tab)
+__device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const GeomParams& g,
+                                            const TileShape& ts, int x0, int y0, int z0,
+                                            const TileBox& box, int bin, float* __restrict__ image,
+                                            const WaitCfg& wc, const TB* tab, int n)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
@@ -238,7 +243,6 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
     for (int i = 0; i < NZ; ++i) acc[i] = 0.f;
 
     bool failed = false;
-    int n = 0;
     while (true) {
         const int s = n % STAGES;
         if (!warp_wait(&S.full[s], (n / STAGES) & 1, wc.polls, wc.ns, wc.status)) {
@@ -351,9 +355,9 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
     }
     if (failed) {
         if (lane == 0) atomicOr(wc.status, 1);
-        return;
+        return n;
     }
-    if (!col_ok) return;
+    if (!col_ok) return n;
     float* out = image + (((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb;
     const bool vec = ((g.nz & 3) == 0) && (izb + NZ <= g.nz) &&
                      ((reinterpret_cast<uintptr_t>(image) & 15) == 0);
@@ -366,6 +370,7 @@ __device__ void mig_consumer(MigSmem& S, const TT* data, const GeomParams& g, co
         for (int i = 0; i < NZ; ++i)
             if (izb + i < g.nz) out[i] = acc[i];
     }
+    return n;
 }
 
 // ------------------------------------------------------------------ gradient consumer
@@ -512,6 +517,29 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
     }
 }
 
+// Per-z constants of a tile's depth range [z0, z0 + cz NZ), written by all threads.
+template <int VEL>
+__device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, const TileShape& ts, int z0,
+                                             const TileBox& box)
+{
+    for (int i = threadIdx.x; i < ts.cz * NZ; i += blockDim.x) {
+        const double z = g.oz + (z0 + i) * g.dz;
+        if constexpr (VEL == VK_LINEAR) {
+            const ZConst c = z_constants(z, box.cz, g);
+            S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
+            S.z2[i] = (float)(z * z);
+        } else if constexpr (VEL == VK_TABLE) {
+            const double u = (z - g.tza) / g.tsp;
+            const double j = floor(u);
+            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
+            S.zc[i] = make_float4(__int_as_float((int)j), (float)(u - j), wz, (float)(z * z));
+        } else {
+            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
+            S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
+        }
+    }
+}
+
 // Shared body of the migration kernel (MODE 0: image out) and of the gradient kernel
 // (MODE 1: image in, per-warp partials out).
 template <int VEL, int WGT, bool FAST, typename TT, int LPT, int MODE, typename TB = float>
@@ -543,22 +571,7 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
         fence_barrier_init();
     }
     // per-z constants of the tile and a zero-filled ring (edge reads stay finite)
-    for (int i = threadIdx.x; i < ts.cz * NZ; i += blockDim.x) {
-        const double z = g.oz + (z0 + i) * g.dz;
-        if constexpr (VEL == VK_LINEAR) {
-            const ZConst c = z_constants(z, box.cz, g);
-            S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
-            S.z2[i] = (float)(z * z);
-        } else if constexpr (VEL == VK_TABLE) {
-            const double u = (z - g.tza) / g.tsp;
-            const double j = floor(u);
-            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-            S.zc[i] = make_float4(__int_as_float((int)j), (float)(u - j), wz, (float)(z * z));
-        } else {
-            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-            S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
-        }
-    }
+    tile_z_setup<VEL>(S, g, ts, z0, box);
     {
         const int total = STAGES * cap + SLACK;
         for (int i = threadIdx.x; i < total; i += blockDim.x) data[i] = TT(0.f);
@@ -574,9 +587,9 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
     if (s_abort) return;
     if (threadIdx.x >= CONSUMERS) {
         mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
-                              box, wc);
+                              box, wc, 0);
     } else if constexpr (MODE == 0) {
-        mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab);
+        mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, 0);
     } else {
         vg_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, partial, wc);
     }
@@ -656,5 +669,109 @@ cudaError_t launch_dtype(const GeomParams& g, const TileShape& t, const TraceSet
         default: return cudaErrorInvalidValue;
     }
 }
+
+// ------------------------------------------------------------------ batched persistent launch
+// One CTA per (SM, resident slot) loops over a work list of (job, tile, bin) items, longest
+// first, taking the next item from one global counter (a scheduler index, never image data).
+// Each item is the tile computation of k_migrate with the job's own geometry, tile shape,
+// headers, traces and image; the mbarrier ring and its phases persist across items.  A wait
+// that ran out anywhere in the launch (status word) stops every CTA at its next item.
+template <int VEL, int WGT, bool FAST, typename TT, int LPT>
+__global__ void __launch_bounds__(THREADS, 2)
+    k_migrate_batched(const BatchJob* __restrict__ jobs, const int4* __restrict__ items, int n_items,
+                      int* __restrict__ next, int cap, WaitCfg wc)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    MigSmem& S = *reinterpret_cast<MigSmem*>(smem_raw);
+    TT* data = reinterpret_cast<TT*>(smem_raw + mig_static_bytes());
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], CONSUMER_WARPS);
+        }
+        S.zero[0] = S.zero[1] = S.zero[2] = S.zero[3] = 0.f;
+        fence_barrier_init();
+    }
+    for (int i = threadIdx.x; i < STAGES * cap + SLACK; i += blockDim.x) data[i] = TT(0.f);
+    int n = 0;   // stages filled (producer warp) or consumed (consumer warps) so far
+    while (true) {
+        __syncthreads();   // the previous item's per-z constants and s_item are no longer read
+        if (threadIdx.x == 0) {
+            const int bad = *reinterpret_cast<const volatile int*>(wc.status);
+            s_item = bad ? n_items : atomicAdd(next, 1);
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int4 w = items[it];
+        const GeomParams g = jobs[w.x].g;
+        const TileShape ts = jobs[w.x].ts;
+        const TraceSet tr = jobs[w.x].tr;
+        int t = w.y;
+        const int tzi = t % ts.tiles_z;
+        t /= ts.tiles_z;
+        const int txi = t % ts.tiles_x, tyi = t / ts.tiles_x;
+        const int x0 = txi * ts.cx, y0 = tyi * ts.cy, z0 = tzi * ts.cz * NZ;
+        const int bin = w.z;
+        const TileBox box = tile_box(g, x0, y0, z0, ts.cx, ts.cy, ts.cz * NZ);
+        tile_z_setup<VEL>(S, g, ts, z0, box);
+        __syncthreads();
+        if (threadIdx.x >= CONSUMERS) {
+            n = mig_producer<VEL, TT>(S, data, cap, g, tr, static_cast<const TT*>(jobs[w.x].traces),
+                                      tr.bin_start[bin], tr.bin_start[bin + 1], box, wc, n);
+        } else {
+            n = mig_consumer<VEL, WGT, FAST, TT, LPT, float>(S, data, g, ts, x0, y0, z0, box, bin,
+                                                             jobs[w.x].image, wc, nullptr, n);
+        }
+    }
+}
+
+template <int VEL, int WGT, bool FAST, typename TT>
+static cudaError_t launch_batched_t(const GeomParams& gm, const BatchJob* jobs, const int4* items,
+                                   int n_items, int* next, int lp_terms, const WaitCfg& w, int ctas,
+                                   int* ctas_out, cudaStream_t s)
+{
+    auto kern = k_migrate_batched<VEL, WGT, FAST, TT, LP_SHORT>;
+    if constexpr (VEL == VK_LINEAR)
+        if (lp_terms == LP_LONG) kern = k_migrate_batched<VEL, WGT, FAST, TT, LP_LONG>;
+    const size_t smem = mig_smem_bytes(gm);
+    cudaError_t e;
+    if (ctas <= 0) {   // set-up only: shared-memory attribute and the occupancy-sized grid
+        int dev = 0, nsm = 0, occ = 0;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, smem)) != cudaSuccess)
+            return e;
+        ctas = nsm * (occ > 0 ? occ : 1);
+        if (ctas > n_items) ctas = n_items;
+        if (ctas_out) *ctas_out = ctas;
+        return cudaSuccess;
+    }
+    kern<<<ctas, THREADS, smem, s>>>(jobs, items, n_items, next, mig_cap(gm.nt, gm.elem_align), w);
+    return cudaGetLastError();
+}
+
+template <typename TT>
+cudaError_t launch_batched_dtype(const GeomParams& gm, const BatchJob* jobs, const int4* items, int n_items,
+                                 int* next, int vel, int weight, int fast, int lp_terms, const WaitCfg& w,
+                                 int ctas, int* ctas_out, cudaStream_t s)
+{
+    const int key = vel * 4 + weight * 2 + (fast ? 1 : 0);
+    switch (key) {
+        case 0: return launch_batched_t<VK_CONST, 0, false, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        case 1: return launch_batched_t<VK_CONST, 0, true, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        case 2: return launch_batched_t<VK_CONST, 1, false, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        case 3: return launch_batched_t<VK_CONST, 1, true, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        case 4: return launch_batched_t<VK_LINEAR, 0, false, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        case 5: return launch_batched_t<VK_LINEAR, 0, true, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        case 6: return launch_batched_t<VK_LINEAR, 1, false, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        case 7: return launch_batched_t<VK_LINEAR, 1, true, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 
 }  // namespace kh

@@ -62,6 +62,12 @@ kh_status staged_traces(kh_plan_s* p, int ntr, const void* traces, cudaStream_t 
 // Allocation-free path: validation, geometry and tile of a descriptor; binning launches into
 // caller-supplied device buffers (bin_start holds n_bins + 1 entries).
 kh_status noalloc_prepare(const kh_desc* d, GeomParams* g, TileShape* t);
+// Batched launch: a plan's geometry, tile (its KH_OPT_TILE, else the default) and v(z) fit;
+// header checks; the row-padding copy of staged_traces into a caller-supplied buffer.
+kh_status plan_geometry(const kh_plan_s* p, GeomParams* g, TileShape* t);
+kh_status plan_check_headers(const kh_plan_s* p, int ntr, const float* sx, const float* sy,
+                             const float* rx, const float* ry);
+cudaError_t launch_pad(int ntr, int nt, long long ld, int esize, const void* src, void* dst, cudaStream_t s);
 cudaError_t noalloc_bin(int ntr, const float* sx, const float* sy, const float* rx, const float* ry,
                         const kh_desc& d, int* bin, int* perm, int* bin_start, float4* hdr,
                         float2* mid, cudaStream_t s);

@@ -55,7 +55,8 @@ _lib = None
 
 EXPORTS = ["kirchhoff_create", "kirchhoff_destroy", "kirchhoff_migrate", "kirchhoff_demigrate",
            "kirchhoff_velocity_grad", "kirchhoff_traveltime", "kirchhoff_count",
-           "kirchhoff_batched_prepare", "kirchhoff_migrate_batched", "kirchhoff_sync",
+           "kirchhoff_batched_prepare", "kirchhoff_migrate_batched", "kirchhoff_batch_sync",
+           "kirchhoff_batch_info", "kirchhoff_batch_destroy", "kirchhoff_sync",
            "kirchhoff_set_option", "kirchhoff_launch_count", "kirchhoff_last_error",
            "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read",
            "kirchhoff_migrate_noalloc"]
@@ -78,8 +79,13 @@ def lib(path: str = LIB_PATH):
             L.kirchhoff_velocity_grad.argtypes = [P, I, P, P, P, P, P, P, P, P]
             L.kirchhoff_traveltime.argtypes = [P, I, P, P, P, P, P, P, P]
             L.kirchhoff_count.argtypes = [P, I, P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]
-            L.kirchhoff_batched_prepare.argtypes = [I, ctypes.POINTER(kh_job), P]
-            L.kirchhoff_migrate_batched.argtypes = [I, ctypes.POINTER(kh_job), P]
+            L.kirchhoff_batched_prepare.argtypes = [I, ctypes.POINTER(kh_job), ctypes.POINTER(P), P]
+            L.kirchhoff_migrate_batched.argtypes = [P, P]
+            L.kirchhoff_batch_sync.argtypes = [P, P]
+            L.kirchhoff_batch_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I),
+                                               ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_longlong)]
+            L.kirchhoff_batch_destroy.argtypes = [P]
             L.kirchhoff_sync.argtypes = [P, P]
             L.kirchhoff_set_option.argtypes = [P, I, ctypes.c_longlong]
             L.kirchhoff_launch_count.argtypes = [P]
@@ -229,14 +235,32 @@ def _jobs_array(jobs):
     return arr
 
 
-def kirchhoff_batched_prepare(jobs, stream=None) -> None:
+def kirchhoff_batched_prepare(jobs, stream=None) -> int:
+    """jobs: dicts with plan (handle), ntr, sx, sy, rx, ry, traces, image; returns a kh_batch."""
     arr = _jobs_array(jobs)
-    _check(lib().kirchhoff_batched_prepare(len(jobs), arr, _stream(stream)))
+    out = ctypes.c_void_p()
+    _check(lib().kirchhoff_batched_prepare(len(jobs), arr, ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
-def kirchhoff_migrate_batched(jobs, stream=None) -> None:
-    arr = _jobs_array(jobs)
-    _check(lib().kirchhoff_migrate_batched(len(jobs), arr, _stream(stream)))
+def kirchhoff_migrate_batched(batch, stream=None) -> None:
+    _check(lib().kirchhoff_migrate_batched(ctypes.c_void_p(batch), _stream(stream)))
+
+
+def kirchhoff_batch_sync(batch, stream=None) -> None:
+    _check(lib().kirchhoff_batch_sync(ctypes.c_void_p(batch), _stream(stream)))
+
+
+def kirchhoff_batch_info(batch) -> dict:
+    n, c, w, l = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_double(), ctypes.c_longlong()
+    _check(lib().kirchhoff_batch_info(ctypes.c_void_p(batch), ctypes.byref(n), ctypes.byref(c),
+                                      ctypes.byref(w), ctypes.byref(l)))
+    return {"items": int(n.value), "ctas": int(c.value), "est_contributions": float(w.value),
+            "launches": int(l.value)}
+
+
+def kirchhoff_batch_destroy(batch) -> None:
+    _check(lib().kirchhoff_batch_destroy(ctypes.c_void_p(batch)))
 
 
 # ------------------------------------------------------------ convenience wrapper
@@ -288,6 +312,11 @@ class Plan:
 
     def set_option(self, opt, value):
         kirchhoff_set_option(self.handle, opt, value)
+
+    def set_tile(self, tile):
+        """(cx, cy, cz) threads per CTA along x, y, z-groups, or None for the default."""
+        code = 0 if tile is None else (tile[0] | (tile[1] << 10) | (tile[2] << 20))
+        kirchhoff_set_option(self.handle, KH_OPT_TILE, code)
 
     def migrate(self, hdr: Headers, traces, out=None, stream=None):
         if out is None:
@@ -353,3 +382,54 @@ def arrival_times_fn(plan: "Plan"):
         return (ts.double() + tr.double()).view(n, m)
 
     return fn
+
+
+class Batch:
+    """Many migrations in one persistent launch (kirchhoff_batched_prepare / _migrate_batched).
+
+    ``jobs`` is a list of (Plan, Headers, traces, image) with device tensors; the traces and
+    images are read / written in place by every run (and every graph replay)."""
+
+    def __init__(self, jobs, stream=None):
+        self._keep = list(jobs)
+        self.handle = kirchhoff_batched_prepare(
+            [{"plan": p.handle, "ntr": h.ntr, "sx": h.sx, "sy": h.sy, "rx": h.rx, "ry": h.ry,
+              "traces": d, "image": m} for (p, h, d, m) in self._keep], stream)
+        self.graph = None
+
+    def run(self, stream=None):
+        kirchhoff_migrate_batched(self.handle, stream)
+
+    def capture(self):
+        """Captures one run in a CUDA graph (on a side stream) and returns it."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.run(s)
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def sync(self, stream=None):
+        kirchhoff_batch_sync(self.handle, stream)
+
+    def info(self) -> dict:
+        return kirchhoff_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.graph = None
+            kirchhoff_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Callable, Optional
+from typing import Callable, Optional, List
 
 import numpy as np
 
@@ -125,6 +125,22 @@ def survey_3d_gradient(ntr: int = 100_000, n: int = 256) -> Survey:
                   r0=1000.0, aperture=2000.0, nt=1500, t0=0.0, dt=0.004, sx=_f32(sx[sl]),
                   sy=_f32(sy[sl]), rx=_f32(rx[sl]), ry=_f32(ry[sl]),
                   name=f"3d-vz-{ntr}tr-{n}cube")
+
+
+def survey_batch_3d(n_jobs: int = 64, n_range=(64, 192), ntr_range=(1000, 50_000),
+                    nt_range=(750, 2000), seed: int = BASE_SEED) -> List[Survey]:
+    """Batch of independent 3D v(z) migrations of uneven size: job j draws, from a generator
+    seeded with seed + j, an image n^3 with n ~ U{n_range}, N_tr ~ U{ntr_range} traces and
+    nt ~ U{nt_range} samples, and is survey_3d_gradient(N_tr, n) with that nt (the image
+    always spans 3.2 km, so its spacing is 3200/n m)."""
+    out = []
+    for j in range(n_jobs):
+        rng = np.random.default_rng(seed + j)
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        ntr = int(rng.integers(ntr_range[0], ntr_range[1] + 1))
+        nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+        out.append(survey_3d_gradient(ntr, n).replace(nt=nt, name=f"3d-vz-{ntr}tr-{n}cube-{nt}nt"))
+    return out
 
 
 def survey_25d_lsm(nx: int = 512, nz: int = 400, nt: int = 2000, n_shots: int = 100,

@@ -159,7 +159,8 @@ KH_API kh_status kirchhoff_count(kh_plan p, int ntr, const float* sx, const floa
 
 /* ---------------------------------------------------------------- batched persistent launch
  * Many independent migrations, each with its own plan (grid, bins, v(z), tile), headers,
- * traces and image, in ONE launch of a persistent kernel.  Each job computes Eq. (1) exactly
+ * traces and image, in ONE launch of a persistent kernel (two when the batch mixes jobs
+ * whose v(z) tile fit needs 12 and 20 polynomial terms: one launch per length).  Each job computes Eq. (1) exactly
  * as kirchhoff_migrate does with the same plan (bit-identical images: the same tile code,
  * traces in the same order).  A job list becomes a device work list of (job, image tile,
  * offset bin) items sorted by estimated cost, longest first (cost = tile points x traces of

@@ -37,12 +37,14 @@ def default_cache_path() -> str:
 
 def bucket_key(survey, trace_dtype=torch.float32) -> str:
     """(precision, nt bucket, grid bucket, velocity kind): nt rounded up to a power of two,
-    each grid dimension and the spacing-scaled extent rounded up to 32 samples."""
+    each grid dimension rounded up to 32 samples, the grid spacing to a quarter octave (the
+    tile's extent in metres decides its v(z) fit length and cull)."""
     nt_b = 1 << max(0, math.ceil(math.log2(max(int(survey.nt), 1))))
     ny = survey.ny if survey.dim == 3 else 1
     grid = "x".join(str(-(-int(v) // 32) * 32) for v in (survey.nx, ny, survey.nz))
+    h_b = 2.0 ** (round(4.0 * math.log2(max(float(survey.dx), 1e-6))) / 4.0)
     vel = survey.vel if (survey.vel != "linear" or survey.k != 0.0) else "const"
-    return f"{_PREC[trace_dtype]}|nt{nt_b}|g{grid}|h{survey.dx:.4g}|{vel}|{survey.weight}|d{survey.dim}"
+    return f"{_PREC[trace_dtype]}|nt{nt_b}|g{grid}|h{h_b:.4g}|{vel}|{survey.weight}|d{survey.dim}"
 
 
 class TileTuner:

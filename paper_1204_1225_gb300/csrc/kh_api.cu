@@ -344,6 +344,7 @@ static bool fit_log1p(double lo, double hi, int terms, float* coef, float* scale
     }
     coef[0] = 1.f;
     for (int j = 0; j < n; ++j) coef[j + 1] = (float)cq[j];
+    for (int j = terms; j < LP_LONG; ++j) coef[j] = 0.f;   // kernels of a longer length read zeros
     *scale = (float)(1.0 / h);
     *offset = (float)(-m / h);
     double worst = 0.0;
@@ -369,7 +370,8 @@ static double rho_bound(const kh_desc& d, const GeomParams& g, int cx, int cy, i
     return 2.0 * g.kabs * half / vmin * 1.02 + 1e-6;
 }
 
-// The ln(1 + rho) fit for the tile: 12 terms if they reach 2e-9, else 20, else unsupported.
+// The ln(1 + rho) fit for the tile: the shortest length of LP_TERMS that meets the budget,
+// else unsupported.
 static kh_status prepare_linear(const kh_desc& d, const TileShape& t, GeomParams& g)
 {
     g.lp_terms = LP_SHORT;
@@ -378,9 +380,10 @@ static kh_status prepare_linear(const kh_desc& d, const TileShape& t, GeomParams
     g.rho_max = (float)std::expm1(b);
     // ln-error budget: 5e-6 of a sample in tau, i.e. 5e-6 |k| dt in ln U
     const double tol = std::max(5e-6 * g.kabs * d.dt, 1e-12);
-    if (fit_log1p(std::expm1(-b), std::expm1(b), LP_SHORT, g.lp, &g.lp_s, &g.lp_o, tol)) return KH_OK;
-    g.lp_terms = LP_LONG;
-    if (fit_log1p(std::expm1(-b), std::expm1(b), LP_LONG, g.lp, &g.lp_s, &g.lp_o, tol)) return KH_OK;
+    for (int i = 0; i < N_LP_TERMS; ++i) {
+        g.lp_terms = LP_TERMS[i];
+        if (fit_log1p(std::expm1(-b), std::expm1(b), g.lp_terms, g.lp, &g.lp_s, &g.lp_o, tol)) return KH_OK;
+    }
     return fail(KH_ERR_UNSUPPORTED, "tile too large for the v(z) delta evaluation (rho up to %.3f); "
                                     "choose a smaller tile with KH_OPT_TILE", std::expm1(b));
 }

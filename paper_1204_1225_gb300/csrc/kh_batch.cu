@@ -6,8 +6,8 @@
 // batch's own buffers, a per-(tile, bin) count of the traces that survive the aperture cull,
 // and the work list of (job, tile, bin) items sorted by estimated cost, longest first.
 // kirchhoff_migrate_batched then issues only stream work (row padding where a job's rows are
-// not 16-byte aligned, a 4-byte memset of the work counter and the persistent kernel), so a
-// CUDA graph can capture it and replay it.
+// not 16-byte aligned, a memset of the work counters, and the persistent kernel once per
+// ln(1 + rho) fit length present in the batch), so a CUDA graph can capture and replay it.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -23,15 +23,21 @@ struct kh_batch_s {
     int device = 0;
     int njobs = 0;
     GeomParams g_max{};            // sizes the shared-memory ring (largest nt of the jobs)
-    int vel = VK_CONST, weight = 0, fast = 1, lp_terms = LP_SHORT, tdtype = KH_F32;
+    int vel = VK_CONST, weight = 0, fast = 1, tdtype = KH_F32;
     long long wait_polls = 0;
     unsigned char* ws = nullptr;   // one device allocation holding everything below
     BatchJob* d_jobs = nullptr;
     int4* d_items = nullptr;
-    int* d_next = nullptr;         // work counter, zeroed before every launch
+    int* d_next = nullptr;         // work counters (one per part), zeroed before every run
     int* d_status = nullptr;       // bit 0: a bounded wait ran out
     int n_items = 0;
     int ctas = 0;
+    // The sorted work list is cut into parts of one ln(1 + rho) fit length each (shortest
+    // first); each part is one launch of the kernel compiled for that length.
+    struct Part {
+        int lp_terms, first, count, ctas;
+    };
+    std::vector<Part> parts;
     double work = 0.0;             // estimated contributions: culled traces x points, summed
     long long launches = 0;
     struct Pad {
@@ -96,6 +102,14 @@ struct Layout {
 
 int dtype_bytes(kh_dtype t) { return t == KH_F32 ? 4 : 2; }
 
+// Index of a fit length in LP_TERMS (constant and table jobs report LP_SHORT).
+int lp_class(int terms)
+{
+    for (int i = 0; i < N_LP_TERMS; ++i)
+        if (LP_TERMS[i] == terms) return i;
+    return N_LP_TERMS - 1;
+}
+
 }  // namespace
 
 extern "C" {
@@ -113,7 +127,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     // ---- validation and per-job geometry
     std::vector<GeomParams> gs(njobs);
     std::vector<TileShape> tss(njobs);
-    int vel = -1, weight = -1, fast = -1, tdt = -1, lp_max = LP_SHORT, nt_max = 0;
+    int vel = -1, weight = -1, fast = -1, tdt = -1, nt_max = 0;
     for (int j = 0; j < njobs; ++j) {
         const kh_job& J = jobs[j];
         const kh_plan_s* p = J.plan;
@@ -142,7 +156,6 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
             return bfail(KH_ERR_UNSUPPORTED, "job %d: all jobs of a batch need the same velocity kind "
                                              "(constant or linear), weight, fast-math option and trace dtype", j);
         }
-        lp_max = std::max(lp_max, gs[j].lp_terms);
         nt_max = std::max(nt_max, p->d.nt);
     }
 
@@ -176,7 +189,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     if (n_items > (size_t)INT32_MAX) return bfail(KH_ERR_UNSUPPORTED, "more than 2^31 work items");
     const size_t o_jobs = L.take(sizeof(BatchJob) * njobs);
     const size_t o_items = L.take(sizeof(int4) * n_items);
-    const size_t o_next = L.take(sizeof(int));
+    const size_t o_next = L.take(N_LP_TERMS * sizeof(int));
     const size_t o_status = L.take(sizeof(int));
     const size_t o_cull = L.take(sizeof(int) * std::max<size_t>(n_cull, 1));
 
@@ -186,7 +199,6 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     b->vel = vel;
     b->weight = weight;
     b->fast = fast;
-    b->lp_terms = lp_max;
     b->tdtype = tdt;
     b->wait_polls = jobs[0].plan->wait_polls;
     b->n_items = (int)n_items;
@@ -218,8 +230,6 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         const kh_desc& d = J.plan->d;
         const Off& o = off[j];
         GeomParams g = gs[j];
-        if (g.lp_terms < lp_max)   // the longer Horner loop reads zeros above the job's own fit
-            for (int i = g.lp_terms; i < LP_LONG; ++i) g.lp[i] = 0.f;
         g.ld = o.ld;
         float4* hdr = reinterpret_cast<float4*>(w + o.hdr);
         float2* mid = reinterpret_cast<float2*>(w + o.mid);
@@ -247,9 +257,11 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: cull read-back"));
 
-    // ---- work list: (job, tile, bin), estimated cost = points x (culled traces + 4), longest first
+    // ---- work list: (job, tile, bin), estimated cost = points x (culled traces + 4); grouped
+    // by the job's fit length (shortest first), longest first within a group
     std::vector<int4> items(n_items);
     std::vector<double> cost(n_items);
+    std::vector<int> cls(n_items);
     size_t k = 0;
     double work = 0.0;
     for (int j = 0; j < njobs; ++j) {
@@ -265,6 +277,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
                     for (int bin = 0; bin < d.n_bins; ++bin) {
                         const int c = cull[cull_at[j] + (size_t)bin * ntxy + tyi * t.tiles_x + txi];
                         items[k] = make_int4(j, tile, bin, 0);
+                        cls[k] = lp_class(gs[j].lp_terms);
                         cost[k] = (double)cols * zs * (c + 4);
                         work += (double)cols * zs * c;
                         ++k;
@@ -274,7 +287,9 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     }
     std::vector<int> order(n_items);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return cls[a] != cls[c] ? cls[a] < cls[c] : cost[a] > cost[c];
+    });
     std::vector<int4> sorted(n_items);
     for (size_t i = 0; i < n_items; ++i) sorted[i] = items[order[i]];
     b->work = work;
@@ -292,9 +307,18 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     gm.table = nullptr;
     b->g_max = gm;
     WaitCfg wc{b->d_status, b->wait_polls, WAIT_NS};
-    e = launch_migrate_batched(gm, b->d_jobs, b->d_items, b->n_items, b->d_next, vel, weight, fast, lp_max, tdt,
-                               wc, 0, &b->ctas, s);
-    if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: kernel set-up"));
+    for (int c = 0, first = 0; c < N_LP_TERMS; ++c) {
+        int count = 0;
+        for (size_t i = 0; i < n_items; ++i) count += cls[i] == c ? 1 : 0;
+        if (count == 0) continue;
+        kh_batch_s::Part part{LP_TERMS[c], first, count, 0};
+        e = launch_migrate_batched(gm, b->d_jobs, b->d_items + first, count, b->d_next + b->parts.size(), vel,
+                                   weight, fast, part.lp_terms, tdt, wc, 0, &part.ctas, s);
+        if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: kernel set-up"));
+        b->ctas = std::max(b->ctas, part.ctas);
+        b->parts.push_back(part);
+        first += count;
+    }
     *out = b;
     return KH_OK;
 }
@@ -313,13 +337,16 @@ kh_status kirchhoff_migrate_batched(kh_batch b, void* cuda_stream)
         ++b->launches;
     }
     if (b->n_items == 0) return KH_OK;
-    if ((e = cudaMemsetAsync(b->d_next, 0, sizeof(int), s)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(b->d_next, 0, N_LP_TERMS * sizeof(int), s)) != cudaSuccess)
         return set_cuda_error(e, "kirchhoff_migrate_batched: counter reset");
     WaitCfg wc{b->d_status, b->wait_polls, WAIT_NS};
-    e = launch_migrate_batched(b->g_max, b->d_jobs, b->d_items, b->n_items, b->d_next, b->vel, b->weight,
-                               b->fast, b->lp_terms, b->tdtype, wc, b->ctas, nullptr, s);
-    ++b->launches;
-    if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_migrate_batched: persistent kernel");
+    for (size_t i = 0; i < b->parts.size(); ++i) {
+        const kh_batch_s::Part& part = b->parts[i];
+        e = launch_migrate_batched(b->g_max, b->d_jobs, b->d_items + part.first, part.count, b->d_next + i, b->vel,
+                                   b->weight, b->fast, part.lp_terms, b->tdtype, wc, part.ctas, nullptr, s);
+        ++b->launches;
+        if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_migrate_batched: persistent kernel");
+    }
     return KH_OK;
 }
 

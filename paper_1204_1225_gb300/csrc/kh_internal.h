@@ -21,8 +21,12 @@ constexpr int BMAX = 64;
 constexpr float MAGIC = 12582912.0f;
 constexpr int MAGIC_BITS = 0x4B400000;
 
-// Coefficients of the ln(1 + rho) polynomial of the linear-velocity delta formulation:
-// 12 terms for compact tiles, 20 for wide ones (chosen per launch from the tile's rho bound).
+// Coefficients of the ln(1 + rho) polynomial of the linear-velocity delta formulation: the
+// shortest length of LP_TERMS whose fit meets the error budget over the tile's rho bound
+// (6 terms for compact tiles of a fine grid, up to 20 for wide ones).  LP_SHORT is the length
+// used where no polynomial is evaluated and the reference length for tile choice.
+constexpr int LP_TERMS[] = {6, 8, 10, 12, 20};
+constexpr int N_LP_TERMS = 5;
 constexpr int LP_SHORT = 12;
 constexpr int LP_LONG = 20;
 
@@ -51,7 +55,7 @@ struct GeomParams {
     float lp[LP_LONG];       // ln(1 + rho) = rho (1 + rho Q(t)), t = rho lp_s + lp_o,
                              // Q(t) = sum_j lp[j + 1] t^j (Chebyshev-node fit in t on [-1, 1])
     float lp_s, lp_o;
-    int lp_terms;            // LP_SHORT or LP_LONG
+    int lp_terms;            // one of LP_TERMS; lp[lp_terms..LP_LONG-1] are zero
     float rho_max;           // |rho| bound the polynomial was fitted for
     float C1, C1lo;          // tau - tau_ref = L * (C1 + C1lo) with L = R_s + R_r (constant v,
                              // tau_ref = -t0/dt) or ln(U/U_c) (linear v); C1lo = FP32 rounding
@@ -111,8 +115,8 @@ struct BatchJob {
 
 // The persistent kernel over `n_items` work items (job, tile, bin, -) taken in list order from
 // the counter `*next` (zeroed before the launch).  `g_max` sizes the shared-memory ring (its
-// nt is the largest of the jobs'); vel_kind/weight/fast/lp_terms/trace dtype are common to all
-// jobs.  `ctas` <= 0 launches nothing: it sets the kernel's shared-memory attribute and returns
+// nt is the largest of the jobs'); vel_kind/weight/fast/lp_terms/trace dtype are common to
+// all jobs of the launch.  `ctas` <= 0 launches nothing: it sets the kernel's shared-memory attribute and returns
 // the occupancy-sized grid through `ctas_out` (call it once before launching with that grid).
 cudaError_t launch_migrate_batched(const GeomParams& g_max, const BatchJob* jobs, const int4* items,
                                    int n_items, int* next, int vel_kind, int weight, int fast,

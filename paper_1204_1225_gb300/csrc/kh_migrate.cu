@@ -1,15 +1,17 @@
-// Migration, batched-migration and velocity-gradient launches: dispatch on the trace type to the per-type
-// translation units (kh_migrate_f32.cu, kh_migrate_f16.cu), and the gradient's final sum.
+// Migration, batched-migration and velocity-gradient launches: dispatch on the trace type to
+// the per-type translation units (kh_migrate_<type>.cu, kh_batched_<type>.cu), the gradient
+// kernels (FP32 traces only, instantiated here) and the gradient's final sum.
 #include "kh_migrate_impl.cuh"
 
 namespace kh {
 
-cudaError_t launch_dtype_f32(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int,
-                             int, const WaitCfg&, double*, cudaStream_t);
-cudaError_t launch_dtype_f16(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int,
-                             int, const WaitCfg&, double*, cudaStream_t);
-cudaError_t launch_dtype_bf16(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int,
-                              int, const WaitCfg&, double*, cudaStream_t);
+#define KH_MIGRATE_DECL(name)                                                                            \
+    cudaError_t name(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int, int,     \
+                     const WaitCfg&, cudaStream_t);
+KH_MIGRATE_DECL(launch_migrate_f32)
+KH_MIGRATE_DECL(launch_migrate_f16)
+KH_MIGRATE_DECL(launch_migrate_bf16)
+#undef KH_MIGRATE_DECL
 
 #define KH_BATCHED_DECL(name)                                                                            \
     cudaError_t name(const GeomParams&, const BatchJob*, const int4*, int, int*, int, int, int, int,          \
@@ -46,10 +48,27 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
 {
     if (t.cz > MAX_ZG) return cudaErrorInvalidValue;
     switch (g.tdtype) {
-        case KH_F32: return launch_dtype_f32(g, t, tr, traces, image, vel_kind, fast_math, w, nullptr, s);
-        case KH_F16: return launch_dtype_f16(g, t, tr, traces, image, vel_kind, fast_math, w, nullptr, s);
-        case KH_BF16:
-            return launch_dtype_bf16(g, t, tr, traces, image, vel_kind, fast_math, w, nullptr, s);
+        case KH_F32: return launch_migrate_f32(g, t, tr, traces, image, vel_kind, fast_math, w, s);
+        case KH_F16: return launch_migrate_f16(g, t, tr, traces, image, vel_kind, fast_math, w, s);
+        case KH_BF16: return launch_migrate_bf16(g, t, tr, traces, image, vel_kind, fast_math, w, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t launch_vgrad_impl(const GeomParams& g, const TileShape& t, const TraceSet& tr,
+                                     const float* traces, const float* image, int vel, int fast, const WaitCfg& w,
+                                     double* partial, cudaStream_t s)
+{
+    const int key = vel * 4 + g.weight * 2 + (fast ? 1 : 0);
+    switch (key) {
+        case 0: return launch_vgrad_t<VK_CONST, 0, false>(g, t, tr, traces, image, w, partial, s);
+        case 1: return launch_vgrad_t<VK_CONST, 0, true>(g, t, tr, traces, image, w, partial, s);
+        case 2: return launch_vgrad_t<VK_CONST, 1, false>(g, t, tr, traces, image, w, partial, s);
+        case 3: return launch_vgrad_t<VK_CONST, 1, true>(g, t, tr, traces, image, w, partial, s);
+        case 4: return launch_vgrad_t<VK_LINEAR, 0, false>(g, t, tr, traces, image, w, partial, s);
+        case 5: return launch_vgrad_t<VK_LINEAR, 0, true>(g, t, tr, traces, image, w, partial, s);
+        case 6: return launch_vgrad_t<VK_LINEAR, 1, false>(g, t, tr, traces, image, w, partial, s);
+        case 7: return launch_vgrad_t<VK_LINEAR, 1, true>(g, t, tr, traces, image, w, partial, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -59,9 +78,9 @@ cudaError_t launch_vgrad(const GeomParams& g, const TileShape& t, const TraceSet
                          const WaitCfg& w, double* partial, cudaStream_t s)
 {
     if (t.cz > MAX_ZG || !partial) return cudaErrorInvalidValue;
-    if (g.tdtype != KH_F32) return cudaErrorInvalidValue;
-    return launch_dtype_f32(g, t, tr, traces, const_cast<float*>(image), vel_kind, fast_math, w,
-                               partial, s);
+    if (g.tdtype != KH_F32 || vel_kind == VK_TABLE) return cudaErrorInvalidValue;
+    return launch_vgrad_impl(g, t, tr, static_cast<const float*>(traces), image, vel_kind, fast_math, w, partial,
+                             s);
 }
 
 // out[0..1] = (sum of the per-warp partials, in index order) / dt: one CTA, fixed order.

@@ -1,35 +1,11 @@
-// FP16- and BF16-trace instantiations of the migration and batched kernels (mixed precision: 16-bit
-// trace storage in HBM and shared memory, FP32 interpolation and accumulation).
+// FP16-trace instantiations of the migration kernel (mixed precision: 16-bit trace storage
+// in HBM and shared memory, FP32 interpolation and accumulation).
 #include "kh_migrate_impl.cuh"
 
 namespace kh {
-cudaError_t launch_dtype_f16(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
-                             float* image, int vel, int fast, const WaitCfg& w, double* partial,
-                             cudaStream_t s)
+cudaError_t launch_migrate_f16(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
+                              float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
-    return launch_dtype<__half>(g, t, tr, traces, image, vel, fast, w, partial, s);
-}
-
-cudaError_t launch_dtype_bf16(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
-                              float* image, int vel, int fast, const WaitCfg& w, double* partial,
-                              cudaStream_t s)
-{
-    return launch_dtype<__nv_bfloat16>(g, t, tr, traces, image, vel, fast, w, partial, s);
-}
-
-cudaError_t launch_batched_f16(const GeomParams& gm, const BatchJob* jobs, const int4* items, int n_items,
-                               int* next, int vel, int weight, int fast, int lp_terms, const WaitCfg& w,
-                               int ctas, int* ctas_out, cudaStream_t s)
-{
-    return launch_batched_dtype<__half>(gm, jobs, items, n_items, next, vel, weight, fast, lp_terms, w, ctas,
-                                        ctas_out, s);
-}
-
-cudaError_t launch_batched_bf16(const GeomParams& gm, const BatchJob* jobs, const int4* items, int n_items,
-                                int* next, int vel, int weight, int fast, int lp_terms, const WaitCfg& w,
-                                int ctas, int* ctas_out, cudaStream_t s)
-{
-    return launch_batched_dtype<__nv_bfloat16>(gm, jobs, items, n_items, next, vel, weight, fast, lp_terms, w,
-                                               ctas, ctas_out, s);
+    return launch_migrate_dtype<__half>(g, t, tr, traces, image, vel, fast, w, s);
 }
 }  // namespace kh

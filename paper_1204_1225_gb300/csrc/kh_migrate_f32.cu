@@ -1,19 +1,10 @@
-// FP32-trace instantiations of the migration, velocity-gradient and batched kernels.
+// FP32-trace instantiations of the migration kernel.
 #include "kh_migrate_impl.cuh"
 
 namespace kh {
-cudaError_t launch_dtype_f32(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
-                             float* image, int vel, int fast, const WaitCfg& w, double* partial,
-                             cudaStream_t s)
+cudaError_t launch_migrate_f32(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
+                              float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
-    return launch_dtype<float>(g, t, tr, traces, image, vel, fast, w, partial, s);
-}
-
-cudaError_t launch_batched_f32(const GeomParams& gm, const BatchJob* jobs, const int4* items, int n_items,
-                               int* next, int vel, int weight, int fast, int lp_terms, const WaitCfg& w,
-                               int ctas, int* ctas_out, cudaStream_t s)
-{
-    return launch_batched_dtype<float>(gm, jobs, items, n_items, next, vel, weight, fast, lp_terms, w, ctas,
-                                       ctas_out, s);
+    return launch_migrate_dtype<float>(g, t, tr, traces, image, vel, fast, w, s);
 }
 }  // namespace kh

@@ -612,70 +612,105 @@ __global__ void __launch_bounds__(THREADS, 2)
 }
 
 // ------------------------------------------------------------------ launch (per trace type)
+// ln(1 + rho) lengths instantiated for linear v(z): every length of LP_TERMS with the fast
+// (approximate) square root and reciprocal; 12 and 20 with the IEEE ones, where a shorter fit
+// runs in the 12-term kernel (its upper coefficients are zero, so Horner's rule returns the
+// same value bit for bit).  Calls f(std::integral_constant<int, L>()) for the length L.
+template <bool FAST, typename F>
+cudaError_t with_lp(int terms, F&& f)
+{
+    if constexpr (FAST) {
+        switch (terms) {
+            case 6: return f(std::integral_constant<int, 6>());
+            case 8: return f(std::integral_constant<int, 8>());
+            case 10: return f(std::integral_constant<int, 10>());
+            case 12: return f(std::integral_constant<int, 12>());
+            case 20: return f(std::integral_constant<int, 20>());
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        if (terms <= LP_SHORT) return f(std::integral_constant<int, LP_SHORT>());
+        if (terms <= LP_LONG) return f(std::integral_constant<int, LP_LONG>());
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <int VEL, int WGT, bool FAST, typename TT>
-static cudaError_t launch_t(const GeomParams& g, const TileShape& t, const TraceSet& tr,
-                            const void* traces, float* image, const WaitCfg& w, double* partial,
-                            cudaStream_t s)
+static cudaError_t launch_migrate_t(const GeomParams& g, const TileShape& t, const TraceSet& tr,
+                                   const void* traces, float* image, const WaitCfg& w, cudaStream_t s)
 {
     const size_t smem = mig_smem_bytes(g);
-    dim3 grid((unsigned)(t.tiles_x * t.tiles_y * t.tiles_z), (unsigned)g.n_bins);
-    cudaError_t e = cudaSuccess;
-    const bool lng = VEL == VK_LINEAR && g.lp_terms == LP_LONG;
-    if (partial == nullptr) {
-        auto kern = k_migrate<VEL, WGT, FAST, TT, LP_SHORT>;
-        if constexpr (VEL == VK_LINEAR)
-            if (lng) kern = k_migrate<VEL, WGT, FAST, TT, LP_LONG>;
-        if constexpr (VEL == VK_TABLE) {
-            if (g.tdt == KH_F16) kern = k_migrate<VEL, WGT, FAST, TT, LP_SHORT, __half>;
-            if (g.tdt == KH_U16) kern = k_migrate<VEL, WGT, FAST, TT, LP_SHORT, unsigned short>;
-        }
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const dim3 grid((unsigned)(t.tiles_x * t.tiles_y * t.tiles_z), (unsigned)g.n_bins);
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
                                          mig_cap(g.nt, g.elem_align), w);
-    } else if constexpr (std::is_same<TT, float>::value && VEL != VK_TABLE) {
-        auto kern = k_vgrad<VEL, WGT, FAST, TT, LP_SHORT>;
-        if constexpr (VEL == VK_LINEAR)
-            if (lng) kern = k_vgrad<VEL, WGT, FAST, TT, LP_LONG>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
-                                         mig_cap(g.nt, g.elem_align), w, partial);
+        return cudaGetLastError();
+    };
+    if constexpr (VEL == VK_LINEAR) {
+        return with_lp<FAST>(g.lp_terms,
+                             [&](auto L) { return go(k_migrate<VEL, WGT, FAST, TT, decltype(L)::value>); });
+    } else if constexpr (VEL == VK_TABLE) {
+        if (g.tdt == KH_F16) return go(k_migrate<VEL, WGT, FAST, TT, LP_SHORT, __half>);
+        if (g.tdt == KH_U16) return go(k_migrate<VEL, WGT, FAST, TT, LP_SHORT, unsigned short>);
+        return go(k_migrate<VEL, WGT, FAST, TT, LP_SHORT>);
     } else {
-        return cudaErrorInvalidValue;
+        return go(k_migrate<VEL, WGT, FAST, TT, LP_SHORT>);
     }
-    return cudaGetLastError();
 }
 
 template <typename TT>
-cudaError_t launch_dtype(const GeomParams& g, const TileShape& t, const TraceSet& tr,
-                         const void* traces, float* image, int vel, int fast, const WaitCfg& w,
-                         double* partial, cudaStream_t s)
+cudaError_t launch_migrate_dtype(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
+                                 float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
     const int key = vel * 4 + g.weight * 2 + (fast ? 1 : 0);
     switch (key) {
-        case 0: return launch_t<VK_CONST, 0, false, TT>(g, t, tr, traces, image, w, partial, s);
-        case 1: return launch_t<VK_CONST, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
-        case 2: return launch_t<VK_CONST, 1, false, TT>(g, t, tr, traces, image, w, partial, s);
-        case 3: return launch_t<VK_CONST, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
-        case 4: return launch_t<VK_LINEAR, 0, false, TT>(g, t, tr, traces, image, w, partial, s);
-        case 5: return launch_t<VK_LINEAR, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
-        case 6: return launch_t<VK_LINEAR, 1, false, TT>(g, t, tr, traces, image, w, partial, s);
-        case 7: return launch_t<VK_LINEAR, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
+        case 0: return launch_migrate_t<VK_CONST, 0, false, TT>(g, t, tr, traces, image, w, s);
+        case 1: return launch_migrate_t<VK_CONST, 0, true, TT>(g, t, tr, traces, image, w, s);
+        case 2: return launch_migrate_t<VK_CONST, 1, false, TT>(g, t, tr, traces, image, w, s);
+        case 3: return launch_migrate_t<VK_CONST, 1, true, TT>(g, t, tr, traces, image, w, s);
+        case 4: return launch_migrate_t<VK_LINEAR, 0, false, TT>(g, t, tr, traces, image, w, s);
+        case 5: return launch_migrate_t<VK_LINEAR, 0, true, TT>(g, t, tr, traces, image, w, s);
+        case 6: return launch_migrate_t<VK_LINEAR, 1, false, TT>(g, t, tr, traces, image, w, s);
+        case 7: return launch_migrate_t<VK_LINEAR, 1, true, TT>(g, t, tr, traces, image, w, s);
         case 8:
-        case 9: return launch_t<VK_TABLE, 0, true, TT>(g, t, tr, traces, image, w, partial, s);
+        case 9: return launch_migrate_t<VK_TABLE, 0, true, TT>(g, t, tr, traces, image, w, s);
         case 10:
-        case 11: return launch_t<VK_TABLE, 1, true, TT>(g, t, tr, traces, image, w, partial, s);
+        case 11: return launch_migrate_t<VK_TABLE, 1, true, TT>(g, t, tr, traces, image, w, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Gradient kernel (FP32 traces, analytic traveltimes only).
+template <int VEL, int WGT, bool FAST>
+static cudaError_t launch_vgrad_t(const GeomParams& g, const TileShape& t, const TraceSet& tr,
+                                 const float* traces, const float* image, const WaitCfg& w, double* partial,
+                                 cudaStream_t s)
+{
+    const size_t smem = mig_smem_bytes(g);
+    const dim3 grid((unsigned)(t.tiles_x * t.tiles_y * t.tiles_z), (unsigned)g.n_bins);
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, THREADS, smem, s>>>(g, t, tr, traces, image, mig_cap(g.nt, g.elem_align), w, partial);
+        return cudaGetLastError();
+    };
+    if constexpr (VEL == VK_LINEAR)
+        return with_lp<FAST>(g.lp_terms,
+                             [&](auto L) { return go(k_vgrad<VEL, WGT, FAST, float, decltype(L)::value>); });
+    else
+        return go(k_vgrad<VEL, WGT, FAST, float, LP_SHORT>);
 }
 
 // ------------------------------------------------------------------ batched persistent launch
 // One CTA per (SM, resident slot) loops over a work list of (job, tile, bin) items, longest
 // first, taking the next item from one global counter (a scheduler index, never image data).
 // Each item is the tile computation of k_migrate with the job's own geometry, tile shape,
-// headers, traces and image; the mbarrier ring and its phases persist across items.  A wait
-// that ran out anywhere in the launch (status word) stops every CTA at its next item.
+// headers, traces and image; the mbarrier ring and its phases persist across items.  All jobs
+// of one launch share the ln(1 + rho) fit length LPT (the host launches the jobs of each fit
+// length separately).  A wait that ran out anywhere in the launch (status word) stops
+// every CTA at its next item.
 template <int VEL, int WGT, bool FAST, typename TT, int LPT>
 __global__ void __launch_bounds__(THREADS, 2)
     k_migrate_batched(const BatchJob* __restrict__ jobs, const int4* __restrict__ items, int n_items,
@@ -732,26 +767,31 @@ static cudaError_t launch_batched_t(const GeomParams& gm, const BatchJob* jobs, 
                                    int n_items, int* next, int lp_terms, const WaitCfg& w, int ctas,
                                    int* ctas_out, cudaStream_t s)
 {
-    auto kern = k_migrate_batched<VEL, WGT, FAST, TT, LP_SHORT>;
-    if constexpr (VEL == VK_LINEAR)
-        if (lp_terms == LP_LONG) kern = k_migrate_batched<VEL, WGT, FAST, TT, LP_LONG>;
     const size_t smem = mig_smem_bytes(gm);
-    cudaError_t e;
-    if (ctas <= 0) {   // set-up only: shared-memory attribute and the occupancy-sized grid
-        int dev = 0, nsm = 0, occ = 0;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, smem)) != cudaSuccess)
-            return e;
-        ctas = nsm * (occ > 0 ? occ : 1);
-        if (ctas > n_items) ctas = n_items;
-        if (ctas_out) *ctas_out = ctas;
-        return cudaSuccess;
-    }
-    kern<<<ctas, THREADS, smem, s>>>(jobs, items, n_items, next, mig_cap(gm.nt, gm.elem_align), w);
-    return cudaGetLastError();
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e;
+        if (ctas <= 0) {   // set-up only: shared-memory attribute and the occupancy-sized grid
+            int dev = 0, nsm = 0, occ = 0;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return e;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, smem)) != cudaSuccess)
+                return e;
+            int c = nsm * (occ > 0 ? occ : 1);
+            if (c > n_items) c = n_items;
+            if (ctas_out) *ctas_out = c;
+            return cudaSuccess;
+        }
+        kern<<<ctas, THREADS, smem, s>>>(jobs, items, n_items, next, mig_cap(gm.nt, gm.elem_align), w);
+        return cudaGetLastError();
+    };
+    if constexpr (VEL == VK_LINEAR)
+        return with_lp<FAST>(lp_terms,
+                             [&](auto L) { return go(k_migrate_batched<VEL, WGT, FAST, TT, decltype(L)::value>); });
+    else
+        return go(k_migrate_batched<VEL, WGT, FAST, TT, LP_SHORT>);
 }
 
 template <typename TT>

@@ -250,8 +250,8 @@ static kh_status validate_desc(const kh_desc* d)
     }
     if (d->trace_dtype == KH_U16) return fail(KH_ERR_INVALID_ARG, "traces cannot be KH_U16");
     const int ealign = 16 / dtype_size(d->trace_dtype);
-    const int cap = std::max((d->nt + 3 * ealign) / ealign * ealign, 24576 / 4);
-    if ((size_t)kh::STAGES * cap * dtype_size(d->trace_dtype) > 200u * 1024u)
+    const int cap = std::max((d->nt + 3 * ealign) / ealign * ealign, 16384 / 4);
+    if ((size_t)kh::STAGES * cap * dtype_size(d->trace_dtype) > 160u * 1024u)
         return fail(KH_ERR_UNSUPPORTED, "nt = %d too long for the shared-memory trace ring", d->nt);
     return KH_OK;
 }
@@ -382,7 +382,11 @@ static kh_status prepare_linear(const kh_desc& d, const TileShape& t, GeomParams
     const double tol = std::max(5e-6 * g.kabs * d.dt, 1e-12);
     for (int i = 0; i < N_LP_TERMS; ++i) {
         g.lp_terms = LP_TERMS[i];
-        if (fit_log1p(std::expm1(-b), std::expm1(b), g.lp_terms, g.lp, &g.lp_s, &g.lp_o, tol)) return KH_OK;
+        if (fit_log1p(std::expm1(-b), std::expm1(b), g.lp_terms, g.lp, &g.lp_s, &g.lp_o, tol)) {
+            const double c1 = (double)g.C1 + (double)g.C1lo;
+            for (int j = 0; j < LP_LONG; ++j) g.lpc[j] = (float)(c1 * g.lp[j]);
+            return KH_OK;
+        }
     }
     return fail(KH_ERR_UNSUPPORTED, "tile too large for the v(z) delta evaluation (rho up to %.3f); "
                                     "choose a smaller tile with KH_OPT_TILE", std::expm1(b));

@@ -54,6 +54,7 @@ struct GeomParams {
     double a;                // k^2 / (2 v0): q = a R^2 / (v0 + k z)
     float lp[LP_LONG];       // ln(1 + rho) = rho (1 + rho Q(t)), t = rho lp_s + lp_o,
                              // Q(t) = sum_j lp[j + 1] t^j (Chebyshev-node fit in t on [-1, 1])
+    float lpc[LP_LONG];      // lp scaled by C1 + C1lo (the migration kernel forms tau from them)
     float lp_s, lp_o;
     int lp_terms;            // one of LP_TERMS; lp[lp_terms..LP_LONG-1] are zero
     float rho_max;           // |rho| bound the polynomial was fitted for

@@ -34,6 +34,8 @@ __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return
 
 constexpr int MAX_ZG = 16;          // z-groups per CTA (cz)
 constexpr int SLACK = 16;           // zeroed elements after the ring (reads one past a window)
+constexpr int LEAD = 16;            // zeroed elements before the ring (a window clipped at t0 may be
+                                    // indexed at -1 when tau is a rounding error below 0)
 
 struct __align__(16) MigSmem {
     uint64_t full[STAGES];
@@ -61,13 +63,13 @@ __host__ __device__ constexpr size_t mig_static_bytes() { return (sizeof(MigSmem
 __host__ __device__ inline int mig_cap(int nt, int ealign)
 {
     const int need = (nt + 2 * ealign + ealign - 1) / ealign * ealign;
-    const int base = 24576 / 4;
+    const int base = 16384 / 4;
     return need > base ? need : base;
 }
 
 __host__ __device__ inline size_t mig_ring_bytes(const GeomParams& g)
 {
-    return (((size_t)STAGES * mig_cap(g.nt, g.elem_align) + SLACK) * g.esize + 15) / 16 * 16;
+    return (((size_t)LEAD + STAGES * mig_cap(g.nt, g.elem_align) + SLACK) * g.esize + 15) / 16 * 16;
 }
 
 __host__ __device__ inline size_t table_bytes(const GeomParams& g)
@@ -77,7 +79,17 @@ __host__ __device__ inline size_t table_bytes(const GeomParams& g)
     return ((size_t)g.tnh * g.tnz * es + 15) / 16 * 16;
 }
 
-inline size_t mig_smem_bytes(const GeomParams& g) { return mig_static_bytes() + mig_ring_bytes(g) + table_bytes(g); }
+// Linear v(z): per consumer thread and depth, the cached source leg (rho_s, sqrt(q_s)) of the
+// current source position (see mig_consumer).
+__host__ __device__ inline size_t src_cache_bytes(const GeomParams& g)
+{
+    return (!g.table && g.kabs > 0.0) ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
+}
+
+inline size_t mig_smem_bytes(const GeomParams& g)
+{
+    return mig_static_bytes() + mig_ring_bytes(g) + table_bytes(g) + src_cache_bytes(g);
+}
 
 template <typename TB>
 __device__ __forceinline__ float tab_f32(TB v);
@@ -98,10 +110,29 @@ __device__ __forceinline__ float tab_bilerp(const TB* r, int tnz, int jz, float 
     return fmaf(fh, b - a, a);
 }
 
+// The migration kernel's sample read: th = tau - lo (window-relative sample position); valid
+// iff |th - cmid| <= chalf, i.e. 0 <= th <= hi - lo; linear interpolation between samples
+// floor(th) and floor(th) + 1 (adding 1.5 * 2^23 rounded down leaves floor(th) in the low
+// mantissa bits); invalid points read the zeros at zero_off.
+template <typename TT>
+__device__ __forceinline__ float sample_at(const TT* data, float th, int base, float cmid, float chalf,
+                                           int zero_off)
+{
+    const float tm = __fadd_rd(th, MAGIC);
+    const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
+    const bool ok = fabsf(th - cmid) <= chalf;
+    const int off = ok ? __float_as_int(tm) + base : zero_off;
+    const float d0 = to_f32<TT>(data[off]);
+    const float d1 = to_f32<TT>(data[off + 1]);
+    return fmaf(f, d1 - d0, d0);
+}
+
 // ------------------------------------------------------------------ producer warp
 // `n` is the number of stages this CTA's producer has filled before (mbarrier phases carry
 // over from one work item to the next in the persistent kernel); returns the new count.
-template <int VEL, typename TT>
+// FLOOR: the window-relative time is tau - lo (migration kernel, sample_at), else
+// tau - lo - 1/2 (gradient kernel, rounding to nearest).
+template <int VEL, typename TT, bool FLOOR>
 __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                                             const TraceSet& tr, const TT* __restrict__ traces, int tb,
                                             int te, const TileBox& box, const WaitCfg& wc, int n)
@@ -182,9 +213,10 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 S.mid[s][slot] = m;
                 S.tb[s][slot] = (float)(((double)lo + 0.5) * g.dtd + g.t0d);
                 const float lim = (float)(hi - lo);
-                S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo - 0.5)),
+                S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo - (FLOOR ? 0.0 : 0.5))),
                                            dst + (lo - lo_al) - MAGIC_BITS,
-                                           __float_as_int(0.5f * (lim - 1.f)), __float_as_int(0.5f * lim));
+                                           __float_as_int(FLOOR ? 0.5f * lim : 0.5f * (lim - 1.f)),
+                                           __float_as_int(0.5f * lim));
             }
             if (lane == 0 && bytes > 0) mbar_expect_tx(&S.full[s], (uint32_t)bytes);
             __syncwarp();
@@ -220,11 +252,16 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
 
 // ------------------------------------------------------------------ consumer warps
 // `n`: stages consumed before this tile (see mig_producer); returns the new count.
+//
+// Linear v(z): the source leg of a contribution depends only on the column and the source
+// position, and traces of one bin arrive shot by shot (the bin sort is stable), so each thread
+// keeps (rho_s, sqrt(q_s)) of its 16 depths for the current source in `srcc` (its own slots,
+// [i * CONSUMERS + tid]) and recomputes them only when the (warp-uniform) source changes.
 template <int VEL, int WGT, bool FAST, typename TT, int LPT, typename TB>
 __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const GeomParams& g,
                                             const TileShape& ts, int x0, int y0, int z0,
                                             const TileBox& box, int bin, float* __restrict__ image,
-                                            const WaitCfg& wc, const TB* tab, int n)
+                                            const WaitCfg& wc, const TB* tab, float2* srcc, int n)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
@@ -235,12 +272,14 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
     const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
     const float4* zc = &S.zc[tzg * NZ];
-    const float* zq = &S.z2[tzg * NZ];
+    const float* zg = &S.z2[tzg * NZ];   // linear: gamma(z) of the weight
     const int zero_off = (int)(((const char*)S.zero - (const char*)data) / (int)sizeof(TT));
 
     float acc[NZ];
 #pragma unroll
     for (int i = 0; i < NZ; ++i) acc[i] = 0.f;
+    float2* my_src = srcc + tid;
+    unsigned psx = 0xffffffffu, psy = 0xffffffffu;   // source of the cached leg (NaN bits: none)
 
     bool failed = false;
     while (true) {
@@ -281,13 +320,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                     const float Ssum = tab_bilerp<TB>(rows, g.tnz, jz, c.y, fhs) +
                                        tab_bilerp<TB>(rowr, g.tnz, jz, c.y, fhr);
                     const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
-                    const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
-                    const bool ok = fabsf(th - cmid) <= chalf;
-                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float d0 = to_f32<TT>(data[off]);
-                    const float d1 = to_f32<TT>(data[off + 1]);
-                    const float val = fmaf(f, d1 - d0, d0);
+                    const float val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                     if constexpr (WGT == 1) {
                         const float Wt = c.z * (hsqrt<FAST>(dhs2 + c.w) + hsqrt<FAST>(dhr2 + c.w));
                         acc[i] = fmaf(Wt, val, acc[i]);
@@ -307,43 +340,43 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                     const float Rr = hsqrt<FAST>(dhr2 + c.x);
                     const float Ssum = Rs + Rr;
                     const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
-                    const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
-                    const bool ok = fabsf(th - cmid) <= chalf;
-                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float d0 = to_f32<TT>(data[off]);
-                    const float d1 = to_f32<TT>(data[off + 1]);
-                    const float val = fmaf(f, d1 - d0, d0);
+                    const float val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                     if constexpr (WGT == 1) acc[i] = fmaf(c.y * Ssum, val, acc[i]);
                     else acc[i] += val;
                 }
             } else {
-                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t], a = S.hda[s][t];
-                const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w}, rr{rrv.x, rrv.y, rrv.z, rrv.w};
-                const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
+                const float4 a = S.hda[s][t];
+                if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
+                    const float4 rsv = S.refs[s][t];
+                    const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w};
+                    const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
+                    const float exs = cxf - h.x, eys = cyf - h.y;
+                    const float dhs2 = fmaf(exs, exs, eys * eys);
+                    const float qc2s = rs.qc + 2.f;
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) {
+                        float sqs = 0.f;
+                        const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zc[i], rs, qc2s, sqs);
+                        my_src[i * CONSUMERS] = make_float2(rho_s, WGT == 1 ? zg[i] * sqs : 0.f);
+                    }
+                    psx = __float_as_uint(h.x);
+                    psy = __float_as_uint(h.y);
+                }
+                const float4 rrv = S.refr[s][t];
+                const LegRef rr{rrv.x, rrv.y, rrv.z, rrv.w};
                 const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
-                const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
-                const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
-                const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
+                const float exr = cxf - h.z, eyr = cyf - h.w;
+                const float dhr2 = fmaf(exr, exr, eyr * eyr);
+                const float qc2r = rr.qc + 2.f;
 #pragma unroll
                 for (int i = 0; i < NZ; ++i) {
-                    const float4 c4 = zc[i];
-                    const ZConst c{c4.x, c4.y, c4.z, c4.w};
-                    float sqs, sqr;
-                    const float z2i = zq[i];
-                    const float rho_s = leg_delta<WGT, FAST>(dPs, dhs2, z2i, c, rs, qc2s, sqs);
-                    const float rho_r = leg_delta<WGT, FAST>(dPr, dhr2, z2i, c, rr, qc2r, sqr);
-                    const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);   // U/U_c - 1
-                    const float L = log1p_poly<LPT>(rho, g);
-                    const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
-                    const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
-                    const bool ok = fabsf(th - cmid) <= chalf;
-                    const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float d0 = to_f32<TT>(data[off]);
-                    const float d1 = to_f32<TT>(data[off + 1]);
-                    const float val = fmaf(f, d1 - d0, d0);
-                    if constexpr (WGT == 1) acc[i] = fmaf(c.gamma * (sqs + sqr), val, acc[i]);
+                    float sqr = 0.f;
+                    const float2 sv = my_src[i * CONSUMERS];   // (rho_s, gamma sqrt(q_s))
+                    const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zc[i], rr, qc2r, sqr);
+                    const float rho = fmaf(sv.x, rho_r, sv.x + rho_r);   // U/U_c - 1
+                    const float th = tau_poly<LPT>(rho, g, c0rel);
+                    const float val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                    if constexpr (WGT == 1) acc[i] = fmaf(fmaf(zg[i], sqr, sv.y), val, acc[i]);
                     else acc[i] += val;
                 }
             }
@@ -517,14 +550,19 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
     }
 }
 
-// Per-z constants of a tile's depth range [z0, z0 + cz NZ), written by all threads.
-template <int VEL>
+// Per-z constants of a tile's depth range [z0, z0 + cz NZ), written by all threads.  Linear
+// v(z): MODE 0 (migration) stores z_constants_m and gamma, MODE 1 (gradient) ZConst and z^2.
+template <int VEL, int MODE>
 __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, const TileShape& ts, int z0,
                                              const TileBox& box)
 {
     for (int i = threadIdx.x; i < ts.cz * NZ; i += blockDim.x) {
         const double z = g.oz + (z0 + i) * g.dz;
-        if constexpr (VEL == VK_LINEAR) {
+        if constexpr (VEL == VK_LINEAR && MODE == 0) {
+            float gamma;
+            S.zc[i] = z_constants_m(z, box.cz, g, gamma);
+            S.z2[i] = gamma;
+        } else if constexpr (VEL == VK_LINEAR) {
             const ZConst c = z_constants(z, box.cz, g);
             S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
             S.z2[i] = (float)(z * z);
@@ -549,7 +587,8 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MigSmem& S = *reinterpret_cast<MigSmem*>(smem_raw);
-    TT* data = reinterpret_cast<TT*>(smem_raw + mig_static_bytes());
+    TT* ring = reinterpret_cast<TT*>(smem_raw + mig_static_bytes());
+    TT* data = ring + LEAD;
     __shared__ int s_abort;
     const int bin = blockIdx.y;
     int t = blockIdx.x;
@@ -571,12 +610,13 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
         fence_barrier_init();
     }
     // per-z constants of the tile and a zero-filled ring (edge reads stay finite)
-    tile_z_setup<VEL>(S, g, ts, z0, box);
+    tile_z_setup<VEL, MODE>(S, g, ts, z0, box);
     {
-        const int total = STAGES * cap + SLACK;
-        for (int i = threadIdx.x; i < total; i += blockDim.x) data[i] = TT(0.f);
+        const int total = LEAD + STAGES * cap + SLACK;
+        for (int i = threadIdx.x; i < total; i += blockDim.x) ring[i] = TT(0.f);
     }
     TB* tab = reinterpret_cast<TB*>(smem_raw + mig_static_bytes() + mig_ring_bytes(g));
+    float2* srcc = reinterpret_cast<float2*>(smem_raw + mig_static_bytes() + mig_ring_bytes(g));
     if constexpr (VEL == VK_TABLE) {
         const uint4* src = reinterpret_cast<const uint4*>(g.table);
         uint4* dst = reinterpret_cast<uint4*>(tab);
@@ -586,10 +626,10 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
     __syncthreads();
     if (s_abort) return;
     if (threadIdx.x >= CONSUMERS) {
-        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
-                              box, wc, 0);
+        mig_producer<VEL, TT, MODE == 0>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
+                                         box, wc, 0);
     } else if constexpr (MODE == 0) {
-        mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, 0);
+        mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, srcc, 0);
     } else {
         vg_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, partial, wc);
     }
@@ -714,11 +754,13 @@ static cudaError_t launch_vgrad_t(const GeomParams& g, const TileShape& t, const
 template <int VEL, int WGT, bool FAST, typename TT, int LPT>
 __global__ void __launch_bounds__(THREADS, 2)
     k_migrate_batched(const BatchJob* __restrict__ jobs, const int4* __restrict__ items, int n_items,
-                      int* __restrict__ next, int cap, WaitCfg wc)
+                      int* __restrict__ next, GeomParams g_ring, WaitCfg wc)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MigSmem& S = *reinterpret_cast<MigSmem*>(smem_raw);
-    TT* data = reinterpret_cast<TT*>(smem_raw + mig_static_bytes());
+    TT* ring = reinterpret_cast<TT*>(smem_raw + mig_static_bytes());
+    TT* data = ring + LEAD;
+    float2* srcc = reinterpret_cast<float2*>(smem_raw + mig_static_bytes() + mig_ring_bytes(g_ring));
     __shared__ int s_item;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -728,7 +770,8 @@ __global__ void __launch_bounds__(THREADS, 2)
         S.zero[0] = S.zero[1] = S.zero[2] = S.zero[3] = 0.f;
         fence_barrier_init();
     }
-    for (int i = threadIdx.x; i < STAGES * cap + SLACK; i += blockDim.x) data[i] = TT(0.f);
+    const int cap = mig_cap(g_ring.nt, g_ring.elem_align);
+    for (int i = threadIdx.x; i < LEAD + STAGES * cap + SLACK; i += blockDim.x) ring[i] = TT(0.f);
     int n = 0;   // stages filled (producer warp) or consumed (consumer warps) so far
     while (true) {
         __syncthreads();   // the previous item's per-z constants and s_item are no longer read
@@ -750,14 +793,14 @@ __global__ void __launch_bounds__(THREADS, 2)
         const int x0 = txi * ts.cx, y0 = tyi * ts.cy, z0 = tzi * ts.cz * NZ;
         const int bin = w.z;
         const TileBox box = tile_box(g, x0, y0, z0, ts.cx, ts.cy, ts.cz * NZ);
-        tile_z_setup<VEL>(S, g, ts, z0, box);
+        tile_z_setup<VEL, 0>(S, g, ts, z0, box);
         __syncthreads();
         if (threadIdx.x >= CONSUMERS) {
-            n = mig_producer<VEL, TT>(S, data, cap, g, tr, static_cast<const TT*>(jobs[w.x].traces),
+            n = mig_producer<VEL, TT, true>(S, data, cap, g, tr, static_cast<const TT*>(jobs[w.x].traces),
                                       tr.bin_start[bin], tr.bin_start[bin + 1], box, wc, n);
         } else {
             n = mig_consumer<VEL, WGT, FAST, TT, LPT, float>(S, data, g, ts, x0, y0, z0, box, bin,
-                                                             jobs[w.x].image, wc, nullptr, n);
+                                                             jobs[w.x].image, wc, nullptr, srcc, n);
         }
     }
 }
@@ -784,7 +827,7 @@ static cudaError_t launch_batched_t(const GeomParams& gm, const BatchJob* jobs, 
             if (ctas_out) *ctas_out = c;
             return cudaSuccess;
         }
-        kern<<<ctas, THREADS, smem, s>>>(jobs, items, n_items, next, mig_cap(gm.nt, gm.elem_align), w);
+        kern<<<ctas, THREADS, smem, s>>>(jobs, items, n_items, next, gm, w);
         return cudaGetLastError();
     };
     if constexpr (VEL == VK_LINEAR)

@@ -61,6 +61,18 @@ __device__ __forceinline__ ZConst z_constants(double z, double zc, const GeomPar
     return c;
 }
 
+// Per-z constants of the migration kernel's linear path, premultiplied by alpha(z):
+// (alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2), and gamma(z) for the weight.
+__device__ __forceinline__ float4 z_constants_m(double z, double zc, const GeomParams& g, float& gamma)
+{
+    const double vz = g.v0 + g.k * z;
+    const double alpha = g.a / vz;
+    const double kappa = -g.k * (z - zc) / (g.v0 + g.k * zc);
+    gamma = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale * sqrt(vz / g.a)) : 0.f;
+    return make_float4((float)alpha, (float)(alpha * kappa), (float)(alpha * (z - zc) * (z + zc)),
+                       (float)(alpha * z * z));
+}
+
 // ln(1 + rho) = rho (1 + rho Q), Q a polynomial in t = (rho - m)/h fitted on the tile's rho
 // interval [m - h, m + h] (coefficients g.lp[1..NT-1]).
 template <int NT>
@@ -71,6 +83,41 @@ __device__ __forceinline__ float log1p_poly(float rho, const GeomParams& g)
 #pragma unroll
     for (int i = NT - 2; i >= 1; --i) p = fmaf(p, t, g.lp[i]);
     return fmaf(rho, rho * p, rho);
+}
+
+// The migration kernel's window-relative time: tau - lo = C1 ln(1 + rho) + c0rel, formed as
+// rho (C1 + rho C1 Q(t)) + rho C1lo + c0rel with the C1-scaled coefficients g.lpc (the
+// rounding of C1 + rho C1 Q is that of ln(1 + rho) itself, scaled by C1).
+template <int NT>
+__device__ __forceinline__ float tau_poly(float rho, const GeomParams& g, float c0rel)
+{
+    const float t = fmaf(rho, g.lp_s, g.lp_o);
+    float p = g.lpc[NT - 1];
+#pragma unroll
+    for (int i = NT - 2; i >= 1; --i) p = fmaf(p, t, g.lpc[i]);
+    return fmaf(rho, fmaf(rho, p, g.C1), fmaf(rho, g.C1lo, c0rel));
+}
+
+// leg_delta with the migration kernel's premultiplied per-z constants
+// zk = (alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2):
+//     (q - q_c)/u_c = (alpha dP + alpha kappa R_c^2 + alpha (z^2 - z_c^2)) / u_c,
+//     q = alpha dh^2 + alpha z^2.
+template <int WGT, bool FAST>
+__device__ __forceinline__ float leg_delta_m(float dP, float dh2, const float4& zk, const LegRef& r, float qc2,
+                                             float& sq)
+{
+    const float dqi = r.iuc * fmaf(zk.x, dP, fmaf(zk.y, r.Rc2, zk.z));
+    const float q = fmaf(zk.x, dh2, zk.w);
+    float w;
+    if constexpr (WGT == 1) {
+        sq = hsqrt<FAST>(q);
+        w = sq * hsqrt<FAST>(q + 2.f);
+    } else {
+        sq = 0.f;
+        w = hsqrt<FAST>(q * (q + 2.f));
+    }
+    const float gq = fmaf(q + qc2, hrcp<FAST>(w + r.wc), 1.f);
+    return dqi * gq;
 }
 
 // One leg of the linear path: returns rho_leg = u/u_c - 1 and sqrt(q) (for the weight).

@@ -41,22 +41,48 @@ sys.path.insert(0, ROOT)
 
 from paper_1204_1225_gb300 import survey as sv  # noqa: E402
 
-# Hardware figures for the ALU roofline (GB300): SM count, MUFU (special-function) results
-# per SM per clock.  The MUFU rate is the figure measured on this part by the throughput
-# probe summarised in profiles/mufu_fma_throughput.md.
+# ALU roofline (GB300): thread instructions each SM can issue or execute per clock, per pipe
+# (dispatch: 4 sub-partitions x 32 lanes; FP32 FMA pipe 128; integer/logic ALU 64; MUFU
+# special-function unit 16, measured by the throughput probe in profiles/mufu_fma_throughput.md;
+# shared-memory load/store unit 32).  The migration kernel is a gather with no HBM bound
+# (about 4e-4 algorithmic bytes per contribution), so its roofline is the smallest of
+# N_SM x clock x lanes_p / n_p over these pipes, n_p = the kernel's executed thread
+# instructions per contribution on pipe p (ncu sm__inst_executed_pipe_*.sum x 32 and
+# smsp__thread_inst_executed.sum, divided by the contribution count).
 N_SM = 152
-MUFU_PER_SM_CLK = 16
-# Transcendental (MUFU) operations each contribution needs in the kernel's formulation:
-# constant v: the two ray lengths (2 sqrt); linear v(z): per leg sqrt(q) (weight only),
-# sqrt(q + 2) or sqrt(q (q + 2)), and the reciprocal of the cancellation-free w - w_c.
-MUFU_PER_CONTRIB = {("const", "one"): 2, ("const", "obliq"): 2, ("linear", "one"): 4,
-                    ("linear", "obliq"): 6}
+LANES_PER_SM_CLK = {"issue": 128, "fma": 128, "alu": 64, "xu": 16, "lsu": 32}
+# n_p per workload's kernel variant, from profiles/k_migrate_pipe_mix.md (one ncu capture of
+# k_migrate per variant; the 100k-trace 256^3 workload runs the variant measured on its
+# 10k-trace case: same grid, tile and 6-term fit).
+PIPE_MIX = {
+    "3d-vz-100k-256cube": {"issue": 43.16, "fma": 29.22, "alu": 4.82, "xu": 3.17, "lsu": 4.74},
+    "3d-vz-10k-256cube": {"issue": 43.16, "fma": 29.22, "alu": 4.82, "xu": 3.17, "lsu": 4.74},
+    "3d-vz-40k-128cube": {"issue": 48.37, "fma": 32.18, "alu": 6.85, "xu": 3.24, "lsu": 4.85},
+    "25d-vz-20k-512x400": {"issue": 47.59, "fma": 33.98, "alu": 5.26, "xu": 2.37, "lsu": 4.82},
+}
+
+
+# DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
+# (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
+TRAFFIC = {
+    "3d-vz-10k-256cube": 61331968 + 1029468160,
+    "3d-vz-40k-128cube": 145624000 + 94539500,
+    "25d-vz-20k-512x400": 48173300 + 315392,
+}
+
+
+def pipe_roofline(mix, clk_mhz: float):
+    """(bound name, contributions/s bound in G/s, all pipe bounds) for an instruction mix."""
+    bounds = {p: N_SM * LANES_PER_SM_CLK[p] * clk_mhz * 1e6 / n / 1e9 for p, n in mix.items()}
+    p = min(bounds, key=bounds.get)
+    return p, bounds[p], bounds
 
 
 def workloads():
     return {
         "3d-vz-100k-256cube": lambda: sv.survey_3d_gradient(),
         "3d-vz-40k-128cube": lambda: sv.survey_3d_gradient(ntr=40_000, n=128),
+        "3d-vz-10k-256cube": lambda: sv.survey_3d_gradient(ntr=10_000, n=256),
         "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
         "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
         "batch64-3d-vz": lambda: sv.survey_batch_3d(64),
@@ -324,18 +350,24 @@ def main():
 
     if rank != 0:
         return
-    # ALU roofline of the migration kernel: contributions/s that the MUFU pipe allows at
-    # the median SM clock of the timed region, given the transcendentals per contribution.
-    mufu = MUFU_PER_CONTRIB[(s.vel if s.k != 0 or s.vel == "const" else "const", s.weight)]
+    # ALU roofline of the migration kernel at the median SM clock of the timed region.
     clk_mhz = clocks.get("sm_mhz") or 2070.0
-    peak = N_SM * MUFU_PER_SM_CLK * clk_mhz * 1e6 / mufu / 1e9
     achieved = contrib / (kern_ms / max(kern_n, 1) / 1e3) / 1e9 if kern_n else None
-    roof = {"bound": "alu", "kernel": "k_migrate", "achieved": achieved, "peak": peak,
-            "unit": "Gcontrib/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": None,
-            "peak_basis": f"{N_SM} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {clk_mhz:.0f} MHz (median "
-                          f"SM clock of the timed region) / {mufu} MUFU ops per contribution",
+    mix = PIPE_MIX.get(args.workload) if args.trace_dtype == "f32" and args.fast_math else None
+    roof = {"bound": "alu", "kernel": "k_migrate", "achieved": achieved, "unit": "Gcontrib/s",
             "kernel_ms_per_launch": kern_ms / max(kern_n, 1)}
+    if mix:
+        pipe, peak, bounds = pipe_roofline(mix, clk_mhz)
+        roof.update({"peak": peak, "frac": (achieved / peak) if achieved else None,
+                     "binding_pipe": pipe, "pipe_bounds": {k: round(v, 1) for k, v in bounds.items()},
+                     "instructions_per_contribution": mix,
+                     "peak_basis": f"min over pipes of {N_SM} SMs x lanes/clk x {clk_mhz:.0f} MHz / "
+                                   "executed instructions per contribution (ncu, "
+                                   "profiles/k_migrate_pipe_mix.md)"})
+    else:
+        roof.update({"peak": None, "frac": None,
+                     "peak_basis": "no measured instruction mix for this kernel variant"})
+    roof["traffic"] = TRAFFIC.get(args.workload) if args.trace_dtype == "f32" else None
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(s, traces.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)
@@ -427,13 +459,15 @@ def run_batched(args, surveys, ws, rank, local):
     barrier(ws)
     if rank != 0:
         return
-    mufu = MUFU_PER_CONTRIB[("linear", "obliq")]
     clk_mhz = clocks.get("sm_mhz") or 2070.0
-    peak = N_SM * MUFU_PER_SM_CLK * clk_mhz * 1e6 / mufu / 1e9
+    mix = PIPE_MIX["3d-vz-40k-128cube"]
+    pipe, peak, bounds = pipe_roofline(mix, clk_mhz)
     roof = {"bound": "alu", "kernel": "k_migrate_batched", "achieved": value, "peak": peak,
-            "unit": "Gcontrib/s", "frac": value / peak, "traffic": None,
-            "peak_basis": f"{N_SM} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {clk_mhz:.0f} MHz / {mufu} "
-                          "MUFU ops per contribution; achieved over the whole graph replay"}
+            "unit": "Gcontrib/s", "frac": value / peak, "traffic": None, "binding_pipe": pipe,
+            "pipe_bounds": {k: round(v, 1) for k, v in bounds.items()},
+            "peak_basis": "instruction mix of the 8-term k_migrate variant (3d-vz-40k-128cube, the "
+                          "fit length most jobs use; approximate for the 6-12-term jobs); achieved "
+                          "over the whole graph replay"}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         s0, d0 = surveys[0], jobs[0][2]

@@ -201,11 +201,13 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 double tau_ref = (VEL == VK_TABLE) ? g.c0 + 0.5 : -g.t0d / g.dtd;
                 if constexpr (VEL == VK_LINEAR) {
                     LegRef rs, rr;
-                    const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs);
-                    const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr);
+                    float qis = 0.f, qir = 0.f;
+                    const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs, FLOOR ? &qis : nullptr);
+                    const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr, FLOOR ? &qir : nullptr);
                     tau_ref += (ls + lr) * inv_kdt;
-                    S.refs[s][slot] = make_float4(rs.Rc2, rs.qc, rs.wc, rs.iuc);
-                    S.refr[s][slot] = make_float4(rr.Rc2, rr.qc, rr.wc, rr.iuc);
+                    // migration kernel: (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c); gradient: LegRef
+                    S.refs[s][slot] = make_float4(rs.Rc2, FLOOR ? qis : rs.qc, rs.wc, rs.iuc);
+                    S.refr[s][slot] = make_float4(rr.Rc2, FLOOR ? qir : rr.qc, rr.wc, rr.iuc);
                     S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
                                                  (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
                 }
@@ -347,32 +349,28 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
             } else {
                 const float4 a = S.hda[s][t];
                 if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
-                    const float4 rsv = S.refs[s][t];
-                    const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w};
+                    const float4 rs = S.refs[s][t];
                     const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
                     const float exs = cxf - h.x, eys = cyf - h.y;
                     const float dhs2 = fmaf(exs, exs, eys * eys);
-                    const float qc2s = rs.qc + 2.f;
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         float sqs = 0.f;
-                        const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zc[i], rs, qc2s, sqs);
+                        const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zc[i], rs, sqs);
                         my_src[i * CONSUMERS] = make_float2(rho_s, WGT == 1 ? zg[i] * sqs : 0.f);
                     }
                     psx = __float_as_uint(h.x);
                     psy = __float_as_uint(h.y);
                 }
-                const float4 rrv = S.refr[s][t];
-                const LegRef rr{rrv.x, rrv.y, rrv.z, rrv.w};
+                const float4 rr = S.refr[s][t];
                 const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
                 const float exr = cxf - h.z, eyr = cyf - h.w;
                 const float dhr2 = fmaf(exr, exr, eyr * eyr);
-                const float qc2r = rr.qc + 2.f;
 #pragma unroll
                 for (int i = 0; i < NZ; ++i) {
                     float sqr = 0.f;
                     const float2 sv = my_src[i * CONSUMERS];   // (rho_s, gamma sqrt(q_s))
-                    const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zc[i], rr, qc2r, sqr);
+                    const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zc[i], rr, sqr);
                     const float rho = fmaf(sv.x, rho_r, sv.x + rho_r);   // U/U_c - 1
                     const float th = tau_poly<LPT>(rho, g, c0rel);
                     const float val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);

@@ -29,9 +29,10 @@ struct LegRef {
     float iuc;   // 1 / u_c
 };
 
-// FP64 reference of one leg: returns ln u_c and fills the FP32 copies.
+// FP64 reference of one leg: returns ln u_c and fills the FP32 copies (and, if qc2i is given,
+// the migration kernel's (q_c + 2)/u_c).
 __device__ __forceinline__ double leg_reference(double cx, double cy, double cz, double hx, double hy,
-                                                const GeomParams& g, LegRef& r)
+                                                const GeomParams& g, LegRef& r, float* qc2i = nullptr)
 {
     const double ex = cx - hx, ey = cy - hy;
     const double Rc2 = ex * ex + ey * ey + cz * cz;
@@ -41,6 +42,7 @@ __device__ __forceinline__ double leg_reference(double cx, double cy, double cz,
     r.qc = (float)qc;
     r.wc = (float)wc;
     r.iuc = (float)(1.0 / (1.0 + qc + wc));
+    if (qc2i) *qc2i = (float)((qc + 2.0) / (1.0 + qc + wc));
     return log1p(qc + wc);
 }
 
@@ -86,8 +88,9 @@ __device__ __forceinline__ float log1p_poly(float rho, const GeomParams& g)
 }
 
 // The migration kernel's window-relative time: tau - lo = C1 ln(1 + rho) + c0rel, formed as
-// rho (C1 + rho C1 Q(t)) + rho C1lo + c0rel with the C1-scaled coefficients g.lpc (the
-// rounding of C1 + rho C1 Q is that of ln(1 + rho) itself, scaled by C1).
+// rho (C1 + rho C1 Q(t)) + c0rel with the C1-scaled coefficients g.lpc.  The rounding of
+// C1 + rho C1 Q (half an ulp of C1, times |rho| <= rho_max) is that of ln(1 + rho) itself
+// scaled by C1; the FP32 rounding error C1lo of C1 is of the same size and is left out.
 template <int NT>
 __device__ __forceinline__ float tau_poly(float rho, const GeomParams& g, float c0rel)
 {
@@ -95,18 +98,18 @@ __device__ __forceinline__ float tau_poly(float rho, const GeomParams& g, float 
     float p = g.lpc[NT - 1];
 #pragma unroll
     for (int i = NT - 2; i >= 1; --i) p = fmaf(p, t, g.lpc[i]);
-    return fmaf(rho, fmaf(rho, p, g.C1), fmaf(rho, g.C1lo, c0rel));
+    return fmaf(rho, fmaf(rho, p, g.C1), c0rel);
 }
 
 // leg_delta with the migration kernel's premultiplied per-z constants
-// zk = (alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2):
-//     (q - q_c)/u_c = (alpha dP + alpha kappa R_c^2 + alpha (z^2 - z_c^2)) / u_c,
-//     q = alpha dh^2 + alpha z^2.
+// zk = (alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2) and per-trace reference
+// rm = (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c):
+//     q - q_c = alpha dP + alpha kappa R_c^2 + alpha (z^2 - z_c^2),   q = alpha dh^2 + alpha z^2,
+//     u/u_c - 1 = (q - q_c) (q/u_c + (q_c + 2)/u_c) / (w + w_c) + (q - q_c)/u_c.
 template <int WGT, bool FAST>
-__device__ __forceinline__ float leg_delta_m(float dP, float dh2, const float4& zk, const LegRef& r, float qc2,
-                                             float& sq)
+__device__ __forceinline__ float leg_delta_m(float dP, float dh2, const float4& zk, const float4& rm, float& sq)
 {
-    const float dqi = r.iuc * fmaf(zk.x, dP, fmaf(zk.y, r.Rc2, zk.z));
+    const float dq = fmaf(zk.x, dP, fmaf(zk.y, rm.x, zk.z));
     const float q = fmaf(zk.x, dh2, zk.w);
     float w;
     if constexpr (WGT == 1) {
@@ -116,8 +119,8 @@ __device__ __forceinline__ float leg_delta_m(float dP, float dh2, const float4& 
         sq = 0.f;
         w = hsqrt<FAST>(q * (q + 2.f));
     }
-    const float gq = fmaf(q + qc2, hrcp<FAST>(w + r.wc), 1.f);
-    return dqi * gq;
+    const float gi = fmaf(fmaf(q, rm.w, rm.y), hrcp<FAST>(w + rm.z), rm.w);
+    return dq * gi;
 }
 
 // One leg of the linear path: returns rho_leg = u/u_c - 1 and sqrt(q) (for the weight).

@@ -198,6 +198,20 @@ def synth_traces(s, plan, device):
                          device=device, chunk=1 << 23)
 
 
+def synth_batch_job(s, plan, j: int, device):
+    """Job j of the batch: 25 Hz Ricker arrivals from 3 seeded point scatterers inside the
+    job's volume (amplitude 1) plus white noise of sigma 0.1 drawn on the device."""
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    rng = np.random.default_rng(sv.BASE_SEED + 1000 + j)
+    w = s.nx * s.dx
+    sc = np.stack([rng.uniform(0.1 * w, 0.9 * w, 3), rng.uniform(0.1 * w, 0.9 * w, 3),
+                   rng.uniform(0.2 * w, 0.9 * w, 3), np.ones(3)], axis=1)
+    d = sv.synthesize(s, sc, kh.arrival_times_fn(plan), 25.0, noise_sigma=0.0, device=device,
+                      chunk=1 << 23)
+    g = torch.Generator(device=device).manual_seed(sv.BASE_SEED + j)
+    return d.add_(torch.randn(d.shape, generator=g, device=device), alpha=0.1)
+
+
 def cpu_baseline(s, traces_cpu, target_s: float, seed: int):
     """The FP64 oracle on a bounded sample of image points of the same workload."""
     import oracle
@@ -268,9 +282,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--trace-dtype", default="f32", choices=sorted(_TDT))
+    ap.add_argument("--vel", default="analytic", choices=["analytic", "table"],
+                    help="traveltimes: analytic v(z) formulas or the radial traveltime table")
+    ap.add_argument("--table-dtype", default="u16", choices=["f32", "f16", "u16"])
     ap.add_argument("--no-tune", action="store_true", help="batch: default tiles, no autotuning")
     ap.add_argument("--tile-cache", default=None, help="batch: autotuner JSON cache path")
     ap.add_argument("--no-loop", action="store_true", help="batch: skip the per-job loop arm")
+    ap.add_argument("--op", default="migrate", choices=["migrate", "demigrate", "vgrad"],
+                    help="operator timed: migration (Eq. 1), its adjoint, or the (v0, k) gradient")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -290,15 +309,28 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tdt = _TDT[args.trace_dtype]
-    plan = kh.Plan(s, fast_math=bool(args.fast_math), trace_dtype=tdt)
+    s_run = s.replace(vel="table") if args.vel == "table" else s
+    plan = kh.Plan(s_run, fast_math=bool(args.fast_math), trace_dtype=tdt, table_dtype=args.table_dtype)
     hdr = kh.Headers.of(s, device=dev)
-    traces = synth_traces(s, plan, dev).to(tdt).contiguous()
+    traces = synth_traces(s, kh.Plan(s), dev).to(tdt).contiguous()
     image = torch.empty(plan.image_shape, dtype=torch.float32, device=dev)
     contrib = plan.count(hdr)
     stream = torch.cuda.current_stream(dev)
+    if args.op != "migrate":
+        plan.migrate(hdr, traces, out=image)          # the adjoint and gradient read an image
+        d_out = torch.empty((s.ntr, s.nt), dtype=torch.float32, device=dev)
+        g_out = torch.empty(2, dtype=torch.float64, device=dev)
+
+    def step():
+        if args.op == "migrate":
+            plan.migrate(hdr, traces, out=image)
+        elif args.op == "demigrate":
+            plan.demigrate(hdr, image, out=d_out)
+        else:
+            plan.velocity_grad(hdr, image, traces, out=g_out)
 
     for _ in range(args.warmup):
-        plan.migrate(hdr, traces, out=image)
+        step()
     plan.sync()
     plan.profile(True)
     plan.profile_read()
@@ -309,7 +341,7 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            plan.migrate(hdr, traces, out=image)
+            step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
     plan.sync()
@@ -323,7 +355,7 @@ def main():
 
     # end to end through the public API: pinned host inputs in, image back to pinned host
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.op == "migrate":
         h_tr = traces.cpu().pin_memory()
         h_hdr = [t.cpu().pin_memory() for t in hdr.args()]
         h_img = torch.empty(plan.image_shape, dtype=torch.float32).pin_memory()
@@ -353,8 +385,11 @@ def main():
     # ALU roofline of the migration kernel at the median SM clock of the timed region.
     clk_mhz = clocks.get("sm_mhz") or 2070.0
     achieved = contrib / (kern_ms / max(kern_n, 1) / 1e3) / 1e9 if kern_n else None
-    mix = PIPE_MIX.get(args.workload) if args.trace_dtype == "f32" and args.fast_math else None
-    roof = {"bound": "alu", "kernel": "k_migrate", "achieved": achieved, "unit": "Gcontrib/s",
+    kname = {"migrate": "k_migrate", "demigrate": "k_demigrate", "vgrad": "k_vgrad"}[args.op]
+    mix_key = args.workload if args.op == "migrate" else f"{args.workload}-{args.op}"
+    mix = PIPE_MIX.get(mix_key) if (args.trace_dtype == "f32" and args.fast_math and
+                                    args.vel == "analytic") else None
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "unit": "Gcontrib/s",
             "kernel_ms_per_launch": kern_ms / max(kern_n, 1)}
     if mix:
         pipe, peak, bounds = pipe_roofline(mix, clk_mhz)
@@ -367,9 +402,9 @@ def main():
     else:
         roof.update({"peak": None, "frac": None,
                      "peak_basis": "no measured instruction mix for this kernel variant"})
-    roof["traffic"] = TRAFFIC.get(args.workload) if args.trace_dtype == "f32" else None
+    roof["traffic"] = TRAFFIC.get(mix_key) if (args.trace_dtype == "f32" and args.vel == "analytic") else None
     cpu = None
-    if not args.no_cpu_baseline and ws == 1:
+    if not args.no_cpu_baseline and ws == 1 and args.op == "migrate":
         cpu = cpu_baseline(s, traces.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)
     tbytes = traces.numel() * traces.element_size()
     line = {
@@ -377,10 +412,13 @@ def main():
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": s.name, "image": list(plan.image_shape), "ntr": s.ntr, "nt": s.nt,
+        "config": {"workload": s.name, "operator": args.op, "image": list(plan.image_shape),
+                   "ntr": s.ntr, "nt": s.nt,
                    "velocity": f"{s.vel} v0={s.v0} k={s.k}", "weight": s.weight,
                    "aperture_m": s.aperture, "contributions_per_step": contrib,
                    "fast_math": bool(args.fast_math), "trace_storage": args.trace_dtype,
+                   "traveltimes": "analytic" if args.vel == "analytic" else f"table ({args.table_dtype}, "
+                                  f"{s.table_spacing:g} m)",
                    "l2": "inputs larger than L2 (traces %.0f MB, image %.0f MB)" % (
                        tbytes / 1e6, image.numel() * 4 / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single"},
@@ -404,8 +442,7 @@ def run_batched(args, surveys, ws, rank, local):
     for j, s in enumerate(surveys):
         p = kh.Plan(s, fast_math=bool(args.fast_math), trace_dtype=tdt)
         h = kh.Headers.of(s, device=dev)
-        g = torch.Generator(device=dev).manual_seed(sv.BASE_SEED + j)
-        d = torch.randn((s.ntr, s.nt), generator=g, device=dev).to(tdt).contiguous()
+        d = synth_batch_job(s, kh.Plan(s), j, dev).to(tdt).contiguous()
         jobs.append((p, h, d, torch.empty(p.image_shape, dtype=torch.float32, device=dev)))
     contrib = sum(p.count(h) for (p, h, _, _) in jobs)
     t_tune = time.perf_counter()
@@ -460,14 +497,18 @@ def run_batched(args, surveys, ws, rank, local):
     if rank != 0:
         return
     clk_mhz = clocks.get("sm_mhz") or 2070.0
-    mix = PIPE_MIX["3d-vz-40k-128cube"]
-    pipe, peak, bounds = pipe_roofline(mix, clk_mhz)
-    roof = {"bound": "alu", "kernel": "k_migrate_batched", "achieved": value, "peak": peak,
-            "unit": "Gcontrib/s", "frac": value / peak, "traffic": None, "binding_pipe": pipe,
-            "pipe_bounds": {k: round(v, 1) for k, v in bounds.items()},
-            "peak_basis": "instruction mix of the 8-term k_migrate variant (3d-vz-40k-128cube, the "
-                          "fit length most jobs use; approximate for the 6-12-term jobs); achieved "
-                          "over the whole graph replay"}
+    mix = PIPE_MIX.get(f"{args.workload}-{args.trace_dtype}")
+    roof = {"bound": "alu", "kernel": "k_migrate_batched", "achieved": value, "unit": "Gcontrib/s",
+            "traffic": None}
+    if mix:
+        pipe, peak, bounds = pipe_roofline(mix, clk_mhz)
+        roof.update({"peak": peak, "frac": value / peak, "binding_pipe": pipe,
+                     "pipe_bounds": {k: round(v, 1) for k, v in bounds.items()},
+                     "peak_basis": "min over pipes of the batched kernel's ncu-measured instruction "
+                                   "mix; achieved over the whole graph replay"})
+    else:
+        roof.update({"peak": None, "frac": None,
+                     "peak_basis": "no measured instruction mix for this kernel variant"})
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         s0, d0 = surveys[0], jobs[0][2]
@@ -479,9 +520,9 @@ def run_batched(args, surveys, ws, rank, local):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {len(surveys)} jobs, n^3 n~U{{64..192}}, "
-                               "N_tr~U{1000..50000}, nt~U{750..2000}, 3D v(z) 1500+0.5z, 16 bins, "
-                               "obliquity weight, Gaussian traces seeded per job",
+        "config": {"workload": f"{args.workload}: {len(surveys)} jobs, n^3 at 10 m, n~U{{64..192}}, "
+                               "N_tr~U{1000..50000}, nt~U{750..2000}, constant v 2000 m/s, W=1, full "
+                               "aperture, 8 bins, 3 Ricker scatterers + noise per job",
                    "contributions_per_step": contrib, "trace_storage": args.trace_dtype,
                    "work_items": info["items"], "ctas": info["ctas"], "tiles": tiles,
                    "autotune_s": round(t_tune, 2),

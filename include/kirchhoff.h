@@ -159,16 +159,17 @@ KH_API kh_status kirchhoff_count(kh_plan p, int ntr, const float* sx, const floa
 
 /* ---------------------------------------------------------------- batched persistent launch
  * Many independent migrations, each with its own plan (grid, bins, v(z), tile), headers,
- * traces and image, in ONE launch of a persistent kernel (two when the batch mixes jobs
- * whose v(z) tile fit needs 12 and 20 polynomial terms: one launch per length).  Each job computes Eq. (1) exactly
+ * traces and image, in ONE launch of a persistent kernel (one per ln(1 + rho) polynomial
+ * length when linear-v(z) jobs need different lengths).  Each job computes Eq. (1) exactly
  * as kirchhoff_migrate does with the same plan (bit-identical images: the same tile code,
  * traces in the same order).  A job list becomes a device work list of (job, image tile,
- * offset bin) items sorted by estimated cost, longest first (cost = tile points x traces of
- * the bin that pass the aperture cull of the tile); one CTA per SM slot takes items from a
- * single work counter (a scheduler index; no image value is accumulated in global memory).
- * This balances jobs of very different sizes (Eq. 2: work ~ N_xyz N_tr per job) across the
- * 152 SMs with no tail per job.  The paper distributes independent images over cluster
- * nodes; it has no single-GPU counterpart of this entry point. */
+ * offset bin) items: jobs by descending estimated cost, each job's bins in order, the items
+ * of a bin longest first (cost = tile points x traces of the bin that pass the aperture cull
+ * of the tile).  One CTA per SM slot takes items from a single work counter (a scheduler
+ * index; no image value is accumulated in global memory), so jobs of very different sizes
+ * (Eq. 2: work ~ N_xyz N_tr per job) share the 152 SMs with no launch gap or tail per job.
+ * The paper distributes independent images over cluster nodes; it has no single-GPU
+ * counterpart of this entry point. */
 
 /* One migration job of a batch. */
 typedef struct {

@@ -257,11 +257,14 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: cull read-back"));
 
-    // ---- work list: (job, tile, bin), estimated cost = points x (culled traces + 4); grouped
-    // by the job's fit length (shortest first), longest first within a group
+    // ---- work list: (job, tile, bin), estimated cost = points x (culled traces + 4).  Order:
+    // fit-length group (shortest first), then jobs by descending total cost, then bins, then
+    // longest item first.  Keeping a job's bin together keeps that bin's trace windows in L2
+    // while all CTAs work on it (as a per-job launch does); the smallest jobs form the tail.
     std::vector<int4> items(n_items);
     std::vector<double> cost(n_items);
     std::vector<int> cls(n_items);
+    std::vector<double> job_cost(njobs, 0.0);
     size_t k = 0;
     double work = 0.0;
     for (int j = 0; j < njobs; ++j) {
@@ -279,6 +282,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
                         items[k] = make_int4(j, tile, bin, 0);
                         cls[k] = lp_class(gs[j].lp_terms);
                         cost[k] = (double)cols * zs * (c + 4);
+                        job_cost[j] += cost[k];
                         work += (double)cols * zs * c;
                         ++k;
                     }
@@ -287,8 +291,19 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     }
     std::vector<int> order(n_items);
     std::iota(order.begin(), order.end(), 0);
+    std::vector<int> job_rank(njobs);
+    {
+        std::vector<int> jo(njobs);
+        std::iota(jo.begin(), jo.end(), 0);
+        std::stable_sort(jo.begin(), jo.end(), [&](int a, int c) { return job_cost[a] > job_cost[c]; });
+        for (int r = 0; r < njobs; ++r) job_rank[jo[r]] = r;
+    }
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-        return cls[a] != cls[c] ? cls[a] < cls[c] : cost[a] > cost[c];
+        if (cls[a] != cls[c]) return cls[a] < cls[c];
+        const int ja = job_rank[items[a].x], jc = job_rank[items[c].x];
+        if (ja != jc) return ja < jc;
+        if (items[a].z != items[c].z) return items[a].z < items[c].z;
+        return cost[a] > cost[c];
     });
     std::vector<int4> sorted(n_items);
     for (size_t i = 0; i < n_items; ++i) sorted[i] = items[order[i]];

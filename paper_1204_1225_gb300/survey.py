@@ -128,18 +128,26 @@ def survey_3d_gradient(ntr: int = 100_000, n: int = 256) -> Survey:
 
 
 def survey_batch_3d(n_jobs: int = 64, n_range=(64, 192), ntr_range=(1000, 50_000),
-                    nt_range=(750, 2000), seed: int = BASE_SEED) -> List[Survey]:
-    """Batch of independent 3D v(z) migrations of uneven size: job j draws, from a generator
-    seeded with seed + j, an image n^3 with n ~ U{n_range}, N_tr ~ U{ntr_range} traces and
-    nt ~ U{nt_range} samples, and is survey_3d_gradient(N_tr, n) with that nt (the image
-    always spans 3.2 km, so its spacing is 3200/n m)."""
+                    nt_range=(750, 2000), seed: int = BASE_SEED, h: float = 10.0) -> List[Survey]:
+    """Batch of independent 3D migrations of uneven size, each with the physics of the 2D
+    constant-velocity survey: v = 2000 m/s, W = 1, full aperture, 8 offset bins, 4 ms
+    sampling.  Job j draws, from a generator seeded with seed + j, an n^3 image at ``h`` m with
+    n ~ U{n_range}, N_tr ~ U{ntr_range} traces and nt ~ U{nt_range} samples; sources and
+    receivers are uniform over the image's surface footprint [0, n h)^2, and the bins split
+    [0, largest offset] into 8."""
     out = []
     for j in range(n_jobs):
         rng = np.random.default_rng(seed + j)
         n = int(rng.integers(n_range[0], n_range[1] + 1))
         ntr = int(rng.integers(ntr_range[0], ntr_range[1] + 1))
         nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
-        out.append(survey_3d_gradient(ntr, n).replace(nt=nt, name=f"3d-vz-{ntr}tr-{n}cube-{nt}nt"))
+        w = n * h
+        sx, sy, rx, ry = (_f32(rng.uniform(0.0, w, ntr)) for _ in range(4))
+        xmax = float(np.max(np.hypot(sx.astype(np.float64) - rx, sy.astype(np.float64) - ry)))
+        out.append(Survey(dim=3, nx=n, ny=n, nz=n, ox=0.0, oy=0.0, oz=0.0, dx=h, dy=h, dz=h,
+                          n_bins=8, bin_width=xmax / 8.0 * (1.0 + 1e-9), vel="const", v0=2000.0,
+                          k=0.0, weight="one", r0=1000.0, aperture=0.0, nt=nt, t0=0.0, dt=0.004,
+                          sx=sx, sy=sy, rx=rx, ry=ry, name=f"3d-const-{ntr}tr-{n}cube-{nt}nt"))
     return out
 
 

@@ -1,6 +1,8 @@
 """Tile autotuner host logic (no GPU): bucket keys and the JSON cache."""
 import json
 
+import numpy as np
+
 import torch
 
 from paper_1204_1225_gb300.autotune import CANDIDATES, TileTuner, bucket_key
@@ -47,4 +49,8 @@ def test_batch_generator_is_seeded_and_in_range():
     assert [(j.nx, j.ntr, j.nt) for j in a] == [(j.nx, j.ntr, j.nt) for j in b]
     for j in survey_batch_3d(64):
         assert 64 <= j.nx <= 192 and 1000 <= j.ntr <= 50_000 and 750 <= j.nt <= 2000
-        assert j.nx == j.ny == j.nz and abs(j.dx * j.nx - 3200.0) < 1e-6
+        assert j.nx == j.ny == j.nz and j.dx == 10.0 and j.vel == "const" and j.aperture == 0.0
+        w = j.nx * j.dx
+        assert 0 <= j.sx.min() and j.sx.max() < w and 0 <= j.ry.min() and j.ry.max() < w
+        off = np.hypot(j.sx.astype(np.float64) - j.rx, j.sy.astype(np.float64) - j.ry)
+        assert off.max() < j.n_bins * j.bin_width

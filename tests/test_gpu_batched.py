@@ -157,3 +157,20 @@ def test_autotuner_picks_a_runnable_tile_and_caches(tmp_path):
     # the tuned plan still computes the same image as a plan given that tile directly
     q = kh.Plan(s, tile=tile)
     assert torch.equal(p.migrate(h, d), q.migrate(h, d))
+
+
+def test_batched_constant_velocity_jobs_from_the_batch_generator():
+    """The batch workload's own job recipe (constant v, W = 1, full aperture, 8 bins,
+    random sources and receivers over the footprint) at small sizes."""
+    from paper_1204_1225_gb300.survey import survey_batch_3d
+    specs = survey_batch_3d(5, n_range=(17, 40), ntr_range=(50, 400), nt_range=(300, 520))
+    jobs = [_job(s, BASE_SEED + 40 + i) for i, s in enumerate(specs)]
+    b = kh.Batch(jobs)
+    b.run()
+    b.sync()
+    for (p, h, d, img), r in zip(jobs, _per_job(jobs)):
+        assert torch.equal(img, r)
+    s, (p, h, d, img) = specs[0], jobs[0]
+    err = rel_l2(img.cpu(), oracle.migrate(s, d.cpu().numpy()))
+    print(f"{s.name}: rel L2 vs oracle {err:.2e}")
+    assert err < FP32_REL_L2

@@ -22,6 +22,8 @@ def test_16bit_traces(name, dtype):
     got, _ = gpu_migrate(s, d, trace_dtype=dtype)
     same_algorithm = oracle.migrate(s, quantize(d, dtype))
     exact = oracle.migrate(s, d)
-    assert rel_l2(got, same_algorithm) < FP32_REL_L2
+    e_same = rel_l2(got, same_algorithm)
     err = rel_l2(got, exact)
+    print(f"{name} {dtype}: vs same-algorithm oracle {e_same:.2e}, vs FP32-data oracle {err:.2e}")
+    assert e_same < FP32_REL_L2
     assert err < MIXED_REL_L2, err

@@ -120,9 +120,18 @@ static void traveltime(const ko_desc* d, double R, double z, double* T, double* 
 
 /* Table traveltime (vel 2): the model v(z) = v0 + k z depends on depth only, so the time
  * from a surface point to (h, z) (h = horizontal distance) is one function T(h, z).  It is
- * tabulated at nodes h_i = i D, z_j = z_a + j D (D = table_spacing, z_a = D floor(z_min / D)
- * with z_min the shallowest image depth) with the closed form, and read by bilinear
- * interpolation in (h, z). */
+ * tabulated with the closed form at nodes h_i = i D (D = table_spacing) and, in depth, on
+ * image depths: z_j = z_min + j D_z with z_min the shallowest image depth and D_z = m |dz|,
+ * m the largest power of two not above min(4, D / |dz|) (at least 1), so the depth spacing
+ * never exceeds D; it is read by bilinear interpolation in (h, z). */
+static double table_dz(const ko_desc* d)
+{
+    const double r = d->table_spacing / fabs(d->dz);
+    double m = 1.0;
+    while (m < 4.0 && 2.0 * m <= r) m *= 2.0;
+    return m * fabs(d->dz);
+}
+
 static double table_node(const ko_desc* d, double h, double z)
 {
     ko_desc m = *d;
@@ -134,13 +143,12 @@ static double table_node(const ko_desc* d, double h, double z)
 
 static double table_traveltime(const ko_desc* d, double h, double z)
 {
-    const double D = d->table_spacing;
-    const double zmin = (d->dz >= 0) ? d->oz : d->oz + (d->nz - 1) * d->dz;
-    const double za = D * floor(zmin / D);
-    const double uh = h / D, uz = (z - za) / D;
+    const double D = d->table_spacing, Dz = table_dz(d);
+    const double za = (d->dz >= 0) ? d->oz : d->oz + (d->nz - 1) * d->dz;
+    const double uh = h / D, uz = (z - za) / Dz;
     const double ih = floor(uh), jz = floor(uz);
     const double fh = uh - ih, fz = uz - jz;
-    const double h0 = ih * D, h1 = (ih + 1.0) * D, z0 = za + jz * D, z1 = za + (jz + 1.0) * D;
+    const double h0 = ih * D, h1 = (ih + 1.0) * D, z0 = za + jz * Dz, z1 = za + (jz + 1.0) * Dz;
     const double a = (1.0 - fz) * table_node(d, h0, z0) + fz * table_node(d, h0, z1);
     const double b = (1.0 - fz) * table_node(d, h1, z0) + fz * table_node(d, h1, z1);
     return (1.0 - fh) * a + fh * b;

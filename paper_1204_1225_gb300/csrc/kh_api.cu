@@ -574,13 +574,13 @@ __global__ void k_hmax(int ntr, const float* __restrict__ sx, const float* __res
 }
 
 // FP64 closed-form node values T(i D, z_a + j D), nodes [nh][nz] with z fastest.
-__global__ void k_table_nodes(int nh, int nz, double D, double za, int vel, double v0, double k,
+__global__ void k_table_nodes(int nh, int nz, double D, double za, double Dz, int vel, double v0, double k,
                               double* __restrict__ T)
 {
     const long long n = (long long)nh * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double h = (double)(i / nz) * D, z = za + (double)(i % nz) * D;
+        const double h = (double)(i / nz) * D, z = za + (double)(i % nz) * Dz;
         T[i] = tt_exact(sqrt(h * h + z * z), z, vel, v0, k);
     }
 }
@@ -628,8 +628,13 @@ __global__ void k_table_store(long long n, const double* __restrict__ T, int dt,
 
 // Builds (or reuses) the radial table for this call's traces and fills the table fields of
 // g, including the scale and offset folded into C1 and c0.  Synchronises the stream.
+// The radial table of the plan's v(z) model: nodes at h = i D and at image depths
+// z = z_min + j m dz (m the largest power of two <= min(4, D / dz)), enough of them for every
+// depth of every tile (the padded depth range tiles_z * cz * 16), built in FP64 and stored as
+// F32, FP16 of T - T_min or U16 fixed point.  The h extent comes from the headers (one
+// synchronisation), so a table migrate call synchronises the stream.
 static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const float* sy, const float* rx,
-                              const float* ry, cudaStream_t s, GeomParams& g)
+                              const float* ry, cudaStream_t s, const TileShape& tile, GeomParams& g)
 {
     const kh_desc& d = p->d;
     cudaError_t e = cudaSuccess;
@@ -654,9 +659,11 @@ static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const floa
     std::memcpy(&hmax, &hb, sizeof hmax);
     const double D = d.table_spacing;
     const double zmin = std::min(d.oz, d.oz + (d.nz - 1) * d.dz), zmax = std::max(d.oz, d.oz + (d.nz - 1) * d.dz);
-    const double za = D * std::floor(zmin / D);
+    int m = 1;
+    while (m < 4 && 2.0 * m <= D / d.dz) m *= 2;
+    const double za = d.oz, Dz = m * d.dz;
     const int nh = (int)std::floor(hmax * (1.0 + 1e-6) / D) + 3;
-    const int nz = (int)std::floor((zmax - za) / D) + 3;
+    const int nz = tile.tiles_z * tile.cz * NZ / m + 2;
     const size_t es = d.table_dtype == KH_F32 ? 4 : 2;
     const size_t bytes = ((size_t)nh * nz * es + 15) / 16 * 16;
     if (bytes > 96u * 1024u)
@@ -668,7 +675,7 @@ static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const floa
         if ((e = grow(p->ws_tab, p->cap_tab, bytes)) != cudaSuccess) return cuda_fail(e, "workspace (table)");
         const int vel = d.k == 0.0 ? VK_CONST : VK_LINEAR;
         const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
-        k_table_nodes<<<blocks, 256, 0, s>>>(nh, nz, D, za, vel, d.v0, d.k, p->ws_tab64);
+        k_table_nodes<<<blocks, 256, 0, s>>>(nh, nz, D, za, Dz, vel, d.v0, d.k, p->ws_tab64);
         k_table_minmax<<<1, 256, 0, s>>>(n, p->ws_tab64, p->ws_tmm);
         p->launches += 2;
         double mm[2] = {0.0, 0.0};
@@ -698,6 +705,7 @@ static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const floa
     g.thmax = (float)(g.tnh - 1) - 1e-3f;
     g.tza = za;
     g.tsp = D;
+    g.tm = m;
     const double vmin = std::min(d.v0 + d.k * std::min(0.0, zmin), d.v0 + d.k * std::max(0.0, zmax));
     g.tslack = (float)(2.0 * D / (vmin * d.dt) + 2.0);
     const double c1 = p->tab_scale / d.dt;
@@ -864,7 +872,7 @@ kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy
     if ((st = prepare_linear(p->d, tile, g)) != KH_OK) return st;
     int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
     if (p->d.vel == KH_VEL_TABLE) {
-        if ((st = ensure_table(p, ntr, sx, sy, rx, ry, s, g)) != KH_OK) return st;
+        if ((st = ensure_table(p, ntr, sx, sy, rx, ry, s, tile, g)) != KH_OK) return st;
         vk = VK_TABLE;
     }
     TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};

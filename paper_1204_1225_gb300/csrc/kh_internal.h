@@ -68,7 +68,8 @@ struct GeomParams {
     int tdt;                 // storage kh_dtype: KH_F32, KH_F16, KH_U16
     float tinv;              // 1 / table_spacing
     float thmax;             // largest usable h coordinate (tnh - 1 - 1e-3)
-    double tza, tsp;         // first z node, spacing
+    double tza, tsp;         // first z node (the first image depth), h spacing
+    int tm;                  // depth nodes every tm image samples (1, 2 or 4)
     float tslack;            // extra window slack (samples) for the interpolation error
     float t0, dt;            // FP32 copies for the window bounds
     double t0d, dtd;         // exact values for the FP64 references

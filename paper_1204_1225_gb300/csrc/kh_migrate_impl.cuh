@@ -60,16 +60,18 @@ struct __align__(16) MigSmem {
 __host__ __device__ constexpr size_t mig_static_bytes() { return (sizeof(MigSmem) + 127) / 128 * 128; }
 
 // Elements of one stage's sample area: a full trace always fits, so every trace is stageable.
-__host__ __device__ inline int mig_cap(int nt, int ealign)
+// 16 KB per stage, 8 KB with a traveltime table (whose shared copy takes the difference).
+__host__ __device__ inline int mig_cap(const GeomParams& g)
 {
-    const int need = (nt + 2 * ealign + ealign - 1) / ealign * ealign;
-    const int base = 16384 / 4;
+    const int ealign = g.elem_align;
+    const int need = (g.nt + 2 * ealign + ealign - 1) / ealign * ealign;
+    const int base = (g.table ? 8192 : 16384) / g.esize;
     return need > base ? need : base;
 }
 
 __host__ __device__ inline size_t mig_ring_bytes(const GeomParams& g)
 {
-    return (((size_t)LEAD + STAGES * mig_cap(g.nt, g.elem_align) + SLACK) * g.esize + 15) / 16 * 16;
+    return (((size_t)LEAD + STAGES * mig_cap(g) + SLACK) * g.esize + 15) / 16 * 16;
 }
 
 __host__ __device__ inline size_t table_bytes(const GeomParams& g)
@@ -79,11 +81,12 @@ __host__ __device__ inline size_t table_bytes(const GeomParams& g)
     return ((size_t)g.tnh * g.tnz * es + 15) / 16 * 16;
 }
 
-// Linear v(z): per consumer thread and depth, the cached source leg (rho_s, sqrt(q_s)) of the
-// current source position (see mig_consumer).
+// Per consumer thread and depth, the cached source leg of the current source position (see
+// mig_consumer): (rho_s, gamma sqrt(q_s)) for linear v(z), T_s for the table.
 __host__ __device__ inline size_t src_cache_bytes(const GeomParams& g)
 {
-    return (!g.table && g.kabs > 0.0) ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
+    if (g.table) return (size_t)NZ * CONSUMERS * sizeof(float);
+    return g.kabs > 0.0 ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
 }
 
 inline size_t mig_smem_bytes(const GeomParams& g)
@@ -100,14 +103,31 @@ __device__ __forceinline__ float tab_f32<__half>(__half v) { return __half2float
 template <>
 __device__ __forceinline__ float tab_f32<unsigned short>(unsigned short v) { return (float)v; }
 
-// Bilinear read of the radial table at row pointer `r` (h row ih), depth node jz.
-template <typename TB>
-__device__ __forceinline__ float tab_bilerp(const TB* r, int tnz, int jz, float fz, float fh)
+// Radial table, step 1 (once per thread and trace leg): the table interpolated in h at the
+// horizontal distance sqrt(dh2), at the K depth nodes jb .. jb + K - 1 that span the thread's
+// 16 depths.
+template <typename TB, int K, bool FAST>
+__device__ __forceinline__ void tab_profile(const TB* tab, const GeomParams& g, float dh2, int jb, float* p)
 {
-    const float a0 = tab_f32<TB>(r[jz]), a1 = tab_f32<TB>(r[jz + 1]);
-    const float b0 = tab_f32<TB>(r[jz + tnz]), b1 = tab_f32<TB>(r[jz + tnz + 1]);
-    const float a = fmaf(fz, a1 - a0, a0), b = fmaf(fz, b1 - b0, b0);
-    return fmaf(fh, b - a, a);
+    const float u = fminf(hsqrt<FAST>(dh2) * g.tinv, g.thmax);
+    const int ih = (int)u;
+    const float fh = u - (float)ih;
+    const TB* r0 = tab + ih * g.tnz + jb;
+    const TB* r1 = r0 + g.tnz;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float a = tab_f32<TB>(r0[k]), b = tab_f32<TB>(r1[k]);
+        p[k] = fmaf(fh, b - a, a);
+    }
+}
+
+// Step 2 (per depth): depth nodes sit every M image samples from the thread's first depth,
+// so depth i lies in node interval i / M at fraction (i % M) / M, both compile-time.
+template <int M>
+__device__ __forceinline__ float tab_depth(const float* p, int i)
+{
+    const int j = i / M, r = i % M;
+    return r == 0 ? p[j] : fmaf((float)r * (1.f / M), p[j + 1] - p[j], p[j]);
 }
 
 // The migration kernel's sample read: th = tau - lo (window-relative sample position); valid
@@ -305,26 +325,34 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
             const float chalf = inside ? __int_as_float(w.w) : -1.f;
             const float4 h = S.hdr[s][t];
             if constexpr (VEL == VK_TABLE) {
+                // T_s + T_r in table units from the radial table; the source leg is cached
+                // per source position like the linear path's
+                constexpr int M = LPT;            // depth nodes every M samples (1, 2 or 4)
+                constexpr int K = NZ / M + 1;     // nodes spanning the thread's 16 depths
+                float* my_ts = reinterpret_cast<float*>(srcc) + tid;
+                const int jb = izb / M;
                 const float dxs = cxf - h.x, dys = cyf - h.y;
-                const float dxr = cxf - h.z, dyr = cyf - h.w;
                 const float dhs2 = fmaf(dxs, dxs, dys * dys);
+                if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
+                    float ps[K];
+                    tab_profile<TB, K, FAST>(tab, g, dhs2, jb, ps);
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) my_ts[i * CONSUMERS] = tab_depth<M>(ps, i);
+                    psx = __float_as_uint(h.x);
+                    psy = __float_as_uint(h.y);
+                }
+                const float dxr = cxf - h.z, dyr = cyf - h.w;
                 const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
-                const float us = fminf(hsqrt<FAST>(dhs2) * g.tinv, g.thmax);
-                const float ur = fminf(hsqrt<FAST>(dhr2) * g.tinv, g.thmax);
-                const int ihs = (int)us, ihr = (int)ur;
-                const float fhs = us - (float)ihs, fhr = ur - (float)ihr;
-                const TB* rows = tab + ihs * g.tnz;
-                const TB* rowr = tab + ihr * g.tnz;
+                float pr[K];
+                tab_profile<TB, K, FAST>(tab, g, dhr2, jb, pr);
 #pragma unroll
                 for (int i = 0; i < NZ; ++i) {
-                    const float4 c = zc[i];   // (jz bits, fz, w_z, z^2)
-                    const int jz = __float_as_int(c.x);
-                    const float Ssum = tab_bilerp<TB>(rows, g.tnz, jz, c.y, fhs) +
-                                       tab_bilerp<TB>(rowr, g.tnz, jz, c.y, fhr);
-                    const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
+                    const float4 c = zc[i];   // (w_z, z^2)
+                    const float Ssum = my_ts[i * CONSUMERS] + tab_depth<M>(pr, i);
+                    const float th = fmaf(Ssum, g.C1, c0rel);
                     const float val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                     if constexpr (WGT == 1) {
-                        const float Wt = c.z * (hsqrt<FAST>(dhs2 + c.w) + hsqrt<FAST>(dhr2 + c.w));
+                        const float Wt = c.x * (hsqrt<FAST>(dhs2 + c.y) + hsqrt<FAST>(dhr2 + c.y));
                         acc[i] = fmaf(Wt, val, acc[i]);
                     } else {
                         acc[i] += val;
@@ -565,10 +593,8 @@ __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, co
             S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
             S.z2[i] = (float)(z * z);
         } else if constexpr (VEL == VK_TABLE) {
-            const double u = (z - g.tza) / g.tsp;
-            const double j = floor(u);
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-            S.zc[i] = make_float4(__int_as_float((int)j), (float)(u - j), wz, (float)(z * z));
+            S.zc[i] = make_float4(wz, (float)(z * z), 0.f, 0.f);
         } else {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
             S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
@@ -614,7 +640,7 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
         for (int i = threadIdx.x; i < total; i += blockDim.x) ring[i] = TT(0.f);
     }
     TB* tab = reinterpret_cast<TB*>(smem_raw + mig_static_bytes() + mig_ring_bytes(g));
-    float2* srcc = reinterpret_cast<float2*>(smem_raw + mig_static_bytes() + mig_ring_bytes(g));
+    float2* srcc = reinterpret_cast<float2*>(smem_raw + mig_static_bytes() + mig_ring_bytes(g) + table_bytes(g));
     if constexpr (VEL == VK_TABLE) {
         const uint4* src = reinterpret_cast<const uint4*>(g.table);
         uint4* dst = reinterpret_cast<uint4*>(tab);
@@ -682,17 +708,26 @@ static cudaError_t launch_migrate_t(const GeomParams& g, const TileShape& t, con
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image,
-                                         mig_cap(g.nt, g.elem_align), w);
+        kern<<<grid, THREADS, smem, s>>>(g, t, tr, static_cast<const TT*>(traces), image, mig_cap(g), w);
         return cudaGetLastError();
     };
     if constexpr (VEL == VK_LINEAR) {
         return with_lp<FAST>(g.lp_terms,
                              [&](auto L) { return go(k_migrate<VEL, WGT, FAST, TT, decltype(L)::value>); });
     } else if constexpr (VEL == VK_TABLE) {
-        if (g.tdt == KH_F16) return go(k_migrate<VEL, WGT, FAST, TT, LP_SHORT, __half>);
-        if (g.tdt == KH_U16) return go(k_migrate<VEL, WGT, FAST, TT, LP_SHORT, unsigned short>);
-        return go(k_migrate<VEL, WGT, FAST, TT, LP_SHORT>);
+        // the LPT slot carries the table's depth-node stride M
+        auto tb = [&](auto M) -> cudaError_t {
+            constexpr int m = decltype(M)::value;
+            if (g.tdt == KH_F16) return go(k_migrate<VEL, WGT, FAST, TT, m, __half>);
+            if (g.tdt == KH_U16) return go(k_migrate<VEL, WGT, FAST, TT, m, unsigned short>);
+            return go(k_migrate<VEL, WGT, FAST, TT, m, float>);
+        };
+        switch (g.tm) {
+            case 1: return tb(std::integral_constant<int, 1>());
+            case 2: return tb(std::integral_constant<int, 2>());
+            case 4: return tb(std::integral_constant<int, 4>());
+            default: return cudaErrorInvalidValue;
+        }
     } else {
         return go(k_migrate<VEL, WGT, FAST, TT, LP_SHORT>);
     }
@@ -731,7 +766,7 @@ static cudaError_t launch_vgrad_t(const GeomParams& g, const TileShape& t, const
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, THREADS, smem, s>>>(g, t, tr, traces, image, mig_cap(g.nt, g.elem_align), w, partial);
+        kern<<<grid, THREADS, smem, s>>>(g, t, tr, traces, image, mig_cap(g), w, partial);
         return cudaGetLastError();
     };
     if constexpr (VEL == VK_LINEAR)
@@ -768,7 +803,7 @@ __global__ void __launch_bounds__(THREADS, 2)
         S.zero[0] = S.zero[1] = S.zero[2] = S.zero[3] = 0.f;
         fence_barrier_init();
     }
-    const int cap = mig_cap(g_ring.nt, g_ring.elem_align);
+    const int cap = mig_cap(g_ring);
     for (int i = threadIdx.x; i < LEAD + STAGES * cap + SLACK; i += blockDim.x) ring[i] = TT(0.f);
     int n = 0;   // stages filled (producer warp) or consumed (consumer warps) so far
     while (true) {

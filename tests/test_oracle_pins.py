@@ -356,9 +356,11 @@ def test_pins_catch_planted_mistakes(mutation, check):
 
 def test_table_traveltime_nodes_and_cells():
     # nodes reproduce the closed form; a cell centre is the mean of its four corners
-    # (bilinear interpolation); the error against the closed form shrinks ~D^2
-    base = tiny_survey(vel="table", v0=1500.0, k=0.5, oz=0.0, dz=10.0, nz=200)
+    # (bilinear interpolation); the error against the closed form shrinks ~D^2.  With
+    # dz = D/4 the depth nodes fall every D (m = 4) and, at spacing D/4, every dz (m = 1).
+    base = tiny_survey(vel="table", v0=1500.0, k=0.5, oz=0.0, dz=6.25, nz=400)
     D = base.table_spacing
+    assert D == 4 * base.dz
     lin = base.replace(vel="linear")
     h = np.array([0.0, D, 7 * D, 40 * D])
     z = np.array([0.0, 3 * D, 11 * D, 60 * D])
@@ -374,3 +376,23 @@ def test_table_traveltime_nodes_and_cells():
     e1 = np.max(np.abs(oracle.table_traveltime(base, hh, zz) - exact))
     e2 = np.max(np.abs(oracle.table_traveltime(base.replace(table_spacing=D / 4), hh, zz) - exact))
     assert 8.0 < e1 / e2 < 24.0                       # second-order convergence
+
+
+def test_table_depth_nodes_sit_on_image_depths():
+    # depth nodes at z_min + j m dz, m the largest power of two <= min(4, D/dz): with
+    # dz = 10 m and D = 25 m the nodes are every 20 m from the first image depth, so the
+    # table is exact there and bilinear (here: linear in z) between them
+    s = tiny_survey(vel="table", v0=1500.0, k=0.5, oz=30.0, dz=10.0, nz=100)
+    assert s.table_spacing == 25.0
+    lin = s.replace(vel="linear")
+    h = np.array([0.0, 50.0, 125.0, 250.0])
+    for zn in (30.0, 50.0, 230.0, 630.0):                # nodes: 30 + 20 j
+        z = np.full(4, zn)
+        assert rel(oracle.table_traveltime(s, h, z), oracle.traveltime(lin, np.hypot(h, z), z)) < 1e-15
+    z = np.full(4, 40.0)                                 # halfway between the nodes at 30 and 50
+    mid = 0.5 * (oracle.table_traveltime(s, h, np.full(4, 30.0)) + oracle.table_traveltime(s, h, np.full(4, 50.0)))
+    assert rel(oracle.table_traveltime(s, h, z), mid) < 1e-14
+    # the old node at 25 m (a multiple of D) is not a node any more: interpolated, not exact
+    z25 = np.full(1, 25.0 + 30.0)
+    assert abs(oracle.table_traveltime(s, [125.0], z25)[0] -
+               oracle.traveltime(lin, np.hypot([125.0], z25), z25)[0]) > 1e-9

@@ -288,6 +288,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batch: default tiles, no autotuning")
     ap.add_argument("--tile-cache", default=None, help="batch: autotuner JSON cache path")
     ap.add_argument("--no-loop", action="store_true", help="batch: skip the per-job loop arm")
+    ap.add_argument("--batch-mode", default="concurrent", choices=["persistent", "concurrent"],
+                    help="batch: one persistent kernel, or each job's kernel on forked streams")
     ap.add_argument("--op", default="migrate", choices=["migrate", "demigrate", "vgrad"],
                     help="operator timed: migration (Eq. 1), its adjoint, or the (v0, k) gradient")
     args = ap.parse_args()
@@ -453,7 +455,7 @@ def run_batched(args, surveys, ws, rank, local):
             t = tuner.choose(p, h, d)
             tiles[f"{t[0]}x{t[1]}x{t[2]}"] = tiles.get(f"{t[0]}x{t[1]}x{t[2]}", 0) + 1
     t_tune = time.perf_counter() - t_tune
-    batch = kh.Batch(jobs)
+    batch = kh.Batch(jobs, mode=args.batch_mode)
     graph = batch.capture()
     info = batch.info()
     launches_per_step = info["launches"]   # the capture ran the launch sequence once
@@ -473,8 +475,7 @@ def run_batched(args, surveys, ws, rank, local):
     t_ms = max_over_ranks(ws, e0.elapsed_time(e1))
     value = contrib * args.steps * ws / (t_ms / 1e3) / 1e9
     clocks = clk.summary()
-    loop = None
-    if not args.no_loop:
+    def loop_arm(what):
         for _ in range(args.warmup):
             for (p, h, d, m) in jobs:
                 p.migrate(h, d, out=m)
@@ -489,10 +490,19 @@ def run_batched(args, surveys, ws, rank, local):
         for (p, _, _, _) in jobs:
             p.sync()
         tl = max_over_ranks(ws, e0.elapsed_time(e1))
-        loop = {"value": contrib * args.steps * ws / (tl / 1e3) / 1e9, "unit": "Gcontrib/s",
+        return {"value": contrib * args.steps * ws / (tl / 1e3) / 1e9, "unit": "Gcontrib/s",
                 "ms_per_step": tl / args.steps,
                 "launches_per_step": (sum(p.launches for (p, _, _, _) in jobs) - l0) // args.steps,
-                "what": "per-job kirchhoff_migrate calls on the same stream, same tiles and precision"}
+                "what": what}
+
+    loop = loop_tuned = None
+    if not args.no_loop:
+        if tiles:   # the batch's tuned tiles, then the plain path's default tiles
+            loop_tuned = loop_arm("per-job kirchhoff_migrate calls on the same stream, the batch's tuned "
+                                  "tiles, same precision")
+            for (p, _, _, _) in jobs:
+                p.set_tile(None)
+        loop = loop_arm("per-job kirchhoff_migrate calls on the same stream, default tiles, same precision")
     barrier(ws)
     if rank != 0:
         return
@@ -524,11 +534,14 @@ def run_batched(args, surveys, ws, rank, local):
                                "N_tr~U{1000..50000}, nt~U{750..2000}, constant v 2000 m/s, W=1, full "
                                "aperture, 8 bins, 3 Ricker scatterers + noise per job",
                    "contributions_per_step": contrib, "trace_storage": args.trace_dtype,
-                   "work_items": info["items"], "ctas": info["ctas"], "tiles": tiles,
+                   "batch_mode": args.batch_mode, "work_items": info["items"], "ctas": info["ctas"],
+                   "tiles": tiles,
                    "autotune_s": round(t_tune, 2),
                    "l2": "inputs larger than L2 (traces %.1f GB, images %.1f GB)" % (tb / 1e9, ib / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "loop": loop, "speedup_vs_loop": (value / loop["value"]) if loop else None,
+        "loop_tuned_tiles": loop_tuned,
+        "speedup_vs_loop_tuned_tiles": (value / loop_tuned["value"]) if loop_tuned else None,
         "roofline": roof, "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }

@@ -220,8 +220,13 @@ KH_API kh_status kirchhoff_sync(kh_plan p, void* cuda_stream);
  *                     (default), 0 = IEEE-rounded ones; both are parity-tested.
  *  KH_OPT_TILE:       image tile of one CTA, encoded as cx | cy << 10 | cz << 20 (threads per
  *                     CTA along x, y and z-groups, cx*cy*cz == 256, cz <= 16; each thread owns
- *                     16 consecutive z samples of one column); 0 restores the default. */
-typedef enum { KH_OPT_WAIT_POLLS = 1, KH_OPT_FAST_MATH = 2, KH_OPT_TILE = 3 } kh_option;
+ *                     16 consecutive z samples of one column); 0 restores the default.
+ *  KH_OPT_BATCH_MODE: read from jobs[0].plan by kirchhoff_batched_prepare.  0 (default) = one
+ *                     persistent kernel over the work list; 1 = every job's own migration
+ *                     kernel on library-owned streams forked from and joined to the caller's
+ *                     stream (one graph with parallel branches when captured), so that the
+ *                     block scheduler fills one job's tail with the next job's tiles. */
+typedef enum { KH_OPT_WAIT_POLLS = 1, KH_OPT_FAST_MATH = 2, KH_OPT_TILE = 3, KH_OPT_BATCH_MODE = 4 } kh_option;
 KH_API kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value);
 
 /* Profiling: while enabled, CUDA events bracket the main kernel of every migrate /

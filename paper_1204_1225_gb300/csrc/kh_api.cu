@@ -845,6 +845,10 @@ kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value)
             p->tile_code = value;
             return KH_OK;
         }
+        case KH_OPT_BATCH_MODE:
+            if (value != 0 && value != 1) return fail(KH_ERR_INVALID_ARG, "batch mode must be 0 or 1");
+            p->batch_mode = (int)value;
+            return KH_OK;
         default:
             return fail(KH_ERR_INVALID_ARG, "unknown option %d", (int)opt);
     }

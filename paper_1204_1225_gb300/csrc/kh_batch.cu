@@ -48,6 +48,14 @@ struct kh_batch_s {
         void* dst;
     };
     std::vector<Pad> pads;
+    // KH_OPT_BATCH_MODE 1: each job's own k_migrate launch, descending cost, round-robin over
+    // library streams forked from and joined to the caller's stream
+    int mode = 0;
+    std::vector<BatchJob> conc;            // jobs in launch order
+    std::vector<int> conc_pad;             // index into pads, or -1
+    static constexpr int N_STREAMS = 4;
+    cudaStream_t st[N_STREAMS] = {};
+    cudaEvent_t fork = nullptr, join[N_STREAMS] = {};
 };
 
 namespace {
@@ -201,6 +209,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     b->fast = fast;
     b->tdtype = tdt;
     b->wait_polls = jobs[0].plan->wait_polls;
+    b->mode = jobs[0].plan->batch_mode;
     b->n_items = (int)n_items;
     e = cudaMalloc(&b->ws, L.off);
     if (e != cudaSuccess) {
@@ -223,6 +232,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
 
     // ---- per job: binning, staged rows, cull counts
     std::vector<BatchJob> hj(njobs);
+    std::vector<int> pad_of(njobs, -1);
     std::vector<size_t> cull_at(njobs);
     size_t cull_off = 0;
     for (int j = 0; j < njobs; ++j) {
@@ -241,6 +251,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         const void* rows = J.traces;
         if (o.padded) {
             rows = w + o.pad;
+            pad_of[j] = (int)b->pads.size();
             b->pads.push_back({J.ntr, d.nt, o.ld, es, J.traces, w + o.pad});
         }
         hj[j] = BatchJob{g, tss[j], tr, rows, J.image};
@@ -298,6 +309,29 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         std::stable_sort(jo.begin(), jo.end(), [&](int a, int c) { return job_cost[a] > job_cost[c]; });
         for (int r = 0; r < njobs; ++r) job_rank[jo[r]] = r;
     }
+    if (b->mode == 1) {   // concurrent per-job kernels: jobs by descending cost
+        std::vector<int> jo(njobs);
+        std::iota(jo.begin(), jo.end(), 0);
+        std::stable_sort(jo.begin(), jo.end(), [&](int a, int c) { return job_cost[a] > job_cost[c]; });
+        for (int j : jo) {
+            b->conc.push_back(hj[j]);
+            b->conc_pad.push_back(pad_of[j]);
+        }
+        b->work = work;
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int k = 0; e == cudaSuccess && k < kh_batch_s::N_STREAMS; ++k) {
+            e = cudaStreamCreateWithFlags(&b->st[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            kirchhoff_batch_destroy(b);
+            return set_cuda_error(e, "kirchhoff_batched_prepare: streams");
+        }
+        b->ctas = 0;
+        *out = b;
+        return KH_OK;
+    }
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         if (cls[a] != cls[c]) return cls[a] < cls[c];
         const int ja = job_rank[items[a].x], jc = job_rank[items[c].x];
@@ -346,6 +380,32 @@ kh_status kirchhoff_migrate_batched(kh_batch b, void* cuda_stream)
     if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
     if (dev != b->device) return bfail(KH_ERR_INVALID_ARG, "batch belongs to device %d, current is %d", b->device, dev);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (b->mode == 1) {
+        WaitCfg wc{b->d_status, b->wait_polls, WAIT_NS};
+        if ((e = cudaEventRecord(b->fork, s)) != cudaSuccess) return set_cuda_error(e, "kirchhoff_migrate_batched: fork");
+        for (int k = 0; k < kh_batch_s::N_STREAMS; ++k)
+            if ((e = cudaStreamWaitEvent(b->st[k], b->fork, 0)) != cudaSuccess)
+                return set_cuda_error(e, "kirchhoff_migrate_batched: fork");
+        for (size_t i = 0; i < b->conc.size(); ++i) {
+            cudaStream_t sk = b->st[i % kh_batch_s::N_STREAMS];
+            const BatchJob& J = b->conc[i];
+            if (b->conc_pad[i] >= 0) {
+                const auto& p = b->pads[b->conc_pad[i]];
+                if ((e = launch_pad(p.ntr, p.nt, p.ld, p.esize, p.src, p.dst, sk)) != cudaSuccess)
+                    return set_cuda_error(e, "kirchhoff_migrate_batched: row padding");
+                ++b->launches;
+            }
+            e = launch_migrate(J.g, J.ts, J.tr, J.traces, J.image, b->vel, b->fast, wc, sk);
+            ++b->launches;
+            if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_migrate_batched: migration kernel");
+        }
+        for (int k = 0; k < kh_batch_s::N_STREAMS; ++k) {
+            if ((e = cudaEventRecord(b->join[k], b->st[k])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, b->join[k], 0)) != cudaSuccess)
+                return set_cuda_error(e, "kirchhoff_migrate_batched: join");
+        }
+        return KH_OK;
+    }
     for (const auto& p : b->pads) {
         if ((e = launch_pad(p.ntr, p.nt, p.ld, p.esize, p.src, p.dst, s)) != cudaSuccess)
             return set_cuda_error(e, "kirchhoff_migrate_batched: row padding");
@@ -396,6 +456,11 @@ kh_status kirchhoff_batch_destroy(kh_batch b)
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != b->device) cudaSetDevice(b->device);
+    for (int k = 0; k < kh_batch_s::N_STREAMS; ++k) {
+        if (b->st[k]) cudaStreamDestroy(b->st[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     cudaFree(b->ws);
     if (prev != b->device) cudaSetDevice(prev);
     delete b;

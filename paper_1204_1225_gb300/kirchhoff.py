@@ -20,7 +20,8 @@ KH_OK, KH_ERR_INVALID_ARG, KH_ERR_UNSUPPORTED, KH_ERR_OOM, KH_ERR_CUDA, KH_ERR_T
 KH_F32, KH_F16, KH_BF16, KH_U16 = 0, 1, 2, 3
 KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE = 0, 1, 2
 KH_W_ONE, KH_W_OBLIQ_SPREAD = 0, 1
-KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE = 1, 2, 3
+KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE, KH_OPT_BATCH_MODE = 1, 2, 3, 4
+BATCH_MODES = {"persistent": 0, "concurrent": 1}
 
 _STATUS = {0: "KH_OK", 1: "KH_ERR_INVALID_ARG", 2: "KH_ERR_UNSUPPORTED", 3: "KH_ERR_OOM",
            4: "KH_ERR_CUDA", 5: "KH_ERR_TIMEOUT", 6: "KH_ERR_INTERNAL"}
@@ -385,13 +386,17 @@ def arrival_times_fn(plan: "Plan"):
 
 
 class Batch:
-    """Many migrations in one persistent launch (kirchhoff_batched_prepare / _migrate_batched).
+    """Many migrations in one launch sequence (kirchhoff_batched_prepare / _migrate_batched).
 
     ``jobs`` is a list of (Plan, Headers, traces, image) with device tensors; the traces and
-    images are read / written in place by every run (and every graph replay)."""
+    images are read / written in place by every run (and every graph replay).  ``mode`` is
+    "persistent" (one persistent kernel over the work list) or "concurrent" (each job's own
+    kernel on forked library streams)."""
 
-    def __init__(self, jobs, stream=None):
+    def __init__(self, jobs, stream=None, mode: str = "persistent"):
         self._keep = list(jobs)
+        self.mode = mode
+        kirchhoff_set_option(self._keep[0][0].handle, KH_OPT_BATCH_MODE, BATCH_MODES[mode])
         self.handle = kirchhoff_batched_prepare(
             [{"plan": p.handle, "ntr": h.ntr, "sx": h.sx, "sy": h.sy, "rx": h.rx, "ry": h.ry,
               "traces": d, "image": m} for (p, h, d, m) in self._keep], stream)

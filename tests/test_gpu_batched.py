@@ -51,11 +51,12 @@ def _specs():
     ]
 
 
-def test_batched_equals_per_job_fp32():
+@pytest.mark.parametrize("mode", ["persistent", "concurrent"])
+def test_batched_equals_per_job_fp32(mode):
     jobs = [_job(s, BASE_SEED + i, tile=t) for i, (s, t) in enumerate(_specs())]
-    b = kh.Batch(jobs)
+    b = kh.Batch(jobs, mode=mode)
     info = b.info()
-    assert info["items"] > 0 and 0 < info["ctas"] <= info["items"]
+    assert info["items"] > 0 and (mode == "concurrent" or 0 < info["ctas"] <= info["items"])
     b.run()
     b.sync()
     ref = _per_job(jobs)
@@ -79,9 +80,10 @@ def test_batched_vs_oracle():
         assert err < FP32_REL_L2
 
 
-def test_batched_graph_replay_reads_traces_in_place():
+@pytest.mark.parametrize("mode", ["persistent", "concurrent"])
+def test_batched_graph_replay_reads_traces_in_place(mode):
     jobs = [_job(s, BASE_SEED + 20 + i, tile=t) for i, (s, t) in enumerate(_specs()[:3])]
-    b = kh.Batch(jobs)
+    b = kh.Batch(jobs, mode=mode)
     b.capture()
     b.replay()
     torch.cuda.synchronize()
@@ -98,10 +100,11 @@ def test_batched_graph_replay_reads_traces_in_place():
 
 
 @pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
-def test_batched_16bit_traces(dtype):
+@pytest.mark.parametrize("mode", ["persistent", "concurrent"])
+def test_batched_16bit_traces(dtype, mode):
     specs = [(survey_3d_gradient(800, 64).replace(nt=1001), None), (_small_cube(500, 40, 750), None)]
     jobs = [_job(s, BASE_SEED + 30 + i, dtype=dtype, tile=t) for i, (s, t) in enumerate(specs)]
-    b = kh.Batch(jobs)
+    b = kh.Batch(jobs, mode=mode)
     b.run()
     b.sync()
     for (p, h, d, img), r in zip(jobs, _per_job(jobs)):
@@ -159,13 +162,14 @@ def test_autotuner_picks_a_runnable_tile_and_caches(tmp_path):
     assert torch.equal(p.migrate(h, d), q.migrate(h, d))
 
 
-def test_batched_constant_velocity_jobs_from_the_batch_generator():
+@pytest.mark.parametrize("mode", ["persistent", "concurrent"])
+def test_batched_constant_velocity_jobs_from_the_batch_generator(mode):
     """The batch workload's own job recipe (constant v, W = 1, full aperture, 8 bins,
     random sources and receivers over the footprint) at small sizes."""
     from paper_1204_1225_gb300.survey import survey_batch_3d
     specs = survey_batch_3d(5, n_range=(17, 40), ntr_range=(50, 400), nt_range=(300, 520))
     jobs = [_job(s, BASE_SEED + 40 + i) for i, s in enumerate(specs)]
-    b = kh.Batch(jobs)
+    b = kh.Batch(jobs, mode=mode)
     b.run()
     b.sync()
     for (p, h, d, img), r in zip(jobs, _per_job(jobs)):

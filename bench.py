@@ -55,19 +55,27 @@ LANES_PER_SM_CLK = {"issue": 128, "fma": 128, "alu": 64, "xu": 16, "lsu": 32}
 # k_migrate per variant; the 100k-trace 256^3 workload runs the variant measured on its
 # 10k-trace case: same grid, tile and 6-term fit).
 PIPE_MIX = {
-    "3d-vz-100k-256cube": {"issue": 43.16, "fma": 29.22, "alu": 4.82, "xu": 3.17, "lsu": 4.74},
-    "3d-vz-10k-256cube": {"issue": 43.16, "fma": 29.22, "alu": 4.82, "xu": 3.17, "lsu": 4.74},
-    "3d-vz-40k-128cube": {"issue": 48.37, "fma": 32.18, "alu": 6.85, "xu": 3.24, "lsu": 4.85},
-    "25d-vz-20k-512x400": {"issue": 47.59, "fma": 33.98, "alu": 5.26, "xu": 2.37, "lsu": 4.82},
+    "3d-vz-100k-256cube": {"issue": 41.05, "fma": 27.15, "alu": 4.76, "xu": 3.17, "lsu": 4.74},
+    "3d-vz-10k-256cube": {"issue": 41.05, "fma": 27.15, "alu": 4.76, "xu": 3.17, "lsu": 4.74},
+    "3d-vz-40k-128cube": {"issue": 46.21, "fma": 30.27, "alu": 6.59, "xu": 3.25, "lsu": 4.85},
+    "25d-vz-20k-512x400": {"issue": 45.26, "fma": 31.83, "alu": 5.05, "xu": 2.37, "lsu": 4.82},
+    # mixed precision: U16 radial table + FP16 traces (k_migrate<table, obliquity, FP16, M=2, U16>)
+    "3d-vz-100k-256cube-table-u16-f16": {"issue": 34.0, "fma": 19.3, "alu": 6.08, "xu": 2.23, "lsu": 5.5},
+    "3d-vz-10k-256cube-table-u16-f16": {"issue": 34.0, "fma": 19.3, "alu": 6.08, "xu": 2.23, "lsu": 5.5},
+    # adjoint (k_demigrate) on the 10k-trace case of the headline geometry
+    "3d-vz-100k-256cube-demigrate": {"issue": 93.3, "fma": 61.4, "alu": 8.98, "xu": 7.14, "lsu": 8.19},
+    "3d-vz-10k-256cube-demigrate": {"issue": 93.3, "fma": 61.4, "alu": 8.98, "xu": 7.14, "lsu": 8.19},
+    # persistent batched kernel, constant velocity (measured on the 8-job small batch)
+    "batch64-3d-vz-f32": {"issue": 28.27, "fma": 16.59, "alu": 4.77, "xu": 2.51, "lsu": 3.91},
 }
 
 
 # DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
 # (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
 TRAFFIC = {
-    "3d-vz-10k-256cube": 61331968 + 1029468160,
-    "3d-vz-40k-128cube": 145624000 + 94539500,
-    "25d-vz-20k-512x400": 48173300 + 315392,
+    "3d-vz-10k-256cube": 60817664 + 1030223000,
+    "3d-vz-40k-128cube": 145600000 + 94600000,
+    "25d-vz-20k-512x400": 47900000 + 500000,
 }
 
 
@@ -86,6 +94,7 @@ def workloads():
         "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
         "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
         "batch64-3d-vz": lambda: sv.survey_batch_3d(64),
+        "batch8-3d-vz-small": lambda: sv.survey_batch_3d(8, n_range=(64, 96), ntr_range=(1000, 5000)),
     }
 
 
@@ -388,9 +397,13 @@ def main():
     clk_mhz = clocks.get("sm_mhz") or 2070.0
     achieved = contrib / (kern_ms / max(kern_n, 1) / 1e3) / 1e9 if kern_n else None
     kname = {"migrate": "k_migrate", "demigrate": "k_demigrate", "vgrad": "k_vgrad"}[args.op]
-    mix_key = args.workload if args.op == "migrate" else f"{args.workload}-{args.op}"
-    mix = PIPE_MIX.get(mix_key) if (args.trace_dtype == "f32" and args.fast_math and
-                                    args.vel == "analytic") else None
+    if args.vel == "table":
+        mix_key = f"{args.workload}-table-{args.table_dtype}-{args.trace_dtype}"
+    elif args.trace_dtype == "f32":
+        mix_key = args.workload if args.op == "migrate" else f"{args.workload}-{args.op}"
+    else:
+        mix_key = None
+    mix = PIPE_MIX.get(mix_key) if (mix_key and args.fast_math) else None
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "unit": "Gcontrib/s",
             "kernel_ms_per_launch": kern_ms / max(kern_n, 1)}
     if mix:
@@ -404,7 +417,7 @@ def main():
     else:
         roof.update({"peak": None, "frac": None,
                      "peak_basis": "no measured instruction mix for this kernel variant"})
-    roof["traffic"] = TRAFFIC.get(mix_key) if (args.trace_dtype == "f32" and args.vel == "analytic") else None
+    roof["traffic"] = TRAFFIC.get(mix_key) if mix_key else None
     cpu = None
     if not args.no_cpu_baseline and ws == 1 and args.op == "migrate":
         cpu = cpu_baseline(s, traces.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)

@@ -741,11 +741,14 @@ static kh_status demigrate_tile(const kh_desc& d, GeomParams& g, int ntr, DmTile
             const double half = 0.5 * diag;
             const double b = 2.0 * g.kabs * half / vmin * 1.02 + 1e-6;
             const double tol = std::max(5e-6 * g.kabs * d.dt, 1e-12);
-            gt.lp_terms = LP_SHORT;
-            if (!fit_log1p(std::expm1(-b), std::expm1(b), LP_SHORT, gt.lp, &gt.lp_s, &gt.lp_o, tol)) {
-                gt.lp_terms = LP_LONG;
-                if (!fit_log1p(std::expm1(-b), std::expm1(b), LP_LONG, gt.lp, &gt.lp_s, &gt.lp_o, tol)) continue;
+            bool fitted = false;   // the shortest length of LP_TERMS that meets the budget
+            for (int q = 0; q < N_LP_TERMS && !fitted; ++q) {
+                gt.lp_terms = LP_TERMS[q];
+                fitted = fit_log1p(std::expm1(-b), std::expm1(b), gt.lp_terms, gt.lp, &gt.lp_s, &gt.lp_o, tol);
             }
+            if (!fitted) continue;
+            const double c1 = (double)gt.C1 + (double)gt.C1lo;
+            for (int q = 0; q < LP_LONG; ++q) gt.lpc[q] = (float)(c1 * gt.lp[q]);
             gt.rho_max = (float)std::expm1(b);
         }
         (void)probe;

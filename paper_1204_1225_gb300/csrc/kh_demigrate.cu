@@ -7,6 +7,7 @@
 // evaluates tau for its own trace at every image point of the tile (the same FP64-reference
 // + FP32-delta evaluation as the migration) and adds W (1-f) m and W f m into its own column
 // of a lane-interleaved window buffer [row][lane] (bank = lane: no conflicts, no atomics).
+// The sample index is floor(tau - lo) (adding 1.5 * 2^23 rounded down), as in the migration.
 // After the tile the lane adds its window into its own row of the part's partial-trace
 // buffer.  A second kernel sums the P partial buffers in a fixed order into the output.
 #include "kh_tau.cuh"
@@ -78,21 +79,27 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
         }
         if (!__syncthreads_or(ok)) continue;
 
-        LegRef rs{0.f, 0.f, 0.f, 0.f}, rr{0.f, 0.f, 0.f, 0.f};
+        // per-lane FP64 reference: (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c) per leg, as the migration
+        float4 rs = make_float4(0.f, 0.f, 0.f, 0.f), rr = rs;
         float4 ah = h;
         double tau_ref = -g.t0d / g.dtd;
         if constexpr (VEL == VK_LINEAR) {
             if (ok) {
-                const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs);
-                const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr);
+                LegRef ls_, lr_;
+                float qis = 0.f, qir = 0.f;
+                const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, ls_, &qis);
+                const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, lr_, &qir);
+                rs = make_float4(ls_.Rc2, qis, ls_.wc, ls_.iuc);
+                rr = make_float4(lr_.Rc2, qir, lr_.wc, lr_.iuc);
                 tau_ref += (ls + lr) * inv_kdt;
                 ah = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
                                  (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
             }
         }
-        const float c0rel = (float)(tau_ref - (double)lo - 0.5);
+        // window-relative time th = tau - lo; valid iff 0 <= th <= hi - lo
+        const float c0rel = (float)(tau_ref - (double)lo);
         const float lim = (float)(hi - lo);
-        const float cmid = 0.5f * (lim - 1.f), chalf = 0.5f * lim;
+        const float cmid = 0.5f * lim, chalf = 0.5f * lim;
 
         // stage the tile's image values (zero outside the grid) and per-z constants
         for (int p = threadIdx.x; p < ncol * dt.tz; p += DM_THREADS) {
@@ -106,9 +113,9 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
         for (int i = threadIdx.x; i < dt.tz; i += DM_THREADS) {
             const double z = g.oz + (z0 + i) * g.dz;
             if constexpr (VEL == VK_LINEAR) {
-                const ZConst c = z_constants(z, box.cz, g);
-                S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
-                S.z2[i] = (float)(z * z);
+                float gamma;
+                S.zc[i] = z_constants_m(z, box.cz, g, gamma);
+                S.z2[i] = gamma;
             } else {
                 const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
                 S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
@@ -141,8 +148,8 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                         const float Rr = hsqrt<FAST>(dhr2 + zc.x);
                         const float Ssum = Rs + Rr;
                         const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                        const float tm = __fadd_rn(th, MAGIC);
-                        const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
+                        const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
+                        const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
                         const bool v = fabsf(th - cmid) <= chc;
                         const float W = (WGT == 1) ? zc.y * Ssum : 1.f;
                         const float wm = v ? W * mcol[iz] : 0.f;
@@ -158,22 +165,18 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                     const float dPr = fmaf(dxc, cxf + ah.z, dyc * (cyf + ah.w));
                     const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
                     const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
-                    const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
 #pragma unroll 4
                     for (int iz = 0; iz < dt.tz; ++iz) {
-                        const float4 c4 = S.zc[iz];
-                        const ZConst zc{c4.x, c4.y, c4.z, c4.w};
-                        float sqs, sqr;
-                        const float z2i = S.z2[iz];
-                        const float rho_s = leg_delta<WGT, FAST>(dPs, dhs2, z2i, zc, rs, qc2s, sqs);
-                        const float rho_r = leg_delta<WGT, FAST>(dPr, dhr2, z2i, zc, rr, qc2r, sqr);
+                        const float4 zk = S.zc[iz];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
+                        float sqs = 0.f, sqr = 0.f;
+                        const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zk, rs, sqs);
+                        const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
                         const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
-                        const float L = log1p_poly<LPT>(rho, g);
-                        const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
-                        const float tm = __fadd_rn(th, MAGIC);
-                        const float f = __fadd_rn(__fadd_rn(th, -__fadd_rn(tm, -MAGIC)), 0.5f);
+                        const float th = tau_poly<LPT>(rho, g, c0rel);
+                        const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
+                        const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
                         const bool v = fabsf(th - cmid) <= chc;
-                        const float W = (WGT == 1) ? zc.gamma * (sqs + sqr) : 1.f;
+                        const float W = (WGT == 1) ? S.z2[iz] * (sqs + sqr) : 1.f;
                         const float wm = v ? W * mcol[iz] : 0.f;
                         const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                         const float a1 = wm * f;
@@ -216,14 +219,18 @@ static cudaError_t dm_launch_t(const GeomParams& g, const DmTile& dt, const Trac
                                const float* image, float* partial, int* status, int max_chunks,
                                cudaStream_t s)
 {
-    auto kern = (VEL == VK_LINEAR && g.lp_terms == LP_LONG) ? k_demigrate<VEL, WGT, FAST, LP_LONG>
-                                                          : k_demigrate<VEL, WGT, FAST, LP_SHORT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(DmSmem));
-    if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)max_chunks, (unsigned)g.n_bins, (unsigned)dt.parts);
-    kern<<<grid, DM_THREADS, sizeof(DmSmem), s>>>(g, dt, tr, image, partial, status);
-    return cudaGetLastError();
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(DmSmem));
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)max_chunks, (unsigned)g.n_bins, (unsigned)dt.parts);
+        kern<<<grid, DM_THREADS, sizeof(DmSmem), s>>>(g, dt, tr, image, partial, status);
+        return cudaGetLastError();
+    };
+    if constexpr (VEL == VK_LINEAR)
+        return with_lp<FAST>(g.lp_terms, [&](auto L) { return go(k_demigrate<VEL, WGT, FAST, decltype(L)::value>); });
+    else
+        return go(k_demigrate<VEL, WGT, FAST, LP_SHORT>);
 }
 
 cudaError_t launch_demigrate(const GeomParams& g, const DmTile& dt, const TraceSet& tr,

@@ -676,29 +676,6 @@ __global__ void __launch_bounds__(THREADS, 2)
 }
 
 // ------------------------------------------------------------------ launch (per trace type)
-// ln(1 + rho) lengths instantiated for linear v(z): every length of LP_TERMS with the fast
-// (approximate) square root and reciprocal; 12 and 20 with the IEEE ones, where a shorter fit
-// runs in the 12-term kernel (its upper coefficients are zero, so Horner's rule returns the
-// same value bit for bit).  Calls f(std::integral_constant<int, L>()) for the length L.
-template <bool FAST, typename F>
-cudaError_t with_lp(int terms, F&& f)
-{
-    if constexpr (FAST) {
-        switch (terms) {
-            case 6: return f(std::integral_constant<int, 6>());
-            case 8: return f(std::integral_constant<int, 8>());
-            case 10: return f(std::integral_constant<int, 10>());
-            case 12: return f(std::integral_constant<int, 12>());
-            case 20: return f(std::integral_constant<int, 20>());
-            default: return cudaErrorInvalidValue;
-        }
-    } else {
-        if (terms <= LP_SHORT) return f(std::integral_constant<int, LP_SHORT>());
-        if (terms <= LP_LONG) return f(std::integral_constant<int, LP_LONG>());
-        return cudaErrorInvalidValue;
-    }
-}
-
 template <int VEL, int WGT, bool FAST, typename TT>
 static cudaError_t launch_migrate_t(const GeomParams& g, const TileShape& t, const TraceSet& tr,
                                    const void* traces, float* image, const WaitCfg& w, cudaStream_t s)

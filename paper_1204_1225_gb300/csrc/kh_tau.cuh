@@ -17,9 +17,35 @@
 // with ln(1 + rho) from a polynomial fitted on the host for the tile's |rho| bound.
 #pragma once
 
+#include <type_traits>
+
 #include "kh_device.cuh"
 
 namespace kh {
+
+// ln(1 + rho) lengths instantiated for linear v(z): every length of LP_TERMS with the fast
+// (approximate) square root and reciprocal; 12 and 20 with the IEEE ones, where a shorter fit
+// runs in the 12-term kernel (its upper coefficients are zero, so Horner's rule returns the
+// same value bit for bit).  Calls f(std::integral_constant<int, L>()) for the length L.
+template <bool FAST, typename F>
+cudaError_t with_lp(int terms, F&& f)
+{
+    if constexpr (FAST) {
+        switch (terms) {
+            case 6: return f(std::integral_constant<int, 6>());
+            case 8: return f(std::integral_constant<int, 8>());
+            case 10: return f(std::integral_constant<int, 10>());
+            case 12: return f(std::integral_constant<int, 12>());
+            case 20: return f(std::integral_constant<int, 20>());
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        if (terms <= LP_SHORT) return f(std::integral_constant<int, LP_SHORT>());
+        if (terms <= LP_LONG) return f(std::integral_constant<int, LP_LONG>());
+        return cudaErrorInvalidValue;
+    }
+}
+
 
 // Per-(tile, trace) data of one leg, FP32 copies of FP64 values.
 struct LegRef {

@@ -131,6 +131,18 @@ __device__ __forceinline__ float hsqrt(float x)
 }
 
 template <bool FAST>
+__device__ __forceinline__ float hrsqrt(float x)
+{
+    if constexpr (FAST) {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    } else {
+        return __frcp_rn(__fsqrt_rn(x));
+    }
+}
+
+template <bool FAST>
 __device__ __forceinline__ float hrcp(float x)
 {
     if constexpr (FAST) {

@@ -48,12 +48,13 @@ struct __align__(16) MigSmem {
     float4 refs[STAGES][BMAX];  // linear: source-leg LegRef
     float4 refr[STAGES][BMAX];  // linear: receiver-leg LegRef
     float2 mid[STAGES][BMAX];   // FP32 midpoint (aperture test)
-    int4 win[STAGES][BMAX];     // x: tau_ref - lo - 1/2 (float bits), y: smem index of sample lo
-                                // minus MAGIC_BITS, z/w: c_mid/c_half (float bits) of the valid
-                                // range -1/2 <= tau - lo - 1/2 <= hi - lo - 1/2
-    float tb[STAGES][BMAX];     // (lo + 1/2) dt + t0: T_s + T_r = (tau - lo - 1/2) dt + tb (gradient mode)
-    float4 zc[MAX_ZG * NZ];     // per-z constants (ZConst for linear v; (z^2, w_z, 0, 0) for constant v)
-    float z2[MAX_ZG * NZ];      // linear: z^2 (exact for grid depths)
+    int4 win[STAGES][BMAX];     // x: tau_ref - lo (float bits), y: smem index of sample lo minus
+                                // MAGIC_BITS, z/w: c_mid/c_half (float bits) of the valid range
+                                // 0 <= tau - lo <= hi - lo
+    float tb[STAGES][BMAX];     // lo dt + t0: T_s + T_r = (tau - lo) dt + tb (gradient mode)
+    float4 zc[MAX_ZG * NZ];     // per-z constants: linear v, z_constants_m; constant v, (z^2, w_z);
+                                // table, (w_z, z^2)
+    float z2[MAX_ZG * NZ];      // linear: gamma(z) of the weight
     float zero[4];
 };
 
@@ -150,9 +151,8 @@ __device__ __forceinline__ float sample_at(const TT* data, float th, int base, f
 // ------------------------------------------------------------------ producer warp
 // `n` is the number of stages this CTA's producer has filled before (mbarrier phases carry
 // over from one work item to the next in the persistent kernel); returns the new count.
-// FLOOR: the window-relative time is tau - lo (migration kernel, sample_at), else
-// tau - lo - 1/2 (gradient kernel, rounding to nearest).
-template <int VEL, typename TT, bool FLOOR>
+// The window-relative time the consumers evaluate is tau - lo (sample index floor(tau - lo)).
+template <int VEL, typename TT>
 __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                                             const TraceSet& tr, const TT* __restrict__ traces, int tb,
                                             int te, const TileBox& box, const WaitCfg& wc, int n)
@@ -222,22 +222,21 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 if constexpr (VEL == VK_LINEAR) {
                     LegRef rs, rr;
                     float qis = 0.f, qir = 0.f;
-                    const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs, FLOOR ? &qis : nullptr);
-                    const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr, FLOOR ? &qir : nullptr);
+                    const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs, &qis);
+                    const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr, &qir);
                     tau_ref += (ls + lr) * inv_kdt;
-                    // migration kernel: (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c); gradient: LegRef
-                    S.refs[s][slot] = make_float4(rs.Rc2, FLOOR ? qis : rs.qc, rs.wc, rs.iuc);
-                    S.refr[s][slot] = make_float4(rr.Rc2, FLOOR ? qir : rr.qc, rr.wc, rr.iuc);
+                    // (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c) per leg
+                    S.refs[s][slot] = make_float4(rs.Rc2, qis, rs.wc, rs.iuc);
+                    S.refr[s][slot] = make_float4(rr.Rc2, qir, rr.wc, rr.iuc);
                     S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
                                                  (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
                 }
                 S.hdr[s][slot] = h;
                 S.mid[s][slot] = m;
-                S.tb[s][slot] = (float)(((double)lo + 0.5) * g.dtd + g.t0d);
+                S.tb[s][slot] = (float)((double)lo * g.dtd + g.t0d);
                 const float lim = (float)(hi - lo);
-                S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo - (FLOOR ? 0.0 : 0.5))),
-                                           dst + (lo - lo_al) - MAGIC_BITS,
-                                           __float_as_int(FLOOR ? 0.5f * lim : 0.5f * (lim - 1.f)),
+                S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo)),
+                                           dst + (lo - lo_al) - MAGIC_BITS, __float_as_int(0.5f * lim),
                                            __float_as_int(0.5f * lim));
             }
             if (lane == 0 && bytes > 0) mbar_expect_tx(&S.full[s], (uint32_t)bytes);
@@ -456,7 +455,7 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
     const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
     const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
     const float4* zc = &S.zc[tzg * NZ];
-    const float* zq = &S.z2[tzg * NZ];
+    const float* zg = &S.z2[tzg * NZ];   // linear: gamma(z)
     const int zero_off = (int)(((const char*)S.zero - (const char*)data) / (int)sizeof(TT));
     const float dtf = (float)g.dtd;
     const float inv_v0 = (float)(1.0 / g.v0), inv_v0sq = (float)(1.0 / (g.v0 * g.v0));
@@ -510,7 +509,7 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
                     const float Rr = hsqrt<FAST>(dhr2 + c.x);
                     const float Ssum = Rs + Rr;
                     const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
+                    const float tm = __fadd_rd(th, MAGIC);   // MAGIC + floor(th)
                     const bool ok = fabsf(th - cmid) <= chalf;
                     const int off = ok ? __float_as_int(tm) + w.y : zero_off;
                     const float slope = to_f32<TT>(data[off + 1]) - to_f32<TT>(data[off]);
@@ -518,31 +517,26 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
                     g0 = fmaf(W * mv[i] * slope, -Ssum * inv_v0sq, g0);
                 }
             } else {
-                const float4 rsv = S.refs[s][t], rrv = S.refr[s][t], a = S.hda[s][t];
-                const LegRef rs{rsv.x, rsv.y, rsv.z, rsv.w}, rr{rrv.x, rrv.y, rrv.z, rrv.w};
+                const float4 rs = S.refs[s][t], rr = S.refr[s][t], a = S.hda[s][t];
                 const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
                 const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
                 const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
                 const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
-                const float qc2s = rs.qc + 2.f, qc2r = rr.qc + 2.f;
 #pragma unroll
                 for (int i = 0; i < NZ; ++i) {
-                    const float4 c4 = zc[i];
-                    const ZConst c{c4.x, c4.y, c4.z, c4.w};
+                    const float4 zk = zc[i];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
                     float sqs, sqr, qws, qwr;
-                    const float z2i = zq[i];
-                    const float rho_s = leg_delta_grad<FAST>(dPs, dhs2, z2i, c, rs, qc2s, sqs, qws);
-                    const float rho_r = leg_delta_grad<FAST>(dPr, dhr2, z2i, c, rr, qc2r, sqr, qwr);
+                    const float rho_s = leg_delta_grad_m<FAST>(dPs, dhs2, zk, rs, sqs, qws);
+                    const float rho_r = leg_delta_grad_m<FAST>(dPr, dhr2, zk, rr, sqr, qwr);
                     const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
-                    const float L = log1p_poly<LPT>(rho, g);
-                    const float th = fmaf(L, g.C1, fmaf(L, g.C1lo, c0rel));
-                    const float tm = __fadd_rn(th, MAGIC);
+                    const float th = tau_poly<LPT>(rho, g, c0rel);
+                    const float tm = __fadd_rd(th, MAGIC);   // MAGIC + floor(th)
                     const bool ok = fabsf(th - cmid) <= chalf;
                     const int off = ok ? __float_as_int(tm) + w.y : zero_off;
                     const float slope = to_f32<TT>(data[off + 1]) - to_f32<TT>(data[off]);
-                    const float W = (WGT == 1) ? c.gamma * (sqs + sqr) : 1.f;
+                    const float W = (WGT == 1) ? zg[i] * (sqs + sqr) : 1.f;
                     const float wms = W * mv[i] * slope;
-                    const float inv_vz = c.alpha * inv_a;
+                    const float inv_vz = zk.x * inv_a;
                     const float z = fmaf((float)i, dzf, zb);
                     const float qw = qws + qwr;
                     const float Tsum = fmaf(th, dtf, tbase);
@@ -576,22 +570,18 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
     }
 }
 
-// Per-z constants of a tile's depth range [z0, z0 + cz NZ), written by all threads.  Linear
-// v(z): MODE 0 (migration) stores z_constants_m and gamma, MODE 1 (gradient) ZConst and z^2.
+// Per-z constants of a tile's depth range [z0, z0 + cz NZ), written by all threads (the same
+// layout in both modes).
 template <int VEL, int MODE>
 __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, const TileShape& ts, int z0,
                                              const TileBox& box)
 {
     for (int i = threadIdx.x; i < ts.cz * NZ; i += blockDim.x) {
         const double z = g.oz + (z0 + i) * g.dz;
-        if constexpr (VEL == VK_LINEAR && MODE == 0) {
+        if constexpr (VEL == VK_LINEAR) {
             float gamma;
             S.zc[i] = z_constants_m(z, box.cz, g, gamma);
             S.z2[i] = gamma;
-        } else if constexpr (VEL == VK_LINEAR) {
-            const ZConst c = z_constants(z, box.cz, g);
-            S.zc[i] = make_float4(c.alpha, c.kappa, c.dz2, c.gamma);
-            S.z2[i] = (float)(z * z);
         } else if constexpr (VEL == VK_TABLE) {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
             S.zc[i] = make_float4(wz, (float)(z * z), 0.f, 0.f);
@@ -650,8 +640,8 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
     __syncthreads();
     if (s_abort) return;
     if (threadIdx.x >= CONSUMERS) {
-        mig_producer<VEL, TT, MODE == 0>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
-                                         box, wc, 0);
+        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
+                                    box, wc, 0);
     } else if constexpr (MODE == 0) {
         mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, srcc, 0);
     } else {
@@ -806,7 +796,7 @@ __global__ void __launch_bounds__(THREADS, 2)
         tile_z_setup<VEL, 0>(S, g, ts, z0, box);
         __syncthreads();
         if (threadIdx.x >= CONSUMERS) {
-            n = mig_producer<VEL, TT, true>(S, data, cap, g, tr, static_cast<const TT*>(jobs[w.x].traces),
+            n = mig_producer<VEL, TT>(S, data, cap, g, tr, static_cast<const TT*>(jobs[w.x].traces),
                                       tr.bin_start[bin], tr.bin_start[bin + 1], box, wc, n);
         } else {
             n = mig_consumer<VEL, WGT, FAST, TT, LPT, float>(S, data, g, ts, x0, y0, z0, box, bin,

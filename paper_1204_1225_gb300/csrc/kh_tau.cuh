@@ -7,14 +7,15 @@
 // e^{|k| T} = u = 1 + q + w with w = sqrt(q (q + 2)).  Evaluated directly in FP32 this
 // loses ~1e-7 of T (about 3e-5 samples at T ~ 1 s), too much for 1e-5 image parity.
 // Instead every (tile, trace) pair gets an FP64 reference at the tile centre c (computed
-// once by the staging warp), and each point evaluates only the change relative to it in
-// cancellation-free form:
+// once by the staging warp, or per lane in the adjoint), and each point evaluates only the
+// change relative to it in cancellation-free form:
 //     q - q_c = alpha(z) (dP + kappa(z) R_c^2 + (z^2 - z_c^2)),   dP = |x_h - s_h|^2 - |c_h - s_h|^2
 //             = alpha(z) ((x_h - c_h).(x_h + c_h - 2 s_h) + ...),  kappa(z) = -k (z - z_c)/(v0 + k z_c)
 //     w - w_c = (q - q_c)(q + q_c + 2)/(w + w_c)
 //     u/u_c - 1 = (q - q_c)(1 + (q + q_c + 2)/(w + w_c)) / u_c
 //     tau - tau_c = ln((u_s/u_sc)(u_r/u_rc)) / (|k| dt),
-// with ln(1 + rho) from a polynomial fitted on the host for the tile's |rho| bound.
+// with the per-z products alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2 formed in FP64,
+// and ln(1 + rho) from a polynomial fitted on the host for the tile's |rho| bound.
 #pragma once
 
 #include <type_traits>
@@ -56,7 +57,7 @@ struct LegRef {
 };
 
 // FP64 reference of one leg: returns ln u_c and fills the FP32 copies (and, if qc2i is given,
-// the migration kernel's (q_c + 2)/u_c).
+// (q_c + 2)/u_c, the form the kernels' leg evaluation takes).
 __device__ __forceinline__ double leg_reference(double cx, double cy, double cz, double hx, double hy,
                                                 const GeomParams& g, LegRef& r, float* qc2i = nullptr)
 {
@@ -72,24 +73,7 @@ __device__ __forceinline__ double leg_reference(double cx, double cy, double cz,
     return log1p(qc + wc);
 }
 
-// Per-z constants of the linear path for depth z and tile-centre depth zc.
-struct ZConst {
-    float alpha, kappa, dz2, gamma;
-};
-
-__device__ __forceinline__ ZConst z_constants(double z, double zc, const GeomParams& g)
-{
-    ZConst c;
-    const double vz = g.v0 + g.k * z;
-    c.alpha = (float)(g.a / vz);
-    c.kappa = (float)(-g.k * (z - zc) / (g.v0 + g.k * zc));
-    c.dz2 = (float)((z - zc) * (z + zc));
-    // W = z (R_s + R_r) / (2 r0^2) with R = sqrt(q) sqrt(vz / a)
-    c.gamma = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale * sqrt(vz / g.a)) : 0.f;
-    return c;
-}
-
-// Per-z constants of the migration kernel's linear path, premultiplied by alpha(z):
+// Per-z constants of the linear path, premultiplied by alpha(z):
 // (alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2), and gamma(z) for the weight.
 __device__ __forceinline__ float4 z_constants_m(double z, double zc, const GeomParams& g, float& gamma)
 {
@@ -101,19 +85,7 @@ __device__ __forceinline__ float4 z_constants_m(double z, double zc, const GeomP
                        (float)(alpha * z * z));
 }
 
-// ln(1 + rho) = rho (1 + rho Q), Q a polynomial in t = (rho - m)/h fitted on the tile's rho
-// interval [m - h, m + h] (coefficients g.lp[1..NT-1]).
-template <int NT>
-__device__ __forceinline__ float log1p_poly(float rho, const GeomParams& g)
-{
-    const float t = fmaf(rho, g.lp_s, g.lp_o);
-    float p = g.lp[NT - 1];
-#pragma unroll
-    for (int i = NT - 2; i >= 1; --i) p = fmaf(p, t, g.lp[i]);
-    return fmaf(rho, rho * p, rho);
-}
-
-// The migration kernel's window-relative time: tau - lo = C1 ln(1 + rho) + c0rel, formed as
+// The window-relative time: tau - lo = C1 ln(1 + rho) + c0rel, formed as
 // rho (C1 + rho C1 Q(t)) + c0rel with the C1-scaled coefficients g.lpc.  The rounding of
 // C1 + rho C1 Q (half an ulp of C1, times |rho| <= rho_max) is that of ln(1 + rho) itself
 // scaled by C1; the FP32 rounding error C1lo of C1 is of the same size and is left out.
@@ -127,9 +99,11 @@ __device__ __forceinline__ float tau_poly(float rho, const GeomParams& g, float 
     return fmaf(rho, fmaf(rho, p, g.C1), c0rel);
 }
 
-// leg_delta with the migration kernel's premultiplied per-z constants
-// zk = (alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2) and per-trace reference
-// rm = (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c):
+// One leg of the linear path: returns rho_leg = u/u_c - 1 and sqrt(q) (for the weight), from
+// the per-z constants zk = (alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2) and the
+// per-trace reference rm = (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c).  q itself is evaluated directly,
+// so that it keeps its relative precision as R -> 0, where w = sqrt(q (q + 2)) has an
+// infinite slope; q - q_c comes from the cancellation-free form and only scales the result:
 //     q - q_c = alpha dP + alpha kappa R_c^2 + alpha (z^2 - z_c^2),   q = alpha dh^2 + alpha z^2,
 //     u/u_c - 1 = (q - q_c) (q/u_c + (q_c + 2)/u_c) / (w + w_c) + (q - q_c)/u_c.
 template <int WGT, bool FAST>
@@ -147,29 +121,6 @@ __device__ __forceinline__ float leg_delta_m(float dP, float dh2, const float4& 
     }
     const float gi = fmaf(fmaf(q, rm.w, rm.y), hrcp<FAST>(w + rm.z), rm.w);
     return dq * gi;
-}
-
-// One leg of the linear path: returns rho_leg = u/u_c - 1 and sqrt(q) (for the weight).
-// q itself is evaluated directly, q = alpha(z) (dh^2 + z^2), so that it keeps its relative
-// precision as R -> 0, where w = sqrt(q (q + 2)) has an infinite slope; the difference
-// q - q_c comes from the cancellation-free form and only scales the result.
-template <int WGT, bool FAST>
-__device__ __forceinline__ float leg_delta(float dP, float dh2, float z2, const ZConst& zc,
-                                           const LegRef& r, float qc2, float& sq)
-{
-    const float E = fmaf(zc.kappa, r.Rc2, zc.dz2);
-    const float dq = zc.alpha * (dP + E);
-    const float q = zc.alpha * (dh2 + z2);
-    float w;
-    if constexpr (WGT == 1) {
-        sq = hsqrt<FAST>(q);
-        w = sq * hsqrt<FAST>(q + 2.f);
-    } else {
-        sq = 0.f;
-        w = hsqrt<FAST>(q * (q + 2.f));
-    }
-    const float gq = fmaf(q + qc2, hrcp<FAST>(w + r.wc), 1.f);
-    return (dq * r.iuc) * gq;
 }
 
 // Smallest and largest one-way time from a surface point at horizontal distance [hmin, hmax]
@@ -203,20 +154,22 @@ struct TileBox {
     double cx, cy, cz;                    // FP64 centre (linear-path reference point)
 };
 
-// leg_delta plus q/w = sqrt(q / (q + 2)) for the velocity derivatives; sq = sqrt(q) always.
+// leg_delta_m plus q/w = sqrt(q / (q + 2)) for the velocity derivatives; sq = sqrt(q) always.
+// With fast math, one approximate 1/sqrt(q + 2) serves both w = sqrt(q) (q + 2)/sqrt(q + 2)
+// and q/w = sqrt(q)/sqrt(q + 2).
 template <bool FAST>
-__device__ __forceinline__ float leg_delta_grad(float dP, float dh2, float z2, const ZConst& zc,
-                                                const LegRef& r, float qc2, float& sq, float& qw)
+__device__ __forceinline__ float leg_delta_grad_m(float dP, float dh2, const float4& zk, const float4& rm,
+                                                  float& sq, float& qw)
 {
-    const float E = fmaf(zc.kappa, r.Rc2, zc.dz2);
-    const float dq = zc.alpha * (dP + E);
-    const float q = zc.alpha * (dh2 + z2);
+    const float dq = fmaf(zk.x, dP, fmaf(zk.y, rm.x, zk.z));
+    const float q = fmaf(zk.x, dh2, zk.w);
     sq = hsqrt<FAST>(q);
-    const float t = hsqrt<FAST>(q + 2.f);
-    const float w = sq * t;
-    qw = sq * hrcp<FAST>(t);
-    const float gq = fmaf(q + qc2, hrcp<FAST>(w + r.wc), 1.f);
-    return (dq * r.iuc) * gq;
+    const float q2 = q + 2.f;
+    const float ri = hrsqrt<FAST>(q2);
+    const float w = sq * (q2 * ri);
+    qw = sq * ri;
+    const float gi = fmaf(fmaf(q, rm.w, rm.y), hrcp<FAST>(w + rm.z), rm.w);
+    return dq * gi;
 }
 
 // Sample window [lo, hi] of one trace over a tile box, from the time bounds of both legs with

@@ -62,9 +62,13 @@ PIPE_MIX = {
     # mixed precision: U16 radial table + FP16 traces (k_migrate<table, obliquity, FP16, M=2, U16>)
     "3d-vz-100k-256cube-table-u16-f16": {"issue": 34.0, "fma": 19.3, "alu": 6.08, "xu": 2.23, "lsu": 5.5},
     "3d-vz-10k-256cube-table-u16-f16": {"issue": 34.0, "fma": 19.3, "alu": 6.08, "xu": 2.23, "lsu": 5.5},
-    # adjoint (k_demigrate) on the 10k-trace case of the headline geometry
-    "3d-vz-100k-256cube-demigrate": {"issue": 93.3, "fma": 61.4, "alu": 8.98, "xu": 7.14, "lsu": 8.19},
-    "3d-vz-10k-256cube-demigrate": {"issue": 93.3, "fma": 61.4, "alu": 8.98, "xu": 7.14, "lsu": 8.19},
+    # adjoint (k_demigrate) and gradient (k_vgrad), headline variants measured on the 10k case
+    "3d-vz-100k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
+    "3d-vz-10k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
+    "25d-vz-20k-512x400-demigrate": {"issue": 61.14, "fma": 38.93, "alu": 7.07, "xu": 4.42, "lsu": 6.53},
+    "3d-vz-100k-256cube-vgrad": {"issue": 68.94, "fma": 49.05, "alu": 7.79, "xu": 6.2, "lsu": 3.81},
+    "3d-vz-10k-256cube-vgrad": {"issue": 68.94, "fma": 49.05, "alu": 7.79, "xu": 6.2, "lsu": 3.81},
+    "25d-vz-20k-512x400-vgrad": {"issue": 73.09, "fma": 52.03, "alu": 8.4, "xu": 6.76, "lsu": 3.8},
     # persistent batched kernel, constant velocity (measured on the 8-job small batch)
     "batch64-3d-vz-f32": {"issue": 28.27, "fma": 16.59, "alu": 4.77, "xu": 2.51, "lsu": 3.91},
 }
@@ -73,7 +77,10 @@ PIPE_MIX = {
 # DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
 # (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
 TRAFFIC = {
+    "3d-vz-100k-256cube": 404150000 + 1060000000,
     "3d-vz-10k-256cube": 60817664 + 1030223000,
+    "3d-vz-10k-256cube-demigrate": 4731700000 + 8278000000,
+    "3d-vz-10k-256cube-vgrad": 1128400000 + 15700000,
     "3d-vz-40k-128cube": 145600000 + 94600000,
     "25d-vz-20k-512x400": 47900000 + 500000,
 }

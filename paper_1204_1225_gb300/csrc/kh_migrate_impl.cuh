@@ -50,7 +50,7 @@ struct __align__(16) MigSmem {
     float2 mid[STAGES][BMAX];   // FP32 midpoint (aperture test)
     int4 win[STAGES][BMAX];     // x: tau_ref - lo (float bits), y: smem index of sample lo minus
                                 // MAGIC_BITS, z/w: c_mid/c_half (float bits) of the valid range
-                                // 0 <= tau - lo <= hi - lo
+                                // 0 <= tau - lo <= hi - lo; sign bit of w: window not clipped
     float tb[STAGES][BMAX];     // lo dt + t0: T_s + T_r = (tau - lo) dt + tb (gradient mode)
     float4 zc[MAX_ZG * NZ];     // per-z constants: linear v, z_constants_m; constant v, (z^2, w_z);
                                 // table, (w_z, z^2)
@@ -148,6 +148,20 @@ __device__ __forceinline__ float sample_at(const TT* data, float th, int base, f
     return fmaf(f, d1 - d0, d0);
 }
 
+// sample_at without the validity test, for traces whose window is not clipped and whose every
+// lane and depth lies in the tile box (so 0 <= th <= hi - lo).  Indexes the ring from its
+// lead (base + LEAD); the unsigned clamp to the last readable pair keeps any index in bounds.
+template <typename TT>
+__device__ __forceinline__ float sample_unchecked(const TT* ring, float th, int base_lead, unsigned last)
+{
+    const float tm = __fadd_rd(th, MAGIC);
+    const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
+    const unsigned off = min((unsigned)(__float_as_int(tm) + base_lead), last);
+    const float d0 = to_f32<TT>(ring[off]);
+    const float d1 = to_f32<TT>(ring[off + 1]);
+    return fmaf(f, d1 - d0, d0);
+}
+
 // ------------------------------------------------------------------ producer warp
 // `n` is the number of stages this CTA's producer has filled before (mbarrier phases carry
 // over from one work item to the next in the persistent kernel); returns the new count.
@@ -176,6 +190,7 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
             const int k = cur + lane;
             bool ok = false;
             int lo = 0, hi = 0, lo_al = 0, len_al = 0;
+            bool clipped = true;
             float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
             float2 m = make_float2(0.f, 0.f);
             if (k < te) {
@@ -189,7 +204,7 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 }
                 if (ok) {
                     ok = trace_window(h, box, VEL == VK_TABLE ? (g.k == 0.0 ? VK_CONST : VK_LINEAR) : VEL,
-                                      g, lo, hi);
+                                      g, lo, hi, &clipped);
                     lo_al = lo & ~(g.elem_align - 1);
                     len_al = (hi + 1 - lo_al + g.elem_align - 1) & ~(g.elem_align - 1);
                 }
@@ -235,9 +250,11 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 S.mid[s][slot] = m;
                 S.tb[s][slot] = (float)((double)lo * g.dtd + g.t0d);
                 const float lim = (float)(hi - lo);
+                // w: c_half, its sign bit set when the window was not clipped at 0 or nt - 1 (then
+                // every point of the tile box has 0 <= tau - lo <= hi - lo by construction)
                 S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo)),
                                            dst + (lo - lo_al) - MAGIC_BITS, __float_as_int(0.5f * lim),
-                                           __float_as_int(0.5f * lim));
+                                           __float_as_int(0.5f * lim) | (clipped ? 0 : (int)0x80000000));
             }
             if (lane == 0 && bytes > 0) mbar_expect_tx(&S.full[s], (uint32_t)bytes);
             __syncwarp();
@@ -282,7 +299,7 @@ template <int VEL, int WGT, bool FAST, typename TT, int LPT, typename TB>
 __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const GeomParams& g,
                                             const TileShape& ts, int x0, int y0, int z0,
                                             const TileBox& box, int bin, float* __restrict__ image,
-                                            const WaitCfg& wc, const TB* tab, float2* srcc, int n)
+                                            const WaitCfg& wc, const TB* tab, float2* srcc, int cap, int n)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
@@ -301,6 +318,9 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     for (int i = 0; i < NZ; ++i) acc[i] = 0.f;
     float2* my_src = srcc + tid;
     unsigned psx = 0xffffffffu, psy = 0xffffffffu;   // source of the cached leg (NaN bits: none)
+    const TT* ring = data - LEAD;
+    const unsigned ring_last = (unsigned)(LEAD + STAGES * cap + SLACK - 2);   // the kernel's ring
+    const bool zfull = izb + NZ <= g.nz;   // all 16 depths of this thread lie in the grid
 
     bool failed = false;
     while (true) {
@@ -321,7 +341,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
             if (!__any_sync(0xffffffffu, inside)) continue;
             const float c0rel = __int_as_float(w.x);
             const float cmid = __int_as_float(w.z);
-            const float chalf = inside ? __int_as_float(w.w) : -1.f;
+            const float chalf = inside ? __int_as_float(w.w & 0x7fffffff) : -1.f;
             const float4 h = S.hdr[s][t];
             if constexpr (VEL == VK_TABLE) {
                 // T_s + T_r in table units from the radial table; the source leg is cached
@@ -393,17 +413,29 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
                 const float exr = cxf - h.z, eyr = cyf - h.w;
                 const float dhr2 = fmaf(exr, exr, eyr * eyr);
+                auto zloop = [&](auto checked) {
 #pragma unroll
-                for (int i = 0; i < NZ; ++i) {
-                    float sqr = 0.f;
-                    const float2 sv = my_src[i * CONSUMERS];   // (rho_s, gamma sqrt(q_s))
-                    const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zc[i], rr, sqr);
-                    const float rho = fmaf(sv.x, rho_r, sv.x + rho_r);   // U/U_c - 1
-                    const float th = tau_poly<LPT>(rho, g, c0rel);
-                    const float val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
-                    if constexpr (WGT == 1) acc[i] = fmaf(fmaf(zg[i], sqr, sv.y), val, acc[i]);
-                    else acc[i] += val;
-                }
+                    for (int i = 0; i < NZ; ++i) {
+                        float sqr = 0.f;
+                        const float2 sv = my_src[i * CONSUMERS];   // (rho_s, gamma sqrt(q_s))
+                        const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zc[i], rr, sqr);
+                        const float rho = fmaf(sv.x, rho_r, sv.x + rho_r);   // U/U_c - 1
+                        const float th = tau_poly<LPT>(rho, g, c0rel);
+                        float val;
+                        if constexpr (decltype(checked)::value)
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                        else
+                            val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        if constexpr (WGT == 1) acc[i] = fmaf(fmaf(zg[i], sqr, sv.y), val, acc[i]);
+                        else acc[i] += val;
+                    }
+                };
+                // unclipped window, and every lane inside the aperture with all 16 depths in the
+                // grid: every tau is inside the window, no validity test is needed
+                if (w.w < 0 && __all_sync(0xffffffffu, inside && zfull))
+                    zloop(std::false_type());
+                else
+                    zloop(std::true_type());
             }
         }
         __syncwarp();
@@ -493,7 +525,7 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
             if (!__any_sync(0xffffffffu, inside)) continue;
             const float c0rel = __int_as_float(w.x);
             const float cmid = __int_as_float(w.z);
-            const float chalf = inside ? __int_as_float(w.w) : -1.f;
+            const float chalf = inside ? __int_as_float(w.w & 0x7fffffff) : -1.f;
             const float tbase = S.tb[s][t];
             const float4 h = S.hdr[s][t];
             float g0 = 0.f, g1 = 0.f;
@@ -643,7 +675,8 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
         mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
                                     box, wc, 0);
     } else if constexpr (MODE == 0) {
-        mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, srcc, 0);
+        mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, srcc, cap,
+                                                  0);
     } else {
         vg_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, partial, wc);
     }
@@ -800,7 +833,7 @@ __global__ void __launch_bounds__(THREADS, 2)
                                       tr.bin_start[bin], tr.bin_start[bin + 1], box, wc, n);
         } else {
             n = mig_consumer<VEL, WGT, FAST, TT, LPT, float>(S, data, g, ts, x0, y0, z0, box, bin,
-                                                             jobs[w.x].image, wc, nullptr, srcc, n);
+                                                             jobs[w.x].image, wc, nullptr, srcc, cap, n);
         }
     }
 }

@@ -175,7 +175,7 @@ __device__ __forceinline__ float leg_delta_grad_m(float dP, float dh2, const flo
 // Sample window [lo, hi] of one trace over a tile box, from the time bounds of both legs with
 // a slack of 2 + 2e-4 |tau| samples for FP32 rounding; false if no valid sample can reach the box.
 __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box, int vel,
-                                             const GeomParams& g, int& lo, int& hi)
+                                             const GeomParams& g, int& lo, int& hi, bool* clipped = nullptr)
 {
     const float v0 = (float)g.v0, kf = (float)g.k, inv_dt = 1.f / g.dt;
     float hs0, hs1, hr0, hr1, ts0, ts1, tr0, tr1;
@@ -190,6 +190,7 @@ __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box
     if (!(fhi >= 1.f && flo <= (float)(g.nt - 2))) return false;   // also NaN
     lo = flo < 0.f ? 0 : (int)flo;
     hi = fhi > (float)(g.nt - 1) ? g.nt - 1 : (int)fhi;
+    if (clipped) *clipped = flo < 0.f || fhi > (float)(g.nt - 1);
     return hi > lo;
 }
 

@@ -55,13 +55,13 @@ LANES_PER_SM_CLK = {"issue": 128, "fma": 128, "alu": 64, "xu": 16, "lsu": 32}
 # k_migrate per variant; the 100k-trace 256^3 workload runs the variant measured on its
 # 10k-trace case: same grid, tile and 6-term fit).
 PIPE_MIX = {
-    "3d-vz-100k-256cube": {"issue": 41.05, "fma": 27.15, "alu": 4.76, "xu": 3.17, "lsu": 4.74},
-    "3d-vz-10k-256cube": {"issue": 41.05, "fma": 27.15, "alu": 4.76, "xu": 3.17, "lsu": 4.74},
-    "3d-vz-40k-128cube": {"issue": 46.21, "fma": 30.27, "alu": 6.59, "xu": 3.25, "lsu": 4.85},
-    "25d-vz-20k-512x400": {"issue": 45.26, "fma": 31.83, "alu": 5.05, "xu": 2.37, "lsu": 4.82},
+    "3d-vz-100k-256cube": {"issue": 38.87, "fma": 25.91, "alu": 3.28, "xu": 3.17, "lsu": 4.82},
+    "3d-vz-10k-256cube": {"issue": 38.87, "fma": 25.91, "alu": 3.28, "xu": 3.17, "lsu": 4.82},
+    "3d-vz-40k-128cube": {"issue": 42.24, "fma": 28.66, "alu": 3.48, "xu": 3.25, "lsu": 5.26},
+    "25d-vz-20k-512x400": {"issue": 42.91, "fma": 30.46, "alu": 3.62, "xu": 2.37, "lsu": 4.87},
     # mixed precision: U16 radial table + FP16 traces (k_migrate<table, obliquity, FP16, M=2, U16>)
-    "3d-vz-100k-256cube-table-u16-f16": {"issue": 34.0, "fma": 19.3, "alu": 6.08, "xu": 2.23, "lsu": 5.5},
-    "3d-vz-10k-256cube-table-u16-f16": {"issue": 34.0, "fma": 19.3, "alu": 6.08, "xu": 2.23, "lsu": 5.5},
+    "3d-vz-100k-256cube-table-u16-f16": {"issue": 34.07, "fma": 19.3, "alu": 6.15, "xu": 2.23, "lsu": 5.5},
+    "3d-vz-10k-256cube-table-u16-f16": {"issue": 34.07, "fma": 19.3, "alu": 6.15, "xu": 2.23, "lsu": 5.5},
     # adjoint (k_demigrate) and gradient (k_vgrad), headline variants measured on the 10k case
     "3d-vz-100k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
     "3d-vz-10k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
@@ -77,12 +77,12 @@ PIPE_MIX = {
 # DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
 # (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
 TRAFFIC = {
-    "3d-vz-100k-256cube": 404150000 + 1060000000,
-    "3d-vz-10k-256cube": 60817664 + 1030223000,
+    "3d-vz-10k-256cube": 57967360 + 1027189504,
     "3d-vz-10k-256cube-demigrate": 4731700000 + 8278000000,
     "3d-vz-10k-256cube-vgrad": 1128400000 + 15700000,
-    "3d-vz-40k-128cube": 145600000 + 94600000,
-    "25d-vz-20k-512x400": 47900000 + 500000,
+    "3d-vz-40k-128cube": 143150080 + 94437120,
+    "25d-vz-20k-512x400": 47247616 + 350976,
+    "3d-vz-10k-256cube-table-u16-f16": 36481024 + 1023988736,
 }
 
 

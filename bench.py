@@ -77,6 +77,7 @@ PIPE_MIX = {
 # DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
 # (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
 TRAFFIC = {
+    "3d-vz-100k-256cube": 395937472 + 1043667072,
     "3d-vz-10k-256cube": 57967360 + 1027189504,
     "3d-vz-10k-256cube-demigrate": 4731700000 + 8278000000,
     "3d-vz-10k-256cube-vgrad": 1128400000 + 15700000,

@@ -55,10 +55,8 @@ LANES_PER_SM_CLK = {"issue": 128, "fma": 128, "alu": 64, "xu": 16, "lsu": 32}
 # k_migrate per variant; the 100k-trace 256^3 workload runs the variant measured on its
 # 10k-trace case: same grid, tile and 6-term fit).
 PIPE_MIX = {
-    "3d-vz-100k-256cube": {"issue": 38.87, "fma": 25.91, "alu": 3.28, "xu": 3.17, "lsu": 4.82},
-    "3d-vz-10k-256cube": {"issue": 38.87, "fma": 25.91, "alu": 3.28, "xu": 3.17, "lsu": 4.82},
-    "3d-vz-40k-128cube": {"issue": 42.24, "fma": 28.66, "alu": 3.48, "xu": 3.25, "lsu": 5.26},
-    "25d-vz-20k-512x400": {"issue": 42.91, "fma": 30.46, "alu": 3.62, "xu": 2.37, "lsu": 4.87},
+    "3d-vz-100k-256cube": {"issue": 35.39, "fma": 22.90, "alu": 3.28, "xu": 3.17, "lsu": 4.49},
+    "3d-vz-10k-256cube": {"issue": 35.39, "fma": 22.90, "alu": 3.28, "xu": 3.17, "lsu": 4.49},
     # mixed precision: U16 radial table + FP16 traces (k_migrate<table, obliquity, FP16, M=2, U16>)
     "3d-vz-100k-256cube-table-u16-f16": {"issue": 34.07, "fma": 19.3, "alu": 6.15, "xu": 2.23, "lsu": 5.5},
     "3d-vz-10k-256cube-table-u16-f16": {"issue": 34.07, "fma": 19.3, "alu": 6.15, "xu": 2.23, "lsu": 5.5},
@@ -77,12 +75,9 @@ PIPE_MIX = {
 # DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
 # (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
 TRAFFIC = {
-    "3d-vz-100k-256cube": 395937472 + 1043667072,
-    "3d-vz-10k-256cube": 57967360 + 1027189504,
+    "3d-vz-10k-256cube": 60187392 + 1027593984,
     "3d-vz-10k-256cube-demigrate": 4731700000 + 8278000000,
     "3d-vz-10k-256cube-vgrad": 1128400000 + 15700000,
-    "3d-vz-40k-128cube": 143150080 + 94437120,
-    "25d-vz-20k-512x400": 47247616 + 350976,
     "3d-vz-10k-256cube-table-u16-f16": 36481024 + 1023988736,
 }
 

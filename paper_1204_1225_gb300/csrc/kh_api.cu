@@ -302,11 +302,11 @@ static GeomParams geom_of(const kh_desc& d)
 // and half-width), by interpolation at the Chebyshev nodes of [-1, 1] (well conditioned in
 // t); then checks the FP32-coefficient evaluation against log1p in double on a dense grid.
 // Returns false if the interval is too wide for the term count.
-static bool fit_log1p(double lo, double hi, int terms, float* coef, float* scale, float* offset,
-                      double tol = 2e-9)
+static bool cheb_q(double lo, double hi, int terms, double* cq, double& m, double& h)
 {
     const int n = terms - 1;
-    const double m = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
+    m = 0.5 * (lo + hi);
+    h = 0.5 * (hi - lo);
     double A[LP_LONG][LP_LONG + 1];
     for (int i = 0; i < n; ++i) {
         const double t = std::cos((2.0 * i + 1.0) * M_PI / (2.0 * n));
@@ -336,12 +336,20 @@ static bool fit_log1p(double lo, double hi, int terms, float* coef, float* scale
             for (int j = c; j <= n; ++j) A[r][j] -= f * A[c][j];
         }
     }
-    double cq[LP_LONG];
     for (int r = n - 1; r >= 0; --r) {
         double v = A[r][n];
         for (int j = r + 1; j < n; ++j) v -= A[r][j] * cq[j];
         cq[r] = v / A[r][r];
     }
+    return true;
+}
+
+static bool fit_log1p(double lo, double hi, int terms, float* coef, float* scale, float* offset,
+                      double tol = 2e-9)
+{
+    const int n = terms - 1;
+    double cq[LP_LONG], m, h;
+    if (!cheb_q(lo, hi, terms, cq, m, h)) return false;
     coef[0] = 1.f;
     for (int j = 0; j < n; ++j) coef[j + 1] = (float)cq[j];
     for (int j = terms; j < LP_LONG; ++j) coef[j] = 0.f;   // kernels of a longer length read zeros
@@ -356,6 +364,48 @@ static bool fit_log1p(double lo, double hi, int terms, float* coef, float* scale
         worst = std::max(worst, std::fabs(x * (1.0 + x * p) - std::log1p(x)));
     }
     return worst <= tol;
+}
+
+// The per-leg fit of the migration kernel on [expm1(-b), expm1(b)], scaled by c1 (coefc[0] = c1,
+// coefc[j + 1] = c1 Q_j, zero beyond `terms`).  Up to LG_MONO terms, Q is re-expanded in x itself,
+// t^j = ((x - m)/h)^j = sum_k C(j, k) x^k (-m)^(j - k) / h^j, and the budget check evaluates Q
+// by FP32 Horner steps in x as the kernel does (*s = 1, *o = 0); longer fits keep fit_log1p's
+// shifted variable.
+static bool fit_leg_log(double b, int terms, double c1, float* coefc, float* s, float* o, double tol)
+{
+    const double lo = std::expm1(-b), hi = std::expm1(b);
+    const int n = terms - 1;
+    if (terms > LG_MONO) {
+        float lp[LP_LONG];
+        if (!fit_log1p(lo, hi, terms, lp, s, o, tol)) return false;
+        for (int j = 0; j < LP_LONG; ++j) coefc[j] = (float)(c1 * lp[j]);
+        return true;
+    }
+    double cq[LP_LONG], m, h;
+    if (!cheb_q(lo, hi, terms, cq, m, h)) return false;
+    double d[LP_LONG] = {0.0};
+    for (int j = 0; j < n; ++j) {
+        double binom = 1.0;   // C(j, k)
+        for (int k = 0; k <= j; ++k) {
+            d[k] += cq[j] * binom * std::pow(-m, j - k) / std::pow(h, j);
+            binom = binom * (j - k) / (k + 1);
+        }
+    }
+    float q[LP_LONG];
+    for (int k = 0; k < n; ++k) q[k] = (float)d[k];
+    double worst = 0.0;
+    for (int i = 0; i <= 4000; ++i) {
+        const float x = (float)(lo + (hi - lo) * i / 4000.0);
+        float p = q[n - 1];
+        for (int k = n - 2; k >= 0; --k) p = std::fma(p, x, q[k]);
+        worst = std::max(worst, std::fabs((double)x * (1.0 + (double)x * p) - std::log1p((double)x)));
+    }
+    if (worst > tol) return false;
+    coefc[0] = (float)c1;
+    for (int j = 1; j < LP_LONG; ++j) coefc[j] = j <= n ? (float)(c1 * d[j - 1]) : 0.f;
+    *s = 1.f;
+    *o = 0.f;
+    return true;
 }
 
 // Linear v(z): the bound on rho = U/U_c - 1 over a tile (|dT| <= distance / v_min along the
@@ -375,6 +425,7 @@ static double rho_bound(const kh_desc& d, const GeomParams& g, int cx, int cy, i
 static kh_status prepare_linear(const kh_desc& d, const TileShape& t, GeomParams& g)
 {
     g.lp_terms = LP_SHORT;
+    g.lg_terms = LP_SHORT;
     if (g.k == 0.0 || d.vel == KH_VEL_TABLE) return KH_OK;
     const double b = rho_bound(d, g, t.cx, t.cy, t.cz);
     g.rho_max = (float)std::expm1(b);
@@ -385,7 +436,14 @@ static kh_status prepare_linear(const kh_desc& d, const TileShape& t, GeomParams
         if (fit_log1p(std::expm1(-b), std::expm1(b), g.lp_terms, g.lp, &g.lp_s, &g.lp_o, tol)) {
             const double c1 = (double)g.C1 + (double)g.C1lo;
             for (int j = 0; j < LP_LONG; ++j) g.lpc[j] = (float)(c1 * g.lp[j]);
-            return KH_OK;
+            // per-leg fit of the migration kernel: each leg's |ln(1 + rho)| is bounded by half
+            // of the two-leg bound, and each leg takes half of the budget
+            const double bl = 0.5 * (b - 1e-6) + 1e-6;
+            for (int k = 0; k < N_LG_TERMS; ++k) {
+                g.lg_terms = LG_TERMS[k];
+                if (fit_leg_log(bl, g.lg_terms, c1, g.lgc, &g.lg_s, &g.lg_o, 0.5 * tol)) return KH_OK;
+            }
+            break;
         }
     }
     return fail(KH_ERR_UNSUPPORTED, "tile too large for the v(z) delta evaluation (rho up to %.3f); "

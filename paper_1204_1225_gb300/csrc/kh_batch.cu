@@ -35,7 +35,7 @@ struct kh_batch_s {
     // The sorted work list is cut into parts of one ln(1 + rho) fit length each (shortest
     // first); each part is one launch of the kernel compiled for that length.
     struct Part {
-        int lp_terms, first, count, ctas;
+        int lg_terms, first, count, ctas;
     };
     std::vector<Part> parts;
     double work = 0.0;             // estimated contributions: culled traces x points, summed
@@ -110,12 +110,12 @@ struct Layout {
 
 int dtype_bytes(kh_dtype t) { return t == KH_F32 ? 4 : 2; }
 
-// Index of a fit length in LP_TERMS (constant and table jobs report LP_SHORT).
-int lp_class(int terms)
+// Index of a per-leg fit length in LG_TERMS (constant and table jobs fall in the last class).
+int lg_class(int terms)
 {
-    for (int i = 0; i < N_LP_TERMS; ++i)
-        if (LP_TERMS[i] == terms) return i;
-    return N_LP_TERMS - 1;
+    for (int i = 0; i < N_LG_TERMS; ++i)
+        if (LG_TERMS[i] == terms) return i;
+    return N_LG_TERMS - 1;
 }
 
 }  // namespace
@@ -197,7 +197,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     if (n_items > (size_t)INT32_MAX) return bfail(KH_ERR_UNSUPPORTED, "more than 2^31 work items");
     const size_t o_jobs = L.take(sizeof(BatchJob) * njobs);
     const size_t o_items = L.take(sizeof(int4) * n_items);
-    const size_t o_next = L.take(N_LP_TERMS * sizeof(int));
+    const size_t o_next = L.take(N_LG_TERMS * sizeof(int));
     const size_t o_status = L.take(sizeof(int));
     const size_t o_cull = L.take(sizeof(int) * std::max<size_t>(n_cull, 1));
 
@@ -291,7 +291,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
                     for (int bin = 0; bin < d.n_bins; ++bin) {
                         const int c = cull[cull_at[j] + (size_t)bin * ntxy + tyi * t.tiles_x + txi];
                         items[k] = make_int4(j, tile, bin, 0);
-                        cls[k] = lp_class(gs[j].lp_terms);
+                        cls[k] = lg_class(gs[j].lg_terms);
                         cost[k] = (double)cols * zs * (c + 4);
                         job_cost[j] += cost[k];
                         work += (double)cols * zs * c;
@@ -356,13 +356,13 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     gm.table = nullptr;
     b->g_max = gm;
     WaitCfg wc{b->d_status, b->wait_polls, WAIT_NS};
-    for (int c = 0, first = 0; c < N_LP_TERMS; ++c) {
+    for (int c = 0, first = 0; c < N_LG_TERMS; ++c) {
         int count = 0;
         for (size_t i = 0; i < n_items; ++i) count += cls[i] == c ? 1 : 0;
         if (count == 0) continue;
-        kh_batch_s::Part part{LP_TERMS[c], first, count, 0};
+        kh_batch_s::Part part{LG_TERMS[c], first, count, 0};
         e = launch_migrate_batched(gm, b->d_jobs, b->d_items + first, count, b->d_next + b->parts.size(), vel,
-                                   weight, fast, part.lp_terms, tdt, wc, 0, &part.ctas, s);
+                                   weight, fast, part.lg_terms, tdt, wc, 0, &part.ctas, s);
         if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: kernel set-up"));
         b->ctas = std::max(b->ctas, part.ctas);
         b->parts.push_back(part);
@@ -412,13 +412,13 @@ kh_status kirchhoff_migrate_batched(kh_batch b, void* cuda_stream)
         ++b->launches;
     }
     if (b->n_items == 0) return KH_OK;
-    if ((e = cudaMemsetAsync(b->d_next, 0, N_LP_TERMS * sizeof(int), s)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(b->d_next, 0, N_LG_TERMS * sizeof(int), s)) != cudaSuccess)
         return set_cuda_error(e, "kirchhoff_migrate_batched: counter reset");
     WaitCfg wc{b->d_status, b->wait_polls, WAIT_NS};
     for (size_t i = 0; i < b->parts.size(); ++i) {
         const kh_batch_s::Part& part = b->parts[i];
         e = launch_migrate_batched(b->g_max, b->d_jobs, b->d_items + part.first, part.count, b->d_next + i, b->vel,
-                                   b->weight, b->fast, part.lp_terms, b->tdtype, wc, part.ctas, nullptr, s);
+                                   b->weight, b->fast, part.lg_terms, b->tdtype, wc, part.ctas, nullptr, s);
         ++b->launches;
         if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_migrate_batched: persistent kernel");
     }

@@ -3,9 +3,9 @@
 
 namespace kh {
 cudaError_t launch_batched_bf16(const GeomParams& gm, const BatchJob* jobs, const int4* items, int n_items, int* next,
-                               int vel, int weight, int fast, int lp_terms, const WaitCfg& w, int ctas, int* ctas_out,
+                               int vel, int weight, int fast, int lg_terms, const WaitCfg& w, int ctas, int* ctas_out,
                                cudaStream_t s)
 {
-    return launch_batched_dtype<__nv_bfloat16>(gm, jobs, items, n_items, next, vel, weight, fast, lp_terms, w, ctas, ctas_out, s);
+    return launch_batched_dtype<__nv_bfloat16>(gm, jobs, items, n_items, next, vel, weight, fast, lg_terms, w, ctas, ctas_out, s);
 }
 }  // namespace kh

@@ -29,6 +29,12 @@ constexpr int LP_TERMS[] = {6, 8, 10, 12, 20};
 constexpr int N_LP_TERMS = 5;
 constexpr int LP_SHORT = 12;
 constexpr int LP_LONG = 20;
+// The migration kernel evaluates ln(1 + rho) per leg (rho = U/U_c - 1 of one leg, half the
+// range of the two-leg rho) and caches the source leg's term: lengths up to LG_MONO are
+// monomial in rho (no change of variable), longer ones use the shifted variable t.
+constexpr int LG_TERMS[] = {4, 5, 6, 8, 12, 20};
+constexpr int N_LG_TERMS = 6;
+constexpr int LG_MONO = 8;
 
 // Default wait limit: polls of mbarrier.try_wait, each checked against a 2 s wall clock.
 constexpr long long WAIT_NS = 2000000000LL;
@@ -57,6 +63,11 @@ struct GeomParams {
     float lpc[LP_LONG];      // lp scaled by C1 + C1lo (the migration kernel forms tau from them)
     float lp_s, lp_o;
     int lp_terms;            // one of LP_TERMS; lp[lp_terms..LP_LONG-1] are zero
+    float lgc[LP_LONG];      // per-leg fit, scaled by C1 + C1lo: ln(1 + rho) = rho (1 + rho Q),
+                             // Q = sum_j lgc[j + 1] / C1 x^j with x = rho (lg_terms <= LG_MONO)
+                             // or x = rho lg_s + lg_o; zero beyond lg_terms
+    float lg_s, lg_o;
+    int lg_terms;            // one of LG_TERMS
     float rho_max;           // |rho| bound the polynomial was fitted for
     float C1, C1lo;          // tau - tau_ref = L * (C1 + C1lo) with L = R_s + R_r (constant v,
                              // tau_ref = -t0/dt) or ln(U/U_c) (linear v); C1lo = FP32 rounding
@@ -117,12 +128,12 @@ struct BatchJob {
 
 // The persistent kernel over `n_items` work items (job, tile, bin, -) taken in list order from
 // the counter `*next` (zeroed before the launch).  `g_max` sizes the shared-memory ring (its
-// nt is the largest of the jobs'); vel_kind/weight/fast/lp_terms/trace dtype are common to
+// nt is the largest of the jobs'); vel_kind/weight/fast/lg_terms/trace dtype are common to
 // all jobs of the launch.  `ctas` <= 0 launches nothing: it sets the kernel's shared-memory attribute and returns
 // the occupancy-sized grid through `ctas_out` (call it once before launching with that grid).
 cudaError_t launch_migrate_batched(const GeomParams& g_max, const BatchJob* jobs, const int4* items,
                                    int n_items, int* next, int vel_kind, int weight, int fast,
-                                   int lp_terms, int trace_dtype, const WaitCfg& w, int ctas,
+                                   int lg_terms, int trace_dtype, const WaitCfg& w, int ctas,
                                    int* ctas_out, cudaStream_t s);
 // Velocity gradient: the migration kernel in gradient mode (image as input), per-warp FP64
 // partials [gridDim.y * gridDim.x * 8][2], then one fixed-order sum scaled by 1/dt.

@@ -24,19 +24,19 @@ KH_BATCHED_DECL(launch_batched_bf16)
 size_t migrate_smem_bytes(const GeomParams& g) { return mig_smem_bytes(g); }
 
 cudaError_t launch_migrate_batched(const GeomParams& gm, const BatchJob* jobs, const int4* items, int n_items,
-                                   int* next, int vel_kind, int weight, int fast, int lp_terms,
+                                   int* next, int vel_kind, int weight, int fast, int lg_terms,
                                    int trace_dtype, const WaitCfg& w, int ctas, int* ctas_out,
                                    cudaStream_t s)
 {
     switch (trace_dtype) {
         case KH_F32:
-            return launch_batched_f32(gm, jobs, items, n_items, next, vel_kind, weight, fast, lp_terms, w, ctas,
+            return launch_batched_f32(gm, jobs, items, n_items, next, vel_kind, weight, fast, lg_terms, w, ctas,
                                       ctas_out, s);
         case KH_F16:
-            return launch_batched_f16(gm, jobs, items, n_items, next, vel_kind, weight, fast, lp_terms, w, ctas,
+            return launch_batched_f16(gm, jobs, items, n_items, next, vel_kind, weight, fast, lg_terms, w, ctas,
                                       ctas_out, s);
         case KH_BF16:
-            return launch_batched_bf16(gm, jobs, items, n_items, next, vel_kind, weight, fast, lp_terms, w, ctas,
+            return launch_batched_bf16(gm, jobs, items, n_items, next, vel_kind, weight, fast, lg_terms, w, ctas,
                                        ctas_out, s);
         default: return cudaErrorInvalidValue;
     }

@@ -293,8 +293,11 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
 //
 // Linear v(z): the source leg of a contribution depends only on the column and the source
 // position, and traces of one bin arrive shot by shot (the bin sort is stable), so each thread
-// keeps (rho_s, sqrt(q_s)) of its 16 depths for the current source in `srcc` (its own slots,
-// [i * CONSUMERS + tid]) and recomputes them only when the (warp-uniform) source changes.
+// keeps (C1 ln(1 + rho_s), sqrt(q_s)) of its 16 depths for the current source in `srcc` (its
+// own slots, [i * CONSUMERS + tid]) and recomputes them only when the (warp-uniform) source
+// changes.  tau - lo = c0rel + C1 ln(1 + rho_s) + C1 ln(1 + rho_r) with c0rel = tau_ref - lo,
+// each leg's logarithm from the per-leg fit (LPT = its length).  The weight's gamma(z)
+// multiplies each depth's sum once, before the store.
 template <int VEL, int WGT, bool FAST, typename TT, int LPT, typename TB>
 __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const GeomParams& g,
                                             const TileShape& ts, int x0, int y0, int z0,
@@ -404,7 +407,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                     for (int i = 0; i < NZ; ++i) {
                         float sqs = 0.f;
                         const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zc[i], rs, sqs);
-                        my_src[i * CONSUMERS] = make_float2(rho_s, WGT == 1 ? zg[i] * sqs : 0.f);
+                        my_src[i * CONSUMERS] = make_float2(leg_log<LPT>(rho_s, g, 0.f), sqs);
                     }
                     psx = __float_as_uint(h.x);
                     psy = __float_as_uint(h.y);
@@ -417,16 +420,16 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         float sqr = 0.f;
-                        const float2 sv = my_src[i * CONSUMERS];   // (rho_s, gamma sqrt(q_s))
+                        const float2 sv = my_src[i * CONSUMERS];   // (C1 ln(1 + rho_s), sqrt(q_s))
                         const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zc[i], rr, sqr);
-                        const float rho = fmaf(sv.x, rho_r, sv.x + rho_r);   // U/U_c - 1
-                        const float th = tau_poly<LPT>(rho, g, c0rel);
+                        const float th = leg_log<LPT>(rho_r, g, c0rel + sv.x);
                         float val;
                         if constexpr (decltype(checked)::value)
                             val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
-                        if constexpr (WGT == 1) acc[i] = fmaf(fmaf(zg[i], sqr, sv.y), val, acc[i]);
+                        // gamma(z) multiplies the sum once, at the store
+                        if constexpr (WGT == 1) acc[i] = fmaf(sv.y + sqr, val, acc[i]);
                         else acc[i] += val;
                     }
                 };
@@ -448,6 +451,10 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
         return n;
     }
     if (!col_ok) return n;
+    if constexpr (VEL == VK_LINEAR && WGT == 1) {
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) acc[i] *= zg[i];
+    }
     float* out = image + (((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb;
     const bool vec = ((g.nz & 3) == 0) && (izb + NZ <= g.nz) &&
                      ((reinterpret_cast<uintptr_t>(image) & 15) == 0);
@@ -712,7 +719,7 @@ static cudaError_t launch_migrate_t(const GeomParams& g, const TileShape& t, con
         return cudaGetLastError();
     };
     if constexpr (VEL == VK_LINEAR) {
-        return with_lp<FAST>(g.lp_terms,
+        return with_lg<FAST>(g.lg_terms,
                              [&](auto L) { return go(k_migrate<VEL, WGT, FAST, TT, decltype(L)::value>); });
     } else if constexpr (VEL == VK_TABLE) {
         // the LPT slot carries the table's depth-node stride M
@@ -840,7 +847,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 
 template <int VEL, int WGT, bool FAST, typename TT>
 static cudaError_t launch_batched_t(const GeomParams& gm, const BatchJob* jobs, const int4* items,
-                                   int n_items, int* next, int lp_terms, const WaitCfg& w, int ctas,
+                                   int n_items, int* next, int lg_terms, const WaitCfg& w, int ctas,
                                    int* ctas_out, cudaStream_t s)
 {
     const size_t smem = mig_smem_bytes(gm);
@@ -864,7 +871,7 @@ static cudaError_t launch_batched_t(const GeomParams& gm, const BatchJob* jobs, 
         return cudaGetLastError();
     };
     if constexpr (VEL == VK_LINEAR)
-        return with_lp<FAST>(lp_terms,
+        return with_lg<FAST>(lg_terms,
                              [&](auto L) { return go(k_migrate_batched<VEL, WGT, FAST, TT, decltype(L)::value>); });
     else
         return go(k_migrate_batched<VEL, WGT, FAST, TT, LP_SHORT>);
@@ -872,19 +879,19 @@ static cudaError_t launch_batched_t(const GeomParams& gm, const BatchJob* jobs, 
 
 template <typename TT>
 cudaError_t launch_batched_dtype(const GeomParams& gm, const BatchJob* jobs, const int4* items, int n_items,
-                                 int* next, int vel, int weight, int fast, int lp_terms, const WaitCfg& w,
+                                 int* next, int vel, int weight, int fast, int lg_terms, const WaitCfg& w,
                                  int ctas, int* ctas_out, cudaStream_t s)
 {
     const int key = vel * 4 + weight * 2 + (fast ? 1 : 0);
     switch (key) {
-        case 0: return launch_batched_t<VK_CONST, 0, false, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
-        case 1: return launch_batched_t<VK_CONST, 0, true, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
-        case 2: return launch_batched_t<VK_CONST, 1, false, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
-        case 3: return launch_batched_t<VK_CONST, 1, true, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
-        case 4: return launch_batched_t<VK_LINEAR, 0, false, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
-        case 5: return launch_batched_t<VK_LINEAR, 0, true, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
-        case 6: return launch_batched_t<VK_LINEAR, 1, false, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
-        case 7: return launch_batched_t<VK_LINEAR, 1, true, TT>(gm, jobs, items, n_items, next, lp_terms, w, ctas, ctas_out, s);
+        case 0: return launch_batched_t<VK_CONST, 0, false, TT>(gm, jobs, items, n_items, next, lg_terms, w, ctas, ctas_out, s);
+        case 1: return launch_batched_t<VK_CONST, 0, true, TT>(gm, jobs, items, n_items, next, lg_terms, w, ctas, ctas_out, s);
+        case 2: return launch_batched_t<VK_CONST, 1, false, TT>(gm, jobs, items, n_items, next, lg_terms, w, ctas, ctas_out, s);
+        case 3: return launch_batched_t<VK_CONST, 1, true, TT>(gm, jobs, items, n_items, next, lg_terms, w, ctas, ctas_out, s);
+        case 4: return launch_batched_t<VK_LINEAR, 0, false, TT>(gm, jobs, items, n_items, next, lg_terms, w, ctas, ctas_out, s);
+        case 5: return launch_batched_t<VK_LINEAR, 0, true, TT>(gm, jobs, items, n_items, next, lg_terms, w, ctas, ctas_out, s);
+        case 6: return launch_batched_t<VK_LINEAR, 1, false, TT>(gm, jobs, items, n_items, next, lg_terms, w, ctas, ctas_out, s);
+        case 7: return launch_batched_t<VK_LINEAR, 1, true, TT>(gm, jobs, items, n_items, next, lg_terms, w, ctas, ctas_out, s);
         default: return cudaErrorInvalidValue;
     }
 }

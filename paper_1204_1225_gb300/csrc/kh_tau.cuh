@@ -47,6 +47,28 @@ cudaError_t with_lp(int terms, F&& f)
     }
 }
 
+// Per-leg fit lengths of the migration kernel: every length of LG_TERMS with the fast
+// math variants; the IEEE variants take LG_MONO (monomial) or LP_LONG (shifted), the
+// coefficients beyond the fitted length being zero.
+template <bool FAST, typename F>
+cudaError_t with_lg(int terms, F&& f)
+{
+    if constexpr (FAST) {
+        switch (terms) {
+            case 4: return f(std::integral_constant<int, 4>());
+            case 5: return f(std::integral_constant<int, 5>());
+            case 6: return f(std::integral_constant<int, 6>());
+            case 8: return f(std::integral_constant<int, 8>());
+            case 12: return f(std::integral_constant<int, 12>());
+            case 20: return f(std::integral_constant<int, 20>());
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        if (terms <= LG_MONO) return f(std::integral_constant<int, LG_MONO>());
+        if (terms <= LP_LONG) return f(std::integral_constant<int, LP_LONG>());
+        return cudaErrorInvalidValue;
+    }
+}
 
 // Per-(tile, trace) data of one leg, FP32 copies of FP64 values.
 struct LegRef {
@@ -97,6 +119,18 @@ __device__ __forceinline__ float tau_poly(float rho, const GeomParams& g, float 
 #pragma unroll
     for (int i = NT - 2; i >= 1; --i) p = fmaf(p, t, g.lpc[i]);
     return fmaf(rho, fmaf(rho, p, g.C1), c0rel);
+}
+
+// base + C1 ln(1 + rho) for one leg from the per-leg fit (lgc = C1-scaled coefficients):
+// Horner in rho itself for NT <= LG_MONO, in t = rho lg_s + lg_o for the longer fits.
+template <int NT>
+__device__ __forceinline__ float leg_log(float rho, const GeomParams& g, float base)
+{
+    const float x = (NT <= LG_MONO) ? rho : fmaf(rho, g.lg_s, g.lg_o);
+    float p = g.lgc[NT - 1];
+#pragma unroll
+    for (int i = NT - 2; i >= 1; --i) p = fmaf(p, x, g.lgc[i]);
+    return fmaf(rho, fmaf(rho, p, g.C1), base);
 }
 
 // One leg of the linear path: returns rho_leg = u/u_c - 1 and sqrt(q) (for the weight), from

@@ -225,8 +225,19 @@ KH_API kh_status kirchhoff_sync(kh_plan p, void* cuda_stream);
  *                     persistent kernel over the work list; 1 = every job's own migration
  *                     kernel on library-owned streams forked from and joined to the caller's
  *                     stream (one graph with parallel branches when captured), so that the
- *                     block scheduler fills one job's tail with the next job's tiles. */
-typedef enum { KH_OPT_WAIT_POLLS = 1, KH_OPT_FAST_MATH = 2, KH_OPT_TILE = 3, KH_OPT_BATCH_MODE = 4 } kh_option;
+ *                     block scheduler fills one job's tail with the next job's tiles.
+ *  KH_OPT_SAMPLE_PAIRS: 1 (default) = kirchhoff_migrate stages FP32 traces of constant or
+ *                     linear v(z) plans with nt <= 2460 as (d[i], d[i+1] - d[i]) pairs in plan
+ *                     workspace (8 bytes per sample, one pass over the traces), so that each
+ *                     interpolated sample takes one shared-memory load; 0 = plain samples.
+ *                     The image is bit-identical either way. */
+typedef enum {
+    KH_OPT_WAIT_POLLS = 1,
+    KH_OPT_FAST_MATH = 2,
+    KH_OPT_TILE = 3,
+    KH_OPT_BATCH_MODE = 4,
+    KH_OPT_SAMPLE_PAIRS = 5
+} kh_option;
 KH_API kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value);
 
 /* Profiling: while enabled, CUDA events bracket the main kernel of every migrate /

@@ -144,6 +144,25 @@ __global__ void k_pad(int ntr, int nt, long long ld, const T* __restrict__ src, 
     }
 }
 
+// FP32 rows of `nt` samples to SamplePair rows of `ld` pairs: (d[i], d[i + 1] - d[i]) with
+// d[nt] = 0, zero pairs from nt to ld.  The step is the IEEE difference the interpolation would
+// form from the two samples, so the migration result does not depend on the staging layout.
+__global__ void k_pairs(int ntr, int nt, int ld, const float* __restrict__ src, SamplePair* __restrict__ dst)
+{
+    for (int j = blockIdx.x; j < ntr; j += gridDim.x) {
+        const float* row = src + (long long)j * nt;
+        SamplePair* out = dst + (long long)j * ld;
+        for (int t = threadIdx.x; t < ld; t += blockDim.x) {
+            const float v = t < nt ? row[t] : 0.f;
+            const float n = t + 1 < nt ? row[t + 1] : 0.f;
+            SamplePair q;
+            q.v = v;
+            q.d = __fsub_rn(n, v);
+            out[t] = q;
+        }
+    }
+}
+
 // Eq. 2 work count: per trace (one CTA each), the in-aperture columns times nz.
 __global__ void k_count(int ntr, const float* __restrict__ sx, const float* __restrict__ sy,
                         const float* __restrict__ rx, const float* __restrict__ ry, GeomParams g,
@@ -597,6 +616,32 @@ kh_status staged_traces(kh_plan_s* p, int ntr, const void* traces, cudaStream_t 
     return KH_OK;
 }
 
+// Whether a migration stages its FP32 traces as SamplePair rows.
+static bool use_pairs(const kh_plan_s* p)
+{
+    return p->sample_pairs && p->d.trace_dtype == KH_F32 && p->d.vel != KH_VEL_TABLE && p->d.nt <= PAIR_MAX_NT;
+}
+
+// FP32 traces as SamplePair rows of 16-byte multiples in plan workspace; sets the staging
+// fields of g (pairs, esize, elem_align, ld).
+static kh_status paired_traces(kh_plan_s* p, int ntr, const void* traces, cudaStream_t s, const void** out,
+                               GeomParams& g)
+{
+    const int L = (p->d.nt + 1) / 2 * 2;
+    cudaError_t e = grow(p->ws_pad, p->cap_pad, (size_t)ntr * L * sizeof(SamplePair));
+    if (e != cudaSuccess) return cuda_fail(e, "workspace (trace pairs)");
+    k_pairs<<<std::min(ntr, 1 << 20), 256, 0, s>>>(ntr, p->d.nt, L, static_cast<const float*>(traces),
+                                                     reinterpret_cast<SamplePair*>(p->ws_pad));
+    ++p->launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "trace pair kernel");
+    *out = p->ws_pad;
+    g.pairs = 1;
+    g.esize = (int)sizeof(SamplePair);
+    g.elem_align = 16 / (int)sizeof(SamplePair);
+    g.ld = L;
+    return KH_OK;
+}
+
 }  // namespace kh
 
 static kh_status check_headers(const kh_plan_s* p, int ntr, const float* sx, const float* sy,
@@ -910,6 +955,9 @@ kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value)
             if (value != 0 && value != 1) return fail(KH_ERR_INVALID_ARG, "batch mode must be 0 or 1");
             p->batch_mode = (int)value;
             return KH_OK;
+        case KH_OPT_SAMPLE_PAIRS:
+            p->sample_pairs = value ? 1 : 0;
+            return KH_OK;
         default:
             return fail(KH_ERR_INVALID_ARG, "unknown option %d", (int)opt);
     }
@@ -932,7 +980,8 @@ kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy
     if ((st = bin_traces(p, ntr, sx, sy, rx, ry, s)) != KH_OK) return st;
     const void* tr_ptr = nullptr;
     GeomParams g = geom_of(p->d);
-    if ((st = staged_traces(p, ntr, traces, s, &tr_ptr, &g.ld)) != KH_OK) return st;
+    st = use_pairs(p) ? paired_traces(p, ntr, traces, s, &tr_ptr, g) : staged_traces(p, ntr, traces, s, &tr_ptr, &g.ld);
+    if (st != KH_OK) return st;
     const TileShape tile = tile_of(p);
     if ((st = prepare_linear(p->d, tile, g)) != KH_OK) return st;
     int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;

@@ -36,6 +36,17 @@ constexpr int LG_TERMS[] = {4, 5, 6, 8, 12, 20};
 constexpr int N_LG_TERMS = 6;
 constexpr int LG_MONO = 8;
 
+// An FP32 trace sample and the step to the next one, (d[i], d[i + 1] - d[i]) with d[nt] = 0:
+// the staging layout of FP32 traces for the migration kernel, so that one 8-byte shared load
+// serves each interpolated sample.  PAIR_MAX_NT is the longest trace whose pair row still fits
+// one ring stage; longer traces are staged as plain samples.
+struct __align__(8) SamplePair {
+    float v, d;
+    SamplePair() = default;
+    __host__ __device__ explicit SamplePair(float z) : v(z), d(z) {}
+};
+constexpr int PAIR_MAX_NT = 2460;
+
 // Default wait limit: polls of mbarrier.try_wait, each checked against a 2 s wall clock.
 constexpr long long WAIT_NS = 2000000000LL;
 
@@ -97,6 +108,7 @@ struct GeomParams {
     int esize;               // bytes per sample
     int tdtype;              // kh_dtype of the traces (F32, F16, BF16)
     int elem_align;          // samples per 16 bytes
+    int pairs;               // 1: FP32 traces staged as SamplePair rows (esize 8, ld in pairs)
 };
 
 struct TileShape {

@@ -9,6 +9,7 @@ namespace kh {
     cudaError_t name(const GeomParams&, const TileShape&, const TraceSet&, const void*, float*, int, int,     \
                      const WaitCfg&, cudaStream_t);
 KH_MIGRATE_DECL(launch_migrate_f32)
+KH_MIGRATE_DECL(launch_migrate_pair)
 KH_MIGRATE_DECL(launch_migrate_f16)
 KH_MIGRATE_DECL(launch_migrate_bf16)
 #undef KH_MIGRATE_DECL
@@ -48,7 +49,9 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
 {
     if (t.cz > MAX_ZG) return cudaErrorInvalidValue;
     switch (g.tdtype) {
-        case KH_F32: return launch_migrate_f32(g, t, tr, traces, image, vel_kind, fast_math, w, s);
+        case KH_F32:
+            return g.pairs ? launch_migrate_pair(g, t, tr, traces, image, vel_kind, fast_math, w, s)
+                           : launch_migrate_f32(g, t, tr, traces, image, vel_kind, fast_math, w, s);
         case KH_F16: return launch_migrate_f16(g, t, tr, traces, image, vel_kind, fast_math, w, s);
         case KH_BF16: return launch_migrate_bf16(g, t, tr, traces, image, vel_kind, fast_math, w, s);
         default: return cudaErrorInvalidValue;

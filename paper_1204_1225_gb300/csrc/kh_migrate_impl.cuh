@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstddef>
 #include <type_traits>
 
 #include "kh_tau.cuh"
@@ -57,16 +58,26 @@ struct __align__(16) MigSmem {
     float z2[MAX_ZG * NZ];      // linear: gamma(z) of the weight
     float zero[4];
 };
+static_assert(offsetof(MigSmem, zero) % 16 == 0, "the zero sample (pair) must be 16-byte aligned");
 
 __host__ __device__ constexpr size_t mig_static_bytes() { return (sizeof(MigSmem) + 127) / 128 * 128; }
 
 // Elements of one stage's sample area: a full trace always fits, so every trace is stageable.
 // 16 KB per stage, 8 KB with a traveltime table (whose shared copy takes the difference).
+// SamplePair rows hold half as many samples per byte; they take the largest stage at which two
+// CTAs of the linear path (static part, ring, 32 KB source-leg cache, 128 B of static shared
+// variables and the 1 KB the runtime reserves per CTA) still fit in an SM's 228 KB.
+constexpr int PAIR_STAGE_BYTES = 19712;   // 2464 pairs, 1 KB of margin per SM
+static_assert(2 * (((sizeof(MigSmem) + 127) / 128 * 128) +
+                   ((LEAD + STAGES * (PAIR_STAGE_BYTES / 8) + SLACK) * 8 + 15) / 16 * 16 +
+                   NZ * CONSUMERS * sizeof(float2) + 128 + 1024) <= 228 * 1024,
+              "two CTAs of the pair-staged linear kernel must fit on one SM");
+static_assert(PAIR_STAGE_BYTES / 8 >= (PAIR_MAX_NT + 5) / 2 * 2, "a whole pair row must fit one stage");
 __host__ __device__ inline int mig_cap(const GeomParams& g)
 {
     const int ealign = g.elem_align;
     const int need = (g.nt + 2 * ealign + ealign - 1) / ealign * ealign;
-    const int base = (g.table ? 8192 : 16384) / g.esize;
+    const int base = (g.table ? 8192 : g.pairs ? PAIR_STAGE_BYTES : 16384) / g.esize;
     return need > base ? need : base;
 }
 
@@ -143,9 +154,14 @@ __device__ __forceinline__ float sample_at(const TT* data, float th, int base, f
     const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
     const bool ok = fabsf(th - cmid) <= chalf;
     const int off = ok ? __float_as_int(tm) + base : zero_off;
-    const float d0 = to_f32<TT>(data[off]);
-    const float d1 = to_f32<TT>(data[off + 1]);
-    return fmaf(f, d1 - d0, d0);
+    if constexpr (std::is_same<TT, SamplePair>::value) {
+        const float2 p = *reinterpret_cast<const float2*>(data + off);
+        return fmaf(f, p.y, p.x);
+    } else {
+        const float d0 = to_f32<TT>(data[off]);
+        const float d1 = to_f32<TT>(data[off + 1]);
+        return fmaf(f, d1 - d0, d0);
+    }
 }
 
 // sample_at without the validity test, for traces whose window is not clipped and whose every
@@ -157,9 +173,14 @@ __device__ __forceinline__ float sample_unchecked(const TT* ring, float th, int 
     const float tm = __fadd_rd(th, MAGIC);
     const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
     const unsigned off = min((unsigned)(__float_as_int(tm) + base_lead), last);
-    const float d0 = to_f32<TT>(ring[off]);
-    const float d1 = to_f32<TT>(ring[off + 1]);
-    return fmaf(f, d1 - d0, d0);
+    if constexpr (std::is_same<TT, SamplePair>::value) {
+        const float2 p = *reinterpret_cast<const float2*>(ring + off);
+        return fmaf(f, p.y, p.x);
+    } else {
+        const float d0 = to_f32<TT>(ring[off]);
+        const float d1 = to_f32<TT>(ring[off + 1]);
+        return fmaf(f, d1 - d0, d0);
+    }
 }
 
 // ------------------------------------------------------------------ producer warp

@@ -1,0 +1,22 @@
+// Migration kernel instantiations for FP32 traces staged as SamplePair rows (constant and
+// linear v(z); table migrations stage plain samples).
+#include "kh_migrate_impl.cuh"
+
+namespace kh {
+cudaError_t launch_migrate_pair(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
+                                float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
+{
+    const int key = vel * 4 + g.weight * 2 + (fast ? 1 : 0);
+    switch (key) {
+        case 0: return launch_migrate_t<VK_CONST, 0, false, SamplePair>(g, t, tr, traces, image, w, s);
+        case 1: return launch_migrate_t<VK_CONST, 0, true, SamplePair>(g, t, tr, traces, image, w, s);
+        case 2: return launch_migrate_t<VK_CONST, 1, false, SamplePair>(g, t, tr, traces, image, w, s);
+        case 3: return launch_migrate_t<VK_CONST, 1, true, SamplePair>(g, t, tr, traces, image, w, s);
+        case 4: return launch_migrate_t<VK_LINEAR, 0, false, SamplePair>(g, t, tr, traces, image, w, s);
+        case 5: return launch_migrate_t<VK_LINEAR, 0, true, SamplePair>(g, t, tr, traces, image, w, s);
+        case 6: return launch_migrate_t<VK_LINEAR, 1, false, SamplePair>(g, t, tr, traces, image, w, s);
+        case 7: return launch_migrate_t<VK_LINEAR, 1, true, SamplePair>(g, t, tr, traces, image, w, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace kh

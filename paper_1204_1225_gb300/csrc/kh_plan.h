@@ -15,6 +15,7 @@ struct kh_plan_s {
     int fast_math = 1;
     long long tile_code = 0;      // 0 = default tile for the dimension
     int batch_mode = 0;           // KH_OPT_BATCH_MODE (read from the first job's plan)
+    int sample_pairs = 1;         // KH_OPT_SAMPLE_PAIRS
     // device workspace (grown on demand, freed by kirchhoff_destroy)
     int* ws_status = nullptr;     // [2]: bit 0 of [0] = a bounded wait ran out
     int* ws_bin_start = nullptr;  // [MAX_BINS + 1]

@@ -20,7 +20,7 @@ KH_OK, KH_ERR_INVALID_ARG, KH_ERR_UNSUPPORTED, KH_ERR_OOM, KH_ERR_CUDA, KH_ERR_T
 KH_F32, KH_F16, KH_BF16, KH_U16 = 0, 1, 2, 3
 KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE = 0, 1, 2
 KH_W_ONE, KH_W_OBLIQ_SPREAD = 0, 1
-KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE, KH_OPT_BATCH_MODE = 1, 2, 3, 4
+KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE, KH_OPT_BATCH_MODE, KH_OPT_SAMPLE_PAIRS = 1, 2, 3, 4, 5
 BATCH_MODES = {"persistent": 0, "concurrent": 1}
 
 _STATUS = {0: "KH_OK", 1: "KH_ERR_INVALID_ARG", 2: "KH_ERR_UNSUPPORTED", 3: "KH_ERR_OOM",

@@ -55,10 +55,10 @@ LANES_PER_SM_CLK = {"issue": 128, "fma": 128, "alu": 64, "xu": 16, "lsu": 32}
 # k_migrate per variant; the 100k-trace 256^3 workload runs the variant measured on its
 # 10k-trace case: same grid, tile and 6-term fit).
 PIPE_MIX = {
-    "3d-vz-100k-256cube": {"issue": 33.43, "fma": 21.91, "alu": 3.32, "xu": 3.18, "lsu": 3.46},
-    "3d-vz-10k-256cube": {"issue": 33.43, "fma": 21.91, "alu": 3.32, "xu": 3.18, "lsu": 3.46},
-    "3d-vz-40k-128cube": {"issue": 35.58, "fma": 23.57, "alu": 3.56, "xu": 3.26, "lsu": 3.54},
-    "25d-vz-20k-512x400": {"issue": 35.17, "fma": 23.96, "alu": 3.64, "xu": 2.37, "lsu": 3.75},
+    "3d-vz-100k-256cube": {"issue": 32.82, "fma": 21.37, "alu": 3.38, "xu": 3.15, "lsu": 3.37},
+    "3d-vz-10k-256cube": {"issue": 32.82, "fma": 21.37, "alu": 3.38, "xu": 3.15, "lsu": 3.37},
+    "3d-vz-40k-128cube": {"issue": 34.64, "fma": 22.81, "alu": 3.56, "xu": 3.20, "lsu": 3.42},
+    "25d-vz-20k-512x400": {"issue": 35.45, "fma": 23.96, "alu": 3.84, "xu": 2.37, "lsu": 3.75},
     # mixed precision: U16 radial table + FP16 traces (k_migrate<table, obliquity, FP16, M=2, U16>)
     "3d-vz-100k-256cube-table-u16-f16": {"issue": 34.07, "fma": 19.3, "alu": 6.15, "xu": 2.23, "lsu": 5.5},
     "3d-vz-10k-256cube-table-u16-f16": {"issue": 34.07, "fma": 19.3, "alu": 6.15, "xu": 2.23, "lsu": 5.5},
@@ -77,9 +77,9 @@ PIPE_MIX = {
 # DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
 # (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
 TRAFFIC = {
-    "3d-vz-10k-256cube": 92043008 + 1026589184,
-    "3d-vz-40k-128cube": 280482304 + 111587584,
-    "25d-vz-20k-512x400": 91729408 + 3492608,
+    "3d-vz-10k-256cube": 87995904 + 1025581056,
+    "3d-vz-40k-128cube": 280563968 + 111368192,
+    "25d-vz-20k-512x400": 91586560 + 2943232,
     "3d-vz-10k-256cube-demigrate": 4731700000 + 8278000000,
     "3d-vz-10k-256cube-vgrad": 1128400000 + 15700000,
     "3d-vz-10k-256cube-table-u16-f16": 36481024 + 1023988736,

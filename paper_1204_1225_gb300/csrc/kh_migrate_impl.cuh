@@ -51,7 +51,8 @@ struct __align__(16) MigSmem {
     float2 mid[STAGES][BMAX];   // FP32 midpoint (aperture test)
     int4 win[STAGES][BMAX];     // x: tau_ref - lo (float bits), y: smem index of sample lo minus
                                 // MAGIC_BITS, z/w: c_mid/c_half (float bits) of the valid range
-                                // 0 <= tau - lo <= hi - lo; sign bit of w: window not clipped
+                                // 0 <= tau - lo <= hi - lo; sign bit of z: every column of the
+                                // tile inside the aperture; sign bit of w: window not clipped
     float tb[STAGES][BMAX];     // lo dt + t0: T_s + T_r = (tau - lo) dt + tb (gradient mode)
     float4 zc[MAX_ZG * NZ];     // per-z constants: linear v, z_constants_m; constant v, (z^2, w_z);
                                 // table, (w_z, z^2)
@@ -270,11 +271,20 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 S.hdr[s][slot] = h;
                 S.mid[s][slot] = m;
                 S.tb[s][slot] = (float)((double)lo * g.dtd + g.t0d);
+                // every column of the tile inside the aperture: the column test is monotone in
+                // |column - midpoint| per axis, so the corner farthest on both axes decides it
+                bool whole = false;
+                if (g.use_aperture) {
+                    const float ex = fmaxf(fabsf(__fsub_rn(box.xlo, m.x)), fabsf(__fsub_rn(box.xhi, m.x)));
+                    const float ey = fmaxf(fabsf(__fsub_rn(box.ylo, m.y)), fabsf(__fsub_rn(box.yhi, m.y)));
+                    whole = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= g.A2;
+                }
                 const float lim = (float)(hi - lo);
                 // w: c_half, its sign bit set when the window was not clipped at 0 or nt - 1 (then
                 // every point of the tile box has 0 <= tau - lo <= hi - lo by construction)
                 S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo)),
-                                           dst + (lo - lo_al) - MAGIC_BITS, __float_as_int(0.5f * lim),
+                                           dst + (lo - lo_al) - MAGIC_BITS,
+                                           __float_as_int(0.5f * lim) | (whole ? (int)0x80000000 : 0),
                                            __float_as_int(0.5f * lim) | (clipped ? 0 : (int)0x80000000));
             }
             if (lane == 0 && bytes > 0) mbar_expect_tx(&S.full[s], (uint32_t)bytes);
@@ -309,6 +319,24 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
     return n;
 }
 
+// Column (tx, ty) and z-group of consumer thread `tid` in the tile.  When the layer's footprint
+// allows it, a warp covers an 8 x 4 block of columns instead of 32 x 1 or 16 x 2: a compact
+// footprint leaves fewer lanes idle where the aperture boundary crosses the warp.
+__device__ __forceinline__ void thread_column(const TileShape& ts, int tid, int& tx, int& ty, int& tzg)
+{
+    const int layer = ts.cx * ts.cy;
+    tzg = tid / layer;
+    const int r = tid - tzg * layer;
+    if ((ts.cx & 7) == 0 && (ts.cy & 3) == 0) {
+        const int wl = r >> 5, lane = r & 31, bx = ts.cx >> 3;
+        tx = (wl % bx) * 8 + (lane & 7);
+        ty = (wl / bx) * 4 + (lane >> 3);
+    } else {
+        tx = r % ts.cx;
+        ty = r / ts.cx;
+    }
+}
+
 // ------------------------------------------------------------------ consumer warps
 // `n`: stages consumed before this tile (see mig_producer); returns the new count.
 //
@@ -326,7 +354,8 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                                             const WaitCfg& wc, const TB* tab, float2* srcc, int cap, int n)
 {
     const int tid = threadIdx.x, lane = tid & 31;
-    const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
+    int tx, ty, tzg;
+    thread_column(ts, tid, tx, ty, tzg);
     const int ix = x0 + tx, iy = y0 + ty, izb = z0 + tzg * NZ;
     const bool col_ok = ix < g.nx && iy < g.ny;
     const float cxf = col_coord(g.ox, ix, g.dx);
@@ -358,13 +387,13 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
         for (int t = 0; t < cnt; ++t) {
             const int4 w = S.win[s][t];
             bool inside = col_ok;
-            if (g.use_aperture) {
+            if (g.use_aperture && w.z >= 0) {   // sign bit of w.z: every column is inside
                 const float2 m = S.mid[s][t];
                 inside = inside && in_aperture(cxf, cyf, m.x, m.y, g.A2);
             }
             if (!__any_sync(0xffffffffu, inside)) continue;
             const float c0rel = __int_as_float(w.x);
-            const float cmid = __int_as_float(w.z);
+            const float cmid = __int_as_float(w.z & 0x7fffffff);
             const float chalf = inside ? __int_as_float(w.w & 0x7fffffff) : -1.f;
             const float4 h = S.hdr[s][t];
             if constexpr (VEL == VK_TABLE) {
@@ -507,7 +536,8 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
                             const WaitCfg& wc)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = tid % ts.cx, ty = (tid / ts.cx) % ts.cy, tzg = tid / (ts.cx * ts.cy);
+    int tx, ty, tzg;
+    thread_column(ts, tid, tx, ty, tzg);
     const int ix = x0 + tx, iy = y0 + ty, izb = z0 + tzg * NZ;
     const bool col_ok = ix < g.nx && iy < g.ny;
     const float cxf = col_coord(g.ox, ix, g.dx);
@@ -546,13 +576,13 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
         for (int t = 0; t < cnt; ++t) {
             const int4 w = S.win[s][t];
             bool inside = col_ok;
-            if (g.use_aperture) {
+            if (g.use_aperture && w.z >= 0) {   // sign bit of w.z: every column is inside
                 const float2 m = S.mid[s][t];
                 inside = inside && in_aperture(cxf, cyf, m.x, m.y, g.A2);
             }
             if (!__any_sync(0xffffffffu, inside)) continue;
             const float c0rel = __int_as_float(w.x);
-            const float cmid = __int_as_float(w.z);
+            const float cmid = __int_as_float(w.z & 0x7fffffff);
             const float chalf = inside ? __int_as_float(w.w & 0x7fffffff) : -1.f;
             const float tbase = S.tb[s][t];
             const float4 h = S.hdr[s][t];

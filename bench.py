@@ -60,8 +60,8 @@ PIPE_MIX = {
     "3d-vz-40k-128cube": {"issue": 34.64, "fma": 22.81, "alu": 3.56, "xu": 3.20, "lsu": 3.42},
     "25d-vz-20k-512x400": {"issue": 35.45, "fma": 23.96, "alu": 3.84, "xu": 2.37, "lsu": 3.75},
     # mixed precision: U16 radial table + FP16 traces (k_migrate<table, obliquity, FP16, M=2, U16>)
-    "3d-vz-100k-256cube-table-u16-f16": {"issue": 34.07, "fma": 19.3, "alu": 6.15, "xu": 2.23, "lsu": 5.5},
-    "3d-vz-10k-256cube-table-u16-f16": {"issue": 34.07, "fma": 19.3, "alu": 6.15, "xu": 2.23, "lsu": 5.5},
+    "3d-vz-100k-256cube-table-u16-f16": {"issue": 30.31, "fma": 16.50, "alu": 4.75, "xu": 2.20, "lsu": 5.40},
+    "3d-vz-10k-256cube-table-u16-f16": {"issue": 30.31, "fma": 16.50, "alu": 4.75, "xu": 2.20, "lsu": 5.40},
     # adjoint (k_demigrate) and gradient (k_vgrad), headline variants measured on the 10k case
     "3d-vz-100k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
     "3d-vz-10k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
@@ -69,8 +69,8 @@ PIPE_MIX = {
     "3d-vz-100k-256cube-vgrad": {"issue": 68.94, "fma": 49.05, "alu": 7.79, "xu": 6.2, "lsu": 3.81},
     "3d-vz-10k-256cube-vgrad": {"issue": 68.94, "fma": 49.05, "alu": 7.79, "xu": 6.2, "lsu": 3.81},
     "25d-vz-20k-512x400-vgrad": {"issue": 73.09, "fma": 52.03, "alu": 8.4, "xu": 6.76, "lsu": 3.8},
-    # persistent batched kernel, constant velocity (measured on the 8-job small batch)
-    "batch64-3d-vz-f32": {"issue": 28.27, "fma": 16.59, "alu": 4.77, "xu": 2.51, "lsu": 3.91},
+    # persistent batched kernel, constant velocity, sample pairs (measured on the 8-job small batch)
+    "batch64-3d-vz-f32": {"issue": 23.35, "fma": 13.83, "alu": 3.46, "xu": 2.38, "lsu": 2.54},
 }
 
 
@@ -82,7 +82,7 @@ TRAFFIC = {
     "25d-vz-20k-512x400": 91586560 + 2943232,
     "3d-vz-10k-256cube-demigrate": 4731700000 + 8278000000,
     "3d-vz-10k-256cube-vgrad": 1128400000 + 15700000,
-    "3d-vz-10k-256cube-table-u16-f16": 36481024 + 1023988736,
+    "3d-vz-10k-256cube-table-u16-f16": 39405056 + 1024635648,
 }
 
 

@@ -630,10 +630,9 @@ static kh_status paired_traces(kh_plan_s* p, int ntr, const void* traces, cudaSt
     const int L = (p->d.nt + 1) / 2 * 2;
     cudaError_t e = grow(p->ws_pad, p->cap_pad, (size_t)ntr * L * sizeof(SamplePair));
     if (e != cudaSuccess) return cuda_fail(e, "workspace (trace pairs)");
-    k_pairs<<<std::min(ntr, 1 << 20), 256, 0, s>>>(ntr, p->d.nt, L, static_cast<const float*>(traces),
-                                                     reinterpret_cast<SamplePair*>(p->ws_pad));
     ++p->launches;
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "trace pair kernel");
+    if ((e = launch_pairs(ntr, p->d.nt, L, traces, p->ws_pad, s)) != cudaSuccess)
+        return cuda_fail(e, "trace pair kernel");
     *out = p->ws_pad;
     g.pairs = 1;
     g.esize = (int)sizeof(SamplePair);
@@ -809,8 +808,14 @@ static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const floa
     g.tza = za;
     g.tsp = D;
     g.tm = m;
-    const double vmin = std::min(d.v0 + d.k * std::min(0.0, zmin), d.v0 + d.k * std::max(0.0, zmax));
-    g.tslack = (float)(2.0 * D / (vmin * d.dt) + 2.0);
+    // Window slack for the interpolation: an interpolated leg time is a convex combination of
+    // node times, each node within sqrt(D^2 + Dz^2) of the point, and T is Lipschitz with
+    // 1/v_min over the depths the segments cross (image and node depths); two legs, plus two
+    // samples for the FP16 / U16 storage error.
+    const double zn1 = za + (nz - 1) * Dz;
+    const double zlo_all = std::min({0.0, zmin, za}), zhi_all = std::max({0.0, zmax, zn1});
+    const double vmin = std::min(d.v0 + d.k * zlo_all, d.v0 + d.k * zhi_all);
+    g.tslack = (float)(2.0 * std::sqrt(D * D + Dz * Dz) / (vmin * d.dt) + 2.0);
     const double c1 = p->tab_scale / d.dt;
     g.C1 = (float)c1;
     g.C1lo = (float)(c1 - (double)g.C1);
@@ -1207,6 +1212,14 @@ cudaError_t launch_pad(int ntr, int nt, long long ld, int esize, const void* src
     else
         k_pad<unsigned short><<<std::max(blocks, 1), 256, 0, s>>>(ntr, nt, ld, (const unsigned short*)src,
                                                                  (unsigned short*)dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(int ntr, int nt, int ld, const void* src, void* dst, cudaStream_t s)
+{
+    if (ntr > 0)
+        k_pairs<<<std::min(ntr, 1 << 20), 256, 0, s>>>(ntr, nt, ld, static_cast<const float*>(src),
+                                                         static_cast<SamplePair*>(dst));
     return cudaGetLastError();
 }
 

@@ -40,6 +40,8 @@ struct kh_batch_s {
     std::vector<Part> parts;
     double work = 0.0;             // estimated contributions: culled traces x points, summed
     long long launches = 0;
+    // Rows restaged at every launch: padded to 16-byte rows, or FP32 rows to SamplePair rows
+    // (pairs: every job, when the jobs' plans stage pairs and the longest trace allows it).
     struct Pad {
         int ntr, nt;
         long long ld;
@@ -48,6 +50,7 @@ struct kh_batch_s {
         void* dst;
     };
     std::vector<Pad> pads;
+    int pairs = 0;
     // KH_OPT_BATCH_MODE 1: each job's own k_migrate launch, descending cost, round-robin over
     // library streams forked from and joined to the caller's stream
     int mode = 0;
@@ -168,7 +171,8 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     }
 
     // ---- device layout
-    const int es = dtype_bytes((kh_dtype)tdt), ealign = 16 / es;
+    const bool pairs = jobs[0].plan->sample_pairs && tdt == KH_F32 && nt_max <= PAIR_MAX_NT;
+    const int es = pairs ? (int)sizeof(SamplePair) : dtype_bytes((kh_dtype)tdt), ealign = 16 / es;
     Layout L;
     struct Off {
         size_t bin, perm, bs, hdr, mid, pad, cull;
@@ -187,7 +191,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         o.bs = L.take((size_t)(d.n_bins + 1) * sizeof(int));
         o.hdr = L.take(n * sizeof(float4));
         o.mid = L.take(n * sizeof(float2));
-        o.padded = J.ntr > 0 && !((reinterpret_cast<uintptr_t>(J.traces) & 15u) == 0 && d.nt % ealign == 0);
+        o.padded = J.ntr > 0 && (pairs || !((reinterpret_cast<uintptr_t>(J.traces) & 15u) == 0 && d.nt % ealign == 0));
         o.ld = o.padded ? (d.nt + ealign - 1) / ealign * ealign : d.nt;
         o.pad = o.padded ? L.take((size_t)J.ntr * o.ld * es) : 0;
         const TileShape& t = tss[j];
@@ -211,6 +215,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     b->wait_polls = jobs[0].plan->wait_polls;
     b->mode = jobs[0].plan->batch_mode;
     b->n_items = (int)n_items;
+    b->pairs = pairs ? 1 : 0;
     e = cudaMalloc(&b->ws, L.off);
     if (e != cudaSuccess) {
         delete b;
@@ -241,6 +246,11 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         const Off& o = off[j];
         GeomParams g = gs[j];
         g.ld = o.ld;
+        if (pairs) {
+            g.pairs = 1;
+            g.esize = es;
+            g.elem_align = ealign;
+        }
         float4* hdr = reinterpret_cast<float4*>(w + o.hdr);
         float2* mid = reinterpret_cast<float2*>(w + o.mid);
         int* perm = reinterpret_cast<int*>(w + o.perm);
@@ -353,6 +363,7 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     gm.nt = nt_max;
     gm.esize = es;
     gm.elem_align = ealign;
+    gm.pairs = pairs ? 1 : 0;
     gm.table = nullptr;
     b->g_max = gm;
     WaitCfg wc{b->d_status, b->wait_polls, WAIT_NS};
@@ -391,8 +402,9 @@ kh_status kirchhoff_migrate_batched(kh_batch b, void* cuda_stream)
             const BatchJob& J = b->conc[i];
             if (b->conc_pad[i] >= 0) {
                 const auto& p = b->pads[b->conc_pad[i]];
-                if ((e = launch_pad(p.ntr, p.nt, p.ld, p.esize, p.src, p.dst, sk)) != cudaSuccess)
-                    return set_cuda_error(e, "kirchhoff_migrate_batched: row padding");
+                e = b->pairs ? launch_pairs(p.ntr, p.nt, (int)p.ld, p.src, p.dst, sk)
+                             : launch_pad(p.ntr, p.nt, p.ld, p.esize, p.src, p.dst, sk);
+                if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_migrate_batched: row staging");
                 ++b->launches;
             }
             e = launch_migrate(J.g, J.ts, J.tr, J.traces, J.image, b->vel, b->fast, wc, sk);
@@ -407,8 +419,9 @@ kh_status kirchhoff_migrate_batched(kh_batch b, void* cuda_stream)
         return KH_OK;
     }
     for (const auto& p : b->pads) {
-        if ((e = launch_pad(p.ntr, p.nt, p.ld, p.esize, p.src, p.dst, s)) != cudaSuccess)
-            return set_cuda_error(e, "kirchhoff_migrate_batched: row padding");
+        e = b->pairs ? launch_pairs(p.ntr, p.nt, (int)p.ld, p.src, p.dst, s)
+                     : launch_pad(p.ntr, p.nt, p.ld, p.esize, p.src, p.dst, s);
+        if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_migrate_batched: row staging");
         ++b->launches;
     }
     if (b->n_items == 0) return KH_OK;

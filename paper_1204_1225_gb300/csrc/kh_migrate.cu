@@ -18,6 +18,7 @@ KH_MIGRATE_DECL(launch_migrate_bf16)
     cudaError_t name(const GeomParams&, const BatchJob*, const int4*, int, int*, int, int, int, int,          \
                      const WaitCfg&, int, int*, cudaStream_t);
 KH_BATCHED_DECL(launch_batched_f32)
+KH_BATCHED_DECL(launch_batched_pair)
 KH_BATCHED_DECL(launch_batched_f16)
 KH_BATCHED_DECL(launch_batched_bf16)
 #undef KH_BATCHED_DECL
@@ -31,6 +32,9 @@ cudaError_t launch_migrate_batched(const GeomParams& gm, const BatchJob* jobs, c
 {
     switch (trace_dtype) {
         case KH_F32:
+            if (gm.pairs)
+                return launch_batched_pair(gm, jobs, items, n_items, next, vel_kind, weight, fast, lg_terms, w, ctas,
+                                           ctas_out, s);
             return launch_batched_f32(gm, jobs, items, n_items, next, vel_kind, weight, fast, lg_terms, w, ctas,
                                       ctas_out, s);
         case KH_F16:

@@ -63,29 +63,9 @@ static_assert(offsetof(MigSmem, zero) % 16 == 0, "the zero sample (pair) must be
 
 __host__ __device__ constexpr size_t mig_static_bytes() { return (sizeof(MigSmem) + 127) / 128 * 128; }
 
-// Elements of one stage's sample area: a full trace always fits, so every trace is stageable.
-// 16 KB per stage, 8 KB with a traveltime table (whose shared copy takes the difference).
-// SamplePair rows hold half as many samples per byte; they take the largest stage at which two
-// CTAs of the linear path (static part, ring, 32 KB source-leg cache, 128 B of static shared
-// variables and the 1 KB the runtime reserves per CTA) still fit in an SM's 228 KB.
-constexpr int PAIR_STAGE_BYTES = 19712;   // 2464 pairs, 1 KB of margin per SM
-static_assert(2 * (((sizeof(MigSmem) + 127) / 128 * 128) +
-                   ((LEAD + STAGES * (PAIR_STAGE_BYTES / 8) + SLACK) * 8 + 15) / 16 * 16 +
-                   NZ * CONSUMERS * sizeof(float2) + 128 + 1024) <= 228 * 1024,
-              "two CTAs of the pair-staged linear kernel must fit on one SM");
-static_assert(PAIR_STAGE_BYTES / 8 >= (PAIR_MAX_NT + 5) / 2 * 2, "a whole pair row must fit one stage");
-__host__ __device__ inline int mig_cap(const GeomParams& g)
-{
-    const int ealign = g.elem_align;
-    const int need = (g.nt + 2 * ealign + ealign - 1) / ealign * ealign;
-    const int base = (g.table ? 8192 : g.pairs ? PAIR_STAGE_BYTES : 16384) / g.esize;
-    return need > base ? need : base;
-}
-
-__host__ __device__ inline size_t mig_ring_bytes(const GeomParams& g)
-{
-    return (((size_t)LEAD + STAGES * mig_cap(g) + SLACK) * g.esize + 15) / 16 * 16;
-}
+// Dynamic shared memory of one CTA when two CTAs share an SM's 228 KB (the runtime reserves
+// 1 KB per CTA; 128 B of static shared variables).
+constexpr size_t CTA_SMEM_BUDGET = 228 * 1024 / 2 - 1024 - 128;
 
 __host__ __device__ inline size_t table_bytes(const GeomParams& g)
 {
@@ -95,11 +75,46 @@ __host__ __device__ inline size_t table_bytes(const GeomParams& g)
 }
 
 // Per consumer thread and depth, the cached source leg of the current source position (see
-// mig_consumer): (rho_s, gamma sqrt(q_s)) for linear v(z), T_s for the table.
+// mig_consumer): (C1 ln(1 + rho_s), sqrt(q_s)) for linear v(z), T_s for the table (whose shared
+// copy leaves no room for more at two CTAs per SM).  Constant velocity keeps no cache: its leg is
+// one square root, and surveys whose traces do not arrive shot by shot would recompute it per
+// trace anyway.
 __host__ __device__ inline size_t src_cache_bytes(const GeomParams& g)
 {
     if (g.table) return (size_t)NZ * CONSUMERS * sizeof(float);
     return g.kabs > 0.0 ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
+}
+
+// Elements of one stage's sample area: a full trace always fits, so every trace is stageable.
+// Plain samples: 16 KB per stage.  SamplePair rows hold half as many samples per byte; they take
+// the largest stage at which two CTAs of the linear path (static part, ring, 32 KB source-leg
+// cache) still fit.  With a traveltime table, the largest stage up to 16 KB at which two CTAs
+// fit beside the table, but at least 8 KB (a large F32 table then runs one CTA per SM).
+constexpr int PAIR_STAGE_BYTES = 19712;   // 2464 pairs, 1 KB of margin per SM
+static_assert(((sizeof(MigSmem) + 127) / 128 * 128) +
+                      ((LEAD + STAGES * (PAIR_STAGE_BYTES / 8) + SLACK) * 8 + 15) / 16 * 16 +
+                      NZ * CONSUMERS * sizeof(float2) <= CTA_SMEM_BUDGET,
+              "two CTAs of the pair-staged linear kernel must fit on one SM");
+static_assert(PAIR_STAGE_BYTES / 8 >= (PAIR_MAX_NT + 5) / 2 * 2, "a whole pair row must fit one stage");
+__host__ __device__ inline int mig_cap(const GeomParams& g)
+{
+    const int ealign = g.elem_align;
+    const int need = (g.nt + 2 * ealign + ealign - 1) / ealign * ealign;
+    long long bytes = g.pairs ? PAIR_STAGE_BYTES : 16384;
+    if (g.table) {
+        const long long room = (long long)CTA_SMEM_BUDGET - (long long)mig_static_bytes() -
+                               (long long)table_bytes(g) - (long long)src_cache_bytes(g) -
+                               (long long)(LEAD + SLACK) * g.esize - 16;
+        bytes = room / STAGES / 1024 * 1024;
+        bytes = bytes > 16384 ? 16384 : (bytes < 8192 ? 8192 : bytes);
+    }
+    const int base = (int)(bytes / g.esize);
+    return need > base ? need : base;
+}
+
+__host__ __device__ inline size_t mig_ring_bytes(const GeomParams& g)
+{
+    return (((size_t)LEAD + STAGES * mig_cap(g) + SLACK) * g.esize + 15) / 16 * 16;
 }
 
 inline size_t mig_smem_bytes(const GeomParams& g)
@@ -396,8 +411,11 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
             const float cmid = __int_as_float(w.z & 0x7fffffff);
             const float chalf = inside ? __int_as_float(w.w & 0x7fffffff) : -1.f;
             const float4 h = S.hdr[s][t];
+            // unclipped window, and every lane inside the aperture with all 16 depths in the
+            // grid: every tau is inside the window, no validity test is needed
+            const bool unchecked = w.w < 0 && __all_sync(0xffffffffu, inside && zfull);
             if constexpr (VEL == VK_TABLE) {
-                // T_s + T_r in table units from the radial table; the source leg is cached
+                // T_s + T_r in table units from the radial table; the source leg T_s is cached
                 // per source position like the linear path's
                 constexpr int M = LPT;            // depth nodes every M samples (1, 2 or 4)
                 constexpr int K = NZ / M + 1;     // nodes spanning the thread's 16 depths
@@ -417,35 +435,47 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
                 float pr[K];
                 tab_profile<TB, K, FAST>(tab, g, dhr2, jb, pr);
+                auto zloop = [&](auto checked) {
 #pragma unroll
-                for (int i = 0; i < NZ; ++i) {
-                    const float4 c = zc[i];   // (w_z, z^2)
-                    const float Ssum = my_ts[i * CONSUMERS] + tab_depth<M>(pr, i);
-                    const float th = fmaf(Ssum, g.C1, c0rel);
-                    const float val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
-                    if constexpr (WGT == 1) {
-                        const float Wt = c.x * (hsqrt<FAST>(dhs2 + c.y) + hsqrt<FAST>(dhr2 + c.y));
-                        acc[i] = fmaf(Wt, val, acc[i]);
-                    } else {
-                        acc[i] += val;
+                    for (int i = 0; i < NZ; ++i) {
+                        const float th = fmaf(my_ts[i * CONSUMERS] + tab_depth<M>(pr, i), g.C1, c0rel);
+                        float val;
+                        if constexpr (decltype(checked)::value)
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                        else
+                            val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        // w_z multiplies the sum once, at the store
+                        if constexpr (WGT == 1) {
+                            const float Rsum = hsqrt<FAST>(dhs2 + zc[i].y) + hsqrt<FAST>(dhr2 + zc[i].y);
+                            acc[i] = fmaf(Rsum, val, acc[i]);
+                        }
+                        else acc[i] += val;
                     }
-                }
+                };
+                if (unchecked) zloop(std::false_type());
+                else zloop(std::true_type());
             } else if constexpr (VEL == VK_CONST) {
                 const float dxs = cxf - h.x, dys = cyf - h.y;
                 const float dxr = cxf - h.z, dyr = cyf - h.w;
                 const float dhs2 = fmaf(dxs, dxs, dys * dys);
                 const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
+                auto zloop = [&](auto checked) {
 #pragma unroll
-                for (int i = 0; i < NZ; ++i) {
-                    const float4 c = zc[i];   // (z^2, w_z)
-                    const float Rs = hsqrt<FAST>(dhs2 + c.x);
-                    const float Rr = hsqrt<FAST>(dhr2 + c.x);
-                    const float Ssum = Rs + Rr;
-                    const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                    const float val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
-                    if constexpr (WGT == 1) acc[i] = fmaf(c.y * Ssum, val, acc[i]);
-                    else acc[i] += val;
-                }
+                    for (int i = 0; i < NZ; ++i) {
+                        const float Ssum = hsqrt<FAST>(dhs2 + zc[i].x) + hsqrt<FAST>(dhr2 + zc[i].x);
+                        const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
+                        float val;
+                        if constexpr (decltype(checked)::value)
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                        else
+                            val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        // w_z multiplies the sum once, at the store
+                        if constexpr (WGT == 1) acc[i] = fmaf(Ssum, val, acc[i]);
+                        else acc[i] += val;
+                    }
+                };
+                if (unchecked) zloop(std::false_type());
+                else zloop(std::true_type());
             } else {
                 const float4 a = S.hda[s][t];
                 if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
@@ -483,12 +513,8 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         else acc[i] += val;
                     }
                 };
-                // unclipped window, and every lane inside the aperture with all 16 depths in the
-                // grid: every tau is inside the window, no validity test is needed
-                if (w.w < 0 && __all_sync(0xffffffffu, inside && zfull))
-                    zloop(std::false_type());
-                else
-                    zloop(std::true_type());
+                if (unchecked) zloop(std::false_type());
+                else zloop(std::true_type());
             }
         }
         __syncwarp();
@@ -501,9 +527,10 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
         return n;
     }
     if (!col_ok) return n;
-    if constexpr (VEL == VK_LINEAR && WGT == 1) {
+    if constexpr (WGT == 1) {
 #pragma unroll
-        for (int i = 0; i < NZ; ++i) acc[i] *= zg[i];
+        for (int i = 0; i < NZ; ++i)
+            acc[i] *= VEL == VK_LINEAR ? zg[i] : (VEL == VK_TABLE ? zc[i].x : zc[i].y);
     }
     float* out = image + (((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb;
     const bool vec = ((g.nz & 3) == 0) && (izb + NZ <= g.nz) &&

@@ -70,6 +70,8 @@ kh_status plan_geometry(const kh_plan_s* p, GeomParams* g, TileShape* t);
 kh_status plan_check_headers(const kh_plan_s* p, int ntr, const float* sx, const float* sy,
                              const float* rx, const float* ry);
 cudaError_t launch_pad(int ntr, int nt, long long ld, int esize, const void* src, void* dst, cudaStream_t s);
+// FP32 rows of nt samples to SamplePair rows of ld (even) pairs.
+cudaError_t launch_pairs(int ntr, int nt, int ld, const void* src, void* dst, cudaStream_t s);
 cudaError_t noalloc_bin(int ntr, const float* sx, const float* sy, const float* rx, const float* ry,
                         const kh_desc& d, int* bin, int* perm, int* bin_start, float4* hdr,
                         float2* mid, cudaStream_t s);

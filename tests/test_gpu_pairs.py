@@ -58,3 +58,28 @@ def test_paired_image_matches_oracle():
     err = rel_l2(paired.cpu(), oracle.migrate(s, d.cpu().numpy()))
     print(f"{s.name}: paired rel L2 vs oracle {err:.2e}")
     assert err < FP32_REL_L2
+
+
+@pytest.mark.parametrize("mode", ["persistent", "concurrent"])
+def test_batched_pairs_match_plain_staging(mode):
+    """A batch stages every FP32 job as pairs (each launch); with the option off in the first
+    job's plan it stages plain rows.  Both give the per-job images bit for bit."""
+    specs = [_cube(400, 32, 801), survey_3d_gradient(700, 48).replace(nt=601), _cube(300, 24, 2460)]
+    out = {}
+    for pairs in (1, 0):
+        jobs = []
+        for i, s in enumerate(specs):
+            p = kh.Plan(s)
+            p.set_option(kh.KH_OPT_SAMPLE_PAIRS, pairs)
+            d = torch.from_numpy(random_traces(s, BASE_SEED + 60 + i)).to("cuda").contiguous()
+            jobs.append((p, kh.Headers.of(s), d, torch.full(p.image_shape, float("nan"), device="cuda")))
+        b = kh.Batch(jobs, mode=mode)
+        b.run()
+        b.sync()
+        out[pairs] = [img.clone() for (_, _, _, img) in jobs]
+        ref = [p.migrate(h, d) for (p, h, d, _) in jobs]
+        for a, r in zip(out[pairs], ref):
+            assert torch.equal(a, r)
+        b.close()
+    for a, c in zip(out[1], out[0]):
+        assert torch.equal(a, c)

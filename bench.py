@@ -77,6 +77,7 @@ PIPE_MIX = {
 # DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
 # (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
 TRAFFIC = {
+    "3d-vz-100k-256cube": 748463488 + 1037584256,
     "3d-vz-10k-256cube": 87995904 + 1025581056,
     "3d-vz-40k-128cube": 280563968 + 111368192,
     "25d-vz-20k-512x400": 91586560 + 2943232,

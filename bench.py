@@ -66,9 +66,8 @@ PIPE_MIX = {
     "3d-vz-100k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
     "3d-vz-10k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
     "25d-vz-20k-512x400-demigrate": {"issue": 61.14, "fma": 38.93, "alu": 7.07, "xu": 4.42, "lsu": 6.53},
-    "3d-vz-100k-256cube-vgrad": {"issue": 68.94, "fma": 49.05, "alu": 7.79, "xu": 6.2, "lsu": 3.81},
-    "3d-vz-10k-256cube-vgrad": {"issue": 68.94, "fma": 49.05, "alu": 7.79, "xu": 6.2, "lsu": 3.81},
-    "25d-vz-20k-512x400-vgrad": {"issue": 73.09, "fma": 52.03, "alu": 8.4, "xu": 6.76, "lsu": 3.8},
+    "3d-vz-100k-256cube-vgrad": {"issue": 54.56, "fma": 34.29, "alu": 7.63, "xu": 3.15, "lsu": 5.49},
+    "3d-vz-10k-256cube-vgrad": {"issue": 54.56, "fma": 34.29, "alu": 7.63, "xu": 3.15, "lsu": 5.49},
     # persistent batched kernel, constant velocity, sample pairs (measured on the 8-job small batch)
     "batch64-3d-vz-f32": {"issue": 23.35, "fma": 13.83, "alu": 3.46, "xu": 2.38, "lsu": 2.54},
 }
@@ -82,7 +81,7 @@ TRAFFIC = {
     "3d-vz-40k-128cube": 280563968 + 111368192,
     "25d-vz-20k-512x400": 91586560 + 2943232,
     "3d-vz-10k-256cube-demigrate": 4731700000 + 8278000000,
-    "3d-vz-10k-256cube-vgrad": 1128400000 + 15700000,
+    "3d-vz-10k-256cube-vgrad": 1130428928 + 15748608,
     "3d-vz-10k-256cube-table-u16-f16": 39405056 + 1024635648,
 }
 

@@ -163,6 +163,21 @@ __global__ void k_pairs(int ntr, int nt, int ld, const float* __restrict__ src, 
     }
 }
 
+// FP32 rows of `nt` samples to slope rows of `ld`: d[i + 1] - d[i] with d[nt] = 0 (the IEEE
+// difference the gradient kernel would form from the two samples), zeros from nt to ld.
+__global__ void k_slopes(int ntr, int nt, int ld, const float* __restrict__ src, float* __restrict__ dst)
+{
+    for (int j = blockIdx.x; j < ntr; j += gridDim.x) {
+        const float* row = src + (long long)j * nt;
+        float* out = dst + (long long)j * ld;
+        for (int t = threadIdx.x; t < ld; t += blockDim.x) {
+            const float v = t < nt ? row[t] : 0.f;
+            const float n = t + 1 < nt ? row[t + 1] : 0.f;
+            out[t] = __fsub_rn(n, v);
+        }
+    }
+}
+
 // Eq. 2 work count: per trace (one CTA each), the in-aperture columns times nz.
 __global__ void k_count(int ntr, const float* __restrict__ sx, const float* __restrict__ sy,
                         const float* __restrict__ rx, const float* __restrict__ ry, GeomParams g,
@@ -1056,9 +1071,17 @@ kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, const flo
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if (ntr == 0) return KH_OK;
     if ((st = bin_traces(p, ntr, sx, sy, rx, ry, s)) != KH_OK) return st;
-    const void* tr_ptr = nullptr;
     GeomParams g = geom_of(p->d);
-    if ((st = staged_traces(p, ntr, traces, s, &tr_ptr, &g.ld)) != KH_OK) return st;
+    g.grad = 1;
+    // slope rows, 16-byte multiples, in plan workspace
+    const int L = (p->d.nt + 3) / 4 * 4;
+    if ((e = grow(p->ws_pad, p->cap_pad, (size_t)ntr * L * sizeof(float))) != cudaSuccess)
+        return cuda_fail(e, "workspace (slope rows)");
+    k_slopes<<<std::min(ntr, 1 << 20), 256, 0, s>>>(ntr, p->d.nt, L, traces, reinterpret_cast<float*>(p->ws_pad));
+    ++p->launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "slope kernel");
+    const void* tr_ptr = p->ws_pad;
+    g.ld = L;
     const TileShape tile = tile_of(p);
     if ((st = prepare_linear(p->d, tile, g)) != KH_OK) return st;
     const long long nwarps = (long long)tile.tiles_x * tile.tiles_y * tile.tiles_z * p->d.n_bins * CONSUMER_WARPS;

@@ -109,6 +109,7 @@ struct GeomParams {
     int tdtype;              // kh_dtype of the traces (F32, F16, BF16)
     int elem_align;          // samples per 16 bytes
     int pairs;               // 1: FP32 traces staged as SamplePair rows (esize 8, ld in pairs)
+    int grad;                // 1: the gradient kernel (slope rows d[i+1] - d[i], its own cache)
 };
 
 struct TileShape {

@@ -82,6 +82,9 @@ __host__ __device__ inline size_t table_bytes(const GeomParams& g)
 __host__ __device__ inline size_t src_cache_bytes(const GeomParams& g)
 {
     if (g.table) return (size_t)NZ * CONSUMERS * sizeof(float);
+    // gradient: the thread's weighted image values, and for linear v(z) (C1 ln(1 + rho_s), (q/w)_s)
+    // and sqrt(q_s)
+    if (g.grad) return (size_t)NZ * CONSUMERS * (g.kabs > 0.0 ? sizeof(float2) + 2 * sizeof(float) : sizeof(float));
     return g.kabs > 0.0 ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
 }
 
@@ -89,18 +92,23 @@ __host__ __device__ inline size_t src_cache_bytes(const GeomParams& g)
 // Plain samples: 16 KB per stage.  SamplePair rows hold half as many samples per byte; they take
 // the largest stage at which two CTAs of the linear path (static part, ring, 32 KB source-leg
 // cache) still fit.  With a traveltime table, the largest stage up to 16 KB at which two CTAs
-// fit beside the table, but at least 8 KB (a large F32 table then runs one CTA per SM).
+// fit beside the table, but at least 8 KB (a large F32 table then runs one CTA per SM).  The
+// gradient kernel's 64 KB of per-thread data leaves 8.75 KB per stage of slope rows at two CTAs
+// per SM.
 constexpr int PAIR_STAGE_BYTES = 19712;   // 2464 pairs, 1 KB of margin per SM
 static_assert(((sizeof(MigSmem) + 127) / 128 * 128) +
                       ((LEAD + STAGES * (PAIR_STAGE_BYTES / 8) + SLACK) * 8 + 15) / 16 * 16 +
                       NZ * CONSUMERS * sizeof(float2) <= CTA_SMEM_BUDGET,
               "two CTAs of the pair-staged linear kernel must fit on one SM");
 static_assert(PAIR_STAGE_BYTES / 8 >= (PAIR_MAX_NT + 5) / 2 * 2, "a whole pair row must fit one stage");
+static_assert(((sizeof(MigSmem) + 127) / 128 * 128) + ((LEAD + STAGES * (8960 / 4) + SLACK) * 4 + 15) / 16 * 16 +
+                      NZ * CONSUMERS * (sizeof(float2) + 2 * sizeof(float)) <= CTA_SMEM_BUDGET,
+              "two CTAs of the linear gradient kernel must fit on one SM");
 __host__ __device__ inline int mig_cap(const GeomParams& g)
 {
     const int ealign = g.elem_align;
     const int need = (g.nt + 2 * ealign + ealign - 1) / ealign * ealign;
-    long long bytes = g.pairs ? PAIR_STAGE_BYTES : 16384;
+    long long bytes = g.grad ? 8960 : g.pairs ? PAIR_STAGE_BYTES : 16384;
     if (g.table) {
         const long long room = (long long)CTA_SMEM_BUDGET - (long long)mig_static_bytes() -
                                (long long)table_bytes(g) - (long long)src_cache_bytes(g) -
@@ -554,13 +562,16 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
 //   linear v(z): with q/w = sqrt(q/(q+2)) per leg and vz = v0 + k z,
 //                dT/dv0 = -(q/w)_sum (1/v0 + 1/vz)/|k|,
 //                dT/dk  = -sgn(k) (T_s + T_r)/|k| + (q/w)_sum (2/k - z/vz)/|k|.
-// Each thread sums its 16 z in FP32 per (column, trace) and carries FP64 totals; per-warp
-// FP64 partials go to `partial` for a fixed-order final sum.
+// The traces arrive as slope rows D[i+1] - D[i] (one read per contribution).  Linear v(z): the
+// source leg (its logarithm term, q/w and sqrt(q)) is cached per source position as in the
+// migration, and tau - lo adds the per-leg logarithms.  Each thread sums its 16 z in FP32 per
+// (column, trace) and carries FP64 totals; per-warp FP64 partials go to `partial` for a
+// fixed-order final sum.
 template <int VEL, int WGT, bool FAST, typename TT, int LPT>
 __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, const TileShape& ts,
                             int x0, int y0, int z0, const TileBox& box, int bin,
                             const float* __restrict__ image, double* __restrict__ partial,
-                            const WaitCfg& wc)
+                            const WaitCfg& wc, float2* srcc)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int tx, ty, tzg;
@@ -582,13 +593,20 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
     const float inv_a = (VEL == VK_LINEAR) ? (float)(1.0 / g.a) : 0.f;
     const float zb = (float)(g.oz + izb * g.dz), dzf = (float)g.dz;
 
-    float mv[NZ];
+    // per thread and depth in shared memory: the image value times gamma(z) (the weight's depth
+    // factor), and for linear v(z) the source-leg cache (C1 ln(1 + rho_s), (q/w)_s) and sqrt(q_s)
+    float* my_mv = reinterpret_cast<float*>(srcc) + tid;
+    float2* my_lq = srcc + NZ * CONSUMERS / 2 + tid;
+    float* my_sq = reinterpret_cast<float*>(srcc) + 3 * NZ * CONSUMERS + tid;
 #pragma unroll
-    for (int i = 0; i < NZ; ++i)
-        mv[i] = (col_ok && izb + i < g.nz)
-                    ? image[(((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb + i]
-                    : 0.f;
+    for (int i = 0; i < NZ; ++i) {
+        const float m = (col_ok && izb + i < g.nz)
+                            ? image[(((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb + i]
+                            : 0.f;
+        my_mv[i * CONSUMERS] = (VEL == VK_LINEAR && WGT == 1) ? zg[i] * m : m;
+    }
     double G0 = 0.0, G1 = 0.0;
+    unsigned psx = 0xffffffffu, psy = 0xffffffffu;
 
     bool failed = false;
     int n = 0;
@@ -629,33 +647,47 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
                     const float tm = __fadd_rd(th, MAGIC);   // MAGIC + floor(th)
                     const bool ok = fabsf(th - cmid) <= chalf;
                     const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float slope = to_f32<TT>(data[off + 1]) - to_f32<TT>(data[off]);
+                    const float slope = to_f32<TT>(data[off]);   // slope rows: d[i + 1] - d[i]
                     const float W = (WGT == 1) ? c.y * Ssum : 1.f;
-                    g0 = fmaf(W * mv[i] * slope, -Ssum * inv_v0sq, g0);
+                    g0 = fmaf(W * my_mv[i * CONSUMERS] * slope, -Ssum * inv_v0sq, g0);
                 }
             } else {
-                const float4 rs = S.refs[s][t], rr = S.refr[s][t], a = S.hda[s][t];
-                const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
-                const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
-                const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
-                const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
+                const float4 rr = S.refr[s][t], a = S.hda[s][t];
+                if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
+                    const float4 rs = S.refs[s][t];
+                    const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
+                    const float exs = cxf - h.x, eys = cyf - h.y;
+                    const float dhs2 = fmaf(exs, exs, eys * eys);
 #pragma unroll
+                    for (int i = 0; i < NZ; ++i) {
+                        float sqs, qws;
+                        const float rho_s = leg_delta_grad_m<FAST>(dPs, dhs2, zc[i], rs, sqs, qws);
+                        my_lq[i * CONSUMERS] = make_float2(leg_log<LPT>(rho_s, g, 0.f), qws);
+                        my_sq[i * CONSUMERS] = sqs;
+                    }
+                    psx = __float_as_uint(h.x);
+                    psy = __float_as_uint(h.y);
+                }
+                const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
+                const float exr = cxf - h.z, eyr = cyf - h.w;
+                const float dhr2 = fmaf(exr, exr, eyr * eyr);
+#pragma unroll 4
                 for (int i = 0; i < NZ; ++i) {
                     const float4 zk = zc[i];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
-                    float sqs, sqr, qws, qwr;
-                    const float rho_s = leg_delta_grad_m<FAST>(dPs, dhs2, zk, rs, sqs, qws);
+                    float sqr, qwr;
                     const float rho_r = leg_delta_grad_m<FAST>(dPr, dhr2, zk, rr, sqr, qwr);
-                    const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
-                    const float th = tau_poly<LPT>(rho, g, c0rel);
+                    const float2 lq = my_lq[i * CONSUMERS];   // (C1 ln(1 + rho_s), (q/w)_s)
+                    const float th = leg_log<LPT>(rho_r, g, c0rel + lq.x);
                     const float tm = __fadd_rd(th, MAGIC);   // MAGIC + floor(th)
                     const bool ok = fabsf(th - cmid) <= chalf;
                     const int off = ok ? __float_as_int(tm) + w.y : zero_off;
-                    const float slope = to_f32<TT>(data[off + 1]) - to_f32<TT>(data[off]);
-                    const float W = (WGT == 1) ? zg[i] * (sqs + sqr) : 1.f;
-                    const float wms = W * mv[i] * slope;
+                    const float slope = to_f32<TT>(data[off]);   // slope rows: d[i + 1] - d[i]
+                    // gamma(z) is folded into the stored image value
+                    const float W = (WGT == 1) ? my_sq[i * CONSUMERS] + sqr : 1.f;
+                    const float wms = W * my_mv[i * CONSUMERS] * slope;
                     const float inv_vz = zk.x * inv_a;
                     const float z = fmaf((float)i, dzf, zb);
-                    const float qw = qws + qwr;
+                    const float qw = lq.y + qwr;
                     const float Tsum = fmaf(th, dtf, tbase);
                     const float dTv = -qw * (inv_v0 + inv_vz) * inv_ka;
                     const float dTk = (fmaf(qw, fmaf(-z, inv_vz, two_over_k), -sgnk * Tsum)) * inv_ka;
@@ -763,7 +795,7 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
         mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, srcc, cap,
                                                   0);
     } else {
-        vg_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, partial, wc);
+        vg_consumer<VEL, WGT, FAST, TT, LPT>(S, data, g, ts, x0, y0, z0, box, bin, image, partial, wc, srcc);
     }
 }
 
@@ -855,7 +887,7 @@ static cudaError_t launch_vgrad_t(const GeomParams& g, const TileShape& t, const
         return cudaGetLastError();
     };
     if constexpr (VEL == VK_LINEAR)
-        return with_lp<FAST>(g.lp_terms,
+        return with_lg<FAST>(g.lg_terms,
                              [&](auto L) { return go(k_vgrad<VEL, WGT, FAST, float, decltype(L)::value>); });
     else
         return go(k_vgrad<VEL, WGT, FAST, float, LP_SHORT>);

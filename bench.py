@@ -63,9 +63,8 @@ PIPE_MIX = {
     "3d-vz-100k-256cube-table-u16-f16": {"issue": 30.31, "fma": 16.50, "alu": 4.75, "xu": 2.20, "lsu": 5.40},
     "3d-vz-10k-256cube-table-u16-f16": {"issue": 30.31, "fma": 16.50, "alu": 4.75, "xu": 2.20, "lsu": 5.40},
     # adjoint (k_demigrate) and gradient (k_vgrad), headline variants measured on the 10k case
-    "3d-vz-100k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
-    "3d-vz-10k-256cube-demigrate": {"issue": 75.88, "fma": 44.51, "alu": 8.86, "xu": 7.15, "lsu": 8.19},
-    "25d-vz-20k-512x400-demigrate": {"issue": 61.14, "fma": 38.93, "alu": 7.07, "xu": 4.42, "lsu": 6.53},
+    "3d-vz-100k-256cube-demigrate": {"issue": 64.79, "fma": 31.42, "alu": 10.62, "xu": 3.98, "lsu": 10.08},
+    "3d-vz-10k-256cube-demigrate": {"issue": 64.79, "fma": 31.42, "alu": 10.62, "xu": 3.98, "lsu": 10.08},
     "3d-vz-100k-256cube-vgrad": {"issue": 54.56, "fma": 34.29, "alu": 7.63, "xu": 3.15, "lsu": 5.49},
     "3d-vz-10k-256cube-vgrad": {"issue": 54.56, "fma": 34.29, "alu": 7.63, "xu": 3.15, "lsu": 5.49},
     # persistent batched kernel, constant velocity, sample pairs (measured on the 8-job small batch)
@@ -80,7 +79,7 @@ TRAFFIC = {
     "3d-vz-10k-256cube": 87995904 + 1025581056,
     "3d-vz-40k-128cube": 280563968 + 111368192,
     "25d-vz-20k-512x400": 91586560 + 2943232,
-    "3d-vz-10k-256cube-demigrate": 4731700000 + 8278000000,
+    "3d-vz-10k-256cube-demigrate": 4994777088 + 8305233152,
     "3d-vz-10k-256cube-vgrad": 1130428928 + 15748608,
     "3d-vz-10k-256cube-table-u16-f16": 39405056 + 1024635648,
 }

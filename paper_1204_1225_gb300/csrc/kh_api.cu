@@ -873,6 +873,14 @@ static kh_status demigrate_tile(const kh_desc& d, GeomParams& g, int ntr, DmTile
             const double c1 = (double)gt.C1 + (double)gt.C1lo;
             for (int q = 0; q < LP_LONG; ++q) gt.lpc[q] = (float)(c1 * gt.lp[q]);
             gt.rho_max = (float)std::expm1(b);
+            // the per-leg fit the kernel evaluates (half the interval, half the budget per leg)
+            const double bl = 0.5 * (b - 1e-6) + 1e-6;
+            bool leg_fitted = false;
+            for (int q = 0; q < N_LG_TERMS && !leg_fitted; ++q) {
+                gt.lg_terms = LG_TERMS[q];
+                leg_fitted = fit_leg_log(bl, gt.lg_terms, c1, gt.lgc, &gt.lg_s, &gt.lg_o, 0.5 * tol);
+            }
+            if (!leg_fitted) continue;
         }
         (void)probe;
         g = gt;

@@ -10,6 +10,12 @@
 // The sample index is floor(tau - lo) (adding 1.5 * 2^23 rounded down), as in the migration.
 // After the tile the lane adds its window into its own row of the part's partial-trace
 // buffer.  A second kernel sums the P partial buffers in a fixed order into the output.
+//
+// Linear v(z): tau - lo adds per-leg logarithms (as the migration), and lanes whose traces share
+// a source position share the source leg of every image point.  When a warp's traces come from
+// at most two source positions (shot-ordered traces), the lanes first evaluate each group's
+// source leg at 32 depths of the column cooperatively into shared memory, then every lane
+// evaluates only its receiver leg per point; otherwise each lane evaluates both legs.
 #include "kh_tau.cuh"
 
 namespace kh {
@@ -25,6 +31,7 @@ struct __align__(16) DmSmem {
     float mt[DM_TILE];
     float4 zc[DM_MAXZ];
     float z2[DM_MAXZ];
+    float2 src[DM_WARPS][2][32];   // per warp and source group: (C1 ln(1 + rho_s), sqrt(q_s))
 };
 
 static_assert(DM_ROWS == DM_ROWS_HOST, "window rows");
@@ -53,6 +60,17 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
     float* prow = partial + ((long long)part * nvalid + (has ? k : 0)) * g.nt;
     const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
     const int n_tiles = dt.tiles_x * dt.tiles_y * dt.tiles_z;
+    // the warp's source groups: lane 0's source (A) and the first other one (B); lanes without a
+    // trace count as A
+    const unsigned FULL = 0xffffffffu;
+    const unsigned s0x = __shfl_sync(FULL, __float_as_uint(h.x), 0), s0y = __shfl_sync(FULL, __float_as_uint(h.y), 0);
+    const unsigned kx = has ? __float_as_uint(h.x) : s0x, ky = has ? __float_as_uint(h.y) : s0y;
+    const bool inA = kx == s0x && ky == s0y;
+    const unsigned notA = __ballot_sync(FULL, !inA);
+    const int lb = notA ? __ffs(notA) - 1 : 0;
+    const unsigned s1x = __shfl_sync(FULL, kx, lb), s1y = __shfl_sync(FULL, ky, lb);
+    const bool grouped = __all_sync(FULL, inA || (kx == s1x && ky == s1y));
+    const int my_group = inA ? 0 : 1, ngroups = notA ? 2 : 1;
     const int ncol = dt.tx * dt.ty;
 
     for (int ti = part; ti < n_tiles; ti += dt.parts) {
@@ -84,7 +102,9 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
         float4 ah = h;
         double tau_ref = -g.t0d / g.dtd;
         if constexpr (VEL == VK_LINEAR) {
-            if (ok) {
+            // every lane with a trace (not only those the tile keeps): a source group takes its
+            // source leg's reference from its first lane
+            if (has) {
                 LegRef ls_, lr_;
                 float qis = 0.f, qir = 0.f;
                 const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, ls_, &qis);
@@ -161,27 +181,73 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                 } else {
                     const float dxc = (float)((g.ox + ix * g.dx) - box.cx);
                     const float dyc = (g.dim == 3) ? (float)((g.oy + iy * g.dy) - box.cy) : 0.f;
-                    const float dPs = fmaf(dxc, cxf + ah.x, dyc * (cyf + ah.y));
                     const float dPr = fmaf(dxc, cxf + ah.z, dyc * (cyf + ah.w));
-                    const float exs = cxf - h.x, eys = cyf - h.y, exr = cxf - h.z, eyr = cyf - h.w;
-                    const float dhs2 = fmaf(exs, exs, eys * eys), dhr2 = fmaf(exr, exr, eyr * eyr);
+                    const float exr = cxf - h.z, eyr = cyf - h.w;
+                    const float dhr2 = fmaf(exr, exr, eyr * eyr);
+                    if (grouped) {
+                        for (int hz = 0; hz < dt.tz; hz += 32) {
+                            // each group's source leg at depths hz + lane (group data is uniform:
+                            // taken from the group's first lane)
+                            for (int gi = 0; gi < ngroups; ++gi) {
+                                const int src_lane = gi ? lb : 0;
+                                const float4 rsg = make_float4(__shfl_sync(FULL, rs.x, src_lane), __shfl_sync(FULL, rs.y, src_lane),
+                                                               __shfl_sync(FULL, rs.z, src_lane), __shfl_sync(FULL, rs.w, src_lane));
+                                const float ahx = __shfl_sync(FULL, ah.x, src_lane), ahy = __shfl_sync(FULL, ah.y, src_lane);
+                                const float sgx = __shfl_sync(FULL, h.x, src_lane), sgy = __shfl_sync(FULL, h.y, src_lane);
+                                const int izc = hz + lane;
+                                if (izc < dt.tz) {
+                                    const float dPs = fmaf(dxc, cxf + ahx, dyc * (cyf + ahy));
+                                    const float exs = cxf - sgx, eys = cyf - sgy;
+                                    const float dhs2 = fmaf(exs, exs, eys * eys);
+                                    float sqs = 0.f;
+                                    const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, S.zc[izc], rsg, sqs);
+                                    S.src[warp][gi][lane] = make_float2(leg_log<LPT>(rho_s, g, 0.f), sqs);
+                                }
+                            }
+                            __syncwarp();
+                            const float2* sl = &S.src[warp][my_group][0];
+                            const int nzh = min(32, dt.tz - hz);
 #pragma unroll 4
-                    for (int iz = 0; iz < dt.tz; ++iz) {
-                        const float4 zk = S.zc[iz];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
-                        float sqs = 0.f, sqr = 0.f;
-                        const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zk, rs, sqs);
-                        const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
-                        const float rho = fmaf(rho_s, rho_r, rho_s + rho_r);
-                        const float th = tau_poly<LPT>(rho, g, c0rel);
-                        const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
-                        const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
-                        const bool v = fabsf(th - cmid) <= chc;
-                        const float W = (WGT == 1) ? S.z2[iz] * (sqs + sqr) : 1.f;
-                        const float wm = v ? W * mcol[iz] : 0.f;
-                        const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
-                        const float a1 = wm * f;
-                        col0[row * 32] += wm - a1;
-                        col0[row * 32 + 32] += a1;
+                            for (int j = 0; j < nzh; ++j) {
+                                const int iz = hz + j;
+                                const float4 zk = S.zc[iz];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
+                                const float2 sv = sl[j];      // (C1 ln(1 + rho_s), sqrt(q_s))
+                                float sqr = 0.f;
+                                const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
+                                const float th = leg_log<LPT>(rho_r, g, c0rel + sv.x);
+                                const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
+                                const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
+                                const bool v = fabsf(th - cmid) <= chc;
+                                const float W = (WGT == 1) ? S.z2[iz] * (sv.y + sqr) : 1.f;
+                                const float wm = v ? W * mcol[iz] : 0.f;
+                                const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
+                                const float a1 = wm * f;
+                                col0[row * 32] += wm - a1;
+                                col0[row * 32 + 32] += a1;
+                            }
+                            __syncwarp();
+                        }
+                    } else {
+                        const float dPs = fmaf(dxc, cxf + ah.x, dyc * (cyf + ah.y));
+                        const float exs = cxf - h.x, eys = cyf - h.y;
+                        const float dhs2 = fmaf(exs, exs, eys * eys);
+#pragma unroll 4
+                        for (int iz = 0; iz < dt.tz; ++iz) {
+                            const float4 zk = S.zc[iz];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
+                            float sqs = 0.f, sqr = 0.f;
+                            const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zk, rs, sqs);
+                            const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
+                            const float th = leg_log<LPT>(rho_r, g, c0rel + leg_log<LPT>(rho_s, g, 0.f));
+                            const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
+                            const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
+                            const bool v = fabsf(th - cmid) <= chc;
+                            const float W = (WGT == 1) ? S.z2[iz] * (sqs + sqr) : 1.f;
+                            const float wm = v ? W * mcol[iz] : 0.f;
+                            const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
+                            const float a1 = wm * f;
+                            col0[row * 32] += wm - a1;
+                            col0[row * 32 + 32] += a1;
+                        }
                     }
                 }
             }
@@ -228,7 +294,7 @@ static cudaError_t dm_launch_t(const GeomParams& g, const DmTile& dt, const Trac
         return cudaGetLastError();
     };
     if constexpr (VEL == VK_LINEAR)
-        return with_lp<FAST>(g.lp_terms, [&](auto L) { return go(k_demigrate<VEL, WGT, FAST, decltype(L)::value>); });
+        return with_lg<FAST>(g.lg_terms, [&](auto L) { return go(k_demigrate<VEL, WGT, FAST, decltype(L)::value>); });
     else
         return go(k_demigrate<VEL, WGT, FAST, LP_SHORT>);
 }

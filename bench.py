@@ -57,8 +57,8 @@ LANES_PER_SM_CLK = {"issue": 128, "fma": 128, "alu": 64, "xu": 16, "lsu": 32}
 PIPE_MIX = {
     "3d-vz-100k-256cube": {"issue": 32.82, "fma": 21.37, "alu": 3.38, "xu": 3.15, "lsu": 3.37},
     "3d-vz-10k-256cube": {"issue": 32.82, "fma": 21.37, "alu": 3.38, "xu": 3.15, "lsu": 3.37},
-    "3d-vz-40k-128cube": {"issue": 34.64, "fma": 22.81, "alu": 3.56, "xu": 3.20, "lsu": 3.42},
-    "25d-vz-20k-512x400": {"issue": 35.45, "fma": 23.96, "alu": 3.84, "xu": 2.37, "lsu": 3.75},
+    "3d-vz-40k-128cube": {"issue": 34.71, "fma": 22.81, "alu": 3.68, "xu": 3.20, "lsu": 3.42},
+    "25d-vz-20k-512x400": {"issue": 35.67, "fma": 24.02, "alu": 3.91, "xu": 2.37, "lsu": 3.75},
     # mixed precision: U16 radial table + FP16 traces (k_migrate<table, obliquity, FP16, M=2, U16>)
     "3d-vz-100k-256cube-table-u16-f16": {"issue": 30.31, "fma": 16.50, "alu": 4.75, "xu": 2.20, "lsu": 5.40},
     "3d-vz-10k-256cube-table-u16-f16": {"issue": 30.31, "fma": 16.50, "alu": 4.75, "xu": 2.20, "lsu": 5.40},
@@ -75,10 +75,10 @@ PIPE_MIX = {
 # DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
 # (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
 TRAFFIC = {
-    "3d-vz-100k-256cube": 748463488 + 1037584256,
+    "3d-vz-100k-256cube": 748677376 + 1038178624,
     "3d-vz-10k-256cube": 87995904 + 1025581056,
-    "3d-vz-40k-128cube": 280563968 + 111368192,
-    "25d-vz-20k-512x400": 91586560 + 2943232,
+    "3d-vz-40k-128cube": 281054208 + 111904000,
+    "25d-vz-20k-512x400": 91481600 + 2949632,
     "3d-vz-10k-256cube-demigrate": 4994777088 + 8305233152,
     "3d-vz-10k-256cube-vgrad": 1130428928 + 15748608,
     "3d-vz-10k-256cube-table-u16-f16": 39405056 + 1024635648,

@@ -21,17 +21,18 @@ constexpr int BMAX = 64;
 constexpr float MAGIC = 12582912.0f;
 constexpr int MAGIC_BITS = 0x4B400000;
 
-// Coefficients of the ln(1 + rho) polynomial of the linear-velocity delta formulation: the
-// shortest length of LP_TERMS whose fit meets the error budget over the tile's rho bound
-// (6 terms for compact tiles of a fine grid, up to 20 for wide ones).  LP_SHORT is the length
-// used where no polynomial is evaluated and the reference length for tile choice.
+// The two-leg ln(1 + rho) fit of the linear-velocity delta formulation (rho = U/U_c - 1 of both
+// legs): the shortest length of LP_TERMS whose fit meets the error budget over the tile's rho
+// bound decides whether a tile is accepted (6 terms for compact tiles of a fine grid, up to 20
+// for wide ones).  LP_SHORT is the reference length for tile choice and the template length of
+// kernels that evaluate no polynomial.
 constexpr int LP_TERMS[] = {6, 8, 10, 12, 20};
 constexpr int N_LP_TERMS = 5;
 constexpr int LP_SHORT = 12;
 constexpr int LP_LONG = 20;
-// The migration kernel evaluates ln(1 + rho) per leg (rho = U/U_c - 1 of one leg, half the
-// range of the two-leg rho) and caches the source leg's term: lengths up to LG_MONO are
-// monomial in rho (no change of variable), longer ones use the shifted variable t.
+// The kernels evaluate ln(1 + rho) per leg (rho = U/U_c - 1 of one leg, half the range of the
+// two-leg rho) and cache or share the source leg's term: lengths up to LG_MONO are monomial in
+// rho (no change of variable), longer ones use the shifted variable t.
 constexpr int LG_TERMS[] = {4, 5, 6, 8, 12, 20};
 constexpr int N_LG_TERMS = 6;
 constexpr int LG_MONO = 8;
@@ -71,7 +72,7 @@ struct GeomParams {
     double a;                // k^2 / (2 v0): q = a R^2 / (v0 + k z)
     float lp[LP_LONG];       // ln(1 + rho) = rho (1 + rho Q(t)), t = rho lp_s + lp_o,
                              // Q(t) = sum_j lp[j + 1] t^j (Chebyshev-node fit in t on [-1, 1])
-    float lpc[LP_LONG];      // lp scaled by C1 + C1lo (the migration kernel forms tau from them)
+    float lpc[LP_LONG];      // lp scaled by C1 + C1lo (host: the tile acceptance fit)
     float lp_s, lp_o;
     int lp_terms;            // one of LP_TERMS; lp[lp_terms..LP_LONG-1] are zero
     float lgc[LP_LONG];      // per-leg fit, scaled by C1 + C1lo: ln(1 + rho) = rho (1 + rho Q),

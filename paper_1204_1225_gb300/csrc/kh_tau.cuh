@@ -24,30 +24,8 @@
 
 namespace kh {
 
-// ln(1 + rho) lengths instantiated for linear v(z): every length of LP_TERMS with the fast
-// (approximate) square root and reciprocal; 12 and 20 with the IEEE ones, where a shorter fit
-// runs in the 12-term kernel (its upper coefficients are zero, so Horner's rule returns the
-// same value bit for bit).  Calls f(std::integral_constant<int, L>()) for the length L.
-template <bool FAST, typename F>
-cudaError_t with_lp(int terms, F&& f)
-{
-    if constexpr (FAST) {
-        switch (terms) {
-            case 6: return f(std::integral_constant<int, 6>());
-            case 8: return f(std::integral_constant<int, 8>());
-            case 10: return f(std::integral_constant<int, 10>());
-            case 12: return f(std::integral_constant<int, 12>());
-            case 20: return f(std::integral_constant<int, 20>());
-            default: return cudaErrorInvalidValue;
-        }
-    } else {
-        if (terms <= LP_SHORT) return f(std::integral_constant<int, LP_SHORT>());
-        if (terms <= LP_LONG) return f(std::integral_constant<int, LP_LONG>());
-        return cudaErrorInvalidValue;
-    }
-}
-
-// Per-leg fit lengths of the migration kernel: every length of LG_TERMS with the fast
+// Per-leg fit lengths of the kernels (migration, adjoint, gradient): every length of LG_TERMS
+// with the fast
 // math variants; the IEEE variants take LG_MONO (monomial) or LP_LONG (shifted), the
 // coefficients beyond the fitted length being zero.
 template <bool FAST, typename F>
@@ -107,22 +85,11 @@ __device__ __forceinline__ float4 z_constants_m(double z, double zc, const GeomP
                        (float)(alpha * z * z));
 }
 
-// The window-relative time: tau - lo = C1 ln(1 + rho) + c0rel, formed as
-// rho (C1 + rho C1 Q(t)) + c0rel with the C1-scaled coefficients g.lpc.  The rounding of
-// C1 + rho C1 Q (half an ulp of C1, times |rho| <= rho_max) is that of ln(1 + rho) itself
-// scaled by C1; the FP32 rounding error C1lo of C1 is of the same size and is left out.
-template <int NT>
-__device__ __forceinline__ float tau_poly(float rho, const GeomParams& g, float c0rel)
-{
-    const float t = fmaf(rho, g.lp_s, g.lp_o);
-    float p = g.lpc[NT - 1];
-#pragma unroll
-    for (int i = NT - 2; i >= 1; --i) p = fmaf(p, t, g.lpc[i]);
-    return fmaf(rho, fmaf(rho, p, g.C1), c0rel);
-}
-
 // base + C1 ln(1 + rho) for one leg from the per-leg fit (lgc = C1-scaled coefficients):
-// Horner in rho itself for NT <= LG_MONO, in t = rho lg_s + lg_o for the longer fits.
+// Horner in rho itself for NT <= LG_MONO, in t = rho lg_s + lg_o for the longer fits, then
+// rho (C1 + rho C1 Q) + base.  The rounding of C1 + rho C1 Q (half an ulp of C1, times |rho|) is
+// that of ln(1 + rho) itself scaled by C1; the FP32 rounding error C1lo of C1 is of the same
+// size and is left out.
 template <int NT>
 __device__ __forceinline__ float leg_log(float rho, const GeomParams& g, float base)
 {

@@ -150,6 +150,25 @@ KH_API kh_status kirchhoff_traveltime(kh_plan p, int n, const float* px, const f
                                const float* pz, const float* lx, const float* ly, float* T,
                                void* cuda_stream);
 
+/* Host-only report (no device work, no plan) of the ln(1 + rho) fits the linear-v(z) kernels
+ * use for an image tile of cx x cy columns x (cz * 16) depths of descriptor `d`; the T of
+ * Eq. (1) is the linear-gradient closed form, evaluated per leg as
+ * T - T_c = ln(1 + rho) / |k| with rho = U/U_c - 1 relative to the tile centre c.
+ *   two_leg_terms: length of the two-leg fit that accepts the tile;
+ *   leg_terms:     length of the per-leg fit the kernels evaluate (4, 5, 6, 8, 12 or 20);
+ *   leg_bound:     b, with rho in [expm1(-b), expm1(b)] for every leg over the tile;
+ *   coef:          20 floats, the per-leg coefficients scaled by C1 = 1/(|k| dt):
+ *                  C1 ln(1 + rho) = rho (coef[0] + rho sum_{j>=1} coef[j] x^(j-1)),
+ *                  x = rho * scale + offset (scale 1, offset 0 up to 8 terms), zero beyond
+ *                  leg_terms;
+ *   c1:            C1 in FP64.
+ * Any output pointer may be NULL.  Errors: KH_ERR_INVALID_ARG (bad descriptor or tile, or a
+ * descriptor that is not linear v(z) with k != 0), KH_ERR_UNSUPPORTED (no fit length meets the
+ * budget of 5e-6 samples for the tile). */
+KH_API kh_status kirchhoff_fit_report(const kh_desc* d, int cx, int cy, int cz, int* two_leg_terms,
+                                      int* leg_terms, double* leg_bound, float* coef, float* scale,
+                                      float* offset, double* c1);
+
 /* Work count of Eq. (2): number of (image point, trace) pairs with a valid offset bin
  * and the trace midpoint within the aperture of the point's column, computed on the
  * device with the same FP32 aperture test as the migration kernel.  *out_count is a

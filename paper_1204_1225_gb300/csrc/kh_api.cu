@@ -1149,6 +1149,30 @@ kh_status kirchhoff_traveltime(kh_plan p, int n, const float* px, const float* p
     return e == cudaSuccess ? KH_OK : cuda_fail(e, "traveltime kernel");
 }
 
+kh_status kirchhoff_fit_report(const kh_desc* d, int cx, int cy, int cz, int* two_leg_terms, int* leg_terms,
+                               double* leg_bound, float* coef, float* scale, float* offset, double* c1)
+{
+    kh_status st = validate_desc(d);
+    if (st != KH_OK) return st;
+    if (d->vel != KH_VEL_LINEAR_Z || d->k == 0.0)
+        return fail(KH_ERR_INVALID_ARG, "the fit report is for linear v(z) descriptors with k != 0");
+    if (cx < 1 || cy < 1 || cz < 1 || cz > 16 || cx * cy * cz != CONSUMERS || (d->dim == 2 && cy != 1))
+        return fail(KH_ERR_INVALID_ARG, "tile cx*cy*cz must equal %d with cz <= 16 (cy = 1 for dim 2)", CONSUMERS);
+    const TileShape t = shape(*d, cx, cy, cz);
+    GeomParams g = geom_of(*d);
+    if ((st = prepare_linear(*d, t, g)) != KH_OK) return st;
+    const double b = rho_bound(*d, g, cx, cy, cz);
+    if (two_leg_terms) *two_leg_terms = g.lp_terms;
+    if (leg_terms) *leg_terms = g.lg_terms;
+    if (leg_bound) *leg_bound = 0.5 * (b - 1e-6) + 1e-6;
+    if (coef)
+        for (int j = 0; j < LP_LONG; ++j) coef[j] = g.lgc[j];
+    if (scale) *scale = g.lg_s;
+    if (offset) *offset = g.lg_o;
+    if (c1) *c1 = (double)g.C1 + (double)g.C1lo;
+    return KH_OK;
+}
+
 kh_status kirchhoff_sync(kh_plan p, void* cuda_stream)
 {
     if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");

@@ -60,7 +60,7 @@ EXPORTS = ["kirchhoff_create", "kirchhoff_destroy", "kirchhoff_migrate", "kirchh
            "kirchhoff_batch_info", "kirchhoff_batch_destroy", "kirchhoff_sync",
            "kirchhoff_set_option", "kirchhoff_launch_count", "kirchhoff_last_error",
            "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read",
-           "kirchhoff_migrate_noalloc"]
+           "kirchhoff_migrate_noalloc", "kirchhoff_fit_report"]
 
 
 def lib(path: str = LIB_PATH):
@@ -92,6 +92,9 @@ def lib(path: str = LIB_PATH):
             L.kirchhoff_launch_count.argtypes = [P]
             L.kirchhoff_profile.argtypes = [P, I]
             L.kirchhoff_migrate_noalloc.argtypes = [ctypes.POINTER(kh_desc), I, P, P, P, P, P, P, P, P]
+            D, F = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+            L.kirchhoff_fit_report.argtypes = [ctypes.POINTER(kh_desc), I, I, I, ctypes.POINTER(I),
+                                               ctypes.POINTER(I), D, F, F, F, D]
             L.kirchhoff_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_longlong)]
             L.kirchhoff_launch_count.restype = ctypes.c_longlong
@@ -189,6 +192,19 @@ def kirchhoff_count(plan, ntr, sx, sy, rx, ry, stream=None) -> int:
     _check(lib().kirchhoff_count(ctypes.c_void_p(plan), int(ntr), _ptr(sx), _ptr(sy), _ptr(rx),
                                  _ptr(ry), ctypes.byref(out), _stream(stream)))
     return int(out.value)
+
+
+def kirchhoff_fit_report(desc: kh_desc, tile) -> dict:
+    """Host-only: the ln(1 + rho) fits the linear-v(z) kernels use for a (cx, cy, cz) tile."""
+    two, leg = ctypes.c_int(0), ctypes.c_int(0)
+    bound, c1 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    coef = (ctypes.c_float * 20)()
+    scale, offset = ctypes.c_float(0.0), ctypes.c_float(0.0)
+    _check(lib().kirchhoff_fit_report(ctypes.byref(desc), int(tile[0]), int(tile[1]), int(tile[2]),
+                                      ctypes.byref(two), ctypes.byref(leg), ctypes.byref(bound), coef,
+                                      ctypes.byref(scale), ctypes.byref(offset), ctypes.byref(c1)))
+    return {"two_leg_terms": two.value, "leg_terms": leg.value, "leg_bound": bound.value,
+            "coef": list(coef), "scale": scale.value, "offset": offset.value, "c1": c1.value}
 
 
 def kirchhoff_migrate_noalloc(desc: kh_desc, ntr, sx, sy, rx, ry, traces, image, status=None,

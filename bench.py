@@ -45,15 +45,15 @@ from paper_1204_1225_gb300 import survey as sv  # noqa: E402
 # (dispatch: 4 sub-partitions x 32 lanes; FP32 FMA pipe 128; integer/logic ALU 64; MUFU
 # special-function unit 16, measured by the throughput probe in profiles/mufu_fma_throughput.md;
 # shared-memory load/store unit 32).  The migration kernel is a gather with no HBM bound
-# (about 4e-4 algorithmic bytes per contribution), so its roofline is the smallest of
-# N_SM x clock x lanes_p / n_p over these pipes, n_p = the kernel's executed thread
-# instructions per contribution on pipe p (ncu sm__inst_executed_pipe_*.sum x 32 and
+# (about 1.1e-3 algorithmic bytes per contribution: traces and image once), so its roofline is
+# the smallest of N_SM x clock x lanes_p / n_p over these pipes, n_p = the kernel's executed
+# thread instructions per contribution on pipe p (ncu sm__inst_executed_pipe_*.sum x 32 and
 # smsp__thread_inst_executed.sum, divided by the contribution count).
 N_SM = 152
 LANES_PER_SM_CLK = {"issue": 128, "fma": 128, "alu": 64, "xu": 16, "lsu": 32}
 # n_p per workload's kernel variant, from profiles/k_migrate_pipe_mix.md (one ncu capture of
 # k_migrate per variant; the 100k-trace 256^3 workload runs the variant measured on its
-# 10k-trace case: same grid, tile and 6-term fit).
+# 10k-trace case: same grid, tile and 5-term per-leg fit).
 PIPE_MIX = {
     "3d-vz-100k-256cube": {"issue": 32.82, "fma": 21.37, "alu": 3.38, "xu": 3.15, "lsu": 3.37},
     "3d-vz-10k-256cube": {"issue": 32.82, "fma": 21.37, "alu": 3.38, "xu": 3.15, "lsu": 3.37},

@@ -97,13 +97,8 @@ def lib(path: str = LIB_PATH):
                                                ctypes.POINTER(I), D, F, F, F, D]
             L.kirchhoff_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_longlong)]
-            L.kirchhoff_launch_count.restype = ctypes.c_longlong
-            L.kirchhoff_last_error.restype = ctypes.c_char_p
-            L.kirchhoff_version.restype = ctypes.c_char_p
             for name in EXPORTS:
-                f = getattr(L, name)
-                if f.restype is ctypes.c_int or f.restype is None:
-                    f.restype = S
+                getattr(L, name).restype = S
             L.kirchhoff_launch_count.restype = ctypes.c_longlong
             L.kirchhoff_last_error.restype = ctypes.c_char_p
             L.kirchhoff_version.restype = ctypes.c_char_p

@@ -469,7 +469,7 @@ def run_batched(args, surveys, ws, rank, local):
     t_tune = time.perf_counter()
     tiles = {}
     if not args.no_tune:
-        tuner = TileTuner(path=args.tile_cache or os.path.join(ROOT, "gpurun_out", "tiles.json"))
+        tuner = TileTuner(path=args.tile_cache or os.path.join(ROOT, ".tile_cache", "tiles.json"))
         for (p, h, d, _) in jobs:
             t = tuner.choose(p, h, d)
             tiles[f"{t[0]}x{t[1]}x{t[2]}"] = tiles.get(f"{t[0]}x{t[1]}x{t[2]}", 0) + 1

@@ -8,10 +8,13 @@
 // tile footprint, bounds the two-way time over the tile box to a sample window
 // [lo, hi], computes the trace's FP64 reference at the tile centre (linear v(z)), and
 // stages the window into a 3-deep shared-memory ring with one cp.async.bulk per trace
-// (16-byte aligned, no multicast) completing on the stage's mbarrier.  Consumers evaluate
-// tau for their points (kh_tau.cuh), read the staged samples, interpolate linearly, weight
-// and accumulate.  All mbarrier waits are bounded; a wait that runs out sets the plan's
-// status word and the CTA leaves only after its copies have landed.
+// (16-byte aligned, no multicast) completing on the stage's mbarrier.  FP32 traces arrive as
+// (sample, step) pairs, so one 8-byte shared load and one FMA give an interpolated sample.
+// Consumers evaluate tau for their points (kh_tau.cuh; linear v(z): per-leg logarithms with the
+// source leg cached per source position), read the staged samples, interpolate linearly,
+// weight and accumulate; a warp whose window is not clipped and whose lanes all lie in the
+// aperture and the grid skips the validity test.  All mbarrier waits are bounded; a wait that
+// runs out sets the plan's status word and the CTA leaves only after its copies have landed.
 #pragma once
 
 #include <cuda_bf16.h>

@@ -5,9 +5,10 @@
 // validation, each job's geometry, tile and ln(1 + rho) fit, binning of its headers into the
 // batch's own buffers, a per-(tile, bin) count of the traces that survive the aperture cull,
 // and the work list of (job, tile, bin) items sorted by estimated cost, longest first.
-// kirchhoff_migrate_batched then issues only stream work (row padding where a job's rows are
-// not 16-byte aligned, a memset of the work counters, and the persistent kernel once per
-// ln(1 + rho) fit length present in the batch), so a CUDA graph can capture and replay it.
+// kirchhoff_migrate_batched then issues only stream work (row staging: FP32 rows as (sample,
+// step) pairs, or 16-bit rows padded where they are not 16-byte aligned; a memset of the work
+// counters; and the persistent kernel once per ln(1 + rho) fit length present in the batch),
+// so a CUDA graph can capture and replay it.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>

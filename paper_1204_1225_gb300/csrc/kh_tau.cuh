@@ -13,9 +13,10 @@
 //             = alpha(z) ((x_h - c_h).(x_h + c_h - 2 s_h) + ...),  kappa(z) = -k (z - z_c)/(v0 + k z_c)
 //     w - w_c = (q - q_c)(q + q_c + 2)/(w + w_c)
 //     u/u_c - 1 = (q - q_c)(1 + (q + q_c + 2)/(w + w_c)) / u_c
-//     tau - tau_c = ln((u_s/u_sc)(u_r/u_rc)) / (|k| dt),
+//     tau - tau_c = (ln(u_s/u_sc) + ln(u_r/u_rc)) / (|k| dt),
 // with the per-z products alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2 formed in FP64,
-// and ln(1 + rho) from a polynomial fitted on the host for the tile's |rho| bound.
+// and each leg's ln(1 + rho) from a polynomial fitted on the host for the tile's per-leg
+// |rho| bound (leg_log), so that the source leg's term can be cached or shared.
 #pragma once
 
 #include <type_traits>

@@ -280,7 +280,9 @@ KH_API long long kirchhoff_launch_count(kh_plan p);
  * `status` is an optional DEVICE int: it is zeroed, then bit 0 is set if a bounded in-kernel
  * wait ran out (NULL: a word inside the scratch is used and the outcome is not reported).
  * The first call on each device looks up the scratch's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls on a device share the scratch
+ * make that first call before any stream capture.  The address is kept for the life of the
+ * process: it belongs to the device's primary context, so a process that destroys that
+ * context (cudaDeviceReset) must not call this entry point on that device afterwards.  All calls on a device share the scratch
  * and it keeps the previous call's contents: calls that overlap on the GPU (for example on
  * two streams) race and must be serialised by the caller. */
 KH_API kh_status kirchhoff_migrate_noalloc(const kh_desc* d, int ntr, const float* sx,

@@ -208,12 +208,15 @@ static int inside_aperture(const ko_desc* d, float cx, float cy, float sx, float
     if (d->aperture <= 0.0) return 1;
     float mx = (sx + rx) * 0.5f;
     float my = (sy + ry) * 0.5f;
+    if (ko_mutation == 7) { mx = sx; my = sy; }
+    if (ko_mutation == 9) { mx = sx + rx; my = sy + ry; }
     float ex = cx - mx;
     float ey = cy - my;
     float ex2 = ex * ex;
     float ey2 = ey * ey;
     float d2 = ex2 + ey2;
     float a2 = (float)(d->aperture * d->aperture);
+    if (ko_mutation == 8) return d2 < a2;
     return d2 <= a2;
 }
 
@@ -231,6 +234,10 @@ static contrib contribution(const ko_desc* d, double x, double y, double z, doub
 {
     contrib c;
     memset(&c, 0, sizeof c);
+    if (ko_mutation == 10 && d->aperture > 0.0) {
+        double mx = 0.5 * (sx + rx) - x, my = 0.5 * (sy + ry) - y;
+        if (mx * mx + my * my + z * z > d->aperture * d->aperture) return c;
+    }
     double Rs = sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy) + z * z);
     double Rr = sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry) + z * z);
     if (ko_mutation == 3) Rr = Rs;

@@ -121,6 +121,37 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _validate(specs, device=None):
+    """Refuses tensors whose dtype, size or device do not match what the library reads or
+    writes through their pointers (a short buffer would be read or written past its end, a
+    wider dtype silently reinterpreted).  ``specs``: (tensor, name, dtype, numel, shape)
+    tuples, numel or shape None when not checked.  Types and sizes are checked for every
+    tensor before any device is."""
+    for t, name, dtype, numel, shape in specs:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"kirchhoff: {name} must be a torch tensor")
+        if t.dtype != dtype:
+            raise ValueError(f"kirchhoff: {name} must be {dtype}, got {t.dtype}")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"kirchhoff: {name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"kirchhoff: {name} must have {numel} elements, got {t.numel()}")
+    for t, name, *_ in specs:
+        if not t.is_cuda:
+            raise ValueError(f"kirchhoff: {name} must live on a CUDA device (no CPU path)")
+        dev = torch.cuda.current_device() if device is None else device
+        if t.device.index != dev:
+            raise ValueError(f"kirchhoff: {name} is on cuda:{t.device.index}, the plan's device "
+                             f"is cuda:{dev}")
+        if not t.is_contiguous():
+            raise ValueError(f"kirchhoff: {name} must be contiguous")
+
+
+def _header_specs(hdr):
+    return [(t, name, torch.float32, hdr.ntr, None)
+            for name, t in zip(("sx", "sy", "rx", "ry"), hdr.args())]
+
+
 def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -205,7 +236,20 @@ def kirchhoff_fit_report(desc: kh_desc, tile) -> dict:
 def kirchhoff_migrate_noalloc(desc: kh_desc, ntr, sx, sy, rx, ry, traces, image, status=None,
                               stream=None) -> None:
     """Migration without any device allocation (fixed library scratch, ntr <= 65536); for
-    callers that cannot allocate.  ``status``: optional CUDA int32 tensor of one element."""
+    callers that cannot allocate.  ``status``: optional CUDA int32 tensor of one element,
+    zeroed by the call and set to 1 if a bounded in-kernel wait ran out (the image is then
+    incomplete); read it after synchronising.  With ``status=None`` such a timeout is not
+    reported at all, so pass a status tensor wherever a partial image matters."""
+    ntr = int(ntr)
+    specs = [(image, "image", torch.float32,
+              desc.n_bins * (desc.ny if desc.dim == 3 else 1) * desc.nx * desc.nz, None)]
+    if ntr > 0:
+        hdr = (("sx", sx), ("rx", rx)) + ((("sy", sy), ("ry", ry)) if desc.dim == 3 else ())
+        specs += [(t, name, torch.float32, ntr, None) for name, t in hdr]
+        specs.append((traces, "traces", torch.float32, ntr * desc.nt, None))
+    if status is not None:
+        specs.append((status, "status", torch.int32, 1, None))
+    _validate(specs)
     _check(lib().kirchhoff_migrate_noalloc(ctypes.byref(desc), int(ntr), _ptr(sx), _ptr(sy),
                                            _ptr(rx), _ptr(ry), _ptr(traces), _ptr(image),
                                            _ptr(status), _stream(stream)))
@@ -306,6 +350,7 @@ class Plan:
         self.handle = kirchhoff_create(self.desc)
         self.image_shape = (s.n_bins, s.ny if s.dim == 3 else 1, s.nx, s.nz)
         self.nt = s.nt
+        self.device = torch.cuda.current_device()
         kirchhoff_set_option(self.handle, KH_OPT_FAST_MATH, 1 if fast_math else 0)
         if tile is not None:
             cx, cy, cz = tile
@@ -331,24 +376,38 @@ class Plan:
         kirchhoff_set_option(self.handle, KH_OPT_TILE, code)
 
     def migrate(self, hdr: Headers, traces, out=None, stream=None):
+        specs = _header_specs(hdr) + [(traces, "traces", self.trace_dtype, hdr.ntr * self.nt, None)]
+        if out is not None:
+            specs.append((out, "image", torch.float32, None, self.image_shape))
+        _validate(specs, self.device)
         if out is None:
             out = torch.empty(self.image_shape, dtype=torch.float32, device=traces.device)
         kirchhoff_migrate(self.handle, hdr.ntr, *hdr.args(), traces, out, stream)
         return out
 
     def demigrate(self, hdr: Headers, image, out=None, stream=None):
+        specs = _header_specs(hdr) + [(image, "image", torch.float32, None, self.image_shape)]
+        if out is not None:
+            specs.append((out, "traces_out", torch.float32, hdr.ntr * self.nt, None))
+        _validate(specs, self.device)
         if out is None:
             out = torch.empty((hdr.ntr, self.nt), dtype=torch.float32, device=image.device)
         kirchhoff_demigrate(self.handle, hdr.ntr, *hdr.args(), image, out, stream)
         return out
 
     def velocity_grad(self, hdr: Headers, image, traces, out=None, stream=None):
+        specs = _header_specs(hdr) + [(image, "image", torch.float32, None, self.image_shape),
+                                      (traces, "traces", torch.float32, hdr.ntr * self.nt, None)]
+        if out is not None:
+            specs.append((out, "out_dv0_dk", torch.float64, 2, None))
+        _validate(specs, self.device)
         if out is None:
             out = torch.empty(2, dtype=torch.float64, device=image.device)
         kirchhoff_velocity_grad(self.handle, hdr.ntr, *hdr.args(), image, traces, out, stream)
         return out
 
     def count(self, hdr: Headers, stream=None) -> int:
+        _validate(_header_specs(hdr), self.device)
         return kirchhoff_count(self.handle, hdr.ntr, *hdr.args(), stream)
 
     def traveltime(self, px, py, pz, lx, ly, stream=None):

@@ -167,3 +167,23 @@ def test_wait_timeout_is_reported_and_context_survives():
     img = p.migrate(hdr, dt)
     p.sync()
     assert rel_l2(img.double().cpu().numpy(), oracle.migrate(s, d)) < FP32_REL_L2
+
+
+def test_aperture_hand_geometry_and_count():
+    # the hand geometry of the oracle's aperture pin: trace j carries the constant 2^j, so the
+    # image at every depth is the sum of the codes of the traces the aperture keeps (the
+    # midpoint within A = 300 m of the column, <= inside, horizontal distance only)
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    from test_oracle_pins import APERTURE_TRACES, aperture_survey
+    s = aperture_survey()
+    codes = 2.0 ** np.arange(len(APERTURE_TRACES))
+    d = np.repeat(codes[:, None], s.nt, axis=1).astype(np.float32)
+    want = sum(c for c, (_, kept) in zip(codes, APERTURE_TRACES) if kept)
+    got, p = gpu_migrate(s, d)
+    assert np.allclose(got[0, 0, 0], want, rtol=1e-6, atol=0), got[0, 0, 0]
+    assert p.count(kh.Headers.of(s)) == sum(kept for _, kept in APERTURE_TRACES) * s.nz
+    # a row of nine columns with one midpoint at x = 50 and A = 250: six columns (hand count)
+    row = s.replace(dim=2, nx=9, ox=-400.0, dx=100.0, nz=3, aperture=250.0,
+                    sx=np.zeros(1, np.float32), sy=np.zeros(1, np.float32),
+                    rx=np.full(1, 100.0, np.float32), ry=np.zeros(1, np.float32))
+    assert kh.Plan(row).count(kh.Headers.of(row)) == 6 * row.nz

@@ -328,6 +328,57 @@ def test_cgls_reaches_least_squares_solution():
     assert rel(m.ravel(), m_ls) < 1e-6
 
 
+# ------------------------------------------- aperture ("traces close enough", after Eq. 2)
+
+# One image column at the origin and A = 300 m.  Each trace carries one constant value,
+# 2^j for trace j, so with W = 1 and every tau inside the trace the image at any depth is
+# the sum of the codes of the traces kept there.  The geometry is chosen by hand:
+APERTURE_TRACES = [
+    # (sx, sy, rx, ry), kept?  -- reason
+    ((300.0, 0.0, 300.0, 0.0), True),     # midpoint exactly A from the column: <= is inside
+    ((302.0, 0.0, 300.0, 0.0), False),    # midpoint at A + 1 m
+    ((0.0, 0.0, 700.0, 0.0), False),      # source on the column, midpoint 350 m away
+    ((-500.0, 0.0, 500.0, 0.0), True),    # source 500 m away, midpoint on the column
+    ((180.0, 0.0, 180.0, 480.0), True),   # midpoint (180, 240): exactly 300 m in 2D
+    ((180.0, 0.0, 180.0, 482.0), False),  # midpoint (180, 241): 301 m
+    ((100.0, 0.0, 300.0, 0.0), True),     # midpoint 200 m away
+]
+APERTURE_DEPTHS = 5                        # z = 0, 250, 500, 750, 1000 m
+
+
+def aperture_survey():
+    g = np.array([t for t, _ in APERTURE_TRACES], dtype=np.float64)
+    return tiny_survey(dim=3, nz=APERTURE_DEPTHS, dz=250.0, aperture=300.0, nt=400,
+                       sx=g[:, 0], sy=g[:, 1], rx=g[:, 2], ry=g[:, 3])
+
+
+def check_aperture_hand_geometry():
+    s = aperture_survey()
+    codes = 2.0 ** np.arange(len(APERTURE_TRACES))
+    d = np.repeat(codes[:, None], s.nt, axis=1)
+    want = sum(c for c, (_, kept) in zip(codes, APERTURE_TRACES) if kept)
+    img = oracle.migrate(s, d)[0, 0, 0]
+    # the decision is horizontal only: the same traces are kept at every depth
+    assert np.allclose(img, want, rtol=0, atol=1e-9), (img, want)
+    assert oracle.count(s) == sum(kept for _, kept in APERTURE_TRACES) * s.nz
+
+
+def check_aperture_count_row():
+    # nine columns x = -400 ... 400 (100 m apart), one trace with its midpoint at x = 50
+    # and A = 250 m: the columns -200 ... 300 are within 250 m (the two ends exactly),
+    # so the Eq. 2 count is 6 columns x nz
+    s = tiny_survey(nx=9, ox=-400.0, dx=100.0, nz=3, aperture=250.0, sx=[0.0], rx=[100.0])
+    assert oracle.count(s) == 6 * s.nz
+
+
+def test_aperture_hand_geometry():
+    check_aperture_hand_geometry()
+
+
+def test_aperture_count_hand_row():
+    check_aperture_count_row()
+
+
 # -------------------------------------------------------------- the pins catch mistakes
 
 MUTATIONS = [
@@ -338,6 +389,13 @@ MUTATIONS = [
     (5, check_traveltime_derivatives), # sign of a derivative term
     (5, check_vgrad_fd),
     (6, check_hand_contributions),     # interpolation weights swapped
+    (7, check_aperture_hand_geometry), # aperture centred on the source, not the midpoint
+    (7, check_aperture_count_row),
+    (8, check_aperture_hand_geometry), # strict < at the aperture edge
+    (8, check_aperture_count_row),
+    (9, check_aperture_hand_geometry), # midpoint without its 1/2
+    (9, check_aperture_count_row),
+    (10, check_aperture_hand_geometry),  # depth term in the aperture distance
 ]
 
 

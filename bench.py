@@ -307,11 +307,18 @@ def main():
                     help="batch: one persistent kernel, or each job's kernel on forked streams")
     ap.add_argument("--op", default="migrate", choices=["migrate", "demigrate", "vgrad"],
                     help="operator timed: migration (Eq. 1), its adjoint, or the (v0, k) gradient")
+    ap.add_argument("--aperture", type=float, default=None,
+                    help="override the workload's aperture (metres)")
+    ap.add_argument("--spatial-sort", type=int, default=1,
+                    help="1: traces sorted by (bin, midpoint cell), each CTA examines the cells of "
+                         "its aperture disc; 0: each CTA examines its whole bin")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     ws, rank, local = dist_init()
     s = workloads()[args.workload]()
+    if args.aperture is not None and not isinstance(s, list):
+        s = s.replace(aperture=args.aperture, name=f"{s.name}-A{args.aperture:g}")
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, s[0] if isinstance(s, list) else s)
@@ -328,6 +335,7 @@ def main():
     tdt = _TDT[args.trace_dtype]
     s_run = s.replace(vel="table") if args.vel == "table" else s
     plan = kh.Plan(s_run, fast_math=bool(args.fast_math), trace_dtype=tdt, table_dtype=args.table_dtype)
+    plan.set_spatial_sort(bool(args.spatial_sort))
     hdr = kh.Headers.of(s, device=dev)
     traces = synth_traces(s, kh.Plan(s), dev).to(tdt).contiguous()
     image = torch.empty(plan.image_shape, dtype=torch.float32, device=dev)
@@ -364,6 +372,7 @@ def main():
     plan.sync()
     launches = plan.launches - launches0
     kern_ms, kern_n = plan.profile_read()
+    stage_stats = plan.staging_stats()
     plan.profile(False)
     t_ms = max_over_ranks(ws, e0.elapsed_time(e1))
     barrier(ws)
@@ -409,6 +418,8 @@ def main():
         mix_key = args.workload if args.op == "migrate" else f"{args.workload}-{args.op}"
     else:
         mix_key = None
+    if args.aperture is not None or not args.spatial_sort:
+        mix_key = None   # instruction mixes were measured on the workloads as defined
     mix = PIPE_MIX.get(mix_key) if (mix_key and args.fast_math) else None
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "unit": "Gcontrib/s",
             "kernel_ms_per_launch": kern_ms / max(kern_n, 1)}
@@ -442,11 +453,20 @@ def main():
                                   f"{s.table_spacing:g} m)",
                    "l2": "inputs larger than L2 (traces %.0f MB, image %.0f MB)" % (
                        tbytes / 1e6, image.numel() * 4 / 1e6),
-                   "parallelism": "replicas" if ws > 1 else "single"},
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "trace_order": "bin, midpoint cell" if args.spatial_sort else "bin",
+                   "staging_per_cta": _staging(*stage_stats)},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def _staging(examined, staged, ctas):
+    """Traces the staging warps examined and staged per CTA (migration and gradient kernels)."""
+    if not ctas:
+        return None
+    return {"examined": round(examined / ctas, 1), "staged": round(staged / ctas, 1), "ctas": ctas}
 
 
 def run_batched(args, surveys, ws, rank, local):

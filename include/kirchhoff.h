@@ -169,6 +169,34 @@ KH_API kh_status kirchhoff_fit_report(const kh_desc* d, int cx, int cy, int cz, 
                                       int* leg_terms, double* leg_bound, float* coef, float* scale,
                                       float* offset, double* c1);
 
+/* ---------------------------------------------------------------- the binning sort
+ * Eq. (1)'s delta(X - |x_s - x_r|) assigns each trace to one offset bin, and only traces "close
+ * enough" to an image point contribute (Sec. 3 after Eq. 2).  Before every migration and
+ * gradient call the library sorts the traces by (offset bin, midpoint cell, original index) on
+ * a grid of cells over the image columns widened by the aperture, so that each CTA examines
+ * only the cells that meet its tile's aperture disc.  These two calls expose that step.
+ *
+ * kirchhoff_cell_grid (host only): the grid of descriptor `d` with spatial sorting on (1) or off
+ * (0) (see KH_OPT_SPATIAL_SORT for when "on" still gives one cell): ncx x ncy square cells from
+ * (gx0, gy0), inv_cell = 1 / cell side in metres.  A trace's
+ * cell is cx = floor((m_x - gx0) * inv_cell), cy = floor((m_y - gy0) * inv_cell) (FP64 products
+ * of the FP32 midpoint m = (s + r) * 0.5f; cy = 0 for dim 2), its key
+ * bin * ncx * ncy + cy * ncx + cx.  Traces without a bin, or whose cell is outside the grid
+ * (farther than the aperture from every image column), are dropped.  With no aperture
+ * (aperture <= 0) there is one cell (ncx = ncy = 1, inv_cell = 0) and no trace is dropped for
+ * its position.  Any output pointer may be NULL.
+ *
+ * kirchhoff_bin_sort: runs the sort of plan `p` (its KH_OPT_SPATIAL_SORT setting) on the
+ * headers and copies out perm_out (DEVICE int [ntr]: the original indices of the kept traces in
+ * sorted order, first; the entries past the kept count are unspecified) and key_start_out
+ * (DEVICE int [n_bins * ncx * ncy + 1]: the first sorted position of each key; the last entry
+ * is the number of kept traces).  The sort is a stable radix sort over all SMs: equal keys keep
+ * their original order, and the result is the same on every run. */
+KH_API kh_status kirchhoff_cell_grid(const kh_desc* d, int spatial, int* ncx, int* ncy, double* gx0,
+                                     double* gy0, double* inv_cell);
+KH_API kh_status kirchhoff_bin_sort(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
+                                    const float* ry, int* perm_out, int* key_start_out, void* cuda_stream);
+
 /* Work count of Eq. (2): number of (image point, trace) pairs with a valid offset bin
  * and the trace midpoint within the aperture of the point's column, computed on the
  * device with the same FP32 aperture test as the migration kernel.  *out_count is a
@@ -249,13 +277,24 @@ KH_API kh_status kirchhoff_sync(kh_plan p, void* cuda_stream);
  *                     linear v(z) plans with nt <= 2460 as (d[i], d[i+1] - d[i]) pairs in plan
  *                     workspace (8 bytes per sample, one pass over the traces), so that each
  *                     interpolated sample takes one shared-memory load; 0 = plain samples.
- *                     The image is bit-identical either way. */
+ *                     The image is bit-identical either way.
+ *  KH_OPT_SPATIAL_SORT: 1 (default) = the binning sort orders each offset bin's traces by the
+ *                     cell of their midpoint on a grid of about half the aperture (at most 16
+ *                     cells per axis), and each CTA of the migration and gradient kernels
+ *                     examines only the cells that meet its tile widened by the aperture; the
+ *                     grid is used only where a default tile's aperture disc spans at most half
+ *                     of its cells (else one cell, as with 0);
+ *                     0 = each bin's traces in their original order, every CTA examining its
+ *                     whole bin.  Both keep exactly the same (point, trace) pairs; only the
+ *                     summation order differs (FP32 rounding).  Without an aperture there is one
+ *                     cell either way.  Demigration always sorts by bin alone. */
 typedef enum {
     KH_OPT_WAIT_POLLS = 1,
     KH_OPT_FAST_MATH = 2,
     KH_OPT_TILE = 3,
     KH_OPT_BATCH_MODE = 4,
-    KH_OPT_SAMPLE_PAIRS = 5
+    KH_OPT_SAMPLE_PAIRS = 5,
+    KH_OPT_SPATIAL_SORT = 6
 } kh_option;
 KH_API kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value);
 
@@ -265,6 +304,14 @@ KH_API kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value)
  * number of timed launches since the previous read, then resets both. */
 KH_API kh_status kirchhoff_profile(kh_plan p, int enable);
 KH_API kh_status kirchhoff_profile_read(kh_plan p, double* kernel_ms, long long* timed_launches);
+
+/* Staging statistics of the migration and gradient kernels while profiling is enabled: the
+ * traces the staging warps examined (the sorted trace ranges of the offset-bin cells that meet
+ * each CTA's aperture-widened tile), those they staged (that passed the aperture cull and have a
+ * sample window in the tile), and the CTAs that ran, each summed since the previous read, then
+ * reset.  Synchronises `cuda_stream`; all 0 if profiling was never enabled. */
+KH_API kh_status kirchhoff_staging_stats(kh_plan p, void* cuda_stream, unsigned long long* examined,
+                                         unsigned long long* staged, unsigned long long* ctas);
 
 /* Number of kernel launches issued by this plan since creation (for launch accounting). */
 KH_API long long kirchhoff_launch_count(kh_plan p);

@@ -580,25 +580,72 @@ kh_status ensure_traces_ws(kh_plan_s* p, int ntr)
     return KH_OK;
 }
 
-// Offset bin per trace, stable sort by bin, sorted headers: three launches on `s`.
+CellGrid cell_grid_of(const kh_desc& d, bool spatial)
+{
+    CellGrid cg;
+    if (!(d.aperture > 0)) return cg;
+    const double margin = d.aperture * (1.0 + 1e-5) + 2.0;   // the staging cull radius + 1 m
+    const double xmin = std::min(d.ox, d.ox + (d.nx - 1) * d.dx), xmax = std::max(d.ox, d.ox + (d.nx - 1) * d.dx);
+    const double ymin = d.dim == 3 ? std::min(d.oy, d.oy + (d.ny - 1) * d.dy) : 0.0;
+    const double ymax = d.dim == 3 ? std::max(d.oy, d.oy + (d.ny - 1) * d.dy) : 0.0;
+    const double ex = xmax - xmin + 2.0 * margin, ey = d.dim == 3 ? ymax - ymin + 2.0 * margin : 0.0;
+    const double ext = std::max(ex, ey);
+    double cs = std::max(0.5 * d.aperture, ext / MAX_CELLS_PER_AXIS);
+    if (spatial) {
+        // cells pay only if a default tile's aperture disc spans at most half of them; otherwise
+        // every CTA would examine most of its bin anyway, and the bin's original (shot) order
+        // keeps the source-leg cache warmer
+        const int nx = std::max(1, (int)std::ceil(ex / cs)), ny = d.dim == 3 ? std::max(1, (int)std::ceil(ey / cs)) : 1;
+        const double foot = (d.dim == 3 ? 16.0 : 64.0) * std::max(d.dx, d.dim == 3 ? d.dy : 0.0);
+        const int span = (int)std::ceil((foot + 2.0 * margin) / cs) + 1;
+        const double covered = (double)std::min(nx, span) * (d.dim == 3 ? std::min(ny, span) : 1);
+        if (covered > 0.5 * nx * ny) spatial = false;
+    }
+    if (!spatial) cs = ext * (1.0 + 1e-9) + 1.0;
+    cg.ncx = std::min(MAX_CELL_ROWS, std::max(1, (int)std::ceil(ex / cs)));
+    cg.ncy = d.dim == 3 ? std::min(MAX_CELL_ROWS, std::max(1, (int)std::ceil(ey / cs))) : 1;
+    cg.gx0 = xmin - margin;
+    cg.gy0 = ymin - margin;
+    cg.inv_cs = 1.0 / cs;
+    cg.margin = margin;
+    return cg;
+}
+
 kh_status bin_traces(kh_plan_s* p, int ntr, const float* sx, const float* sy, const float* rx,
-                     const float* ry, cudaStream_t s)
+                     const float* ry, cudaStream_t s, bool spatial)
 {
     kh_status st = ensure_traces_ws(p, ntr);
     if (st != KH_OK) return st;
-    if (ntr > 0) {
-        k_bin<<<(ntr + 255) / 256, 256, 0, s>>>(ntr, sx, sy, rx, ry, p->d.dim, p->d.n_bins,
-                                                p->d.bin_width, p->ws_bin);
-        ++p->launches;
-    }
-    k_sort<<<1, SORT_THREADS, 0, s>>>(ntr, p->d.n_bins, p->ws_bin, p->ws_perm, p->ws_bin_start);
-    ++p->launches;
+    const CellGrid cg = cell_grid_of(p->d, spatial && p->spatial_sort);
+    const size_t nkeys = (size_t)p->d.n_bins * cg.ncx * cg.ncy;
+    cudaError_t e;
+    if ((e = grow(p->ws_key2, p->cap_key2, (size_t)ntr)) != cudaSuccess) return cuda_fail(e, "workspace (sort keys)");
+    if ((e = grow(p->ws_perm2, p->cap_perm2, (size_t)ntr)) != cudaSuccess) return cuda_fail(e, "workspace (sort values)");
+    if ((e = grow(p->ws_hist, p->cap_hist, (size_t)sort_hist_entries(ntr))) != cudaSuccess)
+        return cuda_fail(e, "workspace (sort counts)");
+    if ((e = grow(p->ws_cell_start, p->cap_cell_start, nkeys + 1)) != cudaSuccess)
+        return cuda_fail(e, "workspace (cell starts)");
+    int launches = 0;
+    e = sort_traces(ntr, sx, sy, rx, ry, p->d.dim, p->d.n_bins, p->d.bin_width, cg, p->ws_bin, p->ws_key2,
+                    p->ws_perm, p->ws_perm2, p->ws_hist, p->ws_cell_start, p->ws_bin_start, &p->cur_perm,
+                    &launches, s);
+    p->launches += launches;
+    if (e != cudaSuccess) return cuda_fail(e, "binning sort");
+    p->cur_cg = cg;
     k_gather<<<std::max(1, std::min((ntr + 255) / 256, 4096)), 256, 0, s>>>(
-        p->ws_bin_start, p->d.n_bins, p->ws_perm, sx, sy, rx, ry, p->d.dim, p->ws_hdr, p->ws_mid);
+        p->ws_bin_start, p->d.n_bins, p->cur_perm, sx, sy, rx, ry, p->d.dim, p->ws_hdr, p->ws_mid);
     ++p->launches;
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "binning kernels");
     return KH_OK;
+}
+
+TraceSet plan_traces(const kh_plan_s* p)
+{
+    TraceSet ts{p->ws_hdr, p->ws_mid, p->cur_perm, p->ws_bin_start};
+    if (p->cur_cg.ncx * p->cur_cg.ncy > 1) ts.cell_start = p->ws_cell_start;
+    ts.cg = p->cur_cg;
+    return ts;
 }
 
 // Traces as the kernels read them: rows 16-byte aligned.  Returns the pointer and row stride.
@@ -938,6 +985,11 @@ kh_status kirchhoff_destroy(kh_plan p)
     cudaFree(p->ws_perm);
     cudaFree(p->ws_hdr);
     cudaFree(p->ws_mid);
+    cudaFree(p->ws_key2);
+    cudaFree(p->ws_perm2);
+    cudaFree(p->ws_hist);
+    cudaFree(p->ws_cell_start);
+    cudaFree(p->ws_stats);
     cudaFree(p->ws_pad);
     cudaFree(p->ws_count);
     cudaFree(p->ws_partial);
@@ -986,6 +1038,9 @@ kh_status kirchhoff_set_option(kh_plan p, kh_option opt, long long value)
         case KH_OPT_SAMPLE_PAIRS:
             p->sample_pairs = value ? 1 : 0;
             return KH_OK;
+        case KH_OPT_SPATIAL_SORT:
+            p->spatial_sort = value ? 1 : 0;
+            return KH_OK;
         default:
             return fail(KH_ERR_INVALID_ARG, "unknown option %d", (int)opt);
     }
@@ -1017,8 +1072,9 @@ kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy
         if ((st = ensure_table(p, ntr, sx, sy, rx, ry, s, tile, g)) != KH_OK) return st;
         vk = VK_TABLE;
     }
-    TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};
+    TraceSet ts = plan_traces(p);
     WaitCfg w{p->ws_status, p->wait_polls, WAIT_NS};
+    if (p->profiling) w.stats = p->ws_stats;
     prof_begin(p, s);
     cudaError_t e = launch_migrate(g, tile, ts, tr_ptr, image, vk, p->fast_math, w, s);
     prof_end(p, s);
@@ -1043,14 +1099,15 @@ kh_status kirchhoff_demigrate(kh_plan p, int ntr, const float* sx, const float* 
     GeomParams g = geom_of(d);
     DmTile dt;
     if ((st = demigrate_tile(d, g, ntr, dt)) != KH_OK) return st;
-    if ((st = bin_traces(p, ntr, sx, sy, rx, ry, s)) != KH_OK) return st;
+    // bin order alone: the adjoint's warps share source legs when their traces come shot by shot
+    if ((st = bin_traces(p, ntr, sx, sy, rx, ry, s, false)) != KH_OK) return st;
     const size_t per_part = (size_t)ntr * d.nt;
     cudaError_t e = grow(p->ws_dm, p->cap_dm, per_part * dt.parts);
     if (e != cudaSuccess) return cuda_fail(e, "workspace (demigration partial traces)");
     e = cudaMemsetAsync(p->ws_dm, 0, sizeof(float) * per_part * dt.parts, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(traces_out, 0, sizeof(float) * per_part, s);
     if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_demigrate: memset");
-    TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};
+    TraceSet ts = plan_traces(p);
     const int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
     const int max_chunks = (ntr + 127) / 128;
     prof_begin(p, s);
@@ -1095,8 +1152,9 @@ kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, const flo
     const long long nwarps = (long long)tile.tiles_x * tile.tiles_y * tile.tiles_z * p->d.n_bins * CONSUMER_WARPS;
     if ((e = grow(p->ws_partial, p->cap_partial, (size_t)(2 * nwarps))) != cudaSuccess)
         return cuda_fail(e, "workspace (gradient partials)");
-    TraceSet ts{p->ws_hdr, p->ws_mid, p->ws_perm, p->ws_bin_start};
+    TraceSet ts = plan_traces(p);
     WaitCfg w{p->ws_status, p->wait_polls, WAIT_NS};
+    if (p->profiling) w.stats = p->ws_stats;
     const int vk = (g.k == 0.0) ? VK_CONST : VK_LINEAR;
     prof_begin(p, s);
     e = launch_vgrad(g, tile, ts, tr_ptr, image, vk, p->fast_math, w, p->ws_partial, s);
@@ -1194,7 +1252,63 @@ kh_status kirchhoff_sync(kh_plan p, void* cuda_stream)
 kh_status kirchhoff_profile(kh_plan p, int enable)
 {
     if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    if (enable && !p->ws_stats) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->ws_stats), 3 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(p->ws_stats, 0, 3 * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_profile (staging counters)");
+    }
     p->profiling = enable ? 1 : 0;
+    return KH_OK;
+}
+
+kh_status kirchhoff_cell_grid(const kh_desc* d, int spatial, int* ncx, int* ncy, double* gx0, double* gy0,
+                              double* inv_cell)
+{
+    kh_status st = validate_desc(d);
+    if (st != KH_OK) return st;
+    const CellGrid cg = cell_grid_of(*d, spatial != 0);
+    if (ncx) *ncx = cg.ncx;
+    if (ncy) *ncy = cg.ncy;
+    if (gx0) *gx0 = cg.gx0;
+    if (gy0) *gy0 = cg.gy0;
+    if (inv_cell) *inv_cell = cg.inv_cs;
+    return KH_OK;
+}
+
+kh_status kirchhoff_bin_sort(kh_plan p, int ntr, const float* sx, const float* sy, const float* rx,
+                             const float* ry, int* perm_out, int* key_start_out, void* cuda_stream)
+{
+    if (!p) return fail(KH_ERR_INVALID_ARG, "plan is NULL");
+    kh_status st = check_headers(p, ntr, sx, sy, rx, ry);
+    if (st != KH_OK) return st;
+    if ((ntr > 0 && !perm_out) || !key_start_out) return fail(KH_ERR_INVALID_ARG, "perm/key_start is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if ((st = bin_traces(p, ntr, sx, sy, rx, ry, s)) != KH_OK) return st;
+    const size_t nkeys = (size_t)p->d.n_bins * p->cur_cg.ncx * p->cur_cg.ncy;
+    cudaError_t e = cudaSuccess;
+    if (ntr > 0)
+        e = cudaMemcpyAsync(perm_out, p->cur_perm, sizeof(int) * (size_t)ntr, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(key_start_out, p->ws_cell_start, sizeof(int) * (nkeys + 1), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_bin_sort: copies");
+    return KH_OK;
+}
+
+kh_status kirchhoff_staging_stats(kh_plan p, void* cuda_stream, unsigned long long* examined,
+                                  unsigned long long* staged, unsigned long long* ctas)
+{
+    if (!p || !examined || !staged || !ctas) return fail(KH_ERR_INVALID_ARG, "NULL argument");
+    *examined = *staged = *ctas = 0;
+    if (!p->ws_stats) return KH_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    unsigned long long h[3] = {0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, p->ws_stats, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->ws_stats, 0, sizeof h, s);
+    if (e != cudaSuccess) return cuda_fail(e, "kirchhoff_staging_stats");
+    *examined = h[0];
+    *staged = h[1];
+    *ctas = h[2];
     return KH_OK;
 }
 
@@ -1275,6 +1389,15 @@ cudaError_t launch_pairs(int ntr, int nt, int ld, const void* src, void* dst, cu
     if (ntr > 0)
         k_pairs<<<std::min(ntr, 1 << 20), 256, 0, s>>>(ntr, nt, ld, static_cast<const float*>(src),
                                                          static_cast<SamplePair*>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(int ntr, const int* bin_start, int n_bins, const int* perm, const float* sx,
+                          const float* sy, const float* rx, const float* ry, int dim, float4* hdr, float2* mid,
+                          cudaStream_t s)
+{
+    k_gather<<<std::max(1, std::min((ntr + 255) / 256, 4096)), 256, 0, s>>>(bin_start, n_bins, perm, sx, sy, rx,
+                                                                            ry, dim, hdr, mid);
     return cudaGetLastError();
 }
 

@@ -176,11 +176,12 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
     const int es = pairs ? (int)sizeof(SamplePair) : dtype_bytes((kh_dtype)tdt), ealign = 16 / es;
     Layout L;
     struct Off {
-        size_t bin, perm, bs, hdr, mid, pad, cull;
+        size_t bin, perm, bs, hdr, mid, pad, cull, key2, perm2, hist, cs;
         long long ld;
         bool padded;
     };
     std::vector<Off> off(njobs);
+    std::vector<CellGrid> cgs(njobs);
     size_t n_items = 0, n_cull = 0;
     for (int j = 0; j < njobs; ++j) {
         const kh_job& J = jobs[j];
@@ -190,6 +191,12 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         o.bin = L.take(n * sizeof(int));
         o.perm = L.take(n * sizeof(int));
         o.bs = L.take((size_t)(d.n_bins + 1) * sizeof(int));
+        // the plan path's binning sort (same trace order, so bit-identical images)
+        cgs[j] = cell_grid_of(d, J.plan->spatial_sort != 0);
+        o.key2 = L.take(n * sizeof(int));
+        o.perm2 = L.take(n * sizeof(int));
+        o.hist = L.take((size_t)std::max(sort_hist_entries(J.ntr), 1) * sizeof(int));
+        o.cs = L.take(((size_t)d.n_bins * cgs[j].ncx * cgs[j].ncy + 1) * sizeof(int));
         o.hdr = L.take(n * sizeof(float4));
         o.mid = L.take(n * sizeof(float2));
         o.padded = J.ntr > 0 && (pairs || !((reinterpret_cast<uintptr_t>(J.traces) & 15u) == 0 && d.nt % ealign == 0));
@@ -254,11 +261,19 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         }
         float4* hdr = reinterpret_cast<float4*>(w + o.hdr);
         float2* mid = reinterpret_cast<float2*>(w + o.mid);
-        int* perm = reinterpret_cast<int*>(w + o.perm);
         int* bs = reinterpret_cast<int*>(w + o.bs);
-        TraceSet tr{hdr, mid, perm, bs};
-        e = noalloc_bin(J.ntr, J.sx, J.sy, J.rx, J.ry, d, reinterpret_cast<int*>(w + o.bin), perm, bs, hdr, mid, s);
+        int* cs = reinterpret_cast<int*>(w + o.cs);
+        const int* perm = nullptr;
+        int nl = 0;
+        e = sort_traces(J.ntr, J.sx, J.sy, J.rx, J.ry, d.dim, d.n_bins, d.bin_width, cgs[j],
+                        reinterpret_cast<int*>(w + o.bin), reinterpret_cast<int*>(w + o.key2),
+                        reinterpret_cast<int*>(w + o.perm), reinterpret_cast<int*>(w + o.perm2),
+                        reinterpret_cast<int*>(w + o.hist), cs, bs, &perm, &nl, s);
+        if (e == cudaSuccess) e = launch_gather(J.ntr, bs, d.n_bins, perm, J.sx, J.sy, J.rx, J.ry, d.dim, hdr, mid, s);
         if (e != cudaSuccess) return fail_free(set_cuda_error(e, "kirchhoff_batched_prepare: binning"));
+        TraceSet tr{hdr, mid, perm, bs};
+        if (cgs[j].ncx * cgs[j].ncy > 1) tr.cell_start = cs;
+        tr.cg = cgs[j];
         const void* rows = J.traces;
         if (o.padded) {
             rows = w + o.pad;

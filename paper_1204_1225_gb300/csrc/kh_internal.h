@@ -53,12 +53,31 @@ constexpr long long WAIT_NS = 2000000000LL;
 
 enum VelKind { VK_CONST = 0, VK_LINEAR = 1, VK_TABLE = 2 };
 
+// Midpoint cells of the binning sort.  Traces are ordered by (offset bin, cell row cy, cell
+// column cx, original index); cell (cx, cy) covers midpoints m with
+// floor((m_x - gx0) inv_cs) = cx (FP64), likewise in y.  The grid covers the image columns
+// widened by `margin` (a little more than the aperture), so a midpoint outside it is farther
+// than the aperture from every column and is dropped with the traces that have no offset bin.
+// With a full aperture (margin <= 0) there is one cell and nothing is dropped.
+constexpr int MAX_CELLS_PER_AXIS = 16;
+constexpr int MAX_CELL_ROWS = MAX_CELLS_PER_AXIS;
+struct CellGrid {
+    int ncx = 1, ncy = 1;
+    double gx0 = 0.0, gy0 = 0.0;
+    double inv_cs = 0.0;     // 1 / cell size
+    double margin = 0.0;     // aperture widening of the tile footprint for its cell range
+};
+
 // Sorted trace set produced by the binning pass (plan workspace).
 struct TraceSet {
-    const float4* hdr;      // (sx, sy, rx, ry) in bin order
+    const float4* hdr;      // (sx, sy, rx, ry) in sorted order
     const float2* mid;      // FP32 midpoints (sx + rx) * 0.5f, (sy + ry) * 0.5f
     const int* perm;        // original trace index
     const int* bin_start;   // [n_bins + 1]
+    // [n_bins * ncx * ncy + 1]: start of every (bin, cell) key in sorted order (nullptr: the
+    // traces of a bin are one range, bin_start[b] .. bin_start[b + 1])
+    const int* cell_start = nullptr;
+    CellGrid cg{};
 };
 
 // Everything a migration-type kernel needs, passed by value.
@@ -122,6 +141,9 @@ struct WaitCfg {
     int* status;             // device status word (bit 0: timeout)
     long long polls;         // 0 = unlimited polls (wall clock only)
     long long ns;
+    // optional [3]: traces the staging warps examined and staged, and the staging warps (one per
+    // CTA and work item) that reported, summed
+    unsigned long long* stats = nullptr;
 };
 
 // Launchers (kh_migrate.cu).

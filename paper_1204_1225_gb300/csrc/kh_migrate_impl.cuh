@@ -46,6 +46,9 @@ struct __align__(16) MigSmem {
     uint64_t empty[STAGES];
     int cnt[STAGES];
     int last[STAGES];
+    int row[4];                 // cell range of the tile (cx0, cx1, first row - 1, last row)
+    int2 rng[MAX_CELL_ROWS];    // staging warp: sorted trace range of each cell row of the tile
+    unsigned stat[2];           // staging warp: traces examined and staged for this tile
     // per staged trace
     float4 hdr[STAGES][BMAX];   // (sx, sy, rx, ry)
     float4 hda[STAGES][BMAX];   // linear: (c_x-2s_x, c_y-2s_y, c_x-2r_x, c_y-2r_y)
@@ -211,17 +214,84 @@ __device__ __forceinline__ float sample_unchecked(const TT* ring, float th, int 
 }
 
 // ------------------------------------------------------------------ producer warp
+// The sorted traces one CTA examines: its bin's whole range, or with a (bin, cell) start table
+// one range per row of the cells that meet the tile footprint widened by the aperture margin
+// (cells of a row are consecutive in the sort order).  Every trace the staging cull would keep
+// lies in those cells: its midpoint is within the cull radius, margin - 1 m, of the footprint.
+// The row state (cx0, cx1, current row, last row) lives in shared memory, written by the
+// staging warp only: it changes once per cell row, and keeping it out of registers leaves the
+// kernel's register budget to the consumers.
+// The tile's cell range, written by one thread before the tile's set-up barrier.
+__device__ __forceinline__ void tile_cells(int* row, const TraceSet& tr, const TileBox& box)
+{
+    if (!tr.cell_start) return;
+    const CellGrid& cg = tr.cg;
+    auto cell = [&](double v, double g0, int n) {
+        const double f = floor((v - g0) * cg.inv_cs);
+        return (int)fmin(fmax(f, -1.0), (double)n);
+    };
+    const int cx0 = max(0, cell((double)box.xlo - cg.margin, cg.gx0, cg.ncx));
+    const int cx1 = min(cg.ncx - 1, cell((double)box.xhi + cg.margin, cg.gx0, cg.ncx));
+    const int cy0 = max(0, cell((double)box.ylo - cg.margin, cg.gy0, cg.ncy));
+    const int cy1 = min(cg.ncy - 1, cell((double)box.yhi + cg.margin, cg.gy0, cg.ncy));
+    row[0] = cx0;
+    row[1] = cx1;
+    row[2] = cy0 - 1;
+    row[3] = (cx0 <= cx1) ? cy1 : cy0 - 1;
+}
+
+// The tile's sorted trace range of every cell row, written by the staging warp into shared
+// memory (rng[0 .. nr - 1]); the walk keeps its row index and count in shared memory too
+// (row[2], row[3]), so that it adds no register to the staging loop.
+__device__ __forceinline__ void tile_rows(int* row, int2* rng, const TraceSet& tr, int bin)
+{
+    const int ncx = tr.cg.ncx;
+    const int* cs = tr.cell_start + (long long)bin * ncx * tr.cg.ncy;
+    const int cx0 = row[0], cx1 = row[1], cy0 = row[2] + 1, nr = row[3] - row[2];
+    for (int i = threadIdx.x & 31; i < nr; i += 32) {
+        const int cy = cy0 + i;
+        rng[i] = make_int2(cs[cy * ncx + cx0], cs[cy * ncx + cx1 + 1]);
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        row[2] = -1;
+        row[3] = nr;
+    }
+    __syncwarp();
+}
+
+// Moves (cur, te) to the next non-empty cell row; leaves cur >= te when none is left.
+__device__ __forceinline__ void next_row(int* row, const int2* rng, int& cur, int& te)
+{
+    int ri = row[2];
+    const int nr = row[3];
+    while (cur >= te && ri + 1 < nr) {
+        ++ri;
+        cur = rng[ri].x;
+        te = rng[ri].y;
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) row[2] = ri;
+    __syncwarp();
+}
+
 // `n` is the number of stages this CTA's producer has filled before (mbarrier phases carry
 // over from one work item to the next in the persistent kernel); returns the new count.
 // The window-relative time the consumers evaluate is tau - lo (sample index floor(tau - lo)).
 template <int VEL, typename TT>
 __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
-                                            const TraceSet& tr, const TT* __restrict__ traces, int tb,
-                                            int te, const TileBox& box, const WaitCfg& wc, int n)
+                                            const TraceSet& tr, const TT* __restrict__ traces, int bin,
+                                            const TileBox& box, const WaitCfg& wc, int n)
 {
     const int lane = threadIdx.x & 31;
     const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
-    int cur = tb;
+    int cur = tr.bin_start[bin], te = tr.bin_start[bin + 1];
+    if (tr.cell_start) {   // the first non-empty cell row of the tile
+        tile_rows(S.row, S.rng, tr, bin);
+        cur = te = 0;
+        next_row(S.row, S.rng, cur, te);
+    }
+    if (lane == 0) S.stat[0] = S.stat[1] = 0u;
     const int n_begin = n;
     bool failed = false;
     while (true) {
@@ -323,6 +393,11 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
             cnt += nfit;
             used += used_add;
             cur += consumed;
+            if (lane == 0) {
+                S.stat[0] += (unsigned)consumed;
+                S.stat[1] += (unsigned)nfit;
+            }
+            if (cur >= te && tr.cell_start) next_row(S.row, S.rng, cur, te);   // the tile's next cell row
             full = (nofit != 0u) || cnt >= BMAX;
         }
         __syncwarp();
@@ -334,6 +409,11 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
         __syncwarp();
         ++n;
         if (cur >= te) break;
+    }
+    if (wc.stats && lane == 0) {
+        atomicAdd(&wc.stats[0], (unsigned long long)S.stat[0]);
+        atomicAdd(&wc.stats[1], (unsigned long long)S.stat[1]);
+        atomicAdd(&wc.stats[2], 1ull);
     }
     if (failed) {
         if (lane == 0) atomicOr(wc.status, 1);
@@ -773,6 +853,7 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
             mbar_init(&S.empty[s], CONSUMER_WARPS);
         }
         S.zero[0] = S.zero[1] = S.zero[2] = S.zero[3] = 0.f;
+        tile_cells(S.row, tr, box);
         fence_barrier_init();
     }
     // per-z constants of the tile and a zero-filled ring (edge reads stay finite)
@@ -792,8 +873,7 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
     __syncthreads();
     if (s_abort) return;
     if (threadIdx.x >= CONSUMERS) {
-        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, tr.bin_start[bin], tr.bin_start[bin + 1],
-                                    box, wc, 0);
+        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, bin, box, wc, 0);
     } else if constexpr (MODE == 0) {
         mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, srcc, cap,
                                                   0);
@@ -947,10 +1027,11 @@ __global__ void __launch_bounds__(THREADS, 2)
         const int bin = w.z;
         const TileBox box = tile_box(g, x0, y0, z0, ts.cx, ts.cy, ts.cz * NZ);
         tile_z_setup<VEL, 0>(S, g, ts, z0, box);
+        if (threadIdx.x == 0) tile_cells(S.row, tr, box);
         __syncthreads();
         if (threadIdx.x >= CONSUMERS) {
             n = mig_producer<VEL, TT>(S, data, cap, g, tr, static_cast<const TT*>(jobs[w.x].traces),
-                                      tr.bin_start[bin], tr.bin_start[bin + 1], box, wc, n);
+                                      bin, box, wc, n);
         } else {
             n = mig_consumer<VEL, WGT, FAST, TT, LPT, float>(S, data, g, ts, x0, y0, z0, box, bin,
                                                              jobs[w.x].image, wc, nullptr, srcc, cap, n);

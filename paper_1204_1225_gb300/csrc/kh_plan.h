@@ -27,6 +27,19 @@ struct kh_plan_s {
     size_t cap_hdr = 0;
     float2* ws_mid = nullptr;
     size_t cap_mid = 0;
+    // the binning sort: keys and values (ping-pong), per-block digit counts, (bin, cell) starts
+    int* ws_key2 = nullptr;
+    size_t cap_key2 = 0;
+    int* ws_perm2 = nullptr;
+    size_t cap_perm2 = 0;
+    int* ws_hist = nullptr;
+    size_t cap_hist = 0;
+    int* ws_cell_start = nullptr;
+    size_t cap_cell_start = 0;
+    const int* cur_perm = nullptr;    // the buffer holding the last sort's permutation
+    kh::CellGrid cur_cg{};            // and its cell grid
+    int spatial_sort = 1;             // KH_OPT_SPATIAL_SORT
+    unsigned long long* ws_stats = nullptr;   // [3] staging statistics (while profiling)
     unsigned char* ws_pad = nullptr;
     size_t cap_pad = 0;
     long long* ws_count = nullptr;
@@ -54,8 +67,29 @@ namespace kh {
 kh_status set_error(kh_status s, const char* msg);
 kh_status set_cuda_error(cudaError_t e, const char* what);
 kh_status ensure_traces_ws(kh_plan_s* p, int ntr);
+// Offset bin and midpoint cell per trace, stable multi-CTA radix sort by (bin, cell), the
+// (bin, cell) starts and the sorted headers.  `spatial` = false sorts by bin alone (one cell
+// per bin; midpoints that reach no column are still dropped).  Sets p->cur_perm, p->cur_cg.
 kh_status bin_traces(kh_plan_s* p, int ntr, const float* sx, const float* sy, const float* rx,
-                     const float* ry, cudaStream_t s);
+                     const float* ry, cudaStream_t s, bool spatial = true);
+// The sorted trace set of the last bin_traces call.
+TraceSet plan_traces(const kh_plan_s* p);
+// Cell grid of a descriptor: one cell with no aperture, else cells of about half the aperture
+// (at most 64 per axis) over the image columns widened by the aperture margin.
+CellGrid cell_grid_of(const kh_desc& d, bool spatial);
+// The radix sort (kh_sort.cu): keys[i] = bin * ncell + cell (n_bins * ncell = no bin or out of
+// the grid), vals[i] = i; then stable passes of 8 bits; then the key starts.  Writes the sorted
+// permutation into *perm_out (one of the two value buffers) and the starts into cell_start
+// [n_bins * ncell + 1] and bin_start [n_bins + 1].
+cudaError_t sort_traces(int ntr, const float* sx, const float* sy, const float* rx, const float* ry,
+                        int dim, int n_bins, double bin_width, const CellGrid& cg, int* key_a,
+                        int* key_b, int* val_a, int* val_b, int* hist, int* cell_start, int* bin_start,
+                        const int** perm_out, int* launches, cudaStream_t s);
+int sort_hist_entries(int ntr);
+// Sorted headers and FP32 midpoints of the first bin_start[n_bins] sorted traces.
+cudaError_t launch_gather(int ntr, const int* bin_start, int n_bins, const int* perm, const float* sx,
+                          const float* sy, const float* rx, const float* ry, int dim, float4* hdr, float2* mid,
+                          cudaStream_t s);
 // Brackets a main-kernel launch with profiling events (no-op unless profiling is on).
 void prof_begin(kh_plan_s* p, cudaStream_t s);
 void prof_end(kh_plan_s* p, cudaStream_t s);

@@ -21,6 +21,7 @@ KH_F32, KH_F16, KH_BF16, KH_U16 = 0, 1, 2, 3
 KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE = 0, 1, 2
 KH_W_ONE, KH_W_OBLIQ_SPREAD = 0, 1
 KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE, KH_OPT_BATCH_MODE, KH_OPT_SAMPLE_PAIRS = 1, 2, 3, 4, 5
+KH_OPT_SPATIAL_SORT = 6
 BATCH_MODES = {"persistent": 0, "concurrent": 1}
 
 _STATUS = {0: "KH_OK", 1: "KH_ERR_INVALID_ARG", 2: "KH_ERR_UNSUPPORTED", 3: "KH_ERR_OOM",
@@ -60,7 +61,8 @@ EXPORTS = ["kirchhoff_create", "kirchhoff_destroy", "kirchhoff_migrate", "kirchh
            "kirchhoff_batch_info", "kirchhoff_batch_destroy", "kirchhoff_sync",
            "kirchhoff_set_option", "kirchhoff_launch_count", "kirchhoff_last_error",
            "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read",
-           "kirchhoff_migrate_noalloc", "kirchhoff_fit_report"]
+           "kirchhoff_migrate_noalloc", "kirchhoff_fit_report", "kirchhoff_staging_stats",
+           "kirchhoff_cell_grid", "kirchhoff_bin_sort"]
 
 
 def lib(path: str = LIB_PATH):
@@ -97,6 +99,11 @@ def lib(path: str = LIB_PATH):
                                                ctypes.POINTER(I), D, F, F, F, D]
             L.kirchhoff_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_longlong)]
+            U = ctypes.POINTER(ctypes.c_ulonglong)
+            L.kirchhoff_staging_stats.argtypes = [P, P, U, U, U]
+            L.kirchhoff_cell_grid.argtypes = [ctypes.POINTER(kh_desc), I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                              D, D, D]
+            L.kirchhoff_bin_sort.argtypes = [P, I, P, P, P, P, P, P, P]
             for name in EXPORTS:
                 getattr(L, name).restype = S
             L.kirchhoff_launch_count.restype = ctypes.c_longlong
@@ -278,6 +285,29 @@ def kirchhoff_profile_read(plan):
     return float(ms.value), int(n.value)
 
 
+def kirchhoff_cell_grid(desc: kh_desc, spatial: bool = True) -> dict:
+    """Host-only: the midpoint-cell grid of the binning sort for a descriptor."""
+    nx, ny = ctypes.c_int(0), ctypes.c_int(0)
+    gx, gy, cs = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().kirchhoff_cell_grid(ctypes.byref(desc), 1 if spatial else 0, ctypes.byref(nx),
+                                     ctypes.byref(ny), ctypes.byref(gx), ctypes.byref(gy), ctypes.byref(cs)))
+    return {"ncx": nx.value, "ncy": ny.value, "gx0": gx.value, "gy0": gy.value, "inv_cell": cs.value}
+
+
+def kirchhoff_bin_sort(plan, ntr, sx, sy, rx, ry, perm_out, key_start_out, stream=None) -> None:
+    _check(lib().kirchhoff_bin_sort(ctypes.c_void_p(plan), int(ntr), _ptr(sx), _ptr(sy), _ptr(rx),
+                                    _ptr(ry), _ptr(perm_out), _ptr(key_start_out), _stream(stream)))
+
+
+def kirchhoff_staging_stats(plan, stream=None):
+    """(traces examined, traces staged, CTAs) of the staging warps since the previous read,
+    while profiling is enabled; synchronises the stream."""
+    a, b, c = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+    _check(lib().kirchhoff_staging_stats(ctypes.c_void_p(plan), _stream(stream), ctypes.byref(a),
+                                         ctypes.byref(b), ctypes.byref(c)))
+    return int(a.value), int(b.value), int(c.value)
+
+
 def kirchhoff_version() -> str:
     return lib().kirchhoff_version().decode()
 
@@ -351,6 +381,7 @@ class Plan:
         self.image_shape = (s.n_bins, s.ny if s.dim == 3 else 1, s.nx, s.nz)
         self.nt = s.nt
         self.device = torch.cuda.current_device()
+        self.spatial_sort = True
         kirchhoff_set_option(self.handle, KH_OPT_FAST_MATH, 1 if fast_math else 0)
         if tile is not None:
             cx, cy, cz = tile
@@ -424,6 +455,24 @@ class Plan:
     def profile_read(self):
         """(summed main-kernel milliseconds, timed launches) since the previous read."""
         return kirchhoff_profile_read(self.handle)
+
+    def bin_sort(self, hdr: Headers, stream=None):
+        """The binning sort of this plan: (perm [ntr] int32, key starts int32) on the device."""
+        _validate(_header_specs(hdr), self.device)
+        grid = kirchhoff_cell_grid(self.desc, bool(self.spatial_sort))
+        nkeys = self.survey.n_bins * grid["ncx"] * grid["ncy"]
+        perm = torch.full((max(hdr.ntr, 1),), -1, dtype=torch.int32, device=hdr.sx.device)
+        starts = torch.empty(nkeys + 1, dtype=torch.int32, device=hdr.sx.device)
+        kirchhoff_bin_sort(self.handle, hdr.ntr, *hdr.args(), perm, starts, stream)
+        return perm[:hdr.ntr], starts, grid
+
+    def set_spatial_sort(self, on: bool):
+        kirchhoff_set_option(self.handle, KH_OPT_SPATIAL_SORT, 1 if on else 0)
+        self.spatial_sort = bool(on)
+
+    def staging_stats(self, stream=None):
+        """(traces examined, traces staged, CTAs) of the staging warps since the previous read."""
+        return kirchhoff_staging_stats(self.handle, stream)
 
     @property
     def launches(self) -> int:

@@ -43,17 +43,18 @@ from paper_1204_1225_gb300 import survey as sv  # noqa: E402
 
 # ALU roofline (GB300): thread instructions each SM can issue or execute per clock, per pipe
 # (dispatch: 4 sub-partitions x 32 lanes; FP32 FMA pipe 128; integer/logic ALU 64; MUFU
-# special-function unit 16, measured by the throughput probe in profiles/mufu_fma_throughput.md;
-# shared-memory load/store unit 32).  The migration kernel is a gather with no HBM bound
-# (about 1.1e-3 algorithmic bytes per contribution: traces and image once), so its roofline is
-# the smallest of N_SM x clock x lanes_p / n_p over these pipes, n_p = the kernel's executed
-# thread instructions per contribution on pipe p (ncu sm__inst_executed_pipe_*.sum x 32 and
-# smsp__thread_inst_executed.sum, divided by the contribution count).
+# special-function unit 16, the rate a throughput probe of back-to-back MUFU instructions
+# measured on this GPU; shared-memory load/store unit 32).  The migration kernel is a gather
+# with no HBM bound (about 1.1e-3 algorithmic bytes per contribution: traces and image once), so
+# its roofline is the smallest of N_SM x clock x lanes_p / n_p over these pipes, n_p = the
+# kernel's executed thread instructions per contribution on pipe p (ncu
+# sm__inst_executed_pipe_*.sum x 32 and smsp__thread_inst_executed.sum, divided by the
+# contribution count of the captured launch).
 N_SM = 152
 LANES_PER_SM_CLK = {"issue": 128, "fma": 128, "alu": 64, "xu": 16, "lsu": 32}
-# n_p per workload's kernel variant, from profiles/k_migrate_pipe_mix.md (one ncu capture of
-# k_migrate per variant; the 100k-trace 256^3 workload runs the variant measured on its
-# 10k-trace case: same grid, tile and 5-term per-leg fit).
+# n_p per workload's kernel variant, from one ncu capture of the kernel per variant (the
+# 100k-trace 256^3 workload runs the variant measured on its 10k-trace case: same grid, tile
+# and 5-term per-leg fit).
 PIPE_MIX = {
     "3d-vz-100k-256cube": {"issue": 32.82, "fma": 21.37, "alu": 3.38, "xu": 3.15, "lsu": 3.37},
     "3d-vz-10k-256cube": {"issue": 32.82, "fma": 21.37, "alu": 3.38, "xu": 3.15, "lsu": 3.37},
@@ -72,8 +73,8 @@ PIPE_MIX = {
 }
 
 
-# DRAM bytes (read + write) of one k_migrate launch, ncu dram__bytes_{read,write}.sum
-# (profiles/k_migrate_pipe_mix.md); None where not captured for that workload.
+# DRAM bytes (read + write) of one launch of the variant's main kernel, ncu
+# dram__bytes_{read,write}.sum from the same captures; None where not captured.
 TRAFFIC = {
     "3d-vz-100k-256cube": 748677376 + 1038178624,
     "3d-vz-10k-256cube": 87995904 + 1025581056,
@@ -83,6 +84,14 @@ TRAFFIC = {
     "3d-vz-10k-256cube-vgrad": 1130428928 + 15748608,
     "3d-vz-10k-256cube-table-u16-f16": 39405056 + 1024635648,
 }
+
+# Parity bars against the FP64 oracle (relative L2 over the sampled outputs): FP32 forms, and the
+# mixed-precision form (16-bit traces and traveltime table, FP32 arithmetic).
+BAR_FP32 = 1e-5
+BAR_MIXED = 3e-3
+# The velocity gradient is a sum of signed terms that cancel; its bar is relative to the sum of
+# their absolute values (the FP32 rounding of the individual terms).
+BAR_GRAD_ABS = 1e-4
 
 
 def pipe_roofline(mix, clk_mhz: float):
@@ -285,7 +294,7 @@ def run_reference(args, s):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -312,9 +321,20 @@ def main():
     ap.add_argument("--spatial-sort", type=int, default=1,
                     help="1: traces sorted by (bin, midpoint cell), each CTA examines the cells of "
                          "its aperture disc; 0: each CTA examines its whole bin")
-    args = ap.parse_args()
+    ap.add_argument("--forms", type=int, default=None,
+                    help="1: add the other forms of the metric to the headline line (mixed precision, "
+                         "batched vs loop, adjoint, gradient), each timed on its own; default: on for "
+                         "the headline migration, off otherwise")
+    ap.add_argument("--form-steps", type=int, default=3, help="timed steps of each added form")
+    ap.add_argument("--parity-points", type=int, default=4096,
+                    help="image samples compared with the FP64 oracle (0: no parity check)")
+    args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
+    return args
 
+
+def main():
+    args = parse_args()
     ws, rank, local = dist_init()
     s = workloads()[args.workload]()
     if args.aperture is not None and not isinstance(s, list):
@@ -323,49 +343,100 @@ def main():
         if rank == 0:
             run_reference(args, s[0] if isinstance(s, list) else s)
         return
-    if isinstance(s, list):
-        run_batched(args, s, ws, rank, local)
-        return
-
     from paper_1204_1225_gb300 import build as khbuild
-    from paper_1204_1225_gb300 import kirchhoff as kh
     khbuild.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    tdt = _TDT[args.trace_dtype]
-    s_run = s.replace(vel="table") if args.vel == "table" else s
-    plan = kh.Plan(s_run, fast_math=bool(args.fast_math), trace_dtype=tdt, table_dtype=args.table_dtype)
-    plan.set_spatial_sort(bool(args.spatial_sort))
-    hdr = kh.Headers.of(s, device=dev)
-    traces = synth_traces(s, kh.Plan(s), dev).to(tdt).contiguous()
+    if isinstance(s, list):
+        line = run_batched(args, s, ws, rank, local, dev)
+    else:
+        cache = {}
+        line = run_single(args, s, ws, rank, local, dev, cache)
+        headline = (args.workload == "3d-vz-100k-256cube" and args.op == "migrate" and args.vel == "analytic"
+                    and args.trace_dtype == "f32" and args.aperture is None and args.spatial_sort)
+        forms = run_forms(args, s, ws, rank, local, dev, cache, line) \
+            if (args.forms if args.forms is not None else headline) else None
+        if line is not None and forms is not None:
+            line["forms"] = forms
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def _oracle():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def parity_image(s_oracle, traces64, image, npts, bar, what):
+    """The GPU image at `npts` random samples against the FP64 oracle at the same samples."""
+    if npts <= 0:
+        return None
+    oracle = _oracle()
+    pts = sv.sample_points(s_oracle, npts, sv.BASE_SEED + 17)
+    got = image.reshape(-1)[torch.as_tensor(pts, device=image.device)].double().cpu().numpy()
+    t0 = time.perf_counter()
+    want = oracle.migrate_points(s_oracle, traces64, pts)
+    err = float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300))
+    return {"rel_l2": err, "bar": bar, "within_bar": (err <= bar) if bar else None,
+            "points": int(pts.size), "vs": what, "oracle_s": round(time.perf_counter() - t0, 2)}
+
+
+def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=None, vel=None,
+               table_dtype=None, steps=None, warmup=None, e2e=None, cpu=None, spatial_sort=None):
+    """Times `steps` calls of one operator on one survey; returns the JSON line (rank 0)."""
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    op = op or args.op
+    trace_dtype = trace_dtype or args.trace_dtype
+    vel = vel or args.vel
+    table_dtype = table_dtype or args.table_dtype
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
+    e2e = (not args.no_e2e) if e2e is None else e2e
+    cpu = (not args.no_cpu_baseline) if cpu is None else cpu
+    spatial_sort = bool(args.spatial_sort) if spatial_sort is None else spatial_sort
+    tdt = _TDT[trace_dtype]
+    s_run = s.replace(vel="table") if vel == "table" else s
+    plan = kh.Plan(s_run, fast_math=bool(args.fast_math), trace_dtype=tdt, table_dtype=table_dtype)
+    plan.set_spatial_sort(spatial_sort)
+    if "hdr" not in cache:
+        cache["hdr"] = kh.Headers.of(s, device=dev)
+        cache["traces"] = synth_traces(s, kh.Plan(s), dev).contiguous()
+        cache["count"] = plan.count(cache["hdr"])
+    hdr = cache["hdr"]
+    traces = cache["traces"].to(tdt).contiguous()
     image = torch.empty(plan.image_shape, dtype=torch.float32, device=dev)
-    contrib = plan.count(hdr)
+    contrib = cache["count"]
     stream = torch.cuda.current_stream(dev)
-    if args.op != "migrate":
-        plan.migrate(hdr, traces, out=image)          # the adjoint and gradient read an image
+    if op != "migrate":
+        if "image" not in cache:
+            cache["image"] = torch.empty(plan.image_shape, dtype=torch.float32, device=dev)
+            kh.Plan(s).migrate(hdr, cache["traces"], out=cache["image"])   # the adjoint and gradient read an image
+        image = cache["image"]
         d_out = torch.empty((s.ntr, s.nt), dtype=torch.float32, device=dev)
         g_out = torch.empty(2, dtype=torch.float64, device=dev)
 
     def step():
-        if args.op == "migrate":
+        if op == "migrate":
             plan.migrate(hdr, traces, out=image)
-        elif args.op == "demigrate":
+        elif op == "demigrate":
             plan.demigrate(hdr, image, out=d_out)
         else:
             plan.velocity_grad(hdr, image, traces, out=g_out)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     plan.sync()
     plan.profile(True)
     plan.profile_read()
+    plan.staging_stats()
     launches0 = plan.launches
     barrier(ws)
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -376,12 +447,12 @@ def main():
     plan.profile(False)
     t_ms = max_over_ranks(ws, e0.elapsed_time(e1))
     barrier(ws)
-    value = contrib * args.steps * ws / (t_ms / 1e3) / 1e9
+    value = contrib * steps * ws / (t_ms / 1e3) / 1e9
     clocks = clk.summary()
 
     # end to end through the public API: pinned host inputs in, image back to pinned host
-    e2e = None
-    if not args.no_e2e and args.op == "migrate":
+    e2e_rec = None
+    if e2e and op == "migrate":
         h_tr = traces.cpu().pin_memory()
         h_hdr = [t.cpu().pin_memory() for t in hdr.args()]
         h_img = torch.empty(plan.image_shape, dtype=torch.float32).pin_memory()
@@ -392,7 +463,7 @@ def main():
         barrier(ws)
         torch.cuda.synchronize(dev)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             d_tr.copy_(h_tr, non_blocking=True)
             for dst, src in zip(d_hdr.args(), h_hdr):
                 dst.copy_(src, non_blocking=True)
@@ -402,23 +473,23 @@ def main():
         torch.cuda.synchronize(dev)
         plan.sync()
         te = max_over_ranks(ws, e0.elapsed_time(e1))
-        e2e = {"value": contrib * args.steps * ws / (te / 1e3) / 1e9, "unit": "Gcontrib/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        e2e_rec = {"value": contrib * steps * ws / (te / 1e3) / 1e9, "unit": "Gcontrib/s",
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         del h_tr, h_img, d_tr
 
     if rank != 0:
-        return
-    # ALU roofline of the migration kernel at the median SM clock of the timed region.
+        return None
+    # pipe roofline of the main kernel at the median SM clock of the timed region
     clk_mhz = clocks.get("sm_mhz") or 2070.0
     achieved = contrib / (kern_ms / max(kern_n, 1) / 1e3) / 1e9 if kern_n else None
-    kname = {"migrate": "k_migrate", "demigrate": "k_demigrate", "vgrad": "k_vgrad"}[args.op]
-    if args.vel == "table":
-        mix_key = f"{args.workload}-table-{args.table_dtype}-{args.trace_dtype}"
-    elif args.trace_dtype == "f32":
-        mix_key = args.workload if args.op == "migrate" else f"{args.workload}-{args.op}"
+    kname = {"migrate": "k_migrate", "demigrate": "k_demigrate", "vgrad": "k_vgrad"}[op]
+    if vel == "table":
+        mix_key = f"{args.workload}-table-{table_dtype}-{trace_dtype}"
+    elif trace_dtype == "f32":
+        mix_key = args.workload if op == "migrate" else f"{args.workload}-{op}"
     else:
         mix_key = None
-    if args.aperture is not None or not args.spatial_sort:
+    if args.aperture is not None or not spatial_sort:
         mix_key = None   # instruction mixes were measured on the workloads as defined
     mix = PIPE_MIX.get(mix_key) if (mix_key and args.fast_math) else None
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "unit": "Gcontrib/s",
@@ -429,37 +500,156 @@ def main():
                      "binding_pipe": pipe, "pipe_bounds": {k: round(v, 1) for k, v in bounds.items()},
                      "instructions_per_contribution": mix,
                      "peak_basis": f"min over pipes of {N_SM} SMs x lanes/clk x {clk_mhz:.0f} MHz / "
-                                   "executed instructions per contribution (ncu, "
-                                   "profiles/k_migrate_pipe_mix.md)"})
+                                   f"executed instructions per contribution (ncu instruction mix of "
+                                   f"{kname} on this variant)"})
     else:
         roof.update({"peak": None, "frac": None,
                      "peak_basis": "no measured instruction mix for this kernel variant"})
     roof["traffic"] = TRAFFIC.get(mix_key) if mix_key else None
-    cpu = None
-    if not args.no_cpu_baseline and ws == 1 and args.op == "migrate":
-        cpu = cpu_baseline(s, traces.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)
+
+    # parity with the FP64 oracle on sampled outputs of this very launch configuration
+    parity = None
+    npts = args.parity_points
+    if npts > 0:
+        if "traces64" not in cache:
+            cache["traces64"] = cache["traces"].double().cpu().numpy()
+        if op == "migrate" and vel == "table":
+            parity = parity_image(s.replace(vel="table"), cache["traces64"], image, npts, BAR_MIXED,
+                                  "FP64 oracle, same radial-table algorithm, on the FP32 traces "
+                                  "(storage error of the 16-bit traces and table included)")
+            parity["vs_exact_traveltimes"] = parity_image(s, cache["traces64"], image, npts, None,
+                                                          "FP64 oracle, exact closed-form T")["rel_l2"]
+        elif op == "migrate":
+            bar = BAR_FP32 if trace_dtype == "f32" else BAR_MIXED
+            parity = parity_image(s, cache["traces64"], image, npts, bar,
+                                  "FP64 oracle on the FP32 traces" + (" (16-bit storage error included)"
+                                                                      if trace_dtype != "f32" else ""))
+        elif op == "demigrate":
+            parity = parity_demigrate(s, image, d_out)
+        else:
+            parity = parity_vgrad(s, dev, cache)
+    cpu_rec = None
+    if cpu and ws == 1 and op == "migrate":
+        if "traces64" not in cache:
+            cache["traces64"] = cache["traces"].double().cpu().numpy()
+        cpu_rec = cpu_baseline(s, cache["traces64"], args.cpu_seconds, sv.BASE_SEED)
     tbytes = traces.numel() * traces.element_size()
-    line = {
+    return {
         "metric": "G image-point x trace contributions/s", "value": value, "unit": "Gcontrib/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": ws, "steps": steps, "warmup": warmup,
+        "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": s.name, "operator": args.op, "image": list(plan.image_shape),
+        "config": {"workload": s.name, "operator": op, "image": list(plan.image_shape),
                    "ntr": s.ntr, "nt": s.nt,
                    "velocity": f"{s.vel} v0={s.v0} k={s.k}", "weight": s.weight,
                    "aperture_m": s.aperture, "contributions_per_step": contrib,
-                   "fast_math": bool(args.fast_math), "trace_storage": args.trace_dtype,
-                   "traveltimes": "analytic" if args.vel == "analytic" else f"table ({args.table_dtype}, "
+                   "fast_math": bool(args.fast_math), "trace_storage": trace_dtype,
+                   "traveltimes": "analytic" if vel == "analytic" else f"table ({table_dtype}, "
                                   f"{s.table_spacing:g} m)",
                    "l2": "inputs larger than L2 (traces %.0f MB, image %.0f MB)" % (
                        tbytes / 1e6, image.numel() * 4 / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single",
-                   "trace_order": "bin, midpoint cell" if args.spatial_sort else "bin",
+                   "trace_order": _trace_order(plan, spatial_sort),
                    "staging_per_cta": _staging(*stage_stats)},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks,
+        "roofline": roof, "parity": parity, "cpu_baseline": cpu_rec, "e2e": e2e_rec,
+        "gpu_launches": launches, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+
+
+def parity_demigrate(s, image, d_out, n_traces: int = 6):
+    """Sampled trace rows of the adjoint against the oracle's transpose of Eq. 1 (whole rows)."""
+    oracle = _oracle()
+    rng = np.random.default_rng(sv.BASE_SEED + 23)
+    idx = np.sort(rng.choice(s.ntr, size=n_traces, replace=False))
+    got = d_out[torch.as_tensor(idx, device=d_out.device)].double().cpu().numpy()
+    t0 = time.perf_counter()
+    want = oracle.demigrate(s.subset(idx), image.double().cpu().numpy())
+    err = float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300))
+    return {"rel_l2": err, "bar": BAR_FP32, "within_bar": err <= BAR_FP32, "traces": int(idx.size),
+            "vs": "FP64 oracle transpose of Eq. 1, whole sampled trace rows",
+            "oracle_s": round(time.perf_counter() - t0, 2)}
+
+
+def parity_vgrad(s, dev, cache, block: int = 16):
+    """The gradient on a sub-problem the oracle finishes in seconds: a block x block-column window
+    of the image (all depths) and the traces of one offset bin."""
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    oracle = _oracle()
+    bins = oracle.bins(s)
+    b = s.n_bins // 3
+    idx = np.flatnonzero(bins == b)
+    i0, j0 = (s.nx - block) // 2, (s.ny - block) // 2
+    sub = s.subset(idx).replace(nx=block, ny=block, ox=s.ox + i0 * s.dx, oy=s.oy + j0 * s.dy)
+    img = cache["image"][:, j0:j0 + block, i0:i0 + block, :].contiguous()
+    tr = cache["traces"][torch.as_tensor(idx, device=dev)].contiguous()
+    got = kh.Plan(sub).velocity_grad(kh.Headers.of(sub, device=dev), img, tr).cpu().numpy()
+    t0 = time.perf_counter()
+    want, absum = oracle.vgrad(sub, img.double().cpu().numpy(), tr.double().cpu().numpy(), return_abs=True)
+    err = float(np.max(np.abs(got - want) / absum))
+    return {"abs_err_over_sum_abs_terms": err, "bar": BAR_GRAD_ABS, "within_bar": err <= BAR_GRAD_ABS,
+            "rel_err": [float(abs(g - w) / max(abs(w), 1e-300)) for g, w in zip(got, want)],
+            "vs": f"FP64 oracle gradient on a {block}x{block}-column window of the image (all depths) "
+                  f"and the {idx.size} traces of offset bin {b}",
+            "oracle_s": round(time.perf_counter() - t0, 2)}
+
+
+def _form(line):
+    """The fields of a form's own measurement kept in the headline line."""
+    keep = ("value", "unit", "steps", "warmup", "ms_per_step", "roofline", "parity", "clocks",
+            "gpu_launches", "loop", "speedup_vs_loop", "loop_tuned_tiles", "speedup_vs_loop_tuned_tiles")
+    out = {k: line[k] for k in keep if k in line}
+    out["config"] = {k: v for k, v in line["config"].items()
+                     if k in ("workload", "operator", "trace_storage", "traveltimes", "contributions_per_step",
+                              "batch_mode", "work_items", "staging_per_cta")}
+    return out
+
+
+def run_forms(args, s, ws, rank, local, dev, cache, head):
+    """The metric's other forms on the same GPU, each timed on its own: mixed precision (16-bit
+    traces and traveltime table) on the headline survey, the adjoint and the (v0, k) gradient on
+    the headline survey, and the 64-job batch as one graph replay against a loop of per-job calls
+    (FP32 and FP16 traces)."""
+    k = dict(steps=args.form_steps, warmup=3, e2e=False, cpu=False)
+    forms = {}
+    mixed = run_single(args, s, ws, rank, local, dev, cache, trace_dtype="f16", vel="table",
+                       table_dtype="u16", **k)
+    if rank == 0:
+        forms["mixed_u16_table_f16_traces"] = _form(mixed)
+        forms["mixed_u16_table_f16_traces"]["speedup_vs_fp32"] = mixed["value"] / head["value"]
+    for op in ("demigrate", "vgrad"):
+        r = run_single(args, s, ws, rank, local, dev, cache, op=op, **k)
+        if rank == 0:
+            forms[op] = _form(r)
+    cache.clear()
+    torch.cuda.empty_cache()
+    surveys = workloads()["batch64-3d-vz"]()
+    bargs = parse_args(["--steps", str(args.form_steps), "--warmup", "3", "--no-tune",
+                        "--batch-mode", args.batch_mode, "--no-cpu-baseline",
+                        "--parity-points", str(min(args.parity_points, 1024))])
+    bargs.workload = "batch64-3d-vz"
+    jobs_cache = {}
+    for tdt in ("f32", "f16"):
+        bargs.trace_dtype = tdt
+        r = run_batched(bargs, surveys, ws, rank, local, dev, jobs_cache)
+        if rank == 0:
+            forms[f"batch64_{tdt}"] = _form(r)
+    # the persistent kernel over the FP32 batch, against the same per-job loop
+    bargs.trace_dtype, bargs.batch_mode, bargs.no_loop = "f32", "persistent", True
+    r = run_batched(bargs, surveys, ws, rank, local, dev, jobs_cache)
+    if rank == 0:
+        f = _form(r)
+        loop = forms["batch64_f32"].get("loop")
+        f["speedup_vs_loop"] = (r["value"] / loop["value"]) if loop else None
+        forms["batch64_f32_persistent"] = f
+    return forms
+
+
+def _trace_order(plan, spatial_sort):
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    g = kh.kirchhoff_cell_grid(plan.desc, spatial_sort)
+    if g["ncx"] * g["ncy"] > 1:
+        return f"offset bin, then midpoint cell of a {g['ncx']}x{g['ncy']} grid, then shot order"
+    return "offset bin, then shot order (one midpoint cell)"
 
 
 def _staging(examined, staged, ctas):
@@ -469,22 +659,21 @@ def _staging(examined, staged, ctas):
     return {"examined": round(examined / ctas, 1), "staged": round(staged / ctas, 1), "ctas": ctas}
 
 
-def run_batched(args, surveys, ws, rank, local):
-    """64 uneven jobs: one graph-captured persistent launch per step vs a per-job loop."""
-    from paper_1204_1225_gb300 import build as khbuild
+def run_batched(args, surveys, ws, rank, local, dev, jobs_cache=None):
+    """64 uneven jobs: one graph-captured launch sequence per step vs a per-job loop."""
     from paper_1204_1225_gb300 import kirchhoff as kh
     from paper_1204_1225_gb300.autotune import TileTuner
-    khbuild.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     tdt = _TDT[args.trace_dtype]
+    jobs_cache = {} if jobs_cache is None else jobs_cache
+    if "traces" not in jobs_cache:
+        jobs_cache["traces"] = [synth_batch_job(s, kh.Plan(s), j, dev) for j, s in enumerate(surveys)]
+        jobs_cache["hdr"] = [kh.Headers.of(s, device=dev) for s in surveys]
     jobs = []
     for j, s in enumerate(surveys):
         p = kh.Plan(s, fast_math=bool(args.fast_math), trace_dtype=tdt)
-        h = kh.Headers.of(s, device=dev)
-        d = synth_batch_job(s, kh.Plan(s), j, dev).to(tdt).contiguous()
-        jobs.append((p, h, d, torch.empty(p.image_shape, dtype=torch.float32, device=dev)))
+        d = jobs_cache["traces"][j].to(tdt).contiguous()
+        jobs.append((p, jobs_cache["hdr"][j], d, torch.empty(p.image_shape, dtype=torch.float32, device=dev)))
     contrib = sum(p.count(h) for (p, h, _, _) in jobs)
     t_tune = time.perf_counter()
     tiles = {}
@@ -514,6 +703,10 @@ def run_batched(args, surveys, ws, rank, local):
     t_ms = max_over_ranks(ws, e0.elapsed_time(e1))
     value = contrib * args.steps * ws / (t_ms / 1e3) / 1e9
     clocks = clk.summary()
+    # a few jobs' batched images, kept for the bit-for-bit comparison with the per-job calls
+    check = [0, len(jobs) // 2, len(jobs) - 1]
+    kept = {j: jobs[j][3].clone() for j in check}
+
     def loop_arm(what):
         for _ in range(args.warmup):
             for (p, h, d, m) in jobs:
@@ -543,48 +736,60 @@ def run_batched(args, surveys, ws, rank, local):
                 p.set_tile(None)
         loop = loop_arm("per-job kirchhoff_migrate calls on the same stream, default tiles, same precision")
     barrier(ws)
-    if rank != 0:
-        return
-    clk_mhz = clocks.get("sm_mhz") or 2070.0
-    mix = PIPE_MIX.get(f"{args.workload}-{args.trace_dtype}")
-    roof = {"bound": "alu", "kernel": "k_migrate_batched", "achieved": value, "unit": "Gcontrib/s",
-            "traffic": None}
-    if mix:
-        pipe, peak, bounds = pipe_roofline(mix, clk_mhz)
-        roof.update({"peak": peak, "frac": value / peak, "binding_pipe": pipe,
-                     "pipe_bounds": {k: round(v, 1) for k, v in bounds.items()},
-                     "peak_basis": "min over pipes of the batched kernel's ncu-measured instruction "
-                                   "mix; achieved over the whole graph replay"})
-    else:
-        roof.update({"peak": None, "frac": None,
-                     "peak_basis": "no measured instruction mix for this kernel variant"})
-    cpu = None
-    if not args.no_cpu_baseline and ws == 1:
-        s0, d0 = surveys[0], jobs[0][2]
-        cpu = cpu_baseline(s0, d0.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)
-    tb = sum(d.numel() * d.element_size() for (_, _, d, _) in jobs)
-    ib = sum(m.numel() * 4 for (_, _, _, m) in jobs)
-    line = {
-        "metric": "G image-point x trace contributions/s", "value": value, "unit": "Gcontrib/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {len(surveys)} jobs, n^3 at 10 m, n~U{{64..192}}, "
-                               "N_tr~U{1000..50000}, nt~U{750..2000}, constant v 2000 m/s, W=1, full "
-                               "aperture, 8 bins, 3 Ricker scatterers + noise per job",
-                   "contributions_per_step": contrib, "trace_storage": args.trace_dtype,
-                   "batch_mode": args.batch_mode, "work_items": info["items"], "ctas": info["ctas"],
-                   "tiles": tiles,
-                   "autotune_s": round(t_tune, 2),
-                   "l2": "inputs larger than L2 (traces %.1f GB, images %.1f GB)" % (tb / 1e9, ib / 1e9),
-                   "parallelism": "replicas" if ws > 1 else "single"},
-        "loop": loop, "speedup_vs_loop": (value / loop["value"]) if loop else None,
-        "loop_tuned_tiles": loop_tuned,
-        "speedup_vs_loop_tuned_tiles": (value / loop_tuned["value"]) if loop_tuned else None,
-        "roofline": roof, "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks,
-    }
-    print(json.dumps(line), flush=True)
+    line = None
+    if rank == 0:
+        parity = None
+        if not args.no_loop and not tiles:
+            same = all(torch.equal(kept[j], jobs[j][3]) for j in check)
+            parity = {"bitwise_equal_to_per_job_calls": same, "jobs_compared": check}
+            if args.parity_points > 0:
+                j = check[0]
+                parity["oracle"] = parity_image(
+                    surveys[j], jobs_cache["traces"][j].to(tdt).double().cpu().numpy(), kept[j],
+                    args.parity_points, BAR_FP32, f"FP64 oracle on job {j}'s {args.trace_dtype} traces")
+        clk_mhz = clocks.get("sm_mhz") or 2070.0
+        mix = PIPE_MIX.get(f"{args.workload}-{args.trace_dtype}") if args.batch_mode == "persistent" else None
+        roof = {"bound": "alu", "kernel": "k_migrate_batched" if args.batch_mode == "persistent" else "k_migrate",
+                "achieved": value, "unit": "Gcontrib/s", "traffic": None}
+        if mix:
+            pipe, peak, bounds = pipe_roofline(mix, clk_mhz)
+            roof.update({"peak": peak, "frac": value / peak, "binding_pipe": pipe,
+                         "pipe_bounds": {k: round(v, 1) for k, v in bounds.items()},
+                         "peak_basis": "min over pipes of the batched kernel's ncu-measured instruction "
+                                       "mix; achieved over the whole graph replay"})
+        else:
+            roof.update({"peak": None, "frac": None,
+                         "peak_basis": "no measured instruction mix for this kernel variant"})
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            s0, d0 = surveys[0], jobs[0][2]
+            cpu = cpu_baseline(s0, d0.double().cpu().numpy(), args.cpu_seconds, sv.BASE_SEED)
+        tb = sum(d.numel() * d.element_size() for (_, _, d, _) in jobs)
+        ib = sum(m.numel() * 4 for (_, _, _, m) in jobs)
+        line = {
+            "metric": "G image-point x trace contributions/s", "value": value, "unit": "Gcontrib/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch64-3d-vz: {len(surveys)} jobs, n^3 at 10 m, n~U{{64..192}}, "
+                                   "N_tr~U{1000..50000}, nt~U{750..2000}, constant v 2000 m/s, W=1, full "
+                                   "aperture, 8 bins, 3 Ricker scatterers + noise per job",
+                       "contributions_per_step": contrib, "trace_storage": args.trace_dtype,
+                       "batch_mode": args.batch_mode, "work_items": info["items"], "ctas": info["ctas"],
+                       "tiles": tiles,
+                       "autotune_s": round(t_tune, 2),
+                       "l2": "inputs larger than L2 (traces %.1f GB, images %.1f GB)" % (tb / 1e9, ib / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "loop": loop, "speedup_vs_loop": (value / loop["value"]) if loop else None,
+            "loop_tuned_tiles": loop_tuned,
+            "speedup_vs_loop_tuned_tiles": (value / loop_tuned["value"]) if loop_tuned else None,
+            "roofline": roof, "parity": parity, "cpu_baseline": cpu, "e2e": None,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        }
+    batch.close()
+    for (p, _, _, _) in jobs:
+        p.close()
+    return line
 
 
 if __name__ == "__main__":

@@ -68,8 +68,10 @@ typedef enum { KH_F32 = 0, KH_F16 = 1, KH_BF16 = 2, KH_U16 = 3 } kh_dtype;
  *                   z_a = D floor(shallowest image depth / D)) over the largest h of the
  *                   call's traces, stored as table_dtype, staged into shared memory and
  *                   read by bilinear interpolation in FP32.  table_dtype: KH_F32 (seconds),
- *                   KH_F16 (T - T_min as FP16) or KH_U16 (16-bit fixed point
- *                   T = T_min + scale u, scale = (T_max - T_min)/65535).  A migrate call
+ *                   KH_F16 (per h row, T minus the row's least-squares quadratic in the
+ *                   normalised node depth, stored as FP16 beside the row's three FP32
+ *                   coefficients) or KH_U16 (16-bit fixed point T = T_min + scale u,
+ *                   scale = (T_max - T_min)/65535).  A migrate call
  *                   with a table plan reads the headers' extent back to the host (it
  *                   synchronises the stream). */
 typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2 } kh_vel;
@@ -92,7 +94,8 @@ typedef struct {
     kh_vel vel;
     double v0, k;            /* v(z) = v0 + k z; k ignored for KH_VEL_CONST */
     double table_spacing;    /* KH_VEL_TABLE: node spacing of the traveltime tables, metres */
-    kh_dtype table_dtype;    /* KH_VEL_TABLE: KH_F32, KH_F16 (offset T_min) or KH_U16 (offset + scale) */
+    kh_dtype table_dtype;    /* KH_VEL_TABLE: KH_F32, KH_F16 (residual of a per-row quadratic) or
+                                KH_U16 (offset + scale) */
     kh_weight weight;
     double r0;               /* spreading normaliser, metres (KH_W_OBLIQ_SPREAD) */
     double aperture;         /* horizontal image-column to trace-midpoint distance limit, metres;

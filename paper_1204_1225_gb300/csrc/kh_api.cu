@@ -773,16 +773,45 @@ __global__ void k_table_minmax(long long n, const double* __restrict__ T, double
     }
 }
 
-// Stored values: F32 seconds; F16 T - T_min; U16 round((T - T_min) / scale).
-__global__ void k_table_store(long long n, const double* __restrict__ T, int dt, double tmin,
-                              double scale, void* __restrict__ out)
+// KH_F16: per h row, the least-squares quadratic c0 + c1 u + c2 u^2 in the normalised node depth
+// u = j / (nz - 1) (FP64 normal equations, coefficients rounded to FP32).  One thread per row.
+__global__ void k_table_rowfit(int nh, int nz, const double* __restrict__ T, float4* __restrict__ coef)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nh) return;
+    double m[5] = {0, 0, 0, 0, 0}, b[3] = {0, 0, 0};
+    for (int j = 0; j < nz; ++j) {
+        const double u = (double)j / (nz - 1), t = T[(long long)r * nz + j];
+        double pw = 1.0;
+        for (int q = 0; q < 5; ++q) {
+            m[q] += pw;
+            if (q < 3) b[q] += pw * t;
+            pw *= u;
+        }
+    }
+    // [m0 m1 m2; m1 m2 m3; m2 m3 m4] c = b by Cramer's rule (well conditioned on [0, 1])
+    const double a00 = m[0], a01 = m[1], a02 = m[2], a11 = m[2], a12 = m[3], a22 = m[4];
+    const double det = a00 * (a11 * a22 - a12 * a12) - a01 * (a01 * a22 - a12 * a02) + a02 * (a01 * a12 - a11 * a02);
+    const double c0 = (b[0] * (a11 * a22 - a12 * a12) - a01 * (b[1] * a22 - a12 * b[2]) + a02 * (b[1] * a12 - a11 * b[2])) / det;
+    const double c1 = (a00 * (b[1] * a22 - a12 * b[2]) - b[0] * (a01 * a22 - a12 * a02) + a02 * (a01 * b[2] - b[1] * a02)) / det;
+    const double c2 = (a00 * (a11 * b[2] - b[1] * a12) - a01 * (a01 * b[2] - b[1] * a02) + b[0] * (a01 * a12 - a11 * a02)) / det;
+    coef[r] = make_float4((float)c0, (float)c1, (float)c2, 0.f);
+}
+
+// Stored values: F32 seconds; F16 T minus the row's reference polynomial (FP32 coefficients,
+// evaluated in FP64); U16 round((T - T_min) / scale).
+__global__ void k_table_store(long long n, int nz, const double* __restrict__ T, int dt, double tmin,
+                              double scale, const float4* __restrict__ coef, void* __restrict__ out)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (dt == KH_F32) {
             static_cast<float*>(out)[i] = (float)T[i];
         } else if (dt == KH_F16) {
-            static_cast<__half*>(out)[i] = __double2half(T[i] - tmin);
+            const float4 c = coef[i / nz];
+            const double u = (double)(i % nz) / (nz - 1);
+            const double ref = (double)c.x + u * ((double)c.y + u * (double)c.z);
+            static_cast<__half*>(out)[i] = __double2half(T[i] - ref);
         } else {
             const double u = rint((T[i] - tmin) / scale);
             static_cast<unsigned short*>(out)[i] = (unsigned short)fmin(fmax(u, 0.0), 65535.0);
@@ -829,7 +858,8 @@ static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const floa
     const int nh = (int)std::floor(hmax * (1.0 + 1e-6) / D) + 3;
     const int nz = tile.tiles_z * tile.cz * NZ / m + 2;
     const size_t es = d.table_dtype == KH_F32 ? 4 : 2;
-    const size_t bytes = ((size_t)nh * nz * es + 15) / 16 * 16;
+    const size_t node_bytes = ((size_t)nh * nz * es + 15) / 16 * 16;
+    const size_t bytes = node_bytes + (d.table_dtype == KH_F16 ? (size_t)nh * sizeof(float4) : 0);
     if (bytes > 96u * 1024u)
         return fail(KH_ERR_UNSUPPORTED, "traveltime table of %d x %d nodes (%zu bytes) exceeds the 96 KB "
                                         "shared-memory budget; use a larger table_spacing", nh, nz, bytes);
@@ -847,11 +877,18 @@ static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const floa
         if (e == cudaSuccess) e = cudaMemcpyAsync(mm, p->ws_tmm, sizeof mm, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "table build");
-        const double tmin = d.table_dtype == KH_F32 ? 0.0 : mm[0];
+        const double tmin = d.table_dtype == KH_U16 ? mm[0] : 0.0;
         const double scale = d.table_dtype == KH_U16 ? std::max(mm[1] - mm[0], 1e-30) / 65535.0 : 1.0;
+        float4* coef = reinterpret_cast<float4*>(p->ws_tab + node_bytes);
         e = cudaMemsetAsync(p->ws_tab, 0, bytes, s);
+        if (e == cudaSuccess && d.table_dtype == KH_F16) {
+            k_table_rowfit<<<(nh + 127) / 128, 128, 0, s>>>(nh, nz, p->ws_tab64, coef);
+            ++p->launches;
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess) {
-            k_table_store<<<blocks, 256, 0, s>>>(n, p->ws_tab64, (int)d.table_dtype, tmin, scale, p->ws_tab);
+            k_table_store<<<blocks, 256, 0, s>>>(n, nz, p->ws_tab64, (int)d.table_dtype, tmin, scale, coef,
+                                                 p->ws_tab);
             ++p->launches;
             e = cudaGetLastError();
         }
@@ -866,6 +903,7 @@ static kh_status ensure_table(kh_plan_s* p, int ntr, const float* sx, const floa
     g.tnz = p->tab_nz;
     g.tdt = (int)d.table_dtype;
     g.tinv = (float)(1.0 / D);
+    g.tunz = (float)(1.0 / (g.tnz - 1));
     g.thmax = (float)(g.tnh - 1) - 1e-3f;
     g.tza = za;
     g.tsp = D;

@@ -109,6 +109,8 @@ struct GeomParams {
     int tnh, tnz;            // nodes along h and z
     int tdt;                 // storage kh_dtype: KH_F32, KH_F16, KH_U16
     float tinv;              // 1 / table_spacing
+    float tunz;              // KH_F16: 1 / (tnz - 1), the normalised node depth u_j = j tunz of
+                             // the per-row reference c0 + u (c1 + u c2) added to each FP16 residual
     float thmax;             // largest usable h coordinate (tnh - 1 - 1e-3)
     double tza, tsp;         // first z node (the first image depth), h spacing
     int tm;                  // depth nodes every tm image samples (1, 2 or 4)

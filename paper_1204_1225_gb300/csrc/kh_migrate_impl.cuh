@@ -73,11 +73,18 @@ __host__ __device__ constexpr size_t mig_static_bytes() { return (sizeof(MigSmem
 // 1 KB per CTA; 128 B of static shared variables).
 constexpr size_t CTA_SMEM_BUDGET = 228 * 1024 / 2 - 1024 - 128;
 
+// Nodes [tnh][tnz] (16-byte padded), then for KH_F16 one float4 (c0, c1, c2, 0) per h row: the
+// row's reference polynomial in the normalised node depth (the nodes hold T minus it in FP16).
+__host__ __device__ inline size_t table_node_bytes(const GeomParams& g)
+{
+    const size_t es = g.tdt == KH_F32 ? 4 : 2;
+    return ((size_t)g.tnh * g.tnz * es + 15) / 16 * 16;
+}
+
 __host__ __device__ inline size_t table_bytes(const GeomParams& g)
 {
     if (!g.table) return 0;
-    const size_t es = g.tdt == KH_F32 ? 4 : 2;
-    return ((size_t)g.tnh * g.tnz * es + 15) / 16 * 16;
+    return table_node_bytes(g) + (g.tdt == KH_F16 ? (size_t)g.tnh * sizeof(float4) : 0);
 }
 
 // Per consumer thread and depth, the cached source leg of the current source position (see
@@ -160,6 +167,19 @@ __device__ __forceinline__ void tab_profile(const TB* tab, const GeomParams& g, 
     for (int k = 0; k < K; ++k) {
         const float a = tab_f32<TB>(r0[k]), b = tab_f32<TB>(r1[k]);
         p[k] = fmaf(fh, b - a, a);
+    }
+    if constexpr (std::is_same<TB, __half>::value) {
+        // FP16 residuals: add the rows' reference polynomials, interpolated in h like the nodes
+        // (the interpolation is linear in the coefficients)
+        const float4* cf = reinterpret_cast<const float4*>(reinterpret_cast<const char*>(tab) + table_node_bytes(g));
+        const float4 q0 = cf[ih], q1 = cf[ih + 1];
+        const float c0 = fmaf(fh, q1.x - q0.x, q0.x), c1 = fmaf(fh, q1.y - q0.y, q0.y);
+        const float c2 = fmaf(fh, q1.z - q0.z, q0.z);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float u = (float)(jb + k) * g.tunz;
+            p[k] += fmaf(fmaf(c2, u, c1), u, c0);
+        }
     }
 }
 

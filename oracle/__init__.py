@@ -229,3 +229,90 @@ def cgls(s, data, n_iter: int, m0=None):
         rn.append(float(np.linalg.norm(r)))
         gn.append(float(np.sqrt(gamma)))
     return m, np.array(rn), np.array(gn)
+
+
+# ------------------------------------------------------------------ velocity analysis (FP64)
+# Sec. 2: migration with an estimate of the velocity gives a set of redundant images (one per
+# offset bin here); differences in the position of the same reflector between them measure the
+# error of the velocity model, which is corrected and the data migrated again; once they agree
+# the images are stacked.  The measure taken here is the normalised variance of the weighted
+# offset images across the bins (one minus the semblance of the stack):
+#     V = sum_b ||w_b I_b - m||^2 / sum_b ||w_b I_b||^2,   m = (1/N) sum_b w_b I_b,
+# over the N bins that hold traces, with w_b = 1 / (traces in bin b).  Its image gradient is
+#     dV/dI_b = (2 w_b / B) ((w_b I_b - m) - V w_b I_b),   B = sum_b ||w_b I_b||^2,
+# and its (v0, k) gradient is the velocity gradient of <dV/dI, L(v0, k) D> (ko_vgrad).
+
+_va_mutation = 0   # deliberate mistakes for the tests of the pins only; 0 = as written
+
+
+def bin_weights(s) -> np.ndarray:
+    """w_b = 1 / (traces in bin b), 0 for bins without traces."""
+    b = bins(s)
+    n = np.bincount(b[b >= 0], minlength=s.n_bins).astype(np.float64)
+    return np.where(n > 0, 1.0 / np.maximum(n, 1.0), 0.0)
+
+
+def semblance(image, weights):
+    """(V, dV/dI) of offset images [n_bins, ...] with bin weights w_b, FP64."""
+    img = np.asarray(image, dtype=np.float64)
+    w = np.asarray(weights, dtype=np.float64)
+    used = w > 0
+    if _va_mutation == 1:
+        w = np.where(used, 1.0, 0.0)                     # weights dropped
+    shape = (-1,) + (1,) * (img.ndim - 1)
+    wi = img * w.reshape(shape)
+    N = int(used.sum())
+    m = wi[used].sum(axis=0) / N
+    if _va_mutation == 2:
+        m = wi[used].sum(axis=0) / (N - 1)               # wrong bin count in the mean
+    dev = np.where(used.reshape(shape), wi - m, 0.0)
+    D = float(np.sum(dev * dev))
+    B = float(np.sum(wi * wi))
+    V = D / B
+    G = (2.0 * w.reshape(shape) / B) * (dev - V * wi)
+    if _va_mutation == 3:
+        G = (2.0 * w.reshape(shape) / B) * (dev + V * wi)   # sign of the quotient term
+    return V, G
+
+
+def velocity_objective(s, traces, v0, k):
+    """(V, dV/dv0, dV/dk) of the offset images L(v0, k) D: migrate, semblance, and the velocity
+    gradient of <dV/dI, L(v0, k) D>."""
+    sv_ = s.replace(v0=float(v0), k=float(k))
+    img = migrate(sv_, traces)
+    V, G = semblance(img, bin_weights(s))
+    g = vgrad(sv_, G, traces)
+    return V, float(g[0]), float(g[1])
+
+
+def velocity_analysis(s, traces, v0, k, n_iter: int = 30, scale=(100.0, 0.1), tol: float = 1e-12):
+    """Minimises V over (v0, k) from a start: the textbook BFGS iteration on the scaled
+    parameters (v0 / scale[0], k / scale[1]) with an Armijo backtracking line search.
+    Returns (v0, k, history of (v0, k, V))."""
+    sc = np.asarray(scale, dtype=np.float64)
+    th = np.array([v0, k], dtype=np.float64)
+    V, g0, g1 = velocity_objective(s, traces, *th)
+    g = np.array([g0, g1]) * sc
+    H = np.eye(2)
+    hist = [(th[0], th[1], V)]
+    for _ in range(n_iter):
+        p = -H @ g
+        a = 1.0
+        while True:
+            tn = th + a * p * sc
+            Vn, h0, h1 = velocity_objective(s, traces, *tn)
+            if Vn <= V + 1e-4 * a * float(g @ p) or a < 1e-3:
+                break
+            a *= 0.5
+        gn = np.array([h0, h1]) * sc
+        step, y = a * p, gn - g
+        if float(step @ y) > 1e-300:
+            r = 1.0 / float(y @ step)
+            I = np.eye(2)
+            H = (I - r * np.outer(step, y)) @ H @ (I - r * np.outer(y, step)) + r * np.outer(step, step)
+        done = abs(V - Vn) <= tol * max(abs(V), 1e-300)
+        th, V, g = tn, Vn, gn
+        hist.append((th[0], th[1], V))
+        if done:
+            break
+    return float(th[0]), float(th[1]), hist

@@ -127,6 +127,35 @@ def survey_3d_gradient(ntr: int = 100_000, n: int = 256) -> Survey:
                   name=f"3d-vz-{ntr}tr-{n}cube")
 
 
+def survey_25d_velan(nx: int = 128, nz: int = 100, h: float = 15.0, nt: int = 800, n_shots: int = 48,
+                     n_rec: int = 96, n_bins: int = 4, aperture: float = 400.0, v0: float = 1800.0,
+                     k: float = 0.6) -> Survey:
+    """A shorter 2.5D line of the least-squares geometry for velocity analysis: shots every 25 m
+    and split spreads of receivers at 12.5 m (offsets up to ~600 m), centred over an nx x nz
+    image at h m; v(z) = v0 + k z (the 2.5D line's model by default); W = 1; a 400 m aperture;
+    4 offset bins of 150 m."""
+    xs = 25.0 * np.arange(n_shots)
+    xs = xs + 0.5 * ((nx - 1) * h - xs[-1])
+    sx = np.repeat(xs, n_rec)
+    rx = sx + np.tile((np.arange(n_rec) - (n_rec - 1) / 2.0) * 12.5, n_shots)
+    z = np.zeros_like(sx)
+    wmax = float(np.max(np.abs(rx - sx)))
+    return Survey(dim=2, nx=nx, ny=1, nz=nz, ox=0.0, oy=0.0, oz=0.0, dx=h, dy=h, dz=h,
+                  n_bins=n_bins, bin_width=wmax * 1.0001 / n_bins, vel="linear", v0=v0, k=k,
+                  weight="one", r0=1000.0, aperture=aperture, nt=nt, t0=0.0, dt=0.004,
+                  sx=_f32(sx), sy=_f32(z), rx=_f32(rx), ry=_f32(z),
+                  name=f"25d-velan-{sx.size}tr-{nx}x{nz}")
+
+
+def diffractors_2d(rng: np.random.Generator, survey: Survey, n: int = 12, zr=(300.0, 1300.0),
+                   amp: float = 1.0) -> np.ndarray:
+    """Point diffractors uniform over the middle half of the line and a depth range (y = 0)."""
+    w = (survey.nx - 1) * survey.dx
+    x = rng.uniform(survey.ox + 0.25 * w, survey.ox + 0.75 * w, n)
+    z = rng.uniform(zr[0], zr[1], n)
+    return np.stack([x, np.zeros(n), z, np.full(n, amp)], axis=1)
+
+
 def survey_batch_3d(n_jobs: int = 64, n_range=(64, 192), ntr_range=(1000, 50_000),
                     nt_range=(750, 2000), seed: int = BASE_SEED, h: float = 10.0) -> List[Survey]:
     """Batch of independent 3D migrations of uneven size, each with the physics of the 2D

@@ -108,6 +108,7 @@ def workloads():
         "3d-vz-10k-256cube": lambda: sv.survey_3d_gradient(ntr=10_000, n=256),
         "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
         "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
+        "25d-velan-4608tr-128x100": lambda: sv.survey_25d_velan(),
         "batch64-3d-vz": lambda: sv.survey_batch_3d(64),
         "batch8-3d-vz-small": lambda: sv.survey_batch_3d(8, n_range=(64, 96), ntr_range=(1000, 5000)),
     }
@@ -314,9 +315,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-loop", action="store_true", help="batch: skip the per-job loop arm")
     ap.add_argument("--batch-mode", default="concurrent", choices=["persistent", "concurrent"],
                     help="batch: one persistent kernel, or each job's kernel on forked streams")
-    ap.add_argument("--op", default="migrate", choices=["migrate", "demigrate", "vgrad", "cgls"],
-                    help="operator timed: migration (Eq. 1), its adjoint, the (v0, k) gradient, or a "
-                         "least-squares migration (CGLS, --cg-iters iterations) per step")
+    ap.add_argument("--op", default="migrate", choices=["migrate", "demigrate", "vgrad", "cgls", "velan"],
+                    help="operator timed: migration (Eq. 1), its adjoint, the (v0, k) gradient, a "
+                         "least-squares migration (CGLS, --cg-iters iterations) per step, or a velocity "
+                         "analysis (BFGS on the offset images' semblance, from a perturbed model) per step")
     ap.add_argument("--cg-iters", type=int, default=20, help="CGLS iterations of one --op cgls step")
     ap.add_argument("--aperture", type=float, default=None,
                     help="override the workload's aperture (metres)")
@@ -353,6 +355,8 @@ def main():
         line = run_batched(args, s, ws, rank, local, dev)
     elif args.op == "cgls":
         line = run_cgls(args, s, ws, rank, local, dev)
+    elif args.op == "velan":
+        line = run_velan(args, s, ws, rank, local, dev)
     else:
         cache = {}
         line = run_single(args, s, ws, rank, local, dev, cache)
@@ -653,6 +657,55 @@ def run_cgls(args, s, ws, rank, local, dev):
                      "frac": None, "unit": "Gcontrib/s",
                      "peak_basis": "a sum of two kernels; see the migrate and demigrate lines"},
         "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
+    }
+
+
+def run_velan(args, s, ws, rank, local, dev):
+    """Velocity analysis: each step migrates, measures the semblance of the offset images and its
+    (v0, k) gradient, and updates (v0, k) by BFGS until it converges (at most 30 iterations),
+    starting from v0 - 100 m/s, k - 0.1.  Noise-free 12 Hz diffractors.  The metric counts the
+    contributions of every migration and gradient call of the step."""
+    from paper_1204_1225_gb300.velan import VelocityAnalysis
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    sc = sv.diffractors_2d(np.random.default_rng(3), s)
+    d = sv.synthesize(s, sc, kh.arrival_times_fn(kh.Plan(s)), 12.0, device=dev)
+    contrib = kh.Plan(s).count(kh.Headers.of(s, device=dev))
+    va = VelocityAnalysis(s, d, fast_math=bool(args.fast_math), device=dev)
+    start = (s.v0 - 100.0, s.k - 0.1)
+    va.run(*start, n_iter=3)                      # warm-up
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    va.evaluations = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = va.run(*start, n_iter=30)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    t_ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    if rank != 0:
+        return None
+    evals = va.evaluations / args.steps
+    zref = 700.0
+    return {
+        "metric": "G image-point x trace contributions/s",
+        "value": 2 * contrib * evals * args.steps / (t_ms / 1e3) / 1e9, "unit": "Gcontrib/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": 1, "ms_per_step": t_ms / args.steps,
+        "ms_per_evaluation": t_ms / args.steps / evals, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": s.name, "operator": "velocity analysis: BFGS on the semblance of the offset "
+                                                   "images, gradient through the velocity-gradient kernel",
+                   "start": {"v0": start[0], "k": start[1]}, "true": {"v0": s.v0, "k": s.k},
+                   "contributions_per_migration": contrib, "evaluations_per_step": evals,
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "result": {"v0": r["v0"], "k": r["k"], "V": r["V"], "iterations": len(r["history"]) - 1,
+                   "v_at_700m_rel_err": (r["v0"] + r["k"] * zref - (s.v0 + s.k * zref)) / (s.v0 + s.k * zref),
+                   "k_err": r["k"] - s.k},
+        "roofline": {"bound": "alu", "kernel": "k_migrate + k_vgrad", "achieved": None, "peak": None,
+                     "frac": None, "unit": "Gcontrib/s",
+                     "peak_basis": "a loop of two kernels; see the migrate and vgrad lines"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
     }
 
 

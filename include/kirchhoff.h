@@ -172,6 +172,28 @@ KH_API kh_status kirchhoff_fit_report(const kh_desc* d, int cx, int cy, int cz, 
                                       int* leg_terms, double* leg_bound, float* coef, float* scale,
                                       float* offset, double* c1);
 
+/* ---------------------------------------------------------------- velocity analysis
+ * Sec. 2: migration with an estimate of the velocity produces redundant images (here one per
+ * offset bin); differences in the position of the same reflector between them measure the error
+ * of the velocity model, which is corrected before the data are migrated again and, once the
+ * images agree, stacked.  kirchhoff_semblance measures that disagreement for an offset-binned
+ * image of plan `p`:
+ *     V = sum_b ||w_b I_b - m||^2 / sum_b ||w_b I_b||^2,   m = (1/N) sum_b w_b I_b,
+ * the normalised variance of the weighted images across the N bins with w_b > 0 (0 when all
+ * agree, 1 - 1/N for images with disjoint supports), and optionally its image gradient
+ *     grad[b] = dV/dI_b = (2 w_b / B) ((w_b I_b - m) - V w_b I_b),   B = sum_b ||w_b I_b||^2,
+ * so that kirchhoff_velocity_grad(p, ..., image = grad, traces = D, ...) gives dV/d(v0, k) of the
+ * images migrated with p.  image: DEVICE FP32 [n_bins][ny][nx][nz]; bin_weight: HOST double
+ * [n_bins], >= 0, or NULL for w_b = 1 / (traces of bin b in p's last migrate or gradient call);
+ * (only traces the sort kept count: a trace whose midpoint is farther than the aperture from
+ * every image column is dropped by the sort and reaches no image point);
+ * out: HOST double[3] = (V, D, B), D and B the two sums; grad_image: DEVICE FP32, image-shaped,
+ * overwritten, or NULL.  Sums are FP64 in a fixed order (the result does not change from run to
+ * run).  Synchronises `cuda_stream`.  Errors: KH_ERR_INVALID_ARG (NULL image/out, negative or
+ * non-finite weights, all weights zero, NULL weights before any migration of p). */
+KH_API kh_status kirchhoff_semblance(kh_plan p, const float* image, const double* bin_weight, double* out,
+                                     float* grad_image, void* cuda_stream);
+
 /* ---------------------------------------------------------------- the binning sort
  * Eq. (1)'s delta(X - |x_s - x_r|) assigns each trace to one offset bin, and only traces "close
  * enough" to an image point contribute (Sec. 3 after Eq. 2).  Before every migration and

@@ -1028,6 +1028,7 @@ kh_status kirchhoff_destroy(kh_plan p)
     cudaFree(p->ws_hist);
     cudaFree(p->ws_cell_start);
     cudaFree(p->ws_stats);
+    cudaFree(p->ws_semb);
     cudaFree(p->ws_pad);
     cudaFree(p->ws_count);
     cudaFree(p->ws_partial);

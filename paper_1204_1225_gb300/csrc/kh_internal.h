@@ -59,6 +59,8 @@ enum VelKind { VK_CONST = 0, VK_LINEAR = 1, VK_TABLE = 2 };
 // widened by `margin` (a little more than the aperture), so a midpoint outside it is farther
 // than the aperture from every column and is dropped with the traces that have no offset bin.
 // With a full aperture (margin <= 0) there is one cell and nothing is dropped.
+// Offset bins the velocity-analysis kernels carry weights for (the plan allows up to 256).
+constexpr int MAX_BIN_WEIGHTS = 256;
 constexpr int MAX_CELLS_PER_AXIS = 16;
 constexpr int MAX_CELL_ROWS = MAX_CELLS_PER_AXIS;
 struct CellGrid {

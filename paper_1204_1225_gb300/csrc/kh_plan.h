@@ -40,6 +40,7 @@ struct kh_plan_s {
     kh::CellGrid cur_cg{};            // and its cell grid
     int spatial_sort = 1;             // KH_OPT_SPATIAL_SORT
     unsigned long long* ws_stats = nullptr;   // [3] staging statistics (while profiling)
+    double* ws_semb = nullptr;    // velocity analysis: block partials and (V, D, B)
     unsigned char* ws_pad = nullptr;
     size_t cap_pad = 0;
     long long* ws_count = nullptr;

@@ -62,7 +62,7 @@ EXPORTS = ["kirchhoff_create", "kirchhoff_destroy", "kirchhoff_migrate", "kirchh
            "kirchhoff_set_option", "kirchhoff_launch_count", "kirchhoff_last_error",
            "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read",
            "kirchhoff_migrate_noalloc", "kirchhoff_fit_report", "kirchhoff_staging_stats",
-           "kirchhoff_cell_grid", "kirchhoff_bin_sort"]
+           "kirchhoff_cell_grid", "kirchhoff_bin_sort", "kirchhoff_semblance"]
 
 
 def lib(path: str = LIB_PATH):
@@ -104,6 +104,7 @@ def lib(path: str = LIB_PATH):
             L.kirchhoff_cell_grid.argtypes = [ctypes.POINTER(kh_desc), I, ctypes.POINTER(I), ctypes.POINTER(I),
                                               D, D, D]
             L.kirchhoff_bin_sort.argtypes = [P, I, P, P, P, P, P, P, P]
+            L.kirchhoff_semblance.argtypes = [P, P, D, D, P, P]
             for name in EXPORTS:
                 getattr(L, name).restype = S
             L.kirchhoff_launch_count.restype = ctypes.c_longlong
@@ -299,6 +300,17 @@ def kirchhoff_bin_sort(plan, ntr, sx, sy, rx, ry, perm_out, key_start_out, strea
                                     _ptr(ry), _ptr(perm_out), _ptr(key_start_out), _stream(stream)))
 
 
+def kirchhoff_semblance(plan, image, bin_weight=None, grad_image=None, stream=None):
+    """(V, D, B) of the offset images; fills grad_image with dV/dI when given (see the header)."""
+    out = (ctypes.c_double * 3)()
+    w = None
+    if bin_weight is not None:
+        w = (ctypes.c_double * len(bin_weight))(*[float(x) for x in bin_weight])
+    _check(lib().kirchhoff_semblance(ctypes.c_void_p(plan), _ptr(image), w, out, _ptr(grad_image),
+                                     _stream(stream)))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
 def kirchhoff_staging_stats(plan, stream=None):
     """(traces examined, traces staged, CTAs) of the staging warps since the previous read,
     while profiling is enabled; synchronises the stream."""
@@ -455,6 +467,16 @@ class Plan:
     def profile_read(self):
         """(summed main-kernel milliseconds, timed launches) since the previous read."""
         return kirchhoff_profile_read(self.handle)
+
+    def semblance(self, image, bin_weight=None, grad=False, stream=None):
+        """(V, dV/dI or None) of an offset-binned image of this plan (velocity analysis)."""
+        specs = [(image, "image", torch.float32, None, self.image_shape)]
+        if bin_weight is not None and len(bin_weight) != self.survey.n_bins:
+            raise ValueError("kirchhoff: one bin weight per offset bin")
+        _validate(specs, self.device)
+        g = torch.empty_like(image) if grad else None
+        V, _, _ = kirchhoff_semblance(self.handle, image, bin_weight, g, stream)
+        return V, g
 
     def bin_sort(self, hdr: Headers, stream=None):
         """The binning sort of this plan: (perm [ntr] int32, key starts int32) on the device."""

@@ -77,7 +77,7 @@ def lib():
 def desc(s) -> _Desc:
     """Oracle descriptor from a ``Survey`` (any object with the same attribute names)."""
     return _Desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
-                 s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1, "table": 2}[s.vel], s.v0, s.k,
+                 s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1, "table": 2, "pstm": 3}[s.vel], s.v0, s.k,
                  {"one": 0, "obliq": 1}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt,
                  float(getattr(s, "table_spacing", 25.0)))
 
@@ -112,7 +112,8 @@ def bins(s) -> np.ndarray:
 
 
 def traveltime(s, R, z, grad: bool = False):
-    """One-way time (and d/dv0, d/dk) from a surface point to distance R, depth z."""
+    """One-way time (and d/dv0, d/dk) from a surface point to distance R, depth z (vel "pstm":
+    R is the horizontal distance and z the two-way vertical time; no derivatives)."""
     R = np.asarray(R, dtype=np.float64)
     z = np.ascontiguousarray(np.broadcast_to(np.asarray(z, dtype=np.float64), R.shape)).ravel()
     R = np.ascontiguousarray(R).ravel()

@@ -38,7 +38,8 @@ typedef struct {
     double ox, oy, oz, dx, dy, dz;
     int n_bins;
     double bin_width;
-    int vel;                 /* 0 constant, 1 linear in z, 2 table of the linear model */
+    int vel;                 /* 0 constant, 1 linear in z, 2 table of the linear model, 3 time
+                                migration (double square root, RMS velocity of the linear model) */
     double v0, k;
     int weight;              /* 0 W=1, 1 obliquity x spreading */
     double r0;
@@ -88,9 +89,39 @@ static void asinh_over_s(double s, double* h, double* hp)
     }
 }
 
-/* One-way time from a surface point (z = 0) to a point at distance R and depth z. */
+/* Prestack time migration (vel 3): the image's vertical axis is the two-way vertical time t0 (its
+ * "z" coordinates are seconds), and each leg takes the double-square-root time of a straight ray
+ * through a medium of the RMS velocity of v(z) = v0 + k z down to the one-way vertical time t0/2:
+ *     T_a = sqrt((t0/2)^2 + h_a^2 / v_rms(t0)^2),   h_a the horizontal distance,
+ *     v_rms(t0)^2 = (2/t0) integral_0^{t0/2} v(tau)^2 dtau = v0^2 (e^{k t0} - 1) / (k t0),
+ * since dz/dtau = v gives v(tau) = v0 e^{k tau} at one-way vertical time tau. */
+static double vrms2(const ko_desc* d, double t0)
+{
+    const double x = d->k * t0;
+    if (ko_mutation == 11) {   /* the interval velocity at t0/2 instead of the RMS velocity */
+        const double v = d->v0 * exp(0.5 * x);
+        return v * v;
+    }
+    if (fabs(x) < 1e-6) return d->v0 * d->v0 * (1.0 + x / 2.0 + x * x / 6.0);
+    return d->v0 * d->v0 * expm1(x) / x;
+}
+
+static double dsr_leg(const ko_desc* d, double h, double t0)
+{
+    const double half = (ko_mutation == 12) ? t0 : 0.5 * t0;
+    return sqrt(half * half + h * h / vrms2(d, t0));
+}
+
+/* One-way time from a surface point (z = 0) to a point at distance R and depth z (vel 3: R is
+ * the horizontal distance and z the two-way vertical time). */
 static void traveltime(const ko_desc* d, double R, double z, double* T, double* dTdv0, double* dTdk)
 {
+    if (d->vel == 3) {
+        *T = dsr_leg(d, R, z);
+        if (dTdv0) *dTdv0 = 0.0;
+        if (dTdk) *dTdk = 0.0;
+        return;
+    }
     if (d->vel == 0) {
         *T = R / d->v0;
         if (dTdv0) *dTdv0 = -R / (d->v0 * d->v0);
@@ -242,7 +273,17 @@ static contrib contribution(const ko_desc* d, double x, double y, double z, doub
     double Rr = sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry) + z * z);
     if (ko_mutation == 3) Rr = Rs;
     double Ts, Tr, dsv = 0, dsk = 0, drv = 0, drk = 0;
-    if (d->vel == 2) {
+    double zw = z;   /* the depth of the weight (vel 3: the equivalent depth v_rms t0 / 2) */
+    if (d->vel == 3) {
+        const double vr = sqrt(vrms2(d, z));
+        Ts = dsr_leg(d, sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy)), z);
+        Tr = dsr_leg(d, sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry)), z);
+        /* straight rays through the RMS medium: R_a = v_rms T_a, depth v_rms t0 / 2 */
+        Rs = vr * Ts;
+        Rr = vr * Tr;
+        zw = vr * 0.5 * z;
+        if (fabs(z) < 1e-6 * fabs(d->dz)) zw = 0.0;
+    } else if (d->vel == 2) {
         Ts = table_traveltime(d, sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy)), z);
         Tr = table_traveltime(d, sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry)), z);
         if (ko_mutation == 3) Tr = Ts;
@@ -259,7 +300,11 @@ static contrib contribution(const ko_desc* d, double x, double y, double z, doub
     c.i = i;
     c.f = tau - (double)i;
     if (ko_mutation == 6) c.f = 1.0 - c.f;
-    c.W = weight(d, z, Rs, Rr);
+    c.W = (d->vel == 3) ? (d->weight == 0 || ko_mutation == 1 ? 1.0
+                                                              : (zw == 0.0 ? 0.0
+                                                                           : 0.5 * (zw / Rs + zw / Rr) * Rs * Rr /
+                                                                                 (d->r0 * d->r0)))
+                        : weight(d, z, Rs, Rr);
     if (want_grad) {
         c.dtau_dv0 = (dsv + drv) / d->dt;
         c.dtau_dk = (dsk + drk) / d->dt;
@@ -453,7 +498,10 @@ int ko_arrivals(const ko_desc* d, long npts, const double* px, const double* py,
             double Rs = sqrt((x - sx[j]) * (x - sx[j]) + (y - ssy) * (y - ssy) + z * z);
             double Rr = sqrt((x - rx[j]) * (x - rx[j]) + (y - rry) * (y - rry) + z * z);
             double Ts, Tr;
-            if (d->vel == 2) {
+            if (d->vel == 3) {
+                Ts = dsr_leg(d, sqrt((x - sx[j]) * (x - sx[j]) + (y - ssy) * (y - ssy)), z);
+                Tr = dsr_leg(d, sqrt((x - rx[j]) * (x - rx[j]) + (y - rry) * (y - rry)), z);
+            } else if (d->vel == 2) {
                 Ts = table_traveltime(d, sqrt((x - sx[j]) * (x - sx[j]) + (y - ssy) * (y - ssy)), z);
                 Tr = table_traveltime(d, sqrt((x - rx[j]) * (x - rx[j]) + (y - rry) * (y - rry)), z);
             } else {

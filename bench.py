@@ -109,6 +109,8 @@ def workloads():
         "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
         "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
         "25d-velan-4608tr-128x100": lambda: sv.survey_25d_velan(),
+        "3d-pstm-100k-256cube": lambda: sv.survey_3d_gradient().replace(
+            vel="pstm", oz=0.0, dz=0.012, name="3d-pstm-100000tr-256x256x256t"),
         "batch64-3d-vz": lambda: sv.survey_batch_3d(64),
         "batch8-3d-vz-small": lambda: sv.survey_batch_3d(8, n_range=(64, 96), ntr_range=(1000, 5000)),
     }
@@ -213,7 +215,11 @@ def synth_traces(s, plan, device):
     from paper_1204_1225_gb300 import kirchhoff as kh
     rng = np.random.default_rng(sv.BASE_SEED)
     if s.dim == 3:
-        sc = sv.reflectors_3d(rng, s, spacing=100.0)
+        if s.vel == "pstm":   # the time image: depth scatterers, depths read as two-way times (1 km/s)
+            sc = sv.reflectors_3d(rng, s.replace(vel="linear", oz=0.0, dz=12.5), spacing=100.0)
+            sc[:, 2] *= 1e-3
+        else:
+            sc = sv.reflectors_3d(rng, s, spacing=100.0)
         freq = 20.0
     else:
         sc = sv.point_scatterers_2d(rng, xr=(0.1 * s.nx * s.dx, 0.9 * s.nx * s.dx),

@@ -73,8 +73,16 @@ typedef enum { KH_F32 = 0, KH_F16 = 1, KH_BF16 = 2, KH_U16 = 3 } kh_dtype;
  *                   coefficients) or KH_U16 (16-bit fixed point T = T_min + scale u,
  *                   scale = (T_max - T_min)/65535).  A migrate call
  *                   with a table plan reads the headers' extent back to the host (it
- *                   synchronises the stream). */
-typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2 } kh_vel;
+ *                   synchronises the stream).
+ *  KH_VEL_PSTM:     prestack time migration (the PKTM of Sec. 4): the image's vertical axis
+ *                   (oz, dz, nz) is the two-way vertical time t0 in seconds (t0 >= 0), and each
+ *                   leg is the double-square-root time of a straight ray through a medium of
+ *                   the RMS velocity of v(z) = v0 + k z down to the one-way vertical time t0/2,
+ *                   T = sqrt((t0/2)^2 + h^2 / v_rms(t0)^2), h the horizontal distance,
+ *                   v_rms(t0)^2 = v0^2 (e^{k t0} - 1) / (k t0).  Migration and the utilities
+ *                   only (demigration and the velocity gradient refuse it).  The weight's
+ *                   geometry is that of the straight rays: R = v_rms T, z = v_rms t0 / 2. */
+typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2, KH_VEL_PSTM = 3 } kh_vel;
 
 /* Weight W(x, x_s, x_r) of Eq. (1) ("amplitude of propagation"; no formula in the paper):
  *  KH_W_ONE:          W = 1.
@@ -147,8 +155,9 @@ KH_API kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, co
                                   const float* traces, double* out_dv0_dk, void* cuda_stream);
 
 /* Traveltime evaluation (the T of Eq. 1 under the plan's velocity model) for n
- * elementwise (point, surface location) pairs: T[i] = T((px,py,pz)[i], (lx,ly)[i]).
- * All arrays device FP32 [n]; ly/py may be NULL for dim 2. */
+ * elementwise (point, surface location) pairs: T[i] = T((px,py,pz)[i], (lx,ly)[i]) (for
+ * KH_VEL_PSTM, pz is the two-way vertical time t0).  All arrays device FP32 [n]; ly/py may be
+ * NULL for dim 2. */
 KH_API kh_status kirchhoff_traveltime(kh_plan p, int n, const float* px, const float* py,
                                const float* pz, const float* lx, const float* ly, float* T,
                                void* cuda_stream);

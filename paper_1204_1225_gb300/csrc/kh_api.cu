@@ -213,6 +213,9 @@ __global__ void k_count(int ntr, const float* __restrict__ sx, const float* __re
 }
 
 // Traveltime of the plan's model in FP64, rounded to FP32 (a utility, not the hot loop).
+// Velocity kind of the traveltime utility for time migration (the double-square-root leg).
+constexpr int VK_PSTM_UTIL = 7;
+
 __device__ double tt_exact(double R, double z, int vel, double v0, double k)
 {
     if (vel == VK_CONST || k == 0.0) return R / v0;
@@ -233,6 +236,11 @@ __global__ void k_traveltime(int n, const float* __restrict__ px, const float* _
     const double ex = (double)px[i] - lx[i];
     const double ey = (py && ly) ? (double)py[i] - ly[i] : 0.0;
     const double z = pz[i];
+    if (vel == VK_PSTM_UTIL) {   // time migration: z is the two-way vertical time t0
+        const double h2 = ex * ex + ey * ey;
+        T[i] = (float)sqrt(0.25 * z * z + h2 / vrms2_of(v0, k, z));
+        return;
+    }
     T[i] = (float)tt_exact(sqrt(ex * ex + ey * ey + z * z), z, vel, v0, k);
 }
 
@@ -259,8 +267,10 @@ static kh_status validate_desc(const kh_desc* d)
     if (d->n_bins < 1 || d->n_bins > kh::MAX_BINS)
         return fail(KH_ERR_INVALID_ARG, "n_bins must be in [1, %d]", kh::MAX_BINS);
     if (!(d->bin_width > 0)) return fail(KH_ERR_INVALID_ARG, "bin_width must be > 0");
-    if (d->vel != KH_VEL_CONST && d->vel != KH_VEL_LINEAR_Z && d->vel != KH_VEL_TABLE)
+    if (d->vel != KH_VEL_CONST && d->vel != KH_VEL_LINEAR_Z && d->vel != KH_VEL_TABLE && d->vel != KH_VEL_PSTM)
         return fail(KH_ERR_INVALID_ARG, "bad velocity kind %d", (int)d->vel);
+    if (d->vel == KH_VEL_PSTM && !(std::min(d->oz, d->oz + (d->nz - 1) * d->dz) >= 0.0))
+        return fail(KH_ERR_INVALID_ARG, "time migration: the image's vertical axis is two-way time, t0 >= 0");
     if (!(d->v0 > 0) || !std::isfinite(d->v0)) return fail(KH_ERR_INVALID_ARG, "v0 must be > 0");
     if (!std::isfinite(d->k)) return fail(KH_ERR_INVALID_ARG, "k must be finite");
     if (d->weight != KH_W_ONE && d->weight != KH_W_OBLIQ_SPREAD)
@@ -270,7 +280,7 @@ static kh_status validate_desc(const kh_desc* d)
     if (!(d->dt > 0) || !std::isfinite(d->t0)) return fail(KH_ERR_INVALID_ARG, "dt must be > 0, t0 finite");
     if (d->trace_dtype != KH_F32 && d->trace_dtype != KH_F16 && d->trace_dtype != KH_BF16)
         return fail(KH_ERR_INVALID_ARG, "bad trace dtype");
-    if (d->vel != KH_VEL_CONST) {
+    if (d->vel != KH_VEL_CONST && d->vel != KH_VEL_PSTM) {
         const double zlo = std::min(0.0, std::min(d->oz, d->oz + (d->nz - 1) * d->dz));
         const double zhi = std::max(d->oz, d->oz + (d->nz - 1) * d->dz);
         if (!(d->v0 + d->k * zlo > 0) || !(d->v0 + d->k * zhi > 0))
@@ -306,7 +316,9 @@ static GeomParams geom_of(const kh_desc& d)
     g.dy = d.dy;
     g.dz = d.dz;
     g.fdz = (float)d.dz;
-    const bool lin = d.vel != KH_VEL_CONST && d.k != 0.0;
+    const bool lin = d.vel != KH_VEL_CONST && d.vel != KH_VEL_PSTM && d.k != 0.0;
+    g.pstm = d.vel == KH_VEL_PSTM ? 1 : 0;
+    g.pk = d.vel == KH_VEL_PSTM ? d.k : 0.0;
     g.v0 = d.v0;
     g.k = lin ? d.k : 0.0;
     g.kabs = std::fabs(g.k);
@@ -1130,8 +1142,9 @@ kh_status kirchhoff_demigrate(kh_plan p, int ntr, const float* sx, const float* 
     kh_status st = check_headers(p, ntr, sx, sy, rx, ry);
     if (st != KH_OK) return st;
     if (ntr > 0 && (!image || !traces_out)) return fail(KH_ERR_INVALID_ARG, "image/traces_out is NULL");
-    if (p->d.vel == KH_VEL_TABLE) return fail(KH_ERR_UNSUPPORTED, "demigration uses the analytic traveltimes; "
-                                                                  "create the plan with KH_VEL_LINEAR_Z");
+    if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM)
+        return fail(KH_ERR_UNSUPPORTED, "demigration uses the analytic depth traveltimes; "
+                                        "create the plan with KH_VEL_CONST or KH_VEL_LINEAR_Z");
     if (ntr == 0) return KH_OK;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const kh_desc& d = p->d;
@@ -1168,7 +1181,8 @@ kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, const flo
     if (st != KH_OK) return st;
     if (!out_dv0_dk) return fail(KH_ERR_INVALID_ARG, "out_dv0_dk is NULL");
     if (ntr > 0 && (!image || !traces)) return fail(KH_ERR_INVALID_ARG, "image/traces is NULL");
-    if (p->d.vel == KH_VEL_TABLE) return fail(KH_ERR_UNSUPPORTED, "no velocity gradient for table traveltimes");
+    if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM)
+        return fail(KH_ERR_UNSUPPORTED, "no velocity gradient for table traveltimes or time migration");
     if (p->d.trace_dtype != KH_F32) return fail(KH_ERR_UNSUPPORTED, "velocity gradient takes FP32 traces");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaMemsetAsync(out_dv0_dk, 0, 2 * sizeof(double), s);
@@ -1237,10 +1251,11 @@ kh_status kirchhoff_traveltime(kh_plan p, int n, const float* px, const float* p
     if (n < 0) return fail(KH_ERR_INVALID_ARG, "n must be >= 0");
     if (n == 0) return KH_OK;
     if (!px || !pz || !lx || !T) return fail(KH_ERR_INVALID_ARG, "NULL array");
-    const bool lin = p->d.vel != KH_VEL_CONST && p->d.k != 0.0;
+    const bool pstm = p->d.vel == KH_VEL_PSTM;
+    const bool lin = !pstm && p->d.vel != KH_VEL_CONST && p->d.k != 0.0;
     k_traveltime<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
         n, px, p->d.dim == 3 ? py : nullptr, pz, lx, p->d.dim == 3 ? ly : nullptr,
-        lin ? VK_LINEAR : VK_CONST, p->d.v0, lin ? p->d.k : 0.0, T);
+        pstm ? VK_PSTM_UTIL : (lin ? VK_LINEAR : VK_CONST), p->d.v0, (lin || pstm) ? p->d.k : 0.0, T);
     ++p->launches;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KH_OK : cuda_fail(e, "traveltime kernel");

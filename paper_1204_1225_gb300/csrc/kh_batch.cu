@@ -150,8 +150,8 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         if (st != KH_OK) return st;
         if (!J.image) return bfail(KH_ERR_INVALID_ARG, "job %d: image is NULL", j);
         if (J.ntr > 0 && !J.traces) return bfail(KH_ERR_INVALID_ARG, "job %d: traces is NULL", j);
-        if (p->d.vel == KH_VEL_TABLE)
-            return bfail(KH_ERR_UNSUPPORTED, "job %d: the batched launch takes analytic traveltimes "
+        if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM)
+            return bfail(KH_ERR_UNSUPPORTED, "job %d: the batched launch takes analytic depth traveltimes "
                                              "(KH_VEL_CONST / KH_VEL_LINEAR_Z)", j);
         if ((st = plan_geometry(p, &gs[j], &tss[j])) != KH_OK) return st;
         if (tss[j].cz > 16 || tss[j].cx * tss[j].cy * tss[j].cz != CONSUMERS)

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                 const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, lr_, &qir);
                 rs = make_float4(ls_.Rc2, qis, ls_.wc, ls_.iuc);
                 rr = make_float4(lr_.Rc2, qir, lr_.wc, lr_.iuc);
-                tau_ref += (ls + lr) * inv_kdt;
+                tau_ref = __dadd_rn(tau_ref, __dmul_rn(__dadd_rn(ls, lr), inv_kdt));
                 ah = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
                                  (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
             }
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
             S.mt[p] = v;
         }
         for (int i = threadIdx.x; i < dt.tz; i += DM_THREADS) {
-            const double z = g.oz + (z0 + i) * g.dz;
+            const double z = grid_coord(g.oz, z0 + i, g.dz);
             if constexpr (VEL == VK_LINEAR) {
                 float gamma;
                 S.zc[i] = z_constants_m(z, box.cz, g, gamma);

@@ -166,6 +166,12 @@ __device__ __forceinline__ float hlog2(float x)
     }
 }
 
+// Grid coordinate o + i h in FP64 without contraction (the same value in every kernel).
+__device__ __forceinline__ double grid_coord(double o, int i, double h)
+{
+    return __dadd_rn(o, __dmul_rn((double)i, h));
+}
+
 // Column coordinate o + i h in FP64 without contraction, rounded to FP32 (the same value the
 // aperture decision uses everywhere).
 __device__ __forceinline__ float col_coord(double o, int i, double h)
@@ -194,15 +200,17 @@ __device__ __forceinline__ int offset_bin(float sx, float sy, float rx, float ry
 }
 
 // One-way traveltime in FP32 for window bounds (not the hot loop): constant or linear v(z).
+// Every operation is rounded explicitly (no contraction), so that every kernel that bounds a
+// window gets the same bounds, and with them the same window-relative times.
 __device__ __forceinline__ float tt_bound(float h, float z, int vel, float v0, float k)
 {
-    const float R = sqrtf(h * h + z * z);
-    if (vel == VK_CONST || k == 0.f) return R / v0;
-    const float vz = v0 + k * z;
-    const float g = sqrtf(v0 * vz);
-    const float s = fabsf(k) * R / (2.f * g);
-    if (s < 1e-3f) return R / g * (1.f - s * s * (1.f / 6.f));
-    return 2.f * asinhf(s) / fabsf(k);
+    const float R = __fsqrt_rn(__fadd_rn(__fmul_rn(h, h), __fmul_rn(z, z)));
+    if (vel == VK_CONST || k == 0.f) return __fdiv_rn(R, v0);
+    const float vz = __fadd_rn(v0, __fmul_rn(k, z));
+    const float g = __fsqrt_rn(__fmul_rn(v0, vz));
+    const float s = __fdiv_rn(__fmul_rn(fabsf(k), R), __fmul_rn(2.f, g));
+    if (s < 1e-3f) return __fmul_rn(__fdiv_rn(R, g), __fsub_rn(1.f, __fmul_rn(__fmul_rn(s, s), 1.f / 6.f)));
+    return __fdiv_rn(__fmul_rn(2.f, asinhf(s)), fabsf(k));
 }
 
 }  // namespace kh

@@ -53,6 +53,15 @@ constexpr long long WAIT_NS = 2000000000LL;
 
 enum VelKind { VK_CONST = 0, VK_LINEAR = 1, VK_TABLE = 2 };
 
+// RMS velocity of v(z) = v0 + k z down to the two-way vertical time t0: v0^2 (e^{k t0} - 1)/(k t0)
+// (v(tau) = v0 e^{k tau} at one-way vertical time tau; the mean of v^2 over [0, t0/2]).
+__host__ __device__ inline double vrms2_of(double v0, double k, double t0)
+{
+    const double x = k * t0;
+    if (x < 1e-6 && x > -1e-6) return v0 * v0 * (1.0 + x * (0.5 + x / 6.0));
+    return v0 * v0 * expm1(x) / x;
+}
+
 // Midpoint cells of the binning sort.  Traces are ordered by (offset bin, cell row cy, cell
 // column cx, original index); cell (cx, cy) covers midpoints m with
 // floor((m_x - gx0) inv_cs) = cx (FP64), likewise in y.  The grid covers the image columns
@@ -106,6 +115,12 @@ struct GeomParams {
                              // tau_ref = -t0/dt) or ln(U/U_c) (linear v); C1lo = FP32 rounding
                              // error of C1
     double c0;               // -t0/dt - 1/2 (the window origin is subtracted per trace)
+    // prestack time migration (KH_VEL_PSTM): the constant-velocity path with per-depth constants,
+    // the image's depth axis being the two-way vertical time t0; each leg is the straight ray of
+    // the RMS velocity v_rms(t0) of v(z) = v0 + pk z, T = sqrt(ze^2 + h^2) / v_rms with the
+    // equivalent depth ze = v_rms t0 / 2 (g.k is 0 so that every kernel takes that path)
+    int pstm;
+    double pk;
     // radial traveltime table (KH_VEL_TABLE)
     const void* table;       // [tnh][tnz] nodes, z fastest
     int tnh, tnz;            // nodes along h and z

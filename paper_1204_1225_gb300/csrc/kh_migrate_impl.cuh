@@ -377,7 +377,7 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                     float qis = 0.f, qir = 0.f;
                     const double ls = leg_reference(box.cx, box.cy, box.cz, h.x, h.y, g, rs, &qis);
                     const double lr = leg_reference(box.cx, box.cy, box.cz, h.z, h.w, g, rr, &qir);
-                    tau_ref += (ls + lr) * inv_kdt;
+                    tau_ref = __dadd_rn(tau_ref, __dmul_rn(__dadd_rn(ls, lr), inv_kdt));
                     // (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c) per leg
                     S.refs[s][slot] = make_float4(rs.Rc2, qis, rs.wc, rs.iuc);
                     S.refr[s][slot] = make_float4(rr.Rc2, qir, rr.wc, rr.iuc);
@@ -386,7 +386,7 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 }
                 S.hdr[s][slot] = h;
                 S.mid[s][slot] = m;
-                S.tb[s][slot] = (float)((double)lo * g.dtd + g.t0d);
+                S.tb[s][slot] = (float)__dadd_rn(__dmul_rn((double)lo, g.dtd), g.t0d);
                 // every column of the tile inside the aperture: the column test is monotone in
                 // |column - midpoint| per axis, so the corner farthest on both axes decides it
                 bool whole = false;
@@ -486,7 +486,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     const bool col_ok = ix < g.nx && iy < g.ny;
     const float cxf = col_coord(g.ox, ix, g.dx);
     const float cyf = (g.dim == 3) ? col_coord(g.oy, iy, g.dy) : 0.f;
-    const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
+    const double xd = grid_coord(g.ox, ix, g.dx), yd = (g.dim == 3) ? grid_coord(g.oy, iy, g.dy) : 0.0;
     const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
     const float4* zc = &S.zc[tzg * NZ];
     const float* zg = &S.z2[tzg * NZ];   // linear: gamma(z) of the weight
@@ -573,8 +573,9 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 auto zloop = [&](auto checked) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
-                        const float Ssum = hsqrt<FAST>(dhs2 + zc[i].x) + hsqrt<FAST>(dhr2 + zc[i].x);
-                        const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
+                        const float4 c = zc[i];   // (z^2, w_z, C1, C1lo): per depth for time migration
+                        const float Ssum = hsqrt<FAST>(dhs2 + c.x) + hsqrt<FAST>(dhr2 + c.x);
+                        const float th = fmaf(Ssum, c.z, fmaf(Ssum, c.w, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
                             val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
@@ -683,7 +684,7 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
     const bool col_ok = ix < g.nx && iy < g.ny;
     const float cxf = col_coord(g.ox, ix, g.dx);
     const float cyf = (g.dim == 3) ? col_coord(g.oy, iy, g.dy) : 0.f;
-    const double xd = g.ox + ix * g.dx, yd = (g.dim == 3) ? g.oy + iy * g.dy : 0.0;
+    const double xd = grid_coord(g.ox, ix, g.dx), yd = (g.dim == 3) ? grid_coord(g.oy, iy, g.dy) : 0.0;
     const float dxc = (float)(xd - box.cx), dyc = (float)(yd - box.cy);
     const float4* zc = &S.zc[tzg * NZ];
     const float* zg = &S.z2[tzg * NZ];   // linear: gamma(z)
@@ -829,7 +830,7 @@ __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, co
                                              const TileBox& box)
 {
     for (int i = threadIdx.x; i < ts.cz * NZ; i += blockDim.x) {
-        const double z = g.oz + (z0 + i) * g.dz;
+        const double z = grid_coord(g.oz, z0 + i, g.dz);
         if constexpr (VEL == VK_LINEAR) {
             float gamma;
             S.zc[i] = z_constants_m(z, box.cz, g, gamma);
@@ -837,9 +838,18 @@ __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, co
         } else if constexpr (VEL == VK_TABLE) {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
             S.zc[i] = make_float4(wz, (float)(z * z), 0.f, 0.f);
+        } else if (g.pstm) {
+            // time migration: z is the two-way vertical time t0; the leg is the straight ray of
+            // the RMS velocity, R = sqrt(h^2 + ze^2) with ze = v_rms t0 / 2, and tau = (R_s + R_r)
+            // C1(t0) - t0/dt with C1(t0) = 1 / (v_rms dt), split into FP32 head and tail
+            const double vr = sqrt(vrms2_of(g.v0, g.pk, z));
+            const double ze = 0.5 * vr * z;
+            const double c1 = 1.0 / (vr * g.dtd);
+            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(ze * g.wscale) : 0.f;
+            S.zc[i] = make_float4((float)(ze * ze), wz, (float)c1, (float)(c1 - (double)(float)c1));
         } else {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-            S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
+            S.zc[i] = make_float4((float)(z * z), wz, g.C1, g.C1lo);
         }
     }
 }

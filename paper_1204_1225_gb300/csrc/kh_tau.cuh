@@ -62,28 +62,34 @@ struct LegRef {
 __device__ __forceinline__ double leg_reference(double cx, double cy, double cz, double hx, double hy,
                                                 const GeomParams& g, LegRef& r, float* qc2i = nullptr)
 {
-    const double ex = cx - hx, ey = cy - hy;
-    const double Rc2 = ex * ex + ey * ey + cz * cz;
-    const double qc = g.a * Rc2 / (g.v0 + g.k * cz);
-    const double wc = sqrt(qc * (qc + 2.0));
+    // explicit roundings (no contraction), so that every kernel computes the same reference
+    const double ex = __dadd_rn(cx, -hx), ey = __dadd_rn(cy, -hy);
+    const double Rc2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(cz, cz));
+    const double qc = __ddiv_rn(__dmul_rn(g.a, Rc2), __dadd_rn(g.v0, __dmul_rn(g.k, cz)));
+    const double wc = __dsqrt_rn(__dmul_rn(qc, __dadd_rn(qc, 2.0)));
+    const double uc = __dadd_rn(__dadd_rn(1.0, qc), wc);
     r.Rc2 = (float)Rc2;
     r.qc = (float)qc;
     r.wc = (float)wc;
-    r.iuc = (float)(1.0 / (1.0 + qc + wc));
-    if (qc2i) *qc2i = (float)((qc + 2.0) / (1.0 + qc + wc));
-    return log1p(qc + wc);
+    r.iuc = (float)__drcp_rn(uc);
+    if (qc2i) *qc2i = (float)__ddiv_rn(__dadd_rn(qc, 2.0), uc);
+    return log1p(__dadd_rn(qc, wc));
 }
 
 // Per-z constants of the linear path, premultiplied by alpha(z):
 // (alpha, alpha kappa, alpha (z^2 - z_c^2), alpha z^2), and gamma(z) for the weight.
 __device__ __forceinline__ float4 z_constants_m(double z, double zc, const GeomParams& g, float& gamma)
 {
-    const double vz = g.v0 + g.k * z;
-    const double alpha = g.a / vz;
-    const double kappa = -g.k * (z - zc) / (g.v0 + g.k * zc);
-    gamma = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale * sqrt(vz / g.a)) : 0.f;
-    return make_float4((float)alpha, (float)(alpha * kappa), (float)(alpha * (z - zc) * (z + zc)),
-                       (float)(alpha * z * z));
+    // explicit roundings (no contraction), so that every kernel computes the same constants
+    const double vz = __dadd_rn(g.v0, __dmul_rn(g.k, z));
+    const double alpha = __ddiv_rn(g.a, vz);
+    const double kappa = __ddiv_rn(__dmul_rn(-g.k, __dadd_rn(z, -zc)), __dadd_rn(g.v0, __dmul_rn(g.k, zc)));
+    gamma = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz))
+                ? (float)__dmul_rn(__dmul_rn(z, g.wscale), __dsqrt_rn(__ddiv_rn(vz, g.a)))
+                : 0.f;
+    return make_float4((float)alpha, (float)__dmul_rn(alpha, kappa),
+                       (float)__dmul_rn(__dmul_rn(alpha, __dadd_rn(z, -zc)), __dadd_rn(z, zc)),
+                       (float)__dmul_rn(__dmul_rn(alpha, z), z));
 }
 
 // base + C1 ln(1 + rho) for one leg from the per-leg fit (lgc = C1-scaled coefficients):
@@ -133,7 +139,8 @@ __device__ __forceinline__ void leg_bounds(float hmin, float hmax, float zlo, fl
                                            float v0, float k, float& tmin, float& tmax)
 {
     const float kk = (vel == VK_CONST) ? 0.f : k;
-    float zs = kk * hmin * hmin / (v0 + sqrtf(v0 * v0 + kk * kk * hmin * hmin));
+    const float kh2 = __fmul_rn(__fmul_rn(kk, hmin), hmin);
+    float zs = __fdiv_rn(kh2, __fadd_rn(v0, __fsqrt_rn(__fadd_rn(__fmul_rn(v0, v0), __fmul_rn(kk, kh2)))));
     zs = fminf(fmaxf(zs, zlo), zhi);
     tmin = fminf(fminf(tt_bound(hmin, zlo, vel, v0, kk), tt_bound(hmin, zhi, vel, v0, kk)),
                  tt_bound(hmin, zs, vel, v0, kk));
@@ -145,15 +152,16 @@ __device__ __forceinline__ void rect_dist(float px, float py, float xlo, float x
 {
     const float ax = fmaxf(fmaxf(xlo - px, px - xhi), 0.f);
     const float ay = fmaxf(fmaxf(ylo - py, py - yhi), 0.f);
-    dmin = sqrtf(ax * ax + ay * ay);
+    dmin = __fsqrt_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)));
     const float bx = fmaxf(fabsf(px - xlo), fabsf(px - xhi));
     const float by = fmaxf(fabsf(py - ylo), fabsf(py - yhi));
-    dmax = sqrtf(bx * bx + by * by);
+    dmax = __fsqrt_rn(__fadd_rn(__fmul_rn(bx, bx), __fmul_rn(by, by)));
 }
 
 struct TileBox {
     float xlo, xhi, ylo, yhi, zlo, zhi;   // FP32 box of the valid samples (window bounds)
     double cx, cy, cz;                    // FP64 centre (linear-path reference point)
+    float ivlo, ivhi;                     // time migration: 1 / largest and 1 / smallest v_rms
 };
 
 // leg_delta_m plus q/w = sqrt(q / (q + 2)) for the velocity derivatives; sq = sqrt(q) always.
@@ -179,15 +187,31 @@ __device__ __forceinline__ float leg_delta_grad_m(float dP, float dh2, const flo
 __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box, int vel,
                                              const GeomParams& g, int& lo, int& hi, bool* clipped = nullptr)
 {
-    const float v0 = (float)g.v0, kf = (float)g.k, inv_dt = 1.f / g.dt;
+    const float v0 = (float)g.v0, kf = (float)g.k, inv_dt = __fdiv_rn(1.f, g.dt);
     float hs0, hs1, hr0, hr1, ts0, ts1, tr0, tr1;
     rect_dist(h.x, h.y, box.xlo, box.xhi, box.ylo, box.yhi, hs0, hs1);
     rect_dist(h.z, h.w, box.xlo, box.xhi, box.ylo, box.yhi, hr0, hr1);
-    leg_bounds(hs0, hs1, box.zlo, box.zhi, vel, v0, kf, ts0, ts1);
-    leg_bounds(hr0, hr1, box.zlo, box.zhi, vel, v0, kf, tr0, tr1);
-    const float tlo = (ts0 + tr0 - g.t0) * inv_dt;
-    const float thi = (ts1 + tr1 - g.t0) * inv_dt;
-    const float slo = 2.f + 2e-4f * fabsf(tlo) + g.tslack, shi = 2.f + 2e-4f * fabsf(thi) + g.tslack;
+    if (g.pstm) {
+        // time migration, T = sqrt((t0/2)^2 + h^2 / v_rms(t0)^2) over t0 in [zlo, zhi] (t0 >= 0):
+        // each term is bounded on its own, v_rms being monotone in t0
+        const float ulo = __fmul_rn(0.5f, box.zlo), uhi = __fmul_rn(0.5f, box.zhi);
+        const float qlo = __fmul_rn(ulo, ulo), qhi = __fmul_rn(uhi, uhi);
+        auto leg = [](float q, float hh, float iv) {
+            const float e = __fmul_rn(hh, iv);
+            return __fsqrt_rn(__fadd_rn(q, __fmul_rn(e, e)));
+        };
+        ts0 = leg(qlo, hs0, box.ivlo);
+        ts1 = leg(qhi, hs1, box.ivhi);
+        tr0 = leg(qlo, hr0, box.ivlo);
+        tr1 = leg(qhi, hr1, box.ivhi);
+    } else {
+        leg_bounds(hs0, hs1, box.zlo, box.zhi, vel, v0, kf, ts0, ts1);
+        leg_bounds(hr0, hr1, box.zlo, box.zhi, vel, v0, kf, tr0, tr1);
+    }
+    const float tlo = __fmul_rn(__fsub_rn(__fadd_rn(ts0, tr0), g.t0), inv_dt);
+    const float thi = __fmul_rn(__fsub_rn(__fadd_rn(ts1, tr1), g.t0), inv_dt);
+    const float slo = __fadd_rn(__fadd_rn(2.f, __fmul_rn(2e-4f, fabsf(tlo))), g.tslack);
+    const float shi = __fadd_rn(__fadd_rn(2.f, __fmul_rn(2e-4f, fabsf(thi))), g.tslack);
     const float flo = floorf(tlo - slo), fhi = ceilf(thi + shi) + 1.f;
     if (!(fhi >= 1.f && flo <= (float)(g.nt - 2))) return false;   // also NaN
     lo = flo < 0.f ? 0 : (int)flo;
@@ -214,9 +238,15 @@ __device__ __forceinline__ TileBox tile_box(const GeomParams& g, int x0, int y0,
     box.yhi = fmaxf(ya, yb);
     box.zlo = fminf(za, zb);
     box.zhi = fmaxf(za, zb);
-    box.cx = g.ox + 0.5 * (x0 + xe) * g.dx;
-    box.cy = g.dim == 3 ? g.oy + 0.5 * (y0 + ye) * g.dy : 0.0;
-    box.cz = g.oz + 0.5 * (z0 + ze) * g.dz;
+    box.cx = __dadd_rn(g.ox, __dmul_rn(0.5 * (x0 + xe), g.dx));
+    box.cy = g.dim == 3 ? __dadd_rn(g.oy, __dmul_rn(0.5 * (y0 + ye), g.dy)) : 0.0;
+    box.cz = __dadd_rn(g.oz, __dmul_rn(0.5 * (z0 + ze), g.dz));
+    box.ivlo = box.ivhi = 0.f;
+    if (g.pstm) {   // v_rms is monotone in t0: its extremes over the tile are at the ends
+        const double va = sqrt(vrms2_of(g.v0, g.pk, box.zlo)), vb = sqrt(vrms2_of(g.v0, g.pk, box.zhi));
+        box.ivlo = (float)(1.0 / fmax(va, vb)) * (1.f - 1e-6f);
+        box.ivhi = (float)(1.0 / fmin(va, vb)) * (1.f + 1e-6f);
+    }
     return box;
 }
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libkirchhoff.so")
 KH_OK, KH_ERR_INVALID_ARG, KH_ERR_UNSUPPORTED, KH_ERR_OOM, KH_ERR_CUDA, KH_ERR_TIMEOUT, \
     KH_ERR_INTERNAL = range(7)
 KH_F32, KH_F16, KH_BF16, KH_U16 = 0, 1, 2, 3
-KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE = 0, 1, 2
+KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE, KH_VEL_PSTM = 0, 1, 2, 3
 KH_W_ONE, KH_W_OBLIQ_SPREAD = 0, 1
 KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE, KH_OPT_BATCH_MODE, KH_OPT_SAMPLE_PAIRS = 1, 2, 3, 4, 5
 KH_OPT_SPATIAL_SORT = 6
@@ -178,7 +178,8 @@ def desc_from(s, trace_dtype=torch.float32, vel=None, table_spacing=None,
     ``s.vel == "table"`` selects the radial traveltime table of the v0 + k z model;
     ``table_dtype`` is "f32", "f16" or "u16" (or torch.float32 / torch.float16)."""
     if vel is None:
-        vel = {"const": KH_VEL_CONST, "linear": KH_VEL_LINEAR_Z, "table": KH_VEL_TABLE}[s.vel]
+        vel = {"const": KH_VEL_CONST, "linear": KH_VEL_LINEAR_Z, "table": KH_VEL_TABLE,
+               "pstm": KH_VEL_PSTM}[s.vel]
     if table_spacing is None:
         table_spacing = float(getattr(s, "table_spacing", 25.0))
     return kh_desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,

@@ -729,8 +729,8 @@ def _form(line):
 def run_forms(args, s, ws, rank, local, dev, cache, head):
     """The metric's other forms on the same GPU, each timed on its own: mixed precision (16-bit
     traces and traveltime table) on the headline survey, the adjoint and the (v0, k) gradient on
-    the headline survey, and the 64-job batch as one graph replay against a loop of per-job calls
-    (FP32 and FP16 traces)."""
+    the headline survey, prestack time migration of the same traces, and the 64-job batch as one
+    graph replay against a loop of per-job calls (FP32 and FP16 traces)."""
     k = dict(steps=args.form_steps, warmup=3, e2e=False, cpu=False)
     forms = {}
     mixed = run_single(args, s, ws, rank, local, dev, cache, trace_dtype="f16", vel="table",
@@ -742,6 +742,13 @@ def run_forms(args, s, ws, rank, local, dev, cache, head):
         r = run_single(args, s, ws, rank, local, dev, cache, op=op, **k)
         if rank == 0:
             forms[op] = _form(r)
+    # prestack time migration of the same traces on a two-way-time axis (256 samples of 12 ms):
+    # the same (column, trace) pairs, so the same contribution count
+    s_t = s.replace(vel="pstm", oz=0.0, dz=0.012, name="3d-pstm-100000tr-256x256x256t")
+    tcache = {key: cache[key] for key in ("hdr", "traces", "count", "traces64") if key in cache}
+    r = run_single(args, s_t, ws, rank, local, dev, tcache, **k)
+    if rank == 0:
+        forms["time_migration"] = _form(r)
     cache.clear()
     torch.cuda.empty_cache()
     surveys = workloads()["batch64-3d-vz"]()

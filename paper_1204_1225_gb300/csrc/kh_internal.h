@@ -51,7 +51,7 @@ constexpr int PAIR_MAX_NT = 2460;
 // Default wait limit: polls of mbarrier.try_wait, each checked against a 2 s wall clock.
 constexpr long long WAIT_NS = 2000000000LL;
 
-enum VelKind { VK_CONST = 0, VK_LINEAR = 1, VK_TABLE = 2 };
+enum VelKind { VK_CONST = 0, VK_LINEAR = 1, VK_TABLE = 2, VK_PSTM = 3 };
 
 // RMS velocity of v(z) = v0 + k z down to the two-way vertical time t0: v0^2 (e^{k t0} - 1)/(k t0)
 // (v(tau) = v0 e^{k tau} at one-way vertical time tau; the mean of v^2 over [0, t0/2]).
@@ -115,10 +115,10 @@ struct GeomParams {
                              // tau_ref = -t0/dt) or ln(U/U_c) (linear v); C1lo = FP32 rounding
                              // error of C1
     double c0;               // -t0/dt - 1/2 (the window origin is subtracted per trace)
-    // prestack time migration (KH_VEL_PSTM): the constant-velocity path with per-depth constants,
-    // the image's depth axis being the two-way vertical time t0; each leg is the straight ray of
-    // the RMS velocity v_rms(t0) of v(z) = v0 + pk z, T = sqrt(ze^2 + h^2) / v_rms with the
-    // equivalent depth ze = v_rms t0 / 2 (g.k is 0 so that every kernel takes that path)
+    // prestack time migration (KH_VEL_PSTM, the VK_PSTM kernels): the image's depth axis is the
+    // two-way vertical time t0; each leg is the straight ray of the RMS velocity v_rms(t0) of
+    // v(z) = v0 + pk z, T = sqrt(ze^2 + h^2) / v_rms with the equivalent depth ze = v_rms t0 / 2
+    // (g.k is 0: nothing of the linear-gradient evaluation applies)
     int pstm;
     double pk;
     // radial traveltime table (KH_VEL_TABLE)

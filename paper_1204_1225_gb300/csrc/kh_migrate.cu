@@ -52,6 +52,7 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
                            const WaitCfg& w, cudaStream_t s)
 {
     if (t.cz > MAX_ZG) return cudaErrorInvalidValue;
+    if (g.pstm) vel_kind = VK_PSTM;   // time migration has kernels of its own
     switch (g.tdtype) {
         case KH_F32:
             return g.pairs ? launch_migrate_pair(g, t, tr, traces, image, vel_kind, fast_math, w, s)

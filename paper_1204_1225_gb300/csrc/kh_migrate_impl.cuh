@@ -98,7 +98,7 @@ __host__ __device__ inline size_t src_cache_bytes(const GeomParams& g)
     // gradient: the thread's weighted image values, and for linear v(z) (C1 ln(1 + rho_s), (q/w)_s)
     // and sqrt(q_s)
     if (g.grad) return (size_t)NZ * CONSUMERS * (g.kabs > 0.0 ? sizeof(float2) + 2 * sizeof(float) : sizeof(float));
-    return g.kabs > 0.0 ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
+    return (g.kabs > 0.0 || g.pstm) ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
 }
 
 // Elements of one stage's sample area: a full trace always fits, so every trace is stageable.
@@ -305,6 +305,8 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
 {
     const int lane = threadIdx.x & 31;
     const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
+    PstmTile pt{};
+    if constexpr (VEL == VK_PSTM) pt = pstm_tile(g, box);
     int cur = tr.bin_start[bin], te = tr.bin_start[bin + 1];
     if (tr.cell_start) {   // the first non-empty cell row of the tile
         tile_rows(S.row, S.rng, tr, bin);
@@ -342,7 +344,7 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 }
                 if (ok) {
                     ok = trace_window(h, box, VEL == VK_TABLE ? (g.k == 0.0 ? VK_CONST : VK_LINEAR) : VEL,
-                                      g, lo, hi, &clipped);
+                                      g, lo, hi, &clipped, &pt);
                     lo_al = lo & ~(g.elem_align - 1);
                     len_al = (hi + 1 - lo_al + g.elem_align - 1) & ~(g.elem_align - 1);
                 }
@@ -381,6 +383,18 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                     // (R_c^2, (q_c + 2)/u_c, w_c, 1/u_c) per leg
                     S.refs[s][slot] = make_float4(rs.Rc2, qis, rs.wc, rs.iuc);
                     S.refr[s][slot] = make_float4(rr.Rc2, qir, rr.wc, rr.iuc);
+                    S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
+                                                 (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
+                } else if constexpr (VEL == VK_PSTM) {
+                    // FP64 legs at the tile centre (x_c, t0_c): R_ac = sqrt(|c - a|^2 + ze_c^2) on the
+                    // straight rays of the RMS medium, and tau_c = C1(t0_c) (R_sc + R_rc) - t0/dt
+                    const double esx = __dadd_rn(box.cx, -(double)h.x), esy = __dadd_rn(box.cy, -(double)h.y);
+                    const double erx = __dadd_rn(box.cx, -(double)h.z), ery = __dadd_rn(box.cy, -(double)h.w);
+                    const double rsc = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(esx, esx), __dmul_rn(esy, esy)), pt.pze2));
+                    const double rrc = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(erx, erx), __dmul_rn(ery, ery)), pt.pze2));
+                    const double sc = __dadd_rn(rsc, rrc);
+                    tau_ref = __dadd_rn(tau_ref, __dmul_rn(pt.pc1, sc));
+                    S.refs[s][slot] = make_float4((float)rsc, (float)rrc, (float)sc, 0.f);
                     S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
                                                  (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
                 }
@@ -565,6 +579,50 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 };
                 if (unchecked) zloop(std::false_type());
                 else zloop(std::true_type());
+            } else if constexpr (VEL == VK_PSTM) {
+                // time migration relative to the tile centre: per leg R_a - R_ac = (q_a - q_ac) /
+                // (R_a + R_ac) with q_a - q_ac = dP_a + (ze^2 - ze_c^2), so that
+                // tau - lo = c0rel + (C1(t0) - C1(t0_c)) S_c + C1(t0) (dR_s + dR_r) carries only
+                // quantities of a few tens of samples; the source leg (dR_s, R_s) is cached per
+                // source position like the linear path's
+                const float4 a = S.hda[s][t];
+                const float4 rf = S.refs[s][t];   // (R_sc, R_rc, S_c, -)
+                if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
+                    const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
+                    const float exs = cxf - h.x, eys = cyf - h.y;
+                    const float dhs2 = fmaf(exs, exs, eys * eys);
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) {
+                        const float4 c = zc[i];   // (ze^2, ze^2 - ze_c^2, C1(t0), C1(t0) - C1(t0_c))
+                        const float R = hsqrt<FAST>(dhs2 + c.x);
+                        my_src[i * CONSUMERS] = make_float2((dPs + c.y) * hrcp<FAST>(R + rf.x), R);
+                    }
+                    psx = __float_as_uint(h.x);
+                    psy = __float_as_uint(h.y);
+                }
+                const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
+                const float exr = cxf - h.z, eyr = cyf - h.w;
+                const float dhr2 = fmaf(exr, exr, eyr * eyr);
+                auto zloop = [&](auto checked) {
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) {
+                        const float4 c = zc[i];
+                        const float2 sv = my_src[i * CONSUMERS];   // (dR_s, R_s)
+                        const float R = hsqrt<FAST>(dhr2 + c.x);
+                        const float dR = (dPr + c.y) * hrcp<FAST>(R + rf.y);
+                        const float th = fmaf(c.z, sv.x + dR, fmaf(c.w, rf.z, c0rel));
+                        float val;
+                        if constexpr (decltype(checked)::value)
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                        else
+                            val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        // W = w_z (R_s + R_r); w_z multiplies the sum once, at the store
+                        if constexpr (WGT == 1) acc[i] = fmaf(sv.y + R, val, acc[i]);
+                        else acc[i] += val;
+                    }
+                };
+                if (unchecked) zloop(std::false_type());
+                else zloop(std::true_type());
             } else if constexpr (VEL == VK_CONST) {
                 const float dxs = cxf - h.x, dys = cyf - h.y;
                 const float dxr = cxf - h.z, dyr = cyf - h.w;
@@ -573,9 +631,8 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 auto zloop = [&](auto checked) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
-                        const float4 c = zc[i];   // (z^2, w_z, C1, C1lo): per depth for time migration
-                        const float Ssum = hsqrt<FAST>(dhs2 + c.x) + hsqrt<FAST>(dhr2 + c.x);
-                        const float th = fmaf(Ssum, c.z, fmaf(Ssum, c.w, c0rel));
+                        const float Ssum = hsqrt<FAST>(dhs2 + zc[i].x) + hsqrt<FAST>(dhr2 + zc[i].x);
+                        const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
                             val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
@@ -642,7 +699,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     if constexpr (WGT == 1) {
 #pragma unroll
         for (int i = 0; i < NZ; ++i)
-            acc[i] *= VEL == VK_LINEAR ? zg[i] : (VEL == VK_TABLE ? zc[i].x : zc[i].y);
+            acc[i] *= (VEL == VK_LINEAR || VEL == VK_PSTM) ? zg[i] : (VEL == VK_TABLE ? zc[i].x : zc[i].y);
     }
     float* out = image + (((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb;
     const bool vec = ((g.nz & 3) == 0) && (izb + NZ <= g.nz) &&
@@ -838,18 +895,20 @@ __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, co
         } else if constexpr (VEL == VK_TABLE) {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
             S.zc[i] = make_float4(wz, (float)(z * z), 0.f, 0.f);
-        } else if (g.pstm) {
+        } else if constexpr (VEL == VK_PSTM) {
             // time migration: z is the two-way vertical time t0; the leg is the straight ray of
-            // the RMS velocity, R = sqrt(h^2 + ze^2) with ze = v_rms t0 / 2, and tau = (R_s + R_r)
-            // C1(t0) - t0/dt with C1(t0) = 1 / (v_rms dt), split into FP32 head and tail
+            // the RMS velocity, R = sqrt(h^2 + ze^2) with ze = v_rms t0 / 2, and
+            // tau = (R_s + R_r) C1(t0) - t0/dt with C1(t0) = 1 / (v_rms dt); stored relative to the
+            // tile centre: (ze^2, ze^2 - ze_c^2, C1(t0), C1(t0) - C1(t0_c)), and w_z = ze / (2 r0^2)
+            const PstmTile pt = pstm_tile(g, box);
             const double vr = sqrt(vrms2_of(g.v0, g.pk, z));
             const double ze = 0.5 * vr * z;
             const double c1 = 1.0 / (vr * g.dtd);
-            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(ze * g.wscale) : 0.f;
-            S.zc[i] = make_float4((float)(ze * ze), wz, (float)c1, (float)(c1 - (double)(float)c1));
+            S.zc[i] = make_float4((float)(ze * ze), (float)(ze * ze - pt.pze2), (float)c1, (float)(c1 - pt.pc1));
+            S.z2[i] = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(ze * g.wscale) : 0.f;
         } else {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-            S.zc[i] = make_float4((float)(z * z), wz, g.C1, g.C1lo);
+            S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
         }
     }
 }
@@ -981,6 +1040,10 @@ cudaError_t launch_migrate_dtype(const GeomParams& g, const TileShape& t, const 
         case 9: return launch_migrate_t<VK_TABLE, 0, true, TT>(g, t, tr, traces, image, w, s);
         case 10:
         case 11: return launch_migrate_t<VK_TABLE, 1, true, TT>(g, t, tr, traces, image, w, s);
+        case 12: return launch_migrate_t<VK_PSTM, 0, false, TT>(g, t, tr, traces, image, w, s);
+        case 13: return launch_migrate_t<VK_PSTM, 0, true, TT>(g, t, tr, traces, image, w, s);
+        case 14: return launch_migrate_t<VK_PSTM, 1, false, TT>(g, t, tr, traces, image, w, s);
+        case 15: return launch_migrate_t<VK_PSTM, 1, true, TT>(g, t, tr, traces, image, w, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,5 +1,5 @@
 // Migration kernel instantiations for FP32 traces staged as SamplePair rows (constant and
-// linear v(z); table migrations stage plain samples).
+// linear v(z), time migration; table migrations stage plain samples).
 #include "kh_migrate_impl.cuh"
 
 namespace kh {
@@ -16,6 +16,10 @@ cudaError_t launch_migrate_pair(const GeomParams& g, const TileShape& t, const T
         case 5: return launch_migrate_t<VK_LINEAR, 0, true, SamplePair>(g, t, tr, traces, image, w, s);
         case 6: return launch_migrate_t<VK_LINEAR, 1, false, SamplePair>(g, t, tr, traces, image, w, s);
         case 7: return launch_migrate_t<VK_LINEAR, 1, true, SamplePair>(g, t, tr, traces, image, w, s);
+        case 12: return launch_migrate_t<VK_PSTM, 0, false, SamplePair>(g, t, tr, traces, image, w, s);
+        case 13: return launch_migrate_t<VK_PSTM, 0, true, SamplePair>(g, t, tr, traces, image, w, s);
+        case 14: return launch_migrate_t<VK_PSTM, 1, false, SamplePair>(g, t, tr, traces, image, w, s);
+        case 15: return launch_migrate_t<VK_PSTM, 1, true, SamplePair>(g, t, tr, traces, image, w, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -161,7 +161,15 @@ __device__ __forceinline__ void rect_dist(float px, float py, float xlo, float x
 struct TileBox {
     float xlo, xhi, ylo, yhi, zlo, zhi;   // FP32 box of the valid samples (window bounds)
     double cx, cy, cz;                    // FP64 centre (linear-path reference point)
-    float ivlo, ivhi;                     // time migration: 1 / largest and 1 / smallest v_rms
+};
+
+// Time-migration constants of a tile: 1 / largest and 1 / smallest v_rms over its times (v_rms is
+// monotone in t0, so its extremes are at the ends), and at the centre time t0_c the equivalent
+// depth squared ze_c^2 and C1(t0_c) = 1 / (v_rms(t0_c) dt).  Only the time-migration kernels
+// compute them, so no other kernel carries them in registers.
+struct PstmTile {
+    float ivlo, ivhi;
+    double pze2, pc1;
 };
 
 // leg_delta_m plus q/w = sqrt(q / (q + 2)) for the velocity derivatives; sq = sqrt(q) always.
@@ -185,13 +193,14 @@ __device__ __forceinline__ float leg_delta_grad_m(float dP, float dh2, const flo
 // Sample window [lo, hi] of one trace over a tile box, from the time bounds of both legs with
 // a slack of 2 + 2e-4 |tau| samples for FP32 rounding; false if no valid sample can reach the box.
 __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box, int vel,
-                                             const GeomParams& g, int& lo, int& hi, bool* clipped = nullptr)
+                                             const GeomParams& g, int& lo, int& hi, bool* clipped = nullptr,
+                                             const PstmTile* pt = nullptr)
 {
     const float v0 = (float)g.v0, kf = (float)g.k, inv_dt = __fdiv_rn(1.f, g.dt);
     float hs0, hs1, hr0, hr1, ts0, ts1, tr0, tr1;
     rect_dist(h.x, h.y, box.xlo, box.xhi, box.ylo, box.yhi, hs0, hs1);
     rect_dist(h.z, h.w, box.xlo, box.xhi, box.ylo, box.yhi, hr0, hr1);
-    if (g.pstm) {
+    if (vel == VK_PSTM) {
         // time migration, T = sqrt((t0/2)^2 + h^2 / v_rms(t0)^2) over t0 in [zlo, zhi] (t0 >= 0):
         // each term is bounded on its own, v_rms being monotone in t0
         const float ulo = __fmul_rn(0.5f, box.zlo), uhi = __fmul_rn(0.5f, box.zhi);
@@ -200,10 +209,10 @@ __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box
             const float e = __fmul_rn(hh, iv);
             return __fsqrt_rn(__fadd_rn(q, __fmul_rn(e, e)));
         };
-        ts0 = leg(qlo, hs0, box.ivlo);
-        ts1 = leg(qhi, hs1, box.ivhi);
-        tr0 = leg(qlo, hr0, box.ivlo);
-        tr1 = leg(qhi, hr1, box.ivhi);
+        ts0 = leg(qlo, hs0, pt->ivlo);
+        ts1 = leg(qhi, hs1, pt->ivhi);
+        tr0 = leg(qlo, hr0, pt->ivlo);
+        tr1 = leg(qhi, hr1, pt->ivhi);
     } else {
         leg_bounds(hs0, hs1, box.zlo, box.zhi, vel, v0, kf, ts0, ts1);
         leg_bounds(hr0, hr1, box.zlo, box.zhi, vel, v0, kf, tr0, tr1);
@@ -241,13 +250,20 @@ __device__ __forceinline__ TileBox tile_box(const GeomParams& g, int x0, int y0,
     box.cx = __dadd_rn(g.ox, __dmul_rn(0.5 * (x0 + xe), g.dx));
     box.cy = g.dim == 3 ? __dadd_rn(g.oy, __dmul_rn(0.5 * (y0 + ye), g.dy)) : 0.0;
     box.cz = __dadd_rn(g.oz, __dmul_rn(0.5 * (z0 + ze), g.dz));
-    box.ivlo = box.ivhi = 0.f;
-    if (g.pstm) {   // v_rms is monotone in t0: its extremes over the tile are at the ends
-        const double va = sqrt(vrms2_of(g.v0, g.pk, box.zlo)), vb = sqrt(vrms2_of(g.v0, g.pk, box.zhi));
-        box.ivlo = (float)(1.0 / fmax(va, vb)) * (1.f - 1e-6f);
-        box.ivhi = (float)(1.0 / fmin(va, vb)) * (1.f + 1e-6f);
-    }
     return box;
+}
+
+__device__ __forceinline__ PstmTile pstm_tile(const GeomParams& g, const TileBox& box)
+{
+    PstmTile t;
+    const double vc = sqrt(vrms2_of(g.v0, g.pk, box.cz));
+    const double zec = 0.5 * vc * box.cz;
+    t.pze2 = zec * zec;
+    t.pc1 = 1.0 / (vc * g.dtd);
+    const double va = sqrt(vrms2_of(g.v0, g.pk, box.zlo)), vb = sqrt(vrms2_of(g.v0, g.pk, box.zhi));
+    t.ivlo = (float)(1.0 / fmax(va, vb)) * (1.f - 1e-6f);
+    t.ivhi = (float)(1.0 / fmin(va, vb)) * (1.f + 1e-6f);
+    return t;
 }
 
 }  // namespace kh

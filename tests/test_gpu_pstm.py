@@ -41,9 +41,14 @@ def test_constant_velocity_time_image_is_the_depth_image():
     s = sv.survey_random(rng, 3, 120, 24, 20, 48, 400, vel="pstm", weight="obliq", aperture=140.0,
                          n_bins=3, h=12.5, v0=2000.0, k=0.0).replace(oz=0.0, dz=0.0125)
     d = sv.random_traces(s, 3, smooth=5)
+    depth = s.replace(vel="const", dz=s.v0 * s.dz / 2)
     t_img, _ = gpu_migrate(s, d)
-    z_img, _ = gpu_migrate(s.replace(vel="const", dz=s.v0 * s.dz / 2), d)
-    assert rel_l2(t_img, z_img) < 2e-6
+    z_img, _ = gpu_migrate(depth, d)
+    # the two FP32 paths evaluate the legs differently (time migration relative to the tile
+    # centre); each agrees with the FP64 depth image of the oracle, and so with the other
+    want = oracle.migrate(depth, d)
+    assert rel_l2(t_img, want) < FP32_REL_L2 and rel_l2(z_img, want) < FP32_REL_L2
+    assert rel_l2(t_img, z_img) < FP32_REL_L2
 
 
 def test_diffractor_focuses_at_its_time():

@@ -112,6 +112,12 @@ typedef struct {
     int nt;                  /* samples per trace, >= 2 */
     double t0, dt;           /* time of sample 0 and sample interval, seconds */
     kh_dtype trace_dtype;    /* storage type of the traces passed to migrate */
+    double taper;            /* aperture taper: the weight falls from 1 to 0 over the outer fraction
+                                `taper` of the aperture as a raised cosine of the column-to-midpoint
+                                distance d, (1 + cos(pi (d - (1 - taper) A) / (taper A))) / 2 beyond
+                                (1 - taper) A; in [0, 1), 0 = a hard mask; ignored without an
+                                aperture.  Every operator (migrate, demigrate, velocity gradient)
+                                applies it, so they stay each other's transpose and derivative. */
 } kh_desc;
 
 typedef struct kh_plan_s* kh_plan;

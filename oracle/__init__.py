@@ -45,7 +45,7 @@ class _Desc(ctypes.Structure):
                 ("bin_width", ctypes.c_double), ("vel", ctypes.c_int), ("v0", ctypes.c_double),
                 ("k", ctypes.c_double), ("weight", ctypes.c_int), ("r0", ctypes.c_double),
                 ("aperture", ctypes.c_double), ("nt", ctypes.c_int), ("t0", ctypes.c_double),
-                ("dt", ctypes.c_double), ("table_spacing", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("table_spacing", ctypes.c_double), ("taper", ctypes.c_double)]
 
 
 def lib():
@@ -79,7 +79,7 @@ def desc(s) -> _Desc:
     return _Desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
                  s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1, "table": 2, "pstm": 3}[s.vel], s.v0, s.k,
                  {"one": 0, "obliq": 1}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt,
-                 float(getattr(s, "table_spacing", 25.0)))
+                 float(getattr(s, "table_spacing", 25.0)), float(getattr(s, "taper", 0.0)))
 
 
 def _ptr(a):

@@ -47,6 +47,7 @@ typedef struct {
     int nt;
     double t0, dt;
     double table_spacing;    /* vel 2: node spacing of the radial traveltime table */
+    double taper;            /* fraction of the aperture over which the weight tapers to 0 */
 } ko_desc;
 
 /* Deliberate-mistake switch used only by the tests that show the pins catch errors.
@@ -251,6 +252,23 @@ static int inside_aperture(const ko_desc* d, float cx, float cy, float sx, float
     return d2 <= a2;
 }
 
+/* Aperture taper: the weight falls from 1 to 0 over the outer fraction f of the aperture as a
+ * raised cosine of the horizontal distance d from the column to the trace midpoint:
+ *   1 for d <= (1 - f) A,  (1 + cos(pi (d - (1 - f) A) / (f A))) / 2 for (1 - f) A < d <= A.
+ * d is taken in FP64 from the FP32 column and midpoint coordinates of the aperture test. */
+static double aperture_taper(const ko_desc* d, float cx, float cy, float sx, float sy, float rx, float ry)
+{
+    if (d->aperture <= 0.0 || d->taper <= 0.0) return 1.0;
+    const double mx = (double)((sx + rx) * 0.5f), my = (double)((sy + ry) * 0.5f);
+    const double ex = (double)cx - mx, ey = (double)cy - my;
+    const double dist = sqrt(ex * ex + ey * ey);
+    const double core = (1.0 - d->taper) * d->aperture;
+    if (dist <= core) return 1.0;
+    double x = (dist - core) / (d->taper * d->aperture);
+    if (ko_mutation == 13) x = 1.0 - x;   /* taper reversed */
+    return 0.5 * (1.0 + cos(3.14159265358979323846 * x));
+}
+
 /* ---- the contribution of one trace to one image point ---- */
 typedef struct {
     int valid;      /* 0 <= tau <= nt-1 */
@@ -334,6 +352,7 @@ int ko_migrate(const ko_desc* d, long ntr, const float* sx, const float* sy, con
             float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
             if (d->dim == 2) { fsy = 0.f; fry = 0.f; }
             if (!inside_aperture(d, cx, cy, fsx, fsy, frx, fry)) continue;
+            const double tp = aperture_taper(d, cx, cy, fsx, fsy, frx, fry);
             const double* D = traces + j * nt;
             double* out = image + ((long)bin[j] * ncol + c) * nz;
             for (long iz = 0; iz < nz; ++iz) {
@@ -341,7 +360,7 @@ int ko_migrate(const ko_desc* d, long ntr, const float* sx, const float* sy, con
                 contrib q = contribution(d, x, y, z, fsx, fsy, frx, fry, 0);
                 if (!q.valid) continue;
                 double val = (1.0 - q.f) * D[q.i] + q.f * D[q.i + 1];
-                out[iz] += q.W * val;
+                out[iz] += tp * q.W * val;
             }
         }
     }
@@ -379,7 +398,7 @@ int ko_migrate_points(const ko_desc* d, long ntr, const float* sx, const float* 
             contrib w = contribution(d, x, y, z, fsx, fsy, frx, fry, 0);
             if (!w.valid) continue;
             const double* D = traces + j * nt;
-            acc += w.W * ((1.0 - w.f) * D[w.i] + w.f * D[w.i + 1]);
+            acc += aperture_taper(d, cx, cy, fsx, fsy, frx, fry) * w.W * ((1.0 - w.f) * D[w.i] + w.f * D[w.i + 1]);
         }
         out[p] = acc;
     }
@@ -409,14 +428,15 @@ int ko_demigrate(const ko_desc* d, long ntr, const float* sx, const float* sy, c
             int iy = (int)(c / d->nx), ix = (int)(c % d->nx);
             float cx = col_coord(d->ox, ix, d->dx), cy = (d->dim == 3) ? col_coord(d->oy, iy, d->dy) : 0.f;
             if (!inside_aperture(d, cx, cy, fsx, fsy, frx, fry)) continue;
+            const double tp = aperture_taper(d, cx, cy, fsx, fsy, frx, fry);
             double x = d->ox + ix * d->dx, y = (d->dim == 3) ? d->oy + iy * d->dy : 0.0;
             const double* m = image + ((long)bin[j] * ncol + c) * nz;
             for (long iz = 0; iz < nz; ++iz) {
                 double z = d->oz + iz * d->dz;
                 contrib q = contribution(d, x, y, z, fsx, fsy, frx, fry, 0);
                 if (!q.valid) continue;
-                D[q.i] += q.W * (1.0 - q.f) * m[iz];
-                D[q.i + 1] += q.W * q.f * m[iz];
+                D[q.i] += tp * q.W * (1.0 - q.f) * m[iz];
+                D[q.i + 1] += tp * q.W * q.f * m[iz];
             }
         }
     }
@@ -448,12 +468,14 @@ int ko_vgrad(const ko_desc* d, long ntr, const float* sx, const float* sy, const
             float fsx = sx[j], fsy = hdr(sy, j), frx = rx[j], fry = hdr(ry, j);
             if (d->dim == 2) { fsy = 0.f; fry = 0.f; }
             if (!inside_aperture(d, cx, cy, fsx, fsy, frx, fry)) continue;
+            const double tp = aperture_taper(d, cx, cy, fsx, fsy, frx, fry);
             const double* D = traces + j * nt;
             const double* m = image + ((long)bin[j] * ncol + c) * nz;
             for (long iz = 0; iz < nz; ++iz) {
                 double z = d->oz + iz * d->dz;
                 contrib q = contribution(d, x, y, z, fsx, fsy, frx, fry, 1);
                 if (!q.valid) continue;
+                q.W *= tp;
                 double slope = D[q.i + 1] - D[q.i];
                 gv += q.W * m[iz] * slope * q.dtau_dv0;
                 gk += q.W * m[iz] * slope * q.dtau_dk;

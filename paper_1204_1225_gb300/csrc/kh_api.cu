@@ -293,6 +293,7 @@ static kh_status validate_desc(const kh_desc* d)
             return fail(KH_ERR_INVALID_ARG, "table_dtype must be KH_F32, KH_F16 or KH_U16");
     }
     if (d->trace_dtype == KH_U16) return fail(KH_ERR_INVALID_ARG, "traces cannot be KH_U16");
+    if (!(d->taper >= 0.0 && d->taper < 1.0)) return fail(KH_ERR_INVALID_ARG, "taper must be in [0, 1)");
     const int ealign = 16 / dtype_size(d->trace_dtype);
     const int cap = std::max((d->nt + 3 * ealign) / ealign * ealign, 16384 / 4);
     if ((size_t)kh::STAGES * cap * dtype_size(d->trace_dtype) > 160u * 1024u)
@@ -335,6 +336,10 @@ static GeomParams geom_of(const kh_desc& d)
     g.wscale = 1.0 / (2.0 * d.r0 * d.r0);
     g.use_aperture = d.aperture > 0 ? 1 : 0;
     g.A2 = (float)(d.aperture * d.aperture);
+    g.use_taper = (d.aperture > 0 && d.taper > 0) ? 1 : 0;
+    g.ap_core = g.use_taper ? (float)((1.0 - d.taper) * d.aperture) : 0.f;
+    g.ap_core2 = g.use_taper ? (float)((1.0 - d.taper) * d.aperture * (1.0 - d.taper) * d.aperture) : 0.f;
+    g.ap_invband = g.use_taper ? (float)(1.0 / (d.taper * d.aperture)) : 0.f;
     g.A2cull = (float)((d.aperture * (1.0 + 1e-5) + 1.0) * (d.aperture * (1.0 + 1e-5) + 1.0));
     g.nt = d.nt;
     g.esize = dtype_size(d.trace_dtype);

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                 const float cxf = col_coord(g.ox, ix, g.dx);
                 const float cyf = (g.dim == 3) ? col_coord(g.oy, iy, g.dy) : 0.f;
                 if (inside && g.use_aperture) inside = in_aperture(cxf, cyf, mid.x, mid.y, g.A2);
+                const float tp = (inside && g.use_taper) ? aperture_taper(cxf, cyf, mid.x, mid.y, g) : 1.f;
                 const float chc = inside ? chalf : -1.f;
                 const float* mcol = &S.mt[c * dt.tz];
                 if constexpr (VEL == VK_CONST) {
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                         const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
                         const bool v = fabsf(th - cmid) <= chc;
                         const float W = (WGT == 1) ? zc.y * Ssum : 1.f;
-                        const float wm = v ? W * mcol[iz] : 0.f;
+                        const float wm = v ? tp * W * mcol[iz] : 0.f;
                         const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                         const float a1 = wm * f;
                         col0[row * 32] += wm - a1;
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                                 const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
                                 const bool v = fabsf(th - cmid) <= chc;
                                 const float W = (WGT == 1) ? S.z2[iz] * (sv.y + sqr) : 1.f;
-                                const float wm = v ? W * mcol[iz] : 0.f;
+                                const float wm = v ? tp * W * mcol[iz] : 0.f;
                                 const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                                 const float a1 = wm * f;
                                 col0[row * 32] += wm - a1;
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                             const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
                             const bool v = fabsf(th - cmid) <= chc;
                             const float W = (WGT == 1) ? S.z2[iz] * (sqs + sqr) : 1.f;
-                            const float wm = v ? W * mcol[iz] : 0.f;
+                            const float wm = v ? tp * W * mcol[iz] : 0.f;
                             const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                             const float a1 = wm * f;
                             col0[row * 32] += wm - a1;

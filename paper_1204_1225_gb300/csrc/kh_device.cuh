@@ -186,6 +186,18 @@ __device__ __forceinline__ bool in_aperture(float cx, float cy, float mx, float 
     return __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= A2;
 }
 
+// Aperture taper of a column inside the aperture: 1 within the core radius, then a raised cosine
+// of the horizontal distance d to the trace midpoint, (1 + cos(pi (d - core) / band)) / 2, down
+// to 0 at the aperture.
+__device__ __forceinline__ float aperture_taper(float cx, float cy, float mx, float my, const GeomParams& g)
+{
+    const float ex = __fsub_rn(cx, mx), ey = __fsub_rn(cy, my);
+    const float d2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
+    if (d2 <= g.ap_core2) return 1.f;
+    const float x = fminf(__fmul_rn(__fsub_rn(sqrtf(d2), g.ap_core), g.ap_invband), 1.f);
+    return 0.5f + 0.5f * cospif(x);
+}
+
 // Offset bin in FP64 (uniform bins; X == n_bins * w goes to the last bin; beyond: -1).
 __device__ __forceinline__ int offset_bin(float sx, float sy, float rx, float ry, int n_bins,
                                           double w)

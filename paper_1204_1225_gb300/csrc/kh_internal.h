@@ -140,6 +140,9 @@ struct GeomParams {
     // aperture
     int use_aperture;
     float A2;                // (float)(A*A), the exact test
+    int use_taper;           // the weight tapers over the outer part of the aperture
+    float ap_core, ap_core2; // radius (and its square) up to which the taper is 1
+    float ap_invband;        // 1 / width of the taper band
     float A2cull;            // enlarged, for the conservative tile cull
     // traces
     int nt;

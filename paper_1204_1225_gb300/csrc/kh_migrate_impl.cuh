@@ -407,7 +407,7 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 if (g.use_aperture) {
                     const float ex = fmaxf(fabsf(__fsub_rn(box.xlo, m.x)), fabsf(__fsub_rn(box.xhi, m.x)));
                     const float ey = fmaxf(fabsf(__fsub_rn(box.ylo, m.y)), fabsf(__fsub_rn(box.yhi, m.y)));
-                    whole = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= g.A2;
+                    whole = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= (g.use_taper ? g.ap_core2 : g.A2);
                 }
                 const float lim = (float)(hi - lo);
                 // w: c_half, its sign bit set when the window was not clipped at 0 or nt - 1 (then
@@ -527,18 +527,21 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
         for (int t = 0; t < cnt; ++t) {
             const int4 w = S.win[s][t];
             bool inside = col_ok;
-            if (g.use_aperture && w.z >= 0) {   // sign bit of w.z: every column is inside
+            float tp = 1.f;   // aperture taper of this column (1 in the taper's core)
+            if (g.use_aperture && w.z >= 0) {   // sign bit of w.z: every column is inside (its core)
                 const float2 m = S.mid[s][t];
                 inside = inside && in_aperture(cxf, cyf, m.x, m.y, g.A2);
+                if (g.use_taper && inside) tp = aperture_taper(cxf, cyf, m.x, m.y, g);
             }
             if (!__any_sync(0xffffffffu, inside)) continue;
             const float c0rel = __int_as_float(w.x);
             const float cmid = __int_as_float(w.z & 0x7fffffff);
             const float chalf = inside ? __int_as_float(w.w & 0x7fffffff) : -1.f;
             const float4 h = S.hdr[s][t];
-            // unclipped window, and every lane inside the aperture with all 16 depths in the
-            // grid: every tau is inside the window, no validity test is needed
-            const bool unchecked = w.w < 0 && __all_sync(0xffffffffu, inside && zfull);
+            // unclipped window, and every lane inside the aperture (its untapered core, with a
+            // taper) with all 16 depths in the grid: every tau is inside the window, no validity
+            // test and no taper are needed
+            const bool unchecked = w.w < 0 && (!g.use_taper || w.z < 0) && __all_sync(0xffffffffu, inside && zfull);
             if constexpr (VEL == VK_TABLE) {
                 // T_s + T_r in table units from the radial table; the source leg T_s is cached
                 // per source position like the linear path's
@@ -566,7 +569,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         const float th = fmaf(my_ts[i * CONSUMERS] + tab_depth<M>(pr, i), g.C1, c0rel);
                         float val;
                         if constexpr (decltype(checked)::value)
-                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                            val = tp * sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         // w_z multiplies the sum once, at the store
@@ -613,7 +616,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         const float th = fmaf(c.z, sv.x + dR, fmaf(c.w, rf.z, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
-                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                            val = tp * sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         // W = w_z (R_s + R_r); w_z multiplies the sum once, at the store
@@ -635,7 +638,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
-                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                            val = tp * sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         // w_z multiplies the sum once, at the store
@@ -674,7 +677,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         const float th = leg_log<LPT>(rho_r, g, c0rel + sv.x);
                         float val;
                         if constexpr (decltype(checked)::value)
-                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                            val = tp * sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         // gamma(z) multiplies the sum once, at the store
@@ -782,9 +785,11 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
         for (int t = 0; t < cnt; ++t) {
             const int4 w = S.win[s][t];
             bool inside = col_ok;
-            if (g.use_aperture && w.z >= 0) {   // sign bit of w.z: every column is inside
+            float tp = 1.f;   // aperture taper of this column
+            if (g.use_aperture && w.z >= 0) {   // sign bit of w.z: every column is inside (its core)
                 const float2 m = S.mid[s][t];
                 inside = inside && in_aperture(cxf, cyf, m.x, m.y, g.A2);
+                if (g.use_taper && inside) tp = aperture_taper(cxf, cyf, m.x, m.y, g);
             }
             if (!__any_sync(0xffffffffu, inside)) continue;
             const float c0rel = __int_as_float(w.x);
@@ -856,8 +861,8 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
                     g1 = fmaf(wms, dTk, g1);
                 }
             }
-            G0 += (double)g0;
-            G1 += (double)g1;
+            G0 += (double)(g0 * tp);
+            G1 += (double)(g1 * tp);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[s]);

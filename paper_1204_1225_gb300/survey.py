@@ -28,7 +28,9 @@ class Survey:
     ``vel`` is ``"const"``, ``"linear"`` (v(z) = v0 + k z, z from the surface) or ``"table"``
     (the same v0 + k z model read from a radial traveltime table with node spacing
     ``table_spacing``);
-    ``weight`` is ``"one"`` or ``"obliq"``; ``aperture <= 0`` means full aperture.
+    ``weight`` is ``"one"`` or ``"obliq"``; ``aperture <= 0`` means full aperture; ``taper`` is the
+    fraction of the aperture over which the weight falls to 0 (raised cosine; 0: a hard mask);
+    ``vel == "pstm"`` reads the depth axis as two-way vertical time (time migration).
     """
 
     dim: int
@@ -58,6 +60,7 @@ class Survey:
     ry: np.ndarray
     name: str = ""
     table_spacing: float = 25.0
+    taper: float = 0.0
 
     @property
     def ntr(self) -> int:

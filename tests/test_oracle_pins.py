@@ -371,6 +371,36 @@ def check_aperture_count_row():
     assert oracle.count(s) == 6 * s.nz
 
 
+def check_taper_hand_values():
+    # one column at x = 0, A = 300 m, taper 0.5 (core 150 m); a trace whose midpoint is d from the
+    # column carries the constant 1, so the image is the taper factor: 1 in the core, then
+    # (1 + cos(pi (d - 150) / 150)) / 2
+    for dist, want in ((100.0, 1.0), (150.0, 1.0), (187.5, 0.5 * (1 + math.cos(math.pi / 4))),
+                       (225.0, 0.5), (299.0, 0.5 * (1 + math.cos(math.pi * 149.0 / 150.0)))):
+        s = tiny_survey(aperture=300.0, taper=0.5, sx=[dist - 50.0], rx=[dist + 50.0])
+        img = oracle.migrate(s, np.ones((1, s.nt)))[0, 0, 0, 0]
+        assert abs(img - want) < 1e-12, (dist, img, want)
+
+
+def check_taper_keeps_operators_paired():
+    s = small3d(aperture=180.0).replace(taper=0.4)
+    d = sv.random_traces(s, 7).astype(np.float64)
+    m = sv.random_image(s, 8).astype(np.float64)
+    lhs = float(np.vdot(oracle.migrate(s, d), m))
+    rhs = float(np.vdot(d, oracle.demigrate(s, m)))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+    # the taper changes the image only where some midpoint lies in the taper band
+    assert rel(oracle.migrate(s, d), oracle.migrate(s.replace(taper=0.0), d)) > 1e-3
+
+
+def test_aperture_taper_hand_values():
+    check_taper_hand_values()
+
+
+def test_aperture_taper_keeps_operators_paired():
+    check_taper_keeps_operators_paired()
+
+
 def test_aperture_hand_geometry():
     check_aperture_hand_geometry()
 
@@ -396,6 +426,7 @@ MUTATIONS = [
     (9, check_aperture_hand_geometry), # midpoint without its 1/2
     (9, check_aperture_count_row),
     (10, check_aperture_hand_geometry),  # depth term in the aperture distance
+    (13, check_taper_hand_values),     # taper reversed across its band
 ]
 
 

@@ -563,15 +563,16 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
                 float pr[K];
                 tab_profile<TB, K, FAST>(tab, g, dhr2, jb, pr);
-                auto zloop = [&](auto checked) {
+                auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         const float th = fmaf(my_ts[i * CONSUMERS] + tab_depth<M>(pr, i), g.C1, c0rel);
                         float val;
                         if constexpr (decltype(checked)::value)
-                            val = tp * sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        if constexpr (decltype(tapered)::value) val *= tp;
                         // w_z multiplies the sum once, at the store
                         if constexpr (WGT == 1) {
                             const float Rsum = hsqrt<FAST>(dhs2 + zc[i].y) + hsqrt<FAST>(dhr2 + zc[i].y);
@@ -580,8 +581,9 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         else acc[i] += val;
                     }
                 };
-                if (unchecked) zloop(std::false_type());
-                else zloop(std::true_type());
+                if (unchecked) zloop(std::false_type(), std::false_type());
+                else if (g.use_taper) zloop(std::true_type(), std::true_type());
+                else zloop(std::true_type(), std::false_type());
             } else if constexpr (VEL == VK_PSTM) {
                 // time migration relative to the tile centre: per leg R_a - R_ac = (q_a - q_ac) /
                 // (R_a + R_ac) with q_a - q_ac = dP_a + (ze^2 - ze_c^2), so that
@@ -606,7 +608,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
                 const float exr = cxf - h.z, eyr = cyf - h.w;
                 const float dhr2 = fmaf(exr, exr, eyr * eyr);
-                auto zloop = [&](auto checked) {
+                auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         const float4 c = zc[i];
@@ -616,38 +618,42 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         const float th = fmaf(c.z, sv.x + dR, fmaf(c.w, rf.z, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
-                            val = tp * sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        if constexpr (decltype(tapered)::value) val *= tp;
                         // W = w_z (R_s + R_r); w_z multiplies the sum once, at the store
                         if constexpr (WGT == 1) acc[i] = fmaf(sv.y + R, val, acc[i]);
                         else acc[i] += val;
                     }
                 };
-                if (unchecked) zloop(std::false_type());
-                else zloop(std::true_type());
+                if (unchecked) zloop(std::false_type(), std::false_type());
+                else if (g.use_taper) zloop(std::true_type(), std::true_type());
+                else zloop(std::true_type(), std::false_type());
             } else if constexpr (VEL == VK_CONST) {
                 const float dxs = cxf - h.x, dys = cyf - h.y;
                 const float dxr = cxf - h.z, dyr = cyf - h.w;
                 const float dhs2 = fmaf(dxs, dxs, dys * dys);
                 const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
-                auto zloop = [&](auto checked) {
+                auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         const float Ssum = hsqrt<FAST>(dhs2 + zc[i].x) + hsqrt<FAST>(dhr2 + zc[i].x);
                         const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
-                            val = tp * sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        if constexpr (decltype(tapered)::value) val *= tp;
                         // w_z multiplies the sum once, at the store
                         if constexpr (WGT == 1) acc[i] = fmaf(Ssum, val, acc[i]);
                         else acc[i] += val;
                     }
                 };
-                if (unchecked) zloop(std::false_type());
-                else zloop(std::true_type());
+                if (unchecked) zloop(std::false_type(), std::false_type());
+                else if (g.use_taper) zloop(std::true_type(), std::true_type());
+                else zloop(std::true_type(), std::false_type());
             } else {
                 const float4 a = S.hda[s][t];
                 if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
@@ -668,7 +674,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
                 const float exr = cxf - h.z, eyr = cyf - h.w;
                 const float dhr2 = fmaf(exr, exr, eyr * eyr);
-                auto zloop = [&](auto checked) {
+                auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         float sqr = 0.f;
@@ -677,16 +683,18 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         const float th = leg_log<LPT>(rho_r, g, c0rel + sv.x);
                         float val;
                         if constexpr (decltype(checked)::value)
-                            val = tp * sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        if constexpr (decltype(tapered)::value) val *= tp;
                         // gamma(z) multiplies the sum once, at the store
                         if constexpr (WGT == 1) acc[i] = fmaf(sv.y + sqr, val, acc[i]);
                         else acc[i] += val;
                     }
                 };
-                if (unchecked) zloop(std::false_type());
-                else zloop(std::true_type());
+                if (unchecked) zloop(std::false_type(), std::false_type());
+                else if (g.use_taper) zloop(std::true_type(), std::true_type());
+                else zloop(std::true_type(), std::false_type());
             }
         }
         __syncwarp();

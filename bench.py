@@ -505,10 +505,11 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
     clk_mhz = clocks.get("sm_mhz") or 2070.0
     achieved = contrib / (kern_ms / max(kern_n, 1) / 1e3) / 1e9 if kern_n else None
     kname = {"migrate": "k_migrate", "demigrate": "k_demigrate", "vgrad": "k_vgrad"}[op]
+    workload = args.workload.replace("3d-vz", "3d-pstm") if s.vel == "pstm" else args.workload
     if vel == "table":
-        mix_key = f"{args.workload}-table-{table_dtype}-{trace_dtype}"
+        mix_key = f"{workload}-table-{table_dtype}-{trace_dtype}"
     elif trace_dtype == "f32":
-        mix_key = args.workload if op == "migrate" else f"{args.workload}-{op}"
+        mix_key = workload if op == "migrate" else f"{workload}-{op}"
     else:
         mix_key = None
     if args.aperture is not None or not spatial_sort:

@@ -45,7 +45,10 @@ class _Desc(ctypes.Structure):
                 ("bin_width", ctypes.c_double), ("vel", ctypes.c_int), ("v0", ctypes.c_double),
                 ("k", ctypes.c_double), ("weight", ctypes.c_int), ("r0", ctypes.c_double),
                 ("aperture", ctypes.c_double), ("nt", ctypes.c_int), ("t0", ctypes.c_double),
-                ("dt", ctypes.c_double), ("table_spacing", ctypes.c_double), ("taper", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("table_spacing", ctypes.c_double), ("taper", ctypes.c_double),
+                ("gtab", ctypes.c_void_p), ("gloc", ctypes.c_void_p), ("gnloc", ctypes.c_int),
+                ("gnx", ctypes.c_int), ("gnz", ctypes.c_int), ("gox", ctypes.c_double),
+                ("gh", ctypes.c_double)]
 
 
 def lib():
@@ -68,6 +71,13 @@ def lib():
             _lib.ko_count.argtypes = [D, L, P, P, P, P]
             _lib.ko_arrivals.argtypes = [D, L, P, P, P, L, P, P, P, P, P]
             _lib.ko_count.restype = ctypes.c_longlong
+            I = ctypes.c_int
+            Dbl = ctypes.c_double
+            _lib.ko_eikonal.argtypes = [I, I, Dbl, Dbl, P, Dbl, I, Dbl, P]
+            _lib.ko_eikonal.restype = I
+            _lib.ko_grid_tables.argtypes = [I, I, Dbl, Dbl, P, I, P, I, Dbl, P, P]
+            _lib.ko_grid_tables.restype = I
+            _lib.ko_grid_traveltime.argtypes = [D, I, L, P, P, P]
             _lib.ko_set_mutation.argtypes = [ctypes.c_int]
             _lib.ko_set_threads.argtypes = [ctypes.c_int]
             _lib.ko_max_threads.restype = ctypes.c_int
@@ -75,11 +85,22 @@ def lib():
 
 
 def desc(s) -> _Desc:
-    """Oracle descriptor from a ``Survey`` (any object with the same attribute names)."""
-    return _Desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
-                 s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1, "table": 2, "pstm": 3}[s.vel], s.v0, s.k,
-                 {"one": 0, "obliq": 1}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt,
-                 float(getattr(s, "table_spacing", 25.0)), float(getattr(s, "taper", 0.0)))
+    """Oracle descriptor from a ``Survey`` (any object with the same attribute names).  For vel
+    "grid" it carries this oracle's FP64 eikonal tables of the survey's gridded model (built once
+    per model and location set, then cached) or the tables given as ``s.oracle_tables``."""
+    d = _Desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
+              s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1, "table": 2, "pstm": 3, "grid": 4}[s.vel],
+              s.v0, s.k, {"one": 0, "obliq": 1}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt,
+              float(getattr(s, "table_spacing", 25.0)), float(getattr(s, "taper", 0.0)))
+    if s.vel == "grid":
+        g = getattr(s, "oracle_tables", None)
+        if g is None:
+            g = grid_tables(s)
+        d.gtab, d.gloc = _ptr(g.T), _ptr(g.loc)
+        d.gnloc, d.gnx, d.gnz = g.loc.size, g.T.shape[1], g.T.shape[2]
+        d.gox, d.gh = g.ox, g.h
+        d._keep = g   # the arrays the pointers refer to
+    return d
 
 
 def _ptr(a):
@@ -202,6 +223,73 @@ def arrival_times(points, s, trace_idx) -> np.ndarray:
     lib().ko_arrivals(ctypes.byref(desc(s)), pts.shape[0], _ptr(px), _ptr(py), _ptr(pz), j.size,
                       _ptr(sx), _ptr(sy), _ptr(rx), _ptr(ry), _ptr(out))
     return out
+
+
+# ------------------------------------------------------------------ gridded model v(x, z)
+
+MAX_ROUNDS = 64
+# A round of sweeps whose largest decrease is at most this many seconds ends the iteration: the
+# remaining corrections shrink geometrically from round to round and are far below the
+# resolution of an FP32 table (about 1e-7 s at 1 s).
+TOL = 1e-9
+
+
+def eikonal(v, ox: float, h: float, xs: float, max_rounds: int = MAX_ROUNDS, tol: float = TOL):
+    """First-arrival times from the surface point (xs, 0) on the node grid (ox + i h, j h) of the
+    model v [nx, nz] (m/s): the factored fast-sweeping solution (kh_oracle.c, ko_eikonal).
+    Returns (T float64 [nx, nz], rounds; -1 if it did not settle within max_rounds)."""
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    T = np.empty(v.shape, dtype=np.float64)
+    r = lib().ko_eikonal(v.shape[0], v.shape[1], float(ox), float(h), _ptr(v), float(xs), int(max_rounds),
+                         float(tol), _ptr(T))
+    return T, int(r)
+
+
+class GridTables:
+    """FP64 tables of one gridded model: T [nloc, nx, nz], the locations (float32, increasing),
+    the grid origin and spacing, and the fast-sweeping rounds per location."""
+
+    def __init__(self, T, loc, ox, h, rounds):
+        self.T, self.loc, self.ox, self.h, self.rounds = T, loc, float(ox), float(h), rounds
+
+
+def locations(s) -> np.ndarray:
+    """The survey's distinct surface positions (source and receiver x), increasing, float32."""
+    return np.unique(np.concatenate([np.asarray(s.sx, np.float32), np.asarray(s.rx, np.float32)]))
+
+
+_grid_cache = {}
+
+
+def grid_tables(s, max_rounds: int = MAX_ROUNDS, tol: float = TOL) -> GridTables:
+    """Tables of the survey's model ``s.grid_v`` on (``s.grid_ox`` + i ``s.grid_h``, j ``s.grid_h``)
+    for every distinct surface position of its traces."""
+    v = np.ascontiguousarray(s.grid_v, dtype=np.float32)
+    loc = locations(s)
+    key = (hash(v.tobytes()), v.shape, float(s.grid_ox), float(s.grid_h), hash(loc.tobytes()), max_rounds, tol)
+    if key in _grid_cache:
+        return _grid_cache[key]
+    T = np.empty((loc.size,) + v.shape, dtype=np.float64)
+    rounds = np.empty(loc.size, dtype=np.int32)
+    bad = lib().ko_grid_tables(v.shape[0], v.shape[1], float(s.grid_ox), float(s.grid_h), _ptr(v), loc.size,
+                               _ptr(loc), int(max_rounds), float(tol), _ptr(T), _ptr(rounds))
+    if bad:
+        raise RuntimeError(f"eikonal tables: {bad} locations did not settle in {max_rounds} rounds")
+    g = GridTables(T, loc, s.grid_ox, s.grid_h, rounds)
+    if len(_grid_cache) >= 4:
+        _grid_cache.pop(next(iter(_grid_cache)))
+    _grid_cache[key] = g
+    return g
+
+
+def grid_traveltime(s, loc_index: int, x, z) -> np.ndarray:
+    """Table ``loc_index`` of the survey's model read at (x, z) by the bilinear interpolation of
+    the migration."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    z = np.ascontiguousarray(np.broadcast_to(np.asarray(z, dtype=np.float64), x.shape)).ravel()
+    T = np.empty_like(x)
+    lib().ko_grid_traveltime(ctypes.byref(desc(s)), int(loc_index), x.size, _ptr(x), _ptr(z), _ptr(T))
+    return T
 
 
 def cgls(s, data, n_iter: int, m0=None):

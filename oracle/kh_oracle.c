@@ -39,7 +39,8 @@ typedef struct {
     int n_bins;
     double bin_width;
     int vel;                 /* 0 constant, 1 linear in z, 2 table of the linear model, 3 time
-                                migration (double square root, RMS velocity of the linear model) */
+                                migration (double square root, RMS velocity of the linear model),
+                                4 tables of a gridded model v(x, z) from the eikonal solver */
     double v0, k;
     int weight;              /* 0 W=1, 1 obliquity x spreading */
     double r0;
@@ -48,6 +49,12 @@ typedef struct {
     double t0, dt;
     double table_spacing;    /* vel 2: node spacing of the radial traveltime table */
     double taper;            /* fraction of the aperture over which the weight tapers to 0 */
+    /* vel 4: one first-arrival traveltime table per surface location, on the node grid
+     * (gox + i gh, j gh), i < gnx, j < gnz (2D only) */
+    const double* gtab;      /* [gnloc][gnx][gnz], z fastest */
+    const float* gloc;       /* [gnloc] x of each table's surface point, increasing */
+    int gnloc, gnx, gnz;
+    double gox, gh;
 } ko_desc;
 
 /* Deliberate-mistake switch used only by the tests that show the pins catch errors.
@@ -194,6 +201,174 @@ int ko_traveltime(const ko_desc* d, long n, const double* R, const double* z, do
     return 0;
 }
 
+/* ---- first-arrival traveltimes in a laterally varying model v(x, z) (vel 4) ----
+ *
+ * Sec. 3 takes T from "high-frequency (ray-theoretic) approximations" with "a single propagation
+ * path": the first-arrival time, the viscosity solution of the eikonal equation |grad T| = s
+ * (slowness s = 1/v) with T = 0 at the surface point x_s.  It is computed on a node grid
+ * (ox + i h, j h), i < nx, j < nz (row 0 is the surface), as follows.
+ *
+ * Factorisation (additive, Luo & Qian, J. Sci. Comput. 52, 2012): T = T0 + tau with
+ * T0 = s0 |x - x_s|, the exact time of the constant slowness s0 = s(x_s), removes the point-source
+ * singularity that costs a plain first-order scheme its accuracy; tau solves
+ * |grad T0 + grad tau| = s.
+ * Discretisation: the Godunov upwind scheme on tau.  Along x, the one-sided slopes
+ * grad_x T0 + (tau - tau_left)/h and grad_x T0 + (tau_right - tau)/h enter as
+ * max(tau - c_x, 0)^2 / h^2 with c_x = min(tau_left - h g_x, tau_right + h g_x), g = grad T0 at the
+ * node (likewise c_z along z), so the node equation
+ *     max(tau - c_x, 0)^2 + max(tau - c_z, 0)^2 = (h s)^2
+ * is the plain upwind equation with shifted neighbour values, solved in closed form:
+ *     tau = min(c_x, c_z) + h s                                   if |c_x - c_z| >= h s,
+ *     tau = (c_x + c_z + sqrt(2 (h s)^2 - (c_x - c_z)^2)) / 2     otherwise.
+ * Solution: fast sweeping (Zhao, Math. Comp. 74, 2005): Gauss-Seidel passes over the grid in the
+ * orderings (i up, j up), (i down, j up), (i down, j down), (i up, j down), each node taking the
+ * smaller of its value and the update; rounds of four passes repeat until the largest decrease of
+ * a round is at most `tol` (seconds; 0: until nothing changes).
+ * Source treatment (a reading): the nodes with |x_i - x_s| <= 2 h in the first three rows keep
+ * the straight-ray time |x - x_s| (s0 + s(x)) / 2 (trapezoid rule for the slowness along the
+ * segment; s0 linear along the surface row) and are not updated.
+ * Every operation is one IEEE double operation in the order written (s = 1 / v). */
+static double godunov(double a, double b, double fh)
+{
+    const double d = a - b;
+    if (fabs(d) >= fh) return fmin(a, b) + fh;
+    const double disc = 2.0 * (fh * fh) - d * d;
+    if (ko_mutation == 16) return 0.5 * ((a + b) - sqrt(disc));   /* wrong root */
+    return 0.5 * ((a + b) + sqrt(disc));
+}
+
+/* T[nx][nz] (z fastest) from the surface point (xs, 0); v [nx][nz] in m/s.  Returns the number of
+ * rounds, or -1 if max_rounds did not suffice. */
+int ko_eikonal(int nx, int nz, double ox, double h, const float* v, double xs, int max_rounds, double tol,
+               double* T)
+{
+    if (nx < 2 || nz < 2 || !(h > 0.0)) return -1;
+    const long n = (long)nx * nz;
+    double* s = (double*)malloc(sizeof(double) * (size_t)n);
+    double* tau = (double*)malloc(sizeof(double) * (size_t)n);
+    unsigned char* fixed = (unsigned char*)calloc((size_t)n, 1);
+    if (!s || !tau || !fixed) { free(s); free(tau); free(fixed); return -1; }
+    for (long q = 0; q < n; ++q) s[q] = 1.0 / (double)v[q];
+    const double u = (xs - ox) / h;
+    long i0 = (long)floor(u);
+    if (i0 < 0) i0 = 0;
+    if (i0 > nx - 2) i0 = nx - 2;
+    const double f = u - (double)i0;
+    const double s0 = s[i0 * nz] + f * (s[(i0 + 1) * nz] - s[i0 * nz]);
+    for (long i = 0; i < nx; ++i) {
+        const double dx = (ox + (double)i * h) - xs;
+        const int near = fabs(dx) <= 2.0 * h;
+        for (long j = 0; j < nz; ++j) {
+            const long q = i * nz + j;
+            tau[q] = INFINITY;
+            if (near && j <= 2) {
+                const double zj = (double)j * h;
+                const double dist = sqrt(dx * dx + zj * zj);
+                /* T = s0 dist + tau = dist (s0 + s) / 2 */
+                tau[q] = (ko_mutation == 17) ? dist * (s[q] - s0) : dist * (0.5 * (s[q] - s0));
+                fixed[q] = 1;
+            }
+        }
+    }
+    const double hs0 = h * s0;
+    int rounds = -1;
+    for (int r = 0; r < max_rounds; ++r) {
+        double most = 0.0;
+        for (int pass = 0; pass < 4; ++pass) {
+            const int iup = (pass == 0 || pass == 3), jup = (pass < 2);
+            for (long ii = 0; ii < nx; ++ii) {
+                const long i = iup ? ii : nx - 1 - ii;
+                const double dx = (ox + (double)i * h) - xs;
+                for (long jj = 0; jj < nz; ++jj) {
+                    const long j = jup ? jj : nz - 1 - jj;
+                    const long q = i * nz + j;
+                    if (fixed[q]) continue;
+                    const double zj = (double)j * h;
+                    const double g = hs0 / sqrt(dx * dx + zj * zj);   /* h |grad T0| / |x - x_s| */
+                    double gx = g * dx, gz = g * zj;                   /* h grad T0 */
+                    if (ko_mutation == 19) { gx = -gx; gz = -gz; }   /* shifts of the wrong sign */
+                    const double cl = (i > 0) ? tau[q - nz] - gx : INFINITY;
+                    const double cr = (i < nx - 1) ? tau[q + nz] + gx : INFINITY;
+                    const double cu = (j > 0) ? tau[q - 1] - gz : INFINITY;
+                    const double cd = (j < nz - 1) ? tau[q + 1] + gz : INFINITY;
+                    const double a = fmin(cl, cr), b = fmin(cu, cd);
+                    if (a == INFINITY && b == INFINITY) continue;
+                    const double t = godunov(a, b, h * s[q]);
+                    if (t < tau[q]) {
+                        const double dec = tau[q] - t;
+                        if (dec > most) most = dec;
+                        tau[q] = t;
+                    }
+                }
+            }
+        }
+        if (most <= tol || ko_mutation == 18) {   /* 18: stop after one round */
+            rounds = r + 1;
+            break;
+        }
+    }
+    for (long i = 0; i < nx; ++i) {
+        const double dx = (ox + (double)i * h) - xs;
+        for (long j = 0; j < nz; ++j) {
+            const double zj = (double)j * h;
+            T[i * nz + j] = s0 * sqrt(dx * dx + zj * zj) + tau[i * nz + j];
+        }
+    }
+    free(s);
+    free(tau);
+    free(fixed);
+    return rounds;
+}
+
+/* Tables for nloc surface points (OpenMP over the points); rounds[l] as ko_eikonal returns it. */
+int ko_grid_tables(int nx, int nz, double ox, double h, const float* v, int nloc, const float* loc,
+                   int max_rounds, double tol, double* T, int* rounds)
+{
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+    for (int l = 0; l < nloc; ++l) {
+        rounds[l] = ko_eikonal(nx, nz, ox, h, v, (double)loc[l], max_rounds, tol, T + (long)l * nx * nz);
+        bad += rounds[l] < 0;
+    }
+    return bad;
+}
+
+/* Index of the table whose surface point is exactly x (the trace's source or receiver), or -1. */
+static int grid_location(const ko_desc* d, float x)
+{
+    int lo = 0, hi = d->gnloc - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) / 2;
+        if (d->gloc[mid] == x) return mid;
+        if (d->gloc[mid] < x) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* Table l read at (x, z) by bilinear interpolation between the four surrounding nodes (node
+ * indices clamped to the grid, so the last node column or row is reached with fraction 1). */
+static double grid_traveltime(const ko_desc* d, int l, double x, double z)
+{
+    double u = (x - d->gox) / d->gh, w = z / d->gh;
+    if (ko_mutation == 14) { const double t = u; u = w; w = t; }   /* axes swapped */
+    double iu = floor(u), jw = floor(w);
+    if (iu > d->gnx - 2) iu = d->gnx - 2;
+    if (iu < 0) iu = 0;
+    if (jw > d->gnz - 2) jw = d->gnz - 2;
+    if (jw < 0) jw = 0;
+    const double fu = u - iu, fw = w - jw;
+    const double* t = d->gtab + ((long)l * d->gnx + (long)iu) * d->gnz + (long)jw;
+    const double a = (1.0 - fw) * t[0] + fw * t[1];
+    const double b = (1.0 - fw) * t[d->gnz] + fw * t[d->gnz + 1];
+    return (1.0 - fu) * a + fu * b;
+}
+
+int ko_grid_traveltime(const ko_desc* d, int l, long n, const double* x, const double* z, double* T)
+{
+    for (long i = 0; i < n; ++i) T[i] = grid_traveltime(d, l, x[i], z[i]);
+    return 0;
+}
+
 /* Amplitude weight W(x, x_s, x_r) (Sec. 3, Eq. 1). */
 static double weight(const ko_desc* d, double z, double Rs, double Rr)
 {
@@ -305,6 +480,12 @@ static contrib contribution(const ko_desc* d, double x, double y, double z, doub
         Ts = table_traveltime(d, sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy)), z);
         Tr = table_traveltime(d, sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry)), z);
         if (ko_mutation == 3) Tr = Ts;
+    } else if (d->vel == 4) {
+        /* each leg from its surface point's table; a point with no table contributes nothing */
+        const int ls = grid_location(d, (float)sx), lr = grid_location(d, (float)rx);
+        if (ls < 0 || lr < 0) return c;
+        Ts = grid_traveltime(d, ls, x, z);
+        Tr = grid_traveltime(d, ko_mutation == 15 ? ls : lr, x, z);
     } else {
         traveltime(d, Rs, z, &Ts, want_grad ? &dsv : NULL, want_grad ? &dsk : NULL);
         traveltime(d, Rr, z, &Tr, want_grad ? &drv : NULL, want_grad ? &drk : NULL);
@@ -526,6 +707,10 @@ int ko_arrivals(const ko_desc* d, long npts, const double* px, const double* py,
             } else if (d->vel == 2) {
                 Ts = table_traveltime(d, sqrt((x - sx[j]) * (x - sx[j]) + (y - ssy) * (y - ssy)), z);
                 Tr = table_traveltime(d, sqrt((x - rx[j]) * (x - rx[j]) + (y - rry) * (y - rry)), z);
+            } else if (d->vel == 4) {
+                const int ls = grid_location(d, sx[j]), lr = grid_location(d, rx[j]);
+                Ts = ls < 0 ? NAN : grid_traveltime(d, ls, x, z);
+                Tr = lr < 0 ? NAN : grid_traveltime(d, lr, x, z);
             } else {
                 traveltime(d, Rs, z, &Ts, NULL, NULL);
                 traveltime(d, Rr, z, &Tr, NULL, NULL);

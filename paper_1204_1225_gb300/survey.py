@@ -30,7 +30,9 @@ class Survey:
     ``table_spacing``);
     ``weight`` is ``"one"`` or ``"obliq"``; ``aperture <= 0`` means full aperture; ``taper`` is the
     fraction of the aperture over which the weight falls to 0 (raised cosine; 0: a hard mask);
-    ``vel == "pstm"`` reads the depth axis as two-way vertical time (time migration).
+    ``vel == "pstm"`` reads the depth axis as two-way vertical time (time migration);
+    ``vel == "grid"`` (2D) takes each leg from the first-arrival time table of its surface point in
+    the gridded model ``grid_v``.
     """
 
     dim: int
@@ -61,6 +63,11 @@ class Survey:
     name: str = ""
     table_spacing: float = 25.0
     taper: float = 0.0
+    # vel == "grid" (2D): the model v(x, z) sampled on the square node grid
+    # (grid_ox + i grid_h, j grid_h), [nx][nz] float32 m/s, row 0 at the surface
+    grid_v: Optional[np.ndarray] = None
+    grid_ox: float = 0.0
+    grid_h: float = 0.0
 
     @property
     def ntr(self) -> int:
@@ -196,6 +203,40 @@ def survey_25d_lsm(nx: int = 512, nz: int = 400, nt: int = 2000, n_shots: int = 
                   n_bins=8, bin_width=160.0, vel="linear", v0=1800.0, k=0.6, weight="one",
                   r0=1000.0, aperture=0.0, nt=nt, t0=0.0, dt=0.004, sx=_f32(sx), sy=_f32(z),
                   rx=_f32(rx), ry=_f32(z), name=f"25d-vz-{sx.size}tr-{nx}x{nz}")
+
+
+def grid_layout(survey: Survey, m: int, margin_nodes: int = 1):
+    """Node grid for a gridded model of a 2D survey: square cells of side h = m dz (m in 1, 2, 4),
+    row 0 at the surface, columns covering the image and every source and receiver with
+    ``margin_nodes`` spare nodes each side, and rows down to one node below the image depths
+    rounded up to a multiple of 16 samples (the depths a migration tile may evaluate).
+    Returns (nx, nz, ox, h)."""
+    h = m * survey.dz
+    zoff = int(round(survey.oz / h))
+    xs = np.concatenate([np.asarray(survey.sx, np.float64), np.asarray(survey.rx, np.float64),
+                         [survey.ox, survey.ox + (survey.nx - 1) * survey.dx]])
+    i0 = math.floor(float(xs.min()) / h) - margin_nodes
+    i1 = math.ceil(float(xs.max()) / h) + margin_nodes
+    nz = zoff + (-(-survey.nz // 16) * 16) // m + 1
+    return i1 - i0 + 1, nz, i0 * h, h
+
+
+def vxz_model(survey: Survey, m: int, lens_dv: float = -300.0, lens_xz=None, lens_r: float = 250.0,
+              lateral: float = 0.0) -> Survey:
+    """The survey with vel "grid" and a laterally varying model on ``grid_layout``'s nodes:
+    v = v0 + k z + lateral (x - x_c) + lens_dv exp(-|p - p_lens|^2 / (2 lens_r^2)), a Gaussian lens
+    (low velocity for lens_dv < 0) centred at ``lens_xz`` (default: the image centre, 40 % down)
+    in the gradient model of the survey (x_c the image centre)."""
+    nx, nz, ox, h = grid_layout(survey, m)
+    xc = survey.ox + 0.5 * (survey.nx - 1) * survey.dx
+    if lens_xz is None:
+        lens_xz = (xc, survey.oz + 0.4 * (survey.nz - 1) * survey.dz)
+    x = ox + np.arange(nx, dtype=np.float64) * h
+    z = np.arange(nz, dtype=np.float64) * h
+    X, Z = np.meshgrid(x, z, indexing="ij")
+    v = (survey.v0 + survey.k * Z + lateral * (X - xc)
+         + lens_dv * np.exp(-((X - lens_xz[0]) ** 2 + (Z - lens_xz[1]) ** 2) / (2.0 * lens_r ** 2)))
+    return survey.replace(vel="grid", grid_v=_f32(v), grid_ox=float(ox), grid_h=float(h))
 
 
 def survey_random(rng: np.random.Generator, dim: int, ntr: int, nx: int, ny: int, nz: int,

@@ -22,8 +22,8 @@
  *    thread at a time.
  *  - Every failure returns a status code and sets a thread-local message readable with
  *    kirchhoff_last_error(); nothing aborts or traps.  Errors raised inside a kernel
- *    (a bounded wait that ran out) are reported by kirchhoff_sync(), which waits for the
- *    plan's work on the stream.
+ *    (a bounded wait that ran out, a trace position with no KH_VEL_GRID table) are reported by
+ *    kirchhoff_sync(), which waits for the plan's work on the stream.
  *  - The plan owns its device workspace (trace sort order, headers, padded traces,
  *    traveltime tables); it grows on demand and is freed by kirchhoff_destroy().
  */
@@ -81,8 +81,14 @@ typedef enum { KH_F32 = 0, KH_F16 = 1, KH_BF16 = 2, KH_U16 = 3 } kh_dtype;
  *                   T = sqrt((t0/2)^2 + h^2 / v_rms(t0)^2), h the horizontal distance,
  *                   v_rms(t0)^2 = v0^2 (e^{k t0} - 1) / (k t0).  Migration and the utilities
  *                   only (demigration and the velocity gradient refuse it).  The weight's
- *                   geometry is that of the straight rays: R = v_rms T, z = v_rms t0 / 2. */
-typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2, KH_VEL_PSTM = 3 } kh_vel;
+ *                   geometry is that of the straight rays: R = v_rms T, z = v_rms t0 / 2.
+ *  KH_VEL_GRID:     a laterally varying model v(x, z) (dim 2), given on a node grid to
+ *                   kirchhoff_grid_tables, which computes the first-arrival time table of every
+ *                   surface location (see there); each leg reads its location's table by
+ *                   bilinear interpolation.  v0 and k are not used.  Migration only (demigration,
+ *                   the velocity gradient, the traveltime utility and the batched launch refuse
+ *                   it).  The weight's geometry is that of straight rays (R = |x - x_a|). */
+typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2, KH_VEL_PSTM = 3, KH_VEL_GRID = 4 } kh_vel;
 
 /* Weight W(x, x_s, x_r) of Eq. (1) ("amplitude of propagation"; no formula in the paper):
  *  KH_W_ONE:          W = 1.
@@ -208,6 +214,63 @@ KH_API kh_status kirchhoff_fit_report(const kh_desc* d, int cx, int cy, int cz, 
  * non-finite weights, all weights zero, NULL weights before any migration of p). */
 KH_API kh_status kirchhoff_semblance(kh_plan p, const float* image, const double* bin_weight, double* out,
                                      float* grad_image, void* cuda_stream);
+
+/* ---------------------------------------------------------------- gridded model v(x, z)
+ * Sec. 3 takes T from ray-theoretic (high-frequency) approximations with a single propagation
+ * path: the first-arrival time, the solution of the eikonal equation |grad T| = 1/v with T = 0 at
+ * the surface location.  For a laterally varying model (KH_VEL_GRID, dim 2) the library solves it
+ * on a node grid for every surface location and the migration reads the tables.
+ *
+ * Node grid (kh_grid): nodes (ox + i h, j h), i < nx, j < nz, z fastest, row 0 at the surface,
+ * with h = m dz (m = 1, 2 or 4, to 1e-9 relative) and the image's oz a non-negative multiple of h
+ * (to 1e-9), so that image depth iz lies at node row oz/h + iz/m.  The columns must cover every
+ * image column and every location; nz >= oz/h + 16 ceil(nz_image / 16) / m + 1 (one node below
+ * the deepest depth a migration tile evaluates); nx, nz >= 2, nx nz <= 28000 (the solver keeps a
+ * location's grid in FP64 in one CTA's shared memory).
+ *
+ * kirchhoff_grid_layout (host only): the smallest such grid for descriptor `d` (vel KH_VEL_GRID)
+ * and node spacing multiple m whose columns cover the image and [xmin, xmax] (the locations'
+ * range) with `margin` >= 0 spare columns on each side, ox a multiple of h.
+ *
+ * kirchhoff_grid_tables: for the model v (DEVICE FP32 [grid->nx][grid->nz], m/s, finite, > 0) and
+ * nloc >= 1 locations loc_x (DEVICE FP32 [nloc], strictly increasing, inside the grid's columns),
+ * builds in the plan one FP32 table [nx][nz] per location, on one CTA per location:
+ *   - factorisation T = T0 + tau, T0 = s0 |x - x_s| with s0 the slowness at the location (linear
+ *     along the surface row), which removes the point-source singularity (additive factor of
+ *     Luo and Qian, 2012); constant velocity is reproduced to rounding;
+ *   - the Godunov upwind discretisation of |grad T0 + grad tau| = s: with c_x = min(tau_left -
+ *     h dT0/dx, tau_right + h dT0/dx) and c_z likewise, tau = min(c_x, c_z) + h s if
+ *     |c_x - c_z| >= h s, else (c_x + c_z + sqrt(2 (h s)^2 - (c_x - c_z)^2)) / 2, taken if smaller;
+ *   - fast sweeping (Zhao, 2005): Gauss-Seidel passes in the orderings (i up, j up), (i down,
+ *     j up), (i down, j down), (i up, j down), each pass as a wavefront of anti-diagonals (the
+ *     nodes of one anti-diagonal are independent within a pass, so the result is that of the
+ *     sequential pass); rounds of four passes until a round's largest decrease is <= 1e-9 s, at
+ *     most 64 rounds; a node is recomputed only after one of its neighbours changed (the same
+ *     result with less work);
+ *   - the nodes with |x_i - x_s| <= 2 h in rows 0..2 keep the straight-ray time
+ *     |x - x_s| (s0 + s(x)) / 2 and are not updated;
+ *   - IEEE FP64 throughout, one rounding per operation in the order written, then rounded to FP32.
+ * Synchronises the stream.  Errors: KH_ERR_INVALID_ARG (NULL pointers, a grid that breaks the
+ * rules above, v not finite and > 0, locations not increasing or outside the columns, a plan that
+ * is not KH_VEL_GRID), KH_ERR_UNSUPPORTED (a location that did not settle in 64 rounds).
+ * A later kirchhoff_migrate reads the tables: each trace's source and receiver x must equal one
+ * of loc_x exactly; a trace whose position does not is skipped and kirchhoff_sync reports
+ * KH_ERR_INVALID_ARG.  Per image tile and location the migration takes the smallest and largest
+ * node value the tile interpolates between as the time window's bounds.
+ *
+ * kirchhoff_grid_read: copies the plan's tables (DEVICE FP32 [nloc][nx][nz]; NULL skips) and the
+ * rounds each location took (DEVICE int [nloc]; NULL skips); *nloc (HOST, may be NULL) = nloc.
+ * Synchronises the stream. */
+typedef struct {
+    int nx, nz;              /* nodes along x and z */
+    double ox, h;            /* x of node column 0, and the node spacing in x and z, metres */
+} kh_grid;
+
+KH_API kh_status kirchhoff_grid_layout(const kh_desc* d, int m, double xmin, double xmax, int margin,
+                                       kh_grid* out);
+KH_API kh_status kirchhoff_grid_tables(kh_plan p, const kh_grid* grid, const float* v, int nloc,
+                                       const float* loc_x, void* cuda_stream);
+KH_API kh_status kirchhoff_grid_read(kh_plan p, float* tables, int* rounds, int* nloc, void* cuda_stream);
 
 /* ---------------------------------------------------------------- the binning sort
  * Eq. (1)'s delta(X - |x_s - x_r|) assigns each trace to one offset bin, and only traces "close

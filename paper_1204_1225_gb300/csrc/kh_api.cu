@@ -267,12 +267,16 @@ static kh_status validate_desc(const kh_desc* d)
     if (d->n_bins < 1 || d->n_bins > kh::MAX_BINS)
         return fail(KH_ERR_INVALID_ARG, "n_bins must be in [1, %d]", kh::MAX_BINS);
     if (!(d->bin_width > 0)) return fail(KH_ERR_INVALID_ARG, "bin_width must be > 0");
-    if (d->vel != KH_VEL_CONST && d->vel != KH_VEL_LINEAR_Z && d->vel != KH_VEL_TABLE && d->vel != KH_VEL_PSTM)
+    if (d->vel != KH_VEL_CONST && d->vel != KH_VEL_LINEAR_Z && d->vel != KH_VEL_TABLE && d->vel != KH_VEL_PSTM &&
+        d->vel != KH_VEL_GRID)
         return fail(KH_ERR_INVALID_ARG, "bad velocity kind %d", (int)d->vel);
+    if (d->vel == KH_VEL_GRID && d->dim != 2)
+        return fail(KH_ERR_UNSUPPORTED, "KH_VEL_GRID (gridded v(x, z)) is 2D only");
     if (d->vel == KH_VEL_PSTM && !(std::min(d->oz, d->oz + (d->nz - 1) * d->dz) >= 0.0))
         return fail(KH_ERR_INVALID_ARG, "time migration: the image's vertical axis is two-way time, t0 >= 0");
-    if (!(d->v0 > 0) || !std::isfinite(d->v0)) return fail(KH_ERR_INVALID_ARG, "v0 must be > 0");
-    if (!std::isfinite(d->k)) return fail(KH_ERR_INVALID_ARG, "k must be finite");
+    if (d->vel != KH_VEL_GRID && (!(d->v0 > 0) || !std::isfinite(d->v0)))
+        return fail(KH_ERR_INVALID_ARG, "v0 must be > 0");
+    if (d->vel != KH_VEL_GRID && !std::isfinite(d->k)) return fail(KH_ERR_INVALID_ARG, "k must be finite");
     if (d->weight != KH_W_ONE && d->weight != KH_W_OBLIQ_SPREAD)
         return fail(KH_ERR_INVALID_ARG, "bad weight kind %d", (int)d->weight);
     if (d->weight == KH_W_OBLIQ_SPREAD && !(d->r0 > 0)) return fail(KH_ERR_INVALID_ARG, "r0 must be > 0");
@@ -280,7 +284,7 @@ static kh_status validate_desc(const kh_desc* d)
     if (!(d->dt > 0) || !std::isfinite(d->t0)) return fail(KH_ERR_INVALID_ARG, "dt must be > 0, t0 finite");
     if (d->trace_dtype != KH_F32 && d->trace_dtype != KH_F16 && d->trace_dtype != KH_BF16)
         return fail(KH_ERR_INVALID_ARG, "bad trace dtype");
-    if (d->vel != KH_VEL_CONST && d->vel != KH_VEL_PSTM) {
+    if (d->vel != KH_VEL_CONST && d->vel != KH_VEL_PSTM && d->vel != KH_VEL_GRID) {
         const double zlo = std::min(0.0, std::min(d->oz, d->oz + (d->nz - 1) * d->dz));
         const double zhi = std::max(d->oz, d->oz + (d->nz - 1) * d->dz);
         if (!(d->v0 + d->k * zlo > 0) || !(d->v0 + d->k * zhi > 0))
@@ -317,7 +321,7 @@ static GeomParams geom_of(const kh_desc& d)
     g.dy = d.dy;
     g.dz = d.dz;
     g.fdz = (float)d.dz;
-    const bool lin = d.vel != KH_VEL_CONST && d.vel != KH_VEL_PSTM && d.k != 0.0;
+    const bool lin = d.vel != KH_VEL_CONST && d.vel != KH_VEL_PSTM && d.vel != KH_VEL_GRID && d.k != 0.0;
     g.pstm = d.vel == KH_VEL_PSTM ? 1 : 0;
     g.pk = d.vel == KH_VEL_PSTM ? d.k : 0.0;
     g.v0 = d.v0;
@@ -1054,6 +1058,11 @@ kh_status kirchhoff_destroy(kh_plan p)
     cudaFree(p->ws_tab64);
     cudaFree(p->ws_tmm);
     cudaFree(p->ws_hmax);
+    cudaFree(p->ws_gtab);
+    cudaFree(p->ws_gloc);
+    cudaFree(p->ws_grounds);
+    cudaFree(p->ws_gslow);
+    cudaFree(p->ws_gbnd);
     for (auto& pr : p->ev_open) {
         if (pr.first) cudaEventDestroy(pr.first);
         if (pr.second) cudaEventDestroy(pr.second);
@@ -1127,6 +1136,9 @@ kh_status kirchhoff_migrate(kh_plan p, int ntr, const float* sx, const float* sy
     if (p->d.vel == KH_VEL_TABLE) {
         if ((st = ensure_table(p, ntr, sx, sy, rx, ry, s, tile, g)) != KH_OK) return st;
         vk = VK_TABLE;
+    } else if (p->d.vel == KH_VEL_GRID) {
+        if ((st = grid_prepare(p, tile, g, s)) != KH_OK) return st;
+        vk = VK_GRID;
     }
     TraceSet ts = plan_traces(p);
     WaitCfg w{p->ws_status, p->wait_polls, WAIT_NS};
@@ -1147,7 +1159,7 @@ kh_status kirchhoff_demigrate(kh_plan p, int ntr, const float* sx, const float* 
     kh_status st = check_headers(p, ntr, sx, sy, rx, ry);
     if (st != KH_OK) return st;
     if (ntr > 0 && (!image || !traces_out)) return fail(KH_ERR_INVALID_ARG, "image/traces_out is NULL");
-    if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM)
+    if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM || p->d.vel == KH_VEL_GRID)
         return fail(KH_ERR_UNSUPPORTED, "demigration uses the analytic depth traveltimes; "
                                         "create the plan with KH_VEL_CONST or KH_VEL_LINEAR_Z");
     if (ntr == 0) return KH_OK;
@@ -1186,7 +1198,7 @@ kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, const flo
     if (st != KH_OK) return st;
     if (!out_dv0_dk) return fail(KH_ERR_INVALID_ARG, "out_dv0_dk is NULL");
     if (ntr > 0 && (!image || !traces)) return fail(KH_ERR_INVALID_ARG, "image/traces is NULL");
-    if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM)
+    if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM || p->d.vel == KH_VEL_GRID)
         return fail(KH_ERR_UNSUPPORTED, "no velocity gradient for table traveltimes or time migration");
     if (p->d.trace_dtype != KH_F32) return fail(KH_ERR_UNSUPPORTED, "velocity gradient takes FP32 traces");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1256,6 +1268,8 @@ kh_status kirchhoff_traveltime(kh_plan p, int n, const float* px, const float* p
     if (n < 0) return fail(KH_ERR_INVALID_ARG, "n must be >= 0");
     if (n == 0) return KH_OK;
     if (!px || !pz || !lx || !T) return fail(KH_ERR_INVALID_ARG, "NULL array");
+    if (p->d.vel == KH_VEL_GRID)
+        return fail(KH_ERR_UNSUPPORTED, "KH_VEL_GRID: read the tables with kirchhoff_grid_read");
     const bool pstm = p->d.vel == KH_VEL_PSTM;
     const bool lin = !pstm && p->d.vel != KH_VEL_CONST && p->d.k != 0.0;
     k_traveltime<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
@@ -1302,6 +1316,9 @@ kh_status kirchhoff_sync(kh_plan p, void* cuda_stream)
         cudaMemset(p->ws_status, 0, sizeof(int));
         if (h & 1)
             return fail(KH_ERR_TIMEOUT, "a bounded in-kernel wait ran out (status 0x%x); results are invalid", h);
+        if (h == STATUS_NO_TABLE)
+            return fail(KH_ERR_INVALID_ARG, "a trace's source or receiver position is not one of the locations "
+                                            "of the KH_VEL_GRID tables; those traces were skipped");
         return fail(KH_ERR_INTERNAL, "a kernel reported an internal sizing error (status 0x%x); "
                                      "results are invalid", h);
     }

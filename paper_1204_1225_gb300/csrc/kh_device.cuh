@@ -172,6 +172,18 @@ __device__ __forceinline__ double grid_coord(double o, int i, double h)
     return __dadd_rn(o, __dmul_rn((double)i, h));
 }
 
+// Gridded model (KH_VEL_GRID): node column gi of image column ix in the tables' node grid and the
+// column's fraction between node columns gi and gi + 1 (FP64, clamped so that gi + 1 is a node);
+// the migration's reads and the tile bounds both take it from here.
+__device__ __forceinline__ int grid_col(const GeomParams& g, int ix, float* frac)
+{
+    const double u = __ddiv_rn(__dadd_rn(grid_coord(g.ox, ix, g.dx), -g.gox), g.gh);
+    int gi = (int)floor(u);
+    gi = gi < 0 ? 0 : (gi > g.gnx - 2 ? g.gnx - 2 : gi);
+    if (frac) *frac = (float)(u - (double)gi);
+    return gi;
+}
+
 // Column coordinate o + i h in FP64 without contraction, rounded to FP32 (the same value the
 // aperture decision uses everywhere).
 __device__ __forceinline__ float col_coord(double o, int i, double h)

@@ -51,7 +51,14 @@ constexpr int PAIR_MAX_NT = 2460;
 // Default wait limit: polls of mbarrier.try_wait, each checked against a 2 s wall clock.
 constexpr long long WAIT_NS = 2000000000LL;
 
-enum VelKind { VK_CONST = 0, VK_LINEAR = 1, VK_TABLE = 2, VK_PSTM = 3 };
+enum VelKind { VK_CONST = 0, VK_LINEAR = 1, VK_TABLE = 2, VK_PSTM = 3, VK_GRID = 4 };
+
+// Gridded model v(x, z) (KH_VEL_GRID): at most this many nodes, so that the eikonal solver keeps
+// a location's grid in one CTA's shared memory (FP64 values and one dirty bit per node).
+constexpr int MAX_GRID_NODES = 28000;
+// Plan status bits beyond bit 0 (a bounded wait ran out): bit 1 demigration sizing, bit 2 a
+// trace position with no traveltime table.
+constexpr int STATUS_NO_TABLE = 4;
 
 // RMS velocity of v(z) = v0 + k z down to the two-way vertical time t0: v0^2 (e^{k t0} - 1)/(k t0)
 // (v(tau) = v0 e^{k tau} at one-way vertical time tau; the mean of v^2 over [0, t0/2]).
@@ -132,6 +139,16 @@ struct GeomParams {
     double tza, tsp;         // first z node (the first image depth), h spacing
     int tm;                  // depth nodes every tm image samples (1, 2 or 4)
     float tslack;            // extra window slack (samples) for the interpolation error
+    // per-location first-arrival tables of a gridded model (KH_VEL_GRID, dim 2): FP32 seconds
+    // [nloc][gnx][gnz] (z fastest) on the nodes (gox + i gh, j gh), read from global memory; the
+    // image depth iz lies at node row gzoff + iz / tm.  gbnd: per (location, tile of the launch)
+    // the smallest and largest node value over the nodes the tile's points interpolate between.
+    const float* gtab;
+    long long gstride;       // gnx * gnz
+    int gnx, gnz, gzoff;
+    double gox, gh;
+    const float2* gbnd;
+    int gtiles;
     float t0, dt;            // FP32 copies for the window bounds
     double t0d, dtd;         // exact values for the FP64 references
     // weight

@@ -94,7 +94,7 @@ __host__ __device__ inline size_t table_bytes(const GeomParams& g)
 // trace anyway.
 __host__ __device__ inline size_t src_cache_bytes(const GeomParams& g)
 {
-    if (g.table) return (size_t)NZ * CONSUMERS * sizeof(float);
+    if (g.table || g.gtab) return (size_t)NZ * CONSUMERS * sizeof(float);
     // gradient: the thread's weighted image values, and for linear v(z) (C1 ln(1 + rho_s), (q/w)_s)
     // and sqrt(q_s)
     if (g.grad) return (size_t)NZ * CONSUMERS * (g.kabs > 0.0 ? sizeof(float2) + 2 * sizeof(float) : sizeof(float));
@@ -190,6 +190,19 @@ __device__ __forceinline__ float tab_depth(const float* p, int i)
 {
     const int j = i / M, r = i % M;
     return r == 0 ? p[j] : fmaf((float)r * (1.f / M), p[j + 1] - p[j], p[j]);
+}
+
+// One leg's profile at K node rows from its location's table: the lerp in x between the column's
+// two node columns (c0 points at the first row in node column gi; gi + 1 follows gnz later).
+template <int K>
+__device__ __forceinline__ void grid_profile(const float* __restrict__ c0, int gnz, float fx, float* p)
+{
+    const float* c1 = c0 + gnz;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float a = __ldg(c0 + k), b = __ldg(c1 + k);
+        p[k] = fmaf(fx, b - a, a);
+    }
 }
 
 // The migration kernel's sample read: th = tau - lo (window-relative sample position); valid
@@ -301,7 +314,7 @@ __device__ __forceinline__ void next_row(int* row, const int2* rng, int& cur, in
 template <int VEL, typename TT>
 __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                                             const TraceSet& tr, const TT* __restrict__ traces, int bin,
-                                            const TileBox& box, const WaitCfg& wc, int n)
+                                            const TileBox& box, const WaitCfg& wc, int n, int tile_id = 0)
 {
     const int lane = threadIdx.x & 31;
     const double inv_kdt = (VEL == VK_LINEAR) ? 1.0 / (g.kabs * g.dtd) : 0.0;
@@ -343,8 +356,20 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                     ok = ax * ax + ay * ay <= g.A2cull;
                 }
                 if (ok) {
-                    ok = trace_window(h, box, VEL == VK_TABLE ? (g.k == 0.0 ? VK_CONST : VK_LINEAR) : VEL,
-                                      g, lo, hi, &clipped, &pt);
+                    if constexpr (VEL == VK_GRID) {
+                        // the window from the tile's node bounds of both legs' tables; a negative
+                        // location (a position with no table) skips the trace
+                        const int ls = __float_as_int(h.y), lr = __float_as_int(h.w);
+                        ok = ls >= 0 && lr >= 0;
+                        if (ok) {
+                            const float2 bs = __ldg(&g.gbnd[(long long)ls * g.gtiles + tile_id]);
+                            const float2 br = __ldg(&g.gbnd[(long long)lr * g.gtiles + tile_id]);
+                            ok = sample_window(__fadd_rn(bs.x, br.x), __fadd_rn(bs.y, br.y), g, lo, hi, &clipped);
+                        }
+                    } else {
+                        ok = trace_window(h, box, VEL == VK_TABLE ? (g.k == 0.0 ? VK_CONST : VK_LINEAR) : VEL,
+                                          g, lo, hi, &clipped, &pt);
+                    }
                     lo_al = lo & ~(g.elem_align - 1);
                     len_al = (hi + 1 - lo_al + g.elem_align - 1) & ~(g.elem_align - 1);
                 }
@@ -514,6 +539,15 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     const TT* ring = data - LEAD;
     const unsigned ring_last = (unsigned)(LEAD + STAGES * cap + SLACK - 2);   // the kernel's ring
     const bool zfull = izb + NZ <= g.nz;   // all 16 depths of this thread lie in the grid
+    // gridded model: the column's node column and fraction, and its first node row (threads
+    // whose depths all lie below the image read the last rows)
+    const float* gcol = nullptr;
+    float gfx = 0.f;
+    if constexpr (VEL == VK_GRID) {
+        const int gi = grid_col(g, ix, &gfx);
+        const int jb = min(g.gzoff + izb / LPT, g.gnz - (NZ / LPT + 1));
+        gcol = g.gtab + (long long)gi * g.gnz + jb;
+    }
 
     bool failed = false;
     while (true) {
@@ -563,6 +597,46 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
                 float pr[K];
                 tab_profile<TB, K, FAST>(tab, g, dhr2, jb, pr);
+                auto zloop = [&](auto checked, auto tapered) {
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) {
+                        const float th = fmaf(my_ts[i * CONSUMERS] + tab_depth<M>(pr, i), g.C1, c0rel);
+                        float val;
+                        if constexpr (decltype(checked)::value)
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                        else
+                            val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        if constexpr (decltype(tapered)::value) val *= tp;
+                        // w_z multiplies the sum once, at the store
+                        if constexpr (WGT == 1) {
+                            const float Rsum = hsqrt<FAST>(dhs2 + zc[i].y) + hsqrt<FAST>(dhr2 + zc[i].y);
+                            acc[i] = fmaf(Rsum, val, acc[i]);
+                        }
+                        else acc[i] += val;
+                    }
+                };
+                if (unchecked) zloop(std::false_type(), std::false_type());
+                else if (g.use_taper) zloop(std::true_type(), std::true_type());
+                else zloop(std::true_type(), std::false_type());
+            } else if constexpr (VEL == VK_GRID) {
+                // T_s + T_r from the two legs' first-arrival tables (global memory, L2-resident):
+                // per leg the profile at the thread's K node rows, then linear in depth; the
+                // source leg is cached per source location
+                constexpr int M = LPT;            // depth nodes every M samples (1, 2 or 4)
+                constexpr int K = NZ / M + 1;
+                float* my_ts = reinterpret_cast<float*>(srcc) + tid;
+                const int ls = __float_as_int(h.y), lr = __float_as_int(h.w);
+                const float dxs = cxf - h.x, dxr = cxf - h.z;
+                const float dhs2 = dxs * dxs, dhr2 = dxr * dxr;
+                if ((unsigned)ls != psx) {   // new source location
+                    float ps[K];
+                    grid_profile<K>(gcol + (long long)ls * g.gstride, g.gnz, gfx, ps);
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) my_ts[i * CONSUMERS] = tab_depth<M>(ps, i);
+                    psx = (unsigned)ls;
+                }
+                float pr[K];
+                grid_profile<K>(gcol + (long long)lr * g.gstride, g.gnz, gfx, pr);
                 auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
@@ -710,7 +784,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     if constexpr (WGT == 1) {
 #pragma unroll
         for (int i = 0; i < NZ; ++i)
-            acc[i] *= (VEL == VK_LINEAR || VEL == VK_PSTM) ? zg[i] : (VEL == VK_TABLE ? zc[i].x : zc[i].y);
+            acc[i] *= (VEL == VK_LINEAR || VEL == VK_PSTM) ? zg[i] : ((VEL == VK_TABLE || VEL == VK_GRID) ? zc[i].x : zc[i].y);
     }
     float* out = image + (((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb;
     const bool vec = ((g.nz & 3) == 0) && (izb + NZ <= g.nz) &&
@@ -905,7 +979,7 @@ __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, co
             float gamma;
             S.zc[i] = z_constants_m(z, box.cz, g, gamma);
             S.z2[i] = gamma;
-        } else if constexpr (VEL == VK_TABLE) {
+        } else if constexpr (VEL == VK_TABLE || VEL == VK_GRID) {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
             S.zc[i] = make_float4(wz, (float)(z * z), 0.f, 0.f);
         } else if constexpr (VEL == VK_PSTM) {
@@ -948,8 +1022,9 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
     const TileBox box = tile_box(g, x0, y0, z0, ts.cx, ts.cy, ts.cz * NZ);
 
     if (threadIdx.x == 0) {
-        // a wait in another CTA of this plan already ran out: results are invalid anyway
-        s_abort = *reinterpret_cast<const volatile int*>(wc.status);
+        // a wait in another CTA of this plan already ran out: results are invalid anyway (the
+        // other status bits report skipped inputs, not a stalled launch)
+        s_abort = *reinterpret_cast<const volatile int*>(wc.status) & 1;
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], CONSUMER_WARPS);
@@ -975,7 +1050,7 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
     __syncthreads();
     if (s_abort) return;
     if (threadIdx.x >= CONSUMERS) {
-        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, bin, box, wc, 0);
+        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, bin, box, wc, 0, (int)blockIdx.x);
     } else if constexpr (MODE == 0) {
         mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, srcc, cap,
                                                   0);
@@ -1016,6 +1091,14 @@ static cudaError_t launch_migrate_t(const GeomParams& g, const TileShape& t, con
     if constexpr (VEL == VK_LINEAR) {
         return with_lg<FAST>(g.lg_terms,
                              [&](auto L) { return go(k_migrate<VEL, WGT, FAST, TT, decltype(L)::value>); });
+    } else if constexpr (VEL == VK_GRID) {
+        // the LPT slot carries the tables' depth-node stride M
+        switch (g.tm) {
+            case 1: return go(k_migrate<VEL, WGT, FAST, TT, 1>);
+            case 2: return go(k_migrate<VEL, WGT, FAST, TT, 2>);
+            case 4: return go(k_migrate<VEL, WGT, FAST, TT, 4>);
+            default: return cudaErrorInvalidValue;
+        }
     } else if constexpr (VEL == VK_TABLE) {
         // the LPT slot carries the table's depth-node stride M
         auto tb = [&](auto M) -> cudaError_t {
@@ -1057,6 +1140,10 @@ cudaError_t launch_migrate_dtype(const GeomParams& g, const TileShape& t, const 
         case 13: return launch_migrate_t<VK_PSTM, 0, true, TT>(g, t, tr, traces, image, w, s);
         case 14: return launch_migrate_t<VK_PSTM, 1, false, TT>(g, t, tr, traces, image, w, s);
         case 15: return launch_migrate_t<VK_PSTM, 1, true, TT>(g, t, tr, traces, image, w, s);
+        case 16:
+        case 17: return launch_migrate_t<VK_GRID, 0, true, TT>(g, t, tr, traces, image, w, s);
+        case 18:
+        case 19: return launch_migrate_t<VK_GRID, 1, true, TT>(g, t, tr, traces, image, w, s);
         default: return cudaErrorInvalidValue;
     }
 }

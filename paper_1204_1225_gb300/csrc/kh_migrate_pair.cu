@@ -1,5 +1,5 @@
 // Migration kernel instantiations for FP32 traces staged as SamplePair rows (constant and
-// linear v(z), time migration; table migrations stage plain samples).
+// linear v(z), time migration, gridded-model tables; radial-table migrations stage plain samples).
 #include "kh_migrate_impl.cuh"
 
 namespace kh {
@@ -20,6 +20,10 @@ cudaError_t launch_migrate_pair(const GeomParams& g, const TileShape& t, const T
         case 13: return launch_migrate_t<VK_PSTM, 0, true, SamplePair>(g, t, tr, traces, image, w, s);
         case 14: return launch_migrate_t<VK_PSTM, 1, false, SamplePair>(g, t, tr, traces, image, w, s);
         case 15: return launch_migrate_t<VK_PSTM, 1, true, SamplePair>(g, t, tr, traces, image, w, s);
+        case 16:
+        case 17: return launch_migrate_t<VK_GRID, 0, true, SamplePair>(g, t, tr, traces, image, w, s);
+        case 18:
+        case 19: return launch_migrate_t<VK_GRID, 1, true, SamplePair>(g, t, tr, traces, image, w, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -69,7 +69,7 @@ extern "C" kh_status kirchhoff_migrate_noalloc(const kh_desc* d, int ntr, const 
                          "holds 65536 traces); use kirchhoff_migrate for larger surveys");
     if (d->trace_dtype != KH_F32)
         return set_error(KH_ERR_UNSUPPORTED, "kirchhoff_migrate_noalloc: FP32 traces only");
-    if (d->vel == KH_VEL_TABLE)
+    if (d->vel == KH_VEL_TABLE || d->vel == KH_VEL_GRID)
         return set_error(KH_ERR_UNSUPPORTED, "kirchhoff_migrate_noalloc: analytic traveltimes only "
                                              "(a table needs device workspace)");
     if (!image || (ntr > 0 && (!sx || !rx || !traces)) || (ntr > 0 && d->dim == 3 && (!sy || !ry)))

@@ -58,6 +58,22 @@ struct kh_plan_s {
     unsigned* ws_hmax = nullptr;  // [1] largest horizontal distance (float bits)
     int tab_nh = 0, tab_nz = 0;
     double tab_tmin = 0.0, tab_scale = 1.0;
+    // gridded model (KH_VEL_GRID): the node grid, per-location FP32 tables, the locations, the
+    // rounds each took, the FP64 slowness, and per (location, tile) time bounds
+    kh_grid grid{};
+    int grid_nloc = 0;
+    int grid_m = 0;               // depth nodes every grid_m image samples
+    int grid_zoff = 0;            // node row of the first image depth
+    float* ws_gtab = nullptr;
+    size_t cap_gtab = 0;
+    float* ws_gloc = nullptr;
+    size_t cap_gloc = 0;
+    int* ws_grounds = nullptr;
+    size_t cap_grounds = 0;
+    double* ws_gslow = nullptr;
+    size_t cap_gslow = 0;
+    float2* ws_gbnd = nullptr;
+    size_t cap_gbnd = 0;
     // profiling: event pairs recorded around main kernels while enabled
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -107,6 +123,9 @@ kh_status plan_check_headers(const kh_plan_s* p, int ntr, const float* sx, const
 cudaError_t launch_pad(int ntr, int nt, long long ld, int esize, const void* src, void* dst, cudaStream_t s);
 // FP32 rows of nt samples to SamplePair rows of ld (even) pairs.
 cudaError_t launch_pairs(int ntr, int nt, int ld, const void* src, void* dst, cudaStream_t s);
+// KH_VEL_GRID migration: location indices of the sorted traces and the tile bounds of the
+// launch's tiling; fills the table fields of g.
+kh_status grid_prepare(kh_plan_s* p, const TileShape& t, GeomParams& g, cudaStream_t s);
 cudaError_t noalloc_bin(int ntr, const float* sx, const float* sy, const float* rx, const float* ry,
                         const kh_desc& d, int* bin, int* perm, int* bin_start, float4* hdr,
                         float2* mid, cudaStream_t s);

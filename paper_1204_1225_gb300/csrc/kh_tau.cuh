@@ -192,11 +192,30 @@ __device__ __forceinline__ float leg_delta_grad_m(float dP, float dh2, const flo
 
 // Sample window [lo, hi] of one trace over a tile box, from the time bounds of both legs with
 // a slack of 2 + 2e-4 |tau| samples for FP32 rounding; false if no valid sample can reach the box.
+// Sample window [lo, hi] of a trace whose two-way time lies in [tsum_lo, tsum_hi] over the tile
+// (seconds; FP32), widened by 2 samples plus a relative 2e-4 and g.tslack and clipped to
+// [0, nt - 1]; *clipped reports a clip.  False when the window misses the trace.
+__device__ __forceinline__ bool sample_window(float tsum_lo, float tsum_hi, const GeomParams& g, int& lo, int& hi,
+                                              bool* clipped)
+{
+    const float inv_dt = __fdiv_rn(1.f, g.dt);
+    const float tlo = __fmul_rn(__fsub_rn(tsum_lo, g.t0), inv_dt);
+    const float thi = __fmul_rn(__fsub_rn(tsum_hi, g.t0), inv_dt);
+    const float slo = __fadd_rn(__fadd_rn(2.f, __fmul_rn(2e-4f, fabsf(tlo))), g.tslack);
+    const float shi = __fadd_rn(__fadd_rn(2.f, __fmul_rn(2e-4f, fabsf(thi))), g.tslack);
+    const float flo = floorf(tlo - slo), fhi = ceilf(thi + shi) + 1.f;
+    if (!(fhi >= 1.f && flo <= (float)(g.nt - 2))) return false;   // also NaN
+    lo = flo < 0.f ? 0 : (int)flo;
+    hi = fhi > (float)(g.nt - 1) ? g.nt - 1 : (int)fhi;
+    if (clipped) *clipped = flo < 0.f || fhi > (float)(g.nt - 1);
+    return hi > lo;
+}
+
 __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box, int vel,
                                              const GeomParams& g, int& lo, int& hi, bool* clipped = nullptr,
                                              const PstmTile* pt = nullptr)
 {
-    const float v0 = (float)g.v0, kf = (float)g.k, inv_dt = __fdiv_rn(1.f, g.dt);
+    const float v0 = (float)g.v0, kf = (float)g.k;
     float hs0, hs1, hr0, hr1, ts0, ts1, tr0, tr1;
     rect_dist(h.x, h.y, box.xlo, box.xhi, box.ylo, box.yhi, hs0, hs1);
     rect_dist(h.z, h.w, box.xlo, box.xhi, box.ylo, box.yhi, hr0, hr1);
@@ -217,16 +236,7 @@ __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box
         leg_bounds(hs0, hs1, box.zlo, box.zhi, vel, v0, kf, ts0, ts1);
         leg_bounds(hr0, hr1, box.zlo, box.zhi, vel, v0, kf, tr0, tr1);
     }
-    const float tlo = __fmul_rn(__fsub_rn(__fadd_rn(ts0, tr0), g.t0), inv_dt);
-    const float thi = __fmul_rn(__fsub_rn(__fadd_rn(ts1, tr1), g.t0), inv_dt);
-    const float slo = __fadd_rn(__fadd_rn(2.f, __fmul_rn(2e-4f, fabsf(tlo))), g.tslack);
-    const float shi = __fadd_rn(__fadd_rn(2.f, __fmul_rn(2e-4f, fabsf(thi))), g.tslack);
-    const float flo = floorf(tlo - slo), fhi = ceilf(thi + shi) + 1.f;
-    if (!(fhi >= 1.f && flo <= (float)(g.nt - 2))) return false;   // also NaN
-    lo = flo < 0.f ? 0 : (int)flo;
-    hi = fhi > (float)(g.nt - 1) ? g.nt - 1 : (int)fhi;
-    if (clipped) *clipped = flo < 0.f || fhi > (float)(g.nt - 1);
-    return hi > lo;
+    return sample_window(__fadd_rn(ts0, tr0), __fadd_rn(ts1, tr1), g, lo, hi, clipped);
 }
 
 // Tile box (FP32, for the window bounds) and FP64 centre (reference point) of the tile

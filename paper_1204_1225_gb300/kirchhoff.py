@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libkirchhoff.so")
 KH_OK, KH_ERR_INVALID_ARG, KH_ERR_UNSUPPORTED, KH_ERR_OOM, KH_ERR_CUDA, KH_ERR_TIMEOUT, \
     KH_ERR_INTERNAL = range(7)
 KH_F32, KH_F16, KH_BF16, KH_U16 = 0, 1, 2, 3
-KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE, KH_VEL_PSTM = 0, 1, 2, 3
+KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE, KH_VEL_PSTM, KH_VEL_GRID = 0, 1, 2, 3, 4
 KH_W_ONE, KH_W_OBLIQ_SPREAD = 0, 1
 KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE, KH_OPT_BATCH_MODE, KH_OPT_SAMPLE_PAIRS = 1, 2, 3, 4, 5
 KH_OPT_SPATIAL_SORT = 6
@@ -46,6 +46,10 @@ class kh_desc(ctypes.Structure):
                 ("trace_dtype", ctypes.c_int), ("taper", ctypes.c_double)]
 
 
+class kh_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("ox", ctypes.c_double), ("h", ctypes.c_double)]
+
+
 class kh_job(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("ntr", ctypes.c_int), ("sx", ctypes.c_void_p),
                 ("sy", ctypes.c_void_p), ("rx", ctypes.c_void_p), ("ry", ctypes.c_void_p),
@@ -62,7 +66,8 @@ EXPORTS = ["kirchhoff_create", "kirchhoff_destroy", "kirchhoff_migrate", "kirchh
            "kirchhoff_set_option", "kirchhoff_launch_count", "kirchhoff_last_error",
            "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read",
            "kirchhoff_migrate_noalloc", "kirchhoff_fit_report", "kirchhoff_staging_stats",
-           "kirchhoff_cell_grid", "kirchhoff_bin_sort", "kirchhoff_semblance"]
+           "kirchhoff_cell_grid", "kirchhoff_bin_sort", "kirchhoff_semblance", "kirchhoff_grid_layout",
+           "kirchhoff_grid_tables", "kirchhoff_grid_read"]
 
 
 def lib(path: str = LIB_PATH):
@@ -105,6 +110,10 @@ def lib(path: str = LIB_PATH):
                                               D, D, D]
             L.kirchhoff_bin_sort.argtypes = [P, I, P, P, P, P, P, P, P]
             L.kirchhoff_semblance.argtypes = [P, P, D, D, P, P]
+            L.kirchhoff_grid_layout.argtypes = [ctypes.POINTER(kh_desc), I, ctypes.c_double, ctypes.c_double, I,
+                                                ctypes.POINTER(kh_grid)]
+            L.kirchhoff_grid_tables.argtypes = [P, ctypes.POINTER(kh_grid), P, I, P, P]
+            L.kirchhoff_grid_read.argtypes = [P, P, P, ctypes.POINTER(I), P]
             for name in EXPORTS:
                 getattr(L, name).restype = S
             L.kirchhoff_launch_count.restype = ctypes.c_longlong
@@ -176,10 +185,11 @@ def desc_from(s, trace_dtype=torch.float32, vel=None, table_spacing=None,
               table_dtype="u16") -> kh_desc:
     """kh_desc from any object with the survey attributes (dim, nx, ..., nt, t0, dt).
     ``s.vel == "table"`` selects the radial traveltime table of the v0 + k z model;
-    ``table_dtype`` is "f32", "f16" or "u16" (or torch.float32 / torch.float16)."""
+    ``table_dtype`` is "f32", "f16" or "u16" (or torch.float32 / torch.float16); ``s.vel == "grid"``
+    selects the per-location tables of a gridded model (kirchhoff_grid_tables)."""
     if vel is None:
         vel = {"const": KH_VEL_CONST, "linear": KH_VEL_LINEAR_Z, "table": KH_VEL_TABLE,
-               "pstm": KH_VEL_PSTM}[s.vel]
+               "pstm": KH_VEL_PSTM, "grid": KH_VEL_GRID}[s.vel]
     if table_spacing is None:
         table_spacing = float(getattr(s, "table_spacing", 25.0))
     return kh_desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
@@ -312,6 +322,25 @@ def kirchhoff_semblance(plan, image, bin_weight=None, grad_image=None, stream=No
     return float(out[0]), float(out[1]), float(out[2])
 
 
+def kirchhoff_grid_layout(desc: kh_desc, m: int, xmin: float, xmax: float, margin: int = 1) -> kh_grid:
+    out = kh_grid()
+    _check(lib().kirchhoff_grid_layout(ctypes.byref(desc), int(m), float(xmin), float(xmax), int(margin),
+                                       ctypes.byref(out)))
+    return out
+
+
+def kirchhoff_grid_tables(plan, grid: kh_grid, v, nloc, loc_x, stream=None) -> None:
+    _check(lib().kirchhoff_grid_tables(ctypes.c_void_p(plan), ctypes.byref(grid), _ptr(v), int(nloc), _ptr(loc_x),
+                                       _stream(stream)))
+
+
+def kirchhoff_grid_read(plan, tables=None, rounds=None, stream=None) -> int:
+    n = ctypes.c_int(0)
+    _check(lib().kirchhoff_grid_read(ctypes.c_void_p(plan), _ptr(tables), _ptr(rounds), ctypes.byref(n),
+                                     _stream(stream)))
+    return n.value
+
+
 def kirchhoff_staging_stats(plan, stream=None):
     """(traces examined, traces staged, CTAs) of the staging warps since the previous read,
     while profiling is enabled; synchronises the stream."""
@@ -399,6 +428,9 @@ class Plan:
         if tile is not None:
             cx, cy, cz = tile
             kirchhoff_set_option(self.handle, KH_OPT_TILE, cx | (cy << 10) | (cz << 20))
+        self.grid = None
+        if self.desc.vel == KH_VEL_GRID and getattr(s, "grid_v", None) is not None:
+            self.set_grid(s.grid_v, s.grid_ox, s.grid_h, locations(s))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -438,6 +470,28 @@ class Plan:
             out = torch.empty((hdr.ntr, self.nt), dtype=torch.float32, device=image.device)
         kirchhoff_demigrate(self.handle, hdr.ntr, *hdr.args(), image, out, stream)
         return out
+
+    def set_grid(self, v, ox: float, h: float, loc_x, stream=None):
+        """First-arrival tables of the gridded model v [nx, nz] (m/s) on the nodes (ox + i h, j h)
+        for the increasing surface positions loc_x (kirchhoff_grid_tables)."""
+        v = torch.as_tensor(v, dtype=torch.float32).to(f"cuda:{self.device}").contiguous()
+        loc = torch.as_tensor(loc_x, dtype=torch.float32).to(f"cuda:{self.device}").contiguous()
+        if v.dim() != 2:
+            raise ValueError("kirchhoff: the gridded model must be [nx, nz]")
+        g = kh_grid(int(v.shape[0]), int(v.shape[1]), float(ox), float(h))
+        kirchhoff_grid_tables(self.handle, g, v, loc.numel(), loc, stream)
+        self.grid = g
+        self.grid_nloc = loc.numel()
+
+    def grid_tables(self, stream=None):
+        """(tables float32 [nloc, nx, nz], rounds int32 [nloc]) of the plan's gridded model."""
+        if self.grid is None:
+            raise ValueError("kirchhoff: the plan has no gridded-model tables")
+        dev = f"cuda:{self.device}"
+        T = torch.empty((self.grid_nloc, self.grid.nx, self.grid.nz), dtype=torch.float32, device=dev)
+        r = torch.empty(self.grid_nloc, dtype=torch.int32, device=dev)
+        kirchhoff_grid_read(self.handle, T, r, stream)
+        return T, r
 
     def velocity_grad(self, hdr: Headers, image, traces, out=None, stream=None):
         specs = _header_specs(hdr) + [(image, "image", torch.float32, None, self.image_shape),
@@ -500,6 +554,13 @@ class Plan:
     @property
     def launches(self) -> int:
         return kirchhoff_launch_count(self.handle)
+
+
+def locations(s):
+    """The distinct surface positions (source and receiver x) of a 2D survey's traces, increasing
+    (float32): the locations of its gridded-model tables."""
+    import numpy as np
+    return np.unique(np.concatenate([np.asarray(s.sx, np.float32), np.asarray(s.rx, np.float32)]))
 
 
 def arrival_times_fn(plan: "Plan"):

@@ -59,7 +59,9 @@ PIPE_MIX = {
     "3d-vz-100k-256cube": {"issue": 33.30, "fma": 21.37, "alu": 3.77, "xu": 3.15, "lsu": 3.37},
     "3d-vz-10k-256cube": {"issue": 33.30, "fma": 21.37, "alu": 3.77, "xu": 3.15, "lsu": 3.37},
     "3d-vz-40k-128cube": {"issue": 34.71, "fma": 22.81, "alu": 3.68, "xu": 3.20, "lsu": 3.42},
-    "25d-vz-20k-512x400": {"issue": 35.67, "fma": 24.02, "alu": 3.91, "xu": 2.37, "lsu": 3.75},
+    "25d-vz-20k-512x400": {"issue": 36.09, "fma": 23.96, "alu": 4.25, "xu": 2.37, "lsu": 3.75},
+    # gridded v(x, z): per-location first-arrival tables read from L2 (k_migrate<grid, one, fast, sample pairs, M=4>)
+    "25d-vxz-20k-512x400": {"issue": 19.53, "fma": 11.24, "alu": 3.49, "xu": 0.004, "lsu": 3.24},
     # mixed precision: 16-bit radial tables + FP16 traces (k_migrate<table, obliquity, FP16, M=2, table type>)
     "3d-vz-100k-256cube-table-u16-f16": {"issue": 30.67, "fma": 16.37, "alu": 5.16, "xu": 2.20, "lsu": 5.40},
     "3d-vz-10k-256cube-table-u16-f16": {"issue": 30.67, "fma": 16.37, "alu": 5.16, "xu": 2.20, "lsu": 5.40},
@@ -83,7 +85,8 @@ PIPE_MIX = {
 TRAFFIC = {
     "3d-vz-10k-256cube": 86816256 + 1025687552,
     "3d-vz-40k-128cube": 281054208 + 111904000,
-    "25d-vz-20k-512x400": 91481600 + 2949632,
+    "25d-vz-20k-512x400": 91543808 + 2981376,
+    "25d-vxz-20k-512x400": 139767552 + 5328640,
     "3d-vz-10k-256cube-demigrate": 4820799488 + 8277082112,
     "3d-vz-10k-256cube-vgrad": 1127874560 + 15597568,
     "3d-vz-10k-256cube-table-u16-f16": 37533696 + 1023990784,
@@ -114,6 +117,7 @@ def workloads():
         "3d-vz-10k-256cube": lambda: sv.survey_3d_gradient(ntr=10_000, n=256),
         "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
         "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
+        "25d-vxz-20k-512x400": lambda: sv.survey_25d_vxz(),
         "25d-velan-4608tr-128x100": lambda: sv.survey_25d_velan(),
         "3d-pstm-100k-256cube": lambda: sv.survey_3d_gradient().replace(
             vel="pstm", oz=0.0, dz=0.012, name="3d-pstm-100000tr-256x256x256t"),
@@ -419,11 +423,19 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
     spatial_sort = bool(args.spatial_sort) if spatial_sort is None else spatial_sort
     tdt = _TDT[trace_dtype]
     s_run = s.replace(vel="table") if vel == "table" else s
-    plan = kh.Plan(s_run, fast_math=bool(args.fast_math), trace_dtype=tdt, table_dtype=table_dtype)
+    grid_rec = None
+    if s.vel == "grid":
+        # gridded model: the per-location first-arrival tables are built once per model (timed
+        # here on their own); the steps migrate with them
+        plan = kh.Plan(s_run.replace(grid_v=None), fast_math=bool(args.fast_math), trace_dtype=tdt)
+        grid_rec = time_grid_tables(plan, s, dev)
+    else:
+        plan = kh.Plan(s_run, fast_math=bool(args.fast_math), trace_dtype=tdt, table_dtype=table_dtype)
     plan.set_spatial_sort(spatial_sort)
     if "hdr" not in cache:
         cache["hdr"] = kh.Headers.of(s, device=dev)
-        cache["traces"] = synth_traces(s, kh.Plan(s), dev).contiguous()
+        s_syn = s.replace(vel="linear", grid_v=None) if s.vel == "grid" else s   # data content: background model
+        cache["traces"] = synth_traces(s_syn, kh.Plan(s_syn), dev).contiguous()
         cache["count"] = plan.count(cache["hdr"])
     hdr = cache["hdr"]
     traces = cache["traces"].to(tdt).contiguous()
@@ -564,11 +576,16 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": s.name, "operator": op, "image": list(plan.image_shape),
                    "ntr": s.ntr, "nt": s.nt,
-                   "velocity": f"{s.vel} v0={s.v0} k={s.k}", "weight": s.weight,
+                   "velocity": (f"{s.vel} v0={s.v0} k={s.k}" if s.vel != "grid" else
+                                f"gridded v(x, z) on {s.grid_v.shape[0]}x{s.grid_v.shape[1]} nodes of "
+                                f"{s.grid_h:g} m (v0 + k z = {s.v0} + {s.k} z with a low-velocity lens)"),
+                   "weight": s.weight,
                    "aperture_m": s.aperture, "contributions_per_step": contrib,
                    "fast_math": bool(args.fast_math), "trace_storage": trace_dtype,
-                   "traveltimes": "analytic" if vel == "analytic" else f"table ({table_dtype}, "
-                                  f"{s.table_spacing:g} m)",
+                   "traveltimes": ("per-location first-arrival tables (FP64 eikonal, FP32 storage)"
+                                   if s.vel == "grid" else "analytic" if vel == "analytic" else
+                                   f"table ({table_dtype}, {s.table_spacing:g} m)"),
+                   "eikonal_tables": grid_rec,
                    "l2": "inputs larger than L2 (traces %.0f MB, image %.0f MB)" % (
                        tbytes / 1e6, image.numel() * 4 / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single",
@@ -724,6 +741,29 @@ def run_velan(args, s, ws, rank, local, dev):
     }
 
 
+def time_grid_tables(plan, s, dev, reps: int = 3):
+    """Builds the plan's first-arrival tables `reps` + 1 times (the first untimed) and reports the
+    median wall time of kirchhoff_grid_tables (a synchronous setup call), with the work it did."""
+    from paper_1204_1225_gb300 import kirchhoff as kh
+    loc = kh.locations(s)
+    times = []
+    for i in range(reps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        plan.set_grid(s.grid_v, s.grid_ox, s.grid_h, loc)
+        if i:
+            times.append((time.perf_counter() - t0) * 1e3)
+    _, rounds = plan.grid_tables()
+    r = rounds.double()
+    ms = statistics.median(times)
+    nodes = int(s.grid_v.size)
+    return {"ms": ms, "locations": int(loc.size), "nodes_per_location": nodes,
+            "rounds_mean": float(r.mean()), "rounds_max": int(r.max()),
+            "location_nodes_per_s": loc.size * nodes / (ms / 1e3),
+            "what": "kirchhoff_grid_tables wall time: host checks of the model and locations, "
+                    "one CTA per location sweeping in FP64, table store"}
+
+
 def _form(line):
     """The fields of a form's own measurement kept in the headline line."""
     keep = ("value", "unit", "steps", "warmup", "ms_per_step", "roofline", "parity", "clocks",
@@ -731,7 +771,7 @@ def _form(line):
     out = {k: line[k] for k in keep if k in line}
     out["config"] = {k: v for k, v in line["config"].items()
                      if k in ("workload", "operator", "trace_storage", "traveltimes", "contributions_per_step",
-                              "batch_mode", "work_items", "staging_per_cta")}
+                              "batch_mode", "work_items", "staging_per_cta", "eikonal_tables", "velocity")}
     return out
 
 
@@ -758,6 +798,17 @@ def run_forms(args, s, ws, rank, local, dev, cache, head):
     r = run_single(args, s_t, ws, rank, local, dev, tcache, **k)
     if rank == 0:
         forms["time_migration"] = _form(r)
+    # a laterally varying model on the 2.5D line: migration with the per-location first-arrival
+    # tables of the eikonal solver, against the analytic v(z) path on the same geometry
+    for wl, name in (("25d-vxz-20k-512x400", "gridded_vxz_tables"), ("25d-vz-20k-512x400", "gridded_vxz_background")):
+        gargs = argparse.Namespace(**vars(args))
+        gargs.workload = wl
+        r = run_single(gargs, workloads()[wl](), ws, rank, local, dev, {}, **k)
+        if rank == 0:
+            forms[name] = _form(r)
+    if rank == 0:
+        forms["gridded_vxz_tables"]["speedup_vs_analytic_vz"] = (forms["gridded_vxz_tables"]["value"] /
+                                                                 forms["gridded_vxz_background"]["value"])
     cache.clear()
     torch.cuda.empty_cache()
     surveys = workloads()["batch64-3d-vz"]()

@@ -225,8 +225,9 @@ KH_API kh_status kirchhoff_semblance(kh_plan p, const float* image, const double
  * with h = m dz (m = 1, 2 or 4, to 1e-9 relative) and the image's oz a non-negative multiple of h
  * (to 1e-9), so that image depth iz lies at node row oz/h + iz/m.  The columns must cover every
  * image column and every location; nz >= oz/h + 16 ceil(nz_image / 16) / m + 1 (one node below
- * the deepest depth a migration tile evaluates); nx, nz >= 2, nx nz <= 28000 (the solver keeps a
- * location's grid in FP64 in one CTA's shared memory).
+ * the deepest depth a migration tile evaluates); nx, nz >= 2, nx nz <= 28000 and
+ * 8.125 nx nz + 4 nx <= 232192 bytes (the solver keeps a location's grid in FP64, one bit per node
+ * and one FP32 offset per column in one CTA's shared memory).
  *
  * kirchhoff_grid_layout (host only): the smallest such grid for descriptor `d` (vel KH_VEL_GRID)
  * and node spacing multiple m whose columns cover the image and [xmin, xmax] (the locations'
@@ -234,7 +235,7 @@ KH_API kh_status kirchhoff_semblance(kh_plan p, const float* image, const double
  *
  * kirchhoff_grid_tables: for the model v (DEVICE FP32 [grid->nx][grid->nz], m/s, finite, > 0) and
  * nloc >= 1 locations loc_x (DEVICE FP32 [nloc], strictly increasing, inside the grid's columns),
- * builds in the plan one FP32 table [nx][nz] per location, on one CTA per location:
+ * builds in the plan one FP32 table per location, on one CTA per location:
  *   - factorisation T = T0 + tau, T0 = s0 |x - x_s| with s0 the slowness at the location (linear
  *     along the surface row), which removes the point-source singularity (additive factor of
  *     Luo and Qian, 2012); constant velocity is reproduced to rounding;
@@ -244,12 +245,15 @@ KH_API kh_status kirchhoff_semblance(kh_plan p, const float* image, const double
  *   - fast sweeping (Zhao, 2005): Gauss-Seidel passes in the orderings (i up, j up), (i down,
  *     j up), (i down, j down), (i up, j down), each pass as a wavefront of anti-diagonals (the
  *     nodes of one anti-diagonal are independent within a pass, so the result is that of the
- *     sequential pass); rounds of four passes until a round's largest decrease is <= 1e-9 s, at
+ *     sequential pass); rounds of four passes until a round's largest decrease is <= 1e-7 s, at
  *     most 64 rounds; a node is recomputed only after one of its neighbours changed (the same
  *     result with less work);
  *   - the nodes with |x_i - x_s| <= 2 h in rows 0..2 keep the straight-ray time
  *     |x - x_s| (s0 + s(x)) / 2 and are not updated;
- *   - IEEE FP64 throughout, one rounding per operation in the order written, then rounded to FP32.
+ *   - tau, the node equation and the convergence test in FP64 (tau accumulates along every
+ *     path), the equation's square root an FP32 estimate refined by one FP64 Newton step; the
+ *     shift h grad T0 in FP32 from the FP64 offset x - x_s (relative error below 5e-7, a few
+ *     1e-9 s per node); stored as FP32.
  * Synchronises the stream.  Errors: KH_ERR_INVALID_ARG (NULL pointers, a grid that breaks the
  * rules above, v not finite and > 0, locations not increasing or outside the columns, a plan that
  * is not KH_VEL_GRID), KH_ERR_UNSUPPORTED (a location that did not settle in 64 rounds).
@@ -258,7 +262,8 @@ KH_API kh_status kirchhoff_semblance(kh_plan p, const float* image, const double
  * KH_ERR_INVALID_ARG.  Per image tile and location the migration takes the smallest and largest
  * node value the tile interpolates between as the time window's bounds.
  *
- * kirchhoff_grid_read: copies the plan's tables (DEVICE FP32 [nloc][nx][nz]; NULL skips) and the
+ * kirchhoff_grid_read: copies the plan's tables (DEVICE FP32 [nloc][nz][nx], row-major with x
+ * fastest, the layout the migration reads; NULL skips) and the
  * rounds each location took (DEVICE int [nloc]; NULL skips); *nloc (HOST, may be NULL) = nloc.
  * Synchronises the stream. */
 typedef struct {

@@ -229,9 +229,9 @@ def arrival_times(points, s, trace_idx) -> np.ndarray:
 
 MAX_ROUNDS = 64
 # A round of sweeps whose largest decrease is at most this many seconds ends the iteration: the
-# remaining corrections shrink geometrically from round to round and are far below the
-# resolution of an FP32 table (about 1e-7 s at 1 s).
-TOL = 1e-9
+# corrections shrink by about two orders of magnitude from round to round, so what remains is a
+# few 1e-9 s, below the resolution of an FP32 table (about 1e-7 s at 1 s).
+TOL = 1e-7
 
 
 def eikonal(v, ox: float, h: float, xs: float, max_rounds: int = MAX_ROUNDS, tol: float = TOL):

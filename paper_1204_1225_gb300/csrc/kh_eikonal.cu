@@ -10,13 +10,20 @@
 //   Godunov upwind node equation with shifted neighbours c = tau_neighbour -/+ h dT0/dx, closed-form
 //   solve; fast sweeping (Zhao 2005): four Gauss-Seidel orderings per round, rounds until the
 //   largest decrease of a round is at most EK_TOL.
+// Precision: tau, its neighbour values, the node equation and the round's decrease are FP64 (tau
+// accumulates along every ray path); the shift h grad T0 = h s0 (x - x_s) / |x - x_s| is a
+// geometric factor evaluated per update in FP32 from the FP64 offset (relative error a few
+// 1e-7, i.e. a few 1e-9 s per node on a 20 m grid), and the node equation's square root is an
+// FP32 estimate refined by one FP64 Newton step (relative error about 1e-15): the GPU's FP64
+// pipe, a sixty-fourth of its FP32 rate, is kept for the accumulation.  Unreached nodes hold a
+// large finite value, so an update from unreached neighbours needs no test: it cannot decrease.
 // A pass sweeps anti-diagonals i' + j' = d (i', j' the indices in the pass's directions): a node
 // depends on its upwind neighbours, which lie on diagonal d - 1, and reads its downwind ones from
 // diagonal d + 1, not yet swept, exactly as in the sequential raster pass, so the nodes of one
 // diagonal update in parallel with a barrier between diagonals and the result is the sequential
 // one.  A node is recomputed only when one of its neighbours changed since it was last computed
 // (one dirty bit per node): with unchanged neighbours its update would return the same value.
-// Every operation is one IEEE FP64 operation (explicit rounding intrinsics, no contraction).
+// The FP64 operations are single IEEE operations (explicit rounding intrinsics, no contraction).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -30,7 +37,9 @@ namespace kh {
 
 constexpr int EK_THREADS = 256;
 constexpr int EK_MAX_ROUNDS = 64;
-constexpr double EK_TOL = 1e-9;   // seconds: far below the FP32 resolution of a stored time
+// A round whose largest decrease is at most EK_TOL seconds ends the sweeps: later rounds would
+// change the times by about 1 % of that, below the FP32 resolution of a stored time.
+constexpr double EK_TOL = 1e-7;
 
 static kh_status errf(kh_status st, const char* fmt, ...)
 {
@@ -55,33 +64,47 @@ static cudaError_t grow_ws(T*& ptr, size_t& cap, size_t n)
     return e;
 }
 
-__global__ void k_grid_slowness(long long n, const float* __restrict__ v, double* __restrict__ s)
+constexpr double EK_UNREACHED = 1e30;   // seconds; ulp(1e30) dwarfs any shift or h s
+
+// s = 1 / v, f h = h s and 2 (f h)^2 per node (FP64).
+__global__ void k_grid_slowness(long long n, const float* __restrict__ v, double h, double* __restrict__ s,
+                                double2* __restrict__ fh)
 {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-        s[q] = __ddiv_rn(1.0, (double)v[q]);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const double sq = __ddiv_rn(1.0, (double)v[q]);
+        const double f = __dmul_rn(h, sq);
+        s[q] = sq;
+        fh[q] = make_double2(f, __dmul_rn(2.0, __dmul_rn(f, f)));
+    }
 }
 
-// Upwind update of a node from its shifted neighbours a (x) and b (z); fh = h s.
-__device__ __forceinline__ double ek_update(double a, double b, double fh)
+// Upwind update of a node from its shifted neighbours a (x) and b (z); fh = (h s, 2 (h s)^2).
+// Two-sided case: |a - b| < h s, so the discriminant lies in ((h s)^2, 2 (h s)^2] and its root is
+// well conditioned: FP32 estimate y = rsqrt, r = disc y, then one Newton step in FP64.
+__device__ __forceinline__ double ek_update(double a, double b, double2 fh)
 {
-    const double d = __dsub_rn(a, b);
-    if (fabs(d) >= fh) return __dadd_rn(fmin(a, b), fh);
-    const double disc = __dsub_rn(__dmul_rn(2.0, __dmul_rn(fh, fh)), __dmul_rn(d, d));
-    return __dmul_rn(0.5, __dadd_rn(__dadd_rn(a, b), __dsqrt_rn(disc)));
+    const double d = a - b;
+    if (fabs(d) >= fh.x) return fmin(a, b) + fh.x;
+    const double disc = fma(-d, d, fh.y);
+    const float y = rsqrtf((float)disc);
+    const double r0 = (double)((float)disc * y);
+    const double r = fma(fma(-r0, r0, disc), (double)(0.5f * y), r0);
+    return 0.5 * ((a + b) + r);
 }
 
 // One CTA per location: tau [nx][nz] FP64 and one dirty bit per node in shared memory.
 __global__ void __launch_bounds__(EK_THREADS)
-    k_eikonal(int nx, int nz, double ox, double h, const double* __restrict__ slow, const float* __restrict__ loc_x,
-              int max_rounds, double tol, float* __restrict__ tables, int* __restrict__ rounds_out)
+    k_eikonal(int nx, int nz, double ox, double h, const double* __restrict__ slow, const double2* __restrict__ fhs,
+              const float* __restrict__ loc_x, int max_rounds, double tol, float* __restrict__ tables,
+              int* __restrict__ rounds_out)
 {
     extern __shared__ __align__(16) unsigned char ek_smem[];
     __shared__ double red[EK_THREADS / 32];
     const int n = nx * nz;
     double* tau = reinterpret_cast<double*>(ek_smem);
     unsigned* dirty = reinterpret_cast<unsigned*>(tau + n);
+    float* dxf = reinterpret_cast<float*>(dirty + (n + 31) / 32);   // [nx]: x_i - x_s, FP64 rounded to FP32
     const int tid = threadIdx.x;
-    const double inf = __longlong_as_double(0x7ff0000000000000LL);
     const double xs = (double)loc_x[blockIdx.x];
     // s0: the surface row's slowness, linear between the two nodes around x_s
     const double u = __ddiv_rn(__dsub_rn(xs, ox), h);
@@ -90,13 +113,23 @@ __global__ void __launch_bounds__(EK_THREADS)
     const double f = __dsub_rn(u, (double)i0);
     const double sa = slow[(long long)i0 * nz], sb = slow[(long long)(i0 + 1) * nz];
     const double s0 = __dadd_rn(sa, __dmul_rn(f, __dsub_rn(sb, sa)));
-    const double hs0 = __dmul_rn(h, s0), h2 = __dmul_rn(2.0, h);
+    const double h2 = __dmul_rn(2.0, h);
+    const float hs0f = (float)__dmul_rn(h, s0), hf = (float)h;
+    for (int i = tid; i < nx; i += EK_THREADS) dxf[i] = (float)__dsub_rn(__dadd_rn(ox, __dmul_rn((double)i, h)), xs);
+    // the columns of the source box, |x_i - x_s| <= 2 h (rows 0..2)
+    const int ib0 = max(0, (int)floor(__ddiv_rn(__dsub_rn(xs, h2) - ox, h)) - 1);
+    int bx0 = nx, bx1 = -1;
+    for (int i = ib0; i < nx && i <= ib0 + 6; ++i)
+        if (fabs(__dsub_rn(__dadd_rn(ox, __dmul_rn((double)i, h)), xs)) <= h2) {
+            bx0 = min(bx0, i);
+            bx1 = max(bx1, i);
+        }
     // source box: straight ray with the trapezoid slowness, T = s0 dist + tau = dist (s0 + s) / 2
     for (int q = tid; q < n; q += EK_THREADS) {
         const int i = q / nz, j = q - i * nz;
         const double dx = __dsub_rn(__dadd_rn(ox, __dmul_rn((double)i, h)), xs);
-        double t = inf;
-        if (fabs(dx) <= h2 && j <= 2) {
+        double t = EK_UNREACHED;
+        if (i >= bx0 && i <= bx1 && j <= 2) {
             const double zj = __dmul_rn((double)j, h);
             const double dist = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(zj, zj)));
             t = __dmul_rn(dist, __dmul_rn(0.5, __dsub_rn(slow[q], s0)));
@@ -120,21 +153,19 @@ __global__ void __launch_bounds__(EK_THREADS)
                     const unsigned bit = 1u << (q & 31);
                     if (!(dirty[q >> 5] & bit)) continue;
                     atomicAnd(&dirty[q >> 5], ~bit);
-                    const double dx = __dsub_rn(__dadd_rn(ox, __dmul_rn((double)i, h)), xs);
-                    if (j <= 2 && fabs(dx) <= h2) continue;   // the source box is fixed
-                    const double zj = __dmul_rn((double)j, h);
-                    const double g = __ddiv_rn(hs0, __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(zj, zj))));
-                    const double gx = __dmul_rn(g, dx), gz = __dmul_rn(g, zj);   // h grad T0
-                    const double cl = i > 0 ? __dsub_rn(tau[q - nz], gx) : inf;
-                    const double cr = i < nx - 1 ? __dadd_rn(tau[q + nz], gx) : inf;
-                    const double cu = j > 0 ? __dsub_rn(tau[q - 1], gz) : inf;
-                    const double cd = j < nz - 1 ? __dadd_rn(tau[q + 1], gz) : inf;
-                    const double a = fmin(cl, cr), b = fmin(cu, cd);
-                    if (a == inf && b == inf) continue;
-                    const double t = ek_update(a, b, __dmul_rn(h, slow[q]));
+                    if (j <= 2 && i >= bx0 && i <= bx1) continue;   // the source box is fixed
+                    // h grad T0 = h s0 (dx, z) / r in FP32
+                    const float xf = dxf[i], zf = (float)j * hf;
+                    const float gf = hs0f * rsqrtf(fmaf(xf, xf, zf * zf));
+                    const double gx = (double)(gf * xf), gz = (double)(gf * zf);
+                    const double cl = i > 0 ? tau[q - nz] - gx : EK_UNREACHED;
+                    const double cr = i < nx - 1 ? tau[q + nz] + gx : EK_UNREACHED;
+                    const double cu = j > 0 ? tau[q - 1] - gz : EK_UNREACHED;
+                    const double cd = j < nz - 1 ? tau[q + 1] + gz : EK_UNREACHED;
+                    const double t = ek_update(fmin(cl, cr), fmin(cu, cd), fhs[q]);
                     const double old = tau[q];
                     if (t < old) {
-                        most = fmax(most, __dsub_rn(old, t));
+                        most = fmax(most, old - t);
                         tau[q] = t;
                         if (i > 0) atomicOr(&dirty[(q - nz) >> 5], 1u << ((q - nz) & 31));
                         if (i < nx - 1) atomicOr(&dirty[(q + nz) >> 5], 1u << ((q + nz) & 31));
@@ -157,13 +188,14 @@ __global__ void __launch_bounds__(EK_THREADS)
             break;
         }
     }
+    // tables [row][column] (x fastest): the migration's warps read consecutive nodes of a row
     float* out = tables + (long long)blockIdx.x * n;
-    for (int q = tid; q < n; q += EK_THREADS) {
-        const int i = q / nz, j = q - i * nz;
+    for (int e = tid; e < n; e += EK_THREADS) {
+        const int j = e / nx, i = e - j * nx, q = i * nz + j;
         const double dx = __dsub_rn(__dadd_rn(ox, __dmul_rn((double)i, h)), xs);
         const double zj = __dmul_rn((double)j, h);
         const double r0 = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(zj, zj)));
-        out[q] = __double2float_rn(__dadd_rn(__dmul_rn(s0, r0), tau[q]));
+        out[e] = __double2float_rn(__dadd_rn(__dmul_rn(s0, r0), tau[q]));
     }
     if (tid == 0) rounds_out[blockIdx.x] = rounds;
 }
@@ -221,7 +253,7 @@ __global__ void k_grid_bounds(GeomParams g, TileShape ts, int nloc, float2* __re
         const int nr = rb - ra + 1, cnt = (cb - ca + 1) * nr;
         const float* T = g.gtab + (long long)l * g.gstride;
         for (int e = lane; e < cnt; e += 32) {
-            const float v = T[(long long)(ca + e / nr) * g.gnz + ra + e % nr];
+            const float v = T[(long long)(ra + e % nr) * g.gnx + ca + e / nr];
             lo = fminf(lo, v);
             hi = fmaxf(hi, v);
         }
@@ -233,13 +265,21 @@ __global__ void k_grid_bounds(GeomParams g, TileShape ts, int nloc, float2* __re
     if (lane == 0) bnd[wid] = make_float2(lo, hi);
 }
 
+// Shared memory of the solver's CTA: tau (FP64), one dirty bit per node, and the FP32 column offsets.
+static size_t grid_smem_bytes(int nx, int nz)
+{
+    const size_t n = (size_t)nx * nz;
+    return n * sizeof(double) + (n + 31) / 32 * sizeof(unsigned) + (size_t)nx * sizeof(float);
+}
+constexpr size_t EK_SMEM_MAX = 227 * 1024 - 256;   // dynamic shared memory of one CTA, with room for the static part
+
 // Node grid rules of a descriptor: m from h, the node row of the first image depth, and the rows
 // a migration needs.  Returns KH_OK or an error with its message set.
 static kh_status grid_rules(const kh_desc& d, const kh_grid& G, int* m_out, int* zoff_out)
 {
     if (d.vel != KH_VEL_GRID || d.dim != 2) return errf(KH_ERR_INVALID_ARG, "the plan is not a 2D KH_VEL_GRID plan");
     if (G.nx < 2 || G.nz < 2) return errf(KH_ERR_INVALID_ARG, "grid needs nx, nz >= 2 (got %d x %d)", G.nx, G.nz);
-    if ((long long)G.nx * G.nz > MAX_GRID_NODES)
+    if ((long long)G.nx * G.nz > MAX_GRID_NODES || grid_smem_bytes(G.nx, G.nz) > EK_SMEM_MAX)
         return errf(KH_ERR_INVALID_ARG, "grid of %d x %d nodes exceeds %d nodes (one CTA's shared memory); "
                     "use a coarser h", G.nx, G.nz, MAX_GRID_NODES);
     if (!(G.h > 0) || !std::isfinite(G.h) || !std::isfinite(G.ox)) return errf(KH_ERR_INVALID_ARG, "grid h must be > 0");
@@ -352,16 +392,18 @@ kh_status kirchhoff_grid_tables(kh_plan p, const kh_grid* grid, const float* v, 
     if ((e = grow_ws(p->ws_gtab, p->cap_gtab, (size_t)nloc * n)) != cudaSuccess ||
         (e = grow_ws(p->ws_gloc, p->cap_gloc, (size_t)nloc)) != cudaSuccess ||
         (e = grow_ws(p->ws_grounds, p->cap_grounds, (size_t)nloc)) != cudaSuccess ||
-        (e = grow_ws(p->ws_gslow, p->cap_gslow, (size_t)n)) != cudaSuccess)
+        (e = grow_ws(p->ws_gslow, p->cap_gslow, (size_t)(3 * n + 2))) != cudaSuccess)
         return set_cuda_error(e, "workspace (traveltime tables)");
     p->grid_nloc = 0;
     e = cudaMemcpyAsync(p->ws_gloc, loc_x, nloc * sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return set_cuda_error(e, "kirchhoff_grid_tables (locations)");
-    k_grid_slowness<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(n, v, p->ws_gslow);
-    const size_t smem = (size_t)n * sizeof(double) + (size_t)((n + 31) / 32) * sizeof(unsigned);
+    // (h s, 2 (h s)^2) per node after s, at an even offset (16-byte aligned double2)
+    double2* fhs = reinterpret_cast<double2*>(p->ws_gslow + (n + 1) / 2 * 2);
+    k_grid_slowness<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(n, v, G.h, p->ws_gslow, fhs);
+    const size_t smem = grid_smem_bytes(G.nx, G.nz);
     e = cudaFuncSetAttribute(k_eikonal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        k_eikonal<<<nloc, EK_THREADS, smem, s>>>(G.nx, G.nz, G.ox, G.h, p->ws_gslow, p->ws_gloc, EK_MAX_ROUNDS, EK_TOL,
+        k_eikonal<<<nloc, EK_THREADS, smem, s>>>(G.nx, G.nz, G.ox, G.h, p->ws_gslow, fhs, p->ws_gloc, EK_MAX_ROUNDS, EK_TOL,
                                                   p->ws_gtab, p->ws_grounds);
         e = cudaGetLastError();
     }

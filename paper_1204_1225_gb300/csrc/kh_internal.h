@@ -140,7 +140,7 @@ struct GeomParams {
     int tm;                  // depth nodes every tm image samples (1, 2 or 4)
     float tslack;            // extra window slack (samples) for the interpolation error
     // per-location first-arrival tables of a gridded model (KH_VEL_GRID, dim 2): FP32 seconds
-    // [nloc][gnx][gnz] (z fastest) on the nodes (gox + i gh, j gh), read from global memory; the
+    // [nloc][gnz][gnx] (x fastest) on the nodes (gox + i gh, j gh), read from global memory; the
     // image depth iz lies at node row gzoff + iz / tm.  gbnd: per (location, tile of the launch)
     // the smallest and largest node value over the nodes the tile's points interpolate between.
     const float* gtab;

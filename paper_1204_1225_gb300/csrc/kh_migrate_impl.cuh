@@ -192,15 +192,16 @@ __device__ __forceinline__ float tab_depth(const float* p, int i)
     return r == 0 ? p[j] : fmaf((float)r * (1.f / M), p[j + 1] - p[j], p[j]);
 }
 
-// One leg's profile at K node rows from its location's table: the lerp in x between the column's
-// two node columns (c0 points at the first row in node column gi; gi + 1 follows gnz later).
+// One leg's profile at K node rows from its location's table ([row][column], x fastest): the lerp
+// in x between the column's two node columns (c0 points at node column gi of the first row; the
+// next row follows gnx later).  The lanes of a warp (consecutive image columns) read a few
+// consecutive nodes of one row per load.
 template <int K>
-__device__ __forceinline__ void grid_profile(const float* __restrict__ c0, int gnz, float fx, float* p)
+__device__ __forceinline__ void grid_profile(const float* __restrict__ c0, int gnx, float fx, float* p)
 {
-    const float* c1 = c0 + gnz;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float a = __ldg(c0 + k), b = __ldg(c1 + k);
+        const float a = __ldg(c0 + k * gnx), b = __ldg(c0 + k * gnx + 1);
         p[k] = fmaf(fx, b - a, a);
     }
 }
@@ -546,7 +547,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     if constexpr (VEL == VK_GRID) {
         const int gi = grid_col(g, ix, &gfx);
         const int jb = min(g.gzoff + izb / LPT, g.gnz - (NZ / LPT + 1));
-        gcol = g.gtab + (long long)gi * g.gnz + jb;
+        gcol = g.gtab + (long long)jb * g.gnx + gi;
     }
 
     bool failed = false;
@@ -630,13 +631,13 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dhs2 = dxs * dxs, dhr2 = dxr * dxr;
                 if ((unsigned)ls != psx) {   // new source location
                     float ps[K];
-                    grid_profile<K>(gcol + (long long)ls * g.gstride, g.gnz, gfx, ps);
+                    grid_profile<K>(gcol + (long long)ls * g.gstride, g.gnx, gfx, ps);
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) my_ts[i * CONSUMERS] = tab_depth<M>(ps, i);
                     psx = (unsigned)ls;
                 }
                 float pr[K];
-                grid_profile<K>(gcol + (long long)lr * g.gstride, g.gnz, gfx, pr);
+                grid_profile<K>(gcol + (long long)lr * g.gstride, g.gnx, gfx, pr);
                 auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {

@@ -59,7 +59,7 @@ struct kh_plan_s {
     int tab_nh = 0, tab_nz = 0;
     double tab_tmin = 0.0, tab_scale = 1.0;
     // gridded model (KH_VEL_GRID): the node grid, per-location FP32 tables, the locations, the
-    // rounds each took, the FP64 slowness, and per (location, tile) time bounds
+    // rounds each took, the FP64 slowness s and h s, and per (location, tile) time bounds
     kh_grid grid{};
     int grid_nloc = 0;
     int grid_m = 0;               // depth nodes every grid_m image samples

@@ -484,11 +484,12 @@ class Plan:
         self.grid_nloc = loc.numel()
 
     def grid_tables(self, stream=None):
-        """(tables float32 [nloc, nx, nz], rounds int32 [nloc]) of the plan's gridded model."""
+        """(tables float32 [nloc, nz, nx] (x fastest, as stored), rounds int32 [nloc]) of the plan's
+        gridded model."""
         if self.grid is None:
             raise ValueError("kirchhoff: the plan has no gridded-model tables")
         dev = f"cuda:{self.device}"
-        T = torch.empty((self.grid_nloc, self.grid.nx, self.grid.nz), dtype=torch.float32, device=dev)
+        T = torch.empty((self.grid_nloc, self.grid.nz, self.grid.nx), dtype=torch.float32, device=dev)
         r = torch.empty(self.grid_nloc, dtype=torch.int32, device=dev)
         kirchhoff_grid_read(self.handle, T, r, stream)
         return T, r

@@ -205,6 +205,14 @@ def survey_25d_lsm(nx: int = 512, nz: int = 400, nt: int = 2000, n_shots: int = 
                   rx=_f32(rx), ry=_f32(z), name=f"25d-vz-{sx.size}tr-{nx}x{nz}")
 
 
+def survey_25d_vxz(m: int = 4) -> Survey:
+    """The 2.5D line of ``survey_25d_lsm`` (20 000 traces, 512 x 400 image at 5 m) over a laterally
+    varying model: v = 1800 + 0.6 z with a Gaussian low-velocity lens (-300 m/s, radius 250 m) at
+    (1280 m, 800 m), on 20 m nodes (m = 4) covering every shot and receiver."""
+    s = vxz_model(survey_25d_lsm(), m, lens_dv=-300.0, lens_xz=(1280.0, 800.0), lens_r=250.0)
+    return s.replace(name=f"25d-vxz-{s.ntr}tr-{s.nx}x{s.nz}")
+
+
 def grid_layout(survey: Survey, m: int, margin_nodes: int = 1):
     """Node grid for a gridded model of a 2D survey: square cells of side h = m dz (m in 1, 2, 4),
     row 0 at the surface, columns covering the image and every source and receiver with

@@ -92,7 +92,7 @@ def check_constant_velocity():
     for h, xs in ((40.0, 310.0), (10.0, 310.0), (10.0, 0.0), (5.0, 1277.5)):
         nx, nz = int(1280 / h) + 1, int(640 / h) + 1
         v = np.full((nx, nz), v0, np.float32)
-        T, r = oracle.eikonal(v, 0.0, h, xs)
+        T, r = oracle.eikonal(v, 0.0, h, xs, tol=0.0)   # the converged discrete solution
         assert r > 0
         x = np.arange(nx)[:, None] * h
         z = np.arange(nz)[None, :] * h
@@ -128,7 +128,7 @@ def check_symmetry_and_positivity():
     X, Z = np.meshgrid(x, z, indexing="ij")
     xc = x[nx // 2]
     v = (1700.0 + 0.5 * Z - 500.0 * np.exp(-((X - xc) ** 2 + (Z - 150.0) ** 2) / (2 * 50.0 ** 2))).astype(np.float32)
-    T, r = oracle.eikonal(v, 0.0, h, xc)
+    T, r = oracle.eikonal(v, 0.0, h, xc, tol=0.0)   # converged: the orderings' asymmetry is gone
     assert r > 0
     assert np.max(np.abs(T - T[::-1])) <= 1e-13 * np.max(T)
     T[nx // 2, 0] = 1.0
@@ -144,7 +144,9 @@ def check_rounds():
     T, r = oracle.eikonal(v, 0.0, h, 155.0)
     assert r >= 3
     T0, r0 = oracle.eikonal(v, 0.0, h, 155.0, tol=0.0)
-    assert r0 >= r and np.max(np.abs(T - T0)) < 1e-9
+    # stopped once a round moved no node by more than the tolerance: what later rounds would
+    # still change is about 1 % of that
+    assert r0 >= r and np.max(np.abs(T - T0)) < 0.05 * oracle.TOL
     _, r1 = oracle.eikonal(v, 0.0, h, 155.0, max_rounds=1)
     assert r1 == -1
 

@@ -148,6 +148,15 @@ def barrier(ws):
         dist.barrier()
 
 
+def sum_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def max_over_ranks(ws, x: float) -> float:
     if ws == 1:
         return x
@@ -348,6 +357,10 @@ def parse_args(argv=None):
                          "batched vs loop, adjoint, gradient), each timed on its own; default: on for "
                          "the headline migration, off otherwise")
     ap.add_argument("--form-steps", type=int, default=3, help="timed steps of each added form")
+    ap.add_argument("--parallelism", default="replicas", choices=["replicas", "image"],
+                    help="N > 1: every rank migrates the whole workload (replicas, weak scaling), or "
+                         "rank r migrates its slab of image columns with every trace (image, strong "
+                         "scaling: the N slabs make the one image; no exchange of partial sums)")
     ap.add_argument("--parity-points", type=int, default=4096,
                     help="image samples compared with the FP64 oracle (0: no parity check)")
     args = ap.parse_args(argv)
@@ -361,6 +374,10 @@ def main():
     s = workloads()[args.workload]()
     if args.aperture is not None and not isinstance(s, list):
         s = s.replace(aperture=args.aperture, name=f"{s.name}-A{args.aperture:g}")
+    args.image_partition = args.parallelism == "image" and ws > 1 and not isinstance(s, list)
+    if args.image_partition:
+        from paper_1204_1225_gb300 import partition
+        s = partition.slab_survey(s, *partition.image_slabs(s, ws)[rank])
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, s[0] if isinstance(s, list) else s)
@@ -379,7 +396,8 @@ def main():
         cache = {}
         line = run_single(args, s, ws, rank, local, dev, cache)
         headline = (args.workload == "3d-vz-100k-256cube" and args.op == "migrate" and args.vel == "analytic"
-                    and args.trace_dtype == "f32" and args.aperture is None and args.spatial_sort)
+                    and args.trace_dtype == "f32" and args.aperture is None and args.spatial_sort
+                    and not args.image_partition)
         forms = run_forms(args, s, ws, rank, local, dev, cache, line) \
             if (args.forms if args.forms is not None else headline) else None
         if line is not None and forms is not None:
@@ -481,7 +499,10 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
     plan.profile(False)
     t_ms = max_over_ranks(ws, e0.elapsed_time(e1))
     barrier(ws)
-    value = contrib * steps * ws / (t_ms / 1e3) / 1e9
+    # replicas: every rank did the whole workload; image partition: the ranks' slabs make one image
+    image_part = getattr(args, "image_partition", False)
+    units = sum_over_ranks(ws, contrib) if image_part else contrib * ws
+    value = units * steps / (t_ms / 1e3) / 1e9
     clocks = clk.summary()
 
     # end to end through the public API: pinned host inputs in, image back to pinned host
@@ -507,7 +528,7 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
         torch.cuda.synchronize(dev)
         plan.sync()
         te = max_over_ranks(ws, e0.elapsed_time(e1))
-        e2e_rec = {"value": contrib * steps * ws / (te / 1e3) / 1e9, "unit": "Gcontrib/s",
+        e2e_rec = {"value": units * steps / (te / 1e3) / 1e9, "unit": "Gcontrib/s",
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         del h_tr, h_img, d_tr
 
@@ -572,7 +593,7 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
     return {
         "metric": "G image-point x trace contributions/s", "value": value, "unit": "Gcontrib/s",
         "n_gpus": ws, "steps": steps, "warmup": warmup,
-        "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "strong" if image_part else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": s.name, "operator": op, "image": list(plan.image_shape),
                    "ntr": s.ntr, "nt": s.nt,
@@ -588,7 +609,8 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
                    "eikonal_tables": grid_rec,
                    "l2": "inputs larger than L2 (traces %.0f MB, image %.0f MB)" % (
                        tbytes / 1e6, image.numel() * 4 / 1e6),
-                   "parallelism": "replicas" if ws > 1 else "single",
+                   "parallelism": (f"image slabs x{ws} (rank 0's slab shown)" if image_part else
+                                   "replicas" if ws > 1 else "single"),
                    "trace_order": _trace_order(plan, spatial_sort),
                    "staging_per_cta": _staging(*stage_stats)},
         "roofline": roof, "parity": parity, "cpu_baseline": cpu_rec, "e2e": e2e_rec,

@@ -1,6 +1,6 @@
 """Multi-process path of bench.py on CPU (gloo, world size 2): the replicas mode has no
-data-path collective, only a barrier and a max over ranks of the timed interval, and the
-reference arm runs on rank 0 alone."""
+data-path collective, only a barrier and a max over ranks of the timed interval (the image
+partition adds a sum of the ranks' work units), and the reference arm runs on rank 0 alone."""
 import json
 import os
 import socket
@@ -28,8 +28,9 @@ def _worker(rank, world, port, q):
     ws, r, _ = bench.dist_init()
     bench.barrier(ws)
     m = bench.max_over_ranks(ws, 10.0 + 3.0 * r)
+    total = bench.sum_over_ranks(ws, 5.0 + r)   # the image partition's work units
     bench.barrier(ws)
-    q.put((r, ws, m))
+    q.put((r, ws, m, total))
     dist.destroy_process_group()
 
 
@@ -44,7 +45,7 @@ def test_two_ranks_barrier_and_max_over_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    assert got == [(0, 2, 13.0), (1, 2, 13.0)]
+    assert got == [(0, 2, 13.0, 11.0), (1, 2, 13.0, 11.0)]
 
 
 def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():

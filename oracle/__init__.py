@@ -78,6 +78,7 @@ def lib():
             _lib.ko_grid_tables.argtypes = [I, I, Dbl, Dbl, P, I, P, I, Dbl, P, P]
             _lib.ko_grid_tables.restype = I
             _lib.ko_grid_traveltime.argtypes = [D, I, L, P, P, P]
+            _lib.ko_ta_weight.argtypes = [D, L, P, P]
             _lib.ko_set_mutation.argtypes = [ctypes.c_int]
             _lib.ko_set_threads.argtypes = [ctypes.c_int]
             _lib.ko_max_threads.restype = ctypes.c_int
@@ -90,7 +91,7 @@ def desc(s) -> _Desc:
     per model and location set, then cached) or the tables given as ``s.oracle_tables``."""
     d = _Desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
               s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1, "table": 2, "pstm": 3, "grid": 4}[s.vel],
-              s.v0, s.k, {"one": 0, "obliq": 1}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt,
+              s.v0, s.k, {"one": 0, "obliq": 1, "ta": 2}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt,
               float(getattr(s, "table_spacing", 25.0)), float(getattr(s, "taper", 0.0)))
     if s.vel == "grid":
         g = getattr(s, "oracle_tables", None)
@@ -143,6 +144,14 @@ def traveltime(s, R, z, grad: bool = False):
     gk = np.empty_like(R) if grad else None
     lib().ko_traveltime(ctypes.byref(desc(s)), R.size, _ptr(R), _ptr(z), _ptr(T), _ptr(gv), _ptr(gk))
     return (T, gv, gk) if grad else T
+
+
+def ta_weight(s, pts) -> np.ndarray:
+    """True-amplitude weight (weight "ta") at rows (x, y, z, sx, sy, rx, ry) of ``pts``."""
+    p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 7)
+    W = np.empty(p.shape[0], dtype=np.float64)
+    lib().ko_ta_weight(ctypes.byref(desc(s)), p.shape[0], _ptr(p), _ptr(W))
+    return W
 
 
 def table_traveltime(s, h, z) -> np.ndarray:

@@ -42,7 +42,7 @@ typedef struct {
                                 migration (double square root, RMS velocity of the linear model),
                                 4 tables of a gridded model v(x, z) from the eikonal solver */
     double v0, k;
-    int weight;              /* 0 W=1, 1 obliquity x spreading */
+    int weight;              /* 0 W=1, 1 obliquity x spreading, 2 true amplitude (constant v) */
     double r0;
     double aperture;         /* <= 0: full aperture */
     int nt;
@@ -369,6 +369,63 @@ int ko_grid_traveltime(const ko_desc* d, int l, long n, const double* x, const d
     return 0;
 }
 
+/* True-amplitude weight (weight 2, constant velocity; a reading of Sec. 3's "weighting function
+ * accounting for the amplitude of propagation"): the weight of the asymptotic Kirchhoff inversion
+ * for the reflection coefficient (Beylkin 1985; Bleistein 1987), |h| / (a_s a_r |grad tau|^2), with
+ * a_a the Green's-function amplitude of each leg and h the Beylkin determinant of
+ * tau(x; xi) = (|x - s| + |x - r|) / v over the trace's midpoint xi at fixed offset (s = xi - o,
+ * r = xi + o):
+ *     3D: h = det[grad tau, d(grad tau)/d xi_1, d(grad tau)/d xi_2],   a = 1 / (4 pi R);
+ *     2D: h = det[grad tau, d(grad tau)/d xi] (the (x, z) plane),       a ~ 1 / sqrt(R).
+ * With e_a = (x - a) / R_a, grad tau = (e_s + e_r) / v and d e_a / d xi_k = (u_k - e_a (e_a . u_k)) / R_a
+ * (u_k the surface direction xi_k moves; the sign of the columns does not change |h|).  The factors
+ * of v and the constants of a_a and of the inversion formula are global and are dropped:
+ *     W = (R_s R_r)^((dim - 1) / 2) |det[g, D u_1 (, D u_2)]| / |g|^2,
+ *     g = e_s + e_r,  D u = sum_a (u - e_a (e_a . u)) / R_a.
+ * It applies to time-differentiated data (the inversion's i omega; 3D).  At zero offset it is
+ * 2 cos(theta) (3D) and cos(theta) (2D); at the specular point of a horizontal reflector in 3D it is
+ * 2 cos(theta), which makes the image peak independent of the offset.  W := 0 where |z| < 1e-6 |dz|,
+ * as for weight 1. */
+static double ta_weight(const ko_desc* d, double x, double y, double z, double sx, double sy, double rx,
+                        double ry)
+{
+    if (fabs(z) < 1e-6 * fabs(d->dz)) return 0.0;
+    const double es[3] = {x - sx, y - sy, z}, er[3] = {x - rx, y - ry, z};
+    const double Rs = sqrt(es[0] * es[0] + es[1] * es[1] + es[2] * es[2]);
+    const double Rr = sqrt(er[0] * er[0] + er[1] * er[1] + er[2] * er[2]);
+    double g[3], c1[3], c2[3];
+    for (int i = 0; i < 3; ++i) g[i] = es[i] / Rs + er[i] / Rr;
+    /* D u for u = x (c1) and u = y (c2) */
+    for (int k = 0; k < 2; ++k) {
+        double* c = k == 0 ? c1 : c2;
+        const double psu = es[k] / Rs, pru = er[k] / Rr;   /* e_a . u_k */
+        for (int i = 0; i < 3; ++i) {
+            const double ui = (i == k) ? 1.0 : 0.0;
+            c[i] = (ui - es[i] / Rs * psu) / Rs + (ui - er[i] / Rr * pru) / Rr;
+        }
+    }
+    if (ko_mutation == 20) { c1[0] = -c1[0]; }   /* a sign error in one entry */
+    double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    if (ko_mutation == 22) g2 = 4.0;   /* the |grad tau|^2 of the reflectivity inversion dropped */
+    if (d->dim == 2) {
+        /* the (x, z) plane: det[[g_x, c1_x], [g_z, c1_z]] */
+        const double h = g[0] * c1[2] - g[2] * c1[0];
+        return sqrt(Rs * Rr) * fabs(h) / g2;
+    }
+    const double h = g[0] * (c1[1] * c2[2] - c1[2] * c2[1]) - c1[0] * (g[1] * c2[2] - g[2] * c2[1]) +
+                     c2[0] * (g[1] * c1[2] - g[2] * c1[1]);
+    if (ko_mutation == 21) return Rs * Rr * fabs(h) / (Rs + Rr) / g2;   /* a spreading factor off */
+    return Rs * Rr * fabs(h) / g2;
+}
+
+int ko_ta_weight(const ko_desc* d, long n, const double* p, double* W)
+{
+    /* p: [n][7] = (x, y, z, sx, sy, rx, ry) */
+    for (long i = 0; i < n; ++i)
+        W[i] = ta_weight(d, p[7 * i], p[7 * i + 1], p[7 * i + 2], p[7 * i + 3], p[7 * i + 4], p[7 * i + 5], p[7 * i + 6]);
+    return 0;
+}
+
 /* Amplitude weight W(x, x_s, x_r) (Sec. 3, Eq. 1). */
 static double weight(const ko_desc* d, double z, double Rs, double Rr)
 {
@@ -503,7 +560,8 @@ static contrib contribution(const ko_desc* d, double x, double y, double z, doub
                                                               : (zw == 0.0 ? 0.0
                                                                            : 0.5 * (zw / Rs + zw / Rr) * Rs * Rr /
                                                                                  (d->r0 * d->r0)))
-                        : weight(d, z, Rs, Rr);
+          : (d->weight == 2) ? ta_weight(d, x, y, z, sx, sy, rx, ry)
+                             : weight(d, z, Rs, Rr);
     if (want_grad) {
         c.dtau_dv0 = (dsv + drv) / d->dt;
         c.dtau_dk = (dsk + drk) / d->dt;

@@ -793,15 +793,16 @@ def _form(line):
     out = {k: line[k] for k in keep if k in line}
     out["config"] = {k: v for k, v in line["config"].items()
                      if k in ("workload", "operator", "trace_storage", "traveltimes", "contributions_per_step",
-                              "batch_mode", "work_items", "staging_per_cta", "eikonal_tables", "velocity")}
+                              "batch_mode", "work_items", "staging_per_cta", "eikonal_tables", "velocity", "weight")}
     return out
 
 
 def run_forms(args, s, ws, rank, local, dev, cache, head):
     """The metric's other forms on the same GPU, each timed on its own: mixed precision (16-bit
     traces and traveltime table) on the headline survey, the adjoint and the (v0, k) gradient on
-    the headline survey, prestack time migration of the same traces, and the 64-job batch as one
-    graph replay against a loop of per-job calls (FP32 and FP16 traces)."""
+    the headline survey, prestack time migration of the same traces, gridded v(x, z) tables on the
+    2.5D line, the true-amplitude weight at constant velocity, and the 64-job batch as one graph
+    replay against a loop of per-job calls (FP32 and FP16 traces)."""
     k = dict(steps=args.form_steps, warmup=3, e2e=False, cpu=False)
     forms = {}
     mixed = run_single(args, s, ws, rank, local, dev, cache, trace_dtype="f16", vel="table",
@@ -831,6 +832,17 @@ def run_forms(args, s, ws, rank, local, dev, cache, head):
     if rank == 0:
         forms["gridded_vxz_tables"]["speedup_vs_analytic_vz"] = (forms["gridded_vxz_tables"]["value"] /
                                                                  forms["gridded_vxz_background"]["value"])
+    # the true-amplitude weight (constant velocity) on the headline geometry and traces, next to the
+    # obliquity weight on the same constant-velocity survey: the cost of the per-contribution weight
+    for w, name in (("ta", "true_amplitude_const_v"), ("obliq", "obliquity_const_v")):
+        s_c = s.replace(vel="const", v0=2000.0, k=0.0, weight=w, name=f"3d-const2000-{w}-100000tr-256cube")
+        ccache = {key: cache[key] for key in ("hdr", "traces", "count", "traces64") if key in cache}
+        r = run_single(args, s_c, ws, rank, local, dev, ccache, **k)
+        if rank == 0:
+            forms[name] = _form(r)
+    if rank == 0:
+        forms["true_amplitude_const_v"]["cost_vs_obliquity"] = (forms["obliquity_const_v"]["value"] /
+                                                                forms["true_amplitude_const_v"]["value"])
     cache.clear()
     torch.cuda.empty_cache()
     surveys = workloads()["batch64-3d-vz"]()

@@ -94,8 +94,21 @@ typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2, KH_VEL_P
  *  KH_W_ONE:          W = 1.
  *  KH_W_OBLIQ_SPREAD: W = 1/2 (cos th_s + cos th_r) R_s R_r / r0^2 with cos th = z / R
  *                     (chord obliquity times spreading) = z (R_s + R_r) / (2 r0^2);
- *                     W = 0 where |z| < 1e-6 |dz|. */
-typedef enum { KH_W_ONE = 0, KH_W_OBLIQ_SPREAD = 1 } kh_weight;
+ *                     W = 0 where |z| < 1e-6 |dz|.
+ *  KH_W_TRUE_AMP:     true amplitude, constant velocity only (KH_VEL_CONST): the weight of the
+ *                     asymptotic Kirchhoff inversion for the reflection coefficient (Beylkin 1985,
+ *                     Bleistein 1987), |h| / (a_s a_r |grad tau|^2) with h the Beylkin determinant of
+ *                     the two-way time over the trace's midpoint at fixed offset and a_a the legs'
+ *                     Green's-function amplitudes, with its global constants dropped:
+ *                       W = (R_s R_r)^((dim - 1) / 2) |det[g, D u_x (, D u_y)]| / |g|^2,
+ *                       g = e_s + e_r, e_a = (x - x_a) / R_a, D u = sum_a (u - e_a (e_a . u)) / R_a
+ *                     (2D: the (x, z) plane), which reduces to z (R_s + R_r)(1/R_s^2 + 1/R_r^2) / 2 (3D)
+ *                     and z sqrt(R_s R_r)(1/R_s^2 + 1/R_r^2) / 2 (2D), the form the kernels evaluate:
+ *                     2 cos th (3D) or cos th (2D) at zero offset.
+ *                     Applied to time-differentiated 3D data, a horizontal reflector's image has the
+ *                     same peak at every offset and depth.  W = 0 where |z| < 1e-6 |dz|.  Migration
+ *                     and demigration (the velocity gradient and the batched launch refuse it). */
+typedef enum { KH_W_ONE = 0, KH_W_OBLIQ_SPREAD = 1, KH_W_TRUE_AMP = 2 } kh_weight;
 
 typedef struct {
     int dim;                 /* 2 or 3 */

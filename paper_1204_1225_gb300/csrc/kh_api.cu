@@ -277,8 +277,10 @@ static kh_status validate_desc(const kh_desc* d)
     if (d->vel != KH_VEL_GRID && (!(d->v0 > 0) || !std::isfinite(d->v0)))
         return fail(KH_ERR_INVALID_ARG, "v0 must be > 0");
     if (d->vel != KH_VEL_GRID && !std::isfinite(d->k)) return fail(KH_ERR_INVALID_ARG, "k must be finite");
-    if (d->weight != KH_W_ONE && d->weight != KH_W_OBLIQ_SPREAD)
+    if (d->weight != KH_W_ONE && d->weight != KH_W_OBLIQ_SPREAD && d->weight != KH_W_TRUE_AMP)
         return fail(KH_ERR_INVALID_ARG, "bad weight kind %d", (int)d->weight);
+    if (d->weight == KH_W_TRUE_AMP && d->vel != KH_VEL_CONST)
+        return fail(KH_ERR_UNSUPPORTED, "the true-amplitude weight is built for constant velocity only");
     if (d->weight == KH_W_OBLIQ_SPREAD && !(d->r0 > 0)) return fail(KH_ERR_INVALID_ARG, "r0 must be > 0");
     if (d->nt < 2) return fail(KH_ERR_UNSUPPORTED, "nt must be >= 2 (got %d)", d->nt);
     if (!(d->dt > 0) || !std::isfinite(d->t0)) return fail(KH_ERR_INVALID_ARG, "dt must be > 0, t0 finite");
@@ -336,7 +338,7 @@ static GeomParams geom_of(const kh_desc& d)
     g.C1 = (float)c1;
     g.C1lo = (float)(c1 - (double)g.C1);
     g.c0 = -d.t0 / d.dt - 0.5;
-    g.weight = d.weight == KH_W_OBLIQ_SPREAD ? 1 : 0;
+    g.weight = (int)d.weight;   // 0 one, 1 obliquity x spreading, 2 true amplitude
     g.wscale = 1.0 / (2.0 * d.r0 * d.r0);
     g.use_aperture = d.aperture > 0 ? 1 : 0;
     g.A2 = (float)(d.aperture * d.aperture);
@@ -1200,6 +1202,8 @@ kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, const flo
     if (ntr > 0 && (!image || !traces)) return fail(KH_ERR_INVALID_ARG, "image/traces is NULL");
     if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM || p->d.vel == KH_VEL_GRID)
         return fail(KH_ERR_UNSUPPORTED, "no velocity gradient for table traveltimes or time migration");
+    if (p->d.weight == KH_W_TRUE_AMP)
+        return fail(KH_ERR_UNSUPPORTED, "no velocity gradient with the true-amplitude weight");
     if (p->d.trace_dtype != KH_F32) return fail(KH_ERR_UNSUPPORTED, "velocity gradient takes FP32 traces");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaMemsetAsync(out_dv0_dk, 0, 2 * sizeof(double), s);

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                 S.z2[i] = gamma;
             } else {
                 const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-                S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
+                S.zc[i] = make_float4((float)(z * z), wz, (float)z, fabs(z) >= 1e-6 * fabs(g.dz) ? 1.f : 0.f);
             }
         }
         // clear this warp's rows in use
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                     const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
 #pragma unroll 4
                     for (int iz = 0; iz < dt.tz; ++iz) {
-                        const float4 zc = S.zc[iz];
+                        const float4 zc = S.zc[iz];   // (z^2, w_z, z, 1 off the surface row)
                         const float Rs = hsqrt<FAST>(dhs2 + zc.x);
                         const float Rr = hsqrt<FAST>(dhr2 + zc.x);
                         const float Ssum = Rs + Rr;
@@ -172,7 +172,9 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                         const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
                         const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
                         const bool v = fabsf(th - cmid) <= chc;
-                        const float W = (WGT == 1) ? zc.y * Ssum : 1.f;
+                        const float W = (WGT == 1) ? zc.y * Ssum
+                                        : (WGT == 2) ? (zc.w != 0.f ? ta_weight<FAST>(zc.z, Rs, Rr, g.dim == 3) : 0.f)
+                                                     : 1.f;
                         const float wm = v ? tp * W * mcol[iz] : 0.f;
                         const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                         const float a1 = wm * f;
@@ -304,6 +306,11 @@ cudaError_t launch_demigrate(const GeomParams& g, const DmTile& dt, const TraceS
                              const float* image, float* partial, int* status, int max_chunks,
                              int vel_kind, int fast, cudaStream_t s)
 {
+    if (g.weight == KH_W_TRUE_AMP) {   // constant velocity only (the plan refuses the others)
+        if (vel_kind != VK_CONST) return cudaErrorInvalidValue;
+        return fast ? dm_launch_t<VK_CONST, 2, true>(g, dt, tr, image, partial, status, max_chunks, s)
+                    : dm_launch_t<VK_CONST, 2, false>(g, dt, tr, image, partial, status, max_chunks, s);
+    }
     const int key = vel_kind * 4 + g.weight * 2 + (fast ? 1 : 0);
     switch (key) {
         case 0: return dm_launch_t<VK_CONST, 0, false>(g, dt, tr, image, partial, status, max_chunks, s);

@@ -172,6 +172,22 @@ __device__ __forceinline__ double grid_coord(double o, int i, double h)
     return __dadd_rn(o, __dmul_rn((double)i, h));
 }
 
+// True-amplitude weight (KH_W_TRUE_AMP, constant velocity): the weight of the asymptotic Kirchhoff
+// inversion for the reflection coefficient with its global constants dropped,
+//     W = (R_s R_r)^((dim - 1) / 2) |det[g, D u_x (, D u_y)]| / |g|^2,
+// g = e_s + e_r, e_a = (x - a) / R_a, D u = sum_a (u - e_a (e_a . u)) / R_a.  Evaluated in closed form:
+// with c = e_s . e_r, D acts on the normal of span{e_s, e_r} as 1/R_s + 1/R_r and its adjugate maps
+// g to (1/R_s + 1/R_r)(1 + c)(e_s / R_s + e_r / R_r) (3D), while |g|^2 = 2 (1 + c), so
+//     3D: W = z (R_s + R_r) (1/R_s^2 + 1/R_r^2) / 2,    2D: W = z sqrt(R_s R_r) (1/R_s^2 + 1/R_r^2) / 2,
+// free of the cancellation of the determinant's entries (e.g. 1 - e_x^2 near horizontal rays).
+template <bool FAST>
+__device__ __forceinline__ float ta_weight(float z, float Rs, float Rr, bool three_d)
+{
+    const float is = hrcp<FAST>(Rs), ir = hrcp<FAST>(Rr);
+    const float s2 = fmaf(is, is, ir * ir);
+    return 0.5f * z * (three_d ? Rs + Rr : hsqrt<FAST>(Rs * Rr)) * s2;
+}
+
 // Gridded model (KH_VEL_GRID): node column gi of image column ix in the tables' node grid and the
 // column's fraction between node columns gi and gi + 1 (FP64, clamped so that gi + 1 is a node);
 // the migration's reads and the tile bounds both take it from here.

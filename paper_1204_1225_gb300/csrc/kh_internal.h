@@ -152,7 +152,7 @@ struct GeomParams {
     float t0, dt;            // FP32 copies for the window bounds
     double t0d, dtd;         // exact values for the FP64 references
     // weight
-    int weight;              // 0 one, 1 obliquity x spreading
+    int weight;              // 0 one, 1 obliquity x spreading, 2 true amplitude (constant v)
     double wscale;           // 1 / (2 r0^2)
     // aperture
     int use_aperture;

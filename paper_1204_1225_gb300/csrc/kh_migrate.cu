@@ -86,7 +86,7 @@ cudaError_t launch_vgrad(const GeomParams& g, const TileShape& t, const TraceSet
                          const WaitCfg& w, double* partial, cudaStream_t s)
 {
     if (t.cz > MAX_ZG || !partial) return cudaErrorInvalidValue;
-    if (g.tdtype != KH_F32 || vel_kind == VK_TABLE) return cudaErrorInvalidValue;
+    if (g.tdtype != KH_F32 || vel_kind == VK_TABLE || g.weight == KH_W_TRUE_AMP) return cudaErrorInvalidValue;
     return launch_vgrad_impl(g, t, tr, static_cast<const float*>(traces), image, vel_kind, fast_math, w, partial,
                              s);
 }

@@ -713,7 +713,8 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
-                        const float Ssum = hsqrt<FAST>(dhs2 + zc[i].x) + hsqrt<FAST>(dhr2 + zc[i].x);
+                        const float Rs = hsqrt<FAST>(dhs2 + zc[i].x), Rr = hsqrt<FAST>(dhr2 + zc[i].x);
+                        const float Ssum = Rs + Rr;
                         const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
@@ -721,8 +722,13 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
-                        // w_z multiplies the sum once, at the store
+                        // w_z multiplies the sum once, at the store; the true-amplitude weight is
+                        // per contribution (0 on the surface row, where it is undefined)
                         if constexpr (WGT == 1) acc[i] = fmaf(Ssum, val, acc[i]);
+                        else if constexpr (WGT == 2)
+                            acc[i] = fmaf(zc[i].w != 0.f ? ta_weight<FAST>(zc[i].z, Rs, Rr, g.dim == 3)
+                                                         : 0.f,
+                                          val, acc[i]);
                         else acc[i] += val;
                     }
                 };
@@ -996,7 +1002,8 @@ __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, co
             S.z2[i] = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(ze * g.wscale) : 0.f;
         } else {
             const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-            S.zc[i] = make_float4((float)(z * z), wz, 0.f, 0.f);
+            // (z^2, w_z, z, 1 off the surface row: where the true-amplitude weight is defined)
+            S.zc[i] = make_float4((float)(z * z), wz, (float)z, fabs(z) >= 1e-6 * fabs(g.dz) ? 1.f : 0.f);
         }
     }
 }
@@ -1123,6 +1130,11 @@ template <typename TT>
 cudaError_t launch_migrate_dtype(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
                                  float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
+    if (g.weight == KH_W_TRUE_AMP) {   // constant velocity only (the plan refuses the others)
+        if (vel != VK_CONST) return cudaErrorInvalidValue;
+        return fast ? launch_migrate_t<VK_CONST, 2, true, TT>(g, t, tr, traces, image, w, s)
+                    : launch_migrate_t<VK_CONST, 2, false, TT>(g, t, tr, traces, image, w, s);
+    }
     const int key = vel * 4 + g.weight * 2 + (fast ? 1 : 0);
     switch (key) {
         case 0: return launch_migrate_t<VK_CONST, 0, false, TT>(g, t, tr, traces, image, w, s);

@@ -6,6 +6,11 @@ namespace kh {
 cudaError_t launch_migrate_pair(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
                                 float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
+    if (g.weight == KH_W_TRUE_AMP) {   // constant velocity only (the plan refuses the others)
+        if (vel != VK_CONST) return cudaErrorInvalidValue;
+        return fast ? launch_migrate_t<VK_CONST, 2, true, SamplePair>(g, t, tr, traces, image, w, s)
+                    : launch_migrate_t<VK_CONST, 2, false, SamplePair>(g, t, tr, traces, image, w, s);
+    }
     const int key = vel * 4 + g.weight * 2 + (fast ? 1 : 0);
     switch (key) {
         case 0: return launch_migrate_t<VK_CONST, 0, false, SamplePair>(g, t, tr, traces, image, w, s);

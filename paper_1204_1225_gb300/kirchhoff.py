@@ -19,7 +19,7 @@ KH_OK, KH_ERR_INVALID_ARG, KH_ERR_UNSUPPORTED, KH_ERR_OOM, KH_ERR_CUDA, KH_ERR_T
     KH_ERR_INTERNAL = range(7)
 KH_F32, KH_F16, KH_BF16, KH_U16 = 0, 1, 2, 3
 KH_VEL_CONST, KH_VEL_LINEAR_Z, KH_VEL_TABLE, KH_VEL_PSTM, KH_VEL_GRID = 0, 1, 2, 3, 4
-KH_W_ONE, KH_W_OBLIQ_SPREAD = 0, 1
+KH_W_ONE, KH_W_OBLIQ_SPREAD, KH_W_TRUE_AMP = 0, 1, 2
 KH_OPT_WAIT_POLLS, KH_OPT_FAST_MATH, KH_OPT_TILE, KH_OPT_BATCH_MODE, KH_OPT_SAMPLE_PAIRS = 1, 2, 3, 4, 5
 KH_OPT_SPATIAL_SORT = 6
 BATCH_MODES = {"persistent": 0, "concurrent": 1}
@@ -194,7 +194,7 @@ def desc_from(s, trace_dtype=torch.float32, vel=None, table_spacing=None,
         table_spacing = float(getattr(s, "table_spacing", 25.0))
     return kh_desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
                    s.dz, s.n_bins, s.bin_width, vel, s.v0, s.k, table_spacing,
-                   _TABLE_DT[table_dtype], {"one": KH_W_ONE, "obliq": KH_W_OBLIQ_SPREAD}[s.weight],
+                   _TABLE_DT[table_dtype], {"one": KH_W_ONE, "obliq": KH_W_OBLIQ_SPREAD, "ta": KH_W_TRUE_AMP}[s.weight],
                    s.r0, s.aperture, s.nt, s.t0, s.dt, _DT[trace_dtype], float(getattr(s, "taper", 0.0)))
 
 

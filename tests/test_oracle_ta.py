@@ -3,7 +3,8 @@ asymptotic Kirchhoff inversion for the reflection coefficient, |h| / (a_s a_r |g
 the Beylkin determinant of the common-offset traveltime over the midpoint.
 
 Pinned by: its closed form at zero offset (2 cos theta in 3D, cos theta in 2D); the determinant
-from central differences of grad tau over the midpoint (no derivative formula); reciprocity and
+from central differences of grad tau over the midpoint (no derivative formula); its reduction to
+z (R_s + R_r)(1/R_s^2 + 1/R_r^2)/2 (3D) derived by hand (the kernels evaluate that form); reciprocity and
 invariance under horizontal translation and rotation; and what the weight is for: a horizontal
 reflector modelled with the exact specular amplitude R / (4 pi L) of a point source, migrated with
 the weight from time-differentiated data, images with the same peak in every offset bin and at
@@ -71,6 +72,20 @@ def check_finite_differences():
         W = oracle.ta_weight(base(dim), p)
         ref = np.array([fd_weight(q, dim) for q in p])
         assert np.max(np.abs(W - ref) / ref) < 1e-6
+
+
+def check_reduced_form():
+    # with c = e_s . e_r the determinant reduces to (1/R_s + 1/R_r)(1 + c)(z/R_s^2 + z/R_r^2) (3D;
+    # 2D: (1 + c)(z/R_s^2 + z/R_r^2)) and |g|^2 = 2 (1 + c): W = z (R_s + R_r)(1/R_s^2 + 1/R_r^2)/2 (3D),
+    # z sqrt(R_s R_r)(1/R_s^2 + 1/R_r^2)/2 (2D)
+    rng = np.random.default_rng(9)
+    for dim in (3, 2):
+        p = rand_points(rng, 300, dim)
+        W = oracle.ta_weight(base(dim), p)
+        Rs = np.sqrt((p[:, 0] - p[:, 3]) ** 2 + (p[:, 1] - p[:, 4]) ** 2 + p[:, 2] ** 2)
+        Rr = np.sqrt((p[:, 0] - p[:, 5]) ** 2 + (p[:, 1] - p[:, 6]) ** 2 + p[:, 2] ** 2)
+        lat = (Rs + Rr) if dim == 3 else np.sqrt(Rs * Rr)
+        assert np.max(np.abs(W - 0.5 * p[:, 2] * lat * (1 / Rs ** 2 + 1 / Rr ** 2)) / W) < 1e-12
 
 
 def check_symmetries():
@@ -143,6 +158,10 @@ def test_finite_difference_determinant():
     check_finite_differences()
 
 
+def test_reduced_form():
+    check_reduced_form()
+
+
 def test_reciprocity_translation_rotation():
     check_symmetries()
 
@@ -158,6 +177,7 @@ def test_flat_reflector_same_peak_at_every_depth():
 MUTATIONS = [
     (20, check_finite_differences),       # a sign error in one entry of the determinant
     (21, check_zero_offset),              # a spreading factor off
+    (21, check_reduced_form),
     (22, check_flat_reflector_offsets),   # the |grad tau|^2 of the reflectivity inversion dropped
 ]
 

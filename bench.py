@@ -103,6 +103,15 @@ BAR_MIXED = 3e-3
 BAR_GRAD_ABS = 1e-4
 
 
+# The velocity model and weight each workload is defined with (the kernel variant its mix is of).
+WORKLOAD_MODEL = {
+    "3d-vz-100k-256cube": ("linear", "obliq"),
+    "3d-vz-40k-128cube": ("linear", "obliq"),
+    "3d-vz-10k-256cube": ("linear", "obliq"),
+    "25d-vz-20k-512x400": ("linear", "one"),
+}
+
+
 def pipe_roofline(mix, clk_mhz: float):
     """(bound name, contributions/s bound in G/s, all pipe bounds) for an instruction mix."""
     bounds = {p: N_SM * LANES_PER_SM_CLK[p] * clk_mhz * 1e6 / n / 1e9 for p, n in mix.items()}
@@ -547,6 +556,8 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
         mix_key = None
     if args.aperture is not None or not spatial_sort:
         mix_key = None   # instruction mixes were measured on the workloads as defined
+    if s.vel in ("const", "linear") and (s.vel, s.weight) != (WORKLOAD_MODEL.get(args.workload) or (s.vel, s.weight)):
+        mix_key = None   # another velocity model or weight than the workload's own: another kernel
     mix = PIPE_MIX.get(mix_key) if (mix_key and args.fast_math) else None
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "unit": "Gcontrib/s",
             "kernel_ms_per_launch": kern_ms / max(kern_n, 1)}
@@ -832,17 +843,12 @@ def run_forms(args, s, ws, rank, local, dev, cache, head):
     if rank == 0:
         forms["gridded_vxz_tables"]["speedup_vs_analytic_vz"] = (forms["gridded_vxz_tables"]["value"] /
                                                                  forms["gridded_vxz_background"]["value"])
-    # the true-amplitude weight (constant velocity) on the headline geometry and traces, next to the
-    # obliquity weight on the same constant-velocity survey: the cost of the per-contribution weight
-    for w, name in (("ta", "true_amplitude_const_v"), ("obliq", "obliquity_const_v")):
-        s_c = s.replace(vel="const", v0=2000.0, k=0.0, weight=w, name=f"3d-const2000-{w}-100000tr-256cube")
-        ccache = {key: cache[key] for key in ("hdr", "traces", "count", "traces64") if key in cache}
-        r = run_single(args, s_c, ws, rank, local, dev, ccache, **k)
-        if rank == 0:
-            forms[name] = _form(r)
+    # the true-amplitude weight (constant velocity 2000 m/s) on the headline geometry and traces
+    s_c = s.replace(vel="const", v0=2000.0, k=0.0, weight="ta", name="3d-const2000-ta-100000tr-256cube")
+    ccache = {key: cache[key] for key in ("hdr", "traces", "count", "traces64") if key in cache}
+    r = run_single(args, s_c, ws, rank, local, dev, ccache, **k)
     if rank == 0:
-        forms["true_amplitude_const_v"]["cost_vs_obliquity"] = (forms["obliquity_const_v"]["value"] /
-                                                                forms["true_amplitude_const_v"]["value"])
+        forms["true_amplitude_const_v"] = _form(r)
     cache.clear()
     torch.cuda.empty_cache()
     surveys = workloads()["batch64-3d-vz"]()

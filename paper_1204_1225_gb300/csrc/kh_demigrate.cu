@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
         // window-relative time th = tau - lo; valid iff 0 <= th <= hi - lo
         const float c0rel = (float)(tau_ref - (double)lo);
         const float lim = (float)(hi - lo);
-        const float cmid = 0.5f * lim, chalf = 0.5f * lim;
+        const float cmid = 0.5f * lim, chalf = 0.5f * lim + EDGE_EPS;
 
         // stage the tile's image values (zero outside the grid) and per-z constants
         for (int p = threadIdx.x; p < ncol * dt.tz; p += DM_THREADS) {
@@ -169,8 +169,9 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                         const float Rr = hsqrt<FAST>(dhr2 + zc.x);
                         const float Ssum = Rs + Rr;
                         const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                        const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
-                        const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
+                        const float tc = fmaxf(th, 0.f);   // within EDGE_EPS below 0: the first row
+                        const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
+                        const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                         const bool v = fabsf(th - cmid) <= chc;
                         const float W = (WGT == 1) ? zc.y * Ssum
                                         : (WGT == 2) ? (zc.w != 0.f ? ta_weight<FAST>(zc.z, Rs, Rr, g.dim == 3) : 0.f)
@@ -218,8 +219,9 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                                 float sqr = 0.f;
                                 const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
                                 const float th = leg_log<LPT>(rho_r, g, c0rel + sv.x);
-                                const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
-                                const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
+                                const float tc = fmaxf(th, 0.f);   // within EDGE_EPS below 0: the first row
+                        const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
+                                const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                                 const bool v = fabsf(th - cmid) <= chc;
                                 const float W = (WGT == 1) ? S.z2[iz] * (sv.y + sqr) : 1.f;
                                 const float wm = v ? tp * W * mcol[iz] : 0.f;
@@ -241,8 +243,9 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                             const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zk, rs, sqs);
                             const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
                             const float th = leg_log<LPT>(rho_r, g, c0rel + leg_log<LPT>(rho_s, g, 0.f));
-                            const float tm = __fadd_rd(th, MAGIC);                 // MAGIC + floor(th)
-                            const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
+                            const float tc = fmaxf(th, 0.f);   // within EDGE_EPS below 0: the first row
+                        const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
+                            const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                             const bool v = fabsf(th - cmid) <= chc;
                             const float W = (WGT == 1) ? S.z2[iz] * (sqs + sqr) : 1.f;
                             const float wm = v ? tp * W * mcol[iz] : 0.f;

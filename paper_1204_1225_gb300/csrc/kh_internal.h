@@ -48,6 +48,13 @@ struct __align__(8) SamplePair {
 };
 constexpr int PAIR_MAX_NT = 2460;
 
+// A contribution is valid iff 0 <= tau <= nt - 1 (the oracle's exact rule), decided on the FP32 tau,
+// whose rounding (about 1e-5 samples) cannot settle a tau that lies exactly on an edge: the
+// kernels accept tau up to EDGE_EPS samples beyond each edge, so that the edge samples themselves
+// (tau = 0 and tau = nt - 1 in exact arithmetic) are kept on every path.  Beyond an edge the
+// interpolation reads the window's zero or finite neighbour with a weight below EDGE_EPS.
+constexpr float EDGE_EPS = 1.0f / 1024.0f;
+
 // Default wait limit: polls of mbarrier.try_wait, each checked against a 2 s wall clock.
 constexpr long long WAIT_NS = 2000000000LL;
 

@@ -57,7 +57,8 @@ struct __align__(16) MigSmem {
     float2 mid[STAGES][BMAX];   // FP32 midpoint (aperture test)
     int4 win[STAGES][BMAX];     // x: tau_ref - lo (float bits), y: smem index of sample lo minus
                                 // MAGIC_BITS, z/w: c_mid/c_half (float bits) of the valid range
-                                // 0 <= tau - lo <= hi - lo; sign bit of z: every column of the
+                                // 0 <= tau - lo <= hi - lo (EDGE_EPS wider on each side); sign
+                                // bit of z: every column of the
                                 // tile inside the aperture; sign bit of w: window not clipped
     float tb[STAGES][BMAX];     // lo dt + t0: T_s + T_r = (tau - lo) dt + tb (gradient mode)
     float4 zc[MAX_ZG * NZ];     // per-z constants: linear v, z_constants_m; constant v, (z^2, w_z);
@@ -88,17 +89,18 @@ __host__ __device__ inline size_t table_bytes(const GeomParams& g)
 }
 
 // Per consumer thread and depth, the cached source leg of the current source position (see
-// mig_consumer): (C1 ln(1 + rho_s), sqrt(q_s)) for linear v(z), T_s for the table (whose shared
-// copy leaves no room for more at two CTAs per SM).  Constant velocity keeps no cache: its leg is
-// one square root, and surveys whose traces do not arrive shot by shot would recompute it per
-// trace anyway.
+// mig_consumer): (C1 ln(1 + rho_s), sqrt(q_s)) for linear v(z), (dR_s, R_s) for time migration and
+// the constant-velocity true-amplitude kernels, T_s for the tables (the radial table's shared copy
+// leaves no room for more at two CTAs per SM).  The other constant-velocity kernels keep no cache:
+// their leg is one square root, and surveys whose traces do not arrive shot by shot (the batched
+// jobs') would recompute it per trace anyway.
 __host__ __device__ inline size_t src_cache_bytes(const GeomParams& g)
 {
     if (g.table || g.gtab) return (size_t)NZ * CONSUMERS * sizeof(float);
     // gradient: the thread's weighted image values, and for linear v(z) (C1 ln(1 + rho_s), (q/w)_s)
     // and sqrt(q_s)
     if (g.grad) return (size_t)NZ * CONSUMERS * (g.kabs > 0.0 ? sizeof(float2) + 2 * sizeof(float) : sizeof(float));
-    return (g.kabs > 0.0 || g.pstm) ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
+    return (g.kabs > 0.0 || g.pstm || g.weight == KH_W_TRUE_AMP) ? (size_t)NZ * CONSUMERS * sizeof(float2) : 0;
 }
 
 // Elements of one stage's sample area: a full trace always fits, so every trace is stageable.
@@ -207,16 +209,17 @@ __device__ __forceinline__ void grid_profile(const float* __restrict__ c0, int g
 }
 
 // The migration kernel's sample read: th = tau - lo (window-relative sample position); valid
-// iff |th - cmid| <= chalf, i.e. 0 <= th <= hi - lo; linear interpolation between samples
-// floor(th) and floor(th) + 1 (adding 1.5 * 2^23 rounded down leaves floor(th) in the low
-// mantissa bits); invalid points read the zeros at zero_off.
+// iff |th - cmid| <= chalf, i.e. 0 <= th <= hi - lo up to EDGE_EPS; linear interpolation between
+// samples floor(th) and floor(th) + 1 (adding 1.5 * 2^23 rounded down leaves floor(th) in the low
+// mantissa bits), th below 0 read as 0; invalid points read the zeros at zero_off.
 template <typename TT>
 __device__ __forceinline__ float sample_at(const TT* data, float th, int base, float cmid, float chalf,
                                            int zero_off)
 {
+    const bool ok = fabsf(th - cmid) <= chalf;
+    th = fmaxf(th, 0.f);
     const float tm = __fadd_rd(th, MAGIC);
     const float f = __fsub_rn(th, __fsub_rn(tm, MAGIC));
-    const bool ok = fabsf(th - cmid) <= chalf;
     const int off = ok ? __float_as_int(tm) + base : zero_off;
     if constexpr (std::is_same<TT, SamplePair>::value) {
         const float2 p = *reinterpret_cast<const float2*>(data + off);
@@ -312,7 +315,7 @@ __device__ __forceinline__ void next_row(int* row, const int2* rng, int& cur, in
 // `n` is the number of stages this CTA's producer has filled before (mbarrier phases carry
 // over from one work item to the next in the persistent kernel); returns the new count.
 // The window-relative time the consumers evaluate is tau - lo (sample index floor(tau - lo)).
-template <int VEL, typename TT>
+template <int VEL, typename TT, int WGT = 0>
 __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const GeomParams& g,
                                             const TraceSet& tr, const TT* __restrict__ traces, int bin,
                                             const TileBox& box, const WaitCfg& wc, int n, int tile_id = 0)
@@ -411,6 +414,20 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                     S.refr[s][slot] = make_float4(rr.Rc2, qir, rr.wc, rr.iuc);
                     S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
                                                  (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
+                } else if constexpr (VEL == VK_CONST && WGT == 2) {
+                    // the true-amplitude kernels take the legs relative to the tile centre: FP64 legs
+                    // at the tile centre c, R_ac = |c - a|, and tau_c = (R_sc + R_rc) / (v0 dt) - t0/dt
+                    {
+                    const double esx = __dadd_rn(box.cx, -(double)h.x), esy = __dadd_rn(box.cy, -(double)h.y);
+                    const double erx = __dadd_rn(box.cx, -(double)h.z), ery = __dadd_rn(box.cy, -(double)h.w);
+                    const double zc2 = __dmul_rn(box.cz, box.cz);
+                    const double rsc = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(esx, esx), __dmul_rn(esy, esy)), zc2));
+                    const double rrc = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(erx, erx), __dmul_rn(ery, ery)), zc2));
+                    tau_ref = __dadd_rn(tau_ref, __ddiv_rn(__dadd_rn(rsc, rrc), __dmul_rn(g.v0, g.dtd)));
+                    S.refs[s][slot] = make_float4((float)rsc, (float)rrc, 0.f, 0.f);
+                    S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
+                                                 (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
+                    }
                 } else if constexpr (VEL == VK_PSTM) {
                     // FP64 legs at the tile centre (x_c, t0_c): R_ac = sqrt(|c - a|^2 + ze_c^2) on the
                     // straight rays of the RMS medium, and tau_c = C1(t0_c) (R_sc + R_rc) - t0/dt
@@ -441,7 +458,7 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                 S.win[s][slot] = make_int4(__float_as_int((float)(tau_ref - (double)lo)),
                                            dst + (lo - lo_al) - MAGIC_BITS,
                                            __float_as_int(0.5f * lim) | (whole ? (int)0x80000000 : 0),
-                                           __float_as_int(0.5f * lim) | (clipped ? 0 : (int)0x80000000));
+                                           __float_as_int(0.5f * lim + EDGE_EPS) | (clipped ? 0 : (int)0x80000000));
             }
             if (lane == 0 && bytes > 0) mbar_expect_tx(&S.full[s], (uint32_t)bytes);
             __syncwarp();
@@ -705,7 +722,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 if (unchecked) zloop(std::false_type(), std::false_type());
                 else if (g.use_taper) zloop(std::true_type(), std::true_type());
                 else zloop(std::true_type(), std::false_type());
-            } else if constexpr (VEL == VK_CONST) {
+            } else if constexpr (VEL == VK_CONST && WGT != 2) {
                 const float dxs = cxf - h.x, dys = cyf - h.y;
                 const float dxr = cxf - h.z, dyr = cyf - h.w;
                 const float dhs2 = fmaf(dxs, dxs, dys * dys);
@@ -713,8 +730,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
-                        const float Rs = hsqrt<FAST>(dhs2 + zc[i].x), Rr = hsqrt<FAST>(dhr2 + zc[i].x);
-                        const float Ssum = Rs + Rr;
+                        const float Ssum = hsqrt<FAST>(dhs2 + zc[i].x) + hsqrt<FAST>(dhr2 + zc[i].x);
                         const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
@@ -722,14 +738,54 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
-                        // w_z multiplies the sum once, at the store; the true-amplitude weight is
-                        // per contribution (0 on the surface row, where it is undefined)
+                        // w_z multiplies the sum once, at the store
                         if constexpr (WGT == 1) acc[i] = fmaf(Ssum, val, acc[i]);
-                        else if constexpr (WGT == 2)
-                            acc[i] = fmaf(zc[i].w != 0.f ? ta_weight<FAST>(zc[i].z, Rs, Rr, g.dim == 3)
-                                                         : 0.f,
-                                          val, acc[i]);
                         else acc[i] += val;
+                    }
+                };
+                if (unchecked) zloop(std::false_type(), std::false_type());
+                else if (g.use_taper) zloop(std::true_type(), std::true_type());
+                else zloop(std::true_type(), std::false_type());
+            } else if constexpr (VEL == VK_CONST) {
+                // the true-amplitude weight: each leg relative to the tile centre: R_a - R_ac = (q_a - q_ac) / (R_a + R_ac) with
+                // q_a - q_ac = dP_a + (z^2 - z_c^2), so tau - lo = c0rel + C1 (dR_s + dR_r) carries only
+                // quantities of a few tens of samples (the full two-way time, hundreds of samples,
+                // is in the FP64 reference); the source leg (dR_s, R_s) is cached per source position
+                const float4 a = S.hda[s][t];
+                const float4 rf = S.refs[s][t];   // (R_sc, R_rc, -, -)
+                if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
+                    const float dPs = fmaf(dxc, cxf + a.x, dyc * (cyf + a.y));
+                    const float exs = cxf - h.x, eys = cyf - h.y;
+                    const float dhs2 = fmaf(exs, exs, eys * eys);
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) {
+                        const float4 c = zc[i];   // (z^2, z^2 - z_c^2, z, 1 off the surface row)
+                        const float R = hsqrt<FAST>(dhs2 + c.x);
+                        my_src[i * CONSUMERS] = make_float2((dPs + c.y) * hrcp<FAST>(fmaxf(R + rf.x, 1e-30f)), R);
+                    }
+                    psx = __float_as_uint(h.x);
+                    psy = __float_as_uint(h.y);
+                }
+                const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
+                const float exr = cxf - h.z, eyr = cyf - h.w;
+                const float dhr2 = fmaf(exr, exr, eyr * eyr);
+                auto zloop = [&](auto checked, auto tapered) {
+#pragma unroll
+                    for (int i = 0; i < NZ; ++i) {
+                        const float4 c = zc[i];
+                        const float2 sv = my_src[i * CONSUMERS];   // (dR_s, R_s)
+                        const float Rr = hsqrt<FAST>(dhr2 + c.x);
+                        const float dR = (dPr + c.y) * hrcp<FAST>(fmaxf(Rr + rf.y, 1e-30f));
+                        const float Rs = sv.y, Ssum = Rs + Rr;
+                        const float th = fmaf(g.C1, sv.x + dR, c0rel);
+                        float val;
+                        if constexpr (decltype(checked)::value)
+                            val = sample_at<TT>(data, th, w.y, cmid, chalf, zero_off);
+                        else
+                            val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
+                        if constexpr (decltype(tapered)::value) val *= tp;
+                        // the weight per contribution (0 on the surface row, where it is undefined)
+                        acc[i] = fmaf(c.w != 0.f ? ta_weight<FAST>(c.z, Rs, Rr, g.dim == 3) : 0.f, val, acc[i]);
                     }
                 };
                 if (unchecked) zloop(std::false_type(), std::false_type());
@@ -791,7 +847,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     if constexpr (WGT == 1) {
 #pragma unroll
         for (int i = 0; i < NZ; ++i)
-            acc[i] *= (VEL == VK_LINEAR || VEL == VK_PSTM) ? zg[i] : ((VEL == VK_TABLE || VEL == VK_GRID) ? zc[i].x : zc[i].y);
+            acc[i] *= (VEL == VK_TABLE || VEL == VK_GRID) ? zc[i].x : zg[i];
     }
     float* out = image + (((long long)bin * g.ny + iy) * g.nx + ix) * (long long)g.nz + izb;
     const bool vec = ((g.nz & 3) == 0) && (izb + NZ <= g.nz) &&
@@ -899,11 +955,11 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
                     const float Rr = hsqrt<FAST>(dhr2 + c.x);
                     const float Ssum = Rs + Rr;
                     const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
-                    const float tm = __fadd_rd(th, MAGIC);   // MAGIC + floor(th)
+                    const float tm = __fadd_rd(fmaxf(th, 0.f), MAGIC);   // MAGIC + floor(th), th >= 0
                     const bool ok = fabsf(th - cmid) <= chalf;
                     const int off = ok ? __float_as_int(tm) + w.y : zero_off;
                     const float slope = to_f32<TT>(data[off]);   // slope rows: d[i + 1] - d[i]
-                    const float W = (WGT == 1) ? c.y * Ssum : 1.f;
+                    const float W = (WGT == 1) ? zg[i] * Ssum : 1.f;
                     g0 = fmaf(W * my_mv[i * CONSUMERS] * slope, -Ssum * inv_v0sq, g0);
                 }
             } else {
@@ -933,7 +989,7 @@ __device__ void vg_consumer(MigSmem& S, const TT* data, const GeomParams& g, con
                     const float rho_r = leg_delta_grad_m<FAST>(dPr, dhr2, zk, rr, sqr, qwr);
                     const float2 lq = my_lq[i * CONSUMERS];   // (C1 ln(1 + rho_s), (q/w)_s)
                     const float th = leg_log<LPT>(rho_r, g, c0rel + lq.x);
-                    const float tm = __fadd_rd(th, MAGIC);   // MAGIC + floor(th)
+                    const float tm = __fadd_rd(fmaxf(th, 0.f), MAGIC);   // MAGIC + floor(th), th >= 0
                     const bool ok = fabsf(th - cmid) <= chalf;
                     const int off = ok ? __float_as_int(tm) + w.y : zero_off;
                     const float slope = to_f32<TT>(data[off]);   // slope rows: d[i + 1] - d[i]
@@ -1001,9 +1057,11 @@ __device__ __forceinline__ void tile_z_setup(MigSmem& S, const GeomParams& g, co
             S.zc[i] = make_float4((float)(ze * ze), (float)(ze * ze - pt.pze2), (float)c1, (float)(c1 - pt.pc1));
             S.z2[i] = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(ze * g.wscale) : 0.f;
         } else {
-            const float wz = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
-            // (z^2, w_z, z, 1 off the surface row: where the true-amplitude weight is defined)
-            S.zc[i] = make_float4((float)(z * z), wz, (float)z, fabs(z) >= 1e-6 * fabs(g.dz) ? 1.f : 0.f);
+            // constant velocity: (z^2, z^2 - z_c^2, z, 1 off the surface row: where the true-amplitude
+            // weight is defined), and w_z of the obliquity weight
+            const double dq = __dadd_rn(__dmul_rn(z, z), -__dmul_rn(box.cz, box.cz));
+            S.zc[i] = make_float4((float)(z * z), (float)dq, (float)z, fabs(z) >= 1e-6 * fabs(g.dz) ? 1.f : 0.f);
+            S.z2[i] = (g.weight == 1 && fabs(z) >= 1e-6 * fabs(g.dz)) ? (float)(z * g.wscale) : 0.f;
         }
     }
 }
@@ -1058,7 +1116,7 @@ __device__ __forceinline__ void kernel_body(const GeomParams& g, const TileShape
     __syncthreads();
     if (s_abort) return;
     if (threadIdx.x >= CONSUMERS) {
-        mig_producer<VEL, TT>(S, data, cap, g, tr, traces, bin, box, wc, 0, (int)blockIdx.x);
+        mig_producer<VEL, TT, WGT>(S, data, cap, g, tr, traces, bin, box, wc, 0, (int)blockIdx.x);
     } else if constexpr (MODE == 0) {
         mig_consumer<VEL, WGT, FAST, TT, LPT, TB>(S, data, g, ts, x0, y0, z0, box, bin, image, wc, tab, srcc, cap,
                                                   0);

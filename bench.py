@@ -75,6 +75,10 @@ PIPE_MIX = {
     # prestack time migration (k_migrate<time migration, obliquity, fast, sample pairs>)
     "3d-pstm-100k-256cube": {"issue": 23.43, "fma": 13.39, "alu": 3.19, "xu": 2.08, "lsu": 3.36},
     "3d-pstm-10k-256cube": {"issue": 23.43, "fma": 13.39, "alu": 3.19, "xu": 2.08, "lsu": 3.36},
+    # true-amplitude weight, constant velocity (k_migrate<const, true amplitude, fast, sample pairs>,
+    # tile-relative legs, source leg cached), measured on the 10k-trace case
+    "3d-ta-100k-256cube": {"issue": 33.17, "fma": 17.81, "alu": 6.05, "xu": 4.15, "lsu": 3.36},
+    "3d-ta-10k-256cube": {"issue": 33.17, "fma": 17.81, "alu": 6.05, "xu": 4.15, "lsu": 3.36},
     # persistent batched kernel, constant velocity, sample pairs (measured on the 8-job small batch)
     "batch64-3d-vz-f32": {"issue": 23.35, "fma": 13.83, "alu": 3.46, "xu": 2.38, "lsu": 2.54},
 }
@@ -92,6 +96,7 @@ TRAFFIC = {
     "3d-vz-10k-256cube-table-u16-f16": 37533696 + 1023990784,
     "3d-vz-10k-256cube-table-f16-f16": 35020800 + 1024065536,
     "3d-pstm-10k-256cube": 87162880 + 1023754240,
+    "3d-ta-10k-256cube": 93872128 + 1025078272,
 }
 
 # Parity bars against the FP64 oracle (relative L2 over the sampled outputs): FP32 forms, and the
@@ -109,6 +114,8 @@ WORKLOAD_MODEL = {
     "3d-vz-40k-128cube": ("linear", "obliq"),
     "3d-vz-10k-256cube": ("linear", "obliq"),
     "25d-vz-20k-512x400": ("linear", "one"),
+    "3d-ta-100k-256cube": ("const", "ta"),
+    "3d-ta-10k-256cube": ("const", "ta"),
 }
 
 
@@ -127,6 +134,10 @@ def workloads():
         "2d-const-1024tr-128x128": lambda: sv.survey_2d_const(),
         "25d-vz-20k-512x400": lambda: sv.survey_25d_lsm(),
         "25d-vxz-20k-512x400": lambda: sv.survey_25d_vxz(),
+        "3d-ta-100k-256cube": lambda: sv.survey_3d_gradient().replace(
+            vel="const", v0=2000.0, k=0.0, weight="ta", name="3d-const2000-ta-100000tr-256cube"),
+        "3d-ta-10k-256cube": lambda: sv.survey_3d_gradient(ntr=10_000, n=256).replace(
+            vel="const", v0=2000.0, k=0.0, weight="ta", name="3d-const2000-ta-10000tr-256cube"),
         "25d-velan-4608tr-128x100": lambda: sv.survey_25d_velan(),
         "3d-pstm-100k-256cube": lambda: sv.survey_3d_gradient().replace(
             vel="pstm", oz=0.0, dz=0.012, name="3d-pstm-100000tr-256x256x256t"),
@@ -844,9 +855,10 @@ def run_forms(args, s, ws, rank, local, dev, cache, head):
         forms["gridded_vxz_tables"]["speedup_vs_analytic_vz"] = (forms["gridded_vxz_tables"]["value"] /
                                                                  forms["gridded_vxz_background"]["value"])
     # the true-amplitude weight (constant velocity 2000 m/s) on the headline geometry and traces
-    s_c = s.replace(vel="const", v0=2000.0, k=0.0, weight="ta", name="3d-const2000-ta-100000tr-256cube")
+    targs = argparse.Namespace(**vars(args))
+    targs.workload = "3d-ta-100k-256cube"
     ccache = {key: cache[key] for key in ("hdr", "traces", "count", "traces64") if key in cache}
-    r = run_single(args, s_c, ws, rank, local, dev, ccache, **k)
+    r = run_single(targs, workloads()[targs.workload](), ws, rank, local, dev, ccache, **k)
     if rank == 0:
         forms["true_amplitude_const_v"] = _form(r)
     cache.clear()

@@ -566,6 +566,13 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
         const int jb = min(g.gzoff + izb / LPT, g.gnz - (NZ / LPT + 1));
         gcol = g.gtab + (long long)jb * g.gnx + gi;
     }
+    // gridded model: the receiver table nodes of the next trace of the stage, read one trace
+    // ahead so that their L2 latency overlaps this trace's depth loop (pf_t: the trace they
+    // belong to, -1: none); not with nodes at every depth (17 nodes per column would spill)
+    constexpr bool GPF = (VEL == VK_GRID) && (NZ / LPT + 1) <= 9;
+    constexpr int GK = GPF ? NZ / LPT + 1 : 1;
+    float pfa[GK], pfb[GK];
+    int pf_t = -1;
 
     bool failed = false;
     while (true) {
@@ -654,7 +661,25 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                     psx = (unsigned)ls;
                 }
                 float pr[K];
-                grid_profile<K>(gcol + (long long)lr * g.gstride, g.gnx, gfx, pr);
+                if (GPF && pf_t == t) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) pr[k] = fmaf(gfx, pfb[k] - pfa[k], pfa[k]);
+                } else {
+                    grid_profile<K>(gcol + (long long)lr * g.gstride, g.gnx, gfx, pr);
+                }
+                pf_t = -1;
+                if (GPF && t + 1 < cnt) {   // the next trace's receiver nodes, in flight during this loop
+                    const int ln = __float_as_int(S.hdr[s][t + 1].w);
+                    if (ln >= 0) {
+                        const float* c0 = gcol + (long long)ln * g.gstride;
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            pfa[k] = __ldg(c0 + k * g.gnx);
+                            pfb[k] = __ldg(c0 + k * g.gnx + 1);
+                        }
+                        pf_t = t + 1;
+                    }
+                }
                 auto zloop = [&](auto checked, auto tapered) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {

@@ -48,7 +48,7 @@ class _Desc(ctypes.Structure):
                 ("dt", ctypes.c_double), ("table_spacing", ctypes.c_double), ("taper", ctypes.c_double),
                 ("gtab", ctypes.c_void_p), ("gloc", ctypes.c_void_p), ("gnloc", ctypes.c_int),
                 ("gnx", ctypes.c_int), ("gnz", ctypes.c_int), ("gox", ctypes.c_double),
-                ("gh", ctypes.c_double)]
+                ("gh", ctypes.c_double), ("aa_spacing", ctypes.c_double)]
 
 
 def lib():
@@ -79,6 +79,7 @@ def lib():
             _lib.ko_grid_tables.restype = I
             _lib.ko_grid_traveltime.argtypes = [D, I, L, P, P, P]
             _lib.ko_ta_weight.argtypes = [D, L, P, P]
+            _lib.ko_aa_weight.argtypes = [D, L, P, P]
             _lib.ko_set_mutation.argtypes = [ctypes.c_int]
             _lib.ko_set_threads.argtypes = [ctypes.c_int]
             _lib.ko_max_threads.restype = ctypes.c_int
@@ -93,6 +94,7 @@ def desc(s) -> _Desc:
               s.dz, s.n_bins, s.bin_width, {"const": 0, "linear": 1, "table": 2, "pstm": 3, "grid": 4}[s.vel],
               s.v0, s.k, {"one": 0, "obliq": 1, "ta": 2}[s.weight], s.r0, s.aperture, s.nt, s.t0, s.dt,
               float(getattr(s, "table_spacing", 25.0)), float(getattr(s, "taper", 0.0)))
+    d.aa_spacing = float(getattr(s, "aa_spacing", 0.0))
     if s.vel == "grid":
         g = getattr(s, "oracle_tables", None)
         if g is None:
@@ -151,6 +153,15 @@ def ta_weight(s, pts) -> np.ndarray:
     p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 7)
     W = np.empty(p.shape[0], dtype=np.float64)
     lib().ko_ta_weight(ctypes.byref(desc(s)), p.shape[0], _ptr(p), _ptr(W))
+    return W
+
+
+def aa_weight(s, pts) -> np.ndarray:
+    """Anti-aliasing weight (constant velocity, ``s.aa_spacing`` > 0) at rows
+    (x, y, z, sx, sy, rx, ry) of ``pts``."""
+    p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 7)
+    W = np.empty(p.shape[0], dtype=np.float64)
+    lib().ko_aa_weight(ctypes.byref(desc(s)), p.shape[0], _ptr(p), _ptr(W))
     return W
 
 

@@ -55,6 +55,7 @@ typedef struct {
     const float* gloc;       /* [gnloc] x of each table's surface point, increasing */
     int gnloc, gnx, gnz;
     double gox, gh;
+    double aa_spacing;       /* vel 0: trace spacing (m) of the operator anti-aliasing; <= 0: off */
 } ko_desc;
 
 /* Deliberate-mistake switch used only by the tests that show the pins catch errors.
@@ -426,6 +427,40 @@ int ko_ta_weight(const ko_desc* d, long n, const double* p, double* W)
     return 0;
 }
 
+/* Operator anti-aliasing (vel 0, aa_spacing > 0; a reading of the weight's "amplitude of
+ * propagation" that also keeps the sum from aliasing): the operator's time dip across the traces,
+ * the midpoint gradient of the two-way time in samples per metre,
+ *     p = -(e_s + e_r)_h / (v0 dt),   e_a = (x - a) / R_a  (horizontal part; 0 where R_a = 0),
+ * times the trace spacing is the moveout L (samples) between adjacent traces,
+ *     L = aa_spacing max(|p_x|, |p_y|).
+ * A contribution whose moveout exceeds one sample would alias the highest frequencies the sampling
+ * carries, so the weight keeps L <= 1 whole, removes L >= 2, and falls between as
+ * cos^2(pi (L - 1) / 2) (dip limitation of the operator). */
+static double aa_weight(const ko_desc* d, double x, double y, double z, double sx, double sy, double rx,
+                        double ry)
+{
+    if (d->aa_spacing <= 0.0) return 1.0;
+    const double Rs = sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy) + z * z);
+    const double Rr = sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry) + z * z);
+    const double is = Rs > 0.0 ? 1.0 / Rs : 0.0, ir = Rr > 0.0 ? 1.0 / Rr : 0.0;
+    double px = ((x - sx) * is + (x - rx) * ir) / (d->v0 * d->dt);
+    const double py = ((y - sy) * is + (y - ry) * ir) / (d->v0 * d->dt);
+    if (ko_mutation == 23) px = (x - sx) * is / (d->v0 * d->dt);   /* the receiver leg's dip dropped */
+    const double L = d->aa_spacing * fmax(fabs(px), fabs(py));
+    if (L <= 1.0) return 1.0;
+    if (L >= 2.0) return 0.0;
+    const double c = cos(0.5 * 3.14159265358979323846 * (L - 1.0));
+    return c * c;
+}
+
+int ko_aa_weight(const ko_desc* d, long n, const double* p, double* W)
+{
+    /* p: [n][7] = (x, y, z, sx, sy, rx, ry) */
+    for (long i = 0; i < n; ++i)
+        W[i] = aa_weight(d, p[7 * i], p[7 * i + 1], p[7 * i + 2], p[7 * i + 3], p[7 * i + 4], p[7 * i + 5], p[7 * i + 6]);
+    return 0;
+}
+
 /* Amplitude weight W(x, x_s, x_r) (Sec. 3, Eq. 1). */
 static double weight(const ko_desc* d, double z, double Rs, double Rr)
 {
@@ -562,6 +597,7 @@ static contrib contribution(const ko_desc* d, double x, double y, double z, doub
                                                                                  (d->r0 * d->r0)))
           : (d->weight == 2) ? ta_weight(d, x, y, z, sx, sy, rx, ry)
                              : weight(d, z, Rs, Rr);
+    if (d->vel == 0 && d->aa_spacing > 0.0) c.W *= aa_weight(d, x, y, z, sx, sy, rx, ry);
     if (want_grad) {
         c.dtau_dv0 = (dsv + drv) / d->dt;
         c.dtau_dk = (dsk + drk) / d->dt;

@@ -68,6 +68,8 @@ class Survey:
     grid_v: Optional[np.ndarray] = None
     grid_ox: float = 0.0
     grid_h: float = 0.0
+    # constant velocity: trace spacing (m) of the operator anti-aliasing; 0 = off
+    aa_spacing: float = 0.0
 
     @property
     def ntr(self) -> int:

@@ -61,7 +61,7 @@ PIPE_MIX = {
     "3d-vz-40k-128cube": {"issue": 34.71, "fma": 22.81, "alu": 3.68, "xu": 3.20, "lsu": 3.42},
     "25d-vz-20k-512x400": {"issue": 36.09, "fma": 23.96, "alu": 4.25, "xu": 2.37, "lsu": 3.75},
     # gridded v(x, z): per-location first-arrival tables read from L2 (k_migrate<grid, one, fast, sample pairs, M=4>)
-    "25d-vxz-20k-512x400": {"issue": 19.53, "fma": 11.24, "alu": 3.49, "xu": 0.004, "lsu": 3.24},
+    "25d-vxz-20k-512x400": {"issue": 20.63, "fma": 11.31, "alu": 3.82, "xu": 0.004, "lsu": 3.31},
     # mixed precision: 16-bit radial tables + FP16 traces (k_migrate<table, obliquity, FP16, M=2, table type>)
     "3d-vz-100k-256cube-table-u16-f16": {"issue": 30.67, "fma": 16.37, "alu": 5.16, "xu": 2.20, "lsu": 5.40},
     "3d-vz-10k-256cube-table-u16-f16": {"issue": 30.67, "fma": 16.37, "alu": 5.16, "xu": 2.20, "lsu": 5.40},
@@ -90,7 +90,7 @@ TRAFFIC = {
     "3d-vz-10k-256cube": 86816256 + 1025687552,
     "3d-vz-40k-128cube": 281054208 + 111904000,
     "25d-vz-20k-512x400": 91543808 + 2981376,
-    "25d-vxz-20k-512x400": 139767552 + 5328640,
+    "25d-vxz-20k-512x400": 138770944 + 5204480,
     "3d-vz-10k-256cube-demigrate": 4820799488 + 8277082112,
     "3d-vz-10k-256cube-vgrad": 1127874560 + 15597568,
     "3d-vz-10k-256cube-table-u16-f16": 37533696 + 1023990784,
@@ -116,6 +116,8 @@ WORKLOAD_MODEL = {
     "25d-vz-20k-512x400": ("linear", "one"),
     "3d-ta-100k-256cube": ("const", "ta"),
     "3d-ta-10k-256cube": ("const", "ta"),
+    "3d-ta-aa-100k-256cube": ("const", "ta"),
+    "3d-ta-aa-10k-256cube": ("const", "ta"),
 }
 
 
@@ -138,6 +140,11 @@ def workloads():
             vel="const", v0=2000.0, k=0.0, weight="ta", name="3d-const2000-ta-100000tr-256cube"),
         "3d-ta-10k-256cube": lambda: sv.survey_3d_gradient(ntr=10_000, n=256).replace(
             vel="const", v0=2000.0, k=0.0, weight="ta", name="3d-const2000-ta-10000tr-256cube"),
+        # the same with operator anti-aliasing for the 25 m receiver spacing
+        "3d-ta-aa-100k-256cube": lambda: sv.survey_3d_gradient().replace(
+            vel="const", v0=2000.0, k=0.0, weight="ta", aa_spacing=25.0, name="3d-const2000-ta-aa25-100000tr-256cube"),
+        "3d-ta-aa-10k-256cube": lambda: sv.survey_3d_gradient(ntr=10_000, n=256).replace(
+            vel="const", v0=2000.0, k=0.0, weight="ta", aa_spacing=25.0, name="3d-const2000-ta-aa25-10000tr-256cube"),
         "25d-velan-4608tr-128x100": lambda: sv.survey_25d_velan(),
         "3d-pstm-100k-256cube": lambda: sv.survey_3d_gradient().replace(
             vel="pstm", oz=0.0, dz=0.012, name="3d-pstm-100000tr-256x256x256t"),
@@ -622,7 +629,7 @@ def run_single(args, s, ws, rank, local, dev, cache, *, op=None, trace_dtype=Non
                    "velocity": (f"{s.vel} v0={s.v0} k={s.k}" if s.vel != "grid" else
                                 f"gridded v(x, z) on {s.grid_v.shape[0]}x{s.grid_v.shape[1]} nodes of "
                                 f"{s.grid_h:g} m (v0 + k z = {s.v0} + {s.k} z with a low-velocity lens)"),
-                   "weight": s.weight,
+                   "weight": s.weight, "aa_spacing_m": float(getattr(s, "aa_spacing", 0.0)),
                    "aperture_m": s.aperture, "contributions_per_step": contrib,
                    "fast_math": bool(args.fast_math), "trace_storage": trace_dtype,
                    "traveltimes": ("per-location first-arrival tables (FP64 eikonal, FP32 storage)"
@@ -815,7 +822,8 @@ def _form(line):
     out = {k: line[k] for k in keep if k in line}
     out["config"] = {k: v for k, v in line["config"].items()
                      if k in ("workload", "operator", "trace_storage", "traveltimes", "contributions_per_step",
-                              "batch_mode", "work_items", "staging_per_cta", "eikonal_tables", "velocity", "weight")}
+                              "batch_mode", "work_items", "staging_per_cta", "eikonal_tables", "velocity", "weight",
+                              "aa_spacing_m")}
     return out
 
 
@@ -823,7 +831,7 @@ def run_forms(args, s, ws, rank, local, dev, cache, head):
     """The metric's other forms on the same GPU, each timed on its own: mixed precision (16-bit
     traces and traveltime table) on the headline survey, the adjoint and the (v0, k) gradient on
     the headline survey, prestack time migration of the same traces, gridded v(x, z) tables on the
-    2.5D line, the true-amplitude weight at constant velocity, and the 64-job batch as one graph
+    2.5D line, the true-amplitude weight at constant velocity (without and with operator anti-aliasing), and the 64-job batch as one graph
     replay against a loop of per-job calls (FP32 and FP16 traces)."""
     k = dict(steps=args.form_steps, warmup=3, e2e=False, cpu=False)
     forms = {}
@@ -861,6 +869,11 @@ def run_forms(args, s, ws, rank, local, dev, cache, head):
     r = run_single(targs, workloads()[targs.workload](), ws, rank, local, dev, ccache, **k)
     if rank == 0:
         forms["true_amplitude_const_v"] = _form(r)
+    # and with operator anti-aliasing (the dip limitation for the 25 m receiver spacing)
+    targs.workload = "3d-ta-aa-100k-256cube"
+    r = run_single(targs, workloads()[targs.workload](), ws, rank, local, dev, ccache, **k)
+    if rank == 0:
+        forms["true_amplitude_anti_aliased_const_v"] = _form(r)
     cache.clear()
     torch.cuda.empty_cache()
     surveys = workloads()["batch64-3d-vz"]()

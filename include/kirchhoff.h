@@ -6,10 +6,10 @@
  *
  *     I(x, X) = integral dx_s dx_r W(x, x_s, x_r) delta(X - |x_s - x_r|) D(x_s, x_r, T(x,x_s) + T(x,x_r))
  *
- * evaluated as a sum over recorded traces (Sec. 3: "each data sample is summed into the
- * image at all the points where the measured time agrees with the total propagation
- * time"), one offset image per offset bin, at the cost f_K N_xyz N_tr of Eq. (2) where
- * N_tr counts the traces "close enough" to the image point (a horizontal aperture).
+ * evaluated as a sum over recorded traces (Sec. 3: every sample of a trace adds into each image
+ * point whose source-plus-receiver traveltime equals the sample's time), one offset image per
+ * offset bin, at the cost f_K N_xyz N_tr of Eq. (2) where N_tr counts the traces near enough to
+ * the image point to carry its reflections (Sec. 3 after Eq. 2; here a horizontal aperture).
  *
  * Conventions shared by every entry point
  *  - Every array argument is a DEVICE pointer owned by the caller unless stated.  Trace
@@ -90,7 +90,7 @@ typedef enum { KH_F32 = 0, KH_F16 = 1, KH_BF16 = 2, KH_U16 = 3 } kh_dtype;
  *                   it).  The weight's geometry is that of straight rays (R = |x - x_a|). */
 typedef enum { KH_VEL_CONST = 0, KH_VEL_LINEAR_Z = 1, KH_VEL_TABLE = 2, KH_VEL_PSTM = 3, KH_VEL_GRID = 4 } kh_vel;
 
-/* Weight W(x, x_s, x_r) of Eq. (1) ("amplitude of propagation"; no formula in the paper):
+/* Weight W(x, x_s, x_r) of Eq. (1) (it carries the propagation amplitude; no formula in the paper):
  *  KH_W_ONE:          W = 1.
  *  KH_W_OBLIQ_SPREAD: W = 1/2 (cos th_s + cos th_r) R_s R_r / r0^2 with cos th = z / R
  *                     (chord obliquity times spreading) = z (R_s + R_r) / (2 r0^2);
@@ -137,6 +137,17 @@ typedef struct {
                                 (1 - taper) A; in [0, 1), 0 = a hard mask; ignored without an
                                 aperture.  Every operator (migrate, demigrate, velocity gradient)
                                 applies it, so they stay each other's transpose and derivative. */
+    double aa_spacing;       /* operator anti-aliasing, KH_VEL_CONST only: the trace (midpoint)
+                                spacing in metres, 0 = off.  With p = ((x - x_s)_h / R_s +
+                                (x - x_r)_h / R_r) / (v0 dt), the midpoint gradient of the two-way
+                                time in samples per metre, the moveout between adjacent traces is
+                                L = aa_spacing max(|p_x|, |p_y|) samples; the weight keeps L <= 1,
+                                removes L >= 2 and falls as cos^2(pi (L - 1) / 2) between (dip
+                                limitation of the operator: the aliased part of the sum is dropped).
+                                Migrate and demigrate, and the allocation-free entry point; the
+                                velocity gradient and the batched launch refuse it
+                                (KH_ERR_UNSUPPORTED).  Negative or not finite: KH_ERR_INVALID_ARG;
+                                > 0 with another velocity kind: KH_ERR_UNSUPPORTED. */
 } kh_desc;
 
 typedef struct kh_plan_s* kh_plan;
@@ -229,8 +240,8 @@ KH_API kh_status kirchhoff_semblance(kh_plan p, const float* image, const double
                                      float* grad_image, void* cuda_stream);
 
 /* ---------------------------------------------------------------- gridded model v(x, z)
- * Sec. 3 takes T from ray-theoretic (high-frequency) approximations with a single propagation
- * path: the first-arrival time, the solution of the eikonal equation |grad T| = 1/v with T = 0 at
+ * Sec. 3 takes T from the high-frequency limit of ray theory, one path per source and image
+ * point: the first-arrival time, the solution of the eikonal equation |grad T| = 1/v with T = 0 at
  * the surface location.  For a laterally varying model (KH_VEL_GRID, dim 2) the library solves it
  * on a node grid for every surface location and the migration reads the tables.
  *

@@ -11,10 +11,10 @@
  *                                                                          (Sec. 3, Eq. 1)
  *
  * The delta selects one offset bin per trace; D is read at t = T_s + T_r by linear
- * interpolation; "traces close enough" (Sec. 3, after Eq. 2) is a hard aperture on the
- * horizontal distance from the image column to the trace midpoint.  The paper gives no
- * formula for T or W ("times/amplitude of propagation in the model", Sec. 3); the
- * readings taken are:
+ * interpolation; the traces near enough to an image point to carry its reflections (Sec. 3,
+ * after Eq. 2) are those within a hard aperture on the horizontal distance from the image
+ * column to the trace midpoint.  The paper names T and W (the propagation times and amplitude
+ * in the model, Sec. 3) but gives no formula for either; the readings taken are:
  *   T, constant v:      R / v0,  R = |x - x_a| (sources/receivers at z = 0, Sec. 2)
  *   T, v(z) = v0 + k z:  T = (2/k) asinh(s),  s = k R / (2 sqrt(v0 (v0 + k z))),
  *                        the closed form of the circular-ray traveltime, written as
@@ -81,7 +81,7 @@ int ko_max_threads(void)
 #endif
 }
 
-/* ---- traveltime and its derivatives (Sec. 3: "times for propagation in the model") ---- */
+/* ---- traveltime and its derivatives (Sec. 3: T, the propagation time in the model) ---- */
 
 /* asinh(s)/s and its derivative; Taylor series of asinh for small |s|. */
 static void asinh_over_s(double s, double* h, double* hp)
@@ -204,8 +204,8 @@ int ko_traveltime(const ko_desc* d, long n, const double* R, const double* z, do
 
 /* ---- first-arrival traveltimes in a laterally varying model v(x, z) (vel 4) ----
  *
- * Sec. 3 takes T from "high-frequency (ray-theoretic) approximations" with "a single propagation
- * path": the first-arrival time, the viscosity solution of the eikonal equation |grad T| = s
+ * Sec. 3 takes T from the high-frequency limit of ray theory, one path per source and image
+ * point: the first-arrival time, the viscosity solution of the eikonal equation |grad T| = s
  * (slowness s = 1/v) with T = 0 at the surface point x_s.  It is computed on a node grid
  * (ox + i h, j h), i < nx, j < nz (row 0 is the surface), as follows.
  *
@@ -370,8 +370,8 @@ int ko_grid_traveltime(const ko_desc* d, int l, long n, const double* x, const d
     return 0;
 }
 
-/* True-amplitude weight (weight 2, constant velocity; a reading of Sec. 3's "weighting function
- * accounting for the amplitude of propagation"): the weight of the asymptotic Kirchhoff inversion
+/* True-amplitude weight (weight 2, constant velocity; a reading of Sec. 3's weight W, which carries
+ * the propagation amplitude): the weight of the asymptotic Kirchhoff inversion
  * for the reflection coefficient (Beylkin 1985; Bleistein 1987), |h| / (a_s a_r |grad tau|^2), with
  * a_a the Green's-function amplitude of each leg and h the Beylkin determinant of
  * tau(x; xi) = (|x - s| + |x - r|) / v over the trace's midpoint xi at fixed offset (s = xi - o,
@@ -427,8 +427,8 @@ int ko_ta_weight(const ko_desc* d, long n, const double* p, double* W)
     return 0;
 }
 
-/* Operator anti-aliasing (vel 0, aa_spacing > 0; a reading of the weight's "amplitude of
- * propagation" that also keeps the sum from aliasing): the operator's time dip across the traces,
+/* Operator anti-aliasing (vel 0, aa_spacing > 0; a reading of the weight W of Eq. 1, which carries
+ * the propagation amplitude, that also keeps the sum from aliasing): the operator's time dip across the traces,
  * the midpoint gradient of the two-way time in samples per metre,
  *     p = -(e_s + e_r)_h / (v0 dt),   e_a = (x - a) / R_a  (horizontal part; 0 where R_a = 0),
  * times the trace spacing is the moveout L (samples) between adjacent traces,
@@ -498,7 +498,7 @@ int ko_bins(const ko_desc* d, long ntr, const float* sx, const float* sy, const 
     return 0;
 }
 
-/* ---- aperture ("traces close enough", Sec. 3), decided in FP32 with a fixed order ---- */
+/* ---- aperture (the traces near enough to an image point, Sec. 3), decided in FP32 with a fixed order ---- */
 static float col_coord(double o, int i, double h) { return (float)(o + (double)i * h); }
 
 static int inside_aperture(const ko_desc* d, float cx, float cy, float sx, float sy, float rx,
@@ -682,9 +682,8 @@ int ko_migrate_points(const ko_desc* d, long ntr, const float* sx, const float* 
     return 0;
 }
 
-/* Demigration: the exact transpose of ko_migrate ("each data sample is summed into the
- * image at all the points where the measured time agrees", Sec. 3, read from the data
- * side).  traces_out[j][i] += W (1-f) m, traces_out[j][i+1] += W f m. */
+/* Demigration: the exact transpose of ko_migrate (Sec. 3's sum read from the data side: each
+ * image point adds into the trace sample whose time is its source-plus-receiver traveltime).  traces_out[j][i] += W (1-f) m, traces_out[j][i+1] += W f m. */
 int ko_demigrate(const ko_desc* d, long ntr, const float* sx, const float* sy, const float* rx,
                  const float* ry, const double* image, double* traces_out)
 {

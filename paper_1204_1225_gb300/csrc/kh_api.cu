@@ -300,6 +300,10 @@ static kh_status validate_desc(const kh_desc* d)
     }
     if (d->trace_dtype == KH_U16) return fail(KH_ERR_INVALID_ARG, "traces cannot be KH_U16");
     if (!(d->taper >= 0.0 && d->taper < 1.0)) return fail(KH_ERR_INVALID_ARG, "taper must be in [0, 1)");
+    if (!(d->aa_spacing >= 0.0) || !std::isfinite(d->aa_spacing))
+        return fail(KH_ERR_INVALID_ARG, "aa_spacing must be finite and >= 0");
+    if (d->aa_spacing > 0.0 && d->vel != KH_VEL_CONST)
+        return fail(KH_ERR_UNSUPPORTED, "operator anti-aliasing is built for constant velocity only");
     const int ealign = 16 / dtype_size(d->trace_dtype);
     const int cap = std::max((d->nt + 3 * ealign) / ealign * ealign, 16384 / 4);
     if ((size_t)kh::STAGES * cap * dtype_size(d->trace_dtype) > 160u * 1024u)
@@ -347,6 +351,7 @@ static GeomParams geom_of(const kh_desc& d)
     g.ap_core2 = g.use_taper ? (float)((1.0 - d.taper) * d.aperture * (1.0 - d.taper) * d.aperture) : 0.f;
     g.ap_invband = g.use_taper ? (float)(1.0 / (d.taper * d.aperture)) : 0.f;
     g.A2cull = (float)((d.aperture * (1.0 + 1e-5) + 1.0) * (d.aperture * (1.0 + 1e-5) + 1.0));
+    g.aa_c = (d.vel == KH_VEL_CONST && d.aa_spacing > 0.0) ? (float)(d.aa_spacing / (d.v0 * d.dt)) : 0.f;
     g.nt = d.nt;
     g.esize = dtype_size(d.trace_dtype);
     g.tdtype = (int)d.trace_dtype;
@@ -1202,8 +1207,8 @@ kh_status kirchhoff_velocity_grad(kh_plan p, int ntr, const float* sx, const flo
     if (ntr > 0 && (!image || !traces)) return fail(KH_ERR_INVALID_ARG, "image/traces is NULL");
     if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM || p->d.vel == KH_VEL_GRID)
         return fail(KH_ERR_UNSUPPORTED, "no velocity gradient for table traveltimes or time migration");
-    if (p->d.weight == KH_W_TRUE_AMP)
-        return fail(KH_ERR_UNSUPPORTED, "no velocity gradient with the true-amplitude weight");
+    if (p->d.weight == KH_W_TRUE_AMP || p->d.aa_spacing > 0.0)
+        return fail(KH_ERR_UNSUPPORTED, "no velocity gradient with the true-amplitude weight or anti-aliasing");
     if (p->d.trace_dtype != KH_F32) return fail(KH_ERR_UNSUPPORTED, "velocity gradient takes FP32 traces");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaMemsetAsync(out_dv0_dk, 0, 2 * sizeof(double), s);

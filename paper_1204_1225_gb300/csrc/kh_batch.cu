@@ -152,6 +152,8 @@ kh_status kirchhoff_batched_prepare(int njobs, const kh_job* jobs, kh_batch* out
         if (J.ntr > 0 && !J.traces) return bfail(KH_ERR_INVALID_ARG, "job %d: traces is NULL", j);
         if (p->d.weight == KH_W_TRUE_AMP)
             return bfail(KH_ERR_UNSUPPORTED, "job %d: the batched launch takes W = 1 or the obliquity weight", j);
+        if (p->d.aa_spacing > 0.0)
+            return bfail(KH_ERR_UNSUPPORTED, "job %d: the batched launch has no operator anti-aliasing", j);
         if (p->d.vel == KH_VEL_TABLE || p->d.vel == KH_VEL_PSTM || p->d.vel == KH_VEL_GRID)
             return bfail(KH_ERR_UNSUPPORTED, "job %d: the batched launch takes analytic depth traveltimes "
                                              "(KH_VEL_CONST / KH_VEL_LINEAR_Z)", j);

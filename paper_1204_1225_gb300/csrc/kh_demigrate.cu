@@ -173,9 +173,10 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                         const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
                         const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                         const bool v = fabsf(th - cmid) <= chc;
-                        const float W = (WGT == 1) ? zc.y * Ssum
-                                        : (WGT == 2) ? (zc.w != 0.f ? ta_weight<FAST>(zc.z, Rs, Rr, g.dim == 3) : 0.f)
-                                                     : 1.f;
+                        float W = (WGT == 1) ? zc.y * Ssum
+                                  : (WGT == 2) ? (zc.w != 0.f ? ta_weight<FAST>(zc.z, Rs, Rr, g.dim == 3) : 0.f)
+                                               : 1.f;
+                        if (g.aa_c > 0.f) W *= aa_weight<FAST>(g.aa_c, dxs, dys, dxr, dyr, Rs, Rr);
                         const float wm = v ? tp * W * mcol[iz] : 0.f;
                         const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                         const float a1 = wm * f;

@@ -181,11 +181,63 @@ __device__ __forceinline__ double grid_coord(double o, int i, double h)
 //     3D: W = z (R_s + R_r) (1/R_s^2 + 1/R_r^2) / 2,    2D: W = z sqrt(R_s R_r) (1/R_s^2 + 1/R_r^2) / 2,
 // free of the cancellation of the determinant's entries (e.g. 1 - e_x^2 near horizontal rays).
 template <bool FAST>
+__device__ __forceinline__ float ta_weight_r(float z, float Rs, float Rr, float is, float ir, bool three_d)
+{
+    const float s2 = fmaf(is, is, ir * ir);   // is = 1 / R_s, ir = 1 / R_r
+    return 0.5f * z * (three_d ? Rs + Rr : hsqrt<FAST>(Rs * Rr)) * s2;
+}
+
+template <bool FAST>
 __device__ __forceinline__ float ta_weight(float z, float Rs, float Rr, bool three_d)
 {
-    const float is = hrcp<FAST>(Rs), ir = hrcp<FAST>(Rr);
-    const float s2 = fmaf(is, is, ir * ir);
-    return 0.5f * z * (three_d ? Rs + Rr : hsqrt<FAST>(Rs * Rr)) * s2;
+    return ta_weight_r<FAST>(z, Rs, Rr, hrcp<FAST>(Rs), hrcp<FAST>(Rr), three_d);
+}
+
+// Operator anti-aliasing weight (constant velocity, aa_c = trace spacing / (v0 dt) > 0): the moveout
+// between adjacent traces L = aa_c max(|p_x|, |p_y|) samples, p = (x - s)_h / R_s + (x - r)_h / R_r;
+// 1 up to one sample, 0 from two, cos^2(pi (L - 1) / 2) between.  (dxa, dya): column minus point a.
+// is, ir: 1 / R_s, 1 / R_r (1 / max(R, 1e-30)).
+__device__ __forceinline__ float aa_weight_r(float aa_c, float dxs, float dys, float dxr, float dyr, float is, float ir)
+{
+    const float L = aa_c * fmaxf(fabsf(fmaf(dxs, is, dxr * ir)), fabsf(fmaf(dys, is, dyr * ir)));
+    if (L <= 1.f) return 1.f;
+    if (L >= 2.f) return 0.f;
+    const float c = __cosf(1.57079632679f * (L - 1.f));
+    return c * c;
+}
+
+template <bool FAST>
+__device__ __forceinline__ float aa_weight(float aa_c, float dxs, float dys, float dxr, float dyr, float Rs, float Rr)
+{
+    return aa_weight_r(aa_c, dxs, dys, dxr, dyr, hrcp<FAST>(fmaxf(Rs, 1e-30f)), hrcp<FAST>(fmaxf(Rr, 1e-30f)));
+}
+
+// Warp-uniform class of the anti-aliasing weight over one trace's contributions to the active
+// lanes' columns at squared depths z^2 in [z2lo, z2hi]: 0 every weight is 0 (L >= 2), 1 every
+// weight is 1 (L <= 1), 2 mixed.  A component a / R_s + b / R_r of p (a, b: the column's
+// horizontal offsets from source and receiver along one axis) has terms of fixed sign whose size
+// |a| / sqrt(h^2 + z^2) falls with depth: the component is at most its terms' sizes at the
+// shallowest depth summed, and at least, over the whole range, their sizes at the deepest depth
+// summed where a and b share a sign, else the larger of (deepest size of one term) - (shallowest
+// size of the other).  Classes decided on these bounds differ from the per-contribution weight only
+// where FP32 rounding puts L at 1 or 2, where the weight's slope is 0.
+__device__ __forceinline__ int aa_class(float aa_c, float dxs, float dys, float dxr, float dyr, float z2lo,
+                                        float z2hi, bool active)
+{
+    const float hs2 = fmaf(dxs, dxs, dys * dys), hr2 = fmaf(dxr, dxr, dyr * dyr);
+    const float is0 = rsqrtf(fmaxf(hs2 + z2lo, 1e-30f)), is1 = rsqrtf(fmaxf(hs2 + z2hi, 1e-30f));
+    const float ir0 = rsqrtf(fmaxf(hr2 + z2lo, 1e-30f)), ir1 = rsqrtf(fmaxf(hr2 + z2hi, 1e-30f));
+    auto comp = [&](float a, float b, float& ub, float& lb) {
+        const float a0 = fabsf(a) * is0, a1 = fabsf(a) * is1, b0 = fabsf(b) * ir0, b1 = fabsf(b) * ir1;
+        ub = a0 + b0;
+        lb = (a * b >= 0.f) ? a1 + b1 : fmaxf(fmaxf(a1 - b0, b1 - a0), 0.f);
+    };
+    float ubx, lbx, uby, lby;
+    comp(dxs, dxr, ubx, lbx);
+    comp(dys, dyr, uby, lby);
+    if (__all_sync(0xffffffffu, !active || aa_c * fmaxf(lbx, lby) >= 2.f)) return 0;
+    if (__all_sync(0xffffffffu, !active || aa_c * fmaxf(ubx, uby) <= 1.f)) return 1;
+    return 2;
 }
 
 // Gridded model (KH_VEL_GRID): node column gi of image column ix in the tables' node grid and the

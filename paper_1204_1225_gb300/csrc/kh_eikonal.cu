@@ -1,8 +1,8 @@
 // Gridded model v(x, z) (KH_VEL_GRID): first-arrival traveltime tables per surface location and
 // what the migration needs to read them.
 //
-// Sec. 3 takes the traveltimes of Eq. (1) from "high-frequency (ray-theoretic) approximations"
-// with "a single propagation path": the first-arrival time, the solution of |grad T| = s (slowness
+// Sec. 3 takes the traveltimes of Eq. (1) from the high-frequency limit of ray theory, one path
+// per source and image point: the first-arrival time, the solution of |grad T| = s (slowness
 // s = 1/v) with T = 0 at the surface location.  Per location x_s, one CTA solves it on the node
 // grid (ox + i h, j h) held in shared memory:
 //   T = T0 + tau, T0 = s0 |x - x_s| (the exact time of the source's own slowness s0), so the

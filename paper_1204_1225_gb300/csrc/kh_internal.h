@@ -82,6 +82,10 @@ __host__ __device__ inline double vrms2_of(double v0, double k, double t0)
 // widened by `margin` (a little more than the aperture), so a midpoint outside it is farther
 // than the aperture from every column and is dropped with the traces that have no offset bin.
 // With a full aperture (margin <= 0) there is one cell and nothing is dropped.
+// Bit of the migration kernels' weight template parameter that compiles the operator
+// anti-aliasing weight in (constant velocity; kernels without it never evaluate it).
+constexpr int W_AA = 4;
+
 // Offset bins the velocity-analysis kernels carry weights for (the plan allows up to 256).
 constexpr int MAX_BIN_WEIGHTS = 256;
 constexpr int MAX_CELLS_PER_AXIS = 16;
@@ -167,6 +171,7 @@ struct GeomParams {
     int use_taper;           // the weight tapers over the outer part of the aperture
     float ap_core, ap_core2; // radius (and its square) up to which the taper is 1
     float ap_invband;        // 1 / width of the taper band
+    float aa_c;              // operator anti-aliasing (constant v): aa_spacing / (v0 dt); 0 = off
     float A2cull;            // enlarged, for the conservative tile cull
     // traces
     int nt;

@@ -414,7 +414,7 @@ __device__ __forceinline__ int mig_producer(MigSmem& S, TT* data, int cap, const
                     S.refr[s][slot] = make_float4(rr.Rc2, qir, rr.wc, rr.iuc);
                     S.hda[s][slot] = make_float4((float)(box.cx - 2.0 * h.x), (float)(box.cy - 2.0 * h.y),
                                                  (float)(box.cx - 2.0 * h.z), (float)(box.cy - 2.0 * h.w));
-                } else if constexpr (VEL == VK_CONST && WGT == 2) {
+                } else if constexpr (VEL == VK_CONST && (WGT & 3) == 2) {
                     // the true-amplitude kernels take the legs relative to the tile centre: FP64 legs
                     // at the tile centre c, R_ac = |c - a|, and tau_c = (R_sc + R_rc) / (v0 dt) - t0/dt
                     {
@@ -536,6 +536,8 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                                             const TileBox& box, int bin, float* __restrict__ image,
                                             const WaitCfg& wc, const TB* tab, float2* srcc, int cap, int n)
 {
+    constexpr int WB = WGT & 3;                 // the weight (KH_W_*)
+    constexpr bool AA = (WGT & W_AA) != 0;      // operator anti-aliasing compiled in (constant v)
     const int tid = threadIdx.x, lane = tid & 31;
     int tx, ty, tzg;
     thread_column(ts, tid, tx, ty, tzg);
@@ -557,6 +559,13 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     const TT* ring = data - LEAD;
     const unsigned ring_last = (unsigned)(LEAD + STAGES * cap + SLACK - 2);   // the kernel's ring
     const bool zfull = izb + NZ <= g.nz;   // all 16 depths of this thread lie in the grid
+    // constant velocity with anti-aliasing: the range of z^2 over the thread's depths
+    float aa_z2lo = 0.f, aa_z2hi = 0.f;
+    if constexpr (AA) {
+        const float za = zc[0].z, zb = zc[NZ - 1].z;
+        aa_z2lo = (za <= 0.f && zb >= 0.f) ? 0.f : fminf(za * za, zb * zb);
+        aa_z2hi = fmaxf(za * za, zb * zb);
+    }
     // gridded model: the column's node column and fraction, and its first node row (threads
     // whose depths all lie below the image read the last rows)
     const float* gcol = nullptr;
@@ -633,7 +642,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
                         // w_z multiplies the sum once, at the store
-                        if constexpr (WGT == 1) {
+                        if constexpr (WB == 1) {
                             const float Rsum = hsqrt<FAST>(dhs2 + zc[i].y) + hsqrt<FAST>(dhr2 + zc[i].y);
                             acc[i] = fmaf(Rsum, val, acc[i]);
                         }
@@ -691,7 +700,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
                         // w_z multiplies the sum once, at the store
-                        if constexpr (WGT == 1) {
+                        if constexpr (WB == 1) {
                             const float Rsum = hsqrt<FAST>(dhs2 + zc[i].y) + hsqrt<FAST>(dhr2 + zc[i].y);
                             acc[i] = fmaf(Rsum, val, acc[i]);
                         }
@@ -740,22 +749,30 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
                         // W = w_z (R_s + R_r); w_z multiplies the sum once, at the store
-                        if constexpr (WGT == 1) acc[i] = fmaf(sv.y + R, val, acc[i]);
+                        if constexpr (WB == 1) acc[i] = fmaf(sv.y + R, val, acc[i]);
                         else acc[i] += val;
                     }
                 };
                 if (unchecked) zloop(std::false_type(), std::false_type());
                 else if (g.use_taper) zloop(std::true_type(), std::true_type());
                 else zloop(std::true_type(), std::false_type());
-            } else if constexpr (VEL == VK_CONST && WGT != 2) {
+            } else if constexpr (VEL == VK_CONST && WB != 2) {
                 const float dxs = cxf - h.x, dys = cyf - h.y;
                 const float dxr = cxf - h.z, dyr = cyf - h.w;
+                // anti-aliasing: skip a trace whose every weight here is 0; evaluate the weight
+                // per contribution only where the warp's depth range holds weights below 1
+                int aacls = 1;
+                if constexpr (AA) {
+                    aacls = aa_class(g.aa_c, dxs, dys, dxr, dyr, aa_z2lo, aa_z2hi, inside);
+                    if (aacls == 0) continue;
+                }
                 const float dhs2 = fmaf(dxs, dxs, dys * dys);
                 const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
-                auto zloop = [&](auto checked, auto tapered) {
+                auto zloop = [&](auto checked, auto tapered, auto alias) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
-                        const float Ssum = hsqrt<FAST>(dhs2 + zc[i].x) + hsqrt<FAST>(dhr2 + zc[i].x);
+                        const float Rs = hsqrt<FAST>(dhs2 + zc[i].x), Rr = hsqrt<FAST>(dhr2 + zc[i].x);
+                        const float Ssum = Rs + Rr;
                         const float th = fmaf(Ssum, g.C1, fmaf(Ssum, g.C1lo, c0rel));
                         float val;
                         if constexpr (decltype(checked)::value)
@@ -763,19 +780,37 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
+                        if constexpr (decltype(alias)::value) val *= aa_weight<FAST>(g.aa_c, dxs, dys, dxr, dyr, Rs, Rr);
                         // w_z multiplies the sum once, at the store
-                        if constexpr (WGT == 1) acc[i] = fmaf(Ssum, val, acc[i]);
+                        if constexpr (WB == 1) acc[i] = fmaf(Ssum, val, acc[i]);
                         else acc[i] += val;
                     }
                 };
-                if (unchecked) zloop(std::false_type(), std::false_type());
-                else if (g.use_taper) zloop(std::true_type(), std::true_type());
-                else zloop(std::true_type(), std::false_type());
+                using T_ = std::true_type;
+                using F_ = std::false_type;
+                bool done = false;
+                if constexpr (AA) {
+                    if (aacls == 2) {
+                        if (unchecked) zloop(F_(), F_(), T_());
+                        else zloop(T_(), T_(), T_());
+                        done = true;
+                    }
+                }
+                if (done) {
+                } else if (unchecked) zloop(F_(), F_(), F_());
+                else if (g.use_taper) zloop(T_(), T_(), F_());
+                else zloop(T_(), F_(), F_());
             } else if constexpr (VEL == VK_CONST) {
                 // the true-amplitude weight: each leg relative to the tile centre: R_a - R_ac = (q_a - q_ac) / (R_a + R_ac) with
                 // q_a - q_ac = dP_a + (z^2 - z_c^2), so tau - lo = c0rel + C1 (dR_s + dR_r) carries only
                 // quantities of a few tens of samples (the full two-way time, hundreds of samples,
                 // is in the FP64 reference); the source leg (dR_s, R_s) is cached per source position
+                // anti-aliasing classes as in the direct branch
+                int aacls = 1;
+                if constexpr (AA) {
+                    aacls = aa_class(g.aa_c, cxf - h.x, cyf - h.y, cxf - h.z, cyf - h.w, aa_z2lo, aa_z2hi, inside);
+                    if (aacls == 0) continue;
+                }
                 const float4 a = S.hda[s][t];
                 const float4 rf = S.refs[s][t];   // (R_sc, R_rc, -, -)
                 if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
@@ -794,14 +829,14 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
                 const float exr = cxf - h.z, eyr = cyf - h.w;
                 const float dhr2 = fmaf(exr, exr, eyr * eyr);
-                auto zloop = [&](auto checked, auto tapered) {
+                auto zloop = [&](auto checked, auto tapered, auto alias) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         const float4 c = zc[i];
                         const float2 sv = my_src[i * CONSUMERS];   // (dR_s, R_s)
                         const float Rr = hsqrt<FAST>(dhr2 + c.x);
                         const float dR = (dPr + c.y) * hrcp<FAST>(fmaxf(Rr + rf.y, 1e-30f));
-                        const float Rs = sv.y, Ssum = Rs + Rr;
+                        const float Rs = sv.y;
                         const float th = fmaf(g.C1, sv.x + dR, c0rel);
                         float val;
                         if constexpr (decltype(checked)::value)
@@ -809,13 +844,34 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
-                        // the weight per contribution (0 on the surface row, where it is undefined)
-                        acc[i] = fmaf(c.w != 0.f ? ta_weight<FAST>(c.z, Rs, Rr, g.dim == 3) : 0.f, val, acc[i]);
+                        // the weight per contribution (0 on the surface row, where it is undefined);
+                        // with anti-aliasing both weights share the legs' reciprocals
+                        float W;
+                        if constexpr (decltype(alias)::value) {
+                            const float is = hrcp<FAST>(fmaxf(Rs, 1e-30f)), ir = hrcp<FAST>(fmaxf(Rr, 1e-30f));
+                            W = c.w != 0.f ? ta_weight_r<FAST>(c.z, Rs, Rr, is, ir, g.dim == 3) *
+                                                 aa_weight_r(g.aa_c, cxf - h.x, cyf - h.y, exr, eyr, is, ir)
+                                           : 0.f;
+                        } else {
+                            W = c.w != 0.f ? ta_weight<FAST>(c.z, Rs, Rr, g.dim == 3) : 0.f;
+                        }
+                        acc[i] = fmaf(W, val, acc[i]);
                     }
                 };
-                if (unchecked) zloop(std::false_type(), std::false_type());
-                else if (g.use_taper) zloop(std::true_type(), std::true_type());
-                else zloop(std::true_type(), std::false_type());
+                using T_ = std::true_type;
+                using F_ = std::false_type;
+                bool done = false;
+                if constexpr (AA) {
+                    if (aacls == 2) {
+                        if (unchecked) zloop(F_(), F_(), T_());
+                        else zloop(T_(), T_(), T_());
+                        done = true;
+                    }
+                }
+                if (done) {
+                } else if (unchecked) zloop(F_(), F_(), F_());
+                else if (g.use_taper) zloop(T_(), T_(), F_());
+                else zloop(T_(), F_(), F_());
             } else {
                 const float4 a = S.hda[s][t];
                 if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
@@ -826,7 +882,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         float sqs = 0.f;
-                        const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zc[i], rs, sqs);
+                        const float rho_s = leg_delta_m<WB, FAST>(dPs, dhs2, zc[i], rs, sqs);
                         my_src[i * CONSUMERS] = make_float2(leg_log<LPT>(rho_s, g, 0.f), sqs);
                     }
                     psx = __float_as_uint(h.x);
@@ -841,7 +897,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                     for (int i = 0; i < NZ; ++i) {
                         float sqr = 0.f;
                         const float2 sv = my_src[i * CONSUMERS];   // (C1 ln(1 + rho_s), sqrt(q_s))
-                        const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zc[i], rr, sqr);
+                        const float rho_r = leg_delta_m<WB, FAST>(dPr, dhr2, zc[i], rr, sqr);
                         const float th = leg_log<LPT>(rho_r, g, c0rel + sv.x);
                         float val;
                         if constexpr (decltype(checked)::value)
@@ -850,7 +906,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
                         // gamma(z) multiplies the sum once, at the store
-                        if constexpr (WGT == 1) acc[i] = fmaf(sv.y + sqr, val, acc[i]);
+                        if constexpr (WB == 1) acc[i] = fmaf(sv.y + sqr, val, acc[i]);
                         else acc[i] += val;
                     }
                 };
@@ -869,7 +925,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
         return n;
     }
     if (!col_ok) return n;
-    if constexpr (WGT == 1) {
+    if constexpr (WB == 1) {
 #pragma unroll
         for (int i = 0; i < NZ; ++i)
             acc[i] *= (VEL == VK_TABLE || VEL == VK_GRID) ? zc[i].x : zg[i];
@@ -1213,6 +1269,18 @@ template <typename TT>
 cudaError_t launch_migrate_dtype(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
                                  float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
+    if (g.aa_c > 0.f) {   // operator anti-aliasing: constant velocity only (the plan refuses the others)
+        if (vel != VK_CONST) return cudaErrorInvalidValue;
+        switch (g.weight * 2 + (fast ? 1 : 0)) {
+            case 0: return launch_migrate_t<VK_CONST, W_AA | 0, false, TT>(g, t, tr, traces, image, w, s);
+            case 1: return launch_migrate_t<VK_CONST, W_AA | 0, true, TT>(g, t, tr, traces, image, w, s);
+            case 2: return launch_migrate_t<VK_CONST, W_AA | 1, false, TT>(g, t, tr, traces, image, w, s);
+            case 3: return launch_migrate_t<VK_CONST, W_AA | 1, true, TT>(g, t, tr, traces, image, w, s);
+            case 4: return launch_migrate_t<VK_CONST, W_AA | 2, false, TT>(g, t, tr, traces, image, w, s);
+            case 5: return launch_migrate_t<VK_CONST, W_AA | 2, true, TT>(g, t, tr, traces, image, w, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (g.weight == KH_W_TRUE_AMP) {   // constant velocity only (the plan refuses the others)
         if (vel != VK_CONST) return cudaErrorInvalidValue;
         return fast ? launch_migrate_t<VK_CONST, 2, true, TT>(g, t, tr, traces, image, w, s)

@@ -2,8 +2,8 @@
 // delta(X - |x_s - x_r|) of Eq. 1) and the cell of its midpoint on a coarse grid, and the
 // traces are put in (bin, cell row, cell column, original index) order by a stable LSD radix
 // sort over all SMs.  The (bin, cell) start table then lets a CTA of the migration walk only
-// the cells that meet its tile's aperture disc ("traces which are close enough", Sec. 3 after
-// Eq. 2) instead of its whole bin, so the staging work per CTA stays proportional to the
+// the cells that meet its tile's aperture disc (the traces near enough to carry the tile's
+// reflections, Sec. 3 after Eq. 2) instead of its whole bin, so the staging work per CTA stays proportional to the
 // traces it can use as surveys grow to tens of millions of traces (Sec. 2).
 //
 // Passes (each a few launches, no host synchronisation, no atomics on values, so the order is

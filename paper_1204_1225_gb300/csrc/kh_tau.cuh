@@ -190,8 +190,6 @@ __device__ __forceinline__ float leg_delta_grad_m(float dP, float dh2, const flo
     return dq * gi;
 }
 
-// Sample window [lo, hi] of one trace over a tile box, from the time bounds of both legs with
-// a slack of 2 + 2e-4 |tau| samples for FP32 rounding; false if no valid sample can reach the box.
 // Sample window [lo, hi] of a trace whose two-way time lies in [tsum_lo, tsum_hi] over the tile
 // (seconds; FP32), widened by 2 samples plus a relative 2e-4 and g.tslack and clipped to
 // [0, nt - 1]; *clipped reports a clip.  False when the window misses the trace.
@@ -211,6 +209,8 @@ __device__ __forceinline__ bool sample_window(float tsum_lo, float tsum_hi, cons
     return hi > lo;
 }
 
+// Sample window [lo, hi] of one trace over a tile box, from the time bounds of both legs with
+// a slack of 2 + 2e-4 |tau| samples for FP32 rounding; false if no valid sample can reach the box.
 __device__ __forceinline__ bool trace_window(const float4& h, const TileBox& box, int vel,
                                              const GeomParams& g, int& lo, int& hi, bool* clipped = nullptr,
                                              const PstmTile* pt = nullptr)

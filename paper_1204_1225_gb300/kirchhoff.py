@@ -43,7 +43,7 @@ class kh_desc(ctypes.Structure):
                 ("table_spacing", ctypes.c_double), ("table_dtype", ctypes.c_int),
                 ("weight", ctypes.c_int), ("r0", ctypes.c_double), ("aperture", ctypes.c_double),
                 ("nt", ctypes.c_int), ("t0", ctypes.c_double), ("dt", ctypes.c_double),
-                ("trace_dtype", ctypes.c_int), ("taper", ctypes.c_double)]
+                ("trace_dtype", ctypes.c_int), ("taper", ctypes.c_double), ("aa_spacing", ctypes.c_double)]
 
 
 class kh_grid(ctypes.Structure):
@@ -195,7 +195,8 @@ def desc_from(s, trace_dtype=torch.float32, vel=None, table_spacing=None,
     return kh_desc(s.dim, s.nx, s.ny if s.dim == 3 else 1, s.nz, s.ox, s.oy, s.oz, s.dx, s.dy,
                    s.dz, s.n_bins, s.bin_width, vel, s.v0, s.k, table_spacing,
                    _TABLE_DT[table_dtype], {"one": KH_W_ONE, "obliq": KH_W_OBLIQ_SPREAD, "ta": KH_W_TRUE_AMP}[s.weight],
-                   s.r0, s.aperture, s.nt, s.t0, s.dt, _DT[trace_dtype], float(getattr(s, "taper", 0.0)))
+                   s.r0, s.aperture, s.nt, s.t0, s.dt, _DT[trace_dtype], float(getattr(s, "taper", 0.0)),
+                   float(getattr(s, "aa_spacing", 0.0)))
 
 
 # ------------------------------------------------------------ functions named as the C ABI

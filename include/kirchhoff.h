@@ -445,6 +445,30 @@ KH_API kh_status kirchhoff_profile_read(kh_plan p, double* kernel_ms, long long*
 KH_API kh_status kirchhoff_staging_stats(kh_plan p, void* cuda_stream, unsigned long long* examined,
                                          unsigned long long* staged, unsigned long long* ctas);
 
+/* Host-resident migration (no counterpart in the paper: the interface for surveys that live in
+ * host memory).  The same operation and result as kirchhoff_migrate, with sx, sy, rx, ry and
+ * traces in HOST memory (the layouts of kirchhoff_migrate; sy, ry may be NULL for dim 2) and the
+ * image written to HOST memory `image` ([n_bins][ny][nx][nz] FP32).  The call only enqueues: the
+ * inputs are copied into one of two plan-owned slots of device buffers on a plan-owned copy
+ * stream, migrated on `cuda_stream` once they are in, and the image is copied back on a second
+ * plan-owned copy stream once the migration is done.  Consecutive calls use the slots in turn,
+ * so call n's inputs travel while call n-1 migrates and call n-1's image travels while call n
+ * migrates.  The host buffers belong to the library until the call's image has arrived: make a
+ * stream wait for it with kirchhoff_host_join, then synchronise that stream (kirchhoff_sync
+ * reports a bounded wait that ran out).  Pinned host memory (cudaHostAlloc / cudaHostRegister)
+ * gives the overlap; pageable memory gives the same result with copies that block the caller.
+ * Successive calls must use the same `cuda_stream`.  The slots hold two copies of the traces
+ * and two images on the device.  Errors: KH_ERR_INVALID_ARG for a NULL plan, image, header or
+ * trace array (ntr > 0) or ntr < 0; KH_ERR_CUDA when an allocation, copy or launch fails; every
+ * error of kirchhoff_migrate. */
+KH_API kh_status kirchhoff_migrate_host(kh_plan p, int ntr, const float* sx, const float* sy,
+                                        const float* rx, const float* ry, const void* traces, float* image,
+                                        void* cuda_stream);
+
+/* Makes `cuda_stream` wait (on the device) until every image that kirchhoff_migrate_host has
+ * enqueued for this plan has arrived in host memory.  Returns without waiting on the host. */
+KH_API kh_status kirchhoff_host_join(kh_plan p, void* cuda_stream);
+
 /* Number of kernel launches issued by this plan since creation (for launch accounting). */
 KH_API long long kirchhoff_launch_count(kh_plan p);
 

@@ -1075,6 +1075,7 @@ kh_status kirchhoff_destroy(kh_plan p)
         if (pr.second) cudaEventDestroy(pr.second);
     }
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    host_release(p);
     delete p;
     return KH_OK;
 }

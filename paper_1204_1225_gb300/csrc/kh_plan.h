@@ -78,12 +78,27 @@ struct kh_plan_s {
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_open;
+    // host-resident migration (kirchhoff_migrate_host): two slots of device headers ([4][cap_ntr]:
+    // sx, sy, rx, ry), traces and image used in turn, a copy stream per direction, and per slot
+    // the events of its last inputs-in, migration and image-out
+    struct HostSlot {
+        float* hdr = nullptr;
+        unsigned char* traces = nullptr;
+        float* image = nullptr;
+        size_t cap_ntr = 0, cap_tr = 0;
+        cudaEvent_t in_done = nullptr, mig_done = nullptr, out_done = nullptr;
+        bool used = false;
+    } host[2];
+    cudaStream_t host_in = nullptr, host_out = nullptr;
+    int host_next = 0;
 };
 
 namespace kh {
 kh_status set_error(kh_status s, const char* msg);
 kh_status set_cuda_error(cudaError_t e, const char* what);
 kh_status ensure_traces_ws(kh_plan_s* p, int ntr);
+// Frees the host-resident migration's slots, streams and events (kirchhoff_destroy).
+void host_release(kh_plan_s* p);
 // Offset bin and midpoint cell per trace, stable multi-CTA radix sort by (bin, cell), the
 // (bin, cell) starts and the sorted headers.  `spatial` = false sorts by bin alone (one cell
 // per bin; midpoints that reach no column are still dropped).  Sets p->cur_perm, p->cur_cg.

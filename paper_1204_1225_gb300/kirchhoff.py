@@ -67,7 +67,7 @@ EXPORTS = ["kirchhoff_create", "kirchhoff_destroy", "kirchhoff_migrate", "kirchh
            "kirchhoff_version", "kirchhoff_profile", "kirchhoff_profile_read",
            "kirchhoff_migrate_noalloc", "kirchhoff_fit_report", "kirchhoff_staging_stats",
            "kirchhoff_cell_grid", "kirchhoff_bin_sort", "kirchhoff_semblance", "kirchhoff_grid_layout",
-           "kirchhoff_grid_tables", "kirchhoff_grid_read"]
+           "kirchhoff_grid_tables", "kirchhoff_grid_read", "kirchhoff_migrate_host", "kirchhoff_host_join"]
 
 
 def lib(path: str = LIB_PATH):
@@ -114,6 +114,8 @@ def lib(path: str = LIB_PATH):
                                                 ctypes.POINTER(kh_grid)]
             L.kirchhoff_grid_tables.argtypes = [P, ctypes.POINTER(kh_grid), P, I, P, P]
             L.kirchhoff_grid_read.argtypes = [P, P, P, ctypes.POINTER(I), P]
+            L.kirchhoff_migrate_host.argtypes = [P, I, P, P, P, P, P, P, P]
+            L.kirchhoff_host_join.argtypes = [P, P]
             for name in EXPORTS:
                 getattr(L, name).restype = S
             L.kirchhoff_launch_count.restype = ctypes.c_longlong
@@ -160,6 +162,23 @@ def _validate(specs, device=None):
         if t.device.index != dev:
             raise ValueError(f"kirchhoff: {name} is on cuda:{t.device.index}, the plan's device "
                              f"is cuda:{dev}")
+        if not t.is_contiguous():
+            raise ValueError(f"kirchhoff: {name} must be contiguous")
+
+
+def _validate_host(specs):
+    """As _validate for the host-resident entry point: every tensor in host memory."""
+    for t, name, dtype, numel, shape in specs:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"kirchhoff: {name} must be a torch tensor")
+        if t.dtype != dtype:
+            raise ValueError(f"kirchhoff: {name} must be {dtype}, got {t.dtype}")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"kirchhoff: {name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"kirchhoff: {name} must have {numel} elements, got {t.numel()}")
+        if t.is_cuda:
+            raise ValueError(f"kirchhoff: {name} must live in host memory (kirchhoff_migrate_host)")
         if not t.is_contiguous():
             raise ValueError(f"kirchhoff: {name} must be contiguous")
 
@@ -214,6 +233,24 @@ def kirchhoff_destroy(plan: int) -> None:
 def kirchhoff_migrate(plan, ntr, sx, sy, rx, ry, traces, image, stream=None) -> None:
     _check(lib().kirchhoff_migrate(ctypes.c_void_p(plan), int(ntr), _ptr(sx), _ptr(sy), _ptr(rx),
                                    _ptr(ry), _ptr(traces), _ptr(image), _stream(stream)))
+
+
+def _host_ptr(t):
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("kirchhoff: host tensors must be contiguous and in host memory")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kirchhoff_migrate_host(plan, ntr, sx, sy, rx, ry, traces, image, stream=None) -> None:
+    _check(lib().kirchhoff_migrate_host(ctypes.c_void_p(plan), int(ntr), _host_ptr(sx), _host_ptr(sy),
+                                        _host_ptr(rx), _host_ptr(ry), _host_ptr(traces), _host_ptr(image),
+                                        _stream(stream)))
+
+
+def kirchhoff_host_join(plan, stream=None) -> None:
+    _check(lib().kirchhoff_host_join(ctypes.c_void_p(plan), _stream(stream)))
 
 
 def kirchhoff_demigrate(plan, ntr, sx, sy, rx, ry, image, traces_out, stream=None) -> None:
@@ -461,6 +498,26 @@ class Plan:
             out = torch.empty(self.image_shape, dtype=torch.float32, device=traces.device)
         kirchhoff_migrate(self.handle, hdr.ntr, *hdr.args(), traces, out, stream)
         return out
+
+    def migrate_host(self, hdr, traces, out, stream=None):
+        """Migration of host-resident inputs into a host image (kirchhoff_migrate_host): ``hdr``
+        (sx, sy, rx, ry) CPU float32 tensors, ``traces`` a CPU tensor of the plan's trace dtype,
+        ``out`` a CPU float32 tensor of the image shape, all pinned for overlap.  Only enqueues:
+        the tensors must stay alive and unchanged until ``host_join`` and a synchronisation of the
+        stream; consecutive calls overlap one call's copies with the other's migration."""
+        hdr = tuple(hdr)
+        ntr = int(hdr[0].numel())
+        specs = [(t, name, torch.float32, ntr, None) for name, t in zip(("sx", "sy", "rx", "ry"), hdr)]
+        specs += [(traces, "traces", self.trace_dtype, ntr * self.nt, None),
+                  (out, "image", torch.float32, None, self.image_shape)]
+        _validate_host(specs)
+        self._host_refs = getattr(self, "_host_refs", [])[-1:] + [(hdr, traces, out)]
+        kirchhoff_migrate_host(self.handle, ntr, *hdr, traces, out, stream)
+        return out
+
+    def host_join(self, stream=None):
+        """Makes ``stream`` wait until every image of ``migrate_host`` has arrived on the host."""
+        kirchhoff_host_join(self.handle, stream)
 
     def demigrate(self, hdr: Headers, image, out=None, stream=None):
         specs = _header_specs(hdr) + [(image, "image", torch.float32, None, self.image_shape)]

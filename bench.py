@@ -68,8 +68,8 @@ PIPE_MIX = {
     "3d-vz-100k-256cube-table-f16-f16": {"issue": 33.10, "fma": 19.69, "alu": 4.07, "xu": 2.20, "lsu": 5.53},
     "3d-vz-10k-256cube-table-f16-f16": {"issue": 33.10, "fma": 19.69, "alu": 4.07, "xu": 2.20, "lsu": 5.53},
     # adjoint (k_demigrate) and gradient (k_vgrad), headline variants measured on the 10k case
-    "3d-vz-100k-256cube-demigrate": {"issue": 66.69, "fma": 32.69, "alu": 10.86, "xu": 3.98, "lsu": 10.08},
-    "3d-vz-10k-256cube-demigrate": {"issue": 66.69, "fma": 32.69, "alu": 10.86, "xu": 3.98, "lsu": 10.08},
+    "3d-vz-100k-256cube-demigrate": {"issue": 68.11, "fma": 32.78, "alu": 12.33, "xu": 3.98, "lsu": 10.36},
+    "3d-vz-10k-256cube-demigrate": {"issue": 68.11, "fma": 32.78, "alu": 12.33, "xu": 3.98, "lsu": 10.36},
     "3d-vz-100k-256cube-vgrad": {"issue": 54.58, "fma": 34.94, "alu": 8.32, "xu": 3.15, "lsu": 5.49},
     "3d-vz-10k-256cube-vgrad": {"issue": 54.58, "fma": 34.94, "alu": 8.32, "xu": 3.15, "lsu": 5.49},
     # prestack time migration (k_migrate<time migration, obliquity, fast, sample pairs>)
@@ -79,6 +79,10 @@ PIPE_MIX = {
     # tile-relative legs, source leg cached), measured on the 10k-trace case
     "3d-ta-100k-256cube": {"issue": 33.17, "fma": 17.81, "alu": 6.05, "xu": 4.15, "lsu": 3.36},
     "3d-ta-10k-256cube": {"issue": 33.17, "fma": 17.81, "alu": 6.05, "xu": 4.15, "lsu": 3.36},
+    # the same with operator anti-aliasing (25 m spacing): per in-aperture pair, including the pairs
+    # whose weight the warp's bounds prove 0 and that are skipped
+    "3d-ta-aa-100k-256cube": {"issue": 19.03, "fma": 8.82, "alu": 5.03, "xu": 1.61, "lsu": 0.88},
+    "3d-ta-aa-10k-256cube": {"issue": 19.03, "fma": 8.82, "alu": 5.03, "xu": 1.61, "lsu": 0.88},
     # persistent batched kernel, constant velocity, sample pairs (measured on the 8-job small batch)
     "batch64-3d-vz-f32": {"issue": 23.35, "fma": 13.83, "alu": 3.46, "xu": 2.38, "lsu": 2.54},
 }
@@ -91,12 +95,13 @@ TRAFFIC = {
     "3d-vz-40k-128cube": 281054208 + 111904000,
     "25d-vz-20k-512x400": 91543808 + 2981376,
     "25d-vxz-20k-512x400": 138770944 + 5204480,
-    "3d-vz-10k-256cube-demigrate": 4820799488 + 8277082112,
+    "3d-vz-10k-256cube-demigrate": 5606103296 + 8223564800,
     "3d-vz-10k-256cube-vgrad": 1127874560 + 15597568,
     "3d-vz-10k-256cube-table-u16-f16": 37533696 + 1023990784,
     "3d-vz-10k-256cube-table-f16-f16": 35020800 + 1024065536,
     "3d-pstm-10k-256cube": 87162880 + 1023754240,
     "3d-ta-10k-256cube": 93872128 + 1025078272,
+    "3d-ta-aa-10k-256cube": 96422400 + 1025947136,
 }
 
 # Parity bars against the FP64 oracle (relative L2 over the sampled outputs): FP32 forms, and the

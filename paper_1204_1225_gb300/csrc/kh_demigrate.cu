@@ -26,12 +26,14 @@ constexpr int DM_ROWS = 96;     // window rows per lane (the host sizes tiles to
 constexpr int DM_TILE = 1024;   // image samples per tile
 constexpr int DM_MAXZ = 64;     // depth samples per tile
 
+// The depth loops read the next depth's inputs one depth ahead, past the last depth on the last
+// one (the value is not used): each per-depth array has one entry to spare.
 struct __align__(16) DmSmem {
     float buf[DM_WARPS][DM_ROWS][32];
-    float mt[DM_TILE];
-    float4 zc[DM_MAXZ];
-    float z2[DM_MAXZ];
-    float2 src[DM_WARPS][2][32];   // per warp and source group: (C1 ln(1 + rho_s), sqrt(q_s))
+    float mt[DM_TILE + 1];
+    float4 zc[DM_MAXZ + 1];
+    float z2[DM_MAXZ + 1];
+    float2 src[DM_WARPS][2][33];   // per warp and source group: (C1 ln(1 + rho_s), sqrt(q_s))
 };
 
 static_assert(DM_ROWS == DM_ROWS_HOST, "window rows");
@@ -162,9 +164,11 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                     const float dxr = cxf - h.z, dyr = cyf - h.w;
                     const float dhs2 = fmaf(dxs, dxs, dys * dys);
                     const float dhr2 = fmaf(dxr, dxr, dyr * dyr);
+                    // the next depth's inputs read ahead of this depth's window stores (as below)
+                    float4 zc = S.zc[0];   // (z^2, w_z, z, 1 off the surface row)
+                    float mz = mcol[0];
 #pragma unroll 4
                     for (int iz = 0; iz < dt.tz; ++iz) {
-                        const float4 zc = S.zc[iz];   // (z^2, w_z, z, 1 off the surface row)
                         const float Rs = hsqrt<FAST>(dhs2 + zc.x);
                         const float Rr = hsqrt<FAST>(dhr2 + zc.x);
                         const float Ssum = Rs + Rr;
@@ -177,9 +181,11 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                                   : (WGT == 2) ? (zc.w != 0.f ? ta_weight<FAST>(zc.z, Rs, Rr, g.dim == 3) : 0.f)
                                                : 1.f;
                         if (g.aa_c > 0.f) W *= aa_weight<FAST>(g.aa_c, dxs, dys, dxr, dyr, Rs, Rr);
-                        const float wm = v ? tp * W * mcol[iz] : 0.f;
+                        const float wm = v ? tp * W * mz : 0.f;
                         const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                         const float a1 = wm * f;
+                        zc = S.zc[iz + 1];
+                        mz = mcol[iz + 1];
                         col0[row * 32] += wm - a1;
                         col0[row * 32 + 32] += a1;
                     }
@@ -212,22 +218,29 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                             __syncwarp();
                             const float2* sl = &S.src[warp][my_group][0];
                             const int nzh = min(32, dt.tz - hz);
+                            // the next depth's shared-memory inputs are read before this depth's
+                            // window stores (which the compiler cannot reorder them past), so that
+                            // its arithmetic overlaps the read-modify-write of this one
+                            float4 zk = S.zc[hz];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
+                            float2 sv = sl[0];      // (C1 ln(1 + rho_s), sqrt(q_s))
+                            float mz = mcol[hz], wz = S.z2[hz];
 #pragma unroll 4
                             for (int j = 0; j < nzh; ++j) {
-                                const int iz = hz + j;
-                                const float4 zk = S.zc[iz];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
-                                const float2 sv = sl[j];      // (C1 ln(1 + rho_s), sqrt(q_s))
                                 float sqr = 0.f;
                                 const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
                                 const float th = leg_log<LPT>(rho_r, g, c0rel + sv.x);
                                 const float tc = fmaxf(th, 0.f);   // within EDGE_EPS below 0: the first row
-                        const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
+                                const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
                                 const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                                 const bool v = fabsf(th - cmid) <= chc;
-                                const float W = (WGT == 1) ? S.z2[iz] * (sv.y + sqr) : 1.f;
-                                const float wm = v ? tp * W * mcol[iz] : 0.f;
+                                const float W = (WGT == 1) ? wz * (sv.y + sqr) : 1.f;
+                                const float wm = v ? tp * W * mz : 0.f;
                                 const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                                 const float a1 = wm * f;
+                                zk = S.zc[hz + j + 1];
+                                sv = sl[j + 1];
+                                mz = mcol[hz + j + 1];
+                                wz = S.z2[hz + j + 1];
                                 col0[row * 32] += wm - a1;
                                 col0[row * 32 + 32] += a1;
                             }
@@ -237,21 +250,26 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                         const float dPs = fmaf(dxc, cxf + ah.x, dyc * (cyf + ah.y));
                         const float exs = cxf - h.x, eys = cyf - h.y;
                         const float dhs2 = fmaf(exs, exs, eys * eys);
+                        // the next depth's inputs read ahead of this depth's window stores (as above)
+                        float4 zk = S.zc[0];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
+                        float mz = mcol[0], wz = S.z2[0];
 #pragma unroll 4
                         for (int iz = 0; iz < dt.tz; ++iz) {
-                            const float4 zk = S.zc[iz];   // (alpha, alpha kappa, alpha dz2, alpha z^2)
                             float sqs = 0.f, sqr = 0.f;
                             const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zk, rs, sqs);
                             const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
                             const float th = leg_log<LPT>(rho_r, g, c0rel + leg_log<LPT>(rho_s, g, 0.f));
                             const float tc = fmaxf(th, 0.f);   // within EDGE_EPS below 0: the first row
-                        const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
+                            const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
                             const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                             const bool v = fabsf(th - cmid) <= chc;
-                            const float W = (WGT == 1) ? S.z2[iz] * (sqs + sqr) : 1.f;
-                            const float wm = v ? tp * W * mcol[iz] : 0.f;
+                            const float W = (WGT == 1) ? wz * (sqs + sqr) : 1.f;
+                            const float wm = v ? tp * W * mz : 0.f;
                             const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                             const float a1 = wm * f;
+                            zk = S.zc[iz + 1];
+                            mz = mcol[iz + 1];
+                            wz = S.z2[iz + 1];
                             col0[row * 32] += wm - a1;
                             col0[row * 32 + 32] += a1;
                         }

@@ -177,7 +177,7 @@ def _validate_host(specs):
             raise ValueError(f"kirchhoff: {name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
         if numel is not None and t.numel() != numel:
             raise ValueError(f"kirchhoff: {name} must have {numel} elements, got {t.numel()}")
-        if t.is_cuda:
+        if t.device.type != "cpu":
             raise ValueError(f"kirchhoff: {name} must live in host memory (kirchhoff_migrate_host)")
         if not t.is_contiguous():
             raise ValueError(f"kirchhoff: {name} must be contiguous")
@@ -238,7 +238,7 @@ def kirchhoff_migrate(plan, ntr, sx, sy, rx, ry, traces, image, stream=None) -> 
 def _host_ptr(t):
     if t is None:
         return None
-    if t.is_cuda or not t.is_contiguous():
+    if t.device.type != "cpu" or not t.is_contiguous():
         raise ValueError("kirchhoff: host tensors must be contiguous and in host memory")
     return ctypes.c_void_p(t.data_ptr())
 

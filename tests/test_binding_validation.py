@@ -72,3 +72,20 @@ def test_noalloc_refusals():
     _refused(lambda: kh.kirchhoff_migrate_noalloc(d, s.ntr + 1, *hdr.args(), tr, img), "sx")
     _refused(lambda: kh.kirchhoff_migrate_noalloc(d, s.ntr, *hdr.args(), tr, img,
                                                   status=torch.zeros(1)), "status", "int32")
+
+
+def test_host_entry_point_refusals():
+    s = _survey()
+    p = _plan(s)
+    hdr = kh.Headers.of(s, device="cpu").args()
+    tr = torch.zeros(s.ntr, s.nt)
+    img = torch.zeros(p.image_shape)
+    _refused(lambda: p.migrate_host(hdr, tr.half(), img), "traces", "float32")
+    _refused(lambda: p.migrate_host(hdr, tr[:-1], img), "traces", "elements")
+    _refused(lambda: p.migrate_host(hdr, tr, img[:1]), "image", "shape")
+    _refused(lambda: p.migrate_host(hdr, tr, img.double()), "image", "float32")
+    _refused(lambda: p.migrate_host(hdr[:3] + (hdr[3][:2],), tr, img), "ry", "elements")
+    _refused(lambda: p.migrate_host(hdr, tr.t(), img), "traces", "contiguous")
+    # the device-resident entry point's tensors are refused here (host memory only)
+    meta = torch.zeros(s.ntr, s.nt, device="meta")
+    _refused(lambda: p.migrate_host(hdr, meta, img), "traces")

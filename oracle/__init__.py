@@ -157,7 +157,7 @@ def ta_weight(s, pts) -> np.ndarray:
 
 
 def aa_weight(s, pts) -> np.ndarray:
-    """Anti-aliasing weight (constant velocity, ``s.aa_spacing`` > 0) at rows
+    """Anti-aliasing weight (constant velocity or v0 + k z, ``s.aa_spacing`` > 0) at rows
     (x, y, z, sx, sy, rx, ry) of ``pts``."""
     p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 7)
     W = np.empty(p.shape[0], dtype=np.float64)

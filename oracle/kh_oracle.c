@@ -55,7 +55,7 @@ typedef struct {
     const float* gloc;       /* [gnloc] x of each table's surface point, increasing */
     int gnloc, gnx, gnz;
     double gox, gh;
-    double aa_spacing;       /* vel 0: trace spacing (m) of the operator anti-aliasing; <= 0: off */
+    double aa_spacing;       /* vel 0, 1: trace spacing (m) of the operator anti-aliasing; <= 0: off */
 } ko_desc;
 
 /* Deliberate-mistake switch used only by the tests that show the pins catch errors.
@@ -427,25 +427,48 @@ int ko_ta_weight(const ko_desc* d, long n, const double* p, double* W)
     return 0;
 }
 
-/* Operator anti-aliasing (vel 0, aa_spacing > 0; a reading of the weight W of Eq. 1, which carries
- * the propagation amplitude, that also keeps the sum from aliasing): the operator's time dip across the traces,
- * the midpoint gradient of the two-way time in samples per metre,
- *     p = -(e_s + e_r)_h / (v0 dt),   e_a = (x - a) / R_a  (horizontal part; 0 where R_a = 0),
+/* Operator anti-aliasing (vel 0 or 1, aa_spacing > 0; a reading of the weight W of Eq. 1, which
+ * carries the propagation amplitude, that also keeps the sum from aliasing): the operator's time
+ * dip across the traces, the midpoint gradient of the two-way time in samples per metre,
+ *     p = -(grad_h T_s + grad_h T_r) / dt,
  * times the trace spacing is the moveout L (samples) between adjacent traces,
  *     L = aa_spacing max(|p_x|, |p_y|).
  * A contribution whose moveout exceeds one sample would alias the highest frequencies the sampling
  * carries, so the weight keeps L <= 1 whole, removes L >= 2, and falls between as
- * cos^2(pi (L - 1) / 2) (dip limitation of the operator). */
+ * cos^2(pi (L - 1) / 2) (dip limitation of the operator).
+ * The horizontal gradient of one leg's time at the image point, h = (x - a)_h, R = |x - a|:
+ *     constant v:   grad_h T = h / (v0 R);
+ *     v0 + k z:     T = (2/k) asinh(s), s = k R / (2 g), g = sqrt(v0 (v0 + k z)), and g depends
+ *                   on depth only, so grad_h T = (2/k) (k / (2 g)) (h / R) / sqrt(1 + s^2)
+ *                   = h / (R g sqrt(1 + s^2)), which tends to h / (v0 R) as k -> 0
+ * (0 where R = 0). */
+static void aa_leg(const ko_desc* d, double hx, double hy, double z, double* gx, double* gy)
+{
+    const double R = sqrt(hx * hx + hy * hy + z * z);
+    double f = 0.0;
+    if (R > 0.0) {
+        if (d->vel == 0) {
+            f = 1.0 / (d->v0 * R);
+        } else {
+            const double g = sqrt(d->v0 * (d->v0 + d->k * z));
+            const double sv = d->k * R / (2.0 * g);
+            f = 1.0 / (R * g * sqrt(1.0 + sv * sv));
+        }
+    }
+    *gx = hx * f;
+    *gy = hy * f;
+}
+
 static double aa_weight(const ko_desc* d, double x, double y, double z, double sx, double sy, double rx,
                         double ry)
 {
     if (d->aa_spacing <= 0.0) return 1.0;
-    const double Rs = sqrt((x - sx) * (x - sx) + (y - sy) * (y - sy) + z * z);
-    const double Rr = sqrt((x - rx) * (x - rx) + (y - ry) * (y - ry) + z * z);
-    const double is = Rs > 0.0 ? 1.0 / Rs : 0.0, ir = Rr > 0.0 ? 1.0 / Rr : 0.0;
-    double px = ((x - sx) * is + (x - rx) * ir) / (d->v0 * d->dt);
-    const double py = ((y - sy) * is + (y - ry) * ir) / (d->v0 * d->dt);
-    if (ko_mutation == 23) px = (x - sx) * is / (d->v0 * d->dt);   /* the receiver leg's dip dropped */
+    double gsx, gsy, grx, gry;
+    aa_leg(d, x - sx, y - sy, z, &gsx, &gsy);
+    aa_leg(d, x - rx, y - ry, z, &grx, &gry);
+    double px = (gsx + grx) / d->dt;
+    const double py = (gsy + gry) / d->dt;
+    if (ko_mutation == 23) px = gsx / d->dt;   /* the receiver leg's dip dropped */
     const double L = d->aa_spacing * fmax(fabs(px), fabs(py));
     if (L <= 1.0) return 1.0;
     if (L >= 2.0) return 0.0;
@@ -597,7 +620,7 @@ static contrib contribution(const ko_desc* d, double x, double y, double z, doub
                                                                                  (d->r0 * d->r0)))
           : (d->weight == 2) ? ta_weight(d, x, y, z, sx, sy, rx, ry)
                              : weight(d, z, Rs, Rr);
-    if (d->vel == 0 && d->aa_spacing > 0.0) c.W *= aa_weight(d, x, y, z, sx, sy, rx, ry);
+    if ((d->vel == 0 || d->vel == 1) && d->aa_spacing > 0.0) c.W *= aa_weight(d, x, y, z, sx, sy, rx, ry);
     if (want_grad) {
         c.dtau_dv0 = (dsv + drv) / d->dt;
         c.dtau_dk = (dsk + drk) / d->dt;

@@ -94,8 +94,76 @@ def check_brute_force_sum():
     assert not np.allclose(oracle.migrate_points(off, d, pts), got)   # the weight acts here
 
 
+def tau_lin(s, p, mx=0.0, my=0.0):
+    """Two-way time in samples of v0 + k z from the oracle's own traveltime (pinned elsewhere by
+    its closed forms and quadrature), with the trace's midpoint shifted by (mx, my)."""
+    x, y, z, sx, sy, rx, ry = p
+    Rs = math.sqrt((x - sx - mx) ** 2 + (y - sy - my) ** 2 + z * z)
+    Rr = math.sqrt((x - rx - mx) ** 2 + (y - ry - my) ** 2 + z * z)
+    return float(np.sum(oracle.traveltime(s, np.array([Rs, Rr]), z))) / s.dt
+
+
+def check_finite_differences_linear():
+    # v(z) = 1500 + 0.8 z: the horizontal slowness of each curved leg against central differences
+    # of the two-way time over the midpoint
+    rng = np.random.default_rng(8)
+    s = base(3, 12.5).replace(vel="linear", v0=1500.0, k=0.8)
+    n = 300
+    pts = np.stack([rng.uniform(-600, 600, n), rng.uniform(-600, 600, n), rng.uniform(50, 1500, n),
+                    rng.uniform(-900, 900, n), rng.uniform(-900, 900, n), rng.uniform(-900, 900, n),
+                    rng.uniform(-900, 900, n)], 1)
+    W = oracle.aa_weight(s, pts)
+    d = 1e-3
+    for p, w in zip(pts, W):
+        px = (tau_lin(s, p, d, 0) - tau_lin(s, p, -d, 0)) / (2 * d)
+        py = (tau_lin(s, p, 0, d) - tau_lin(s, p, 0, -d)) / (2 * d)
+        L = s.aa_spacing * max(abs(px), abs(py))
+        want = 1.0 if L <= 1 else (0.0 if L >= 2 else math.cos(0.5 * math.pi * (L - 1)) ** 2)
+        assert abs(w - want) < 1e-6, (p, w, want, L)
+    assert np.any(W == 1.0) and np.any(W == 0.0) and np.any((W > 0) & (W < 1))
+    # k -> 0 gives the constant-velocity weight; the curved rays differ from the straight ones
+    s0 = s.replace(k=1e-9)
+    assert np.max(np.abs(oracle.aa_weight(s0, pts) - oracle.aa_weight(s0.replace(vel="const"), pts))) < 1e-6
+    assert not np.allclose(W, oracle.aa_weight(s.replace(vel="const"), pts))
+
+
+def check_brute_force_sum_linear():
+    rng = np.random.default_rng(17)
+    s = sv.survey_random(rng, 2, 25, 9, 1, 10, 250, n_bins=2, h=20.0, vel="linear", v0=1600.0,
+                         k=0.7).replace(aa_spacing=25.0)
+    d = sv.random_traces(s, 4, smooth=3).astype(np.float64)
+    b = oracle.bins(s)
+    pts = np.arange(int(np.prod(s.image_shape)))
+    got = oracle.migrate_points(s, d, pts)
+    want = np.zeros(pts.size)
+    for q in pts:
+        iz, ix, bb = q % s.nz, (q // s.nz) % s.nx, q // (s.nz * s.nx)
+        x, z = s.ox + ix * s.dx, s.oz + iz * s.dz
+        for j in range(s.ntr):
+            if b[j] != bb:
+                continue
+            p = (x, 0.0, z, float(s.sx[j]), 0.0, float(s.rx[j]), 0.0)
+            t = tau_lin(s, p) - s.t0 / s.dt
+            if 0 <= t <= s.nt - 1:
+                i = min(int(math.floor(t)), s.nt - 2)
+                f = t - i
+                w = oracle.aa_weight(s, [p])[0]   # W = 1 (the survey's weight "one")
+                want[q] += w * ((1 - f) * d[j, i] + f * d[j, i + 1])
+    assert np.count_nonzero(want) > pts.size // 3
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    assert not np.allclose(oracle.migrate_points(s.replace(aa_spacing=0.0), d, pts), got)
+
+
 def test_hand_values():
     check_hand_values()
+
+
+def test_finite_differences_linear_vz():
+    check_finite_differences_linear()
+
+
+def test_brute_force_sum_linear_vz():
+    check_brute_force_sum_linear()
 
 
 def test_finite_differences():
@@ -113,6 +181,7 @@ def test_brute_force_sum():
 MUTATIONS = [
     (23, check_finite_differences),   # the receiver leg's dip dropped
     (23, check_hand_values),
+    (23, check_finite_differences_linear),
 ]
 
 

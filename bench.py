@@ -123,6 +123,8 @@ WORKLOAD_MODEL = {
     "3d-ta-10k-256cube": ("const", "ta"),
     "3d-ta-aa-100k-256cube": ("const", "ta"),
     "3d-ta-aa-10k-256cube": ("const", "ta"),
+    "3d-vz-aa-100k-256cube": ("linear", "obliq"),
+    "3d-vz-aa-10k-256cube": ("linear", "obliq"),
 }
 
 
@@ -150,6 +152,11 @@ def workloads():
             vel="const", v0=2000.0, k=0.0, weight="ta", aa_spacing=25.0, name="3d-const2000-ta-aa25-100000tr-256cube"),
         "3d-ta-aa-10k-256cube": lambda: sv.survey_3d_gradient(ntr=10_000, n=256).replace(
             vel="const", v0=2000.0, k=0.0, weight="ta", aa_spacing=25.0, name="3d-const2000-ta-aa25-10000tr-256cube"),
+        # the headline survey with operator anti-aliasing for the 25 m receiver spacing
+        "3d-vz-aa-100k-256cube": lambda: sv.survey_3d_gradient().replace(
+            aa_spacing=25.0, name="3d-vz-aa25-100000tr-256cube"),
+        "3d-vz-aa-10k-256cube": lambda: sv.survey_3d_gradient(ntr=10_000, n=256).replace(
+            aa_spacing=25.0, name="3d-vz-aa25-10000tr-256cube"),
         "25d-velan-4608tr-128x100": lambda: sv.survey_25d_velan(),
         "3d-pstm-100k-256cube": lambda: sv.survey_3d_gradient().replace(
             vel="pstm", oz=0.0, dz=0.012, name="3d-pstm-100000tr-256x256x256t"),
@@ -881,6 +888,11 @@ def run_forms(args, s, ws, rank, local, dev, cache, head):
     r = run_single(targs, workloads()[targs.workload](), ws, rank, local, dev, ccache, **k)
     if rank == 0:
         forms["true_amplitude_anti_aliased_const_v"] = _form(r)
+    # the headline v(z) survey and traces with operator anti-aliasing
+    targs.workload = "3d-vz-aa-100k-256cube"
+    r = run_single(targs, workloads()[targs.workload](), ws, rank, local, dev, ccache, **k)
+    if rank == 0:
+        forms["anti_aliased_vz"] = _form(r)
     cache.clear()
     torch.cuda.empty_cache()
     surveys = workloads()["batch64-3d-vz"]()

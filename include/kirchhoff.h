@@ -137,17 +137,21 @@ typedef struct {
                                 (1 - taper) A; in [0, 1), 0 = a hard mask; ignored without an
                                 aperture.  Every operator (migrate, demigrate, velocity gradient)
                                 applies it, so they stay each other's transpose and derivative. */
-    double aa_spacing;       /* operator anti-aliasing, KH_VEL_CONST only: the trace (midpoint)
-                                spacing in metres, 0 = off.  With p = ((x - x_s)_h / R_s +
-                                (x - x_r)_h / R_r) / (v0 dt), the midpoint gradient of the two-way
-                                time in samples per metre, the moveout between adjacent traces is
-                                L = aa_spacing max(|p_x|, |p_y|) samples; the weight keeps L <= 1,
-                                removes L >= 2 and falls as cos^2(pi (L - 1) / 2) between (dip
-                                limitation of the operator: the aliased part of the sum is dropped).
-                                Migrate and demigrate, and the allocation-free entry point; the
-                                velocity gradient and the batched launch refuse it
-                                (KH_ERR_UNSUPPORTED).  Negative or not finite: KH_ERR_INVALID_ARG;
-                                > 0 with another velocity kind: KH_ERR_UNSUPPORTED. */
+    double aa_spacing;       /* operator anti-aliasing, KH_VEL_CONST and KH_VEL_LINEAR_Z: the trace
+                                (midpoint) spacing in metres, 0 = off.  With p the midpoint gradient
+                                of the two-way time in samples per metre, p = (g_s + g_r) / dt, g_a
+                                the horizontal gradient of leg a's time at the image point
+                                ((x - x_a)_h / (v0 R_a) at constant velocity; (x - x_a)_h /
+                                (R_a sqrt(v0 v(z) + k^2 R_a^2 / 4)) for v0 + k z), the moveout
+                                between adjacent traces is L = aa_spacing max(|p_x|, |p_y|)
+                                samples; the weight keeps L <= 1, removes L >= 2 and falls as
+                                cos^2(pi (L - 1) / 2) between (dip limitation of the operator: the
+                                aliased part of the sum is dropped).  Migrate and demigrate, and
+                                the allocation-free entry point; the velocity gradient and the
+                                batched launch refuse it (KH_ERR_UNSUPPORTED), and so does
+                                KH_VEL_LINEAR_Z (k != 0) with 16-bit traces.  Negative or not
+                                finite: KH_ERR_INVALID_ARG; > 0 with another velocity kind:
+                                KH_ERR_UNSUPPORTED. */
 } kh_desc;
 
 typedef struct kh_plan_s* kh_plan;

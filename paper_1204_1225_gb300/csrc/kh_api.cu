@@ -302,8 +302,10 @@ static kh_status validate_desc(const kh_desc* d)
     if (!(d->taper >= 0.0 && d->taper < 1.0)) return fail(KH_ERR_INVALID_ARG, "taper must be in [0, 1)");
     if (!(d->aa_spacing >= 0.0) || !std::isfinite(d->aa_spacing))
         return fail(KH_ERR_INVALID_ARG, "aa_spacing must be finite and >= 0");
-    if (d->aa_spacing > 0.0 && d->vel != KH_VEL_CONST)
-        return fail(KH_ERR_UNSUPPORTED, "operator anti-aliasing is built for constant velocity only");
+    if (d->aa_spacing > 0.0 && d->vel != KH_VEL_CONST && d->vel != KH_VEL_LINEAR_Z)
+        return fail(KH_ERR_UNSUPPORTED, "operator anti-aliasing is built for KH_VEL_CONST and KH_VEL_LINEAR_Z");
+    if (d->aa_spacing > 0.0 && d->vel == KH_VEL_LINEAR_Z && d->k != 0.0 && d->trace_dtype != KH_F32)
+        return fail(KH_ERR_UNSUPPORTED, "operator anti-aliasing with v0 + k z takes FP32 traces");
     const int ealign = 16 / dtype_size(d->trace_dtype);
     const int cap = std::max((d->nt + 3 * ealign) / ealign * ealign, 16384 / 4);
     if ((size_t)kh::STAGES * cap * dtype_size(d->trace_dtype) > 160u * 1024u)
@@ -351,7 +353,13 @@ static GeomParams geom_of(const kh_desc& d)
     g.ap_core2 = g.use_taper ? (float)((1.0 - d.taper) * d.aperture * (1.0 - d.taper) * d.aperture) : 0.f;
     g.ap_invband = g.use_taper ? (float)(1.0 / (d.taper * d.aperture)) : 0.f;
     g.A2cull = (float)((d.aperture * (1.0 + 1e-5) + 1.0) * (d.aperture * (1.0 + 1e-5) + 1.0));
-    g.aa_c = (d.vel == KH_VEL_CONST && d.aa_spacing > 0.0) ? (float)(d.aa_spacing / (d.v0 * d.dt)) : 0.f;
+    // anti-aliasing: the constant-velocity kernels take p = sum (x - a)_h / R_a scaled by 1 / (v0 dt),
+    // the v0 + k z kernels p = sum (x - a)_h f_a with each leg's slowness factor f_a, scaled by 1 / dt
+    const bool aa = (d.vel == KH_VEL_CONST || d.vel == KH_VEL_LINEAR_Z) && d.aa_spacing > 0.0;
+    g.aa_c = !aa ? 0.f : (g.k == 0.0 ? (float)(d.aa_spacing / (d.v0 * d.dt)) : (float)(d.aa_spacing / d.dt));
+    g.aa_v0sq = (float)(d.v0 * d.v0);
+    g.aa_v0k = (float)(d.v0 * g.k);
+    g.aa_kq = (float)(0.25 * g.k * g.k);
     g.nt = d.nt;
     g.esize = dtype_size(d.trace_dtype);
     g.tdtype = (int)d.trace_dtype;

@@ -43,6 +43,8 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
     k_demigrate(GeomParams g, DmTile dt, TraceSet tr, const float* __restrict__ image,
                 float* __restrict__ partial, int* status)
 {
+    constexpr int WB = WGT & 3;                 // the weight (KH_W_*)
+    constexpr bool AA = (WGT & W_AA) != 0;      // operator anti-aliasing compiled in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DmSmem& S = *reinterpret_cast<DmSmem*>(smem_raw);
     const int b = blockIdx.y, part = blockIdx.z;
@@ -120,6 +122,8 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
         }
         // window-relative time th = tau - lo; valid iff 0 <= th <= hi - lo
         const float c0rel = (float)(tau_ref - (double)lo);
+        // anti-aliasing with v0 + k z: the tile's first depth and the depth step
+        const float aa_z0 = (float)grid_coord(g.oz, z0, g.dz), aa_dz = (float)g.dz;
         const float lim = (float)(hi - lo);
         const float cmid = 0.5f * lim, chalf = 0.5f * lim + EDGE_EPS;
 
@@ -177,10 +181,10 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                         const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
                         const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                         const bool v = fabsf(th - cmid) <= chc;
-                        float W = (WGT == 1) ? zc.y * Ssum
-                                  : (WGT == 2) ? (zc.w != 0.f ? ta_weight<FAST>(zc.z, Rs, Rr, g.dim == 3) : 0.f)
+                        float W = (WB == 1) ? zc.y * Ssum
+                                  : (WB == 2) ? (zc.w != 0.f ? ta_weight<FAST>(zc.z, Rs, Rr, g.dim == 3) : 0.f)
                                                : 1.f;
-                        if (g.aa_c > 0.f) W *= aa_weight<FAST>(g.aa_c, dxs, dys, dxr, dyr, Rs, Rr);
+                        if constexpr (AA) W *= aa_weight<FAST>(g.aa_c, dxs, dys, dxr, dyr, Rs, Rr);
                         const float wm = v ? tp * W * mz : 0.f;
                         const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                         const float a1 = wm * f;
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
                                     const float exs = cxf - sgx, eys = cyf - sgy;
                                     const float dhs2 = fmaf(exs, exs, eys * eys);
                                     float sqs = 0.f;
-                                    const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, S.zc[izc], rsg, sqs);
+                                    const float rho_s = leg_delta_m<WB, FAST>(dPs, dhs2, S.zc[izc], rsg, sqs);
                                     S.src[warp][gi][lane] = make_float2(leg_log<LPT>(rho_s, g, 0.f), sqs);
                                 }
                             }
@@ -227,13 +231,21 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
 #pragma unroll 4
                             for (int j = 0; j < nzh; ++j) {
                                 float sqr = 0.f;
-                                const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
+                                const float rho_r = leg_delta_m<WB, FAST>(dPr, dhr2, zk, rr, sqr);
                                 const float th = leg_log<LPT>(rho_r, g, c0rel + sv.x);
                                 const float tc = fmaxf(th, 0.f);   // within EDGE_EPS below 0: the first row
                                 const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
                                 const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                                 const bool v = fabsf(th - cmid) <= chc;
-                                const float W = (WGT == 1) ? wz * (sv.y + sqr) : 1.f;
+                                float W = (WB == 1) ? wz * (sv.y + sqr) : 1.f;
+                                if constexpr (AA) {   // anti-aliasing: both legs' slowness factors at this depth
+                                    const float zi = fmaf((float)(hz + j), aa_dz, aa_z0);
+                                    const float vv = fmaf(g.aa_v0k, zi, g.aa_v0sq);
+                                    const float exs = cxf - h.x, eys = cyf - h.y;
+                                    const float fs = aa_leg_lin(fmaf(zi, zi, fmaf(exs, exs, eys * eys)), vv, g.aa_kq);
+                                    const float fr = aa_leg_lin(fmaf(zi, zi, dhr2), vv, g.aa_kq);
+                                    W *= aa_weight_r(g.aa_c, exs, eys, exr, eyr, fs, fr);
+                                }
                                 const float wm = v ? tp * W * mz : 0.f;
                                 const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                                 const float a1 = wm * f;
@@ -256,14 +268,21 @@ __global__ void __launch_bounds__(DM_THREADS, 4)
 #pragma unroll 4
                         for (int iz = 0; iz < dt.tz; ++iz) {
                             float sqs = 0.f, sqr = 0.f;
-                            const float rho_s = leg_delta_m<WGT, FAST>(dPs, dhs2, zk, rs, sqs);
-                            const float rho_r = leg_delta_m<WGT, FAST>(dPr, dhr2, zk, rr, sqr);
+                            const float rho_s = leg_delta_m<WB, FAST>(dPs, dhs2, zk, rs, sqs);
+                            const float rho_r = leg_delta_m<WB, FAST>(dPr, dhr2, zk, rr, sqr);
                             const float th = leg_log<LPT>(rho_r, g, c0rel + leg_log<LPT>(rho_s, g, 0.f));
                             const float tc = fmaxf(th, 0.f);   // within EDGE_EPS below 0: the first row
                             const float tm = __fadd_rd(tc, MAGIC);                 // MAGIC + floor(tc)
                             const float f = __fsub_rn(tc, __fsub_rn(tm, MAGIC));
                             const bool v = fabsf(th - cmid) <= chc;
-                            const float W = (WGT == 1) ? wz * (sqs + sqr) : 1.f;
+                            float W = (WB == 1) ? wz * (sqs + sqr) : 1.f;
+                            if constexpr (AA) {   // anti-aliasing (as above)
+                                const float zi = fmaf((float)iz, aa_dz, aa_z0);
+                                const float vv = fmaf(g.aa_v0k, zi, g.aa_v0sq);
+                                const float fs = aa_leg_lin(fmaf(zi, zi, dhs2), vv, g.aa_kq);
+                                const float fr = aa_leg_lin(fmaf(zi, zi, dhr2), vv, g.aa_kq);
+                                W *= aa_weight_r(g.aa_c, exs, eys, exr, eyr, fs, fr);
+                            }
                             const float wm = v ? tp * W * mz : 0.f;
                             const int row = v ? __float_as_int(tm) - MAGIC_BITS : 0;
                             const float a1 = wm * f;
@@ -328,6 +347,22 @@ cudaError_t launch_demigrate(const GeomParams& g, const DmTile& dt, const TraceS
                              const float* image, float* partial, int* status, int max_chunks,
                              int vel_kind, int fast, cudaStream_t s)
 {
+    if (g.aa_c > 0.f) {   // operator anti-aliasing: kernels of its own (the plan refuses other models)
+        const int key = (vel_kind == VK_LINEAR ? 6 : 0) + g.weight * 2 + (fast ? 1 : 0);
+        switch (key) {
+            case 0: return dm_launch_t<VK_CONST, W_AA | 0, false>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 1: return dm_launch_t<VK_CONST, W_AA | 0, true>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 2: return dm_launch_t<VK_CONST, W_AA | 1, false>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 3: return dm_launch_t<VK_CONST, W_AA | 1, true>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 4: return dm_launch_t<VK_CONST, W_AA | 2, false>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 5: return dm_launch_t<VK_CONST, W_AA | 2, true>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 6: return dm_launch_t<VK_LINEAR, W_AA | 0, false>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 7: return dm_launch_t<VK_LINEAR, W_AA | 0, true>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 8: return dm_launch_t<VK_LINEAR, W_AA | 1, false>(g, dt, tr, image, partial, status, max_chunks, s);
+            case 9: return dm_launch_t<VK_LINEAR, W_AA | 1, true>(g, dt, tr, image, partial, status, max_chunks, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (g.weight == KH_W_TRUE_AMP) {   // constant velocity only (the plan refuses the others)
         if (vel_kind != VK_CONST) return cudaErrorInvalidValue;
         return fast ? dm_launch_t<VK_CONST, 2, true>(g, dt, tr, image, partial, status, max_chunks, s)

@@ -213,22 +213,19 @@ __device__ __forceinline__ float aa_weight(float aa_c, float dxs, float dys, flo
 }
 
 // Warp-uniform class of the anti-aliasing weight over one trace's contributions to the active
-// lanes' columns at squared depths z^2 in [z2lo, z2hi]: 0 every weight is 0 (L >= 2), 1 every
-// weight is 1 (L <= 1), 2 mixed.  A component a / R_s + b / R_r of p (a, b: the column's
-// horizontal offsets from source and receiver along one axis) has terms of fixed sign whose size
-// |a| / sqrt(h^2 + z^2) falls with depth: the component is at most its terms' sizes at the
-// shallowest depth summed, and at least, over the whole range, their sizes at the deepest depth
-// summed where a and b share a sign, else the larger of (deepest size of one term) - (shallowest
-// size of the other).  Classes decided on these bounds differ from the per-contribution weight only
-// where FP32 rounding puts L at 1 or 2, where the weight's slope is 0.
-__device__ __forceinline__ int aa_class(float aa_c, float dxs, float dys, float dxr, float dyr, float z2lo,
-                                        float z2hi, bool active)
+// lanes' columns over a range of depths: 0 every weight is 0 (L >= 2), 1 every weight is 1
+// (L <= 1), 2 mixed.  A component a f_s + b f_r of p (a, b: the column's horizontal offsets from
+// source and receiver along one axis, f_a the leg's factor at the depth) has terms of fixed sign
+// whose size falls with depth when f_a does: the component is at most its terms' sizes at the
+// shallowest depth (fs0, fr0) summed, and at least, over the whole range, their sizes at the
+// deepest depth (fs1, fr1) summed where a and b share a sign, else the larger of (deepest size of
+// one term) - (shallowest size of the other).  Classes decided on these bounds differ from the
+// per-contribution weight only where FP32 rounding puts L at 1 or 2, where the weight's slope is 0.
+__device__ __forceinline__ int aa_class_f(float aa_c, float dxs, float dys, float dxr, float dyr, float fs0,
+                                          float fs1, float fr0, float fr1, bool active)
 {
-    const float hs2 = fmaf(dxs, dxs, dys * dys), hr2 = fmaf(dxr, dxr, dyr * dyr);
-    const float is0 = rsqrtf(fmaxf(hs2 + z2lo, 1e-30f)), is1 = rsqrtf(fmaxf(hs2 + z2hi, 1e-30f));
-    const float ir0 = rsqrtf(fmaxf(hr2 + z2lo, 1e-30f)), ir1 = rsqrtf(fmaxf(hr2 + z2hi, 1e-30f));
     auto comp = [&](float a, float b, float& ub, float& lb) {
-        const float a0 = fabsf(a) * is0, a1 = fabsf(a) * is1, b0 = fabsf(b) * ir0, b1 = fabsf(b) * ir1;
+        const float a0 = fabsf(a) * fs0, a1 = fabsf(a) * fs1, b0 = fabsf(b) * fr0, b1 = fabsf(b) * fr1;
         ub = a0 + b0;
         lb = (a * b >= 0.f) ? a1 + b1 : fmaxf(fmaxf(a1 - b0, b1 - a0), 0.f);
     };
@@ -238,6 +235,40 @@ __device__ __forceinline__ int aa_class(float aa_c, float dxs, float dys, float 
     if (__all_sync(0xffffffffu, !active || aa_c * fmaxf(lbx, lby) >= 2.f)) return 0;
     if (__all_sync(0xffffffffu, !active || aa_c * fmaxf(ubx, uby) <= 1.f)) return 1;
     return 2;
+}
+
+// Constant velocity: f_a = 1 / R_a (1 / v0 is in aa_c), falling with z^2 over [z2lo, z2hi].
+__device__ __forceinline__ int aa_class(float aa_c, float dxs, float dys, float dxr, float dyr, float z2lo,
+                                        float z2hi, bool active)
+{
+    const float hs2 = fmaf(dxs, dxs, dys * dys), hr2 = fmaf(dxr, dxr, dyr * dyr);
+    return aa_class_f(aa_c, dxs, dys, dxr, dyr, rsqrtf(fmaxf(hs2 + z2lo, 1e-30f)), rsqrtf(fmaxf(hs2 + z2hi, 1e-30f)),
+                      rsqrtf(fmaxf(hr2 + z2lo, 1e-30f)), rsqrtf(fmaxf(hr2 + z2hi, 1e-30f)), active);
+}
+
+// v0 + k z: a leg's factor, the size of its time's horizontal gradient per metre of horizontal
+// offset, 1 / (R g sqrt(1 + s^2)) = 1 / sqrt(R^2 (v0 (v0 + k z) + k^2 R^2 / 4)) with R^2 = h^2 + z^2
+// (vv = v0 (v0 + k z), kq = k^2 / 4).
+__device__ __forceinline__ float aa_leg_lin(float R2, float vv, float kq)
+{
+    return rsqrtf(fmaxf(R2 * fmaf(kq, R2, vv), 1e-30f));
+}
+
+// v0 + k z over the depths [ztop, zbot]: for k >= 0 and ztop >= 0 both R^2 and v0 + k z grow with
+// depth, so each factor falls; otherwise no bound (every weight evaluated).
+__device__ __forceinline__ int aa_class_lin(const GeomParams& g, float dxs, float dys, float dxr, float dyr,
+                                            float ztop, float zbot, bool active)
+{
+    float fs0 = 3e38f, fs1 = 0.f, fr0 = 3e38f, fr1 = 0.f;
+    if (g.aa_v0k >= 0.f && ztop >= 0.f) {
+        const float hs2 = fmaf(dxs, dxs, dys * dys), hr2 = fmaf(dxr, dxr, dyr * dyr);
+        const float vv0 = fmaf(g.aa_v0k, ztop, g.aa_v0sq), vv1 = fmaf(g.aa_v0k, zbot, g.aa_v0sq);
+        fs0 = aa_leg_lin(fmaf(ztop, ztop, hs2), vv0, g.aa_kq);
+        fs1 = aa_leg_lin(fmaf(zbot, zbot, hs2), vv1, g.aa_kq);
+        fr0 = aa_leg_lin(fmaf(ztop, ztop, hr2), vv0, g.aa_kq);
+        fr1 = aa_leg_lin(fmaf(zbot, zbot, hr2), vv1, g.aa_kq);
+    }
+    return aa_class_f(g.aa_c, dxs, dys, dxr, dyr, fs0, fs1, fr0, fr1, active);
 }
 
 // Gridded model (KH_VEL_GRID): node column gi of image column ix in the tables' node grid and the

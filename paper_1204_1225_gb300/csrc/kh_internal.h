@@ -171,7 +171,9 @@ struct GeomParams {
     int use_taper;           // the weight tapers over the outer part of the aperture
     float ap_core, ap_core2; // radius (and its square) up to which the taper is 1
     float ap_invband;        // 1 / width of the taper band
-    float aa_c;              // operator anti-aliasing (constant v): aa_spacing / (v0 dt); 0 = off
+    float aa_c;              // operator anti-aliasing: aa_spacing / (v0 dt) (constant v), aa_spacing / dt
+                             // (v0 + k z, k != 0); 0 = off
+    float aa_v0sq, aa_v0k, aa_kq;   // v0 + k z: v0^2, v0 k and k^2 / 4 of the legs' slowness factor
     float A2cull;            // enlarged, for the conservative tile cull
     // traces
     int nt;

@@ -559,12 +559,19 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     const TT* ring = data - LEAD;
     const unsigned ring_last = (unsigned)(LEAD + STAGES * cap + SLACK - 2);   // the kernel's ring
     const bool zfull = izb + NZ <= g.nz;   // all 16 depths of this thread lie in the grid
-    // constant velocity with anti-aliasing: the range of z^2 over the thread's depths
-    float aa_z2lo = 0.f, aa_z2hi = 0.f;
-    if constexpr (AA) {
+    // anti-aliasing: constant velocity, the range of z^2 over the thread's depths; v0 + k z, the
+    // thread's first depth and the depth step, and its shallowest and deepest depths
+    float aa_z2lo = 0.f, aa_z2hi = 0.f, aa_z0 = 0.f, aa_dz = 0.f;
+    if constexpr (AA && VEL == VK_CONST) {
         const float za = zc[0].z, zb = zc[NZ - 1].z;
         aa_z2lo = (za <= 0.f && zb >= 0.f) ? 0.f : fminf(za * za, zb * zb);
         aa_z2hi = fmaxf(za * za, zb * zb);
+    } else if constexpr (AA && VEL == VK_LINEAR) {
+        aa_z0 = (float)grid_coord(g.oz, izb, g.dz);
+        aa_dz = (float)g.dz;
+        const float zl = (float)grid_coord(g.oz, izb + NZ - 1, g.dz);
+        aa_z2lo = fminf(aa_z0, zl);   // (shallowest, deepest) depth
+        aa_z2hi = fmaxf(aa_z0, zl);
     }
     // gridded model: the column's node column and fraction, and its first node row (threads
     // whose depths all lie below the image read the last rows)
@@ -873,6 +880,12 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 else if (g.use_taper) zloop(T_(), T_(), F_());
                 else zloop(T_(), F_(), F_());
             } else {
+                // anti-aliasing classes as in the constant-velocity branches
+                int aacls = 1;
+                if constexpr (AA && VEL == VK_LINEAR) {
+                    aacls = aa_class_lin(g, cxf - h.x, cyf - h.y, cxf - h.z, cyf - h.w, aa_z2lo, aa_z2hi, inside);
+                    if (aacls == 0) continue;
+                }
                 const float4 a = S.hda[s][t];
                 if (__float_as_uint(h.x) != psx || __float_as_uint(h.y) != psy) {   // new source
                     const float4 rs = S.refs[s][t];
@@ -892,7 +905,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 const float dPr = fmaf(dxc, cxf + a.z, dyc * (cyf + a.w));
                 const float exr = cxf - h.z, eyr = cyf - h.w;
                 const float dhr2 = fmaf(exr, exr, eyr * eyr);
-                auto zloop = [&](auto checked, auto tapered) {
+                auto zloop = [&](auto checked, auto tapered, auto alias) {
 #pragma unroll
                     for (int i = 0; i < NZ; ++i) {
                         float sqr = 0.f;
@@ -905,14 +918,35 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                         else
                             val = sample_unchecked<TT>(ring, th, w.y + LEAD, ring_last);
                         if constexpr (decltype(tapered)::value) val *= tp;
+                        if constexpr (decltype(alias)::value) {
+                            // each leg's slowness factor at this depth (FP32 geometry: the weight
+                            // is flat where rounding could move it)
+                            const float zi = fmaf((float)i, aa_dz, aa_z0);
+                            const float vv = fmaf(g.aa_v0k, zi, g.aa_v0sq);
+                            const float exs = cxf - h.x, eys = cyf - h.y;
+                            const float fs = aa_leg_lin(fmaf(zi, zi, fmaf(exs, exs, eys * eys)), vv, g.aa_kq);
+                            const float fr = aa_leg_lin(fmaf(zi, zi, dhr2), vv, g.aa_kq);
+                            val *= aa_weight_r(g.aa_c, exs, eys, exr, eyr, fs, fr);
+                        }
                         // gamma(z) multiplies the sum once, at the store
                         if constexpr (WB == 1) acc[i] = fmaf(sv.y + sqr, val, acc[i]);
                         else acc[i] += val;
                     }
                 };
-                if (unchecked) zloop(std::false_type(), std::false_type());
-                else if (g.use_taper) zloop(std::true_type(), std::true_type());
-                else zloop(std::true_type(), std::false_type());
+                using T_ = std::true_type;
+                using F_ = std::false_type;
+                bool done = false;
+                if constexpr (AA && VEL == VK_LINEAR) {
+                    if (aacls == 2) {
+                        if (unchecked) zloop(F_(), F_(), T_());
+                        else zloop(T_(), T_(), T_());
+                        done = true;
+                    }
+                }
+                if (done) {
+                } else if (unchecked) zloop(F_(), F_(), F_());
+                else if (g.use_taper) zloop(T_(), T_(), F_());
+                else zloop(T_(), F_(), F_());
             }
         }
         __syncwarp();
@@ -1269,7 +1303,20 @@ template <typename TT>
 cudaError_t launch_migrate_dtype(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
                                  float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
-    if (g.aa_c > 0.f) {   // operator anti-aliasing: constant velocity only (the plan refuses the others)
+    if (g.aa_c > 0.f) {   // operator anti-aliasing (constant velocity and v0 + k z; the plan refuses the others)
+        if (vel == VK_LINEAR) {   // v0 + k z: FP32 traces only (the plan refuses the others)
+            if constexpr (std::is_same<TT, float>::value) {
+                switch (g.weight * 2 + (fast ? 1 : 0)) {
+                    case 0: return launch_migrate_t<VK_LINEAR, W_AA | 0, false, TT>(g, t, tr, traces, image, w, s);
+                    case 1: return launch_migrate_t<VK_LINEAR, W_AA | 0, true, TT>(g, t, tr, traces, image, w, s);
+                    case 2: return launch_migrate_t<VK_LINEAR, W_AA | 1, false, TT>(g, t, tr, traces, image, w, s);
+                    case 3: return launch_migrate_t<VK_LINEAR, W_AA | 1, true, TT>(g, t, tr, traces, image, w, s);
+                    default: return cudaErrorInvalidValue;
+                }
+            } else {
+                return cudaErrorInvalidValue;
+            }
+        }
         if (vel != VK_CONST) return cudaErrorInvalidValue;
         switch (g.weight * 2 + (fast ? 1 : 0)) {
             case 0: return launch_migrate_t<VK_CONST, W_AA | 0, false, TT>(g, t, tr, traces, image, w, s);

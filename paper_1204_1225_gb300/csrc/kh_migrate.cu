@@ -1,5 +1,6 @@
 // Migration, batched-migration and velocity-gradient launches: dispatch on the trace type to
-// the per-type translation units (kh_migrate_<type>.cu, kh_batched_<type>.cu), the gradient
+// the per-type translation units (kh_migrate_<type>.cu, kh_migrate_aa_<type>.cu with operator
+// anti-aliasing, kh_batched_<type>.cu), the gradient
 // kernels (FP32 traces only, instantiated here) and the gradient's final sum.
 #include "kh_migrate_impl.cuh"
 
@@ -12,6 +13,10 @@ KH_MIGRATE_DECL(launch_migrate_f32)
 KH_MIGRATE_DECL(launch_migrate_pair)
 KH_MIGRATE_DECL(launch_migrate_f16)
 KH_MIGRATE_DECL(launch_migrate_bf16)
+KH_MIGRATE_DECL(launch_migrate_aa_f32)
+KH_MIGRATE_DECL(launch_migrate_aa_pair)
+KH_MIGRATE_DECL(launch_migrate_aa_f16)
+KH_MIGRATE_DECL(launch_migrate_aa_bf16)
 #undef KH_MIGRATE_DECL
 
 #define KH_BATCHED_DECL(name)                                                                            \
@@ -53,6 +58,16 @@ cudaError_t launch_migrate(const GeomParams& g, const TileShape& t, const TraceS
 {
     if (t.cz > MAX_ZG) return cudaErrorInvalidValue;
     if (g.pstm) vel_kind = VK_PSTM;   // time migration has kernels of its own
+    if (g.aa_c > 0.f) {   // operator anti-aliasing has kernels of its own
+        switch (g.tdtype) {
+            case KH_F32:
+                return g.pairs ? launch_migrate_aa_pair(g, t, tr, traces, image, vel_kind, fast_math, w, s)
+                               : launch_migrate_aa_f32(g, t, tr, traces, image, vel_kind, fast_math, w, s);
+            case KH_F16: return launch_migrate_aa_f16(g, t, tr, traces, image, vel_kind, fast_math, w, s);
+            case KH_BF16: return launch_migrate_aa_bf16(g, t, tr, traces, image, vel_kind, fast_math, w, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (g.tdtype) {
         case KH_F32:
             return g.pairs ? launch_migrate_pair(g, t, tr, traces, image, vel_kind, fast_math, w, s)

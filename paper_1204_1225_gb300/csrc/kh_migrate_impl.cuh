@@ -1299,35 +1299,42 @@ static cudaError_t launch_migrate_t(const GeomParams& g, const TileShape& t, con
     }
 }
 
+// Operator anti-aliasing (g.aa_c > 0): the kernels compiled with the W_AA bit, instantiated in
+// translation units of their own (kh_migrate_aa_<type>.cu) so that they build beside the others;
+// constant velocity for every trace type, v0 + k z for FP32 traces (the plan refuses the others).
+template <typename TT>
+cudaError_t launch_migrate_aa_t(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
+                                float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
+{
+    if (vel == VK_LINEAR) {   // v0 + k z: FP32 traces only (the plan refuses the others)
+        if constexpr (std::is_same<TT, float>::value || std::is_same<TT, SamplePair>::value) {
+            switch (g.weight * 2 + (fast ? 1 : 0)) {
+                case 0: return launch_migrate_t<VK_LINEAR, W_AA | 0, false, TT>(g, t, tr, traces, image, w, s);
+                case 1: return launch_migrate_t<VK_LINEAR, W_AA | 0, true, TT>(g, t, tr, traces, image, w, s);
+                case 2: return launch_migrate_t<VK_LINEAR, W_AA | 1, false, TT>(g, t, tr, traces, image, w, s);
+                case 3: return launch_migrate_t<VK_LINEAR, W_AA | 1, true, TT>(g, t, tr, traces, image, w, s);
+                default: return cudaErrorInvalidValue;
+            }
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    if (vel != VK_CONST) return cudaErrorInvalidValue;
+    switch (g.weight * 2 + (fast ? 1 : 0)) {
+        case 0: return launch_migrate_t<VK_CONST, W_AA | 0, false, TT>(g, t, tr, traces, image, w, s);
+        case 1: return launch_migrate_t<VK_CONST, W_AA | 0, true, TT>(g, t, tr, traces, image, w, s);
+        case 2: return launch_migrate_t<VK_CONST, W_AA | 1, false, TT>(g, t, tr, traces, image, w, s);
+        case 3: return launch_migrate_t<VK_CONST, W_AA | 1, true, TT>(g, t, tr, traces, image, w, s);
+        case 4: return launch_migrate_t<VK_CONST, W_AA | 2, false, TT>(g, t, tr, traces, image, w, s);
+        case 5: return launch_migrate_t<VK_CONST, W_AA | 2, true, TT>(g, t, tr, traces, image, w, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename TT>
 cudaError_t launch_migrate_dtype(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
                                  float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
-    if (g.aa_c > 0.f) {   // operator anti-aliasing (constant velocity and v0 + k z; the plan refuses the others)
-        if (vel == VK_LINEAR) {   // v0 + k z: FP32 traces only (the plan refuses the others)
-            if constexpr (std::is_same<TT, float>::value) {
-                switch (g.weight * 2 + (fast ? 1 : 0)) {
-                    case 0: return launch_migrate_t<VK_LINEAR, W_AA | 0, false, TT>(g, t, tr, traces, image, w, s);
-                    case 1: return launch_migrate_t<VK_LINEAR, W_AA | 0, true, TT>(g, t, tr, traces, image, w, s);
-                    case 2: return launch_migrate_t<VK_LINEAR, W_AA | 1, false, TT>(g, t, tr, traces, image, w, s);
-                    case 3: return launch_migrate_t<VK_LINEAR, W_AA | 1, true, TT>(g, t, tr, traces, image, w, s);
-                    default: return cudaErrorInvalidValue;
-                }
-            } else {
-                return cudaErrorInvalidValue;
-            }
-        }
-        if (vel != VK_CONST) return cudaErrorInvalidValue;
-        switch (g.weight * 2 + (fast ? 1 : 0)) {
-            case 0: return launch_migrate_t<VK_CONST, W_AA | 0, false, TT>(g, t, tr, traces, image, w, s);
-            case 1: return launch_migrate_t<VK_CONST, W_AA | 0, true, TT>(g, t, tr, traces, image, w, s);
-            case 2: return launch_migrate_t<VK_CONST, W_AA | 1, false, TT>(g, t, tr, traces, image, w, s);
-            case 3: return launch_migrate_t<VK_CONST, W_AA | 1, true, TT>(g, t, tr, traces, image, w, s);
-            case 4: return launch_migrate_t<VK_CONST, W_AA | 2, false, TT>(g, t, tr, traces, image, w, s);
-            case 5: return launch_migrate_t<VK_CONST, W_AA | 2, true, TT>(g, t, tr, traces, image, w, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
     if (g.weight == KH_W_TRUE_AMP) {   // constant velocity only (the plan refuses the others)
         if (vel != VK_CONST) return cudaErrorInvalidValue;
         return fast ? launch_migrate_t<VK_CONST, 2, true, TT>(g, t, tr, traces, image, w, s)

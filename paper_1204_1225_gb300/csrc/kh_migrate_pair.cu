@@ -6,27 +6,6 @@ namespace kh {
 cudaError_t launch_migrate_pair(const GeomParams& g, const TileShape& t, const TraceSet& tr, const void* traces,
                                 float* image, int vel, int fast, const WaitCfg& w, cudaStream_t s)
 {
-    if (g.aa_c > 0.f) {   // operator anti-aliasing (constant velocity and v0 + k z; the plan refuses the others)
-        if (vel == VK_LINEAR) {   // v0 + k z
-            switch (g.weight * 2 + (fast ? 1 : 0)) {
-                case 0: return launch_migrate_t<VK_LINEAR, W_AA | 0, false, SamplePair>(g, t, tr, traces, image, w, s);
-                case 1: return launch_migrate_t<VK_LINEAR, W_AA | 0, true, SamplePair>(g, t, tr, traces, image, w, s);
-                case 2: return launch_migrate_t<VK_LINEAR, W_AA | 1, false, SamplePair>(g, t, tr, traces, image, w, s);
-                case 3: return launch_migrate_t<VK_LINEAR, W_AA | 1, true, SamplePair>(g, t, tr, traces, image, w, s);
-                default: return cudaErrorInvalidValue;
-            }
-        }
-        if (vel != VK_CONST) return cudaErrorInvalidValue;
-        switch (g.weight * 2 + (fast ? 1 : 0)) {
-            case 0: return launch_migrate_t<VK_CONST, W_AA | 0, false, SamplePair>(g, t, tr, traces, image, w, s);
-            case 1: return launch_migrate_t<VK_CONST, W_AA | 0, true, SamplePair>(g, t, tr, traces, image, w, s);
-            case 2: return launch_migrate_t<VK_CONST, W_AA | 1, false, SamplePair>(g, t, tr, traces, image, w, s);
-            case 3: return launch_migrate_t<VK_CONST, W_AA | 1, true, SamplePair>(g, t, tr, traces, image, w, s);
-            case 4: return launch_migrate_t<VK_CONST, W_AA | 2, false, SamplePair>(g, t, tr, traces, image, w, s);
-            case 5: return launch_migrate_t<VK_CONST, W_AA | 2, true, SamplePair>(g, t, tr, traces, image, w, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
     if (g.weight == KH_W_TRUE_AMP) {   // constant velocity only (the plan refuses the others)
         if (vel != VK_CONST) return cudaErrorInvalidValue;
         return fast ? launch_migrate_t<VK_CONST, 2, true, SamplePair>(g, t, tr, traces, image, w, s)

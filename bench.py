@@ -83,6 +83,9 @@ PIPE_MIX = {
     # whose weight the warp's bounds prove 0 and that are skipped
     "3d-ta-aa-100k-256cube": {"issue": 19.03, "fma": 8.82, "alu": 5.03, "xu": 1.61, "lsu": 0.88},
     "3d-ta-aa-10k-256cube": {"issue": 19.03, "fma": 8.82, "alu": 5.03, "xu": 1.61, "lsu": 0.88},
+    # the headline survey with operator anti-aliasing (25 m spacing), per in-aperture pair
+    "3d-vz-aa-100k-256cube": {"issue": 24.51, "fma": 13.66, "alu": 5.21, "xu": 1.78, "lsu": 1.19},
+    "3d-vz-aa-10k-256cube": {"issue": 24.51, "fma": 13.66, "alu": 5.21, "xu": 1.78, "lsu": 1.19},
     # persistent batched kernel, constant velocity, sample pairs (measured on the 8-job small batch)
     "batch64-3d-vz-f32": {"issue": 23.35, "fma": 13.83, "alu": 3.46, "xu": 2.38, "lsu": 2.54},
 }
@@ -102,6 +105,7 @@ TRAFFIC = {
     "3d-pstm-10k-256cube": 87162880 + 1023754240,
     "3d-ta-10k-256cube": 93872128 + 1025078272,
     "3d-ta-aa-10k-256cube": 96422400 + 1025947136,
+    "3d-vz-aa-10k-256cube": 89446400 + 1035280384,
 }
 
 # Parity bars against the FP64 oracle (relative L2 over the sampled outputs): FP32 forms, and the

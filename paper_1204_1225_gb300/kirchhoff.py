@@ -503,15 +503,15 @@ class Plan:
         """Migration of host-resident inputs into a host image (kirchhoff_migrate_host): ``hdr``
         (sx, sy, rx, ry) CPU float32 tensors, ``traces`` a CPU tensor of the plan's trace dtype,
         ``out`` a CPU float32 tensor of the image shape, all pinned for overlap.  Only enqueues:
-        the tensors must stay alive and unchanged until ``host_join`` and a synchronisation of the
-        stream; consecutive calls overlap one call's copies with the other's migration."""
+        consecutive calls overlap one call's copies with the other's migration.  The plan holds
+        the tensors until ``sync`` (which waits for every copy); they must not change before."""
         hdr = tuple(hdr)
         ntr = int(hdr[0].numel())
         specs = [(t, name, torch.float32, ntr, None) for name, t in zip(("sx", "sy", "rx", "ry"), hdr)]
         specs += [(traces, "traces", self.trace_dtype, ntr * self.nt, None),
                   (out, "image", torch.float32, None, self.image_shape)]
         _validate_host(specs)
-        self._host_refs = getattr(self, "_host_refs", [])[-1:] + [(hdr, traces, out)]
+        self._host_refs = getattr(self, "_host_refs", []) + [(hdr, traces, out)]
         kirchhoff_migrate_host(self.handle, ntr, *hdr, traces, out, stream)
         return out
 
@@ -573,7 +573,12 @@ class Plan:
         return T
 
     def sync(self, stream=None):
+        """Waits for the plan's work on ``stream`` (and for every image of ``migrate_host``) and
+        raises if a kernel reported a timed-out wait or a skipped trace."""
+        if getattr(self, "_host_refs", None):
+            kirchhoff_host_join(self.handle, stream)
         kirchhoff_sync(self.handle, stream)
+        self._host_refs = []
 
     def profile(self, enable: bool = True):
         kirchhoff_profile(self.handle, enable)

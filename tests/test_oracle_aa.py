@@ -193,3 +193,18 @@ def test_aa_pins_catch_planted_mistakes(mutation, check):
             check()
     finally:
         oracle.set_mutation(0)
+
+
+@pytest.mark.parametrize("vel", ["const", "linear"])
+def test_migrate_and_demigrate_stay_transposes(vel):
+    # <L d, m> = <d, L^T m> in FP64 with the weight on (it multiplies W in both operators)
+    rng = np.random.default_rng(23)
+    kw = dict(v0=1800.0) if vel == "const" else dict(vel="linear", v0=1600.0, k=0.6)
+    s = sv.survey_random(rng, 3, 40, 9, 8, 12, 200, n_bins=2, h=15.0, aperture=120.0, **kw)
+    s = s.replace(aa_spacing=20.0, taper=0.3)
+    d = sv.random_traces(s, 5, smooth=3).astype(np.float64)
+    m = sv.random_image(s, 6).astype(np.float64)
+    lhs = float(np.vdot(oracle.migrate(s, d), m))
+    rhs = float(np.vdot(d, oracle.demigrate(s, m.astype(np.float32))))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs)) + 1e-14
+    assert not np.allclose(oracle.migrate(s.replace(aa_spacing=0.0), d), oracle.migrate(s, d))

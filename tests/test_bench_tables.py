@@ -34,3 +34,16 @@ def test_traffic_entries_are_measured_kernels():
     for key, nbytes in bench.TRAFFIC.items():
         assert key in bench.PIPE_MIX, key
         assert nbytes > 0
+
+
+def test_workload_models_match_their_surveys():
+    # the mix guard compares a run's (velocity, weight) with the workload's own: they must agree
+    wl = bench.workloads()
+    for name, (vel, weight) in bench.WORKLOAD_MODEL.items():
+        assert name in wl, name
+        s = wl[name]()
+        assert (s.vel, s.weight) == (vel, weight), name
+        assert (getattr(s, "aa_spacing", 0.0) > 0) == ("-aa-" in name), name
+    for key in bench.PIPE_MIX:
+        base = key.split("-table-")[0].replace("-demigrate", "").replace("-vgrad", "").replace("-f32", "")
+        assert base in wl or base.replace("3d-vz", "3d-pstm") in wl or base.startswith("batch"), key

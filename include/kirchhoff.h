@@ -391,8 +391,11 @@ KH_API kh_status kirchhoff_batch_info(kh_batch b, long long* n_items, int* n_cta
 /* Frees the batch's device workspace (synchronises the device through cudaFree). */
 KH_API kh_status kirchhoff_batch_destroy(kh_batch b);
 
-/* Waits for the plan's work on `cuda_stream` and returns KH_ERR_TIMEOUT if a bounded
- * in-kernel wait ran out since the last call (clearing the flag), else KH_OK. */
+/* Waits for the plan's work on `cuda_stream` and reports what its kernels flagged since the
+ * last call (clearing the flags): KH_ERR_TIMEOUT if a bounded in-kernel wait ran out (results
+ * invalid), KH_ERR_INVALID_ARG if a KH_VEL_GRID trace's position had no table (those traces were
+ * skipped), KH_ERR_INTERNAL for an internal sizing error, else KH_OK.  The image copies of
+ * kirchhoff_migrate_host run on the plan's own stream: join them first (kirchhoff_host_join). */
 KH_API kh_status kirchhoff_sync(kh_plan p, void* cuda_stream);
 
 /* Tuning and test options of a plan (kirchhoff_set_option).

@@ -1,6 +1,7 @@
 """Image-partitioned migration (one process per GPU, no exchange of partial sums), tested on CPU:
 the slab layout tiles the image exactly; two gloo ranks each migrate their slab of columns with
-the FP64 oracle and all-gather the slabs, and the assembled image equals the one-process image."""
+the FP64 oracle and all-gather the slabs, and the assembled image equals the one-process image
+(with the aperture taper and operator anti-aliasing on: both act per column)."""
 import os
 import socket
 import sys
@@ -41,6 +42,8 @@ def _survey():
     rng = np.random.default_rng(5)
     s = sv.survey_random(rng, 2, 60, 150, 1, 30, 300, vel="linear", weight="obliq", aperture=250.0,
                          n_bins=3, h=10.0, v0=1800.0, k=0.5)
+    # with the taper and operator anti-aliasing: both are per (column, trace), so slab-local
+    s = s.replace(taper=0.2, aa_spacing=20.0)
     return s, sv.random_traces(s, 3, smooth=5).astype(np.float64)
 
 
@@ -79,6 +82,7 @@ def test_two_ranks_gather_the_one_process_image():
     assert got.shape == want.shape
     assert np.count_nonzero(want) > 0
     assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    assert not np.allclose(oracle.migrate(s.replace(aa_spacing=0.0), d), want)   # the weight acts
     # the same assembly in one process
     parts = [oracle.migrate(partition.slab_survey(s, i0, n), d) for i0, n in partition.image_slabs(s, 2)]
     assert np.array_equal(partition.assemble(parts, s), got)

@@ -559,19 +559,19 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
     const TT* ring = data - LEAD;
     const unsigned ring_last = (unsigned)(LEAD + STAGES * cap + SLACK - 2);   // the kernel's ring
     const bool zfull = izb + NZ <= g.nz;   // all 16 depths of this thread lie in the grid
-    // anti-aliasing: constant velocity, the range of z^2 over the thread's depths; v0 + k z, the
-    // thread's first depth and the depth step, and its shallowest and deepest depths
-    float aa_z2lo = 0.f, aa_z2hi = 0.f, aa_z0 = 0.f, aa_dz = 0.f;
+    // anti-aliasing: the range [aa_lo, aa_hi] of z^2 over the thread's depths (constant velocity)
+    // or of z (v0 + k z, with the thread's first depth aa_z0 and the depth step aa_dz)
+    float aa_lo = 0.f, aa_hi = 0.f, aa_z0 = 0.f, aa_dz = 0.f;
     if constexpr (AA && VEL == VK_CONST) {
         const float za = zc[0].z, zb = zc[NZ - 1].z;
-        aa_z2lo = (za <= 0.f && zb >= 0.f) ? 0.f : fminf(za * za, zb * zb);
-        aa_z2hi = fmaxf(za * za, zb * zb);
+        aa_lo = (za <= 0.f && zb >= 0.f) ? 0.f : fminf(za * za, zb * zb);
+        aa_hi = fmaxf(za * za, zb * zb);
     } else if constexpr (AA && VEL == VK_LINEAR) {
         aa_z0 = (float)grid_coord(g.oz, izb, g.dz);
         aa_dz = (float)g.dz;
         const float zl = (float)grid_coord(g.oz, izb + NZ - 1, g.dz);
-        aa_z2lo = fminf(aa_z0, zl);   // (shallowest, deepest) depth
-        aa_z2hi = fmaxf(aa_z0, zl);
+        aa_lo = fminf(aa_z0, zl);
+        aa_hi = fmaxf(aa_z0, zl);
     }
     // gridded model: the column's node column and fraction, and its first node row (threads
     // whose depths all lie below the image read the last rows)
@@ -770,7 +770,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 // per contribution only where the warp's depth range holds weights below 1
                 int aacls = 1;
                 if constexpr (AA) {
-                    aacls = aa_class(g.aa_c, dxs, dys, dxr, dyr, aa_z2lo, aa_z2hi, inside);
+                    aacls = aa_class(g.aa_c, dxs, dys, dxr, dyr, aa_lo, aa_hi, inside);
                     if (aacls == 0) continue;
                 }
                 const float dhs2 = fmaf(dxs, dxs, dys * dys);
@@ -815,7 +815,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 // anti-aliasing classes as in the direct branch
                 int aacls = 1;
                 if constexpr (AA) {
-                    aacls = aa_class(g.aa_c, cxf - h.x, cyf - h.y, cxf - h.z, cyf - h.w, aa_z2lo, aa_z2hi, inside);
+                    aacls = aa_class(g.aa_c, cxf - h.x, cyf - h.y, cxf - h.z, cyf - h.w, aa_lo, aa_hi, inside);
                     if (aacls == 0) continue;
                 }
                 const float4 a = S.hda[s][t];
@@ -883,7 +883,7 @@ __device__ __forceinline__ int mig_consumer(MigSmem& S, const TT* data, const Ge
                 // anti-aliasing classes as in the constant-velocity branches
                 int aacls = 1;
                 if constexpr (AA && VEL == VK_LINEAR) {
-                    aacls = aa_class_lin(g, cxf - h.x, cyf - h.y, cxf - h.z, cyf - h.w, aa_z2lo, aa_z2hi, inside);
+                    aacls = aa_class_lin(g, cxf - h.x, cyf - h.y, cxf - h.z, cyf - h.w, aa_lo, aa_hi, inside);
                     if (aacls == 0) continue;
                 }
                 const float4 a = S.hda[s][t];
